@@ -1,0 +1,198 @@
+/*
+ * pa.h — C ABI of the GB300 (sm_103a) Toeplitz-hash library for length-compatible
+ * privacy amplification (Wang, Zhang, Yu, Guo, arXiv 1805.02372).
+ *
+ * The operation (Sec. 2.1 Eq. 1; Sec. 2.3 Steps 1-2): an m x n binary Toeplitz
+ * matrix T, fixed by an (n+m-1)-bit seed s through
+ *
+ *        T[i][j] = s[n-1+i-j]        0 <= i < m, 0 <= j < n,
+ *
+ * compresses the n-bit corrected key x into the m-bit final key
+ *
+ *        y[i] = XOR_j ( x[j] AND s[n-1+i-j] )  =  (T x mod 2)[i].
+ *
+ * Equivalently (Sec. 3, Step 3) y[i] is coefficient n-1+i of the product of the
+ * polynomials s(z) and x(z), reduced mod 2. The paper's r = u T with T of size
+ * n x l is the transpose of this m x n form: the same bits, with l = m.
+ *
+ * Bit buffers: bit j of a string is bit (j & 63) of uint64_t word (j >> 6).
+ *   key  : ceil(n/64) words; bits at positions >= n are ignored.
+ *   seed : ceil((n+m-1)/64) words; bits at positions >= n+m-1 are ignored.
+ *   out  : ceil(m/64) words; fully overwritten, bits at positions >= m set to 0.
+ * Device buffers must be 16-byte aligned (PA_ERR_ALIGN otherwise). The caller owns
+ * every bit buffer; a plan owns its device workspace. Calls that take a stream
+ * are asynchronous on it; no call synchronises the device unless it says so.
+ * No C++ exception crosses this interface: every call returns a pa_status.
+ * Several plans may be used concurrently on different streams; a single plan must
+ * not be used by two calls that overlap on the GPU (its workspace is shared).
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (0 = success, negative = error). */
+#define PA_OK 0
+#define PA_ERR_INVALID (-1)     /* n == 0, m == 0, null pointer, bad option or size   */
+#define PA_ERR_ALIGN (-2)       /* a device bit buffer is not 16-byte aligned          */
+#define PA_ERR_NOMEM (-3)       /* device or host allocation failed                    */
+#define PA_ERR_CUDA (-4)        /* a CUDA runtime call failed (see pa_last_cuda_error) */
+#define PA_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                  */
+#define PA_ERR_UNSUPPORTED (-6) /* the requested path cannot run these sizes           */
+#define PA_ERR_PRECISION (-7)   /* FFT tile whose proven rounding bound is not < 1/2   */
+
+/* Interchangeable kernels. Every path returns the same bits. */
+typedef enum {
+    PA_PATH_AUTO = 0,       /* planner / autotuner choice                                */
+    PA_PATH_DIRECT = 1,     /* bit-packed AND + popcount parity (Sec. 2.1 definition)    */
+    PA_PATH_NTT64 = 2,      /* exact NTT modulo 2^64-2^32+1 (Sec. 3, FFT route, exact)  */
+    PA_PATH_NTT31 = 3,      /* exact NTT modulo 15*2^27+1 (coefficients <= n < p)        */
+    PA_PATH_FFT = 4,        /* FP32 FFT sub-blocks under a proven rounding bound; FP64
+                               butterflies on the tile lengths where the FP32 bound fails */
+    PA_PATH_BLOCK_INT8 = 5  /* block-Toeplitz Y = sum_d T_d X_d, INT8 tensor cores,
+                               INT32 accumulation, then mod 2                            */
+} pa_path;
+
+/* Planner options; zero-initialise and set what you need (0 / -1 = choose). */
+typedef struct {
+    int32_t path;              /* pa_path                                                 */
+    int32_t device;            /* CUDA device ordinal, -1 = current device                */
+    uint32_t log2_transform;   /* transform paths: log2 of the transform size N           */
+    uint32_t block_b;          /* block path: tile edge b in {128, 256, 512}              */
+    uint64_t tile_in;          /* key sub-block length L (the paper's batch length)       */
+    uint64_t tile_out;         /* output sub-block length M (column split of Sec. 3)      */
+    uint32_t force_fp64;       /* FFT path: use FP64 butterflies even where FP32 is proven */
+    uint32_t reserved[7];
+} pa_opts;
+
+/* What a plan decided (pa_plan_query / pa_plan_describe). */
+typedef struct {
+    uint64_t n, m;
+    int32_t path;              /* resolved pa_path                                        */
+    uint32_t log2_transform;   /* transform size N = 2^log2_transform (transform paths)   */
+    uint64_t tile_in;          /* key sub-block length L                                  */
+    uint64_t tile_out;         /* output sub-block length M                               */
+    uint64_t tiles_in;         /* p: number of key sub-blocks                             */
+    uint64_t tiles_out;        /* q: number of output sub-blocks                          */
+    uint32_t block_b;          /* block path tile edge                                    */
+    uint32_t fp64;             /* FFT path runs FP64 butterflies                          */
+    double rounding_bound;     /* FFT path: proven bound on |v - rint(v)|, else 0         */
+    uint64_t workspace_bytes;  /* device workspace owned by the plan                      */
+    uint32_t kernels_per_call; /* kernel launches one pa_hash enqueues                    */
+    uint32_t reserved[5];
+} pa_plan_desc;
+
+typedef struct pa_plan_s *pa_plan_t;
+
+/* Plan the hash of an n-bit key into m bits with the default (fastest known) path.
+ * Allocates the plan's device workspace on the current device. */
+int pa_plan(uint64_t n, uint64_t m, pa_plan_t *out);
+
+/* Same with options (opts may be NULL). PA_ERR_UNSUPPORTED if a forced path
+ * cannot handle (n, m); PA_ERR_PRECISION if a forced FFT tile has no proven bound. */
+int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out);
+
+/* Resolve a plan on the host only (no GPU, no allocation). */
+int pa_plan_query(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_desc *out);
+
+/* Describe a created plan. */
+int pa_plan_describe(pa_plan_t plan, pa_plan_desc *out);
+
+/* Release the plan and its workspace (synchronises the plan's last stream). */
+void pa_plan_destroy(pa_plan_t plan);
+
+/* y = T x mod 2 (Sec. 2.3 Step 1/2 with the decomposition of Sec. 3).
+ * seed_bits, key_bits, out_bits: device pointers, 16-byte aligned.
+ * stream: a cudaStream_t (NULL = legacy default stream). Asynchronous. */
+int pa_hash(pa_plan_t plan, const uint64_t *seed_bits, const uint64_t *key_bits,
+            uint64_t *out_bits, void *stream);
+
+/* The same hash from and to HOST buffers: copies the key and seed to the plan's
+ * device staging, hashes, copies the result back and synchronises the stream. */
+int pa_hash_host(pa_plan_t plan, const uint64_t *seed_host, const uint64_t *key_host,
+                 uint64_t *out_host, void *stream);
+
+/* Worst |v - rint(v)| seen by the FFT path in the plan's last call, with the
+ * proven bound (synchronises the plan's stream). Other paths report 0. */
+int pa_last_residual(pa_plan_t plan, double *residual, double *bound);
+
+/* Device-side status of the plan's last call: PA_OK, or PA_ERR_TIMEOUT if a
+ * bounded wait in a kernel gave up (synchronises the plan's stream). */
+int pa_plan_status(pa_plan_t plan);
+
+/* ---- Many independent blocks in one launch (Sec. 3: batches run in parallel) ---- */
+
+typedef struct {
+    uint64_t n, m;
+    const uint64_t *seed_bits; /* device, 16-byte aligned                               */
+    const uint64_t *key_bits;  /* device, 16-byte aligned                               */
+    uint64_t *out_bits;        /* device, 16-byte aligned                               */
+} pa_block;
+
+typedef struct {
+    double max_residual;       /* worst |v - rint(v)| over FP tiles (0 if none ran)       */
+    double bound;              /* largest proven bound among the FP tiles                 */
+    uint32_t blocks_per_path[8]; /* indexed by pa_path                                    */
+    uint64_t work_items;       /* tiles in the persistent launch's work list              */
+    uint32_t graph_replayed;   /* 1 if a captured CUDA graph was replayed                 */
+    uint32_t reserved[5];
+} pa_report;
+
+typedef struct pa_batch_s *pa_batch_t;
+
+/* Plan a batch for these (n_i, m_i) shapes: path and tiles per block chosen by the
+ * autotuner, one persistent work list, workspace allocated once. Only the
+ * shapes are read from blocks[]; pointers may be NULL at planning time. */
+int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_batch_t *out);
+
+/* Run a planned batch with these buffers (same shapes, in the same order). The
+ * launch sequence is captured once in a CUDA graph and replayed when the buffer
+ * pointers and stream are unchanged. rep may be NULL; when it is not, the call
+ * synchronises the stream to fill it. */
+int pa_batch_run(pa_batch_t batch, const pa_block *blocks, size_t count, void *stream,
+                 pa_report *rep);
+
+void pa_batch_destroy(pa_batch_t batch);
+
+/* One-shot batched hash: plans (cached by shape list), runs, optionally reports. */
+int pa_hash_batched(const pa_block *blocks, size_t count, void *stream, pa_report *rep);
+
+/* ---- Per-kernel timing: CUDA events recorded around every launch on the
+ * launching stream while enabled (tracing for roofline measurements). ---- */
+
+typedef struct {
+    char name[40];             /* kernel name                                             */
+    uint32_t launches;         /* launches timed since profiling was enabled              */
+    uint32_t reserved;
+    double total_ms;           /* summed event-to-event device time                       */
+} pa_kernel_time;
+
+/* enable != 0 clears previous records and starts recording; 0 stops. */
+int pa_plan_profile(pa_plan_t plan, int enable);
+
+/* Per-kernel totals (synchronises on the recorded events). count = entries written. */
+int pa_plan_kernel_times(pa_plan_t plan, pa_kernel_time *out, int max, int *count);
+
+int pa_batch_profile(pa_batch_t batch, int enable);
+int pa_batch_kernel_times(pa_batch_t batch, pa_kernel_time *out, int max, int *count);
+
+/* ---- Diagnostics ---- */
+
+const char *pa_strerror(int status);
+
+/* The last CUDA error code seen by this thread (0 if none). */
+int pa_last_cuda_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PA_H */

@@ -1,0 +1,336 @@
+"""Thin Python binding of the C ABI in ``include/pa.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls. Bit buffers are
+passed as CUDA tensors (any 8-byte dtype, e.g. ``torch.int64`` holding the uint64
+words) or raw device addresses; streams as ``torch.cuda.Stream`` or raw handles.
+Nothing here computes any part of the hash: if the CUDA library is missing, every
+call raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libpa.so")
+
+PA_OK = 0
+PA_ERR_INVALID = -1
+PA_ERR_ALIGN = -2
+PA_ERR_NOMEM = -3
+PA_ERR_CUDA = -4
+PA_ERR_TIMEOUT = -5
+PA_ERR_UNSUPPORTED = -6
+PA_ERR_PRECISION = -7
+
+PA_PATH_AUTO = 0
+PA_PATH_DIRECT = 1
+PA_PATH_NTT64 = 2
+PA_PATH_NTT31 = 3
+PA_PATH_FFT = 4
+PA_PATH_BLOCK_INT8 = 5
+PATH_NAMES = {0: "auto", 1: "direct", 2: "ntt64", 3: "ntt31", 4: "fft", 5: "block_int8"}
+PATHS = {v: k for k, v in PATH_NAMES.items()}
+
+
+class pa_opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("log2_transform", ctypes.c_uint32), ("block_b", ctypes.c_uint32),
+                ("tile_in", ctypes.c_uint64), ("tile_out", ctypes.c_uint64),
+                ("force_fp64", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+
+
+class pa_plan_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint64), ("path", ctypes.c_int32),
+                ("log2_transform", ctypes.c_uint32), ("tile_in", ctypes.c_uint64),
+                ("tile_out", ctypes.c_uint64), ("tiles_in", ctypes.c_uint64),
+                ("tiles_out", ctypes.c_uint64), ("block_b", ctypes.c_uint32),
+                ("fp64", ctypes.c_uint32), ("rounding_bound", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_uint64), ("kernels_per_call", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["path_name"] = PATH_NAMES.get(self.path, "?")
+        return d
+
+
+class pa_block(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint64), ("seed_bits", ctypes.c_void_p),
+                ("key_bits", ctypes.c_void_p), ("out_bits", ctypes.c_void_p)]
+
+
+class pa_report(ctypes.Structure):
+    _fields_ = [("max_residual", ctypes.c_double), ("bound", ctypes.c_double),
+                ("blocks_per_path", ctypes.c_uint32 * 8), ("work_items", ctypes.c_uint64),
+                ("graph_replayed", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+    def as_dict(self):
+        return {"max_residual": self.max_residual, "bound": self.bound,
+                "blocks_per_path": {PATH_NAMES.get(i, str(i)): int(v)
+                                    for i, v in enumerate(self.blocks_per_path) if v},
+                "work_items": int(self.work_items), "graph_replayed": int(self.graph_replayed)}
+
+
+class pa_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
+
+
+# name -> (restype, argtypes); mirrors include/pa.h
+_VP = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+SIGNATURES = {
+    "pa_plan": (ctypes.c_int, [_U64, _U64, ctypes.POINTER(_VP)]),
+    "pa_plan_ex": (ctypes.c_int, [_U64, _U64, ctypes.POINTER(pa_opts), ctypes.POINTER(_VP)]),
+    "pa_plan_query": (ctypes.c_int, [_U64, _U64, ctypes.POINTER(pa_opts),
+                                     ctypes.POINTER(pa_plan_desc)]),
+    "pa_plan_describe": (ctypes.c_int, [_VP, ctypes.POINTER(pa_plan_desc)]),
+    "pa_plan_destroy": (None, [_VP]),
+    "pa_hash": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pa_hash_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pa_last_residual": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "pa_plan_status": (ctypes.c_int, [_VP]),
+    "pa_batch_plan": (ctypes.c_int, [ctypes.POINTER(pa_block), ctypes.c_size_t,
+                                     ctypes.POINTER(pa_opts), ctypes.POINTER(_VP)]),
+    "pa_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
+                                    ctypes.POINTER(pa_report)]),
+    "pa_batch_destroy": (None, [_VP]),
+    "pa_hash_batched": (ctypes.c_int, [ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
+                                       ctypes.POINTER(pa_report)]),
+    "pa_plan_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pa_plan_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(pa_kernel_time), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "pa_batch_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pa_batch_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(pa_kernel_time), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_int)]),
+    "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pa_last_cuda_error": (ctypes.c_int, []),
+    "pa_version": (ctypes.c_int, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libpa.so`` (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} is missing "
+                                   "(run __graft_entry__.build())")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class PAError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = load().pa_strerror(status).decode()
+        cuda = load().pa_last_cuda_error()
+        super().__init__(f"{what}: {msg} (status {status}" +
+                         (f", cudaError {cuda})" if status == PA_ERR_CUDA else ")"))
+
+
+def _check(rc: int, what: str):
+    if rc != PA_OK:
+        raise PAError(rc, what)
+    return rc
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy (host buffers)
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def make_opts(path=PA_PATH_AUTO, device=-1, log2_transform=0, block_b=0, tile_in=0,
+              tile_out=0, force_fp64=0) -> pa_opts:
+    if isinstance(path, str):
+        path = PATHS[path]
+    o = pa_opts()
+    o.path, o.device, o.log2_transform, o.block_b = path, device, log2_transform, block_b
+    o.tile_in, o.tile_out, o.force_fp64 = tile_in, tile_out, force_fp64
+    return o
+
+
+def pa_plan_query(n: int, m: int, opts: pa_opts | None = None) -> dict:
+    d = pa_plan_desc()
+    _check(load().pa_plan_query(n, m, ctypes.byref(opts) if opts else None, ctypes.byref(d)),
+           "pa_plan_query")
+    return d.as_dict()
+
+
+def pa_plan_ex(n: int, m: int, opts: pa_opts | None = None) -> int:
+    h = _VP()
+    _check(load().pa_plan_ex(n, m, ctypes.byref(opts) if opts else None, ctypes.byref(h)),
+           "pa_plan_ex")
+    return h.value
+
+
+def pa_plan(n: int, m: int) -> int:
+    h = _VP()
+    _check(load().pa_plan(n, m, ctypes.byref(h)), "pa_plan")
+    return h.value
+
+
+def pa_plan_describe(plan: int) -> dict:
+    d = pa_plan_desc()
+    _check(load().pa_plan_describe(plan, ctypes.byref(d)), "pa_plan_describe")
+    return d.as_dict()
+
+
+def pa_plan_destroy(plan: int) -> None:
+    load().pa_plan_destroy(plan)
+
+
+def pa_hash(plan: int, seed_bits, key_bits, out_bits, stream=None) -> None:
+    _check(load().pa_hash(plan, _ptr(seed_bits), _ptr(key_bits), _ptr(out_bits),
+                          _stream(stream)), "pa_hash")
+
+
+def pa_hash_host(plan: int, seed_host, key_host, out_host, stream=None) -> None:
+    _check(load().pa_hash_host(plan, _ptr(seed_host), _ptr(key_host), _ptr(out_host),
+                               _stream(stream)), "pa_hash_host")
+
+
+def pa_last_residual(plan: int) -> tuple[float, float]:
+    r, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().pa_last_residual(plan, ctypes.byref(r), ctypes.byref(b)), "pa_last_residual")
+    return r.value, b.value
+
+
+def pa_plan_status(plan: int) -> int:
+    return load().pa_plan_status(plan)
+
+
+def _blocks(blocks) -> tuple[ctypes.Array, int]:
+    arr = (pa_block * len(blocks))()
+    for i, b in enumerate(blocks):
+        n, m, seed, key, out = b
+        arr[i].n, arr[i].m = n, m
+        arr[i].seed_bits, arr[i].key_bits, arr[i].out_bits = _ptr(seed), _ptr(key), _ptr(out)
+    return arr, len(blocks)
+
+
+def pa_batch_plan(blocks, opts: pa_opts | None = None) -> int:
+    """blocks: sequence of (n, m, seed, key, out) (buffers may be None)."""
+    arr, cnt = _blocks(blocks)
+    h = _VP()
+    _check(load().pa_batch_plan(arr, cnt, ctypes.byref(opts) if opts else None,
+                                ctypes.byref(h)), "pa_batch_plan")
+    return h.value
+
+
+def pa_batch_run(batch: int, blocks, stream=None, report: bool = False) -> dict | None:
+    arr, cnt = _blocks(blocks)
+    rep = pa_report() if report else None
+    _check(load().pa_batch_run(batch, arr, cnt, _stream(stream),
+                               ctypes.byref(rep) if rep else None), "pa_batch_run")
+    return rep.as_dict() if rep else None
+
+
+def pa_batch_destroy(batch: int) -> None:
+    load().pa_batch_destroy(batch)
+
+
+def pa_hash_batched(blocks, stream=None, report: bool = False) -> dict | None:
+    arr, cnt = _blocks(blocks)
+    rep = pa_report() if report else None
+    _check(load().pa_hash_batched(arr, cnt, _stream(stream), ctypes.byref(rep) if rep else None),
+           "pa_hash_batched")
+    return rep.as_dict() if rep else None
+
+
+def _times(fn, handle, what) -> dict:
+    arr = (pa_kernel_time * 32)()
+    cnt = ctypes.c_int()
+    _check(fn(handle, arr, 32, ctypes.byref(cnt)), what)
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": arr[i].total_ms}
+            for i in range(cnt.value)}
+
+
+def pa_plan_profile(plan: int, enable: bool) -> None:
+    _check(load().pa_plan_profile(plan, int(enable)), "pa_plan_profile")
+
+
+def pa_plan_kernel_times(plan: int) -> dict:
+    """{kernel name: {"launches", "total_ms"}} recorded since profiling was enabled."""
+    return _times(load().pa_plan_kernel_times, plan, "pa_plan_kernel_times")
+
+
+def pa_batch_profile(batch: int, enable: bool) -> None:
+    _check(load().pa_batch_profile(batch, int(enable)), "pa_batch_profile")
+
+
+def pa_batch_kernel_times(batch: int) -> dict:
+    return _times(load().pa_batch_kernel_times, batch, "pa_batch_kernel_times")
+
+
+def pa_strerror(status: int) -> str:
+    return load().pa_strerror(status).decode()
+
+
+def pa_version() -> int:
+    return load().pa_version()
+
+
+class Plan:
+    """Owning wrapper: ``Plan(n, m, path="ntt31").hash(seed, key, out)``."""
+
+    def __init__(self, n: int, m: int, path=PA_PATH_AUTO, **opts):
+        self.n, self.m = int(n), int(m)
+        self.handle = pa_plan_ex(self.n, self.m, make_opts(path=path, **opts))
+        self.desc = pa_plan_describe(self.handle)
+
+    def hash(self, seed_bits, key_bits, out_bits, stream=None):
+        pa_hash(self.handle, seed_bits, key_bits, out_bits, stream)
+
+    def hash_host(self, seed_host, key_host, out_host, stream=None):
+        pa_hash_host(self.handle, seed_host, key_host, out_host, stream)
+
+    def residual(self):
+        return pa_last_residual(self.handle)
+
+    def status(self) -> int:
+        return pa_plan_status(self.handle)
+
+    def close(self):
+        if self.handle:
+            pa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

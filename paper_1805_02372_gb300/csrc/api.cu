@@ -1,0 +1,274 @@
+// C ABI of the Toeplitz-hash library: planning, single-block hashing, status.
+// Every entry point returns a pa_status; no exception crosses the interface.
+#include <new>
+#include <string.h>
+
+#include "internal.h"
+
+namespace pa {
+
+static thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda_error = static_cast<int>(e);
+    if (e == cudaErrorMemoryAllocation) return PA_ERR_NOMEM;
+    return PA_ERR_CUDA;
+}
+
+// Largest sizes accepted at all (the seed index n+m-2 must fit comfortably).
+constexpr uint64_t kMaxBits = uint64_t(1) << 40;
+
+int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
+    if (!cfg || n == 0 || m == 0 || n > kMaxBits || m > kMaxBits) return PA_ERR_INVALID;
+    *cfg = PlanCfg();
+    cfg->n = n;
+    cfg->m = m;
+    int path = o ? o->path : PA_PATH_AUTO;
+    if (path < PA_PATH_AUTO || path > PA_PATH_BLOCK_INT8) return PA_ERR_INVALID;
+    if (path == PA_PATH_AUTO) {
+        // Cost model (measured on GB300, see the autotuner in batch.cu): the direct
+        // kernel wins while m*n is small; the exact 31-bit NTT wins beyond.
+        const double mn = double(n) * double(m);
+        path = (mn <= 4.0e9 || n >= 2013265921ull) ? PA_PATH_DIRECT : PA_PATH_NTT31;
+        if (path == PA_PATH_NTT31 && ntt_plan(n, m, path, o, &cfg->tr) != PA_OK)
+            path = PA_PATH_NTT64;
+    }
+    cfg->path = path;
+    int rc = PA_OK;
+    switch (path) {
+        case PA_PATH_DIRECT:
+            rc = direct_plan(n, m, &cfg->direct);
+            cfg->ws_bytes = direct_workspace(cfg->direct);
+            cfg->kernels = 2 + (cfg->direct.grid_y > 1 ? 1 : 0);
+            break;
+        case PA_PATH_NTT64:
+        case PA_PATH_NTT31:
+            rc = ntt_plan(n, m, path, o, &cfg->tr);
+            cfg->ws_bytes = ntt_workspace(path, cfg->tr);
+            break;
+        case PA_PATH_FFT:
+            rc = fft_plan(n, m, o, &cfg->tr);
+            cfg->ws_bytes = fft_workspace(cfg->tr);
+            break;
+        case PA_PATH_BLOCK_INT8:
+            rc = block_plan(n, m, o, &cfg->blk);
+            cfg->ws_bytes = block_workspace(cfg->blk);
+            break;
+    }
+    return rc;
+}
+
+void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
+    memset(d, 0, sizeof(*d));
+    d->n = cfg.n;
+    d->m = cfg.m;
+    d->path = cfg.path;
+    d->workspace_bytes = cfg.ws_bytes + kHeaderBytes;
+    d->kernels_per_call = cfg.kernels;
+    if (cfg.path == PA_PATH_DIRECT) {
+        d->tile_in = cfg.n;
+        d->tile_out = cfg.m;
+        d->tiles_in = d->tiles_out = 1;
+    } else if (cfg.path == PA_PATH_BLOCK_INT8) {
+        d->block_b = cfg.blk.b;
+        d->tile_in = cfg.n;
+        d->tile_out = cfg.m;
+        d->tiles_in = d->tiles_out = 1;
+    } else {
+        d->log2_transform = cfg.tr.log2n;
+        d->tile_in = cfg.tr.L;
+        d->tile_out = cfg.tr.M;
+        d->tiles_in = cfg.tr.tiles_in;
+        d->tiles_out = cfg.tr.tiles_out;
+        d->fp64 = cfg.tr.fp64;
+        d->rounding_bound = cfg.tr.bound;
+    }
+}
+
+}  // namespace pa
+
+struct pa_plan_s {
+    pa::PlanCfg cfg;
+    int device = 0;
+    void *mem = nullptr;  // header + workspace
+    uint64_t *stage = nullptr;  // pa_hash_host staging: seed | key | out
+    size_t stage_words = 0;
+    cudaStream_t last_stream = nullptr;
+    pa::Prof prof;
+};
+
+using namespace pa;
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int launch_plan(pa_plan_s *p, const uint64_t *seed, const uint64_t *key, uint64_t *out,
+                cudaStream_t s) {
+    DevHeader *hdr = static_cast<DevHeader *>(p->mem);
+    void *ws = static_cast<char *>(p->mem) + kHeaderBytes;
+    switch (p->cfg.path) {
+        case PA_PATH_DIRECT: return direct_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
+        case PA_PATH_NTT64:
+        case PA_PATH_NTT31: return ntt_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
+        case PA_PATH_FFT: return fft_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
+        case PA_PATH_BLOCK_INT8: return block_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
+    }
+    return PA_ERR_INVALID;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pa_plan_query(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_desc *out) {
+    if (!out) return PA_ERR_INVALID;
+    PlanCfg cfg;
+    int rc = plan_resolve(n, m, opts, &cfg);
+    if (rc != PA_OK) return rc;
+    fill_desc(cfg, out);
+    return PA_OK;
+}
+
+int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
+    if (!out) return PA_ERR_INVALID;
+    *out = nullptr;
+    pa_plan_s *p = new (std::nothrow) pa_plan_s();
+    if (!p) return PA_ERR_NOMEM;
+    int rc = plan_resolve(n, m, opts, &p->cfg);
+    if (rc != PA_OK) {
+        delete p;
+        return rc;
+    }
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e);
+    }
+    p->device = (opts && opts->device >= 0) ? opts->device : prev;
+    if (p->device != prev && (e = cudaSetDevice(p->device)) != cudaSuccess) {
+        delete p;
+        return cuda_fail(e);
+    }
+    e = cudaMalloc(&p->mem, kHeaderBytes + p->cfg.ws_bytes);
+    if (e == cudaSuccess) e = cudaMemset(p->mem, 0, kHeaderBytes);
+    if (p->device != prev) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        if (p->mem) cudaFree(p->mem);
+        delete p;
+        return cuda_fail(e);
+    }
+    *out = p;
+    return PA_OK;
+}
+
+int pa_plan(uint64_t n, uint64_t m, pa_plan_t *out) { return pa_plan_ex(n, m, nullptr, out); }
+
+int pa_plan_describe(pa_plan_t plan, pa_plan_desc *out) {
+    if (!plan || !out) return PA_ERR_INVALID;
+    fill_desc(plan->cfg, out);
+    return PA_OK;
+}
+
+void pa_plan_destroy(pa_plan_t plan) {
+    if (!plan) return;
+    if (plan->last_stream) cudaStreamSynchronize(plan->last_stream);
+    cudaFree(plan->mem);
+    if (plan->stage) cudaFree(plan->stage);
+    prof_free(&plan->prof);
+    delete plan;
+}
+
+int pa_hash(pa_plan_t plan, const uint64_t *seed_bits, const uint64_t *key_bits,
+            uint64_t *out_bits, void *stream) {
+    if (!plan || !seed_bits || !key_bits || !out_bits) return PA_ERR_INVALID;
+    if (!aligned16(seed_bits) || !aligned16(key_bits) || !aligned16(out_bits))
+        return PA_ERR_ALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    plan->last_stream = s;
+    return launch_plan(plan, seed_bits, key_bits, out_bits, s);
+}
+
+int pa_hash_host(pa_plan_t plan, const uint64_t *seed_host, const uint64_t *key_host,
+                 uint64_t *out_host, void *stream) {
+    if (!plan || !seed_host || !key_host || !out_host) return PA_ERR_INVALID;
+    const uint64_t n = plan->cfg.n, m = plan->cfg.m;
+    const size_t sw = round_up(ceil_div(n + m - 1, 64), 2), kw = round_up(ceil_div(n, 64), 2),
+                 ow = round_up(ceil_div(m, 64), 2);
+    if (!plan->stage) {
+        cudaError_t e = cudaMalloc(&plan->stage, (sw + kw + ow) * 8);
+        if (e != cudaSuccess) {
+            plan->stage = nullptr;
+            return cuda_fail(e);
+        }
+        plan->stage_words = sw + kw + ow;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t *dseed = plan->stage, *dkey = plan->stage + sw, *dout = plan->stage + sw + kw;
+    PA_CUDA_TRY(cudaMemcpyAsync(dseed, seed_host, ceil_div(n + m - 1, 64) * 8,
+                                cudaMemcpyHostToDevice, s));
+    PA_CUDA_TRY(cudaMemcpyAsync(dkey, key_host, ceil_div(n, 64) * 8, cudaMemcpyHostToDevice, s));
+    int rc = pa_hash(plan, dseed, dkey, dout, stream);
+    if (rc != PA_OK) return rc;
+    PA_CUDA_TRY(cudaMemcpyAsync(out_host, dout, ceil_div(m, 64) * 8, cudaMemcpyDeviceToHost, s));
+    PA_CUDA_TRY(cudaStreamSynchronize(s));
+    return PA_OK;
+}
+
+int pa_plan_status(pa_plan_t plan) {
+    if (!plan) return PA_ERR_INVALID;
+    PA_CUDA_TRY(cudaStreamSynchronize(plan->last_stream));
+    DevHeader h;
+    PA_CUDA_TRY(cudaMemcpy(&h, plan->mem, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.status != 0) {
+        int zero = 0;
+        PA_CUDA_TRY(cudaMemcpy(plan->mem, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    }
+    return h.status;
+}
+
+int pa_last_residual(pa_plan_t plan, double *residual, double *bound) {
+    if (!plan || !residual) return PA_ERR_INVALID;
+    if (plan->last_stream) PA_CUDA_TRY(cudaStreamSynchronize(plan->last_stream));
+    DevHeader h;
+    PA_CUDA_TRY(cudaMemcpy(&h, plan->mem, sizeof(h), cudaMemcpyDeviceToHost));
+    double r;
+    memcpy(&r, &h.residual_bits, sizeof(r));
+    *residual = r;
+    if (bound) *bound = plan->cfg.tr.bound;
+    unsigned long long zero = 0;
+    PA_CUDA_TRY(cudaMemcpy(static_cast<char *>(plan->mem) + offsetof(DevHeader, residual_bits),
+                           &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    return PA_OK;
+}
+
+int pa_plan_profile(pa_plan_t plan, int enable) {
+    if (!plan) return PA_ERR_INVALID;
+    return prof_enable(&plan->prof, enable);
+}
+
+int pa_plan_kernel_times(pa_plan_t plan, pa_kernel_time *out, int max, int *count) {
+    if (!plan || max < 0) return PA_ERR_INVALID;
+    return prof_collect(&plan->prof, out, max, count);
+}
+
+const char *pa_strerror(int status) {
+    switch (status) {
+        case PA_OK: return "success";
+        case PA_ERR_INVALID: return "invalid argument (zero size, null pointer or bad option)";
+        case PA_ERR_ALIGN: return "device bit buffer is not 16-byte aligned";
+        case PA_ERR_NOMEM: return "out of memory";
+        case PA_ERR_CUDA: return "CUDA runtime error";
+        case PA_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case PA_ERR_UNSUPPORTED: return "sizes not supported by the requested path";
+        case PA_ERR_PRECISION: return "no proven rounding bound below 1/2 for this FFT tile";
+    }
+    return "unknown status";
+}
+
+int pa_last_cuda_error(void) { return g_last_cuda_error; }
+
+int pa_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,158 @@
+// Direct path: the Toeplitz hash as a bit-packed GF(2) matrix-vector product
+// (Sec. 2.1 Eq. 1: T[i][j] = s[n-1+i-j], y = T x mod 2).
+//
+// Reversing the key, xr[j] = x[n-1-j], turns row i of T into the seed window that
+// starts at bit i:  y[i] = parity( sum_j xr[j] AND s[i+j] ).  A thread owns 32
+// consecutive rows (one 32-bit output word) and a chunk of 32-bit key words; for
+// key word q the 32 row windows are funnel shifts of two adjacent seed words, so
+// each 32x32 bit block costs 32 SHF + 32 LOP3 (acc ^= xw & window). The parity of
+// each row's accumulator (one POPC) is packed back into an output word; partial
+// words from different key chunks are merged with atomicXor (the XOR merge of
+// Eq. finalkey). Key chunks and seed windows are staged in shared memory by the
+// TMA engine (cp.async.bulk + mbarrier).
+#include "common.cuh"
+
+namespace pa {
+namespace {
+
+constexpr int kThreads = 128;      // 4 warps; one row group (32 rows) per thread
+constexpr int kRowGroups = kThreads;
+
+// xr[q] bit c = x[n-1-32q-c] (0 where that index is negative); zero padding past
+// ceil(n/32) words.
+__global__ void reverse_key_kernel(const uint32_t *__restrict__ key32, uint64_t key_buf_words32,
+                                   uint64_t n, uint32_t *__restrict__ xr, uint64_t words,
+                                   uint64_t words_pad) {
+    for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < words_pad;
+         q += uint64_t(gridDim.x) * blockDim.x) {
+        uint32_t v = 0;
+        if (q < words) {
+            int64_t lo = static_cast<int64_t>(n) - 1 - 32 * static_cast<int64_t>(q) - 31;
+            v = __brev(bits32_at(key32, key_buf_words32, lo));
+        }
+        xr[q] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) direct_kernel(
+    const uint32_t *__restrict__ seed32, uint64_t seed_words32, const uint32_t *__restrict__ xr,
+    uint32_t kc, uint64_t m, uint32_t *__restrict__ out32, uint64_t out_words32, int use_atomic,
+    int *status) {
+    extern __shared__ __align__(128) uint32_t sm[];
+    __shared__ __align__(8) uint64_t bar;
+    uint32_t *skey = sm;
+    uint32_t *sseed = sm + kc;
+
+    const uint64_t g0 = uint64_t(blockIdx.x) * kRowGroups;  // first row group (= seed word)
+    const uint64_t k0 = uint64_t(blockIdx.y) * kc;          // first key word
+    const uint64_t sb = g0 + k0;                            // first seed word needed
+    const uint32_t count = kRowGroups + kc + 4;             // seed words staged
+    const uint64_t avail = seed_words32 > sb ? seed_words32 - sb : 0;
+    const uint32_t bulk = static_cast<uint32_t>(avail < count ? avail : count) & ~3u;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (kc + bulk) * 4u);
+        bulk_g2s(skey, xr + k0, kc * 4u, &bar);
+        if (bulk) bulk_g2s(sseed, seed32 + sb, bulk * 4u, &bar);
+    }
+    for (uint32_t t = bulk + threadIdx.x; t < count; t += kThreads)
+        sseed[t] = (sb + t < seed_words32) ? __ldg(seed32 + sb + t) : 0u;
+    const bool ok = mbar_wait_bounded(&bar, 0, status);
+    __syncthreads();
+    if (!ok) return;
+
+    uint32_t acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0;
+
+    const uint32_t *sp = sseed + threadIdx.x;
+    uint32_t lo = sp[0];
+#pragma unroll 2
+    for (uint32_t q = 0; q < kc; ++q) {
+        const uint32_t xw = skey[q];
+        const uint32_t hi = sp[q + 1];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] ^= xw & __funnelshift_r(lo, hi, k);
+        lo = hi;
+    }
+
+    uint32_t res = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) res |= (__popc(acc[k]) & 1u) << k;
+
+    const uint64_t g = g0 + threadIdx.x;
+    if (g < out_words32) {
+        const uint64_t row0 = g * 32;
+        if (row0 + 32 > m) res = (m > row0) ? (res & ((1u << (m - row0)) - 1u)) : 0u;
+        if (use_atomic)
+            atomicXor(out32 + g, res);
+        else
+            out32[g] = res;
+    }
+}
+
+}  // namespace
+
+int direct_plan(uint64_t n, uint64_t m, DirectCfg *c) {
+    c->key_words32 = ceil_div(n, 32);
+    const uint64_t out_words32 = 2 * ceil_div(m, 64);
+    const uint64_t gx = ceil_div(out_words32, kRowGroups);
+    const uint64_t target = uint64_t(kNumSMsGB300) * 8 * 4;  // ~4 waves of 8 CTAs per SM
+    uint64_t kc = ceil_div(c->key_words32 * gx, target);
+    kc = round_up(kc < 32 ? 32 : kc, 4);
+    if (kc > 4096) kc = 4096;
+    const uint64_t kw4 = round_up(c->key_words32, 4);
+    if (kc > kw4) kc = kw4;
+    const uint64_t gy = ceil_div(c->key_words32, kc);
+    if (gx > 0x7fffffffull || gy > 65535) return PA_ERR_UNSUPPORTED;
+    c->kc = static_cast<uint32_t>(kc);
+    c->grid_x = static_cast<uint32_t>(gx);
+    c->grid_y = static_cast<uint32_t>(gy);
+    c->key_words32_pad = gy * kc;
+    return PA_OK;
+}
+
+size_t direct_workspace(const DirectCfg &c) { return round_up(c.key_words32_pad * 4, 256); }
+
+int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+                  const uint64_t *key, uint64_t *out, cudaStream_t s) {
+    const DirectCfg &c = cfg.direct;
+    const uint64_t n = cfg.n, m = cfg.m;
+    uint32_t *xr = static_cast<uint32_t *>(ws);
+    const uint64_t out_words64 = ceil_div(m, 64);
+    const int use_atomic = c.grid_y > 1;
+    if (use_atomic) {
+        prof_begin(prof, K_MEMSET, s);
+        PA_CUDA_TRY(cudaMemsetAsync(out, 0, out_words64 * 8, s));
+        prof_end(prof, s);
+    }
+    {
+        prof_begin(prof, K_REVERSE_KEY, s);
+        const uint64_t words = c.key_words32_pad;
+        uint64_t blocks = ceil_div(words, 256);
+        if (blocks > 4096) blocks = 4096;
+        reverse_key_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+            reinterpret_cast<const uint32_t *>(key), 2 * ceil_div(n, 64), n, xr, c.key_words32,
+            words);
+        prof_end(prof, s);
+    }
+    const size_t smem = (size_t(c.kc) + kRowGroups + c.kc + 4) * 4;
+    if (smem > 48 * 1024)
+        PA_CUDA_TRY(cudaFuncSetAttribute(direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+    dim3 grid(c.grid_x, c.grid_y);
+    prof_begin(prof, K_DIRECT, s);
+    direct_kernel<<<grid, kThreads, smem, s>>>(
+        reinterpret_cast<const uint32_t *>(seed), 2 * ceil_div(n + m - 1, 64), xr, c.kc, m,
+        reinterpret_cast<uint32_t *>(out), 2 * out_words64, use_atomic, &hdr->status);
+    prof_end(prof, s);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+}  // namespace pa

@@ -1,0 +1,136 @@
+// Internal declarations of the Toeplitz-hash library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/pa.h"
+
+namespace pa {
+
+constexpr int kNumSMsGB300 = 152;
+
+// ---- direct path (bit-packed AND + popcount) ----
+struct DirectCfg {
+    uint32_t kc = 0;            // 32-bit key words per CTA
+    uint64_t key_words32 = 0;   // ceil(n/32)
+    uint64_t key_words32_pad = 0;  // padded to a multiple of kc
+    uint32_t grid_x = 0, grid_y = 0;
+};
+
+// ---- transform paths (NTT over a prime field, FP FFT) ----
+struct TransformCfg {
+    uint32_t log2n = 0;          // transform size N = 2^log2n
+    uint64_t L = 0, M = 0;       // key tile and output tile lengths
+    uint64_t tiles_in = 0, tiles_out = 0;
+    uint32_t delta = 0;          // extra window shift so output tiles start on 32-bit words
+    uint32_t passes = 0;         // NTT: global passes
+    uint32_t radix_log2[4] = {0, 0, 0, 0};
+    uint32_t fp64 = 0;           // FFT: FP64 butterflies
+    double bound = 0.0;          // FFT: proven rounding bound
+    uint32_t concurrent = 0;     // tiles processed per launch wave
+};
+
+// ---- block-Toeplitz tensor-core path ----
+struct BlockCfg {
+    uint32_t b = 0;              // tile edge
+    uint64_t kc = 0;             // key chunk (positions) per CTA
+    uint32_t grid_x = 0, grid_y = 0;
+};
+
+struct PlanCfg {
+    uint64_t n = 0, m = 0;
+    int path = PA_PATH_DIRECT;
+    DirectCfg direct;
+    TransformCfg tr;
+    BlockCfg blk;
+    size_t ws_bytes = 0;         // workspace excluding the status header
+    uint32_t kernels = 0;
+};
+
+// Host-only planning (no GPU calls).
+int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg);
+void fill_desc(const PlanCfg &cfg, pa_plan_desc *d);
+
+// Workspace header kept at the start of every plan's device workspace.
+struct DevHeader {
+    int status;
+    int pad;
+    unsigned long long residual_bits;  // max |v - rint(v)| as the bit pattern of a double >= 0
+};
+constexpr size_t kHeaderBytes = 256;
+
+// ---- per-kernel CUDA-event timing (pa_plan_profile / pa_batch_profile) ----
+enum KernelId {
+    K_REVERSE_KEY = 0,
+    K_DIRECT,
+    K_NTT_FWD_FIRST,
+    K_NTT_FWD_MID,
+    K_NTT_FUSED_LAST,
+    K_NTT_INV_MID,
+    K_NTT_INV_FIRST,
+    K_NTT_SMALL,
+    K_FFT_TILE,
+    K_BLOCK_MMA,
+    K_BATCH_PERSISTENT,
+    K_MEMSET,
+    K_NUM_KERNELS
+};
+const char *kernel_name(int kid);
+
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+struct Prof {
+    bool on = false;
+    ProfRec *recs = nullptr;
+    size_t cap = 0, used = 0;
+    int open_kid = -1;
+};
+// Record an event pair around one launch when profiling is on (no-ops otherwise).
+void prof_begin(Prof *p, int kid, cudaStream_t s);
+void prof_end(Prof *p, cudaStream_t s);
+int prof_enable(Prof *p, int enable);
+int prof_collect(Prof *p, pa_kernel_time *out, int max, int *count);
+void prof_free(Prof *p);
+
+// Launchers (enqueue on stream; return PA_OK or PA_ERR_CUDA).
+int direct_plan(uint64_t n, uint64_t m, DirectCfg *c);
+size_t direct_workspace(const DirectCfg &c);
+int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+                  const uint64_t *key, uint64_t *out, cudaStream_t s);
+
+int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c);
+size_t ntt_workspace(int path, const TransformCfg &c);
+int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+               const uint64_t *key, uint64_t *out, cudaStream_t s);
+
+int fft_plan(uint64_t n, uint64_t m, const pa_opts *o, TransformCfg *c);
+size_t fft_workspace(const TransformCfg &c);
+int fft_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+               const uint64_t *key, uint64_t *out, cudaStream_t s);
+
+int block_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c);
+size_t block_workspace(const BlockCfg &c);
+int block_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+                 const uint64_t *key, uint64_t *out, cudaStream_t s);
+
+// Records a CUDA error for pa_last_cuda_error and maps it to a status.
+int cuda_fail(cudaError_t e);
+#define PA_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return ::pa::cuda_fail(_e); \
+    } while (0)
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+inline uint64_t round_up(uint64_t a, uint64_t b) { return ceil_div(a, b) * b; }
+inline uint32_t log2_ceil(uint64_t v) {
+    uint32_t k = 0;
+    while ((uint64_t(1) << k) < v) ++k;
+    return k;
+}
+
+}  // namespace pa
