@@ -233,11 +233,11 @@ def roofline(kt: dict, blocks, steps: int, clocks):
     pk, src = peaks()
     out = {"kernel": name, "launch_ms": per_launch_ms, "launches": v["launches"]}
     if bound == "alu":
-        # 152 SMs x 128 INT32 lanes x max SM clock (2070 MHz).
-        peak = 152 * 128 * 2070e6 / 1e12
+        # 152 SMs x 64 INT32 (LOP3/SHF) lanes x max SM clock (2070 MHz).
+        peak = 152 * 64 * 2070e6 / 1e12
         ach = units / (per_launch_ms * 1e-3) / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": unit,
-                    "frac": ach / peak, "peak_source": "derived: 152 SM x 128 lanes x 2070 MHz"})
+                    "frac": ach / peak, "peak_source": "derived: 152 SM x 64 INT32 lanes x 2070 MHz"})
     elif bound == "hbm":
         peak = pk["hbm_gbs"]
         ach = units / (per_launch_ms * 1e-3) / 1e9

@@ -30,8 +30,11 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
         // kernel wins while m*n is small; the exact 31-bit NTT wins beyond.
         const double mn = double(n) * double(m);
         path = (mn <= 4.0e9 || n >= 2013265921ull) ? PA_PATH_DIRECT : PA_PATH_NTT31;
-        if (path == PA_PATH_NTT31 && ntt_plan(n, m, path, o, &cfg->tr) != PA_OK)
+        TransformCfg probe;
+        if (path == PA_PATH_NTT31 && ntt_plan(n, m, path, o, &probe) != PA_OK)
             path = PA_PATH_NTT64;
+        if (path == PA_PATH_NTT64 && ntt_plan(n, m, path, o, &probe) != PA_OK)
+            path = PA_PATH_DIRECT;
     }
     cfg->path = path;
     int rc = PA_OK;
@@ -45,6 +48,10 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
         case PA_PATH_NTT31:
             rc = ntt_plan(n, m, path, o, &cfg->tr);
             cfg->ws_bytes = ntt_workspace(path, cfg->tr);
+            cfg->kernels = cfg->tr.passes == 1
+                               ? 1
+                               : 3 * static_cast<uint32_t>(ceil_div(
+                                         cfg->tr.tiles_in * cfg->tr.tiles_out, cfg->tr.concurrent));
             break;
         case PA_PATH_FFT:
             rc = fft_plan(n, m, o, &cfg->tr);
@@ -153,6 +160,15 @@ int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
     }
     e = cudaMalloc(&p->mem, kHeaderBytes + p->cfg.ws_bytes);
     if (e == cudaSuccess) e = cudaMemset(p->mem, 0, kHeaderBytes);
+    if (e == cudaSuccess && (p->cfg.path == PA_PATH_NTT31 || p->cfg.path == PA_PATH_NTT64)) {
+        rc = ntt_init(p->cfg, static_cast<char *>(p->mem) + kHeaderBytes);
+        if (rc != PA_OK) {
+            if (p->device != prev) cudaSetDevice(prev);
+            cudaFree(p->mem);
+            delete p;
+            return rc;
+        }
+    }
     if (p->device != prev) cudaSetDevice(prev);
     if (e != cudaSuccess) {
         if (p->mem) cudaFree(p->mem);

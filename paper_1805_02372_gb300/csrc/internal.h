@@ -104,6 +104,7 @@ int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, cons
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c);
 size_t ntt_workspace(int path, const TransformCfg &c);
+int ntt_init(const PlanCfg &cfg, void *ws);  // uploads tile descriptors, builds root tables
 int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                const uint64_t *key, uint64_t *out, cudaStream_t s);
 

@@ -1,6 +1,695 @@
-#include "internal.h"
+// Exact transform path: the tile products of the length-compatible decomposition
+// (Sec. 3, Fig. 1-2, Steps 1-3) computed with number-theoretic transforms over a
+// prime field instead of floating-point FFTs, so no rounding bound is needed.
+//
+// Decomposition. Output tile I covers rows [i0, i0+M), key tile J covers key bits
+// [j0, j0+L) (L a multiple of 32, M of 64). With a[t] = x[j0+t] and the seed window
+// w[u] = s[n-1+i0-j0-L+u] (positions outside the seed read as 0), output row i0+v
+// receives coefficient L+v of the linear convolution a*w, and a cyclic convolution
+// of size N >= L+M gives those coefficients unaliased. The tile's bits are XORed into
+// the output (Eq. finalkey).
+//
+// Transforms. N = R1*R2 (a four-step split; R1, R2 <= 2^11) or N <= 2^12 in one CTA.
+// Forward: decimation in frequency, natural input, bit-reversed spectrum; inverse:
+// decimation in time from the bit-reversed spectrum, so no permutation pass exists.
+// Each CTA does R-point transforms on columns in shared memory, two radix-2 stages
+// per shared-memory round trip (radix-4 groups in registers).
+//   ntt_fwd_first : pass 1 (stride R2) on the key tile and the seed window, read
+//                   straight from the packed bits, then the four-step twiddles.
+//   ntt_fused_last: pass 2 (contiguous rows of R2) of both spectra, the pointwise
+//                   product, and inverse pass 2.
+//   ntt_inv_first : twiddles, inverse pass 1, scale by N^-1, take bit 0, XOR the
+//                   tile's output bytes into the packed output.
+//   ntt_small     : N <= 2^12: all of the above in one CTA per tile.
+#include <mutex>
+#include <stdio.h>
+#include <string.h>
+#include <vector>
+
+#include "common.cuh"
+#include "ntt_field.cuh"
+
 namespace pa {
-int ntt_plan(uint64_t, uint64_t, int, const pa_opts *, TransformCfg *) { return PA_ERR_UNSUPPORTED; }
-size_t ntt_workspace(int, const TransformCfg &) { return 0; }
-int ntt_launch(const PlanCfg &, void *, DevHeader *, Prof *, const uint64_t *, const uint64_t *, uint64_t *, cudaStream_t) { return PA_ERR_UNSUPPORTED; }
+
+constexpr int kLogMax = 22;           // largest transform: 2^22
+constexpr int kLogSmallMax = 12;      // one-CTA transforms up to 2^12
+constexpr int kThreads = 512;
+
+struct NttPair {
+    int64_t key_bit0;   // first key bit of the tile
+    uint64_t key_len;   // valid key bits in the tile
+    int64_t win_bit0;   // seed bit of window position 0 (may be negative)
+    uint64_t win_len;   // window positions read (beyond: 0)
+    uint64_t out_bit0;  // first output row of the tile (multiple of 64)
+    uint32_t out_len;   // valid output rows
+    uint32_t K0;        // convolution index of output row out_bit0
+    uint32_t blk;       // block index (batched launches)
+    uint32_t pad;
+};
+
+struct BlockPtrs {
+    const uint32_t *key32;
+    const uint32_t *seed32;
+    uint32_t *out32;
+    uint64_t n, m;
+};
+
+// ---------------------------------------------------------------- host tables
+
+namespace {
+
+uint64_t mulmod_host(uint64_t a, uint64_t b, uint64_t p) {
+    return static_cast<uint64_t>((static_cast<unsigned __int128>(a) * b) % p);
 }
+uint64_t powmod_host(uint64_t a, uint64_t e, uint64_t p) {
+    uint64_t r = 1;
+    a %= p;
+    while (e) {
+        if (e & 1) r = mulmod_host(r, a, p);
+        a = mulmod_host(a, a, p);
+        e >>= 1;
+    }
+    return r;
+}
+// Primitive 2^k-th root of unity: g^((p-1)/2^k) for a generator g of the group.
+uint64_t root_of_unity(uint64_t p, const uint64_t *odd_factors, int nf, int two_adicity, int k) {
+    for (uint64_t g = 2;; ++g) {
+        bool ok = powmod_host(g, (p - 1) / 2, p) != 1;
+        for (int i = 0; ok && i < nf; ++i) ok = powmod_host(g, (p - 1) / odd_factors[i], p) != 1;
+        if (ok) return powmod_host(g, (p - 1) >> k, p);
+        (void)two_adicity;
+    }
+}
+
+template <class F>
+struct FieldHost;
+template <>
+struct FieldHost<F31> {
+    static uint64_t p() { return F31::P; }
+    static uint64_t root(int k) {
+        const uint64_t f[] = {3, 5};
+        return root_of_unity(F31::P, f, 2, 27, k);
+    }
+    static F31::Tw tw(uint64_t w) {
+        F31::Tw t;
+        t.w = static_cast<uint32_t>(w);
+        t.q = static_cast<uint32_t>((w << 32) / F31::P);
+        return t;
+    }
+    // Final scale: N^-1 * 2^32 (undoes the unnormalised transforms and the Montgomery factor).
+    static F31::Tw scale(int logn) {
+        uint64_t ninv = powmod_host(uint64_t(1) << logn, F31::P - 2, F31::P);
+        return tw(mulmod_host(ninv, (uint64_t(1) << 32) % F31::P, F31::P));
+    }
+};
+template <>
+struct FieldHost<F64> {
+    static uint64_t p() { return F64::P; }
+    static uint64_t root(int k) {
+        const uint64_t f[] = {3, 5, 17, 257, 65537};
+        return root_of_unity(F64::P, f, 5, 32, k);
+    }
+    static F64::Tw tw(uint64_t w) { return w; }
+    static F64::Tw scale(int logn) {
+        return powmod_host(uint64_t(1) << logn, F64::P - 2, F64::P);
+    }
+};
+
+// Per-device tables: fwd[e] = w^e, inv[e] = w^-e for e < 2^(kLogMax-1), w of order 2^kLogMax.
+struct Tables {
+    void *fwd = nullptr, *inv = nullptr;
+};
+std::mutex g_tab_mu;
+Tables g_tabs[2][64];
+
+template <class F>
+int get_tables(int field, Tables *out) {
+    int dev = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return PA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    Tables &t = g_tabs[field][dev];
+    if (!t.fwd) {
+        using Tw = typename F::Tw;
+        const size_t half = size_t(1) << (kLogMax - 1);
+        std::vector<Tw> f(half), i(half);
+        const uint64_t p = FieldHost<F>::p();
+        const uint64_t w = FieldHost<F>::root(kLogMax);
+        const uint64_t wi = powmod_host(w, p - 2, p);
+        uint64_t a = 1, b = 1;
+        for (size_t e = 0; e < half; ++e) {
+            f[e] = FieldHost<F>::tw(a);
+            i[e] = FieldHost<F>::tw(b);
+            a = mulmod_host(a, w, p);
+            b = mulmod_host(b, wi, p);
+        }
+        void *df = nullptr, *di = nullptr;
+        cudaError_t e = cudaMalloc(&df, half * sizeof(Tw));
+        if (e == cudaSuccess) e = cudaMalloc(&di, half * sizeof(Tw));
+        if (e == cudaSuccess) e = cudaMemcpy(df, f.data(), half * sizeof(Tw), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(di, i.data(), half * sizeof(Tw), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(df);
+            cudaFree(di);
+            return cuda_fail(e);
+        }
+        t.fwd = df;
+        t.inv = di;
+    }
+    *out = t;
+    return PA_OK;
+}
+
+// ---------------------------------------------------------------- device pieces
+
+__device__ __forceinline__ uint32_t get_bit(const uint32_t *__restrict__ v, uint64_t pos) {
+    return (__ldg(v + (pos >> 5)) >> (pos & 31)) & 1u;
+}
+
+__device__ __forceinline__ uint32_t key_bit(const NttPair &pr, const BlockPtrs &bp, uint64_t t) {
+    return t < pr.key_len ? get_bit(bp.key32, uint64_t(pr.key_bit0) + t) : 0u;
+}
+
+__device__ __forceinline__ uint32_t win_bit(const NttPair &pr, const BlockPtrs &bp, uint64_t u) {
+    if (u >= pr.win_len) return 0u;
+    const int64_t p = pr.win_bit0 + static_cast<int64_t>(u);
+    if (p < 0 || static_cast<uint64_t>(p) >= bp.n + bp.m - 1) return 0u;
+    return get_bit(bp.seed32, static_cast<uint64_t>(p));
+}
+
+// Twiddle w^E (E < 2^kLogMax) from a half table: w^(E + 2^(kLogMax-1)) = -w^E.
+template <class F>
+__device__ __forceinline__ typename F::Tw tw_at(const typename F::Tw *__restrict__ tab, uint32_t E) {
+    constexpr uint32_t half = 1u << (kLogMax - 1);
+    if (E < half) return tab[E];
+    return F::neg_tw(tab[E - half]);
+}
+
+// Stage tables of an R-point transform into shared memory: st[h-1+j] = w_{2h}^(+-j).
+template <class F>
+__device__ void load_stage_tables(typename F::Tw *st, const typename F::Tw *__restrict__ tab,
+                                  int logR) {
+    const int R = 1 << logR;
+    for (int idx = threadIdx.x; idx < R - 1; idx += blockDim.x) {
+        const int lh = 31 - __clz(idx + 1);
+        const uint32_t j = static_cast<uint32_t>(idx + 1 - (1 << lh));
+        st[idx] = tab[j << (kLogMax - 1 - lh)];
+    }
+}
+
+// Element (r, c) of a shared tile at base[r*rs + c*cs]. CF: consecutive threads take
+// consecutive columns (when cs == 1), else consecutive rows (when rs == 1).
+template <class F, bool CF>
+__device__ __forceinline__ void dif_round4(typename F::T *sm, int logR, int logC, int rs, int cs,
+                                           int lq, const typename F::Tw *tw) {
+    using T = typename F::T;
+    const int q = 1 << lq, h = 2 * q;
+    const int logG = logR - 2;
+    const int total = 1 << (logG + logC);
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int c, g;
+        if (CF) {
+            c = w & ((1 << logC) - 1);
+            g = w >> logC;
+        } else {
+            g = w & ((1 << logG) - 1);
+            c = w >> logG;
+        }
+        const int j = g & (q - 1);
+        const int i0 = ((g >> lq) << (lq + 2)) + j;
+        T *b = sm + c * cs;
+        const T x0 = b[i0 * rs], x1 = b[(i0 + q) * rs], x2 = b[(i0 + 2 * q) * rs],
+                x3 = b[(i0 + 3 * q) * rs];
+        const typename F::Tw w1 = tw[h - 1 + j], w2 = tw[h - 1 + j + q], w3 = tw[q - 1 + j];
+        const T y0 = F::add(x0, x2), y2 = F::mul_tw(F::sub(x0, x2), w1);
+        const T y1 = F::add(x1, x3), y3 = F::mul_tw(F::sub(x1, x3), w2);
+        b[i0 * rs] = F::add(y0, y1);
+        b[(i0 + q) * rs] = F::mul_tw(F::sub(y0, y1), w3);
+        b[(i0 + 2 * q) * rs] = F::add(y2, y3);
+        b[(i0 + 3 * q) * rs] = F::mul_tw(F::sub(y2, y3), w3);
+    }
+}
+
+template <class F, bool CF>
+__device__ __forceinline__ void dit_round4(typename F::T *sm, int logR, int logC, int rs, int cs,
+                                           int lq, const typename F::Tw *tw) {
+    using T = typename F::T;
+    const int q = 1 << lq, h = 2 * q;
+    const int logG = logR - 2;
+    const int total = 1 << (logG + logC);
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int c, g;
+        if (CF) {
+            c = w & ((1 << logC) - 1);
+            g = w >> logC;
+        } else {
+            g = w & ((1 << logG) - 1);
+            c = w >> logG;
+        }
+        const int j = g & (q - 1);
+        const int i0 = ((g >> lq) << (lq + 2)) + j;
+        T *b = sm + c * cs;
+        const T z0 = b[i0 * rs], z1 = b[(i0 + q) * rs], z2 = b[(i0 + 2 * q) * rs],
+                z3 = b[(i0 + 3 * q) * rs];
+        const typename F::Tw w1 = tw[h - 1 + j], w2 = tw[h - 1 + j + q], w3 = tw[q - 1 + j];
+        T t = F::mul_tw(z1, w3);
+        const T y0 = F::add(z0, t), y1 = F::sub(z0, t);
+        t = F::mul_tw(z3, w3);
+        const T y2 = F::add(z2, t), y3 = F::sub(z2, t);
+        t = F::mul_tw(y2, w1);
+        b[i0 * rs] = F::add(y0, t);
+        b[(i0 + 2 * q) * rs] = F::sub(y0, t);
+        t = F::mul_tw(y3, w2);
+        b[(i0 + q) * rs] = F::add(y1, t);
+        b[(i0 + 3 * q) * rs] = F::sub(y1, t);
+    }
+}
+
+template <class F, bool CF, bool DIF>
+__device__ __forceinline__ void round2(typename F::T *sm, int logR, int logC, int rs, int cs,
+                                       const typename F::Tw *tw) {
+    // single stage with half-size 1: pairs (2g, 2g+1), twiddle w_2^0 = 1
+    using T = typename F::T;
+    const int logG = logR - 1;
+    const int total = 1 << (logG + logC);
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int c, g;
+        if (CF) {
+            c = w & ((1 << logC) - 1);
+            g = w >> logC;
+        } else {
+            g = w & ((1 << logG) - 1);
+            c = w >> logG;
+        }
+        T *b = sm + c * cs;
+        const T a = b[(2 * g) * rs], d = b[(2 * g + 1) * rs];
+        b[(2 * g) * rs] = F::add(a, d);
+        b[(2 * g + 1) * rs] = F::sub(a, d);
+    }
+    (void)tw;
+}
+
+// Forward R-point DIF on every column (natural in, bit-reversed out).
+template <class F, bool CF>
+__device__ void dif_columns(typename F::T *sm, int logR, int logC, int rs, int cs,
+                            const typename F::Tw *tw) {
+    int lq = logR - 2;
+    for (; lq >= 0; lq -= 2) {
+        dif_round4<F, CF>(sm, logR, logC, rs, cs, lq, tw);
+        __syncthreads();
+    }
+    if (logR & 1) {
+        round2<F, CF, true>(sm, logR, logC, rs, cs, tw);
+        __syncthreads();
+    }
+}
+
+// Inverse R-point DIT on every column (bit-reversed in, natural out, unnormalised).
+template <class F, bool CF>
+__device__ void dit_columns(typename F::T *sm, int logR, int logC, int rs, int cs,
+                            const typename F::Tw *tw) {
+    int lq = 0;
+    if (logR & 1) {
+        round2<F, CF, false>(sm, logR, logC, rs, cs, tw);
+        __syncthreads();
+        lq = 1;
+    }
+    for (; lq <= logR - 2; lq += 2) {
+        dit_round4<F, CF>(sm, logR, logC, rs, cs, lq, tw);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ BlockPtrs pick(const BlockPtrs *blks, const BlockPtrs &one, uint32_t b) {
+    return blks ? blks[b] : one;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// One CTA per tile; the whole transform of size 2^logN <= 2^12 in shared memory.
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_small(const NttPair *__restrict__ pairs,
+                                                      const BlockPtrs *__restrict__ blks,
+                                                      BlockPtrs one, int logN,
+                                                      const typename F::Tw *__restrict__ tfwd,
+                                                      const typename F::Tw *__restrict__ tinv,
+                                                      typename F::Tw scale) {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = 1 << logN;
+    Tw *stf = reinterpret_cast<Tw *>(smraw);
+    Tw *sti = stf + N;
+    T *sm = reinterpret_cast<T *>(sti + N);  // column 0: key tile, column 1: window
+    const NttPair pr = pairs[blockIdx.x];
+    const BlockPtrs bp = pick(blks, one, pr.blk);
+    load_stage_tables<F>(stf, tfwd, logN);
+    load_stage_tables<F>(sti, tinv, logN);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        sm[t] = key_bit(pr, bp, t);
+        sm[N + t] = win_bit(pr, bp, t);
+    }
+    __syncthreads();
+    dif_columns<F, false>(sm, logN, 1, 1, N, stf);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) sm[N + t] = F::mont(sm[t], sm[N + t]);
+    __syncthreads();
+    dit_columns<F, false>(sm + N, logN, 0, 1, N, sti);
+    // outputs: conv index K0 + v, v < out_len; 32 rows per warp step, packed by ballot
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nw = (pr.out_len + 31) / 32;
+    for (uint32_t w = warp; w < nw; w += blockDim.x / 32) {
+        const uint32_t v = w * 32 + lane;
+        uint32_t bit = 0;
+        if (v < pr.out_len) bit = F::low_bit(F::mul_tw(sm[N + pr.K0 + v], scale));
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+        if (lane == 0 && word) atomicXor(bp.out32 + (pr.out_bit0 >> 5) + w, word);
+    }
+}
+
+// Pass 1 forward on C columns of stride S1 = 2^logS (rows R1 = 2^logR1) for the key
+// tile (blockIdx.y even) or the seed window (odd); writes spectra to ws.
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_fwd_first(
+    const NttPair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
+    int logN, int logR1, int logC, typename F::T *__restrict__ ws,
+    const typename F::Tw *__restrict__ tfwd) {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int R1 = 1 << logR1, C = 1 << logC, logS = logN - logR1;
+    Tw *st = reinterpret_cast<Tw *>(smraw);
+    T *sm = reinterpret_cast<T *>(st + R1);
+    const int which = blockIdx.y & 1;
+    const uint32_t pi = blockIdx.y >> 1;
+    const NttPair pr = pairs[pi];
+    const BlockPtrs bp = pick(blks, one, pr.blk);
+    const uint64_t c0 = uint64_t(blockIdx.x) << logC;
+    load_stage_tables<F>(st, tfwd, logR1);
+    for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
+        const int r = e >> logC, c = e & (C - 1);
+        const uint64_t t = (uint64_t(r) << logS) + c0 + c;
+        sm[e] = which ? win_bit(pr, bp, t) : key_bit(pr, bp, t);
+    }
+    __syncthreads();
+    dif_columns<F, true>(sm, logR1, logC, C, 1, st);
+    T *dst = ws + (uint64_t(pi) * 2 + which) * (uint64_t(1) << logN);
+    for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
+        const int r = e >> logC, c = e & (C - 1);
+        const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
+        const uint64_t tlo = c0 + c;
+        const uint32_t E = static_cast<uint32_t>((tlo * f) << (kLogMax - logN));
+        dst[(uint64_t(r) << logS) + tlo] = F::mul_tw(sm[e], tw_at<F>(tfwd, E));
+    }
+}
+
+// Pass 2 of both spectra (contiguous rows of R2 = 2^logR2), the pointwise product,
+// and the inverse pass 2, for C2 = 2^logC rows; result written over the window's rows.
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2, int logC,
+                                                           typename F::T *__restrict__ ws,
+                                                           const typename F::Tw *__restrict__ tfwd,
+                                                           const typename F::Tw *__restrict__ tinv) {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int R2 = 1 << logR2;
+    Tw *stf = reinterpret_cast<Tw *>(smraw);
+    Tw *sti = stf + R2;
+    T *sm = reinterpret_cast<T *>(sti + R2);  // columns 0..C-1: key spectrum rows, C..2C-1: window
+    const uint32_t pi = blockIdx.y;
+    T *X = ws + (uint64_t(pi) * 2) * (uint64_t(1) << logN);
+    T *W = X + (uint64_t(1) << logN);
+    const uint64_t row0 = uint64_t(blockIdx.x) << logC;
+    load_stage_tables<F>(stf, tfwd, logR2);
+    load_stage_tables<F>(sti, tinv, logR2);
+    const int cnt = R2 << logC;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        sm[e] = X[(row0 << logR2) + e];
+        sm[cnt + e] = W[(row0 << logR2) + e];
+    }
+    __syncthreads();
+    dif_columns<F, false>(sm, logR2, logC + 1, 1, R2, stf);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[cnt + e] = F::mont(sm[e], sm[cnt + e]);
+    __syncthreads();
+    dit_columns<F, false>(sm + cnt, logR2, logC, 1, R2, sti);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) W[(row0 << logR2) + e] = sm[cnt + e];
+}
+
+// Inverse pass 1 on C columns of the product, scale, low bit, XOR output bytes.
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_inv_first(
+    const NttPair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
+    int logN, int logR1, int logC, const typename F::T *__restrict__ ws,
+    const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int R1 = 1 << logR1, C = 1 << logC, logS = logN - logR1;
+    Tw *st = reinterpret_cast<Tw *>(smraw);
+    T *sm = reinterpret_cast<T *>(st + R1);
+    const uint32_t pi = blockIdx.y;
+    const NttPair pr = pairs[pi];
+    const BlockPtrs bp = pick(blks, one, pr.blk);
+    const uint64_t c0 = uint64_t(blockIdx.x) << logC;
+    const T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
+    load_stage_tables<F>(st, tinv, logR1);
+    for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
+        const int r = e >> logC, c = e & (C - 1);
+        const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
+        const uint64_t tlo = c0 + c;
+        const uint32_t E = static_cast<uint32_t>((tlo * f) << (kLogMax - logN));
+        sm[e] = F::mul_tw(src[(uint64_t(r) << logS) + tlo], tw_at<F>(tinv, E));
+    }
+    __syncthreads();
+    dit_columns<F, true>(sm, logR1, logC, C, 1, st);
+    // row r holds conv indices k = r*S1 + c0 + c (c < C = 8): one output byte per row
+    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
+        const uint64_t k0 = (uint64_t(r) << logS) + c0;
+        if (k0 + C <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
+        uint32_t byte = 0;
+        for (int c = 0; c < C; ++c) {
+            const uint64_t k = k0 + c;
+            if (k >= pr.K0 && k < uint64_t(pr.K0) + pr.out_len)
+                byte |= F::low_bit(F::mul_tw(sm[(r << logC) + c], scale)) << c;
+        }
+        if (byte) {
+            const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of 8
+            atomicXor(bp.out32 + (pos >> 5), byte << (pos & 31));
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- planning
+
+namespace {
+
+struct Geo {
+    uint32_t logn;
+    uint64_t L, M, pairs;
+};
+
+// Tile geometry for transform size 2^logn with output tile M: key tile L = N - M
+// rounded down to 32 bits.
+bool geo_for(uint64_t n, uint64_t m, uint32_t logn, uint64_t M, Geo *g) {
+    const uint64_t N = uint64_t(1) << logn;
+    if (M == 0 || M >= N) return false;
+    uint64_t L = ((N - M) / 32) * 32;
+    const uint64_t Lneed = round_up(n, 32);
+    if (L > Lneed) L = Lneed;
+    if (L == 0) return false;
+    g->logn = logn;
+    g->L = L;
+    g->M = M;
+    g->pairs = ceil_div(n, L) * ceil_div(m, M);
+    return true;
+}
+
+}  // namespace
+
+int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c) {
+    *c = TransformCfg();
+    const int twoadic = path == PA_PATH_NTT31 ? F31::kTwoAdicity : F64::kTwoAdicity;
+    (void)twoadic;
+    if (path == PA_PATH_NTT31 && n >= F31::P) return PA_ERR_UNSUPPORTED;  // counts must stay < p
+    Geo best{};
+    double best_cost = 1e300;
+    const uint32_t lo = 5, hi = kLogMax;
+    const uint32_t force = o ? o->log2_transform : 0;
+    const uint64_t Mforce = o ? o->tile_out : 0, Lforce = o ? o->tile_in : 0;
+    for (uint32_t k = lo; k <= hi; ++k) {
+        if (force && k != force) continue;
+        const uint64_t N = uint64_t(1) << k;
+        uint64_t cands[24];
+        int nc = 0;
+        if (Mforce) {
+            cands[nc++] = round_up(Mforce, 64);
+        } else {
+            cands[nc++] = round_up(m, 64);
+            for (uint64_t f = 2; f <= 1024 && nc < 24 && N / f >= 64; f *= 2)
+                cands[nc++] = round_up(N / f, 64);
+        }
+        for (int i = 0; i < nc; ++i) {
+            Geo g;
+            uint64_t M = cands[i];
+            if (M > round_up(m, 64)) M = round_up(m, 64);
+            if (!geo_for(n, m, k, M, &g)) continue;
+            if (Lforce) {
+                const uint64_t L = round_up(Lforce, 32);
+                if (L + M > N) continue;
+                g.L = L;
+                g.pairs = ceil_div(n, L) * ceil_div(m, M);
+            }
+            // cost ~ pairs * (3 transforms of N log N + fixed per-tile overhead)
+            const double cost = double(g.pairs) * (double(N) * (k + 6) + 4096.0);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = g;
+            }
+        }
+    }
+    if (best_cost >= 1e300) return PA_ERR_UNSUPPORTED;
+    c->log2n = best.logn;
+    c->L = best.L;
+    c->M = best.M;
+    c->tiles_in = ceil_div(n, best.L);
+    c->tiles_out = ceil_div(m, best.M);
+    if (best.logn <= kLogSmallMax) {
+        c->passes = 1;
+        c->radix_log2[0] = best.logn;
+    } else {
+        c->passes = 2;
+        c->radix_log2[0] = (best.logn + 1) / 2;  // R1 (strided pass)
+        c->radix_log2[1] = best.logn / 2;        // R2 (contiguous pass)
+    }
+    const uint64_t pairs = c->tiles_in * c->tiles_out;
+    const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
+    const uint64_t per_pair = c->passes == 1 ? 0 : 2 * (uint64_t(1) << best.logn) * elem;
+    uint64_t conc = pairs;
+    const uint64_t cap = uint64_t(2) << 30;  // 2 GiB of spectra per wave
+    if (per_pair && conc * per_pair > cap) conc = cap / per_pair ? cap / per_pair : 1;
+    if (conc > 65535 / 2) conc = 65535 / 2;
+    c->concurrent = static_cast<uint32_t>(conc);
+    return PA_OK;
+}
+
+size_t ntt_workspace(int path, const TransformCfg &c) {
+    const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
+    const uint64_t pairs = c.tiles_in * c.tiles_out;
+    size_t bytes = round_up(pairs * sizeof(NttPair), 256);
+    if (c.passes > 1) bytes += size_t(c.concurrent) * 2 * (size_t(1) << c.log2n) * elem;
+    return bytes;
+}
+
+// Pair descriptors of one block, in (output tile, key tile) order.
+static void make_pairs(uint64_t n, uint64_t m, const TransformCfg &c, uint32_t blk,
+                       std::vector<NttPair> *out) {
+    for (uint64_t I = 0; I < c.tiles_out; ++I) {
+        for (uint64_t J = 0; J < c.tiles_in; ++J) {
+            NttPair p{};
+            const uint64_t i0 = I * c.M, j0 = J * c.L;
+            p.key_bit0 = static_cast<int64_t>(j0);
+            p.key_len = (n - j0 < c.L) ? n - j0 : c.L;
+            p.K0 = static_cast<uint32_t>(c.L);
+            p.win_bit0 = static_cast<int64_t>(n) - 1 + static_cast<int64_t>(i0) -
+                         static_cast<int64_t>(j0) - static_cast<int64_t>(c.L);
+            p.win_len = c.L + c.M;
+            p.out_bit0 = i0;
+            p.out_len = static_cast<uint32_t>((m - i0 < c.M) ? m - i0 : c.M);
+            p.blk = blk;
+            out->push_back(p);
+        }
+    }
+}
+
+int ntt_init(const PlanCfg &cfg, void *ws) {
+    std::vector<NttPair> pairs;
+    make_pairs(cfg.n, cfg.m, cfg.tr, 0, &pairs);
+    PA_CUDA_TRY(cudaMemcpy(ws, pairs.data(), pairs.size() * sizeof(NttPair), cudaMemcpyHostToDevice));
+    Tables t;
+    if (cfg.path == PA_PATH_NTT31) return get_tables<F31>(0, &t);
+    return get_tables<F64>(1, &t);
+}
+
+namespace {
+
+template <class F>
+int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed, const uint64_t *key,
+                 uint64_t *out, cudaStream_t s, int field) {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    Tables tab;
+    int rc = get_tables<F>(field, &tab);
+    if (rc != PA_OK) return rc;
+    const TransformCfg &c = cfg.tr;
+    const uint64_t npairs = c.tiles_in * c.tiles_out;
+    const NttPair *pairs = static_cast<const NttPair *>(ws);
+    T *spec = reinterpret_cast<T *>(static_cast<char *>(ws) + round_up(npairs * sizeof(NttPair), 256));
+    BlockPtrs one{reinterpret_cast<const uint32_t *>(key), reinterpret_cast<const uint32_t *>(seed),
+                  reinterpret_cast<uint32_t *>(out), cfg.n, cfg.m};
+    const Tw *tf = static_cast<const Tw *>(tab.fwd), *ti = static_cast<const Tw *>(tab.inv);
+    const Tw scale = FieldHost<F>::scale(c.log2n);
+    const int logN = static_cast<int>(c.log2n);
+
+    prof_begin(prof, K_MEMSET, s);
+    PA_CUDA_TRY(cudaMemsetAsync(out, 0, ceil_div(cfg.m, 64) * 8, s));
+    prof_end(prof, s);
+
+    if (c.passes == 1) {
+        const size_t smem = size_t(2) * (size_t(1) << logN) * (sizeof(Tw) + sizeof(T));
+        PA_CUDA_TRY(cudaFuncSetAttribute(ntt_small<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem)));
+        for (uint64_t p0 = 0; p0 < npairs; p0 += 65535) {
+            const uint64_t cnt = npairs - p0 < 65535 ? npairs - p0 : 65535;
+            prof_begin(prof, K_NTT_SMALL, s);
+            ntt_small<F><<<static_cast<unsigned>(cnt), kThreads, smem, s>>>(pairs + p0, nullptr, one,
+                                                                           logN, tf, ti, scale);
+            prof_end(prof, s);
+        }
+        PA_CUDA_TRY(cudaGetLastError());
+        return PA_OK;
+    }
+    const int logR1 = static_cast<int>(c.radix_log2[0]), logR2 = static_cast<int>(c.radix_log2[1]);
+    const int logC1 = sizeof(T) == 4 ? 3 : 2;  // 32-byte row segments
+    const int logC2 = sizeof(T) == 4 ? 2 : 1;
+    const size_t sm1 = (size_t(1) << logR1) * sizeof(Tw) + (size_t(1) << (logR1 + logC1)) * sizeof(T);
+    const size_t sm2 =
+        2 * (size_t(1) << logR2) * sizeof(Tw) + 2 * (size_t(1) << (logR2 + logC2)) * sizeof(T);
+    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_fwd_first<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(sm1)));
+    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_inv_first<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(sm1)));
+    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_fused_last<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(sm2)));
+    const unsigned gx1 = static_cast<unsigned>((uint64_t(1) << (logN - logR1)) >> logC1);
+    const unsigned gx2 = static_cast<unsigned>((uint64_t(1) << logR1) >> logC2);
+    for (uint64_t p0 = 0; p0 < npairs; p0 += c.concurrent) {
+        const uint64_t cnt = npairs - p0 < c.concurrent ? npairs - p0 : c.concurrent;
+        prof_begin(prof, K_NTT_FWD_FIRST, s);
+        ntt_fwd_first<F><<<dim3(gx1, static_cast<unsigned>(2 * cnt)), kThreads, sm1, s>>>(
+            pairs + p0, nullptr, one, logN, logR1, logC1, spec, tf);
+        prof_end(prof, s);
+        prof_begin(prof, K_NTT_FUSED_LAST, s);
+        ntt_fused_last<F><<<dim3(gx2, static_cast<unsigned>(cnt)), kThreads, sm2, s>>>(
+            logN, logR2, logC2, spec, tf, ti);
+        prof_end(prof, s);
+        prof_begin(prof, K_NTT_INV_FIRST, s);
+        ntt_inv_first<F><<<dim3(gx1, static_cast<unsigned>(cnt)), kThreads, sm1, s>>>(
+            pairs + p0, nullptr, one, logN, logR1, logC1, spec, ti, scale);
+        prof_end(prof, s);
+    }
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+}  // namespace
+
+int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+               const uint64_t *key, uint64_t *out, cudaStream_t s) {
+    (void)hdr;
+    if (cfg.path == PA_PATH_NTT31) return launch_field<F31>(cfg, ws, prof, seed, key, out, s, 0);
+    return launch_field<F64>(cfg, ws, prof, seed, key, out, s, 1);
+}
+
+}  // namespace pa

@@ -1,0 +1,93 @@
+// Prime fields of the exact transform path and their host-side root tables.
+//
+// F31: p = 15 * 2^27 + 1 (2-adicity 27). Every convolution coefficient of a tile is a
+//      count of at most L < p bit products, so the residue IS the integer and its low
+//      bit is the hash bit. Twiddles carry Shoup quotients (one high-half multiply
+//      per twiddle product); the pointwise product is a Montgomery product.
+// F64: p = 2^64 - 2^32 + 1 (2-adicity 32); products reduced with 2^64 = 2^32 - 1 mod p.
+#pragma once
+
+#include <stdint.h>
+
+namespace pa {
+
+// Inverse of an odd 32-bit modulus mod 2^32 (Newton iteration, 3 -> 6 -> ... -> 96 bits).
+constexpr uint32_t inverse_mod_2_32(uint32_t p) {
+    uint32_t x = p;
+    for (int i = 0; i < 5; ++i) x *= 2u - p * x;
+    return x;
+}
+
+struct F31 {
+    using T = uint32_t;
+    struct Tw {
+        uint32_t w, q;  // value and Shoup quotient floor(w * 2^32 / p)
+    };
+    static constexpr uint32_t P = 2013265921u;
+    static constexpr int kTwoAdicity = 27;
+    static constexpr uint32_t PINV = inverse_mod_2_32(2013265921u);  // p^-1 mod 2^32
+    static_assert(PINV * 2013265921u == 1u, "Montgomery inverse");
+
+    __device__ static __forceinline__ T add(T a, T b) {
+        T s = a + b;
+        return min(s, s - P);
+    }
+    __device__ static __forceinline__ T sub(T a, T b) {
+        T d = a + (P - b);
+        return min(d, d - P);
+    }
+    __device__ static __forceinline__ T mul_tw(T a, Tw w) {
+        uint32_t q = __umulhi(a, w.q);
+        uint32_t r = a * w.w - q * P;  // in [0, 2p)
+        return min(r, r - P);
+    }
+    // a * b * 2^-32 mod p.
+    __device__ static __forceinline__ T mont(T a, T b) {
+        uint32_t lo = a * b, hi = __umulhi(a, b);
+        uint32_t mq = lo * PINV;
+        uint32_t r = hi - __umulhi(mq, P);  // (ab - mq p) / 2^32, in (-p, p)
+        return static_cast<int32_t>(r) < 0 ? r + P : r;
+    }
+    __device__ static __forceinline__ uint32_t low_bit(T a) { return a & 1u; }
+    __device__ static __forceinline__ Tw neg_tw(Tw w) {
+        // -w mod p with its own quotient: floor((p - w) 2^32 / p) = 2^32 - 1 - q for w != 0.
+        Tw r;
+        r.w = w.w ? P - w.w : 0u;
+        r.q = w.w ? 0xFFFFFFFFu - w.q : 0u;
+        return r;
+    }
+};
+
+struct F64 {
+    using T = uint64_t;
+    using Tw = uint64_t;
+    static constexpr uint64_t P = 0xFFFFFFFF00000001ull;
+    static constexpr uint64_t EPS = 0xFFFFFFFFull;  // 2^64 mod p
+    static constexpr int kTwoAdicity = 32;
+
+    __device__ static __forceinline__ T add(T a, T b) {
+        T s = a + b;
+        if (s < a) return s + EPS;  // wrapped: a+b-2^64+(2^32-1) < p
+        return s >= P ? s - P : s;
+    }
+    __device__ static __forceinline__ T sub(T a, T b) {
+        T d = a - b;
+        return a < b ? d - EPS : d;  // a-b+2^64-(2^32-1) = a-b+p
+    }
+    __device__ static __forceinline__ T reduce128(uint64_t lo, uint64_t hi) {
+        const uint64_t hh = hi >> 32, hl = hi & EPS;
+        uint64_t t0 = lo - hh;
+        if (lo < hh) t0 -= EPS;
+        const uint64_t t1 = hl * EPS;
+        uint64_t r = t0 + t1;
+        if (r < t1) r += EPS;
+        return r >= P ? r - P : r;
+    }
+    __device__ static __forceinline__ T mul(T a, T b) { return reduce128(a * b, __umul64hi(a, b)); }
+    __device__ static __forceinline__ T mul_tw(T a, Tw w) { return mul(a, w); }
+    __device__ static __forceinline__ T mont(T a, T b) { return mul(a, b); }
+    __device__ static __forceinline__ uint32_t low_bit(T a) { return static_cast<uint32_t>(a & 1u); }
+    __device__ static __forceinline__ Tw neg_tw(Tw w) { return w ? P - w : 0; }
+};
+
+}  // namespace pa

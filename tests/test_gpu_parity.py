@@ -110,7 +110,8 @@ def test_finite_size_sampled_rows(path):
     gbits = oracle.unpack(got, b.m)[rows]
     assert np.array_equal(gbits, want), f"{path}: sampled rows differ ({desc})"
     # Output tail bits zero.
-    assert int(got[-1]) >> (b.m % 64) == 0
+    if b.m % 64:
+        assert int(got[-1]) >> (b.m % 64) == 0
     # Linearity in the key holds at any size: h(x1 ^ x2) = h(x1) ^ h(x2).
     key2 = inputs.random_bits(b.n, 777)
     g2, _ = run_path(b.n, b.m, key2, seed, path=path)
