@@ -121,6 +121,13 @@ int pa_hash_host(pa_plan_t plan, const uint64_t *seed_host, const uint64_t *key_
  * proven bound (synchronises the plan's stream). Other paths report 0. */
 int pa_last_residual(pa_plan_t plan, double *residual, double *bound);
 
+/* The proven bound on |v - rint(v)| used by the FFT path for a tile of transform
+ * size 2^log2_transform, key sub-block tile_in and output sub-block tile_out, for
+ * FP32 (fp64 = 0) or FP64 butterflies. A tile is used only if its bound is < 1/2.
+ * Host only. */
+int pa_fft_rounding_bound(uint32_t log2_transform, uint64_t tile_in, uint64_t tile_out, int fp64,
+                          double *bound);
+
 /* Device-side status of the plan's last call: PA_OK, or PA_ERR_TIMEOUT if a
  * bounded wait in a kernel gave up (synchronises the plan's stream). */
 int pa_plan_status(pa_plan_t plan);

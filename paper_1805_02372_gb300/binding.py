@@ -93,6 +93,8 @@ SIGNATURES = {
     "pa_last_residual": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
     "pa_plan_status": (ctypes.c_int, [_VP]),
+    "pa_fft_rounding_bound": (ctypes.c_int, [ctypes.c_uint32, _U64, _U64, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_double)]),
     "pa_batch_plan": (ctypes.c_int, [ctypes.POINTER(pa_block), ctypes.c_size_t,
                                      ctypes.POINTER(pa_opts), ctypes.POINTER(_VP)]),
     "pa_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
@@ -227,6 +229,13 @@ def pa_last_residual(plan: int) -> tuple[float, float]:
     r, b = ctypes.c_double(), ctypes.c_double()
     _check(load().pa_last_residual(plan, ctypes.byref(r), ctypes.byref(b)), "pa_last_residual")
     return r.value, b.value
+
+
+def pa_fft_rounding_bound(log2_transform: int, tile_in: int, tile_out: int, fp64: bool) -> float:
+    b = ctypes.c_double()
+    _check(load().pa_fft_rounding_bound(log2_transform, tile_in, tile_out, int(fp64),
+                                        ctypes.byref(b)), "pa_fft_rounding_bound")
+    return b.value
 
 
 def pa_plan_status(plan: int) -> int:

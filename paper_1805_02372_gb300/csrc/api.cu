@@ -56,6 +56,7 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
         case PA_PATH_FFT:
             rc = fft_plan(n, m, o, &cfg->tr);
             cfg->ws_bytes = fft_workspace(cfg->tr);
+            cfg->kernels = 1 + static_cast<uint32_t>((cfg->tr.tiles_in * cfg->tr.tiles_out) >> 30);
             break;
         case PA_PATH_BLOCK_INT8:
             rc = block_plan(n, m, o, &cfg->blk);

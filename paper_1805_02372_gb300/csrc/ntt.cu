@@ -28,31 +28,14 @@
 
 #include "common.cuh"
 #include "ntt_field.cuh"
+#include "tiles.cuh"
+#include "dft.cuh"
 
 namespace pa {
 
 constexpr int kLogMax = 22;           // largest transform: 2^22
 constexpr int kLogSmallMax = 12;      // one-CTA transforms up to 2^12
 constexpr int kThreads = 512;
-
-struct NttPair {
-    int64_t key_bit0;   // first key bit of the tile
-    uint64_t key_len;   // valid key bits in the tile
-    int64_t win_bit0;   // seed bit of window position 0 (may be negative)
-    uint64_t win_len;   // window positions read (beyond: 0)
-    uint64_t out_bit0;  // first output row of the tile (multiple of 64)
-    uint32_t out_len;   // valid output rows
-    uint32_t K0;        // convolution index of output row out_bit0
-    uint32_t blk;       // block index (batched launches)
-    uint32_t pad;
-};
-
-struct BlockPtrs {
-    const uint32_t *key32;
-    const uint32_t *seed32;
-    uint32_t *out32;
-    uint64_t n, m;
-};
 
 // ---------------------------------------------------------------- host tables
 
@@ -162,21 +145,6 @@ int get_tables(int field, Tables *out) {
 
 // ---------------------------------------------------------------- device pieces
 
-__device__ __forceinline__ uint32_t get_bit(const uint32_t *__restrict__ v, uint64_t pos) {
-    return (__ldg(v + (pos >> 5)) >> (pos & 31)) & 1u;
-}
-
-__device__ __forceinline__ uint32_t key_bit(const NttPair &pr, const BlockPtrs &bp, uint64_t t) {
-    return t < pr.key_len ? get_bit(bp.key32, uint64_t(pr.key_bit0) + t) : 0u;
-}
-
-__device__ __forceinline__ uint32_t win_bit(const NttPair &pr, const BlockPtrs &bp, uint64_t u) {
-    if (u >= pr.win_len) return 0u;
-    const int64_t p = pr.win_bit0 + static_cast<int64_t>(u);
-    if (p < 0 || static_cast<uint64_t>(p) >= bp.n + bp.m - 1) return 0u;
-    return get_bit(bp.seed32, static_cast<uint64_t>(p));
-}
-
 // Twiddle w^E (E < 2^kLogMax) from a half table: w^(E + 2^(kLogMax-1)) = -w^E.
 template <class F>
 __device__ __forceinline__ typename F::Tw tw_at(const typename F::Tw *__restrict__ tab, uint32_t E) {
@@ -185,150 +153,11 @@ __device__ __forceinline__ typename F::Tw tw_at(const typename F::Tw *__restrict
     return F::neg_tw(tab[E - half]);
 }
 
-// Stage tables of an R-point transform into shared memory: st[h-1+j] = w_{2h}^(+-j).
-template <class F>
-__device__ void load_stage_tables(typename F::Tw *st, const typename F::Tw *__restrict__ tab,
-                                  int logR) {
-    const int R = 1 << logR;
-    for (int idx = threadIdx.x; idx < R - 1; idx += blockDim.x) {
-        const int lh = 31 - __clz(idx + 1);
-        const uint32_t j = static_cast<uint32_t>(idx + 1 - (1 << lh));
-        st[idx] = tab[j << (kLogMax - 1 - lh)];
-    }
-}
-
-// Element (r, c) of a shared tile at base[r*rs + c*cs]. CF: consecutive threads take
-// consecutive columns (when cs == 1), else consecutive rows (when rs == 1).
-template <class F, bool CF>
-__device__ __forceinline__ void dif_round4(typename F::T *sm, int logR, int logC, int rs, int cs,
-                                           int lq, const typename F::Tw *tw) {
-    using T = typename F::T;
-    const int q = 1 << lq, h = 2 * q;
-    const int logG = logR - 2;
-    const int total = 1 << (logG + logC);
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int c, g;
-        if (CF) {
-            c = w & ((1 << logC) - 1);
-            g = w >> logC;
-        } else {
-            g = w & ((1 << logG) - 1);
-            c = w >> logG;
-        }
-        const int j = g & (q - 1);
-        const int i0 = ((g >> lq) << (lq + 2)) + j;
-        T *b = sm + c * cs;
-        const T x0 = b[i0 * rs], x1 = b[(i0 + q) * rs], x2 = b[(i0 + 2 * q) * rs],
-                x3 = b[(i0 + 3 * q) * rs];
-        const typename F::Tw w1 = tw[h - 1 + j], w2 = tw[h - 1 + j + q], w3 = tw[q - 1 + j];
-        const T y0 = F::add(x0, x2), y2 = F::mul_tw(F::sub(x0, x2), w1);
-        const T y1 = F::add(x1, x3), y3 = F::mul_tw(F::sub(x1, x3), w2);
-        b[i0 * rs] = F::add(y0, y1);
-        b[(i0 + q) * rs] = F::mul_tw(F::sub(y0, y1), w3);
-        b[(i0 + 2 * q) * rs] = F::add(y2, y3);
-        b[(i0 + 3 * q) * rs] = F::mul_tw(F::sub(y2, y3), w3);
-    }
-}
-
-template <class F, bool CF>
-__device__ __forceinline__ void dit_round4(typename F::T *sm, int logR, int logC, int rs, int cs,
-                                           int lq, const typename F::Tw *tw) {
-    using T = typename F::T;
-    const int q = 1 << lq, h = 2 * q;
-    const int logG = logR - 2;
-    const int total = 1 << (logG + logC);
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int c, g;
-        if (CF) {
-            c = w & ((1 << logC) - 1);
-            g = w >> logC;
-        } else {
-            g = w & ((1 << logG) - 1);
-            c = w >> logG;
-        }
-        const int j = g & (q - 1);
-        const int i0 = ((g >> lq) << (lq + 2)) + j;
-        T *b = sm + c * cs;
-        const T z0 = b[i0 * rs], z1 = b[(i0 + q) * rs], z2 = b[(i0 + 2 * q) * rs],
-                z3 = b[(i0 + 3 * q) * rs];
-        const typename F::Tw w1 = tw[h - 1 + j], w2 = tw[h - 1 + j + q], w3 = tw[q - 1 + j];
-        T t = F::mul_tw(z1, w3);
-        const T y0 = F::add(z0, t), y1 = F::sub(z0, t);
-        t = F::mul_tw(z3, w3);
-        const T y2 = F::add(z2, t), y3 = F::sub(z2, t);
-        t = F::mul_tw(y2, w1);
-        b[i0 * rs] = F::add(y0, t);
-        b[(i0 + 2 * q) * rs] = F::sub(y0, t);
-        t = F::mul_tw(y3, w2);
-        b[(i0 + q) * rs] = F::add(y1, t);
-        b[(i0 + 3 * q) * rs] = F::sub(y1, t);
-    }
-}
-
-template <class F, bool CF, bool DIF>
-__device__ __forceinline__ void round2(typename F::T *sm, int logR, int logC, int rs, int cs,
-                                       const typename F::Tw *tw) {
-    // single stage with half-size 1: pairs (2g, 2g+1), twiddle w_2^0 = 1
-    using T = typename F::T;
-    const int logG = logR - 1;
-    const int total = 1 << (logG + logC);
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int c, g;
-        if (CF) {
-            c = w & ((1 << logC) - 1);
-            g = w >> logC;
-        } else {
-            g = w & ((1 << logG) - 1);
-            c = w >> logG;
-        }
-        T *b = sm + c * cs;
-        const T a = b[(2 * g) * rs], d = b[(2 * g + 1) * rs];
-        b[(2 * g) * rs] = F::add(a, d);
-        b[(2 * g + 1) * rs] = F::sub(a, d);
-    }
-    (void)tw;
-}
-
-// Forward R-point DIF on every column (natural in, bit-reversed out).
-template <class F, bool CF>
-__device__ void dif_columns(typename F::T *sm, int logR, int logC, int rs, int cs,
-                            const typename F::Tw *tw) {
-    int lq = logR - 2;
-    for (; lq >= 0; lq -= 2) {
-        dif_round4<F, CF>(sm, logR, logC, rs, cs, lq, tw);
-        __syncthreads();
-    }
-    if (logR & 1) {
-        round2<F, CF, true>(sm, logR, logC, rs, cs, tw);
-        __syncthreads();
-    }
-}
-
-// Inverse R-point DIT on every column (bit-reversed in, natural out, unnormalised).
-template <class F, bool CF>
-__device__ void dit_columns(typename F::T *sm, int logR, int logC, int rs, int cs,
-                            const typename F::Tw *tw) {
-    int lq = 0;
-    if (logR & 1) {
-        round2<F, CF, false>(sm, logR, logC, rs, cs, tw);
-        __syncthreads();
-        lq = 1;
-    }
-    for (; lq <= logR - 2; lq += 2) {
-        dit_round4<F, CF>(sm, logR, logC, rs, cs, lq, tw);
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ BlockPtrs pick(const BlockPtrs *blks, const BlockPtrs &one, uint32_t b) {
-    return blks ? blks[b] : one;
-}
-
 // ---------------------------------------------------------------- kernels
 
 // One CTA per tile; the whole transform of size 2^logN <= 2^12 in shared memory.
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_small(const NttPair *__restrict__ pairs,
+__global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict__ pairs,
                                                       const BlockPtrs *__restrict__ blks,
                                                       BlockPtrs one, int logN,
                                                       const typename F::Tw *__restrict__ tfwd,
@@ -341,10 +170,10 @@ __global__ void __launch_bounds__(kThreads) ntt_small(const NttPair *__restrict_
     Tw *stf = reinterpret_cast<Tw *>(smraw);
     Tw *sti = stf + N;
     T *sm = reinterpret_cast<T *>(sti + N);  // column 0: key tile, column 1: window
-    const NttPair pr = pairs[blockIdx.x];
+    const TilePair pr = pairs[blockIdx.x];
     const BlockPtrs bp = pick(blks, one, pr.blk);
-    load_stage_tables<F>(stf, tfwd, logN);
-    load_stage_tables<F>(sti, tinv, logN);
+    load_stage_tables<F>(stf, tfwd, logN, kLogMax);
+    load_stage_tables<F>(sti, tinv, logN, kLogMax);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
         sm[t] = key_bit(pr, bp, t);
         sm[N + t] = win_bit(pr, bp, t);
@@ -370,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) ntt_small(const NttPair *__restrict_
 // tile (blockIdx.y even) or the seed window (odd); writes spectra to ws.
 template <class F>
 __global__ void __launch_bounds__(kThreads) ntt_fwd_first(
-    const NttPair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
+    const TilePair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
     int logN, int logR1, int logC, typename F::T *__restrict__ ws,
     const typename F::Tw *__restrict__ tfwd) {
     using T = typename F::T;
@@ -381,10 +210,10 @@ __global__ void __launch_bounds__(kThreads) ntt_fwd_first(
     T *sm = reinterpret_cast<T *>(st + R1);
     const int which = blockIdx.y & 1;
     const uint32_t pi = blockIdx.y >> 1;
-    const NttPair pr = pairs[pi];
+    const TilePair pr = pairs[pi];
     const BlockPtrs bp = pick(blks, one, pr.blk);
     const uint64_t c0 = uint64_t(blockIdx.x) << logC;
-    load_stage_tables<F>(st, tfwd, logR1);
+    load_stage_tables<F>(st, tfwd, logR1, kLogMax);
     for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
         const int r = e >> logC, c = e & (C - 1);
         const uint64_t t = (uint64_t(r) << logS) + c0 + c;
@@ -420,8 +249,8 @@ __global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2, 
     T *X = ws + (uint64_t(pi) * 2) * (uint64_t(1) << logN);
     T *W = X + (uint64_t(1) << logN);
     const uint64_t row0 = uint64_t(blockIdx.x) << logC;
-    load_stage_tables<F>(stf, tfwd, logR2);
-    load_stage_tables<F>(sti, tinv, logR2);
+    load_stage_tables<F>(stf, tfwd, logR2, kLogMax);
+    load_stage_tables<F>(sti, tinv, logR2, kLogMax);
     const int cnt = R2 << logC;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         sm[e] = X[(row0 << logR2) + e];
@@ -438,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2, 
 // Inverse pass 1 on C columns of the product, scale, low bit, XOR output bytes.
 template <class F>
 __global__ void __launch_bounds__(kThreads) ntt_inv_first(
-    const NttPair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
+    const TilePair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
     int logN, int logR1, int logC, const typename F::T *__restrict__ ws,
     const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
     using T = typename F::T;
@@ -448,11 +277,11 @@ __global__ void __launch_bounds__(kThreads) ntt_inv_first(
     Tw *st = reinterpret_cast<Tw *>(smraw);
     T *sm = reinterpret_cast<T *>(st + R1);
     const uint32_t pi = blockIdx.y;
-    const NttPair pr = pairs[pi];
+    const TilePair pr = pairs[pi];
     const BlockPtrs bp = pick(blks, one, pr.blk);
     const uint64_t c0 = uint64_t(blockIdx.x) << logC;
     const T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
-    load_stage_tables<F>(st, tinv, logR1);
+    load_stage_tables<F>(st, tinv, logR1, kLogMax);
     for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
         const int r = e >> logC, c = e & (C - 1);
         const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
@@ -577,36 +406,15 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
 size_t ntt_workspace(int path, const TransformCfg &c) {
     const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
     const uint64_t pairs = c.tiles_in * c.tiles_out;
-    size_t bytes = round_up(pairs * sizeof(NttPair), 256);
+    size_t bytes = round_up(pairs * sizeof(TilePair), 256);
     if (c.passes > 1) bytes += size_t(c.concurrent) * 2 * (size_t(1) << c.log2n) * elem;
     return bytes;
 }
 
-// Pair descriptors of one block, in (output tile, key tile) order.
-static void make_pairs(uint64_t n, uint64_t m, const TransformCfg &c, uint32_t blk,
-                       std::vector<NttPair> *out) {
-    for (uint64_t I = 0; I < c.tiles_out; ++I) {
-        for (uint64_t J = 0; J < c.tiles_in; ++J) {
-            NttPair p{};
-            const uint64_t i0 = I * c.M, j0 = J * c.L;
-            p.key_bit0 = static_cast<int64_t>(j0);
-            p.key_len = (n - j0 < c.L) ? n - j0 : c.L;
-            p.K0 = static_cast<uint32_t>(c.L);
-            p.win_bit0 = static_cast<int64_t>(n) - 1 + static_cast<int64_t>(i0) -
-                         static_cast<int64_t>(j0) - static_cast<int64_t>(c.L);
-            p.win_len = c.L + c.M;
-            p.out_bit0 = i0;
-            p.out_len = static_cast<uint32_t>((m - i0 < c.M) ? m - i0 : c.M);
-            p.blk = blk;
-            out->push_back(p);
-        }
-    }
-}
-
 int ntt_init(const PlanCfg &cfg, void *ws) {
-    std::vector<NttPair> pairs;
+    std::vector<TilePair> pairs;
     make_pairs(cfg.n, cfg.m, cfg.tr, 0, &pairs);
-    PA_CUDA_TRY(cudaMemcpy(ws, pairs.data(), pairs.size() * sizeof(NttPair), cudaMemcpyHostToDevice));
+    PA_CUDA_TRY(cudaMemcpy(ws, pairs.data(), pairs.size() * sizeof(TilePair), cudaMemcpyHostToDevice));
     Tables t;
     if (cfg.path == PA_PATH_NTT31) return get_tables<F31>(0, &t);
     return get_tables<F64>(1, &t);
@@ -624,8 +432,8 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
     if (rc != PA_OK) return rc;
     const TransformCfg &c = cfg.tr;
     const uint64_t npairs = c.tiles_in * c.tiles_out;
-    const NttPair *pairs = static_cast<const NttPair *>(ws);
-    T *spec = reinterpret_cast<T *>(static_cast<char *>(ws) + round_up(npairs * sizeof(NttPair), 256));
+    const TilePair *pairs = static_cast<const TilePair *>(ws);
+    T *spec = reinterpret_cast<T *>(static_cast<char *>(ws) + round_up(npairs * sizeof(TilePair), 256));
     BlockPtrs one{reinterpret_cast<const uint32_t *>(key), reinterpret_cast<const uint32_t *>(seed),
                   reinterpret_cast<uint32_t *>(out), cfg.n, cfg.m};
     const Tw *tf = static_cast<const Tw *>(tab.fwd), *ti = static_cast<const Tw *>(tab.inv);

@@ -53,3 +53,33 @@ def test_plan_query_direct(lib, n, m):
     d = pkg.pa_plan_query(n, m, binding.make_opts(path="direct"))
     assert d["path_name"] == "direct" and d["n"] == n and d["m"] == m
     assert d["workspace_bytes"] >= 4 * ((n + 31) // 32)
+
+
+def test_fft_bound_properties(lib):
+    b = pkg.pa_fft_rounding_bound
+    # grows with the key tile, the output tile and the transform size; FP64 far smaller
+    assert b(12, 512, 1024, False) < b(12, 1024, 1024, False) < b(12, 1024, 2048, False)
+    assert b(11, 512, 512, False) < b(12, 512, 512, False)
+    assert b(12, 2048, 2048, True) < 1e-8 < b(12, 32, 64, False)
+    # the worst-case inverse term alone: alpha * L * sqrt(L + M) with alpha >= k * u
+    assert b(12, 2048, 2048, False) > 12 * 2 ** -24 * 2048 * 4096 ** 0.5
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (100_003, 25_000), (1_000_000, 500_000),
+                                 (100_000_007, 10_000_000)])
+def test_fft_planner_stays_under_half(lib, n, m):
+    d = pkg.pa_plan_query(n, m, binding.make_opts(path="fft"))
+    assert d["fp64"] == 0 and 0 < d["rounding_bound"] < 0.5
+    assert d["tile_in"] + d["tile_out"] <= 1 << d["log2_transform"]
+    assert d["rounding_bound"] == pkg.pa_fft_rounding_bound(d["log2_transform"], d["tile_in"],
+                                                            d["tile_out"], False)
+
+
+def test_fft_fp64_only_where_fp32_bound_fails(lib):
+    # N = 2^12 with L = M = 2048: the FP32 bound exceeds 1/2, so FP64 butterflies.
+    d = pkg.pa_plan_query(100_000, 50_000, binding.make_opts(path="fft", log2_transform=12,
+                                                              tile_in=2048, tile_out=2048))
+    assert d["fp64"] == 1 and d["rounding_bound"] < 1e-8
+    d = pkg.pa_plan_query(100_000, 50_000, binding.make_opts(path="fft", log2_transform=12,
+                                                              tile_in=1024, tile_out=2048))
+    assert d["fp64"] == 0 and d["rounding_bound"] < 0.5
