@@ -61,6 +61,7 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
         case PA_PATH_BLOCK_INT8:
             rc = block_plan(n, m, o, &cfg->blk);
             cfg->ws_bytes = block_workspace(cfg->blk);
+            cfg->kernels = 2 + (cfg->blk.grid_y > 1 ? 1 : 0);
             break;
     }
     return rc;

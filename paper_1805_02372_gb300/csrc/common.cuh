@@ -76,6 +76,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
 
 // ---- bit helpers ----
 
+__device__ __forceinline__ uint64_t ceil_div_dev(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
 // 32 bits of a packed string starting at bit position `bit` (may be negative:
 // positions < 0 read as 0). `words` is the number of valid 32-bit words; positions
 // past them read as 0.

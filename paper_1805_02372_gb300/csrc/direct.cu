@@ -117,6 +117,15 @@ int direct_plan(uint64_t n, uint64_t m, DirectCfg *c) {
     return PA_OK;
 }
 
+void reverse_key_launch(const uint64_t *key, uint64_t n, uint32_t *xr, uint64_t words,
+                        uint64_t words_pad, cudaStream_t s) {
+    uint64_t blocks = ceil_div(words_pad, 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks == 0) blocks = 1;
+    reverse_key_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
+        reinterpret_cast<const uint32_t *>(key), 2 * ceil_div(n, 64), n, xr, words, words_pad);
+}
+
 size_t direct_workspace(const DirectCfg &c) { return round_up(c.key_words32_pad * 4, 256); }
 
 int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,

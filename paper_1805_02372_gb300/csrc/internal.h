@@ -34,9 +34,10 @@ struct TransformCfg {
 
 // ---- block-Toeplitz tensor-core path ----
 struct BlockCfg {
-    uint32_t b = 0;              // tile edge
-    uint64_t kc = 0;             // key chunk (positions) per CTA
+    uint32_t b = 0;              // tile edge (rows of each T_d)
+    uint64_t kc = 0;             // contraction positions per CTA (multiple of 32)
     uint32_t grid_x = 0, grid_y = 0;
+    uint64_t xr_words = 0, xr_words_pad = 0;  // reversed key in the workspace
 };
 
 struct PlanCfg {
@@ -98,6 +99,9 @@ void prof_free(Prof *p);
 
 // Launchers (enqueue on stream; return PA_OK or PA_ERR_CUDA).
 int direct_plan(uint64_t n, uint64_t m, DirectCfg *c);
+// xr[q] bit c = x[n-1-32q-c] for q < words, zero up to words_pad.
+void reverse_key_launch(const uint64_t *key, uint64_t n, uint32_t *xr, uint64_t words,
+                        uint64_t words_pad, cudaStream_t s);
 size_t direct_workspace(const DirectCfg &c);
 int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                   const uint64_t *key, uint64_t *out, cudaStream_t s);

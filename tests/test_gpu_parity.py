@@ -145,3 +145,10 @@ def test_host_entry_point(path):
     plan.hash_host(np.ascontiguousarray(seed), np.ascontiguousarray(key), out)
     plan.close()
     assert np.array_equal(out, want)
+
+
+@pytest.mark.parametrize("b", [128, 256, 512])
+@pytest.mark.parametrize("n,m", [(1, 1), (777, 9000), (100_003, 25_000), (33_333, 70_001)])
+def test_block_tile_sizes(b, n, m):
+    key, seed, want = _case(n, m, 21 + n, 23 + m)
+    _check("block_int8", n, m, key, seed, want, block_b=b)
