@@ -67,7 +67,9 @@ typedef struct {
     uint64_t tile_in;          /* key sub-block length L (the paper's batch length)       */
     uint64_t tile_out;         /* output sub-block length M (column split of Sec. 3)      */
     uint32_t force_fp64;       /* FFT path: use FP64 butterflies even where FP32 is proven */
-    uint32_t reserved[7];
+    uint32_t max_slots;        /* batches: at most this many transform spectra resident at
+                                  once (reused round-robin, >= 4); 0 = automatic         */
+    uint32_t reserved[6];
 } pa_opts;
 
 /* What a plan decided (pa_plan_query / pa_plan_describe). */
@@ -163,6 +165,14 @@ int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_
  * synchronises the stream to fill it. */
 int pa_batch_run(pa_batch_t batch, const pa_block *blocks, size_t count, void *stream,
                  pa_report *rep);
+
+/* Same as pa_batch_run with HOST bit buffers: copies every key and seed to device
+ * staging owned by the batch, runs, copies the outputs back, synchronises. */
+int pa_batch_run_host(pa_batch_t batch, const pa_block *host_blocks, size_t count, void *stream,
+                      pa_report *rep);
+
+/* The path (pa_path) the batch plan chose for each block. */
+int pa_batch_describe(pa_batch_t batch, uint32_t *paths, size_t count);
 
 void pa_batch_destroy(pa_batch_t batch);
 

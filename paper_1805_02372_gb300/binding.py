@@ -38,7 +38,8 @@ class pa_opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("log2_transform", ctypes.c_uint32), ("block_b", ctypes.c_uint32),
                 ("tile_in", ctypes.c_uint64), ("tile_out", ctypes.c_uint64),
-                ("force_fp64", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+                ("force_fp64", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
 
 
 class pa_plan_desc(ctypes.Structure):
@@ -100,6 +101,9 @@ SIGNATURES = {
     "pa_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
                                     ctypes.POINTER(pa_report)]),
     "pa_batch_destroy": (None, [_VP]),
+    "pa_batch_run_host": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
+                                         ctypes.POINTER(pa_report)]),
+    "pa_batch_describe": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.c_size_t]),
     "pa_hash_batched": (ctypes.c_int, [ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
                                        ctypes.POINTER(pa_report)]),
     "pa_plan_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -176,12 +180,13 @@ def _stream(s) -> int | None:
 
 
 def make_opts(path=PA_PATH_AUTO, device=-1, log2_transform=0, block_b=0, tile_in=0,
-              tile_out=0, force_fp64=0) -> pa_opts:
+              tile_out=0, force_fp64=0, max_slots=0) -> pa_opts:
     if isinstance(path, str):
         path = PATHS[path]
     o = pa_opts()
     o.path, o.device, o.log2_transform, o.block_b = path, device, log2_transform, block_b
     o.tile_in, o.tile_out, o.force_fp64 = tile_in, tile_out, force_fp64
+    o.max_slots = max_slots
     return o
 
 
@@ -266,6 +271,21 @@ def pa_batch_run(batch: int, blocks, stream=None, report: bool = False) -> dict 
     _check(load().pa_batch_run(batch, arr, cnt, _stream(stream),
                                ctypes.byref(rep) if rep else None), "pa_batch_run")
     return rep.as_dict() if rep else None
+
+
+def pa_batch_run_host(batch: int, blocks, stream=None, report: bool = False) -> dict | None:
+    """blocks: (n, m, seed, key, out) with HOST buffers (numpy or pinned tensors)."""
+    arr, cnt = _blocks(blocks)
+    rep = pa_report() if report else None
+    _check(load().pa_batch_run_host(batch, arr, cnt, _stream(stream),
+                                    ctypes.byref(rep) if rep else None), "pa_batch_run_host")
+    return rep.as_dict() if rep else None
+
+
+def pa_batch_describe(batch: int, count: int) -> list:
+    arr = (ctypes.c_uint32 * count)()
+    _check(load().pa_batch_describe(batch, arr, count), "pa_batch_describe")
+    return [PATH_NAMES.get(int(v), "?") for v in arr]
 
 
 def pa_batch_destroy(batch: int) -> None:

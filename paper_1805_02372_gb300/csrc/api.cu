@@ -144,6 +144,17 @@ int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
     *out = nullptr;
     pa_plan_s *p = new (std::nothrow) pa_plan_s();
     if (!p) return PA_ERR_NOMEM;
+    pa_opts tuned;
+    if ((!opts || opts->path == PA_PATH_AUTO) && n > 0 && m > 0) {
+        // AUTO: the autotuner's measured-cost choice (calibrates once per device)
+        int trc = tuned_opts(n, m, &tuned);
+        if (trc != PA_OK) {
+            delete p;
+            return trc;
+        }
+        if (opts) tuned.device = opts->device;
+        opts = &tuned;
+    }
     int rc = plan_resolve(n, m, opts, &p->cfg);
     if (rc != PA_OK) {
         delete p;

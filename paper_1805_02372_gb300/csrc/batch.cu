@@ -1,9 +1,656 @@
-#include "internal.h"
-extern "C" {
-int pa_batch_plan(const pa_block *, size_t, const pa_opts *, pa_batch_t *out) { if (out) *out = nullptr; return PA_ERR_UNSUPPORTED; }
-int pa_batch_run(pa_batch_t, const pa_block *, size_t, void *, pa_report *) { return PA_ERR_UNSUPPORTED; }
-void pa_batch_destroy(pa_batch_t) {}
-int pa_batch_profile(pa_batch_t, int) { return PA_ERR_UNSUPPORTED; }
-int pa_batch_kernel_times(pa_batch_t, pa_kernel_time *, int, int *) { return PA_ERR_UNSUPPORTED; }
-int pa_hash_batched(const pa_block *, size_t, void *, pa_report *) { return PA_ERR_UNSUPPORTED; }
+// Many independent blocks at once (Sec. 3: batches run in parallel on the GPU;
+// Sec. 4: later batches wait for resources), plus the autotuner that picks each
+// block's path and tile geometry from measured costs.
+//
+// A batch plan assigns each block a path. All exact-transform blocks of one prime
+// field become tiles of ONE persistent launch (ntt_persistent); blocks the tuner
+// gives to another path get their own launches. The whole sequence (output zeroing,
+// the persistent launch, the other launches) is captured once in a CUDA graph and
+// replayed while the stream and the buffers of non-persistent blocks are unchanged;
+// block pointers of persistent tiles are read from a device table each run.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "tiles.cuh"
+
+namespace pa {
+
+// ---------------------------------------------------------------- autotuner
+
+namespace {
+
+constexpr int kTuneLogMin = 8, kTuneLogMax = 22;
+
+struct Tuner {
+    bool valid = false;
+    double direct = 0;           // s per bit product
+    double block[3] = {0, 0, 0};  // s per (m * (n + 8192)), b = 128, 256, 512
+    double fft = 0;              // s per tile of the default FP32 geometry (per unit N log N)
+    double ntt[2][kTuneLogMax + 1] = {};  // s per tile of size 2^k, field 0 / 1
+    double launch = 3e-6;        // s per launch
+};
+
+std::mutex g_tune_mu;
+Tuner g_tuner[64];
+
+__global__ void fill_pattern(uint32_t *p, uint64_t words, uint32_t salt) {
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < words;
+         i += uint64_t(gridDim.x) * blockDim.x) {
+        uint32_t z = static_cast<uint32_t>(i) * 0x9E3779B9u + salt;
+        z ^= z >> 16;
+        z *= 0x85EBCA6Bu;
+        z ^= z >> 13;
+        p[i] = z;
+    }
 }
+
+// Time one plan on synthetic bits (best of a few runs after a warm-up).
+double time_plan(const PlanCfg &cfg, uint64_t *key, uint64_t *seed, uint64_t *out, cudaStream_t s) {
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, kHeaderBytes + cfg.ws_bytes) != cudaSuccess) return INFINITY;
+    cudaMemset(mem, 0, kHeaderBytes);
+    DevHeader *hdr = static_cast<DevHeader *>(mem);
+    void *ws = static_cast<char *>(mem) + kHeaderBytes;
+    if ((cfg.path == PA_PATH_NTT31 || cfg.path == PA_PATH_NTT64) && ntt_init(cfg, ws) != PA_OK) {
+        cudaFree(mem);
+        return INFINITY;
+    }
+    auto run = [&]() -> int {
+        switch (cfg.path) {
+            case PA_PATH_DIRECT: return direct_launch(cfg, ws, hdr, nullptr, seed, key, out, s);
+            case PA_PATH_NTT31:
+            case PA_PATH_NTT64: return ntt_launch(cfg, ws, hdr, nullptr, seed, key, out, s);
+            case PA_PATH_FFT: return fft_launch(cfg, ws, hdr, nullptr, seed, key, out, s);
+            default: return block_launch(cfg, ws, hdr, nullptr, seed, key, out, s);
+        }
+    };
+    double best = INFINITY;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    if (run() == PA_OK && cudaStreamSynchronize(s) == cudaSuccess) {
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(a, s);
+            if (run() != PA_OK) break;
+            cudaEventRecord(b, s);
+            if (cudaEventSynchronize(b) != cudaSuccess) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            best = std::min(best, ms * 1e-3);
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamSynchronize(s);
+    cudaFree(mem);
+    return best;
+}
+
+int calibrate(Tuner *t) {
+    const uint64_t max_bits = uint64_t(13) << 20;  // key and seed capacity
+    uint64_t *key = nullptr, *seed = nullptr, *out = nullptr;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&key, max_bits / 8 + 64);
+    if (e == cudaSuccess) e = cudaMalloc(&seed, 2 * max_bits / 8 + 64);
+    if (e == cudaSuccess) e = cudaMalloc(&out, max_bits / 8 + 64);
+    if (e != cudaSuccess) {
+        cudaFree(key);
+        cudaFree(seed);
+        cudaFree(out);
+        if (s) cudaStreamDestroy(s);
+        return cuda_fail(e);
+    }
+    fill_pattern<<<256, 256, 0, s>>>(reinterpret_cast<uint32_t *>(key), max_bits / 32, 1);
+    fill_pattern<<<256, 256, 0, s>>>(reinterpret_cast<uint32_t *>(seed), 2 * max_bits / 32, 2);
+    auto tplan = [&](uint64_t n, uint64_t m, const pa_opts &o, PlanCfg *cfg) -> double {
+        if (plan_resolve(n, m, &o, cfg) != PA_OK) return INFINITY;
+        return time_plan(*cfg, key, seed, out, s);
+    };
+    PlanCfg cfg;
+    pa_opts o;
+    memset(&o, 0, sizeof(o));
+    o.device = -1;
+    o.path = PA_PATH_DIRECT;
+    {
+        const uint64_t n = uint64_t(1) << 20, m = uint64_t(1) << 13;
+        t->direct = tplan(n, m, o, &cfg) / (double(n) * m);
+    }
+    o.path = PA_PATH_BLOCK_INT8;
+    for (int i = 0; i < 3; ++i) {
+        o.block_b = 128u << i;
+        const uint64_t n = uint64_t(1) << 20, m = uint64_t(1) << 14;
+        t->block[i] = tplan(n, m, o, &cfg) / (double(m) * (n + 8192));
+    }
+    o.block_b = 0;
+    o.path = PA_PATH_FFT;
+    {
+        const uint64_t n = uint64_t(1) << 18, m = uint64_t(1) << 13;
+        const double tt = tplan(n, m, o, &cfg);
+        t->fft = tt / double(cfg.tr.tiles_in * cfg.tr.tiles_out) /
+                 (double(uint64_t(1) << cfg.tr.log2n) * (cfg.tr.log2n + 2));
+    }
+    for (int f = 0; f < 2; ++f) {
+        o.path = f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64;
+        for (int k = kTuneLogMin; k <= kTuneLogMax; ++k) {
+            const uint64_t N = uint64_t(1) << k, M = N / 4, L = N - M;
+            uint64_t tiles = std::max<uint64_t>(4, std::min<uint64_t>(1024, (uint64_t(1) << 24) >> k));
+            while (tiles > 1 && L * tiles > max_bits - 64) tiles /= 2;
+            o.log2_transform = static_cast<uint32_t>(k);
+            o.tile_out = M;
+            o.tile_in = L;
+            const double tt = tplan(L * tiles, M, o, &cfg);
+            t->ntt[f][k] = tt / double(cfg.tr.tiles_in * cfg.tr.tiles_out);
+        }
+        o.log2_transform = 0;
+        o.tile_in = o.tile_out = 0;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(key);
+    cudaFree(seed);
+    cudaFree(out);
+    cudaStreamDestroy(s);
+    t->valid = true;
+    return PA_OK;
+}
+
+bool load_cache(Tuner *t, const char *path, const char *dev_name) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char name[256] = {0};
+    bool ok = fgets(name, sizeof(name), f) != nullptr;
+    if (ok) {
+        name[strcspn(name, "\n")] = 0;
+        ok = strcmp(name, dev_name) == 0;
+    }
+    ok = ok && fscanf(f, "%lf %lf %lf %lf %lf", &t->direct, &t->block[0], &t->block[1],
+                      &t->block[2], &t->fft) == 5;
+    for (int fl = 0; ok && fl < 2; ++fl)
+        for (int k = 0; ok && k <= kTuneLogMax; ++k) ok = fscanf(f, "%lf", &t->ntt[fl][k]) == 1;
+    fclose(f);
+    t->valid = ok;
+    return ok;
+}
+
+void save_cache(const Tuner &t, const char *path, const char *dev_name) {
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    fprintf(f, "%s\n%.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0], t.block[1],
+            t.block[2], t.fft);
+    for (int fl = 0; fl < 2; ++fl) {
+        for (int k = 0; k <= kTuneLogMax; ++k) fprintf(f, "%.6e ", t.ntt[fl][k]);
+        fprintf(f, "\n");
+    }
+    fclose(f);
+}
+
+int get_tuner(Tuner *out) {
+    int dev = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return PA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    Tuner &t = g_tuner[dev];
+    if (!t.valid) {
+        cudaDeviceProp prop;
+        PA_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+        const char *cache = getenv("PA_TUNER_CACHE");
+        if (!(cache && load_cache(&t, cache, prop.name))) {
+            int rc = calibrate(&t);
+            if (rc != PA_OK) return rc;
+            if (cache) save_cache(t, cache, prop.name);
+        }
+    }
+    *out = t;
+    return PA_OK;
+}
+
+// Estimated seconds of one block on each path; fills opts with the best choice.
+double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *best) {
+    memset(best, 0, sizeof(*best));
+    best->device = -1;
+    double bt = INFINITY;
+    auto consider = [&](double tt, const pa_opts &o) {
+        if (tt < bt) {
+            bt = tt;
+            *best = o;
+        }
+    };
+    pa_opts o;
+    memset(&o, 0, sizeof(o));
+    o.device = -1;
+    o.path = PA_PATH_DIRECT;
+    consider(t.direct * double(n) * double(m) + 2 * t.launch, o);
+    o.path = PA_PATH_BLOCK_INT8;
+    for (int i = 0; i < 3; ++i) {
+        o.block_b = 128u << i;
+        consider(t.block[i] * double(m) * double(n + 8192) + 2 * t.launch, o);
+    }
+    o.block_b = 0;
+    // FFT path at its usual proven geometry (N = 2^12, L = 1536, M = 2560)
+    o.path = PA_PATH_FFT;
+    consider(t.fft * double(ceil_div(n, 1536)) * double(ceil_div(m, 2560)) * 4096.0 * 14.0 +
+                 t.launch,
+             o);
+    // transform paths: geometry search with measured per-tile costs
+    for (int f = 0; f < 2; ++f) {
+        if (f == 0 && n >= 2013265921ull) continue;
+        o.path = f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64;
+        for (int k = kTuneLogMin; k <= kTuneLogMax; ++k) {
+            const uint64_t N = uint64_t(1) << k;
+            const uint64_t mc = round_up(m, 64);
+            for (uint64_t div = 1; div <= 256; div *= 2) {
+                uint64_t M = div == 1 ? mc : round_up(N / div, 64);
+                if (M > mc) M = mc;
+                if (M == 0 || M + 32 > N) continue;
+                uint64_t L = ((N - M) / 32) * 32;
+                if (L > round_up(n, 32)) L = round_up(n, 32);
+                const double pairs = double(ceil_div(n, L)) * double(ceil_div(m, M));
+                const double launches = batched ? 0.0 : (k > 12 ? 3.0 : 1.0);
+                o.log2_transform = static_cast<uint32_t>(k);
+                o.tile_out = M;
+                o.tile_in = L;
+                consider(pairs * t.ntt[f][k] + (launches + 1) * t.launch, o);
+            }
+        }
+        o.log2_transform = 0;
+        o.tile_in = o.tile_out = 0;
+    }
+    return bt;
+}
+
+}  // namespace
+
+// Path choice for a single AUTO plan (calibrates on first use on this device).
+int tuned_opts(uint64_t n, uint64_t m, pa_opts *out) {
+    Tuner t;
+    int rc = get_tuner(&t);
+    if (rc != PA_OK) return rc;
+    best_path(n, m, t, false, out);
+    return PA_OK;
+}
+
+// ---------------------------------------------------------------- batch zeroing
+
+namespace {
+__global__ void batch_zero(const BlockPtrs *__restrict__ blks, const uint32_t *__restrict__ idx) {
+    const BlockPtrs b = blks[idx[blockIdx.x]];
+    const uint64_t words = 2 * ((b.m + 63) >> 6);
+    for (uint64_t w = threadIdx.x; w < words; w += blockDim.x) b.out32[w] = 0u;
+}
+}  // namespace
+
+}  // namespace pa
+
+using namespace pa;
+
+struct pa_batch_s {
+    int device = 0;
+    std::vector<uint64_t> n, m;
+    std::vector<PlanCfg> cfg;
+    std::vector<size_t> ws_off;       // per block (non-persistent paths)
+    std::vector<uint32_t> in_ntt[2];  // blocks run by the persistent launch, per field
+    NttBatchInfo ntt[2];
+    size_t off_blks = 0, off_idx[2] = {0, 0}, off_ntt[2] = {0, 0}, bytes = 0;
+    void *mem = nullptr;
+    std::vector<BlockPtrs> hblks;
+    bool blks_valid = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+    cudaStream_t last_stream = nullptr;
+    bool graph_ok = false;
+    Prof prof;
+    uint32_t per_path[8] = {0};
+    uint64_t work_items = 0;
+    double bound = 0;
+    // staging for pa_batch_run_host
+    void *stage = nullptr;
+    std::vector<size_t> st_seed, st_key, st_out;
+    size_t stage_bytes = 0;
+};
+
+namespace {
+
+DevHeader *batch_hdr(pa_batch_s *b) { return static_cast<DevHeader *>(b->mem); }
+
+int enqueue_all(pa_batch_s *b, cudaStream_t s) {
+    char *base = static_cast<char *>(b->mem);
+    const BlockPtrs *dblks = reinterpret_cast<const BlockPtrs *>(base + b->off_blks);
+    DevHeader *hdr = batch_hdr(b);
+    Prof *prof = b->prof.on ? &b->prof : nullptr;
+    for (int f = 0; f < 2; ++f) {
+        if (b->in_ntt[f].empty()) continue;
+        prof_begin(prof, K_MEMSET, s);
+        batch_zero<<<static_cast<unsigned>(b->in_ntt[f].size()), 256, 0, s>>>(
+            dblks, reinterpret_cast<const uint32_t *>(base + b->off_idx[f]));
+        prof_end(prof, s);
+        PA_CUDA_TRY(cudaGetLastError());
+        int rc = ntt_batch_launch(b->ntt[f], base + b->off_ntt[f], dblks, &hdr->status, prof, s);
+        if (rc != PA_OK) return rc;
+    }
+    for (size_t i = 0; i < b->cfg.size(); ++i) {
+        const PlanCfg &c = b->cfg[i];
+        if (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64) continue;
+        const BlockPtrs &p = b->hblks[i];
+        const uint64_t *seed = reinterpret_cast<const uint64_t *>(p.seed32);
+        const uint64_t *key = reinterpret_cast<const uint64_t *>(p.key32);
+        uint64_t *out = reinterpret_cast<uint64_t *>(p.out32);
+        void *ws = base + b->ws_off[i];
+        int rc = PA_OK;
+        if (c.path == PA_PATH_DIRECT) rc = direct_launch(c, ws, hdr, prof, seed, key, out, s);
+        else if (c.path == PA_PATH_FFT) rc = fft_launch(c, ws, hdr, prof, seed, key, out, s);
+        else rc = block_launch(c, ws, hdr, prof, seed, key, out, s);
+        if (rc != PA_OK) return rc;
+    }
+    return PA_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_batch_t *out) {
+    if (!out || !blocks || count == 0 || count > (size_t(1) << 24)) return PA_ERR_INVALID;
+    *out = nullptr;
+    pa_batch_s *b = new (std::nothrow) pa_batch_s();
+    if (!b) return PA_ERR_NOMEM;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e);
+    }
+    const bool forced = opts && opts->path != PA_PATH_AUTO;
+    Tuner t;
+    if (!forced) {
+        int rc = get_tuner(&t);
+        if (rc != PA_OK) {
+            delete b;
+            return rc;
+        }
+    }
+    std::vector<BatchBlock> nb[2];
+    size_t off = kHeaderBytes;
+    b->off_blks = off;
+    off = round_up(off + count * sizeof(BlockPtrs), 256);
+    b->cfg.resize(count);
+    b->ws_off.assign(count, 0);
+    for (size_t i = 0; i < count; ++i) {
+        const uint64_t n = blocks[i].n, m = blocks[i].m;
+        b->n.push_back(n);
+        b->m.push_back(m);
+        pa_opts o;
+        if (forced) {
+            o = *opts;
+        } else {
+            best_path(n, m, t, true, &o);
+        }
+        int rc = plan_resolve(n, m, &o, &b->cfg[i]);
+        if (rc != PA_OK) {
+            delete b;
+            return rc;
+        }
+        const PlanCfg &c = b->cfg[i];
+        b->per_path[c.path] += 1;
+        if (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64) {
+            const int f = c.path == PA_PATH_NTT31 ? 0 : 1;
+            BatchBlock bb;
+            bb.index = static_cast<uint32_t>(i);
+            bb.n = n;
+            bb.m = m;
+            bb.tr = c.tr;
+            nb[f].push_back(bb);
+            b->in_ntt[f].push_back(static_cast<uint32_t>(i));
+        } else {
+            b->ws_off[i] = off;
+            off = round_up(off + c.ws_bytes, 256);
+            b->work_items += c.path == PA_PATH_FFT ? c.tr.tiles_in * c.tr.tiles_out
+                                                   : (c.path == PA_PATH_DIRECT
+                                                          ? uint64_t(c.direct.grid_x) * c.direct.grid_y
+                                                          : uint64_t(c.blk.grid_x) * c.blk.grid_y);
+            if (c.path == PA_PATH_FFT) b->bound = std::max(b->bound, c.tr.bound);
+        }
+    }
+    for (int f = 0; f < 2; ++f) {
+        if (nb[f].empty()) continue;
+        int rc = ntt_batch_build(f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64, nb[f],
+                                 opts ? opts->max_slots : 0, &b->ntt[f]);
+        if (rc != PA_OK) {
+            delete b;
+            return rc;
+        }
+        b->work_items += b->ntt[f].nitems;
+        b->off_idx[f] = off;
+        off = round_up(off + b->in_ntt[f].size() * sizeof(uint32_t), 256);
+        b->off_ntt[f] = off;
+        off = round_up(off + b->ntt[f].bytes, 256);
+    }
+    b->bytes = off;
+    e = cudaMalloc(&b->mem, b->bytes);
+    if (e == cudaSuccess) e = cudaMemset(b->mem, 0, kHeaderBytes);
+    for (int f = 0; e == cudaSuccess && f < 2; ++f)
+        if (!b->in_ntt[f].empty())
+            e = cudaMemcpy(static_cast<char *>(b->mem) + b->off_idx[f], b->in_ntt[f].data(),
+                           b->in_ntt[f].size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->mem);
+        delete b;
+        return cuda_fail(e);
+    }
+    for (int f = 0; f < 2; ++f) {
+        if (b->in_ntt[f].empty()) continue;
+        int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f]);
+        if (rc != PA_OK) {
+            cudaFree(b->mem);
+            delete b;
+            return rc;
+        }
+    }
+    // root tables of the FFT path are created now, not inside a graph capture
+    for (size_t i = 0; i < count; ++i)
+        if (b->cfg[i].path == PA_PATH_FFT) {
+            int rc = fft_prepare(b->cfg[i].tr.fp64);
+            if (rc != PA_OK) {
+                cudaFree(b->mem);
+                delete b;
+                return rc;
+            }
+        }
+    b->hblks.resize(count);
+    *out = b;
+    return PA_OK;
+}
+
+int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *stream, pa_report *rep) {
+    if (!b || !blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+    bool changed_other = false, changed_any = !b->blks_valid;
+    for (size_t i = 0; i < count; ++i) {
+        const pa_block &x = blocks[i];
+        if (x.n != b->n[i] || x.m != b->m[i] || !x.seed_bits || !x.key_bits || !x.out_bits)
+            return PA_ERR_INVALID;
+        if (!aligned16(x.seed_bits) || !aligned16(x.key_bits) || !aligned16(x.out_bits))
+            return PA_ERR_ALIGN;
+        BlockPtrs p{reinterpret_cast<const uint32_t *>(x.key_bits),
+                    reinterpret_cast<const uint32_t *>(x.seed_bits),
+                    reinterpret_cast<uint32_t *>(x.out_bits), x.n, x.m};
+        BlockPtrs &h = b->hblks[i];
+        if (h.key32 != p.key32 || h.seed32 != p.seed32 || h.out32 != p.out32) {
+            changed_any = true;
+            const int path = b->cfg[i].path;
+            if (path != PA_PATH_NTT31 && path != PA_PATH_NTT64) changed_other = true;
+            h = p;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (changed_any) {
+        PA_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(b->mem) + b->off_blks, b->hblks.data(),
+                                    count * sizeof(BlockPtrs), cudaMemcpyHostToDevice, s));
+        b->blks_valid = true;
+    }
+    uint32_t replayed = 0;
+    if (b->prof.on) {
+        int rc = enqueue_all(b, s);
+        if (rc != PA_OK) return rc;
+    } else {
+        if (!b->graph_ok || changed_other) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            b->graph_ok = false;
+            // capture on a private stream (the caller's may be the legacy default
+            // stream, which cannot be captured); the graph is launched on the caller's
+            if (!b->cap_stream)
+                PA_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            PA_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_all(b, b->cap_stream);
+            cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+            if (rc != PA_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(e);
+            e = cudaGraphInstantiate(&b->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e);
+            b->graph_ok = true;
+        } else {
+            replayed = 1;
+        }
+        PA_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    }
+    b->last_stream = s;
+    if (rep) {
+        PA_CUDA_TRY(cudaStreamSynchronize(s));
+        DevHeader h;
+        PA_CUDA_TRY(cudaMemcpy(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost));
+        memset(rep, 0, sizeof(*rep));
+        memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
+        rep->bound = b->bound;
+        for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
+        rep->work_items = b->work_items;
+        rep->graph_replayed = replayed;
+        if (h.status != 0) {
+            int zero = 0;
+            cudaMemcpy(b->mem, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+            return h.status;
+        }
+    }
+    return PA_OK;
+}
+
+int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, void *stream,
+                      pa_report *rep) {
+    if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+    if (!b->stage) {
+        size_t off = 0;
+        for (size_t i = 0; i < count; ++i) {
+            b->st_seed.push_back(off);
+            off = round_up(off + ceil_div(b->n[i] + b->m[i] - 1, 64) * 8, 256);
+            b->st_key.push_back(off);
+            off = round_up(off + ceil_div(b->n[i], 64) * 8, 256);
+            b->st_out.push_back(off);
+            off = round_up(off + ceil_div(b->m[i], 64) * 8, 256);
+        }
+        cudaError_t e = cudaMalloc(&b->stage, off);
+        if (e != cudaSuccess) {
+            b->stage = nullptr;
+            return cuda_fail(e);
+        }
+        b->stage_bytes = off;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *st = static_cast<char *>(b->stage);
+    std::vector<pa_block> dev(count);
+    for (size_t i = 0; i < count; ++i) {
+        const pa_block &h = host_blocks[i];
+        if (h.n != b->n[i] || h.m != b->m[i] || !h.seed_bits || !h.key_bits || !h.out_bits)
+            return PA_ERR_INVALID;
+        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits, ceil_div(h.n + h.m - 1, 64) * 8,
+                                    cudaMemcpyHostToDevice, s));
+        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
+                                    cudaMemcpyHostToDevice, s));
+        dev[i] = {h.n, h.m, reinterpret_cast<const uint64_t *>(st + b->st_seed[i]),
+                  reinterpret_cast<const uint64_t *>(st + b->st_key[i]),
+                  reinterpret_cast<uint64_t *>(st + b->st_out[i])};
+    }
+    int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
+    if (rc != PA_OK) return rc;
+    for (size_t i = 0; i < count; ++i)
+        PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i],
+                                    ceil_div(b->m[i], 64) * 8, cudaMemcpyDeviceToHost, s));
+    PA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (rep) {
+        DevHeader h;
+        PA_CUDA_TRY(cudaMemcpy(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost));
+        memset(rep, 0, sizeof(*rep));
+        memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
+        rep->bound = b->bound;
+        for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
+        rep->work_items = b->work_items;
+        if (h.status != 0) return h.status;
+    }
+    return PA_OK;
+}
+
+void pa_batch_destroy(pa_batch_t b) {
+    if (!b) return;
+    if (b->last_stream) cudaStreamSynchronize(b->last_stream);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->mem);
+    if (b->stage) cudaFree(b->stage);
+    prof_free(&b->prof);
+    delete b;
+}
+
+int pa_batch_profile(pa_batch_t b, int enable) {
+    if (!b) return PA_ERR_INVALID;
+    return prof_enable(&b->prof, enable);
+}
+
+int pa_batch_kernel_times(pa_batch_t b, pa_kernel_time *out, int max, int *count) {
+    if (!b || max < 0) return PA_ERR_INVALID;
+    return prof_collect(&b->prof, out, max, count);
+}
+
+int pa_batch_describe(pa_batch_t b, uint32_t *paths, size_t count) {
+    if (!b || !paths || count != b->cfg.size()) return PA_ERR_INVALID;
+    for (size_t i = 0; i < count; ++i) paths[i] = static_cast<uint32_t>(b->cfg[i].path);
+    return PA_OK;
+}
+
+// One-shot: the batch plan is cached for the last shape list (per thread).
+int pa_hash_batched(const pa_block *blocks, size_t count, void *stream, pa_report *rep) {
+    static thread_local pa_batch_s *cached = nullptr;
+    static thread_local std::vector<uint64_t> shape;
+    if (!blocks || count == 0) return PA_ERR_INVALID;
+    std::vector<uint64_t> sh;
+    sh.reserve(2 * count);
+    for (size_t i = 0; i < count; ++i) {
+        sh.push_back(blocks[i].n);
+        sh.push_back(blocks[i].m);
+    }
+    int dev = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    if (!cached || sh != shape || cached->device != dev) {
+        if (cached) pa_batch_destroy(cached);
+        cached = nullptr;
+        int rc = pa_batch_plan(blocks, count, nullptr, &cached);
+        if (rc != PA_OK) return rc;
+        shape = sh;
+    }
+    return pa_batch_run(cached, blocks, count, stream, rep);
+}
+
+}  // extern "C"

@@ -284,6 +284,11 @@ int fft_plan(uint64_t n, uint64_t m, const pa_opts *o, TransformCfg *c) {
 
 size_t fft_workspace(const TransformCfg &) { return 0; }
 
+int fft_prepare(int fp64) {
+    const void *t = nullptr;
+    return fft_tables(fp64, &t);
+}
+
 int fft_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                const uint64_t *key, uint64_t *out, cudaStream_t s) {
     (void)ws;

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/pa.h"
 
 namespace pa {
@@ -49,6 +51,10 @@ struct PlanCfg {
     size_t ws_bytes = 0;         // workspace excluding the status header
     uint32_t kernels = 0;
 };
+
+// Autotuner: the measured-cost choice of path and tile geometry for one block
+// (calibrates by timing each path on the current device on first use).
+int tuned_opts(uint64_t n, uint64_t m, pa_opts *out);
 
 // Host-only planning (no GPU calls).
 int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg);
@@ -113,6 +119,7 @@ int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const u
                const uint64_t *key, uint64_t *out, cudaStream_t s);
 
 int fft_plan(uint64_t n, uint64_t m, const pa_opts *o, TransformCfg *c);
+int fft_prepare(int fp64);  // creates the twiddle table (outside any graph capture)
 size_t fft_workspace(const TransformCfg &c);
 int fft_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                const uint64_t *key, uint64_t *out, cudaStream_t s);
@@ -121,6 +128,29 @@ int block_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c);
 size_t block_workspace(const BlockCfg &c);
 int block_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                  const uint64_t *key, uint64_t *out, cudaStream_t s);
+
+// ---- batches of transform blocks in one persistent launch ----
+struct BatchBlock {
+    uint32_t index;        // position in the batch (BlockPtrs table index)
+    uint64_t n, m;
+    TransformCfg tr;
+};
+struct NttBatchInfo {
+    int field = 0;         // 0: 31-bit prime, 1: 64-bit prime
+    uint64_t ntiles = 0, nitems = 0;
+    uint32_t slots = 1;    // spectra slots reused round-robin
+    size_t smem = 0;
+    size_t off_tiles = 0, off_items = 0, off_counters = 0, counter_bytes = 0, off_spec = 0;
+    size_t bytes = 0;      // workspace bytes
+    std::vector<unsigned char> host_tiles;
+    std::vector<uint64_t> host_items;
+};
+int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
+                    NttBatchInfo *info);
+int ntt_batch_upload(const NttBatchInfo &info, void *ws);
+// blks: device array of the batch's BlockPtrs (see tiles.cuh)
+int ntt_batch_launch(const NttBatchInfo &info, void *ws, const void *blks, int *status, Prof *prof,
+                     cudaStream_t s);
 
 // Records a CUDA error for pa_last_cuda_error and maps it to a status.
 int cuda_fail(cudaError_t e);

@@ -21,6 +21,7 @@
 //   ntt_inv_first : twiddles, inverse pass 1, scale by N^-1, take bit 0, XOR the
 //                   tile's output bytes into the packed output.
 //   ntt_small     : N <= 2^12: all of the above in one CTA per tile.
+#include <algorithm>
 #include <mutex>
 #include <stdio.h>
 #include <string.h>
@@ -36,6 +37,17 @@ namespace pa {
 constexpr int kLogMax = 22;           // largest transform: 2^22
 constexpr int kLogSmallMax = 12;      // one-CTA transforms up to 2^12
 constexpr int kThreads = 512;
+
+// A transform tile of a batch: geometry plus its transform shape and spectra slot.
+struct NttTile {
+    TilePair p;
+    uint64_t ws_off;  // element offset of the key spectrum (window spectrum follows)
+    uint64_t scale;   // final scale as the bits of F::Tw
+    uint32_t logN, logR1, logR2;
+    uint32_t g1;      // pass-1 column groups (per input)
+    uint32_t g2;      // pass-2 row groups
+    uint32_t pad[3];
+};
 
 // ---------------------------------------------------------------- host tables
 
@@ -153,25 +165,21 @@ __device__ __forceinline__ typename F::Tw tw_at(const typename F::Tw *__restrict
     return F::neg_tw(tab[E - half]);
 }
 
-// ---------------------------------------------------------------- kernels
+// ---------------------------------------------------------------- tile bodies
+// Each body is run by all threads of a CTA; the standalone kernels and the
+// persistent batched kernel call the same bodies.
 
-// One CTA per tile; the whole transform of size 2^logN <= 2^12 in shared memory.
+// Whole transform of size 2^logN <= 2^12 in shared memory for one tile.
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict__ pairs,
-                                                      const BlockPtrs *__restrict__ blks,
-                                                      BlockPtrs one, int logN,
-                                                      const typename F::Tw *__restrict__ tfwd,
-                                                      const typename F::Tw *__restrict__ tinv,
-                                                      typename F::Tw scale) {
+__device__ void body_small(unsigned char *smraw, const TilePair &pr, const BlockPtrs &bp, int logN,
+                           const typename F::Tw *__restrict__ tfwd,
+                           const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
     using T = typename F::T;
     using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
     const int N = 1 << logN;
     Tw *stf = reinterpret_cast<Tw *>(smraw);
     Tw *sti = stf + N;
     T *sm = reinterpret_cast<T *>(sti + N);  // column 0: key tile, column 1: window
-    const TilePair pr = pairs[blockIdx.x];
-    const BlockPtrs bp = pick(blks, one, pr.blk);
     load_stage_tables<F>(stf, tfwd, logN, kLogMax);
     load_stage_tables<F>(sti, tinv, logN, kLogMax);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -183,7 +191,6 @@ __global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict
     for (int t = threadIdx.x; t < N; t += blockDim.x) sm[N + t] = F::mont(sm[t], sm[N + t]);
     __syncthreads();
     dit_columns<F, false>(sm + N, logN, 0, 1, N, sti);
-    // outputs: conv index K0 + v, v < out_len; 32 rows per warp step, packed by ballot
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nw = (pr.out_len + 31) / 32;
     for (uint32_t w = warp; w < nw; w += blockDim.x / 32) {
@@ -193,105 +200,120 @@ __global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict
         const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
         if (lane == 0 && word) atomicXor(bp.out32 + (pr.out_bit0 >> 5) + w, word);
     }
+    __syncthreads();
 }
 
-// Pass 1 forward on C columns of stride S1 = 2^logS (rows R1 = 2^logR1) for the key
-// tile (blockIdx.y even) or the seed window (odd); writes spectra to ws.
+// C consecutive bits of the key tile (which = 0) or window (which = 1) starting at
+// tile position t (C <= 8), as a mask.
+__device__ __forceinline__ uint32_t tile_bits8(const TilePair &pr, const BlockPtrs &bp, int which,
+                                               uint64_t t, int C) {
+    uint32_t v = 0;
+    if (which == 0) {
+        if (t >= pr.key_len) return 0u;
+        const uint64_t pos = uint64_t(pr.key_bit0) + t;
+        const uint64_t kw = 2 * ((bp.n + 63) >> 6);
+        v = bits32_at(bp.key32, kw, static_cast<int64_t>(pos));
+        const uint64_t left = pr.key_len - t;  // valid bits from t
+        if (left < 32) v &= (1u << left) - 1u;
+    } else {
+        if (t >= pr.win_len) return 0u;
+        const int64_t pos = pr.win_bit0 + static_cast<int64_t>(t);
+        const uint64_t sl = bp.n + bp.m - 1;  // seed length
+        const uint64_t sw = 2 * ((sl + 63) >> 6);
+        v = bits32_at(bp.seed32, sw, pos);
+        // positions >= seed length or >= window length read as 0 (< 0 handled by bits32_at)
+        const int64_t lim1 = static_cast<int64_t>(sl) - pos;
+        const int64_t lim2 = static_cast<int64_t>(pr.win_len - t);
+        const int64_t lim = lim1 < lim2 ? lim1 : lim2;
+        if (lim <= 0) return 0u;
+        if (lim < 32) v &= (1u << lim) - 1u;
+    }
+    return v & ((1u << C) - 1u);
+}
+
+// Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1).
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_fwd_first(
-    const TilePair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
-    int logN, int logR1, int logC, typename F::T *__restrict__ ws,
-    const typename F::Tw *__restrict__ tfwd) {
+__device__ void body_fwd_first(unsigned char *smraw, const TilePair &pr, const BlockPtrs &bp,
+                               int which, uint64_t cg, int logN, int logR1, int logC,
+                               typename F::T *__restrict__ dst,
+                               const typename F::Tw *__restrict__ tfwd) {
     using T = typename F::T;
     using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
     const int R1 = 1 << logR1, C = 1 << logC, logS = logN - logR1;
     Tw *st = reinterpret_cast<Tw *>(smraw);
     T *sm = reinterpret_cast<T *>(st + R1);
-    const int which = blockIdx.y & 1;
-    const uint32_t pi = blockIdx.y >> 1;
-    const TilePair pr = pairs[pi];
-    const BlockPtrs bp = pick(blks, one, pr.blk);
-    const uint64_t c0 = uint64_t(blockIdx.x) << logC;
+    const uint64_t c0 = cg << logC;
     load_stage_tables<F>(st, tfwd, logR1, kLogMax);
-    for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
-        const int r = e >> logC, c = e & (C - 1);
-        const uint64_t t = (uint64_t(r) << logS) + c0 + c;
-        sm[e] = which ? win_bit(pr, bp, t) : key_bit(pr, bp, t);
+    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
+        const uint32_t bits = tile_bits8(pr, bp, which, (uint64_t(r) << logS) + c0, C);
+#pragma unroll 8
+        for (int c = 0; c < C; ++c) sm[(r << logC) + c] = (bits >> c) & 1u;
     }
     __syncthreads();
     dif_columns<F, true>(sm, logR1, logC, C, 1, st);
-    T *dst = ws + (uint64_t(pi) * 2 + which) * (uint64_t(1) << logN);
     for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
         const int r = e >> logC, c = e & (C - 1);
         const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
         const uint64_t tlo = c0 + c;
         const uint32_t E = static_cast<uint32_t>((tlo * f) << (kLogMax - logN));
-        dst[(uint64_t(r) << logS) + tlo] = F::mul_tw(sm[e], tw_at<F>(tfwd, E));
+        __stcg(dst + (uint64_t(r) << logS) + tlo, F::mul_tw(sm[e], tw_at<F>(tfwd, E)));
     }
+    __syncthreads();
 }
 
-// Pass 2 of both spectra (contiguous rows of R2 = 2^logR2), the pointwise product,
-// and the inverse pass 2, for C2 = 2^logC rows; result written over the window's rows.
+// Pass 2 of both spectra (rows of R2 = 2^logR2, C2 = 2^logC rows from row group rg),
+// the pointwise product and the inverse pass 2; X = key spectrum, W = window spectrum.
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2, int logC,
-                                                           typename F::T *__restrict__ ws,
-                                                           const typename F::Tw *__restrict__ tfwd,
-                                                           const typename F::Tw *__restrict__ tinv) {
+__device__ void body_fused_last(unsigned char *smraw, uint64_t rg, int logR2, int logC,
+                                typename F::T *__restrict__ X, typename F::T *__restrict__ W,
+                                const typename F::Tw *__restrict__ tfwd,
+                                const typename F::Tw *__restrict__ tinv) {
     using T = typename F::T;
     using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
     const int R2 = 1 << logR2;
     Tw *stf = reinterpret_cast<Tw *>(smraw);
     Tw *sti = stf + R2;
-    T *sm = reinterpret_cast<T *>(sti + R2);  // columns 0..C-1: key spectrum rows, C..2C-1: window
-    const uint32_t pi = blockIdx.y;
-    T *X = ws + (uint64_t(pi) * 2) * (uint64_t(1) << logN);
-    T *W = X + (uint64_t(1) << logN);
-    const uint64_t row0 = uint64_t(blockIdx.x) << logC;
+    T *sm = reinterpret_cast<T *>(sti + R2);
+    const uint64_t base = (rg << logC) << logR2;
     load_stage_tables<F>(stf, tfwd, logR2, kLogMax);
     load_stage_tables<F>(sti, tinv, logR2, kLogMax);
     const int cnt = R2 << logC;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        sm[e] = X[(row0 << logR2) + e];
-        sm[cnt + e] = W[(row0 << logR2) + e];
+        sm[e] = __ldcg(X + base + e);
+        sm[cnt + e] = __ldcg(W + base + e);
     }
     __syncthreads();
     dif_columns<F, false>(sm, logR2, logC + 1, 1, R2, stf);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[cnt + e] = F::mont(sm[e], sm[cnt + e]);
     __syncthreads();
     dit_columns<F, false>(sm + cnt, logR2, logC, 1, R2, sti);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) W[(row0 << logR2) + e] = sm[cnt + e];
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) __stcg(W + base + e, sm[cnt + e]);
+    __syncthreads();
 }
 
-// Inverse pass 1 on C columns of the product, scale, low bit, XOR output bytes.
+// Inverse pass 1 on column group cg of the product, scale, low bit, XOR output bits.
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_inv_first(
-    const TilePair *__restrict__ pairs, const BlockPtrs *__restrict__ blks, BlockPtrs one,
-    int logN, int logR1, int logC, const typename F::T *__restrict__ ws,
-    const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
+__device__ void body_inv_first(unsigned char *smraw, const TilePair &pr, const BlockPtrs &bp,
+                               uint64_t cg, int logN, int logR1, int logC,
+                               const typename F::T *__restrict__ src,
+                               const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
     using T = typename F::T;
     using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
     const int R1 = 1 << logR1, C = 1 << logC, logS = logN - logR1;
     Tw *st = reinterpret_cast<Tw *>(smraw);
     T *sm = reinterpret_cast<T *>(st + R1);
-    const uint32_t pi = blockIdx.y;
-    const TilePair pr = pairs[pi];
-    const BlockPtrs bp = pick(blks, one, pr.blk);
-    const uint64_t c0 = uint64_t(blockIdx.x) << logC;
-    const T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
+    const uint64_t c0 = cg << logC;
     load_stage_tables<F>(st, tinv, logR1, kLogMax);
     for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
         const int r = e >> logC, c = e & (C - 1);
         const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
         const uint64_t tlo = c0 + c;
         const uint32_t E = static_cast<uint32_t>((tlo * f) << (kLogMax - logN));
-        sm[e] = F::mul_tw(src[(uint64_t(r) << logS) + tlo], tw_at<F>(tinv, E));
+        sm[e] = F::mul_tw(__ldcg(src + (uint64_t(r) << logS) + tlo), tw_at<F>(tinv, E));
     }
     __syncthreads();
     dit_columns<F, true>(sm, logR1, logC, C, 1, st);
-    // row r holds conv indices k = r*S1 + c0 + c (c < C = 8): one output byte per row
+    // row r holds conv indices k = r*S1 + c0 + c (c < C): C output bits per row
     for (int r = threadIdx.x; r < R1; r += blockDim.x) {
         const uint64_t k0 = (uint64_t(r) << logS) + c0;
         if (k0 + C <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
@@ -302,8 +324,154 @@ __global__ void __launch_bounds__(kThreads) ntt_inv_first(
                 byte |= F::low_bit(F::mul_tw(sm[(r << logC) + c], scale)) << c;
         }
         if (byte) {
-            const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of 8
+            const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of C
             atomicXor(bp.out32 + (pos >> 5), byte << (pos & 31));
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- standalone kernels
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict__ pairs, BlockPtrs bp,
+                                                      int logN,
+                                                      const typename F::Tw *__restrict__ tfwd,
+                                                      const typename F::Tw *__restrict__ tinv,
+                                                      typename F::Tw scale) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const TilePair pr = pairs[blockIdx.x];
+    body_small<F>(smraw, pr, bp, logN, tfwd, tinv, scale);
+}
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_fwd_first(const TilePair *__restrict__ pairs,
+                                                          BlockPtrs bp, int logN, int logR1, int logC,
+                                                          typename F::T *__restrict__ ws,
+                                                          const typename F::Tw *__restrict__ tfwd) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int which = blockIdx.y & 1;
+    const uint32_t pi = blockIdx.y >> 1;
+    const TilePair pr = pairs[pi];
+    typename F::T *dst = ws + (uint64_t(pi) * 2 + which) * (uint64_t(1) << logN);
+    body_fwd_first<F>(smraw, pr, bp, which, blockIdx.x, logN, logR1, logC, dst, tfwd);
+}
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2, int logC,
+                                                           typename F::T *__restrict__ ws,
+                                                           const typename F::Tw *__restrict__ tfwd,
+                                                           const typename F::Tw *__restrict__ tinv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename F::T *X = ws + (uint64_t(blockIdx.y) * 2) * (uint64_t(1) << logN);
+    body_fused_last<F>(smraw, blockIdx.x, logR2, logC, X, X + (uint64_t(1) << logN), tfwd, tinv);
+}
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_inv_first(const TilePair *__restrict__ pairs,
+                                                          BlockPtrs bp, int logN, int logR1, int logC,
+                                                          const typename F::T *__restrict__ ws,
+                                                          const typename F::Tw *__restrict__ tinv,
+                                                          typename F::Tw scale) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const uint32_t pi = blockIdx.y;
+    const TilePair pr = pairs[pi];
+    const typename F::T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
+    body_inv_first<F>(smraw, pr, bp, blockIdx.x, logN, logR1, logC, src, tinv, scale);
+}
+
+// ---------------------------------------------------------------- persistent batched kernel
+//
+// One launch runs the transform tiles of every block of a batch. CTAs pull items from
+// a work list with an atomic counter; the list is ordered so that each item depends
+// only on items before it (pass 1 -> pass 2 -> pass 3 of the same tile), which are
+// already claimed by running CTAs, so every wait ends. Waits are bounded anyway: on
+// timeout the status word gets PA_ERR_TIMEOUT and the item is skipped.
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool wait_count(const uint32_t *c, uint32_t target, int *status, int *flag) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint32_t it = 0;
+        while (ld_acquire(c) < target) {
+            if (++it > kSpinLimit) {
+                set_status(status, PA_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+__device__ __forceinline__ void signal_count(uint32_t *c) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(c, 1u);
+    }
+}
+
+template <class F>
+__global__ void __launch_bounds__(kThreads) ntt_persistent(
+    const uint64_t *__restrict__ items, uint32_t nitems, const NttTile *__restrict__ tiles,
+    const BlockPtrs *__restrict__ blks, typename F::T *__restrict__ ws,
+    const typename F::Tw *__restrict__ tfwd, const typename F::Tw *__restrict__ tinv,
+    uint32_t *c1, uint32_t *c2, uint32_t *c3, uint32_t slots, uint32_t *next, int *status) {
+    using Tw = typename F::Tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint64_t cur;
+    __shared__ int flag;
+    const int logC1 = sizeof(typename F::T) == 4 ? 3 : 2;
+    const int logC2 = sizeof(typename F::T) == 4 ? 2 : 1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t i = atomicAdd(next, 1u);
+            cur = i < nitems ? items[i] : ~0ull;
+        }
+        __syncthreads();
+        const uint64_t it = cur;
+        __syncthreads();
+        if (it == ~0ull) break;
+        const uint32_t type = static_cast<uint32_t>(it >> 62);
+        const uint32_t ti = static_cast<uint32_t>((it >> 32) & 0x3FFFFFFFu);
+        const uint32_t sub = static_cast<uint32_t>(it);
+        const NttTile tl = tiles[ti];
+        const BlockPtrs bp = blks[tl.p.blk];
+        Tw scale;
+        memcpy(&scale, &tl.scale, sizeof(Tw));
+        const int logN = static_cast<int>(tl.logN);
+        typename F::T *X = ws + tl.ws_off;
+        typename F::T *W = X + (uint64_t(1) << logN);
+        if (type == 0) {
+            body_small<F>(smraw, tl.p, bp, logN, tfwd, tinv, scale);
+        } else if (type == 1) {
+            // the spectra slot is reused: wait until the tile `slots` earlier released it
+            bool ok = true;
+            if (ti >= slots) ok = wait_count(c3 + (ti - slots), tiles[ti - slots].g1, status, &flag);
+            const int which = sub >= tl.g1 ? 1 : 0;
+            if (ok)
+                body_fwd_first<F>(smraw, tl.p, bp, which, sub - which * tl.g1, logN,
+                                  static_cast<int>(tl.logR1), logC1, which ? W : X, tfwd);
+            signal_count(c1 + ti);
+        } else if (type == 2) {
+            if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
+                body_fused_last<F>(smraw, sub, static_cast<int>(tl.logR2), logC2, X, W, tfwd, tinv);
+            signal_count(c2 + ti);
+        } else {
+            if (wait_count(c2 + ti, tl.g2, status, &flag))
+                body_inv_first<F>(smraw, tl.p, bp, sub, logN, static_cast<int>(tl.logR1), logC1, W,
+                                  tinv, scale);
+            signal_count(c3 + ti);
         }
     }
 }
@@ -451,8 +619,8 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
         for (uint64_t p0 = 0; p0 < npairs; p0 += 65535) {
             const uint64_t cnt = npairs - p0 < 65535 ? npairs - p0 : 65535;
             prof_begin(prof, K_NTT_SMALL, s);
-            ntt_small<F><<<static_cast<unsigned>(cnt), kThreads, smem, s>>>(pairs + p0, nullptr, one,
-                                                                           logN, tf, ti, scale);
+            ntt_small<F><<<static_cast<unsigned>(cnt), kThreads, smem, s>>>(pairs + p0, one, logN, tf,
+                                                                           ti, scale);
             prof_end(prof, s);
         }
         PA_CUDA_TRY(cudaGetLastError());
@@ -476,7 +644,7 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
         const uint64_t cnt = npairs - p0 < c.concurrent ? npairs - p0 : c.concurrent;
         prof_begin(prof, K_NTT_FWD_FIRST, s);
         ntt_fwd_first<F><<<dim3(gx1, static_cast<unsigned>(2 * cnt)), kThreads, sm1, s>>>(
-            pairs + p0, nullptr, one, logN, logR1, logC1, spec, tf);
+            pairs + p0, one, logN, logR1, logC1, spec, tf);
         prof_end(prof, s);
         prof_begin(prof, K_NTT_FUSED_LAST, s);
         ntt_fused_last<F><<<dim3(gx2, static_cast<unsigned>(cnt)), kThreads, sm2, s>>>(
@@ -484,7 +652,7 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
         prof_end(prof, s);
         prof_begin(prof, K_NTT_INV_FIRST, s);
         ntt_inv_first<F><<<dim3(gx1, static_cast<unsigned>(cnt)), kThreads, sm1, s>>>(
-            pairs + p0, nullptr, one, logN, logR1, logC1, spec, ti, scale);
+            pairs + p0, one, logN, logR1, logC1, spec, ti, scale);
         prof_end(prof, s);
     }
     PA_CUDA_TRY(cudaGetLastError());
@@ -492,6 +660,164 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- batches
+
+namespace {
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+}  // namespace
+
+int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
+                    NttBatchInfo *info) {
+    *info = NttBatchInfo();
+    info->field = path == PA_PATH_NTT31 ? 0 : 1;
+    const size_t elem = info->field == 0 ? 4 : 8, twsz = 8;
+    std::vector<NttTile> big, small;
+    for (const BatchBlock &b : blocks) {
+        std::vector<TilePair> pairs;
+        make_pairs(b.n, b.m, b.tr, b.index, &pairs);
+        for (const TilePair &p : pairs) {
+            NttTile t{};
+            t.p = p;
+            t.logN = b.tr.log2n;
+            if (info->field == 0) {
+                const F31::Tw sc = FieldHost<F31>::scale(t.logN);
+                memcpy(&t.scale, &sc, sizeof(sc));
+            } else {
+                const F64::Tw sc = FieldHost<F64>::scale(t.logN);
+                memcpy(&t.scale, &sc, sizeof(sc));
+            }
+            if (t.logN <= static_cast<uint32_t>(kLogSmallMax)) {
+                small.push_back(t);
+            } else {
+                t.logR1 = (t.logN + 1) / 2;
+                t.logR2 = t.logN / 2;
+                const int logC1 = elem == 4 ? 3 : 2, logC2 = elem == 4 ? 2 : 1;
+                t.g1 = static_cast<uint32_t>((uint64_t(1) << (t.logN - t.logR1)) >> logC1);
+                t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> logC2);
+                big.push_back(t);
+            }
+        }
+    }
+    // largest transforms first; slots of the largest spectra size, reused round-robin
+    std::stable_sort(big.begin(), big.end(),
+                     [](const NttTile &a, const NttTile &b) { return a.logN > b.logN; });
+    size_t slot_elems = 0;
+    for (const NttTile &t : big) slot_elems = std::max(slot_elems, size_t(2) << t.logN);
+    const size_t cap = size_t(4) << 30;
+    size_t slots = big.size();
+    if (slot_elems && slots * slot_elems * elem > cap) slots = std::max<size_t>(4, cap / (slot_elems * elem));
+    // slot reuse waits on the tile `slots` earlier, whose pass 3 precedes this pass 1
+    // in the work list only when slots >= 3
+    if (max_slots) slots = std::min<size_t>(slots, std::max<uint32_t>(max_slots, 4));
+    if (slots > big.size()) slots = big.size();
+    for (size_t i = 0; i < big.size(); ++i) big[i].ws_off = (i % (slots ? slots : 1)) * slot_elems;
+    std::vector<NttTile> tiles = big;
+    tiles.insert(tiles.end(), small.begin(), small.end());
+    if (tiles.size() >= (size_t(1) << 30)) return PA_ERR_UNSUPPORTED;
+    std::vector<uint64_t> items;
+    auto push = [&items](uint64_t type, uint64_t ti, uint64_t sub) {
+        items.push_back((type << 62) | (ti << 32) | sub);
+    };
+    // software pipeline: pass 1 of tile t, pass 2 of tile t-1, pass 3 of tile t-2
+    const size_t nb = big.size();
+    for (size_t t = 0; t < nb + 2; ++t) {
+        if (t < nb)
+            for (uint32_t k = 0; k < 2 * big[t].g1; ++k) push(1, t, k);
+        if (t >= 1 && t - 1 < nb)
+            for (uint32_t k = 0; k < big[t - 1].g2; ++k) push(2, t - 1, k);
+        if (t >= 2 && t - 2 < nb)
+            for (uint32_t k = 0; k < big[t - 2].g1; ++k) push(3, t - 2, k);
+    }
+    for (size_t i = 0; i < small.size(); ++i) push(0, nb + i, 0);
+    if (items.size() >= (size_t(1) << 32)) return PA_ERR_UNSUPPORTED;
+    info->ntiles = tiles.size();
+    info->nitems = items.size();
+    info->slots = static_cast<uint32_t>(slots ? slots : 1);
+    // shared memory: the largest need among the bodies present
+    size_t smem = 0;
+    for (const NttTile &t : tiles) {
+        if (t.logN <= static_cast<uint32_t>(kLogSmallMax)) {
+            smem = std::max(smem, (size_t(2) << t.logN) * (twsz + elem));
+        } else {
+            const int logC1 = elem == 4 ? 3 : 2, logC2 = elem == 4 ? 2 : 1;
+            smem = std::max(smem, (size_t(1) << t.logR1) * twsz + (size_t(1) << (t.logR1 + logC1)) * elem);
+            smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
+                                      2 * (size_t(1) << (t.logR2 + logC2)) * elem);
+        }
+    }
+    info->smem = smem;
+    // workspace layout
+    size_t off = 0;
+    info->off_tiles = off;
+    off = align256(off + tiles.size() * sizeof(NttTile));
+    info->off_items = off;
+    off = align256(off + items.size() * sizeof(uint64_t));
+    info->off_counters = off;
+    info->counter_bytes = (3 * tiles.size() + 1) * sizeof(uint32_t);
+    off = align256(off + info->counter_bytes);
+    info->off_spec = off;
+    off = align256(off + size_t(info->slots) * slot_elems * elem);
+    info->bytes = off;
+    info->host_tiles.resize(tiles.size() * sizeof(NttTile));
+    memcpy(info->host_tiles.data(), tiles.data(), info->host_tiles.size());
+    info->host_items = items;
+    return PA_OK;
+}
+
+int ntt_batch_upload(const NttBatchInfo &info, void *ws) {
+    char *b = static_cast<char *>(ws);
+    if (!info.host_tiles.empty())
+        PA_CUDA_TRY(cudaMemcpy(b + info.off_tiles, info.host_tiles.data(), info.host_tiles.size(),
+                               cudaMemcpyHostToDevice));
+    if (!info.host_items.empty())
+        PA_CUDA_TRY(cudaMemcpy(b + info.off_items, info.host_items.data(),
+                               info.host_items.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    Tables t;
+    return info.field == 0 ? get_tables<F31>(0, &t) : get_tables<F64>(1, &t);
+}
+
+namespace {
+template <class F>
+int batch_launch_field(const NttBatchInfo &info, void *ws, const void *blks, int *status, Prof *prof,
+                       cudaStream_t s) {
+    using Tw = typename F::Tw;
+    Tables tab;
+    int rc = get_tables<F>(info.field, &tab);
+    if (rc != PA_OK) return rc;
+    char *b = static_cast<char *>(ws);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(b + info.off_counters);
+    const uint32_t nt = static_cast<uint32_t>(info.ntiles);
+    PA_CUDA_TRY(cudaMemsetAsync(cnt, 0, info.counter_bytes, s));
+    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_persistent<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(info.smem)));
+    int per_sm = 0;
+    PA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ntt_persistent<F>, kThreads,
+                                                              info.smem));
+    int dev = 0, sms = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    PA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint64_t grid = uint64_t(per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > info.nitems) grid = info.nitems;
+    prof_begin(prof, K_BATCH_PERSISTENT, s);
+    ntt_persistent<F><<<static_cast<unsigned>(grid), kThreads, info.smem, s>>>(
+        reinterpret_cast<const uint64_t *>(b + info.off_items), static_cast<uint32_t>(info.nitems),
+        reinterpret_cast<const NttTile *>(b + info.off_tiles), static_cast<const BlockPtrs *>(blks),
+        reinterpret_cast<typename F::T *>(b + info.off_spec), static_cast<const Tw *>(tab.fwd),
+        static_cast<const Tw *>(tab.inv), cnt, cnt + nt, cnt + 2 * nt, info.slots, cnt + 3 * nt,
+        status);
+    prof_end(prof, s);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+}  // namespace
+
+int ntt_batch_launch(const NttBatchInfo &info, void *ws, const void *blks, int *status, Prof *prof,
+                     cudaStream_t s) {
+    if (info.nitems == 0) return PA_OK;
+    if (info.field == 0) return batch_launch_field<F31>(info, ws, blks, status, prof, s);
+    return batch_launch_field<F64>(info, ws, blks, status, prof, s);
+}
 
 int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                const uint64_t *key, uint64_t *out, cudaStream_t s) {

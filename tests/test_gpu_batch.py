@@ -1,0 +1,122 @@
+"""Batched hashing: many blocks of uneven n and m in one persistent launch (graph-replayed).
+
+Each block's bits must equal the oracle's, and equal the same block hashed alone.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1805_02372_gb300 as pkg
+from paper_1805_02372_gb300 import binding, inputs
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+MIXED = [(100_003, 25_000), (1, 1), (64, 70_001), (4_097, 4_095), (1_000_000, 10_000),
+         (262_145, 131_071), (2_000_003, 900_001), (33_333, 33_333), (1_048_577, 3),
+         (150_000, 1_500), (700_001, 350_000), (5, 900)]
+
+
+def _blocks(shapes, salt=0):
+    bl = [inputs.single_block(n, m, 1000 + 2 * i + salt, 1001 + 2 * i + salt)
+          for i, (n, m) in enumerate(shapes)]
+    keys = [b.key() for b in bl]
+    seeds = [b.seed() for b in bl]
+    return bl, keys, seeds
+
+
+def _run_batch(bl, keys, seeds, opts=None, runs=2):
+    import torch
+    kd = [dev(k) for k in keys]
+    sd = [dev(s) for s in seeds]
+    od = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in bl]
+    desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sd, kd, od)]
+    batch = pkg.pa_batch_plan(desc, opts)
+    reps = [pkg.pa_batch_run(batch, desc, report=True) for _ in range(runs)]
+    paths = pkg.pa_batch_describe(batch, len(bl))
+    pkg.pa_batch_destroy(batch)
+    return [host(o) for o in od], reps, paths
+
+
+@pytest.mark.parametrize("path", ["auto", "ntt31", "ntt64", "direct", "fft", "block_int8"])
+def test_mixed_batch_matches_oracle(path):
+    bl, keys, seeds = _blocks(MIXED)
+    if path == "fft":  # keep the FP tile count modest
+        bl, keys, seeds = _blocks([s for s in MIXED if s[0] * s[1] < 5e10])
+    outs, reps, paths = _run_batch(bl, keys, seeds, binding.make_opts(path=path))
+    for b, k, s, y in zip(bl, keys, seeds, outs):
+        assert np.array_equal(y, oracle.hash_full(b.n, b.m, s, k)), (path, b.n, b.m)
+    assert reps[0]["graph_replayed"] == 0 and reps[1]["graph_replayed"] == 1
+    assert sum(reps[0]["blocks_per_path"].values()) == len(bl)
+    if path != "auto":
+        assert set(paths) == {path}
+
+
+def test_spectra_slot_reuse():
+    # Few slots force pass 1 of later tiles to wait for earlier tiles' pass 3.
+    shapes = [(1_000_000 + 7 * i, 300_000 + 11 * i) for i in range(10)]
+    bl, keys, seeds = _blocks(shapes, salt=50)
+    outs, _, _ = _run_batch(bl, keys, seeds, binding.make_opts(path="ntt31", max_slots=4), runs=3)
+    for b, k, s, y in zip(bl, keys, seeds, outs):
+        assert np.array_equal(y, oracle.hash_full(b.n, b.m, s, k))
+
+
+def test_alone_equals_in_the_mix():
+    import torch
+    bl, keys, seeds = _blocks(MIXED, salt=7)
+    outs, _, _ = _run_batch(bl, keys, seeds)
+    for b, k, s, y in zip(bl, keys, seeds, outs):
+        plan = pkg.Plan(b.n, b.m)
+        o = torch.zeros((b.m + 63) // 64, dtype=torch.int64, device="cuda")
+        plan.hash(dev(s), dev(k), o)
+        torch.cuda.synchronize()
+        plan.close()
+        assert np.array_equal(host(o), y)
+
+
+def test_one_shot_and_host_entry():
+    import torch
+    bl, keys, seeds = _blocks(MIXED[:6], salt=3)
+    kd = [dev(k) for k in keys]
+    sd = [dev(s) for s in seeds]
+    od = [torch.zeros((b.m + 63) // 64, dtype=torch.int64, device="cuda") for b in bl]
+    desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sd, kd, od)]
+    pkg.pa_hash_batched(desc)
+    rep = pkg.pa_hash_batched(desc, report=True)
+    assert rep["graph_replayed"] == 1
+    want = [oracle.hash_full(b.n, b.m, s, k) for b, k, s in zip(bl, keys, seeds)]
+    for o, w in zip(od, want):
+        assert np.array_equal(host(o), w)
+    batch = pkg.pa_batch_plan(desc)
+    hout = [np.zeros((b.m + 63) // 64, np.uint64) for b in bl]
+    hdesc = [(b.n, b.m, np.ascontiguousarray(s), np.ascontiguousarray(k), o)
+             for b, s, k, o in zip(bl, seeds, keys, hout)]
+    pkg.pa_batch_run_host(batch, hdesc)
+    pkg.pa_batch_destroy(batch)
+    for o, w in zip(hout, want):
+        assert np.array_equal(o, w)
+
+
+def test_batched_workload_256_blocks():
+    import torch
+    with open(os.path.join(HERE, "golden", "batched256.json")) as f:
+        gold = json.load(f)["blocks"]
+    bl = inputs.batched_blocks()
+    keys = [b.key() for b in bl]
+    seeds = [b.seed() for b in bl]
+    outs, reps, paths = _run_batch(bl, keys, seeds)
+    for i, (b, y, g) in enumerate(zip(bl, outs, gold)):
+        assert (b.n, b.m) == (g["n"], g["m"])
+        assert hashlib.sha256(y.astype("<u8").tobytes()).hexdigest() == g["sha256"], i
+    # and sampled rows straight from the oracle
+    rng = np.random.default_rng(1)
+    for i in rng.choice(len(bl), 8, replace=False):
+        b = bl[i]
+        rows = rng.integers(0, b.m, 64)
+        assert np.array_equal(oracle.hash_rows(b.n, b.m, seeds[i], keys[i], rows),
+                              oracle.unpack(outs[i], b.m)[rows])
