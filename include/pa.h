@@ -45,6 +45,7 @@ extern "C" {
 #define PA_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                  */
 #define PA_ERR_UNSUPPORTED (-6) /* the requested path cannot run these sizes           */
 #define PA_ERR_PRECISION (-7)   /* FFT tile whose proven rounding bound is not < 1/2   */
+#define PA_ERR_TOO_LARGE (-8)   /* sizes exceed pa_hash_direct_static's fixed scratch  */
 
 /* Interchangeable kernels. Every path returns the same bits. */
 typedef enum {
@@ -133,6 +134,24 @@ int pa_fft_rounding_bound(uint32_t log2_transform, uint64_t tile_in, uint64_t ti
 /* Device-side status of the plan's last call: PA_OK, or PA_ERR_TIMEOUT if a
  * bounded wait in a kernel gave up (synchronises the plan's stream). */
 int pa_plan_status(pa_plan_t plan);
+
+/* y = T x mod 2 on the direct path WITHOUT allocating anything. The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc (a pipeline that reserved
+ * its device memory once and forbids allocation later, a process whose device memory
+ * belongs to another framework's allocator, code that must not meet out-of-memory
+ * mid-key). The kernel's scratch (reversed key, status word) is a static device array of
+ * about 4 MiB that every GPU loading this library holds until the process exits.
+ *   n <= 2^25 (33,554,432) key bits, else PA_ERR_TOO_LARGE; m as for pa_hash.
+ *   seed_bits, key_bits, out_bits: device pointers, 16-byte aligned, same layout as
+ *   pa_hash; stream: cudaStream_t (NULL = legacy default stream); asynchronous.
+ * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. Every call
+ * shares the one array and leaves its contents behind (the status word is cleared at each
+ * call, the reversed key is rewritten in full): calls that overlap on the GPU race, so
+ * serialise them (one stream, or events). Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+int pa_hash_direct_static(uint64_t n, uint64_t m, const uint64_t *seed_bits,
+                          const uint64_t *key_bits, uint64_t *out_bits, void *stream);
 
 /* ---- Many independent blocks in one launch (Sec. 3: batches run in parallel) ---- */
 

@@ -23,6 +23,7 @@ PA_ERR_CUDA = -4
 PA_ERR_TIMEOUT = -5
 PA_ERR_UNSUPPORTED = -6
 PA_ERR_PRECISION = -7
+PA_ERR_TOO_LARGE = -8
 
 PA_PATH_AUTO = 0
 PA_PATH_DIRECT = 1
@@ -112,6 +113,7 @@ SIGNATURES = {
     "pa_batch_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pa_batch_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(pa_kernel_time), ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_int)]),
+    "pa_hash_direct_static": (ctypes.c_int, [_U64, _U64, _VP, _VP, _VP, _VP]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_last_cuda_error": (ctypes.c_int, []),
     "pa_version": (ctypes.c_int, []),
@@ -323,6 +325,12 @@ def pa_batch_profile(batch: int, enable: bool) -> None:
 
 def pa_batch_kernel_times(batch: int) -> dict:
     return _times(load().pa_batch_kernel_times, batch, "pa_batch_kernel_times")
+
+
+def pa_hash_direct_static(n: int, m: int, seed_bits, key_bits, out_bits, stream=None) -> None:
+    """Direct-path hash with no device allocation (fixed static scratch, n <= 2^25)."""
+    _check(load().pa_hash_direct_static(n, m, _ptr(seed_bits), _ptr(key_bits), _ptr(out_bits),
+                                        _stream(stream)), "pa_hash_direct_static")
 
 
 def pa_strerror(status: int) -> str:

@@ -292,6 +292,7 @@ const char *pa_strerror(int status) {
         case PA_ERR_TIMEOUT: return "a bounded device-side wait timed out";
         case PA_ERR_UNSUPPORTED: return "sizes not supported by the requested path";
         case PA_ERR_PRECISION: return "no proven rounding bound below 1/2 for this FFT tile";
+        case PA_ERR_TOO_LARGE: return "sizes exceed the fixed scratch of pa_hash_direct_static";
     }
     return "unknown status";
 }

@@ -10,6 +10,8 @@
 // words from different key chunks are merged with atomicXor (the XOR merge of
 // Eq. finalkey). Key chunks and seed windows are staged in shared memory by the
 // TMA engine (cp.async.bulk + mbarrier).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace pa {
@@ -165,3 +167,69 @@ int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, cons
 }
 
 }  // namespace pa
+
+// ---------------------------------------------------------------- no-allocation entry point
+//
+// Some callers cannot call cudaMalloc: a post-processing pipeline that reserved its device
+// memory once at start-up and forbids allocation afterwards (allocation can synchronise the
+// device and stall the real-time stream), a host process whose memory arena belongs to
+// another framework, or code that must not fail on out-of-memory halfway through a key.
+// For them, pa_hash_direct_static runs the direct kernel with its scratch (the reversed
+// key and the status word) in the fixed array below, which every GPU that loads this
+// library holds until the process exits. Inputs and outputs remain the caller's.
+namespace pa {
+namespace {
+
+constexpr uint64_t kStaticMaxKeyBits = uint64_t(1) << 25;  // n <= 33,554,432 key bits
+constexpr uint64_t kStaticHeaderWords = kHeaderBytes / 4;  // status word area
+// reversed key of up to kStaticMaxKeyBits bits, padded to the largest key chunk (4096 words)
+constexpr uint64_t kStaticScratchWords = kStaticHeaderWords + kStaticMaxKeyBits / 32 + 4096;
+
+static __device__ __align__(256) uint32_t g_static_scratch[kStaticScratchWords];
+
+std::mutex g_static_mu;
+uint32_t *g_static_ptr[64] = {nullptr};
+
+// Device address of the array on the current device (looked up once per device).
+int static_scratch(uint32_t **out) {
+    int dev = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return PA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        uint32_t *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return PA_OK;
+}
+
+}  // namespace
+}  // namespace pa
+
+extern "C" int pa_hash_direct_static(uint64_t n, uint64_t m, const uint64_t *seed_bits,
+                                     const uint64_t *key_bits, uint64_t *out_bits, void *stream) {
+    using namespace pa;
+    if (n == 0 || m == 0 || !seed_bits || !key_bits || !out_bits) return PA_ERR_INVALID;
+    if (((reinterpret_cast<uintptr_t>(seed_bits) | reinterpret_cast<uintptr_t>(key_bits) |
+          reinterpret_cast<uintptr_t>(out_bits)) & 15u) != 0)
+        return PA_ERR_ALIGN;
+    if (n > kStaticMaxKeyBits || m > (uint64_t(1) << 40)) return PA_ERR_TOO_LARGE;
+    PlanCfg cfg;
+    cfg.n = n;
+    cfg.m = m;
+    cfg.path = PA_PATH_DIRECT;
+    int rc = direct_plan(n, m, &cfg.direct);
+    if (rc != PA_OK) return rc;
+    if (kStaticHeaderWords + cfg.direct.key_words32_pad > kStaticScratchWords) return PA_ERR_TOO_LARGE;
+    uint32_t *scratch = nullptr;
+    rc = static_scratch(&scratch);
+    if (rc != PA_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the status word must start at zero; the reversed key is fully rewritten below
+    PA_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(DevHeader), s));
+    return direct_launch(cfg, scratch + kStaticHeaderWords, reinterpret_cast<DevHeader *>(scratch),
+                         nullptr, seed_bits, key_bits, out_bits, s);
+}

@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_strerror_and_version(lib):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert pkg.pa_strerror(code) and pkg.pa_strerror(code) != "unknown status"
     assert pkg.pa_strerror(-99) == "unknown status"
     assert pkg.pa_version() >= 100
