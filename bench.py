@@ -42,6 +42,10 @@ def workload(name: str):
             "workload": "batched: 256 independent blocks, n_i log-uniform in [1e5, 4e6], "
                         "r_i uniform in [0.01, 0.5], m_i = floor(r_i n_i), fresh seed per block",
             "blocks": 256}
+    if name.startswith("batched") and name != "batched256":
+        k = int(name[len("batched"):])
+        return inputs.batched_blocks()[:k], {
+            "workload": f"batched (first {k} of the 256 blocks)", "blocks": k}
     if name == "plain_single":
         b = inputs.PLAIN_SINGLE
         return [b], {"workload": f"plain single block n={b.n} m={b.m}", "blocks": 1}
@@ -118,31 +122,36 @@ class ClockSampler:
 # --------------------------------------------------------------------------- runners
 
 class Runner:
-    """Device-resident buffers + plans for a list of blocks; one step = all blocks."""
+    """Device-resident buffers + plans for a list of blocks; one step = all blocks.
 
-    def __init__(self, blocks, path: str, device):
+    Several blocks run as one batch (pa_batch_plan / pa_batch_run: one persistent
+    launch, graph-replayed); a single block runs through pa_plan / pa_hash."""
+
+    def __init__(self, blocks, path: str, device, keys_h=None, seeds_h=None, force_single=False):
         import torch
 
         import paper_1805_02372_gb300 as pkg
         self.pkg, self.torch = pkg, torch
         self.blocks = blocks
         self.path = path
-        self.keys_h = [b.key() for b in blocks]
-        self.seeds_h = [b.seed() for b in blocks]
+        self.keys_h = keys_h if keys_h is not None else [b.key() for b in blocks]
+        self.seeds_h = seeds_h if seeds_h is not None else [b.seed() for b in blocks]
         t = lambda a: torch.from_numpy(a.view(np.int64)).to(device)
         self.keys = [t(k) for k in self.keys_h]
         self.seeds = [t(s) for s in self.seeds_h]
         self.outs = [torch.zeros((b.m + 63) // 64, dtype=torch.int64, device=device)
                      for b in blocks]
-        self.batched = len(blocks) > 1
+        self.batched = len(blocks) > 1 and not force_single
         self.stream = torch.cuda.current_stream()
         if self.batched:
             self.desc = [(b.n, b.m, s, k, o) for b, s, k, o in
                          zip(blocks, self.seeds, self.keys, self.outs)]
             self.batch = pkg.pa_batch_plan(self.desc, pkg.make_opts(path=path))
             self.plans = None
+            self.plan_desc = pkg.pa_batch_describe(self.batch, len(blocks))
         else:
             self.plans = [pkg.Plan(b.n, b.m, path=path) for b in blocks]
+            self.plan_desc = [p.desc for p in self.plans]
         self.units = sum(b.n for b in blocks)
 
     def step(self):
@@ -170,11 +179,37 @@ class Runner:
                 t["total_ms"] += v["total_ms"]
         return tot
 
-    def describe(self):
+    def paths(self) -> dict:
+        out = {}
+        for d in self.plan_desc:
+            out[d["path_name"]] = out.get(d["path_name"], 0) + 1
+        return out
+
+    def e2e(self, steps: int):
+        """Same metric through the host-buffer entry points (pinned host memory), copies
+        inside the timed region; returns (Gbps, h2d bytes, d2h bytes) per step."""
+        torch = self.torch
+        pin = lambda a: torch.from_numpy(a.view(np.int64)).pin_memory()
+        kh = [pin(k) for k in self.keys_h]
+        sh = [pin(s) for s in self.seeds_h]
+        oh = [torch.zeros((b.m + 63) // 64, dtype=torch.int64).pin_memory() for b in self.blocks]
+        h2d = sum(8 * (k.numel() + s.numel()) for k, s in zip(kh, sh))
+        d2h = sum(8 * o.numel() for o in oh)
         if self.batched:
-            rep = self.pkg.pa_batch_run(self.batch, self.desc, self.stream, report=True)
-            return {"report": rep}
-        return {"plans": [p.desc for p in self.plans]}
+            desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh)]
+            run = lambda: self.pkg.pa_batch_run_host(self.batch, desc, self.stream)
+        else:
+            run = lambda: [p.hash_host(s, k, o, self.stream)
+                           for p, s, k, o in zip(self.plans, sh, kh, oh)]
+        run()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            run()
+        dt = (time.perf_counter() - t0) / steps
+        for o, w in zip(oh, self.outs):
+            if not np.array_equal(o.numpy(), w.cpu().numpy()):
+                raise SystemExit("host-buffer entry point disagrees with the device one")
+        return self.units / dt / 1e9, h2d, d2h
 
 
 def check_sampled(runner, rows_per_block=64, seed=7):
@@ -200,18 +235,74 @@ def _source_digest(paths):
     return h.hexdigest()[:16]
 
 
+CSRC = "paper_1805_02372_gb300/csrc/"
 KERNEL_SOURCES = {
-    "direct": ["paper_1805_02372_gb300/csrc/direct.cu", "paper_1805_02372_gb300/csrc/common.cuh"],
+    "direct": [CSRC + "direct.cu", CSRC + "common.cuh"],
+    "batch_persistent": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh",
+                         CSRC + "tiles.cuh", CSRC + "common.cuh"],
+    "ntt_fwd_first": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh"],
+    "ntt_fused_last": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh"],
+    "ntt_inv_first": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh"],
+    "ntt_small": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh"],
+    "fft_tile": [CSRC + "fft.cu", CSRC + "dft.cuh", CSRC + "tiles.cuh"],
+    "block_mma": [CSRC + "block.cu", CSRC + "common.cuh"],
 }
 
+CLOCK_HZ = 2070e6
+SMS = 152
 
-def algorithmic(kernel: str, blocks, launches_per_step: int):
-    """(bound, algorithmic units per launch, unit). Counts per DESIGN's roofline section."""
+
+def _ntt_ops(descs, kernel):
+    """8 integer ops per butterfly; a tile of size N costs 3 (N/2) log2 N + N/2 butterflies
+    (two forward transforms, one inverse, the pointwise product)."""
+    ops = 0.0
+    for d in descs:
+        if d["path_name"] not in ("ntt31", "ntt64"):
+            continue
+        k = d["log2_transform"]
+        N = 2.0 ** k
+        tiles = d["tiles_in"] * d["tiles_out"]
+        if kernel == "ntt_small" and k > 12:
+            continue
+        if kernel in ("ntt_fwd_first", "ntt_fused_last", "ntt_inv_first") and k <= 12:
+            continue
+        per_tile = 3 * (N / 2) * k + N / 2
+        if kernel == "ntt_fwd_first":
+            per_tile = 2 * (N / 2) * ((k + 1) // 2)
+        elif kernel == "ntt_fused_last":
+            per_tile = 3 * (N / 2) * (k // 2) + N / 2
+        elif kernel == "ntt_inv_first":
+            per_tile = (N / 2) * ((k + 1) // 2)
+        ops += 8.0 * tiles * per_tile
+    return ops
+
+
+def algorithmic(kernel: str, blocks, descs):
+    """(bound, algorithmic units per step, unit, peak, peak_source) for a kernel."""
+    int_alu = SMS * 64 * CLOCK_HZ / 1e12
+    int_all = SMS * 128 * CLOCK_HZ / 1e12
     if kernel == "direct":
         # 32 funnel shifts + 32 LOP3 per 32 rows x 32 key bits: m*n/16 integer ops.
-        ops = sum(2.0 * b.m * b.n / 32.0 for b in blocks) / launches_per_step
-        return "alu", ops, "Tops/s"
-    return None, None, None
+        ops = sum(2.0 * b.m * b.n / 32.0 for b, d in zip(blocks, descs)
+                  if d["path_name"] == "direct")
+        return "alu", ops, "Tops/s", int_alu, "derived: 152 SM x 64 INT32 lanes x 2070 MHz"
+    if kernel in ("batch_persistent", "ntt_small", "ntt_fwd_first", "ntt_fused_last",
+                  "ntt_inv_first"):
+        return ("alu", _ntt_ops(descs, kernel), "Tops/s", int_all,
+                "derived: 152 SM x (64 ALU + 64 FMA-pipe IMAD) lanes x 2070 MHz")
+    if kernel == "block_mma":
+        ops = sum(2.0 * b.m * (b.n + 8192) for b, d in zip(blocks, descs)
+                  if d["path_name"] == "block_int8")
+        return "tensor", ops, "Tops/s", 150.8, "measured: legacy mma.sync s8 peak on GB300"
+    if kernel == "fft_tile":
+        fl = 0.0
+        for b, d in zip(blocks, descs):
+            if d["path_name"] == "fft":
+                N = 2.0 ** d["log2_transform"]
+                fl += d["tiles_in"] * d["tiles_out"] * 3 * (N / 2) * d["log2_transform"] * 10
+        return ("alu", fl, "TFLOP/s", SMS * 128 * 2 * CLOCK_HZ / 1e12,
+                "derived: 152 SM x 128 FP32 lanes x 2 flops x 2070 MHz")
+    return None, None, None, None, None
 
 
 def peaks():
@@ -222,29 +313,30 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def roofline(kt: dict, blocks, steps: int, clocks):
-    if not kt:
+def compulsory_bytes(blocks):
+    return sum(8 * ((b.n + 63) // 64 + (b.n + b.m - 1 + 63) // 64 + (b.m + 63) // 64)
+               for b in blocks)
+
+
+def roofline(kt: dict, blocks, descs, steps: int):
+    work = {k: v for k, v in kt.items() if k != "memset"}
+    if not work:
         return None
-    dom = max(kt.items(), key=lambda kv: kv[1]["total_ms"])
-    name, v = dom
-    per_launch_ms = v["total_ms"] / max(v["launches"], 1)
-    launches_per_step = max(1, round(v["launches"] / steps))
-    bound, units, unit = algorithmic(name, blocks, launches_per_step)
-    pk, src = peaks()
-    out = {"kernel": name, "launch_ms": per_launch_ms, "launches": v["launches"]}
-    if bound == "alu":
-        # 152 SMs x 64 INT32 (LOP3/SHF) lanes x max SM clock (2070 MHz).
-        peak = 152 * 64 * 2070e6 / 1e12
-        ach = units / (per_launch_ms * 1e-3) / 1e12
-        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": unit,
-                    "frac": ach / peak, "peak_source": "derived: 152 SM x 64 INT32 lanes x 2070 MHz"})
-    elif bound == "hbm":
-        peak = pk["hbm_gbs"]
-        ach = units / (per_launch_ms * 1e-3) / 1e9
-        out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+    name, v = max(work.items(), key=lambda kv: kv[1]["total_ms"])
+    launches_per_step = max(1.0, v["launches"] / steps)
+    per_launch_ms = v["total_ms"] / v["launches"]
+    bound, units, unit, peak, src = algorithmic(name, blocks, descs)
+    out = {"kernel": name, "launch_ms": per_launch_ms, "launches": v["launches"],
+           "share": v["total_ms"] / sum(x["total_ms"] for x in kt.values())}
+    if bound is not None and units:
+        ach = units / launches_per_step / (per_launch_ms * 1e-3) / 1e12
+        out.update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                     "frac": ach / peak, "peak_source": src})
+    pk, psrc = peaks()
+    hbm = compulsory_bytes(blocks) / launches_per_step / (per_launch_ms * 1e-3) / 1e9
+    out["hbm_compulsory"] = {"achieved_gbs": hbm, "peak_gbs": pk["hbm_gbs"],
+                             "frac": hbm / pk["hbm_gbs"], "peak_source": psrc + " (MEASURED_PEAKS)"}
     out["traffic"] = traffic_for(name)
-    out["share"] = v["total_ms"] / sum(x["total_ms"] for x in kt.values())
     return out
 
 
@@ -336,15 +428,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed(runner, steps, flush, stream, scratch):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        if flush:
+            scratch.add_(1)
+        a.record(stream)
+        runner.step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="plain_vs_transform_m500000")
+    ap.add_argument("--workload", default="batched256")
     ap.add_argument("--path", default="auto")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-kernel comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -369,24 +477,16 @@ def main():
     in_bytes = sum(8 * (len(k) + len(s)) for k, s in zip(runner.keys_h, runner.seeds_h))
     flush = in_bytes < 2 * L2_BYTES
     scratch = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=device) if flush else None
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    runner.profile(True)
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        for a, b in evs:
-            if flush:
-                scratch.add_(1)
-            a.record(stream)
-            runner.step()
-            b.record(stream)
-        torch.cuda.synchronize()
+        ms = timed(runner, args.steps, flush, stream, scratch)   # graph replay, no tracing
         wall = time.perf_counter() - t0
-    runner.profile(False)
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        # per-kernel CUDA-event durations (eager launches with event pairs)
+        runner.profile(True)
+        ms_traced = timed(runner, args.steps, flush, stream, scratch)
+        runner.profile(False)
     if world > 1:
         t = torch.tensor([ms], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -395,23 +495,7 @@ def main():
     kt = runner.kernel_times()
     exact = check_sampled(runner)
     clocks = clk.summary()
-
-    # e2e through the public host-buffer entry point, copies inside the timed region
-    e2e = None
-    if not runner.batched:
-        p = runner.plans[0]
-        b = blocks[0]
-        kh = torch.from_numpy(runner.keys_h[0].view(np.int64)).pin_memory()
-        sh = torch.from_numpy(runner.seeds_h[0].view(np.int64)).pin_memory()
-        oh = torch.zeros((b.m + 63) // 64, dtype=torch.int64).pin_memory()
-        p.hash_host(sh, kh, oh, stream)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            p.hash_host(sh, kh, oh, stream)
-        dt = (time.perf_counter() - t0) / args.steps
-        e2e = {"value": b.n / dt / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(kh.numel() * 8 + sh.numel() * 8),
-               "d2h_bytes_per_step": int(oh.numel() * 8)}
+    e2e_gbps, h2d, d2h = runner.e2e(max(3, args.steps // 2))
 
     units = runner.units * world
     value = units / (ms * 1e-3) / 1e9
@@ -420,13 +504,27 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": dict(cfg, path=args.path, l2="flushed between steps" if flush else
-                       "inputs larger than L2", bit_exact_sampled=exact),
-        "roofline": roofline(kt, blocks, args.steps, clocks),
-        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks,
+        "config": dict(cfg, path=args.path, paths_chosen=runner.paths(),
+                       l2="flushed between steps" if flush else "inputs larger than L2",
+                       bit_exact_sampled=exact),
+        "roofline": roofline(kt, blocks, runner.plan_desc, args.steps),
+        "e2e": {"value": e2e_gbps * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps, "clocks": clocks,
         "kernel_times_ms": {k: round(v["total_ms"] / args.steps, 5) for k, v in kt.items()},
-        "wall_s": wall,
+        "ms_per_step_traced": ms_traced, "wall_s": wall,
     }
+    if not exact:
+        line["error"] = "sampled rows disagree with the oracle"
+    if len(blocks) > 1 and not args.no_plain and rank == 0:
+        # the plain single-block kernel (direct path), block by block, same blocks
+        plain = Runner(blocks, "direct", device, runner.keys_h, runner.seeds_h,
+                       force_single=True)
+        plain.step()
+        pms = timed(plain, 2, flush, stream, scratch)
+        line["plain_kernel"] = {"value": runner.units / (pms * 1e-3) / 1e9, "unit": UNIT,
+                                "path": "direct, one pa_hash per block", "ms_per_step": pms,
+                                "batched_over_plain": value / (runner.units / (pms * 1e-3) / 1e9)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, cores, desc = cpu_oracle_gbps(blocks)
         line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -190,8 +190,9 @@ int pa_batch_run(pa_batch_t batch, const pa_block *blocks, size_t count, void *s
 int pa_batch_run_host(pa_batch_t batch, const pa_block *host_blocks, size_t count, void *stream,
                       pa_report *rep);
 
-/* The path (pa_path) the batch plan chose for each block. */
-int pa_batch_describe(pa_batch_t batch, uint32_t *paths, size_t count);
+/* What the batch plan chose for each block (path, tiles, transform size); count must be
+ * the batch's block count. */
+int pa_batch_describe(pa_batch_t batch, pa_plan_desc *out, size_t count);
 
 void pa_batch_destroy(pa_batch_t batch);
 

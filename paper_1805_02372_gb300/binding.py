@@ -104,7 +104,7 @@ SIGNATURES = {
     "pa_batch_destroy": (None, [_VP]),
     "pa_batch_run_host": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
                                          ctypes.POINTER(pa_report)]),
-    "pa_batch_describe": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.c_size_t]),
+    "pa_batch_describe": (ctypes.c_int, [_VP, ctypes.POINTER(pa_plan_desc), ctypes.c_size_t]),
     "pa_hash_batched": (ctypes.c_int, [ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
                                        ctypes.POINTER(pa_report)]),
     "pa_plan_profile": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -285,9 +285,10 @@ def pa_batch_run_host(batch: int, blocks, stream=None, report: bool = False) -> 
 
 
 def pa_batch_describe(batch: int, count: int) -> list:
-    arr = (ctypes.c_uint32 * count)()
+    """Per-block plan descriptors (dicts, with "path_name") chosen by the batch plan."""
+    arr = (pa_plan_desc * count)()
     _check(load().pa_batch_describe(batch, arr, count), "pa_batch_describe")
-    return [PATH_NAMES.get(int(v), "?") for v in arr]
+    return [arr[i].as_dict() for i in range(count)]
 
 
 def pa_batch_destroy(batch: int) -> None:

@@ -624,9 +624,9 @@ int pa_batch_kernel_times(pa_batch_t b, pa_kernel_time *out, int max, int *count
     return prof_collect(&b->prof, out, max, count);
 }
 
-int pa_batch_describe(pa_batch_t b, uint32_t *paths, size_t count) {
-    if (!b || !paths || count != b->cfg.size()) return PA_ERR_INVALID;
-    for (size_t i = 0; i < count; ++i) paths[i] = static_cast<uint32_t>(b->cfg[i].path);
+int pa_batch_describe(pa_batch_t b, pa_plan_desc *out, size_t count) {
+    if (!b || !out || count != b->cfg.size()) return PA_ERR_INVALID;
+    for (size_t i = 0; i < count; ++i) fill_desc(b->cfg[i], &out[i]);
     return PA_OK;
 }
 

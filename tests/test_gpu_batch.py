@@ -38,7 +38,7 @@ def _run_batch(bl, keys, seeds, opts=None, runs=2):
     desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sd, kd, od)]
     batch = pkg.pa_batch_plan(desc, opts)
     reps = [pkg.pa_batch_run(batch, desc, report=True) for _ in range(runs)]
-    paths = pkg.pa_batch_describe(batch, len(bl))
+    paths = [d["path_name"] for d in pkg.pa_batch_describe(batch, len(bl))]
     pkg.pa_batch_destroy(batch)
     return [host(o) for o in od], reps, paths
 
