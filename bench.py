@@ -428,6 +428,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def serving_probe(rates, count):
+    """Continuous-batching server on the serving workload: Poisson arrivals at each rate,
+    n log-uniform in [1e5, 1e8], r uniform in [0.01, 0.5], device-resident requests."""
+    from paper_1805_02372_gb300 import serve
+    out = []
+    for i, rate in enumerate(rates):
+        reqs = serve.make_requests(count, rate, master=4 + 100 * i)
+        st = serve.replay(reqs, slots=3, max_blocks_per_wave=32)
+        st["rate_hz"] = rate
+        out.append(st)
+        del reqs
+    return {"workload": "serving: Poisson arrivals, n log-uniform in [1e5, 1e8], r uniform "
+                        "in [0.01, 0.5], device-resident keys and seeds, 3 stream slots",
+            "requests_per_rate": count, "rates": out}
+
+
 def timed(runner, steps, flush, stream, scratch):
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -453,6 +469,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-kernel comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving latency probe")
+    ap.add_argument("--serving-rates", default="100,1000",
+                    help="comma-separated request rates (req/s) for the serving probe")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -525,6 +544,11 @@ def main():
         line["plain_kernel"] = {"value": runner.units / (pms * 1e-3) / 1e9, "unit": UNIT,
                                 "path": "direct, one pa_hash per block", "ms_per_step": pms,
                                 "batched_over_plain": value / (runner.units / (pms * 1e-3) / 1e9)}
+    if rank == 0 and not args.no_serving:
+        rates = [float(r) for r in args.serving_rates.split(",") if r]
+        line["serving"] = serving_probe(rates, 60)
+        worst = max(r["p99_ms"] for r in line["serving"]["rates"])
+        line["p99_latency_ms"] = worst
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, cores, desc = cpu_oracle_gbps(blocks)
         line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",

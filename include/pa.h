@@ -199,6 +199,40 @@ void pa_batch_destroy(pa_batch_t batch);
 /* One-shot batched hash: plans (cached by shape list), runs, optionally reports. */
 int pa_hash_batched(const pa_block *blocks, size_t count, void *stream, pa_report *rep);
 
+/* ---- Serving: continuous batching of requests arriving by device memory ----
+ * A server owns `slots` CUDA streams and a device-memory budget. Submitted requests
+ * queue in FIFO order; each poll retires finished waves and, for every free slot, plans
+ * the requests waiting at that moment as one batch (one persistent launch for the
+ * transform blocks) and launches it on the slot's stream, so waves overlap on the GPU.
+ * A wave whose workspace does not fit the budget next to the waves in flight waits.
+ * Request buffers are the caller's (device, 16-byte aligned) and must stay valid until
+ * the request completes. Batches of a server allocate and free in stream order. */
+
+typedef struct {
+    uint32_t slots;               /* concurrent waves (streams), default 2                 */
+    uint32_t max_blocks_per_wave; /* default 64                                            */
+    uint64_t memory_budget_bytes; /* 0 = unlimited                                         */
+    uint32_t reserved[4];
+} pa_server_opts;
+
+typedef struct {
+    uint64_t tag;                 /* the tag given at submit                               */
+    int32_t status;               /* PA_OK or the wave's error                             */
+    uint32_t reserved;
+} pa_completion;
+
+typedef struct pa_server_s *pa_server_t;
+
+/* Creates the streams and calibrates the autotuner (synchronous, once per device). */
+int pa_server_create(const pa_server_opts *opts, pa_server_t *out);
+/* Queues one request; thread-safe; does not launch (poll does). */
+int pa_server_submit(pa_server_t server, const pa_block *request, uint64_t tag);
+/* Retires finished waves into done[0..max) (count = entries written), then admits. */
+int pa_server_poll(pa_server_t server, pa_completion *done, size_t max, size_t *count);
+int pa_server_pending(pa_server_t server, uint64_t *queued, uint64_t *in_flight);
+/* Waits for the waves in flight, then releases everything. */
+void pa_server_destroy(pa_server_t server);
+
 /* ---- Per-kernel timing: CUDA events recorded around every launch on the
  * launching stream while enabled (tracing for roofline measurements). ---- */
 

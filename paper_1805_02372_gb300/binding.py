@@ -75,6 +75,16 @@ class pa_report(ctypes.Structure):
                 "work_items": int(self.work_items), "graph_replayed": int(self.graph_replayed)}
 
 
+class pa_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_blocks_per_wave", ctypes.c_uint32),
+                ("memory_budget_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class pa_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
+
+
 class pa_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
@@ -114,6 +124,13 @@ SIGNATURES = {
     "pa_batch_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(pa_kernel_time), ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_int)]),
     "pa_hash_direct_static": (ctypes.c_int, [_U64, _U64, _VP, _VP, _VP, _VP]),
+    "pa_server_create": (ctypes.c_int, [ctypes.POINTER(pa_server_opts), ctypes.POINTER(_VP)]),
+    "pa_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_uint64]),
+    "pa_server_poll": (ctypes.c_int, [_VP, ctypes.POINTER(pa_completion), ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "pa_server_pending": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "pa_server_destroy": (None, [_VP]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_last_cuda_error": (ctypes.c_int, []),
     "pa_version": (ctypes.c_int, []),
@@ -332,6 +349,41 @@ def pa_hash_direct_static(n: int, m: int, seed_bits, key_bits, out_bits, stream=
     """Direct-path hash with no device allocation (fixed static scratch, n <= 2^25)."""
     _check(load().pa_hash_direct_static(n, m, _ptr(seed_bits), _ptr(key_bits), _ptr(out_bits),
                                         _stream(stream)), "pa_hash_direct_static")
+
+
+def pa_server_create(slots: int = 2, max_blocks_per_wave: int = 64,
+                     memory_budget_bytes: int = 0) -> int:
+    o = pa_server_opts()
+    o.slots, o.max_blocks_per_wave, o.memory_budget_bytes = slots, max_blocks_per_wave, \
+        memory_budget_bytes
+    h = _VP()
+    _check(load().pa_server_create(ctypes.byref(o), ctypes.byref(h)), "pa_server_create")
+    return h.value
+
+
+def pa_server_submit(server: int, n: int, m: int, seed_bits, key_bits, out_bits, tag: int) -> None:
+    b = pa_block()
+    b.n, b.m = n, m
+    b.seed_bits, b.key_bits, b.out_bits = _ptr(seed_bits), _ptr(key_bits), _ptr(out_bits)
+    _check(load().pa_server_submit(server, ctypes.byref(b), tag), "pa_server_submit")
+
+
+def pa_server_poll(server: int, max_done: int = 4096) -> list:
+    """[(tag, status)] of requests finished since the last poll; also admits new waves."""
+    arr = (pa_completion * max_done)()
+    cnt = ctypes.c_size_t()
+    _check(load().pa_server_poll(server, arr, max_done, ctypes.byref(cnt)), "pa_server_poll")
+    return [(int(arr[i].tag), int(arr[i].status)) for i in range(cnt.value)]
+
+
+def pa_server_pending(server: int) -> tuple[int, int]:
+    q, f = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().pa_server_pending(server, ctypes.byref(q), ctypes.byref(f)), "pa_server_pending")
+    return q.value, f.value
+
+
+def pa_server_destroy(server: int) -> None:
+    load().pa_server_destroy(server)
 
 
 def pa_strerror(status: int) -> str:

@@ -310,6 +310,8 @@ struct pa_batch_s {
     uint32_t per_path[8] = {0};
     uint64_t work_items = 0;
     double bound = 0;
+    bool eager = false;               // launch without graph capture (serving waves)
+    cudaStream_t alloc_stream = nullptr;  // stream-ordered allocation (serving waves)
     // staging for pa_batch_run_host
     void *stage = nullptr;
     std::vector<size_t> st_seed, st_key, st_out;
@@ -356,13 +358,26 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 }  // namespace
 
-extern "C" {
+namespace pa {
 
-int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_batch_t *out) {
+void batch_free(pa_batch_s *b) {
+    if (!b) return;
+    if (b->alloc_stream) {
+        if (b->mem) cudaFreeAsync(b->mem, b->alloc_stream);
+    } else {
+        cudaFree(b->mem);
+    }
+    b->mem = nullptr;
+}
+
+int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
+                    cudaStream_t alloc_stream, bool eager, pa_batch_s **out) {
     if (!out || !blocks || count == 0 || count > (size_t(1) << 24)) return PA_ERR_INVALID;
     *out = nullptr;
     pa_batch_s *b = new (std::nothrow) pa_batch_s();
     if (!b) return PA_ERR_NOMEM;
+    b->eager = eager;
+    b->alloc_stream = alloc_stream;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e != cudaSuccess) {
         delete b;
@@ -434,32 +449,35 @@ int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_
         off = round_up(off + b->ntt[f].bytes, 256);
     }
     b->bytes = off;
-    e = cudaMalloc(&b->mem, b->bytes);
-    if (e == cudaSuccess) e = cudaMemset(b->mem, 0, kHeaderBytes);
+    cudaStream_t as = alloc_stream;
+    e = as ? cudaMallocAsync(&b->mem, b->bytes, as) : cudaMalloc(&b->mem, b->bytes);
+    if (e == cudaSuccess)
+        e = as ? cudaMemsetAsync(b->mem, 0, kHeaderBytes, as) : cudaMemset(b->mem, 0, kHeaderBytes);
     for (int f = 0; e == cudaSuccess && f < 2; ++f)
         if (!b->in_ntt[f].empty())
-            e = cudaMemcpy(static_cast<char *>(b->mem) + b->off_idx[f], b->in_ntt[f].data(),
-                           b->in_ntt[f].size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpyAsync(static_cast<char *>(b->mem) + b->off_idx[f], b->in_ntt[f].data(),
+                                b->in_ntt[f].size() * sizeof(uint32_t), cudaMemcpyHostToDevice, as);
     if (e != cudaSuccess) {
-        cudaFree(b->mem);
+        batch_free(b);
         delete b;
         return cuda_fail(e);
     }
     for (int f = 0; f < 2; ++f) {
         if (b->in_ntt[f].empty()) continue;
-        int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f]);
+        int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f], as);
         if (rc != PA_OK) {
-            cudaFree(b->mem);
+            batch_free(b);
             delete b;
             return rc;
         }
     }
+    if (!as) PA_CUDA_TRY(cudaStreamSynchronize(nullptr));
     // root tables of the FFT path are created now, not inside a graph capture
     for (size_t i = 0; i < count; ++i)
         if (b->cfg[i].path == PA_PATH_FFT) {
             int rc = fft_prepare(b->cfg[i].tr.fp64);
             if (rc != PA_OK) {
-                cudaFree(b->mem);
+                batch_free(b);
                 delete b;
                 return rc;
             }
@@ -467,6 +485,32 @@ int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_
     b->hblks.resize(count);
     *out = b;
     return PA_OK;
+}
+
+// Release a batch. Server-owned batches free their memory in stream order and do not
+// synchronise the device; others synchronise their last stream first.
+void batch_destroy_impl(pa_batch_s *b) {
+    if (!b) return;
+    if (!b->alloc_stream) {
+        if (b->last_stream) cudaStreamSynchronize(b->last_stream);
+        if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    batch_free(b);
+    if (b->stage) cudaFree(b->stage);
+    prof_free(&b->prof);
+    delete b;
+}
+
+size_t batch_bytes(const pa_batch_s *b) { return b ? b->bytes : 0; }
+
+}  // namespace pa
+
+extern "C" {
+
+int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_batch_t *out) {
+    return batch_plan_impl(blocks, count, opts, nullptr, false, out);
 }
 
 int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *stream, pa_report *rep) {
@@ -496,7 +540,7 @@ int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *strea
         b->blks_valid = true;
     }
     uint32_t replayed = 0;
-    if (b->prof.on) {
+    if (b->prof.on || b->eager) {
         int rc = enqueue_all(b, s);
         if (rc != PA_OK) return rc;
     } else {
@@ -602,17 +646,7 @@ int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, v
     return PA_OK;
 }
 
-void pa_batch_destroy(pa_batch_t b) {
-    if (!b) return;
-    if (b->last_stream) cudaStreamSynchronize(b->last_stream);
-    cudaDeviceSynchronize();
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    cudaFree(b->mem);
-    if (b->stage) cudaFree(b->stage);
-    prof_free(&b->prof);
-    delete b;
-}
+void pa_batch_destroy(pa_batch_t b) { batch_destroy_impl(b); }
 
 int pa_batch_profile(pa_batch_t b, int enable) {
     if (!b) return PA_ERR_INVALID;

@@ -9,6 +9,8 @@
 
 #include "../../include/pa.h"
 
+struct pa_batch_s;
+
 namespace pa {
 
 constexpr int kNumSMsGB300 = 152;
@@ -147,10 +149,18 @@ struct NttBatchInfo {
 };
 int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
                     NttBatchInfo *info);
-int ntt_batch_upload(const NttBatchInfo &info, void *ws);
+// host tables are copied on stream s (kept alive by info until the copy ran)
+int ntt_batch_upload(const NttBatchInfo &info, void *ws, cudaStream_t s);
 // blks: device array of the batch's BlockPtrs (see tiles.cuh)
 int ntt_batch_launch(const NttBatchInfo &info, void *ws, const void *blks, int *status, Prof *prof,
                      cudaStream_t s);
+
+// Batch plans for the serving engine: alloc_stream != nullptr allocates and frees in
+// stream order on it (no device-wide synchronisation); eager = no graph capture.
+int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
+                    cudaStream_t alloc_stream, bool eager, pa_batch_s **out);
+void batch_destroy_impl(pa_batch_s *b);
+size_t batch_bytes(const pa_batch_s *b);
 
 // Records a CUDA error for pa_last_cuda_error and maps it to a status.
 int cuda_fail(cudaError_t e);

@@ -765,14 +765,15 @@ int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t ma
     return PA_OK;
 }
 
-int ntt_batch_upload(const NttBatchInfo &info, void *ws) {
+int ntt_batch_upload(const NttBatchInfo &info, void *ws, cudaStream_t s) {
     char *b = static_cast<char *>(ws);
     if (!info.host_tiles.empty())
-        PA_CUDA_TRY(cudaMemcpy(b + info.off_tiles, info.host_tiles.data(), info.host_tiles.size(),
-                               cudaMemcpyHostToDevice));
+        PA_CUDA_TRY(cudaMemcpyAsync(b + info.off_tiles, info.host_tiles.data(),
+                                    info.host_tiles.size(), cudaMemcpyHostToDevice, s));
     if (!info.host_items.empty())
-        PA_CUDA_TRY(cudaMemcpy(b + info.off_items, info.host_items.data(),
-                               info.host_items.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+        PA_CUDA_TRY(cudaMemcpyAsync(b + info.off_items, info.host_items.data(),
+                                    info.host_items.size() * sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, s));
     Tables t;
     return info.field == 0 ? get_tables<F31>(0, &t) : get_tables<F64>(1, &t);
 }
