@@ -1,13 +1,42 @@
 // Shared-memory R-point transforms over a ring policy F (a prime field or complex
 // floating point): F::T element, F::Tw twiddle, F::add, F::sub, F::mul_tw.
+//
 // Forward = decimation in frequency (natural order in, bit-reversed out); inverse =
-// decimation in time (bit-reversed in, natural out, unnormalised), each round doing
-// two radix-2 stages on a group of four elements held in registers.
+// decimation in time (bit-reversed in, natural out, unnormalised). Every radix-2
+// butterfly is the textbook one: (a, b) -> (a + b, (a - b) w) forward, and
+// (a, b) -> (a + b w^-1, a - b w^-1) inverse, with w = w_{2h}^(i mod h) for the stage of
+// half-size h. A round holds a group of 2^S elements (i0 + k q, k < 2^S) in registers
+// and performs S consecutive stages on it, so shared memory is read and written once
+// per S stages. Rounds are ordered so the group stride q is >= 256, 16 or 1.
+//
+// Twiddles come from stage tables st[h - 1 + j] = w_{2h}^(+-j), j < h (R - 1 entries).
+//
+// Two bank-conflict-free layouts of a tile with R rows and C columns:
+//   RowMajor: element (r, c) at slot(r) * C + c, where slot rotates the rows inside each
+//             aligned group of four by (r >> 4) (C * sizeof(T) = 32 bytes per row);
+//   ColMajor: element (r, c) at c * (R + R/16) + r + (r >> 4) (one word of skew per 16).
 #pragma once
 
 namespace pa {
 
-// Stage tables of an R-point transform into shared memory: st[h-1+j] = w_{2h}^(+-j).
+struct RowMajor {
+    int logC;
+    __device__ __forceinline__ int at(int r, int c) const {
+        const int slot = (r & ~3) | ((r + (r >> 4)) & 3);
+        return (slot << logC) + c;
+    }
+    static __host__ __device__ __forceinline__ int words(int R, int C) { return R * C; }
+};
+
+struct ColMajor {
+    int cs;  // column stride R + R/16
+    __device__ __forceinline__ int at(int r, int c) const { return c * cs + r + (r >> 4); }
+    static __host__ __device__ __forceinline__ int stride(int R) { return R + (R >> 4); }
+    static __host__ __device__ __forceinline__ int words(int R, int C) { return C * stride(R); }
+};
+
+// Stage tables of an R-point transform into shared memory: st[h-1+j] = w_{2h}^(+-j),
+// read from a table of the 2^logmax-th roots (first half).
 template <class F>
 __device__ void load_stage_tables(typename F::Tw *st, const typename F::Tw *__restrict__ tab,
                                   int logR, int logmax) {
@@ -19,15 +48,54 @@ __device__ void load_stage_tables(typename F::Tw *st, const typename F::Tw *__re
     }
 }
 
-// Element (r, c) of a shared tile at base[r*rs + c*cs]. CF: consecutive threads take
-// consecutive columns (when cs == 1), else consecutive rows (when rs == 1).
-template <class F, bool CF>
-__device__ __forceinline__ void dif_round4(typename F::T *sm, int logR, int logC, int rs, int cs,
-                                           int lq, const typename F::Tw *tw) {
+// S decimation-in-frequency stages on x[0 .. 2^S) (element k at row i0 + k q).
+template <class F, int S>
+__device__ __forceinline__ void dif_group(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+                                          int j, int q) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int half = 1 << (S - 1 - s);   // pair distance in k
+        const int h = q * half;              // stage half-size in rows
+#pragma unroll
+        for (int k = 0; k < (1 << S); ++k) {
+            if (k & half) continue;
+            const typename F::Tw w = tw[h - 1 + j + (k & (half - 1)) * q];
+            const typename F::T a = x[k], b = x[k + half];
+            x[k] = F::add(a, b);
+            x[k + half] = F::mul_tw(F::sub(a, b), w);
+        }
+    }
+}
+
+// The inverse of dif_group (times 2^S) with inverse stage tables.
+template <class F, int S>
+__device__ __forceinline__ void dit_group(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+                                          int j, int q) {
+#pragma unroll
+    for (int s = S - 1; s >= 0; --s) {
+        const int half = 1 << (S - 1 - s);
+        const int h = q * half;
+#pragma unroll
+        for (int k = 0; k < (1 << S); ++k) {
+            if (k & half) continue;
+            const typename F::Tw w = tw[h - 1 + j + (k & (half - 1)) * q];
+            const typename F::T a = x[k];
+            const typename F::T t = F::mul_tw(x[k + half], w);
+            x[k] = F::add(a, t);
+            x[k + half] = F::sub(a, t);
+        }
+    }
+}
+
+// One round of S stages over every column: groups g = (block, j), i0 = block 2^S q + j.
+// CF: consecutive threads take consecutive columns (RowMajor), else consecutive groups.
+template <class F, int S, bool DIF, bool CF, class Lay>
+__device__ __forceinline__ void round_s(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                        int lq, const typename F::Tw *tw) {
     using T = typename F::T;
-    const int q = 1 << lq, h = 2 * q;
-    const int logG = logR - 2;
+    const int logG = logR - S;
     const int total = 1 << (logG + logC);
+    const int q = 1 << lq;
     for (int w = threadIdx.x; w < total; w += blockDim.x) {
         int c, g;
         if (CF) {
@@ -38,108 +106,53 @@ __device__ __forceinline__ void dif_round4(typename F::T *sm, int logR, int logC
             c = w >> logG;
         }
         const int j = g & (q - 1);
-        const int i0 = ((g >> lq) << (lq + 2)) + j;
-        T *b = sm + c * cs;
-        const T x0 = b[i0 * rs], x1 = b[(i0 + q) * rs], x2 = b[(i0 + 2 * q) * rs],
-                x3 = b[(i0 + 3 * q) * rs];
-        const typename F::Tw w1 = tw[h - 1 + j], w2 = tw[h - 1 + j + q], w3 = tw[q - 1 + j];
-        const T y0 = F::add(x0, x2), y2 = F::mul_tw(F::sub(x0, x2), w1);
-        const T y1 = F::add(x1, x3), y3 = F::mul_tw(F::sub(x1, x3), w2);
-        b[i0 * rs] = F::add(y0, y1);
-        b[(i0 + q) * rs] = F::mul_tw(F::sub(y0, y1), w3);
-        b[(i0 + 2 * q) * rs] = F::add(y2, y3);
-        b[(i0 + 3 * q) * rs] = F::mul_tw(F::sub(y2, y3), w3);
+        const int i0 = ((g >> lq) << (lq + S)) + j;
+        T x[1 << S];
+#pragma unroll
+        for (int k = 0; k < (1 << S); ++k) x[k] = sm[lay.at(i0 + k * q, c)];
+        if (DIF)
+            dif_group<F, S>(x, tw, j, q);
+        else
+            dit_group<F, S>(x, tw, j, q);
+#pragma unroll
+        for (int k = 0; k < (1 << S); ++k) sm[lay.at(i0 + k * q, c)] = x[k];
     }
 }
 
-template <class F, bool CF>
-__device__ __forceinline__ void dit_round4(typename F::T *sm, int logR, int logC, int rs, int cs,
-                                           int lq, const typename F::Tw *tw) {
-    using T = typename F::T;
-    const int q = 1 << lq, h = 2 * q;
-    const int logG = logR - 2;
-    const int total = 1 << (logG + logC);
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int c, g;
-        if (CF) {
-            c = w & ((1 << logC) - 1);
-            g = w >> logC;
-        } else {
-            g = w & ((1 << logG) - 1);
-            c = w >> logG;
-        }
-        const int j = g & (q - 1);
-        const int i0 = ((g >> lq) << (lq + 2)) + j;
-        T *b = sm + c * cs;
-        const T z0 = b[i0 * rs], z1 = b[(i0 + q) * rs], z2 = b[(i0 + 2 * q) * rs],
-                z3 = b[(i0 + 3 * q) * rs];
-        const typename F::Tw w1 = tw[h - 1 + j], w2 = tw[h - 1 + j + q], w3 = tw[q - 1 + j];
-        T t = F::mul_tw(z1, w3);
-        const T y0 = F::add(z0, t), y1 = F::sub(z0, t);
-        t = F::mul_tw(z3, w3);
-        const T y2 = F::add(z2, t), y3 = F::sub(z2, t);
-        t = F::mul_tw(y2, w1);
-        b[i0 * rs] = F::add(y0, t);
-        b[(i0 + 2 * q) * rs] = F::sub(y0, t);
-        t = F::mul_tw(y3, w2);
-        b[(i0 + q) * rs] = F::add(y1, t);
-        b[(i0 + 3 * q) * rs] = F::sub(y1, t);
+template <class F, bool DIF, bool CF, class Lay>
+__device__ __forceinline__ void round_any(int S, typename F::T *sm, const Lay &lay, int logR,
+                                          int logC, int lq, const typename F::Tw *tw) {
+    switch (S) {
+        case 1: round_s<F, 1, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        case 2: round_s<F, 2, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        case 3: round_s<F, 3, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        default: round_s<F, 4, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
     }
+    __syncthreads();
 }
 
-template <class F, bool CF, bool DIF>
-__device__ __forceinline__ void round2(typename F::T *sm, int logR, int logC, int rs, int cs,
-                                       const typename F::Tw *tw) {
-    // single stage with half-size 1: pairs (2g, 2g+1), twiddle w_2^0 = 1
-    using T = typename F::T;
-    const int logG = logR - 1;
-    const int total = 1 << (logG + logC);
-    for (int w = threadIdx.x; w < total; w += blockDim.x) {
-        int c, g;
-        if (CF) {
-            c = w & ((1 << logC) - 1);
-            g = w >> logC;
-        } else {
-            g = w & ((1 << logG) - 1);
-            c = w >> logG;
-        }
-        T *b = sm + c * cs;
-        const T a = b[(2 * g) * rs], d = b[(2 * g + 1) * rs];
-        b[(2 * g) * rs] = F::add(a, d);
-        b[(2 * g + 1) * rs] = F::sub(a, d);
-    }
-    (void)tw;
-}
-
-// Forward R-point DIF on every column (natural in, bit-reversed out).
-template <class F, bool CF>
-__device__ void dif_columns(typename F::T *sm, int logR, int logC, int rs, int cs,
+// Forward R-point DIF on every column: a top round of logR mod 4 stages (if any), then
+// rounds of four stages down to the stage of half-size 1.
+template <class F, bool CF, class Lay>
+__device__ void dif_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                             const typename F::Tw *tw) {
-    int lq = logR - 2;
-    for (; lq >= 0; lq -= 2) {
-        dif_round4<F, CF>(sm, logR, logC, rs, cs, lq, tw);
-        __syncthreads();
+    int done = 0;
+    const int s0 = logR & 3;
+    if (s0) {
+        round_any<F, true, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
+        done = s0;
     }
-    if (logR & 1) {
-        round2<F, CF, true>(sm, logR, logC, rs, cs, tw);
-        __syncthreads();
-    }
+    for (; done < logR; done += 4) round_any<F, true, CF>(4, sm, lay, logR, logC, logR - done - 4, tw);
 }
 
-// Inverse R-point DIT on every column (bit-reversed in, natural out, unnormalised).
-template <class F, bool CF>
-__device__ void dit_columns(typename F::T *sm, int logR, int logC, int rs, int cs,
+// Inverse R-point DIT on every column: the rounds of dif_columns in reverse order.
+template <class F, bool CF, class Lay>
+__device__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                             const typename F::Tw *tw) {
-    int lq = 0;
-    if (logR & 1) {
-        round2<F, CF, false>(sm, logR, logC, rs, cs, tw);
-        __syncthreads();
-        lq = 1;
-    }
-    for (; lq <= logR - 2; lq += 2) {
-        dit_round4<F, CF>(sm, logR, logC, rs, cs, lq, tw);
-        __syncthreads();
-    }
+    const int s0 = logR & 3;
+    for (int done = logR; done > s0; done -= 4)
+        round_any<F, false, CF>(4, sm, lay, logR, logC, logR - done, tw);
+    if (s0) round_any<F, false, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
 }
 
 }  // namespace pa

@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_tile(FftGrid g, uint64_t tile
     const int N = 1 << logN;
     T *st = reinterpret_cast<T *>(smraw);
     T *sm = st + N;  // column 0: key tile, column 1: window
+    const ColMajor lay{ColMajor::stride(N)};
     const TilePair pr = tile_at(g, tile0 + blockIdx.x);
     load_stage_tables<F>(st, tab, logN, kFftLogMax);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -181,15 +182,16 @@ __global__ void __launch_bounds__(kFftThreads) fft_tile(FftGrid g, uint64_t tile
         a.y = 0;
         w.x = static_cast<R>(win_bit(pr, bp, t));
         w.y = 0;
-        sm[t] = a;
-        sm[N + t] = w;
+        sm[lay.at(t, 0)] = a;
+        sm[lay.at(t, 1)] = w;
     }
     __syncthreads();
-    dif_columns<F, false>(sm, logN, 1, 1, N, st);
-    for (int t = threadIdx.x; t < N; t += blockDim.x) sm[N + t] = F::mul_tw(sm[t], sm[N + t]);
+    dif_columns<F, false>(sm, lay, logN, 1, st);
+    for (int t = threadIdx.x; t < N; t += blockDim.x)
+        sm[lay.at(t, 1)] = F::mul_tw(sm[lay.at(t, 0)], sm[lay.at(t, 1)]);
     for (int t = threadIdx.x; t < N - 1; t += blockDim.x) st[t].y = -st[t].y;  // conjugate twiddles
     __syncthreads();
-    dit_columns<F, false>(sm + N, logN, 0, 1, N, st);
+    dit_columns<F, false>(sm + lay.cs, lay, logN, 0, st);
     const R inv_n = static_cast<R>(1) / static_cast<R>(N);  // power of two: exact
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nw = (pr.out_len + 31) / 32;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_tile(FftGrid g, uint64_t tile
         const uint32_t v = wv * 32 + lane;
         uint32_t bit = 0;
         if (v < pr.out_len) {
-            const R val = sm[N + pr.K0 + v].x * inv_n;
+            const R val = sm[lay.at(pr.K0 + v, 1)].x * inv_n;
             const R r = rint_(val);
             worst = fmax(worst, fabs(val - r));
             bit = static_cast<uint32_t>(static_cast<long long>(r)) & 1u;
@@ -306,7 +308,7 @@ int fft_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const u
     prof_end(prof, s);
     const uint64_t chunk = 1u << 30;
     if (c.fp64) {
-        const size_t smem = (size_t(1) << logN) * 3 * sizeof(double2);
+        const size_t smem = ((size_t(1) << logN) + ColMajor::words(1 << logN, 2)) * sizeof(double2);
         PA_CUDA_TRY(cudaFuncSetAttribute(fft_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem)));
         for (uint64_t t0 = 0; t0 < tiles; t0 += chunk) {
@@ -317,7 +319,7 @@ int fft_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const u
             prof_end(prof, s);
         }
     } else {
-        const size_t smem = (size_t(1) << logN) * 3 * sizeof(float2);
+        const size_t smem = ((size_t(1) << logN) + ColMajor::words(1 << logN, 2)) * sizeof(float2);
         PA_CUDA_TRY(cudaFuncSetAttribute(fft_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem)));
         for (uint64_t t0 = 0; t0 < tiles; t0 += chunk) {

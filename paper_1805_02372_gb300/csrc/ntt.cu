@@ -113,7 +113,9 @@ struct FieldHost<F64> {
 // Per-device tables: fwd[e] = w^e, inv[e] = w^-e for e < 2^(kLogMax-1), w of order 2^kLogMax.
 struct Tables {
     void *fwd = nullptr, *inv = nullptr;
+    void *stage = nullptr;  // compact stage tables, see stage_table()
 };
+constexpr int kStageBlock = 4096;  // entries per (direction, log2 R) block
 std::mutex g_tab_mu;
 Tables g_tabs[2][64];
 
@@ -138,24 +140,48 @@ int get_tables(int field, Tables *out) {
             a = mulmod_host(a, w, p);
             b = mulmod_host(b, wi, p);
         }
-        void *df = nullptr, *di = nullptr;
+        // compact stage tables: block (dir, logR) holds st[h-1+j] = w_{2h}^(+-j), R-1 entries
+        std::vector<Tw> st(size_t(2) * (kLogSmallMax + 1) * kStageBlock);
+        for (int dir = 0; dir < 2; ++dir)
+            for (int lr = 1; lr <= kLogSmallMax; ++lr)
+                for (int idx = 0; idx < (1 << lr) - 1; ++idx) {
+                    int lh = 0;
+                    while ((2 << lh) <= idx + 1) ++lh;
+                    const size_t j = size_t(idx + 1 - (1 << lh));
+                    st[(size_t(dir) * (kLogSmallMax + 1) + lr) * kStageBlock + idx] =
+                        (dir ? i : f)[j << (kLogMax - 1 - lh)];
+                }
+        void *df = nullptr, *di = nullptr, *ds = nullptr;
         cudaError_t e = cudaMalloc(&df, half * sizeof(Tw));
         if (e == cudaSuccess) e = cudaMalloc(&di, half * sizeof(Tw));
+        if (e == cudaSuccess) e = cudaMalloc(&ds, st.size() * sizeof(Tw));
         if (e == cudaSuccess) e = cudaMemcpy(df, f.data(), half * sizeof(Tw), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(di, i.data(), half * sizeof(Tw), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ds, st.data(), st.size() * sizeof(Tw), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             cudaFree(df);
             cudaFree(di);
+            cudaFree(ds);
             return cuda_fail(e);
         }
         t.fwd = df;
         t.inv = di;
+        t.stage = ds;
     }
     *out = t;
     return PA_OK;
 }
 
 // ---------------------------------------------------------------- device pieces
+
+// Copy the compact stage table of an R-point transform (dir 0: forward, 1: inverse).
+template <class F>
+__device__ __forceinline__ void load_stage(typename F::Tw *st, const typename F::Tw *__restrict__ stage,
+                                           int dir, int logR) {
+    const typename F::Tw *src = stage + (size_t(dir) * (kLogSmallMax + 1) + logR) * kStageBlock;
+    for (int idx = threadIdx.x; idx < (1 << logR) - 1; idx += blockDim.x) st[idx] = src[idx];
+}
 
 // Twiddle w^E (E < 2^kLogMax) from a half table: w^(E + 2^(kLogMax-1)) = -w^E.
 template <class F>
@@ -166,47 +192,13 @@ __device__ __forceinline__ typename F::Tw tw_at(const typename F::Tw *__restrict
 }
 
 // ---------------------------------------------------------------- tile bodies
-// Each body is run by all threads of a CTA; the standalone kernels and the
-// persistent batched kernel call the same bodies.
+// Each body is run by all threads of a CTA, with its stage tables already in shared
+// memory; the standalone kernels and the persistent batched kernel call the same bodies.
 
-// Whole transform of size 2^logN <= 2^12 in shared memory for one tile.
-template <class F>
-__device__ void body_small(unsigned char *smraw, const TilePair &pr, const BlockPtrs &bp, int logN,
-                           const typename F::Tw *__restrict__ tfwd,
-                           const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
-    using T = typename F::T;
-    using Tw = typename F::Tw;
-    const int N = 1 << logN;
-    Tw *stf = reinterpret_cast<Tw *>(smraw);
-    Tw *sti = stf + N;
-    T *sm = reinterpret_cast<T *>(sti + N);  // column 0: key tile, column 1: window
-    load_stage_tables<F>(stf, tfwd, logN, kLogMax);
-    load_stage_tables<F>(sti, tinv, logN, kLogMax);
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        sm[t] = key_bit(pr, bp, t);
-        sm[N + t] = win_bit(pr, bp, t);
-    }
-    __syncthreads();
-    dif_columns<F, false>(sm, logN, 1, 1, N, stf);
-    for (int t = threadIdx.x; t < N; t += blockDim.x) sm[N + t] = F::mont(sm[t], sm[N + t]);
-    __syncthreads();
-    dit_columns<F, false>(sm + N, logN, 0, 1, N, sti);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t nw = (pr.out_len + 31) / 32;
-    for (uint32_t w = warp; w < nw; w += blockDim.x / 32) {
-        const uint32_t v = w * 32 + lane;
-        uint32_t bit = 0;
-        if (v < pr.out_len) bit = F::low_bit(F::mul_tw(sm[N + pr.K0 + v], scale));
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
-        if (lane == 0 && word) atomicXor(bp.out32 + (pr.out_bit0 >> 5) + w, word);
-    }
-    __syncthreads();
-}
-
-// C consecutive bits of the key tile (which = 0) or window (which = 1) starting at
-// tile position t (C <= 8), as a mask.
-__device__ __forceinline__ uint32_t tile_bits8(const TilePair &pr, const BlockPtrs &bp, int which,
-                                               uint64_t t, int C) {
+// 32 consecutive bits of the key tile (which = 0) or window (which = 1) starting at tile
+// position t; positions outside the tile or the string read as 0.
+__device__ __forceinline__ uint32_t tile_bits(const TilePair &pr, const BlockPtrs &bp, int which,
+                                              uint64_t t) {
     uint32_t v = 0;
     if (which == 0) {
         if (t >= pr.key_len) return 0u;
@@ -228,100 +220,166 @@ __device__ __forceinline__ uint32_t tile_bits8(const TilePair &pr, const BlockPt
         if (lim <= 0) return 0u;
         if (lim < 32) v &= (1u << lim) - 1u;
     }
-    return v & ((1u << C) - 1u);
+    return v;
 }
 
-// Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1).
+// Whole transform of size 2^logN <= 2^12 in shared memory for one tile.
 template <class F>
-__device__ void body_fwd_first(unsigned char *smraw, const TilePair &pr, const BlockPtrs &bp,
-                               int which, uint64_t cg, int logN, int logR1, int logC,
-                               typename F::T *__restrict__ dst,
-                               const typename F::Tw *__restrict__ tfwd) {
+__device__ void body_small(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
+                           const TilePair &pr, const BlockPtrs &bp, int logN, typename F::Tw scale) {
     using T = typename F::T;
-    using Tw = typename F::Tw;
-    const int R1 = 1 << logR1, C = 1 << logC, logS = logN - logR1;
-    Tw *st = reinterpret_cast<Tw *>(smraw);
-    T *sm = reinterpret_cast<T *>(st + R1);
-    const uint64_t c0 = cg << logC;
-    load_stage_tables<F>(st, tfwd, logR1, kLogMax);
-    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
-        const uint32_t bits = tile_bits8(pr, bp, which, (uint64_t(r) << logS) + c0, C);
+    const int N = 1 << logN;
+    const ColMajor lay{ColMajor::stride(N)};
+    // 32 tile positions per thread from one or two 32-bit words of each input
+    for (int t0 = threadIdx.x * 32; t0 < N; t0 += blockDim.x * 32) {
+        const uint32_t kb = tile_bits(pr, bp, 0, t0), wb = tile_bits(pr, bp, 1, t0);
 #pragma unroll 8
-        for (int c = 0; c < C; ++c) sm[(r << logC) + c] = (bits >> c) & 1u;
+        for (int k = 0; k < 32; ++k) {
+            sm[lay.at(t0 + k, 0)] = (kb >> k) & 1u;
+            sm[lay.at(t0 + k, 1)] = (wb >> k) & 1u;
+        }
     }
     __syncthreads();
-    dif_columns<F, true>(sm, logR1, logC, C, 1, st);
-    for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
-        const int r = e >> logC, c = e & (C - 1);
-        const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
-        const uint64_t tlo = c0 + c;
-        const uint32_t E = static_cast<uint32_t>((tlo * f) << (kLogMax - logN));
-        __stcg(dst + (uint64_t(r) << logS) + tlo, F::mul_tw(sm[e], tw_at<F>(tfwd, E)));
+    dif_columns<F, false>(sm, lay, logN, 1, stf);
+    for (int t = threadIdx.x; t < N; t += blockDim.x)
+        sm[lay.at(t, 1)] = F::mont(sm[lay.at(t, 0)], sm[lay.at(t, 1)]);
+    __syncthreads();
+    dit_columns<F, false>(sm + lay.cs, lay, logN, 0, sti);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nw = (pr.out_len + 31) / 32;
+    for (uint32_t w = warp; w < nw; w += blockDim.x / 32) {
+        const uint32_t v = w * 32 + lane;
+        uint32_t bit = 0;
+        if (v < pr.out_len) bit = F::low_bit(F::mul_tw(sm[lay.at(pr.K0 + v, 1)], scale));
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+        if (lane == 0 && word) atomicXor(bp.out32 + (pr.out_bit0 >> 5) + w, word);
     }
     __syncthreads();
 }
 
-// Pass 2 of both spectra (rows of R2 = 2^logR2, C2 = 2^logC rows from row group rg),
-// the pointwise product and the inverse pass 2; X = key spectrum, W = window spectrum.
+// Row r of a pass-1 column group holds frequency f = brev(r); its C columns t = c0 + c
+// need the twiddles w_N^(t f): w_N^(c0 f) from the table, then powers of w_N^f.
+template <class F, int C>
+__device__ __forceinline__ void row_twiddle(typename F::T (&x)[C], const typename F::Tw *tab,
+                                            uint64_t c0, uint32_t f, int logN) {
+    const int sh = kLogMax - logN;
+    const typename F::Tw w0 = tw_at<F>(tab, static_cast<uint32_t>((c0 * f) << sh));
+    const typename F::Tw step = tw_at<F>(tab, f << sh);
+    typename F::T wf = F::full_form(w0);
+    x[0] = F::mul_tw(x[0], w0);
+#pragma unroll
+    for (int c = 1; c < C; ++c) {
+        wf = F::step_full(wf, step);
+        x[c] = F::mul_full(x[c], wf);
+    }
+}
+
+// Pass 1 forward on column group cg (C columns at stride S1 = N / R1).
 template <class F>
-__device__ void body_fused_last(unsigned char *smraw, uint64_t rg, int logR2, int logC,
-                                typename F::T *__restrict__ X, typename F::T *__restrict__ W,
-                                const typename F::Tw *__restrict__ tfwd,
-                                const typename F::Tw *__restrict__ tinv) {
+__device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
+                               const BlockPtrs &bp, int which, uint64_t cg, int logN, int logR1,
+                               typename F::T *__restrict__ dst, const typename F::Tw *__restrict__ tfwd) {
     using T = typename F::T;
-    using Tw = typename F::Tw;
-    const int R2 = 1 << logR2;
-    Tw *stf = reinterpret_cast<Tw *>(smraw);
-    Tw *sti = stf + R2;
-    T *sm = reinterpret_cast<T *>(sti + R2);
-    const uint64_t base = (rg << logC) << logR2;
-    load_stage_tables<F>(stf, tfwd, logR2, kLogMax);
-    load_stage_tables<F>(sti, tinv, logR2, kLogMax);
-    const int cnt = R2 << logC;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        sm[e] = __ldcg(X + base + e);
-        sm[cnt + e] = __ldcg(W + base + e);
+    constexpr int C = 32 / sizeof(T), logC = sizeof(T) == 4 ? 3 : 2;
+    const int R1 = 1 << logR1, logS = logN - logR1;
+    const uint64_t c0 = cg << logC;
+    const RowMajor lay{logC};
+    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
+        const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) sm[lay.at(r, c)] = (bits >> c) & 1u;
     }
     __syncthreads();
-    dif_columns<F, false>(sm, logR2, logC + 1, 1, R2, stf);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[cnt + e] = F::mont(sm[e], sm[cnt + e]);
+    dif_columns<F, true>(sm, lay, logR1, logC, st);
+    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
+        T x[C];
+        const uint4 *src = reinterpret_cast<const uint4 *>(sm + lay.at(r, 0));
+        *reinterpret_cast<uint4 *>(&x[0]) = src[0];
+        *reinterpret_cast<uint4 *>(&x[C / 2]) = src[1];
+        row_twiddle<F, C>(x, tfwd, c0, __brev(static_cast<uint32_t>(r)) >> (32 - logR1), logN);
+        uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0);
+        __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
+        __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[C / 2]));
+    }
     __syncthreads();
-    dit_columns<F, false>(sm + cnt, logR2, logC, 1, R2, sti);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) __stcg(W + base + e, sm[cnt + e]);
+}
+
+// Pass 2 of both spectra (rows of R2 = 2^logR2, C2 rows from row group rg), the pointwise
+// product and the inverse pass 2; X = key spectrum, W = window spectrum.
+template <class F>
+__device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
+                                const typename F::Tw *sti, uint64_t rg, int logR2,
+                                typename F::T *__restrict__ X, typename F::T *__restrict__ W) {
+    using T = typename F::T;
+    constexpr int logC = sizeof(T) == 4 ? 2 : 1, C = 1 << logC;
+    constexpr int V = 16 / sizeof(T);  // elements per 16-byte vector
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(X + base + e));
+        const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(W + base + e));
+        const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            sm[lay.at(r + k, c)] = xs[k];
+            sm[lay.at(r + k, C + c)] = ws[k];
+        }
+    }
+    __syncthreads();
+    dif_columns<F, false>(sm, lay, logR2, logC + 1, stf);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        sm[lay.at(r, C + c)] = F::mont(sm[lay.at(r, c)], sm[lay.at(r, C + c)]);
+    }
+    __syncthreads();
+    dit_columns<F, false>(sm + C * lay.cs, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, C + c)];
+        __stcg(reinterpret_cast<uint4 *>(W + base + e), ov);
+    }
     __syncthreads();
 }
 
 // Inverse pass 1 on column group cg of the product, scale, low bit, XOR output bits.
 template <class F>
-__device__ void body_inv_first(unsigned char *smraw, const TilePair &pr, const BlockPtrs &bp,
-                               uint64_t cg, int logN, int logR1, int logC,
+__device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
+                               const BlockPtrs &bp, uint64_t cg, int logN, int logR1,
                                const typename F::T *__restrict__ src,
                                const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
     using T = typename F::T;
-    using Tw = typename F::Tw;
-    const int R1 = 1 << logR1, C = 1 << logC, logS = logN - logR1;
-    Tw *st = reinterpret_cast<Tw *>(smraw);
-    T *sm = reinterpret_cast<T *>(st + R1);
+    constexpr int C = 32 / sizeof(T), logC = sizeof(T) == 4 ? 3 : 2;
+    const int R1 = 1 << logR1, logS = logN - logR1;
     const uint64_t c0 = cg << logC;
-    load_stage_tables<F>(st, tinv, logR1, kLogMax);
-    for (int e = threadIdx.x; e < (R1 << logC); e += blockDim.x) {
-        const int r = e >> logC, c = e & (C - 1);
-        const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
-        const uint64_t tlo = c0 + c;
-        const uint32_t E = static_cast<uint32_t>((tlo * f) << (kLogMax - logN));
-        sm[e] = F::mul_tw(__ldcg(src + (uint64_t(r) << logS) + tlo), tw_at<F>(tinv, E));
+    const RowMajor lay{logC};
+    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
+        T x[C];
+        const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0);
+        *reinterpret_cast<uint4 *>(&x[0]) = __ldcg(g);
+        *reinterpret_cast<uint4 *>(&x[C / 2]) = __ldcg(g + 1);
+        row_twiddle<F, C>(x, tinv, c0, __brev(static_cast<uint32_t>(r)) >> (32 - logR1), logN);
+        uint4 *d = reinterpret_cast<uint4 *>(sm + lay.at(r, 0));
+        d[0] = *reinterpret_cast<uint4 *>(&x[0]);
+        d[1] = *reinterpret_cast<uint4 *>(&x[C / 2]);
     }
     __syncthreads();
-    dit_columns<F, true>(sm, logR1, logC, C, 1, st);
+    dit_columns<F, true>(sm, lay, logR1, logC, st);
     // row r holds conv indices k = r*S1 + c0 + c (c < C): C output bits per row
     for (int r = threadIdx.x; r < R1; r += blockDim.x) {
         const uint64_t k0 = (uint64_t(r) << logS) + c0;
         if (k0 + C <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
         uint32_t byte = 0;
+#pragma unroll
         for (int c = 0; c < C; ++c) {
             const uint64_t k = k0 + c;
             if (k >= pr.K0 && k < uint64_t(pr.K0) + pr.out_len)
-                byte |= F::low_bit(F::mul_tw(sm[(r << logC) + c], scale)) << c;
+                byte |= F::low_bit(F::mul_tw(sm[lay.at(r, c)], scale)) << c;
         }
         if (byte) {
             const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of C
@@ -336,48 +394,67 @@ __device__ void body_inv_first(unsigned char *smraw, const TilePair &pr, const B
 template <class F>
 __global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict__ pairs, BlockPtrs bp,
                                                       int logN,
-                                                      const typename F::Tw *__restrict__ tfwd,
-                                                      const typename F::Tw *__restrict__ tinv,
+                                                      const typename F::Tw *__restrict__ stage,
                                                       typename F::Tw scale) {
+    using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
+    Tw *stf = reinterpret_cast<Tw *>(smraw);
+    Tw *sti = stf + (1 << logN);
     const TilePair pr = pairs[blockIdx.x];
-    body_small<F>(smraw, pr, bp, logN, tfwd, tinv, scale);
+    load_stage<F>(stf, stage, 0, logN);
+    load_stage<F>(sti, stage, 1, logN);
+    body_small<F>(reinterpret_cast<typename F::T *>(sti + (1 << logN)), stf, sti, pr, bp, logN, scale);
 }
 
 template <class F>
 __global__ void __launch_bounds__(kThreads) ntt_fwd_first(const TilePair *__restrict__ pairs,
-                                                          BlockPtrs bp, int logN, int logR1, int logC,
+                                                          BlockPtrs bp, int logN, int logR1,
                                                           typename F::T *__restrict__ ws,
+                                                          const typename F::Tw *__restrict__ stage,
                                                           const typename F::Tw *__restrict__ tfwd) {
+    using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
+    Tw *st = reinterpret_cast<Tw *>(smraw);
     const int which = blockIdx.y & 1;
     const uint32_t pi = blockIdx.y >> 1;
     const TilePair pr = pairs[pi];
     typename F::T *dst = ws + (uint64_t(pi) * 2 + which) * (uint64_t(1) << logN);
-    body_fwd_first<F>(smraw, pr, bp, which, blockIdx.x, logN, logR1, logC, dst, tfwd);
+    load_stage<F>(st, stage, 0, logR1);
+    body_fwd_first<F>(reinterpret_cast<typename F::T *>(st + (1 << logR1)), st, pr, bp, which,
+                      blockIdx.x, logN, logR1, dst, tfwd);
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2, int logC,
+__global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2,
                                                            typename F::T *__restrict__ ws,
-                                                           const typename F::Tw *__restrict__ tfwd,
-                                                           const typename F::Tw *__restrict__ tinv) {
+                                                           const typename F::Tw *__restrict__ stage) {
+    using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
+    Tw *stf = reinterpret_cast<Tw *>(smraw);
+    Tw *sti = stf + (1 << logR2);
     typename F::T *X = ws + (uint64_t(blockIdx.y) * 2) * (uint64_t(1) << logN);
-    body_fused_last<F>(smraw, blockIdx.x, logR2, logC, X, X + (uint64_t(1) << logN), tfwd, tinv);
+    load_stage<F>(stf, stage, 0, logR2);
+    load_stage<F>(sti, stage, 1, logR2);
+    body_fused_last<F>(reinterpret_cast<typename F::T *>(sti + (1 << logR2)), stf, sti, blockIdx.x,
+                       logR2, X, X + (uint64_t(1) << logN));
 }
 
 template <class F>
 __global__ void __launch_bounds__(kThreads) ntt_inv_first(const TilePair *__restrict__ pairs,
-                                                          BlockPtrs bp, int logN, int logR1, int logC,
+                                                          BlockPtrs bp, int logN, int logR1,
                                                           const typename F::T *__restrict__ ws,
+                                                          const typename F::Tw *__restrict__ stage,
                                                           const typename F::Tw *__restrict__ tinv,
                                                           typename F::Tw scale) {
+    using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
+    Tw *st = reinterpret_cast<Tw *>(smraw);
     const uint32_t pi = blockIdx.y;
     const TilePair pr = pairs[pi];
     const typename F::T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
-    body_inv_first<F>(smraw, pr, bp, blockIdx.x, logN, logR1, logC, src, tinv, scale);
+    load_stage<F>(st, stage, 1, logR1);
+    body_inv_first<F>(reinterpret_cast<typename F::T *>(st + (1 << logR1)), st, pr, bp, blockIdx.x,
+                      logN, logR1, src, tinv, scale);
 }
 
 // ---------------------------------------------------------------- persistent batched kernel
@@ -425,14 +502,15 @@ template <class F>
 __global__ void __launch_bounds__(kThreads) ntt_persistent(
     const uint64_t *__restrict__ items, uint32_t nitems, const NttTile *__restrict__ tiles,
     const BlockPtrs *__restrict__ blks, typename F::T *__restrict__ ws,
-    const typename F::Tw *__restrict__ tfwd, const typename F::Tw *__restrict__ tinv,
-    uint32_t *c1, uint32_t *c2, uint32_t *c3, uint32_t slots, uint32_t *next, int *status) {
+    const typename F::Tw *__restrict__ stage, const typename F::Tw *__restrict__ tfwd,
+    const typename F::Tw *__restrict__ tinv, uint32_t *c1, uint32_t *c2, uint32_t *c3,
+    uint32_t slots, uint32_t *next, int *status) {
+    using T = typename F::T;
     using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint64_t cur;
     __shared__ int flag;
-    const int logC1 = sizeof(typename F::T) == 4 ? 3 : 2;
-    const int logC2 = sizeof(typename F::T) == 4 ? 2 : 1;
+    Tw *st0 = reinterpret_cast<Tw *>(smraw);
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t i = atomicAdd(next, 1u);
@@ -450,27 +528,37 @@ __global__ void __launch_bounds__(kThreads) ntt_persistent(
         Tw scale;
         memcpy(&scale, &tl.scale, sizeof(Tw));
         const int logN = static_cast<int>(tl.logN);
-        typename F::T *X = ws + tl.ws_off;
-        typename F::T *W = X + (uint64_t(1) << logN);
+        const int logR1 = static_cast<int>(tl.logR1), logR2 = static_cast<int>(tl.logR2);
+        T *X = ws + tl.ws_off;
+        T *W = X + (uint64_t(1) << logN);
         if (type == 0) {
-            body_small<F>(smraw, tl.p, bp, logN, tfwd, tinv, scale);
+            Tw *sti = st0 + (1 << logN);
+            load_stage<F>(st0, stage, 0, logN);
+            load_stage<F>(sti, stage, 1, logN);
+            body_small<F>(reinterpret_cast<T *>(sti + (1 << logN)), st0, sti, tl.p, bp, logN, scale);
         } else if (type == 1) {
             // the spectra slot is reused: wait until the tile `slots` earlier released it
             bool ok = true;
             if (ti >= slots) ok = wait_count(c3 + (ti - slots), tiles[ti - slots].g1, status, &flag);
             const int which = sub >= tl.g1 ? 1 : 0;
+            load_stage<F>(st0, stage, 0, logR1);
             if (ok)
-                body_fwd_first<F>(smraw, tl.p, bp, which, sub - which * tl.g1, logN,
-                                  static_cast<int>(tl.logR1), logC1, which ? W : X, tfwd);
+                body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, which,
+                                  sub - which * tl.g1, logN, logR1, which ? W : X, tfwd);
             signal_count(c1 + ti);
         } else if (type == 2) {
+            Tw *sti = st0 + (1 << logR2);
+            load_stage<F>(st0, stage, 0, logR2);
+            load_stage<F>(sti, stage, 1, logR2);
             if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
-                body_fused_last<F>(smraw, sub, static_cast<int>(tl.logR2), logC2, X, W, tfwd, tinv);
+                body_fused_last<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
+                                   X, W);
             signal_count(c2 + ti);
         } else {
+            load_stage<F>(st0, stage, 1, logR1);
             if (wait_count(c2 + ti, tl.g2, status, &flag))
-                body_inv_first<F>(smraw, tl.p, bp, sub, logN, static_cast<int>(tl.logR1), logC1, W,
-                                  tinv, scale);
+                body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
+                                  logN, logR1, W, tinv, scale);
             signal_count(c3 + ti);
         }
     }
@@ -605,6 +693,7 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
     BlockPtrs one{reinterpret_cast<const uint32_t *>(key), reinterpret_cast<const uint32_t *>(seed),
                   reinterpret_cast<uint32_t *>(out), cfg.n, cfg.m};
     const Tw *tf = static_cast<const Tw *>(tab.fwd), *ti = static_cast<const Tw *>(tab.inv);
+    const Tw *stg = static_cast<const Tw *>(tab.stage);
     const Tw scale = FieldHost<F>::scale(c.log2n);
     const int logN = static_cast<int>(c.log2n);
 
@@ -613,14 +702,15 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
     prof_end(prof, s);
 
     if (c.passes == 1) {
-        const size_t smem = size_t(2) * (size_t(1) << logN) * (sizeof(Tw) + sizeof(T));
+        const size_t smem = size_t(2) * (size_t(1) << logN) * sizeof(Tw) +
+                            size_t(ColMajor::words(1 << logN, 2)) * sizeof(T);
         PA_CUDA_TRY(cudaFuncSetAttribute(ntt_small<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem)));
         for (uint64_t p0 = 0; p0 < npairs; p0 += 65535) {
             const uint64_t cnt = npairs - p0 < 65535 ? npairs - p0 : 65535;
             prof_begin(prof, K_NTT_SMALL, s);
-            ntt_small<F><<<static_cast<unsigned>(cnt), kThreads, smem, s>>>(pairs + p0, one, logN, tf,
-                                                                           ti, scale);
+            ntt_small<F><<<static_cast<unsigned>(cnt), kThreads, smem, s>>>(pairs + p0, one, logN,
+                                                                           stg, scale);
             prof_end(prof, s);
         }
         PA_CUDA_TRY(cudaGetLastError());
@@ -630,8 +720,8 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
     const int logC1 = sizeof(T) == 4 ? 3 : 2;  // 32-byte row segments
     const int logC2 = sizeof(T) == 4 ? 2 : 1;
     const size_t sm1 = (size_t(1) << logR1) * sizeof(Tw) + (size_t(1) << (logR1 + logC1)) * sizeof(T);
-    const size_t sm2 =
-        2 * (size_t(1) << logR2) * sizeof(Tw) + 2 * (size_t(1) << (logR2 + logC2)) * sizeof(T);
+    const size_t sm2 = 2 * (size_t(1) << logR2) * sizeof(Tw) +
+                       size_t(ColMajor::words(1 << logR2, 2 << logC2)) * sizeof(T);
     PA_CUDA_TRY(cudaFuncSetAttribute(ntt_fwd_first<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(sm1)));
     PA_CUDA_TRY(cudaFuncSetAttribute(ntt_inv_first<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -644,15 +734,15 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
         const uint64_t cnt = npairs - p0 < c.concurrent ? npairs - p0 : c.concurrent;
         prof_begin(prof, K_NTT_FWD_FIRST, s);
         ntt_fwd_first<F><<<dim3(gx1, static_cast<unsigned>(2 * cnt)), kThreads, sm1, s>>>(
-            pairs + p0, one, logN, logR1, logC1, spec, tf);
+            pairs + p0, one, logN, logR1, spec, stg, tf);
         prof_end(prof, s);
         prof_begin(prof, K_NTT_FUSED_LAST, s);
         ntt_fused_last<F><<<dim3(gx2, static_cast<unsigned>(cnt)), kThreads, sm2, s>>>(
-            logN, logR2, logC2, spec, tf, ti);
+            logN, logR2, spec, stg);
         prof_end(prof, s);
         prof_begin(prof, K_NTT_INV_FIRST, s);
         ntt_inv_first<F><<<dim3(gx1, static_cast<unsigned>(cnt)), kThreads, sm1, s>>>(
-            pairs + p0, one, logN, logR1, logC1, spec, ti, scale);
+            pairs + p0, one, logN, logR1, spec, stg, ti, scale);
         prof_end(prof, s);
     }
     PA_CUDA_TRY(cudaGetLastError());
@@ -738,12 +828,13 @@ int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t ma
     size_t smem = 0;
     for (const NttTile &t : tiles) {
         if (t.logN <= static_cast<uint32_t>(kLogSmallMax)) {
-            smem = std::max(smem, (size_t(2) << t.logN) * (twsz + elem));
+            smem = std::max(smem, (size_t(2) << t.logN) * twsz +
+                                      size_t(ColMajor::words(1 << t.logN, 2)) * elem);
         } else {
             const int logC1 = elem == 4 ? 3 : 2, logC2 = elem == 4 ? 2 : 1;
             smem = std::max(smem, (size_t(1) << t.logR1) * twsz + (size_t(1) << (t.logR1 + logC1)) * elem);
             smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
-                                      2 * (size_t(1) << (t.logR2 + logC2)) * elem);
+                                      size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
         }
     }
     info->smem = smem;
@@ -804,9 +895,9 @@ int batch_launch_field(const NttBatchInfo &info, void *ws, const void *blks, int
     ntt_persistent<F><<<static_cast<unsigned>(grid), kThreads, info.smem, s>>>(
         reinterpret_cast<const uint64_t *>(b + info.off_items), static_cast<uint32_t>(info.nitems),
         reinterpret_cast<const NttTile *>(b + info.off_tiles), static_cast<const BlockPtrs *>(blks),
-        reinterpret_cast<typename F::T *>(b + info.off_spec), static_cast<const Tw *>(tab.fwd),
-        static_cast<const Tw *>(tab.inv), cnt, cnt + nt, cnt + 2 * nt, info.slots, cnt + 3 * nt,
-        status);
+        reinterpret_cast<typename F::T *>(b + info.off_spec), static_cast<const Tw *>(tab.stage),
+        static_cast<const Tw *>(tab.fwd), static_cast<const Tw *>(tab.inv), cnt, cnt + nt,
+        cnt + 2 * nt, info.slots, cnt + 3 * nt, status);
     prof_end(prof, s);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;

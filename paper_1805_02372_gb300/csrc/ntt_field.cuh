@@ -49,6 +49,19 @@ struct F31 {
         return static_cast<int32_t>(r) < 0 ? r + P : r;
     }
     __device__ static __forceinline__ uint32_t low_bit(T a) { return a & 1u; }
+    // A twiddle in the form mul_full expects: w * 2^32 mod p (Montgomery form).
+    static constexpr uint32_t R_MOD = static_cast<uint32_t>((uint64_t(1) << 32) % 2013265921u);
+    static constexpr uint32_t R_Q = static_cast<uint32_t>((uint64_t(R_MOD) << 32) / 2013265921u);
+    __device__ static __forceinline__ T full_form(Tw w) {
+        Tw r;
+        r.w = R_MOD;
+        r.q = R_Q;
+        return mul_tw(w.w, r);
+    }
+    // a * w for w in full form (no precomputed quotient): Montgomery product.
+    __device__ static __forceinline__ T mul_full(T a, T wf) { return mont(a, wf); }
+    // next twiddle in full form: wf * step
+    __device__ static __forceinline__ T step_full(T wf, Tw step) { return mul_tw(wf, step); }
     __device__ static __forceinline__ Tw neg_tw(Tw w) {
         // -w mod p with its own quotient: floor((p - w) 2^32 / p) = 2^32 - 1 - q for w != 0.
         Tw r;
@@ -87,6 +100,9 @@ struct F64 {
     __device__ static __forceinline__ T mul_tw(T a, Tw w) { return mul(a, w); }
     __device__ static __forceinline__ T mont(T a, T b) { return mul(a, b); }
     __device__ static __forceinline__ uint32_t low_bit(T a) { return static_cast<uint32_t>(a & 1u); }
+    __device__ static __forceinline__ T full_form(Tw w) { return w; }
+    __device__ static __forceinline__ T mul_full(T a, T wf) { return mul(a, wf); }
+    __device__ static __forceinline__ T step_full(T wf, Tw step) { return mul(wf, step); }
     __device__ static __forceinline__ Tw neg_tw(Tw w) { return w ? P - w : 0; }
 };
 
