@@ -155,4 +155,59 @@ __device__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int log
     if (s0) round_any<F, false, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
 }
 
+// The forward rounds of dif_columns except the last (the four stages of half-size 8..1),
+// and the inverse rounds of dit_columns except the first: the caller runs those two in
+// registers around the pointwise product (product_round). Needs logR >= 4.
+template <class F, bool CF, class Lay>
+__device__ void dif_columns_head(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                 const typename F::Tw *tw) {
+    int done = 0;
+    const int s0 = logR & 3;
+    if (s0) {
+        round_any<F, true, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
+        done = s0;
+    }
+    for (; done < logR - 4; done += 4)
+        round_any<F, true, CF>(4, sm, lay, logR, logC, logR - done - 4, tw);
+}
+
+template <class F, bool CF, class Lay>
+__device__ void dit_columns_tail(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                 const typename F::Tw *tw) {
+    const int s0 = logR & 3;
+    for (int done = logR - 4; done > s0; done -= 4)
+        round_any<F, false, CF>(4, sm, lay, logR, logC, logR - done, tw);
+    if (s0) round_any<F, false, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
+}
+
+// For each of C column pairs (key column c, window column C + c): the last four forward
+// stages of both, the pointwise product Mul, the first four inverse stages of the
+// product, written over the window column. Groups are 16 consecutive rows (q = 1).
+template <class F, class Lay, class Mul>
+__device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int logC,
+                              const typename F::Tw *twf, const typename F::Tw *twi, Mul mul) {
+    using T = typename F::T;
+    const int logG = logR - 4;
+    const int C = 1 << logC;
+    const int total = 1 << (logG + logC);
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int g = w & ((1 << logG) - 1), c = w >> logG;
+        const int i0 = g << 4;
+        T x[16], y[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            x[k] = sm[lay.at(i0 + k, c)];
+            y[k] = sm[lay.at(i0 + k, C + c)];
+        }
+        dif_group<F, 4>(x, twf, 0, 1);
+        dif_group<F, 4>(y, twf, 0, 1);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
+        dit_group<F, 4>(y, twi, 0, 1);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sm[lay.at(i0 + k, C + c)] = y[k];
+    }
+    __syncthreads();
+}
+
 }  // namespace pa

@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_tile(FftGrid g, uint64_t tile
     dif_columns<F, false>(sm, lay, logN, 1, st);
     for (int t = threadIdx.x; t < N; t += blockDim.x)
         sm[lay.at(t, 1)] = F::mul_tw(sm[lay.at(t, 0)], sm[lay.at(t, 1)]);
+    __syncthreads();
     for (int t = threadIdx.x; t < N - 1; t += blockDim.x) st[t].y = -st[t].y;  // conjugate twiddles
     __syncthreads();
     dit_columns<F, false>(sm + lay.cs, lay, logN, 0, st);

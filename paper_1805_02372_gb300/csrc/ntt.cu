@@ -37,6 +37,9 @@ namespace pa {
 constexpr int kLogMax = 22;           // largest transform: 2^22
 constexpr int kLogSmallMax = 12;      // one-CTA transforms up to 2^12
 constexpr int kThreads = 512;
+// Two CTAs of 512 threads per SM for the 32-bit field (<= 64 registers), one for 64-bit.
+template <class F>
+constexpr int kMinBlocks = sizeof(typename F::T) == 4 ? 2 : 1;
 
 // A transform tile of a batch: geometry plus its transform shape and spectra slot.
 struct NttTile {
@@ -240,11 +243,18 @@ __device__ void body_small(typename F::T *sm, const typename F::Tw *stf, const t
         }
     }
     __syncthreads();
-    dif_columns<F, false>(sm, lay, logN, 1, stf);
-    for (int t = threadIdx.x; t < N; t += blockDim.x)
-        sm[lay.at(t, 1)] = F::mont(sm[lay.at(t, 0)], sm[lay.at(t, 1)]);
-    __syncthreads();
-    dit_columns<F, false>(sm + lay.cs, lay, logN, 0, sti);
+    const auto mul = [](T a, T b) { return F::mont(a, b); };
+    if (logN >= 4) {
+        dif_columns_head<F, false>(sm, lay, logN, 1, stf);
+        product_round<F>(sm, lay, logN, 0, stf, sti, mul);
+        dit_columns_tail<F, false>(sm + lay.cs, lay, logN, 0, sti);
+    } else {
+        dif_columns<F, false>(sm, lay, logN, 1, stf);
+        for (int t = threadIdx.x; t < N; t += blockDim.x)
+            sm[lay.at(t, 1)] = F::mont(sm[lay.at(t, 0)], sm[lay.at(t, 1)]);
+        __syncthreads();
+        dit_columns<F, false>(sm + lay.cs, lay, logN, 0, sti);
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nw = (pr.out_len + 31) / 32;
     for (uint32_t w = warp; w < nw; w += blockDim.x / 32) {
@@ -329,13 +339,10 @@ __device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
         }
     }
     __syncthreads();
-    dif_columns<F, false>(sm, lay, logR2, logC + 1, stf);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        sm[lay.at(r, C + c)] = F::mont(sm[lay.at(r, c)], sm[lay.at(r, C + c)]);
-    }
-    __syncthreads();
-    dit_columns<F, false>(sm + C * lay.cs, lay, logR2, logC, sti);
+    // logR2 >= 6 for every two-pass transform (N >= 2^13)
+    dif_columns_head<F, false>(sm, lay, logR2, logC + 1, stf);
+    product_round<F>(sm, lay, logR2, logC, stf, sti, [](T a, T b) { return F::mont(a, b); });
+    dit_columns_tail<F, false>(sm + C * lay.cs, lay, logR2, logC, sti);
     for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
         const int c = e >> logR2, r = e & (R2 - 1);
         uint4 ov;
@@ -392,7 +399,7 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
 // ---------------------------------------------------------------- standalone kernels
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict__ pairs, BlockPtrs bp,
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_small(const TilePair *__restrict__ pairs, BlockPtrs bp,
                                                       int logN,
                                                       const typename F::Tw *__restrict__ stage,
                                                       typename F::Tw scale) {
@@ -407,7 +414,7 @@ __global__ void __launch_bounds__(kThreads) ntt_small(const TilePair *__restrict
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_fwd_first(const TilePair *__restrict__ pairs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fwd_first(const TilePair *__restrict__ pairs,
                                                           BlockPtrs bp, int logN, int logR1,
                                                           typename F::T *__restrict__ ws,
                                                           const typename F::Tw *__restrict__ stage,
@@ -425,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) ntt_fwd_first(const TilePair *__rest
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2,
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fused_last(int logN, int logR2,
                                                            typename F::T *__restrict__ ws,
                                                            const typename F::Tw *__restrict__ stage) {
     using Tw = typename F::Tw;
@@ -440,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) ntt_fused_last(int logN, int logR2,
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_inv_first(const TilePair *__restrict__ pairs,
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_inv_first(const TilePair *__restrict__ pairs,
                                                           BlockPtrs bp, int logN, int logR1,
                                                           const typename F::T *__restrict__ ws,
                                                           const typename F::Tw *__restrict__ stage,
@@ -499,7 +506,7 @@ __device__ __forceinline__ void signal_count(uint32_t *c) {
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads) ntt_persistent(
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
     const uint64_t *__restrict__ items, uint32_t nitems, const NttTile *__restrict__ tiles,
     const BlockPtrs *__restrict__ blks, typename F::T *__restrict__ ws,
     const typename F::Tw *__restrict__ stage, const typename F::Tw *__restrict__ tfwd,
