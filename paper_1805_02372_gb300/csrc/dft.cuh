@@ -19,11 +19,27 @@
 
 namespace pa {
 
+// addrs<LQ, K>(i0, c, a): addresses of rows i0 + k 2^LQ (k < K) of column c, for the
+// strides the rounds use (LQ = 0 with i0 a multiple of 16 and K <= 16, LQ = 4, LQ >= 8).
 struct RowMajor {
     int logC;
     __device__ __forceinline__ int at(int r, int c) const {
         const int slot = (r & ~3) | ((r + (r >> 4)) & 3);
         return (slot << logC) + c;
+    }
+    template <int LQ, int K>
+    __device__ __forceinline__ void addrs(int i0, int c, int (&a)[K]) const {
+        if (LQ >= 8) {
+            const int b = at(i0, c);
+#pragma unroll
+            for (int k = 0; k < K; ++k) a[k] = b + (k << (LQ + logC));
+        } else {
+            const int rot0 = (i0 + (i0 >> 4)) & 3;
+            const int b = ((i0 & ~3) << logC) + c;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                a[k] = b + ((LQ == 0 ? (k & ~3) : (k << LQ)) << logC) + (((rot0 + k) & 3) << logC);
+        }
     }
     static __host__ __device__ __forceinline__ int words(int R, int C) { return R * C; }
 };
@@ -31,6 +47,13 @@ struct RowMajor {
 struct ColMajor {
     int cs;  // column stride R + R/16
     __device__ __forceinline__ int at(int r, int c) const { return c * cs + r + (r >> 4); }
+    template <int LQ, int K>
+    __device__ __forceinline__ void addrs(int i0, int c, int (&a)[K]) const {
+        const int b = at(i0, c);
+        const int step = LQ == 0 ? 1 : (1 << LQ) + (1 << (LQ - 4));
+#pragma unroll
+        for (int k = 0; k < K; ++k) a[k] = b + k * step;
+    }
     static __host__ __device__ __forceinline__ int stride(int R) { return R + (R >> 4); }
     static __host__ __device__ __forceinline__ int words(int R, int C) { return C * stride(R); }
 };
@@ -89,10 +112,11 @@ __device__ __forceinline__ void dit_group(typename F::T (&x)[1 << S], const type
 
 // One round of S stages over every column: groups g = (block, j), i0 = block 2^S q + j.
 // CF: consecutive threads take consecutive columns (RowMajor), else consecutive groups.
-template <class F, int S, bool DIF, bool CF, class Lay>
+template <class F, int S, bool DIF, bool CF, class Lay, int LQ>
 __device__ __forceinline__ void round_s(typename F::T *sm, const Lay &lay, int logR, int logC,
-                                        int lq, const typename F::Tw *tw) {
+                                        int lq_rt, const typename F::Tw *tw) {
     using T = typename F::T;
+    const int lq = LQ >= 0 ? LQ : lq_rt;
     const int logG = logR - S;
     const int total = 1 << (logG + logC);
     const int q = 1 << lq;
@@ -108,25 +132,46 @@ __device__ __forceinline__ void round_s(typename F::T *sm, const Lay &lay, int l
         const int j = g & (q - 1);
         const int i0 = ((g >> lq) << (lq + S)) + j;
         T x[1 << S];
+        int a[1 << S];
+        if (LQ >= 0) {
+            lay.template addrs<(LQ >= 0 ? LQ : 0), (1 << S)>(i0, c, a);
+        } else {
 #pragma unroll
-        for (int k = 0; k < (1 << S); ++k) x[k] = sm[lay.at(i0 + k * q, c)];
+            for (int k = 0; k < (1 << S); ++k) a[k] = lay.at(i0 + k * q, c);
+        }
+#pragma unroll
+        for (int k = 0; k < (1 << S); ++k) x[k] = sm[a[k]];
         if (DIF)
             dif_group<F, S>(x, tw, j, q);
         else
             dit_group<F, S>(x, tw, j, q);
 #pragma unroll
-        for (int k = 0; k < (1 << S); ++k) sm[lay.at(i0 + k * q, c)] = x[k];
+        for (int k = 0; k < (1 << S); ++k) sm[a[k]] = x[k];
     }
+}
+
+template <class F, int S, bool DIF, bool CF, class Lay>
+__device__ __forceinline__ void round_q(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                        int lq, const typename F::Tw *tw) {
+    // strides 1, 16, 256 have compile-time addressing (rounds of transforms with R >= 16)
+    if (logR >= 4 && lq == 0)
+        round_s<F, S, DIF, CF, Lay, 0>(sm, lay, logR, logC, lq, tw);
+    else if (logR >= 4 && lq == 4)
+        round_s<F, S, DIF, CF, Lay, 4>(sm, lay, logR, logC, lq, tw);
+    else if (logR >= 4 && lq == 8)
+        round_s<F, S, DIF, CF, Lay, 8>(sm, lay, logR, logC, lq, tw);
+    else
+        round_s<F, S, DIF, CF, Lay, -1>(sm, lay, logR, logC, lq, tw);
 }
 
 template <class F, bool DIF, bool CF, class Lay>
 __device__ __forceinline__ void round_any(int S, typename F::T *sm, const Lay &lay, int logR,
                                           int logC, int lq, const typename F::Tw *tw) {
     switch (S) {
-        case 1: round_s<F, 1, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
-        case 2: round_s<F, 2, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
-        case 3: round_s<F, 3, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
-        default: round_s<F, 4, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        case 1: round_q<F, 1, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        case 2: round_q<F, 2, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        case 3: round_q<F, 3, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
+        default: round_q<F, 4, DIF, CF, Lay>(sm, lay, logR, logC, lq, tw); break;
     }
     __syncthreads();
 }
@@ -194,10 +239,13 @@ __device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int l
         const int g = w & ((1 << logG) - 1), c = w >> logG;
         const int i0 = g << 4;
         T x[16], y[16];
+        int ax[16], ay[16];
+        lay.template addrs<0, 16>(i0, c, ax);
+        lay.template addrs<0, 16>(i0, C + c, ay);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            x[k] = sm[lay.at(i0 + k, c)];
-            y[k] = sm[lay.at(i0 + k, C + c)];
+            x[k] = sm[ax[k]];
+            y[k] = sm[ay[k]];
         }
         dif_group<F, 4>(x, twf, 0, 1);
         dif_group<F, 4>(y, twf, 0, 1);
@@ -205,7 +253,7 @@ __device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int l
         for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
         dit_group<F, 4>(y, twi, 0, 1);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) sm[lay.at(i0 + k, C + c)] = y[k];
+        for (int k = 0; k < 16; ++k) sm[ay[k]] = y[k];
     }
     __syncthreads();
 }

@@ -49,8 +49,21 @@ struct NttTile {
     uint32_t logN, logR1, logR2;
     uint32_t g1;      // pass-1 column groups (per input)
     uint32_t g2;      // pass-2 row groups
-    uint32_t pad[3];
+    uint32_t logC1;   // pass-1/3 columns per item (log2)
+    uint32_t logC2;   // pass-2 rows per item (log2)
+    uint32_t pad;
 };
+
+// Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
+// segment, and enough to give a 512-thread CTA about 8192 (32-bit) elements per item.
+inline void pass_columns(int logN, size_t elem, int *logC1, int *logC2) {
+    const int logR1 = (logN + 1) / 2, logR2 = logN / 2, logS = logN - logR1;
+    const int target = elem == 4 ? 13 : 12;
+    int c1 = std::max(elem == 4 ? 3 : 2, target - logR1);
+    int c2 = std::max(elem == 4 ? 2 : 1, target - logR2);
+    *logC1 = std::min(c1, logS);
+    *logC2 = std::min(c2, logR1);
+}
 
 // ---------------------------------------------------------------- host tables
 
@@ -284,44 +297,51 @@ __device__ __forceinline__ void row_twiddle(typename F::T (&x)[C], const typenam
     }
 }
 
-// Pass 1 forward on column group cg (C columns at stride S1 = N / R1).
+// Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1); each
+// thread handles 32-byte row segments (SEG columns).
 template <class F>
 __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
                                const BlockPtrs &bp, int which, uint64_t cg, int logN, int logR1,
-                               typename F::T *__restrict__ dst, const typename F::Tw *__restrict__ tfwd) {
+                               int logC, typename F::T *__restrict__ dst,
+                               const typename F::Tw *__restrict__ tfwd) {
     using T = typename F::T;
-    constexpr int C = 32 / sizeof(T), logC = sizeof(T) == 4 ? 3 : 2;
-    const int R1 = 1 << logR1, logS = logN - logR1;
+    constexpr int SEG = 32 / sizeof(T), logSEG = sizeof(T) == 4 ? 3 : 2;
+    const int R1 = 1 << logR1, logS = logN - logR1, C = 1 << logC;
     const uint64_t c0 = cg << logC;
     const RowMajor lay{logC};
-    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
-        const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0);
+    const int seglog = logC - logSEG;  // segments per row (log2)
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG);
 #pragma unroll
-        for (int c = 0; c < C; ++c) sm[lay.at(r, c)] = (bits >> c) & 1u;
+        for (int c = 0; c < SEG; ++c) sm[lay.at(r, sg * SEG + c)] = (bits >> c) & 1u;
     }
     __syncthreads();
     dif_columns<F, true>(sm, lay, logR1, logC, st);
-    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
-        T x[C];
-        const uint4 *src = reinterpret_cast<const uint4 *>(sm + lay.at(r, 0));
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        T x[SEG];
+        const uint4 *src = reinterpret_cast<const uint4 *>(sm + lay.at(r, sg * SEG));
         *reinterpret_cast<uint4 *>(&x[0]) = src[0];
-        *reinterpret_cast<uint4 *>(&x[C / 2]) = src[1];
-        row_twiddle<F, C>(x, tfwd, c0, __brev(static_cast<uint32_t>(r)) >> (32 - logR1), logN);
-        uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0);
+        *reinterpret_cast<uint4 *>(&x[SEG / 2]) = src[1];
+        row_twiddle<F, SEG>(x, tfwd, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
+                            logN);
+        uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
         __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
-        __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[C / 2]));
+        __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[SEG / 2]));
     }
     __syncthreads();
+    (void)C;
 }
 
 // Pass 2 of both spectra (rows of R2 = 2^logR2, C2 rows from row group rg), the pointwise
 // product and the inverse pass 2; X = key spectrum, W = window spectrum.
 template <class F>
 __device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
-                                const typename F::Tw *sti, uint64_t rg, int logR2,
+                                const typename F::Tw *sti, uint64_t rg, int logR2, int logC,
                                 typename F::T *__restrict__ X, typename F::T *__restrict__ W) {
     using T = typename F::T;
-    constexpr int logC = sizeof(T) == 4 ? 2 : 1, C = 1 << logC;
+    const int C = 1 << logC;
     constexpr int V = 16 / sizeof(T);  // elements per 16-byte vector
     const int R2 = 1 << logR2;
     const uint64_t base = (rg << logC) << logR2;
@@ -357,39 +377,43 @@ __device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
 // Inverse pass 1 on column group cg of the product, scale, low bit, XOR output bits.
 template <class F>
 __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
-                               const BlockPtrs &bp, uint64_t cg, int logN, int logR1,
+                               const BlockPtrs &bp, uint64_t cg, int logN, int logR1, int logC,
                                const typename F::T *__restrict__ src,
                                const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
     using T = typename F::T;
-    constexpr int C = 32 / sizeof(T), logC = sizeof(T) == 4 ? 3 : 2;
+    constexpr int SEG = 32 / sizeof(T), logSEG = sizeof(T) == 4 ? 3 : 2;
     const int R1 = 1 << logR1, logS = logN - logR1;
     const uint64_t c0 = cg << logC;
     const RowMajor lay{logC};
-    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
-        T x[C];
-        const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0);
+    const int seglog = logC - logSEG;
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        T x[SEG];
+        const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0 + sg * SEG);
         *reinterpret_cast<uint4 *>(&x[0]) = __ldcg(g);
-        *reinterpret_cast<uint4 *>(&x[C / 2]) = __ldcg(g + 1);
-        row_twiddle<F, C>(x, tinv, c0, __brev(static_cast<uint32_t>(r)) >> (32 - logR1), logN);
-        uint4 *d = reinterpret_cast<uint4 *>(sm + lay.at(r, 0));
+        *reinterpret_cast<uint4 *>(&x[SEG / 2]) = __ldcg(g + 1);
+        row_twiddle<F, SEG>(x, tinv, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
+                            logN);
+        uint4 *d = reinterpret_cast<uint4 *>(sm + lay.at(r, sg * SEG));
         d[0] = *reinterpret_cast<uint4 *>(&x[0]);
-        d[1] = *reinterpret_cast<uint4 *>(&x[C / 2]);
+        d[1] = *reinterpret_cast<uint4 *>(&x[SEG / 2]);
     }
     __syncthreads();
     dit_columns<F, true>(sm, lay, logR1, logC, st);
-    // row r holds conv indices k = r*S1 + c0 + c (c < C): C output bits per row
-    for (int r = threadIdx.x; r < R1; r += blockDim.x) {
-        const uint64_t k0 = (uint64_t(r) << logS) + c0;
-        if (k0 + C <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
+    // segment (r, sg) holds conv indices k = r*S1 + c0 + sg*SEG + c: SEG output bits
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        const uint64_t k0 = (uint64_t(r) << logS) + c0 + sg * SEG;
+        if (k0 + SEG <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
         uint32_t byte = 0;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
+        for (int c = 0; c < SEG; ++c) {
             const uint64_t k = k0 + c;
             if (k >= pr.K0 && k < uint64_t(pr.K0) + pr.out_len)
-                byte |= F::low_bit(F::mul_tw(sm[lay.at(r, c)], scale)) << c;
+                byte |= F::low_bit(F::mul_tw(sm[lay.at(r, sg * SEG + c)], scale)) << c;
         }
         if (byte) {
-            const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of C
+            const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of SEG
             atomicXor(bp.out32 + (pos >> 5), byte << (pos & 31));
         }
     }
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_small(const TileP
 
 template <class F>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fwd_first(const TilePair *__restrict__ pairs,
-                                                          BlockPtrs bp, int logN, int logR1,
+                                                          BlockPtrs bp, int logN, int logR1, int logC,
                                                           typename F::T *__restrict__ ws,
                                                           const typename F::Tw *__restrict__ stage,
                                                           const typename F::Tw *__restrict__ tfwd) {
@@ -428,11 +452,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fwd_first(const T
     typename F::T *dst = ws + (uint64_t(pi) * 2 + which) * (uint64_t(1) << logN);
     load_stage<F>(st, stage, 0, logR1);
     body_fwd_first<F>(reinterpret_cast<typename F::T *>(st + (1 << logR1)), st, pr, bp, which,
-                      blockIdx.x, logN, logR1, dst, tfwd);
+                      blockIdx.x, logN, logR1, logC, dst, tfwd);
 }
 
 template <class F>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fused_last(int logN, int logR2,
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fused_last(int logN, int logR2, int logC,
                                                            typename F::T *__restrict__ ws,
                                                            const typename F::Tw *__restrict__ stage) {
     using Tw = typename F::Tw;
@@ -443,12 +467,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fused_last(int lo
     load_stage<F>(stf, stage, 0, logR2);
     load_stage<F>(sti, stage, 1, logR2);
     body_fused_last<F>(reinterpret_cast<typename F::T *>(sti + (1 << logR2)), stf, sti, blockIdx.x,
-                       logR2, X, X + (uint64_t(1) << logN));
+                       logR2, logC, X, X + (uint64_t(1) << logN));
 }
 
 template <class F>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_inv_first(const TilePair *__restrict__ pairs,
-                                                          BlockPtrs bp, int logN, int logR1,
+                                                          BlockPtrs bp, int logN, int logR1, int logC,
                                                           const typename F::T *__restrict__ ws,
                                                           const typename F::Tw *__restrict__ stage,
                                                           const typename F::Tw *__restrict__ tinv,
@@ -461,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_inv_first(const T
     const typename F::T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
     load_stage<F>(st, stage, 1, logR1);
     body_inv_first<F>(reinterpret_cast<typename F::T *>(st + (1 << logR1)), st, pr, bp, blockIdx.x,
-                      logN, logR1, src, tinv, scale);
+                      logN, logR1, logC, src, tinv, scale);
 }
 
 // ---------------------------------------------------------------- persistent batched kernel
@@ -551,7 +575,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
             load_stage<F>(st0, stage, 0, logR1);
             if (ok)
                 body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, which,
-                                  sub - which * tl.g1, logN, logR1, which ? W : X, tfwd);
+                                  sub - which * tl.g1, logN, logR1, static_cast<int>(tl.logC1),
+                                  which ? W : X, tfwd);
             signal_count(c1 + ti);
         } else if (type == 2) {
             Tw *sti = st0 + (1 << logR2);
@@ -559,13 +584,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
             load_stage<F>(sti, stage, 1, logR2);
             if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
                 body_fused_last<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
-                                   X, W);
+                                   static_cast<int>(tl.logC2), X, W);
             signal_count(c2 + ti);
         } else {
             load_stage<F>(st0, stage, 1, logR1);
             if (wait_count(c2 + ti, tl.g2, status, &flag))
                 body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
-                                  logN, logR1, W, tinv, scale);
+                                  logN, logR1, static_cast<int>(tl.logC1), W, tinv, scale);
             signal_count(c3 + ti);
         }
     }
@@ -724,8 +749,8 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
         return PA_OK;
     }
     const int logR1 = static_cast<int>(c.radix_log2[0]), logR2 = static_cast<int>(c.radix_log2[1]);
-    const int logC1 = sizeof(T) == 4 ? 3 : 2;  // 32-byte row segments
-    const int logC2 = sizeof(T) == 4 ? 2 : 1;
+    int logC1 = 0, logC2 = 0;
+    pass_columns(logN, sizeof(T), &logC1, &logC2);
     const size_t sm1 = (size_t(1) << logR1) * sizeof(Tw) + (size_t(1) << (logR1 + logC1)) * sizeof(T);
     const size_t sm2 = 2 * (size_t(1) << logR2) * sizeof(Tw) +
                        size_t(ColMajor::words(1 << logR2, 2 << logC2)) * sizeof(T);
@@ -741,15 +766,15 @@ int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed,
         const uint64_t cnt = npairs - p0 < c.concurrent ? npairs - p0 : c.concurrent;
         prof_begin(prof, K_NTT_FWD_FIRST, s);
         ntt_fwd_first<F><<<dim3(gx1, static_cast<unsigned>(2 * cnt)), kThreads, sm1, s>>>(
-            pairs + p0, one, logN, logR1, spec, stg, tf);
+            pairs + p0, one, logN, logR1, logC1, spec, stg, tf);
         prof_end(prof, s);
         prof_begin(prof, K_NTT_FUSED_LAST, s);
         ntt_fused_last<F><<<dim3(gx2, static_cast<unsigned>(cnt)), kThreads, sm2, s>>>(
-            logN, logR2, spec, stg);
+            logN, logR2, logC2, spec, stg);
         prof_end(prof, s);
         prof_begin(prof, K_NTT_INV_FIRST, s);
         ntt_inv_first<F><<<dim3(gx1, static_cast<unsigned>(cnt)), kThreads, sm1, s>>>(
-            pairs + p0, one, logN, logR1, spec, stg, ti, scale);
+            pairs + p0, one, logN, logR1, logC1, spec, stg, ti, scale);
         prof_end(prof, s);
     }
     PA_CUDA_TRY(cudaGetLastError());
@@ -789,7 +814,10 @@ int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t ma
             } else {
                 t.logR1 = (t.logN + 1) / 2;
                 t.logR2 = t.logN / 2;
-                const int logC1 = elem == 4 ? 3 : 2, logC2 = elem == 4 ? 2 : 1;
+                int logC1 = 0, logC2 = 0;
+                pass_columns(static_cast<int>(t.logN), elem, &logC1, &logC2);
+                t.logC1 = static_cast<uint32_t>(logC1);
+                t.logC2 = static_cast<uint32_t>(logC2);
                 t.g1 = static_cast<uint32_t>((uint64_t(1) << (t.logN - t.logR1)) >> logC1);
                 t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> logC2);
                 big.push_back(t);
@@ -838,7 +866,7 @@ int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t ma
             smem = std::max(smem, (size_t(2) << t.logN) * twsz +
                                       size_t(ColMajor::words(1 << t.logN, 2)) * elem);
         } else {
-            const int logC1 = elem == 4 ? 3 : 2, logC2 = elem == 4 ? 2 : 1;
+            const int logC1 = static_cast<int>(t.logC1), logC2 = static_cast<int>(t.logC2);
             smem = std::max(smem, (size_t(1) << t.logR1) * twsz + (size_t(1) << (t.logR1 + logC1)) * elem);
             smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
                                       size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
