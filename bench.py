@@ -479,12 +479,12 @@ def main():
         return run_reference(args)
 
     import torch
-    import torch.distributed as dist
+
+    from paper_1805_02372_gb300.dist import Group
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=device)
+    group = Group("nccl", rank, world, device=device) if world > 1 else None
 
     blocks, cfg = workload(args.workload)
     runner = Runner(blocks, args.path, device)
@@ -496,8 +496,9 @@ def main():
     in_bytes = sum(8 * (len(k) + len(s)) for k, s in zip(runner.keys_h, runner.seeds_h))
     flush = in_bytes < 2 * L2_BYTES
     scratch = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=device) if flush else None
-    if world > 1:
-        dist.barrier()
+    if group:
+        group.checked_barrier("timed")
+        torch.distributed.barrier()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         ms = timed(runner, args.steps, flush, stream, scratch)   # graph replay, no tracing
@@ -506,11 +507,9 @@ def main():
         runner.profile(True)
         ms_traced = timed(runner, args.steps, flush, stream, scratch)
         runner.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    if group:
+        ms = group.max(ms)   # the job's step time is the slowest rank's
+        torch.distributed.barrier()
     kt = runner.kernel_times()
     exact = check_sampled(runner)
     clocks = clk.summary()
@@ -555,8 +554,8 @@ def main():
                                 "sample": desc}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    if group:
+        group.close()
 
 
 if __name__ == "__main__":

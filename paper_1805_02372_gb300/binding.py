@@ -131,6 +131,7 @@ SIGNATURES = {
     "pa_server_pending": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64)]),
     "pa_server_destroy": (None, [_VP]),
+    "pa_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_last_cuda_error": (ctypes.c_int, []),
     "pa_version": (ctypes.c_int, []),
@@ -384,6 +385,13 @@ def pa_server_pending(server: int) -> tuple[int, int]:
 
 def pa_server_destroy(server: int) -> None:
     load().pa_server_destroy(server)
+
+
+def pa_selftest(which: int) -> int:
+    """Device status after a deliberately unsatisfiable bounded wait (expect PA_ERR_TIMEOUT)."""
+    st = ctypes.c_int()
+    _check(load().pa_selftest(which, ctypes.byref(st)), "pa_selftest")
+    return st.value
 
 
 def pa_strerror(status: int) -> str:

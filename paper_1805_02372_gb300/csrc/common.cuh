@@ -74,6 +74,41 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
     return false;
 }
 
+// ---- counters between CTAs of one launch ----
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_count(const uint32_t *c, uint32_t target, int *status, int *flag) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint32_t it = 0;
+        while (ld_acquire(c) < target) {
+            if (++it > kSpinLimit) {
+                set_status(status, PA_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+__device__ __forceinline__ void signal_count(uint32_t *c) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(c, 1u);
+    }
+}
+
 // ---- bit helpers ----
 
 __device__ __forceinline__ uint64_t ceil_div_dev(uint64_t a, uint64_t b) { return (a + b - 1) / b; }

@@ -496,39 +496,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_inv_first(const T
 // already claimed by running CTAs, so every wait ends. Waits are bounded anyway: on
 // timeout the status word gets PA_ERR_TIMEOUT and the item is skipped.
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ bool wait_count(const uint32_t *c, uint32_t target, int *status, int *flag) {
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        uint32_t it = 0;
-        while (ld_acquire(c) < target) {
-            if (++it > kSpinLimit) {
-                set_status(status, PA_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        *flag = ok;
-    }
-    __syncthreads();
-    return *flag != 0;
-}
-
-__device__ __forceinline__ void signal_count(uint32_t *c) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(c, 1u);
-    }
-}
-
 template <class F>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
     const uint64_t *__restrict__ items, uint32_t nitems, const NttTile *__restrict__ tiles,
