@@ -28,14 +28,15 @@ class Group:
     def __init__(self, backend: str, rank: int, world: int, timeout_s: float = 60.0,
                  device=None):
         import torch.distributed as dist
+        from torch.distributed import distributed_c10d as c10d
         self.dist, self.rank, self.world, self.device = dist, rank, world, device
-        host = os.environ.get("MASTER_ADDR", "127.0.0.1")
-        port = int(os.environ.get("MASTER_PORT", "29500"))
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         td = datetime.timedelta(seconds=timeout_s)
-        self.store = dist.TCPStore(host, port, world, rank == 0, td)
         kw = {"device_id": device} if (backend == "nccl" and device is not None) else {}
-        dist.init_process_group(backend, store=self.store, rank=rank, world_size=world,
+        # env:// works both under torchrun (its agent hosts the store) and plain env vars
+        dist.init_process_group(backend, init_method="env://", rank=rank, world_size=world,
                                 timeout=td, **kw)
+        self.store = c10d._get_default_store()
 
     def _tensor(self, x):
         import torch
