@@ -358,42 +358,42 @@ def traffic_for(kernel: str):
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_gbps(blocks, budget_s: float = 12.0, seed: int = 3):
-    """The oracle as it stands on a bounded uniform sample of output rows of the workload.
+def cpu_oracle_gbps(blocks, rows_per_block: int = 1024, seed: int = 3, max_blocks: int = 256):
+    """The oracle as it stands (all host cores), timed on a bounded sample of each block.
 
-    Rows are drawn uniformly over all sum(m) rows; the full-job time is the sample time
-    scaled by sum(m) / rows. Returns (Gbps, cores, description)."""
+    The oracle's full hash of a block is one set-up (seed reversal, key masking) plus m row
+    evaluations spread over the cores. Per block it is timed on R/4 and on R rows: the
+    difference gives the per-row cost (set-up and thread start cancel), the full-block
+    time is set-up + m x per-row, summed over the blocks (a uniform sample of at most
+    max_blocks of them, scaled up). Returns (Gbps, cores, description)."""
     import oracle
     rng = np.random.default_rng(seed)
-    total_m = sum(b.m for b in blocks)
-    avg_n = sum(b.n * b.m for b in blocks) / total_m
-    # calibrate: oracle row cost ~ n/64 word ops; start small, grow to the budget
-    rows_total = max(8, int(2000 * 1e6 / avg_n))
-    spent, done_rows, elapsed = 0.0, 0, 0.0
-    keys = {}
-    while spent < budget_s:
-        pick = rng.integers(0, total_m, rows_total)
-        edges = np.cumsum([0] + [b.m for b in blocks])
-        which = np.searchsorted(edges, pick, side="right") - 1
+    idx = np.arange(len(blocks))
+    if len(idx) > max_blocks:
+        idx = rng.choice(idx, max_blocks, replace=False)
+    est, measured = 0.0, 0.0
+    for i in idx:
+        b = blocks[i]
+        k, s = b.key(), b.seed()
+        # about 2e10 bit products per block sampled (bounded CPU time), at least R rows
+        r = max(8, min(b.m, max(rows_per_block, int(2e10 / b.n / len(idx)))))
+        r1 = max(1, r // 4)
+        rows = rng.integers(0, b.m, r)
         t0 = time.perf_counter()
-        for bi in np.unique(which):
-            b = blocks[bi]
-            if bi not in keys:
-                keys[bi] = (b.key(), b.seed())
-            k, s = keys[bi]
-            rows = pick[which == bi] - edges[bi]
-            oracle.hash_rows(b.n, b.m, s, k, rows)
-        dt = time.perf_counter() - t0
-        spent += dt
-        elapsed += dt
-        done_rows += rows_total
-        if dt < budget_s / 8:
-            rows_total *= 4
-    full_s = elapsed * total_m / done_rows
-    gbps = sum(b.n for b in blocks) / full_s / 1e9
+        oracle.hash_rows(b.n, b.m, s, k, rows[:r1])
+        t1 = time.perf_counter()
+        oracle.hash_rows(b.n, b.m, s, k, rows)
+        t2 = time.perf_counter()
+        per_row = max((t2 - t1) - (t1 - t0), 0.0) / (r - r1)
+        setup = max((t1 - t0) - per_row * r1, 0.0)
+        est += setup + per_row * b.m
+        measured += t2 - t0
+    est *= len(blocks) / len(idx)
+    gbps = sum(b.n for b in blocks) / est / 1e9
     cores = os.cpu_count() or 1
-    return gbps, cores, (f"{done_rows} output rows drawn uniformly from the workload's "
-                         f"{total_m} rows ({elapsed:.1f} s), scaled by sum(m)/rows")
+    return gbps, cores, (f"{len(idx)} of {len(blocks)} blocks, each timed on R/4 and R >= "
+                         f"{rows_per_block} uniformly drawn output rows ({measured:.1f} s "
+                         f"measured); full-block time = set-up + m x per-row time")
 
 
 # --------------------------------------------------------------------------- main
@@ -403,16 +403,48 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+# Table 1 of the paper: n = 4..128 Mbit, l = 10% of n, TITAN Xp FP32 (context only).
+TABLE1_PAPER_GBPS = {4: 1.25, 8: 1.33, 16: 1.37, 32: 1.38, 64: 1.38, 128: 1.35}
+
+
+def run_table1(args):
+    """Table 1 shapes on this GPU: one block per size, m = floor(0.1 n), AUTO path."""
+    import torch
+    from paper_1805_02372_gb300 import inputs
+    device = torch.device("cuda", 0)
+    rows = []
+    for mbit, paper in TABLE1_PAPER_GBPS.items():
+        n = mbit * 1_000_000
+        b = inputs.single_block(n, n // 10, 10 + mbit, 11 + mbit)
+        r = Runner([b], args.path, device)
+        for _ in range(args.warmup):
+            r.step()
+        ms = timed(r, args.steps, False, r.stream, None)
+        exact = check_sampled(r, rows_per_block=32)
+        rows.append({"n_mbit": mbit, "m": b.m, "gbps": n / (ms * 1e-3) / 1e9, "ms": ms,
+                     "path": r.plan_desc[0]["path_name"], "bit_exact_sampled": exact,
+                     "paper_titan_xp_gbps": paper})
+        del r
+    val = float(np.mean([x["gbps"] for x in rows]))
+    print(json.dumps({"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                      "data": "synthetic",
+                      "config": {"workload": "Table 1 shapes: n = 4..128 Mbit, l = 10% n, "
+                                             "one block each (mean Gbps over sizes)"},
+                      "sizes": rows}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     blocks, cfg = workload(args.workload)
     per_step = []
-    for _ in range(args.warmup):
-        cpu_oracle_gbps(blocks, budget_s=2.0)
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_gbps(blocks, rows_per_block=64, max_blocks=8)
     for k in range(args.steps):
-        g, cores, desc = cpu_oracle_gbps(blocks, budget_s=8.0, seed=100 + k)
+        g, cores, desc = cpu_oracle_gbps(blocks, seed=100 + k, max_blocks=64)
         per_step.append(g)
     val = float(np.mean(per_step))
     total_bits = sum(b.n for b in blocks)
@@ -477,6 +509,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "table1":
+        return run_table1(args)
 
     import torch
 
