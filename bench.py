@@ -240,10 +240,6 @@ KERNEL_SOURCES = {
     "direct": [CSRC + "direct.cu", CSRC + "common.cuh"],
     "batch_persistent": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh",
                          CSRC + "tiles.cuh", CSRC + "common.cuh"],
-    "ntt_fwd_first": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh"],
-    "ntt_fused_last": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh"],
-    "ntt_inv_first": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh"],
-    "ntt_small": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh"],
     "fft_tile": [CSRC + "fft.cu", CSRC + "dft.cuh", CSRC + "tiles.cuh"],
     "block_mma": [CSRC + "block.cu", CSRC + "common.cuh"],
 }
@@ -252,28 +248,22 @@ CLOCK_HZ = 2070e6
 SMS = 152
 
 
-def _ntt_ops(descs, kernel):
-    """8 integer ops per butterfly; a tile of size N costs 3 (N/2) log2 N + N/2 butterflies
-    (two forward transforms, one inverse, the pointwise product)."""
+def _ntt_ops(descs):
+    """8 integer ops per butterfly. A standard tile pair of size N costs 3 (N/2) log2 N + N/2
+    butterflies (two forward transforms, one inverse, the pointwise product); a block under
+    transform-domain accumulation costs (Q + W + P) (N/2) log2 N for its Q key, W window and
+    P output transforms plus P Q N products summed."""
     ops = 0.0
     for d in descs:
         if d["path_name"] not in ("ntt31", "ntt64"):
             continue
         k = d["log2_transform"]
         N = 2.0 ** k
-        tiles = d["tiles_in"] * d["tiles_out"]
-        if kernel == "ntt_small" and k > 12:
-            continue
-        if kernel in ("ntt_fwd_first", "ntt_fused_last", "ntt_inv_first") and k <= 12:
-            continue
-        per_tile = 3 * (N / 2) * k + N / 2
-        if kernel == "ntt_fwd_first":
-            per_tile = 2 * (N / 2) * ((k + 1) // 2)
-        elif kernel == "ntt_fused_last":
-            per_tile = 3 * (N / 2) * (k // 2) + N / 2
-        elif kernel == "ntt_inv_first":
-            per_tile = (N / 2) * ((k + 1) // 2)
-        ops += 8.0 * tiles * per_tile
+        P, Q = d["tiles_out"], d["tiles_in"]
+        if d.get("fd"):
+            ops += 8.0 * ((Q + d["windows"] + P) * (N / 2) * k + P * Q * N)
+        else:
+            ops += 8.0 * P * Q * (3 * (N / 2) * k + N / 2)
     return ops
 
 
@@ -286,9 +276,8 @@ def algorithmic(kernel: str, blocks, descs):
         ops = sum(2.0 * b.m * b.n / 32.0 for b, d in zip(blocks, descs)
                   if d["path_name"] == "direct")
         return "alu", ops, "Tops/s", int_alu, "derived: 152 SM x 64 INT32 lanes x 2070 MHz"
-    if kernel in ("batch_persistent", "ntt_small", "ntt_fwd_first", "ntt_fused_last",
-                  "ntt_inv_first"):
-        return ("alu", _ntt_ops(descs, kernel), "Tops/s", int_all,
+    if kernel == "batch_persistent":
+        return ("alu", _ntt_ops(descs), "Tops/s", int_all,
                 "derived: 152 SM x (64 ALU + 64 FMA-pipe IMAD) lanes x 2070 MHz")
     if kernel == "block_mma":
         ops = sum(2.0 * b.m * (b.n + 8192) for b, d in zip(blocks, descs)

@@ -70,7 +70,12 @@ typedef struct {
     uint32_t force_fp64;       /* FFT path: use FP64 butterflies even where FP32 is proven */
     uint32_t max_slots;        /* batches: at most this many transform spectra resident at
                                   once (reused round-robin, >= 4); 0 = automatic         */
-    uint32_t reserved[6];
+    uint32_t fd_mode;          /* NTT paths with several key and output sub-blocks: sum the
+                                  products of an output sub-block in the transform domain
+                                  (each key and seed-window spectrum computed once, one
+                                  inverse per output sub-block). 0 = when the planner
+                                  estimates it faster, 1 = never, 2 = whenever possible   */
+    uint32_t reserved[5];
 } pa_opts;
 
 /* What a plan decided (pa_plan_query / pa_plan_describe). */
@@ -87,7 +92,9 @@ typedef struct {
     double rounding_bound;     /* FFT path: proven bound on |v - rint(v)|, else 0         */
     uint64_t workspace_bytes;  /* device workspace owned by the plan                      */
     uint32_t kernels_per_call; /* kernel launches one pa_hash enqueues                    */
-    uint32_t reserved[5];
+    uint32_t fd;               /* NTT: transform-domain accumulation (see pa_opts.fd_mode) */
+    uint64_t windows;          /* with fd: seed-window spectra computed (distinct offsets) */
+    uint32_t reserved[2];
 } pa_plan_desc;
 
 typedef struct pa_plan_s *pa_plan_t;

@@ -40,7 +40,7 @@ class pa_opts(ctypes.Structure):
                 ("log2_transform", ctypes.c_uint32), ("block_b", ctypes.c_uint32),
                 ("tile_in", ctypes.c_uint64), ("tile_out", ctypes.c_uint64),
                 ("force_fp64", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("fd_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 class pa_plan_desc(ctypes.Structure):
@@ -50,7 +50,8 @@ class pa_plan_desc(ctypes.Structure):
                 ("tiles_out", ctypes.c_uint64), ("block_b", ctypes.c_uint32),
                 ("fp64", ctypes.c_uint32), ("rounding_bound", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_uint64), ("kernels_per_call", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("fd", ctypes.c_uint32), ("windows", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint32 * 2)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -200,13 +201,13 @@ def _stream(s) -> int | None:
 
 
 def make_opts(path=PA_PATH_AUTO, device=-1, log2_transform=0, block_b=0, tile_in=0,
-              tile_out=0, force_fp64=0, max_slots=0) -> pa_opts:
+              tile_out=0, force_fp64=0, max_slots=0, fd_mode=0) -> pa_opts:
     if isinstance(path, str):
         path = PATHS[path]
     o = pa_opts()
     o.path, o.device, o.log2_transform, o.block_b = path, device, log2_transform, block_b
     o.tile_in, o.tile_out, o.force_fp64 = tile_in, tile_out, force_fp64
-    o.max_slots = max_slots
+    o.max_slots, o.fd_mode = max_slots, fd_mode
     return o
 
 

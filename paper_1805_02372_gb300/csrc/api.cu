@@ -47,11 +47,9 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
         case PA_PATH_NTT64:
         case PA_PATH_NTT31:
             rc = ntt_plan(n, m, path, o, &cfg->tr);
-            cfg->ws_bytes = ntt_workspace(path, cfg->tr);
-            cfg->kernels = cfg->tr.passes == 1
-                               ? 1
-                               : 3 * static_cast<uint32_t>(ceil_div(
-                                         cfg->tr.tiles_in * cfg->tr.tiles_out, cfg->tr.concurrent));
+            if (rc == PA_OK) rc = ntt_layout(n, m, path, &cfg->tr);
+            cfg->ws_bytes = cfg->tr.lay.bytes;
+            cfg->kernels = 2;  // output zeroing + the persistent launch
             break;
         case PA_PATH_FFT:
             rc = fft_plan(n, m, o, &cfg->tr);
@@ -91,6 +89,8 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->tiles_out = cfg.tr.tiles_out;
         d->fp64 = cfg.tr.fp64;
         d->rounding_bound = cfg.tr.bound;
+        d->fd = cfg.tr.fd;
+        d->windows = cfg.tr.windows;
     }
 }
 

@@ -147,11 +147,13 @@ int calibrate(Tuner *t) {
             o.log2_transform = static_cast<uint32_t>(k);
             o.tile_out = M;
             o.tile_in = L;
+            o.fd_mode = 1;  // calibrate standard pairs
             const double tt = tplan(L * tiles, M, o, &cfg);
             t->ntt[f][k] = tt / double(cfg.tr.tiles_in * cfg.tr.tiles_out);
         }
         o.log2_transform = 0;
         o.tile_in = o.tile_out = 0;
+        o.fd_mode = 0;
     }
     cudaStreamSynchronize(s);
     cudaFree(key);
@@ -252,12 +254,15 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 if (M == 0 || M + 32 > N) continue;
                 uint64_t L = ((N - M) / 32) * 32;
                 if (L > round_up(n, 32)) L = round_up(n, 32);
-                const double pairs = double(ceil_div(n, L)) * double(ceil_div(m, M));
-                const double launches = batched ? 0.0 : (k > 12 ? 3.0 : 1.0);
+                uint32_t fd = 0;
+                uint64_t windows = 0;
+                const double units = ntt_geometry_cost(n, m, o.path, static_cast<uint32_t>(k), M, L,
+                                                       0, &fd, &windows);
+                const double launches = batched ? 0.0 : 2.0;
                 o.log2_transform = static_cast<uint32_t>(k);
                 o.tile_out = M;
                 o.tile_in = L;
-                consider(pairs * t.ntt[f][k] + (launches + 1) * t.launch, o);
+                consider(units * t.ntt[f][k] + launches * t.launch, o);
             }
         }
         o.log2_transform = 0;

@@ -24,6 +24,17 @@ struct DirectCfg {
 };
 
 // ---- transform paths (NTT over a prime field, FP FFT) ----
+// Workspace layout and launch shape of one persistent NTT launch (see ntt.cu).
+struct NttLayout {
+    int field = 0;         // 0: 31-bit prime, 1: 64-bit prime
+    uint64_t ntiles = 0, nitems = 0, nfd = 0;
+    uint32_t slots = 1;    // spectra slots of standard tiles, reused round-robin
+    size_t smem = 0;
+    size_t off_tiles = 0, off_items = 0, off_fd = 0, off_wmap = 0, off_counters = 0;
+    size_t counter_bytes = 0, off_spec = 0;
+    size_t bytes = 0;      // workspace bytes
+};
+
 struct TransformCfg {
     uint32_t log2n = 0;          // transform size N = 2^log2n
     uint64_t L = 0, M = 0;       // key tile and output tile lengths
@@ -33,7 +44,9 @@ struct TransformCfg {
     uint32_t radix_log2[4] = {0, 0, 0, 0};
     uint32_t fp64 = 0;           // FFT: FP64 butterflies
     double bound = 0.0;          // FFT: proven rounding bound
-    uint32_t concurrent = 0;     // tiles processed per launch wave
+    uint32_t fd = 0;             // NTT: transform-domain accumulation over key tiles
+    uint64_t windows = 0;        // NTT with fd: distinct seed-window spectra
+    NttLayout lay;               // NTT single-block plans: their persistent launch
 };
 
 // ---- block-Toeplitz tensor-core path ----
@@ -74,12 +87,6 @@ constexpr size_t kHeaderBytes = 256;
 enum KernelId {
     K_REVERSE_KEY = 0,
     K_DIRECT,
-    K_NTT_FWD_FIRST,
-    K_NTT_FWD_MID,
-    K_NTT_FUSED_LAST,
-    K_NTT_INV_MID,
-    K_NTT_INV_FIRST,
-    K_NTT_SMALL,
     K_FFT_TILE,
     K_BLOCK_MMA,
     K_BATCH_PERSISTENT,
@@ -115,8 +122,13 @@ int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, cons
                   const uint64_t *key, uint64_t *out, cudaStream_t s);
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c);
-size_t ntt_workspace(int path, const TransformCfg &c);
-int ntt_init(const PlanCfg &cfg, void *ws);  // uploads tile descriptors, builds root tables
+// Modelled cost of a tile geometry in units of one standard tile pair of size 2^k
+// (+inf if invalid); *fd / *windows: whether transform-domain accumulation is used.
+double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t M, uint64_t L,
+                         uint32_t fd_mode, uint32_t *fd, uint64_t *windows);
+// Lays out the single-block plan's persistent launch (fills c->lay; host only).
+int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c);
+int ntt_init(const PlanCfg &cfg, void *ws);  // uploads the work list, builds root tables
 int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                const uint64_t *key, uint64_t *out, cudaStream_t s);
 
@@ -137,15 +149,10 @@ struct BatchBlock {
     uint64_t n, m;
     TransformCfg tr;
 };
-struct NttBatchInfo {
-    int field = 0;         // 0: 31-bit prime, 1: 64-bit prime
-    uint64_t ntiles = 0, nitems = 0;
-    uint32_t slots = 1;    // spectra slots reused round-robin
-    size_t smem = 0;
-    size_t off_tiles = 0, off_items = 0, off_counters = 0, counter_bytes = 0, off_spec = 0;
-    size_t bytes = 0;      // workspace bytes
-    std::vector<unsigned char> host_tiles;
+struct NttBatchInfo : NttLayout {
+    std::vector<unsigned char> host_tiles, host_fd;
     std::vector<uint64_t> host_items;
+    std::vector<uint32_t> host_wmap;
 };
 int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
                     NttBatchInfo *info);

@@ -6,24 +6,42 @@
 // [j0, j0+L) (L a multiple of 32, M of 64). With a[t] = x[j0+t] and the seed window
 // w[u] = s[n-1+i0-j0-L+u] (positions outside the seed read as 0), output row i0+v
 // receives coefficient L+v of the linear convolution a*w, and a cyclic convolution
-// of size N >= L+M gives those coefficients unaliased. The tile's bits are XORed into
-// the output (Eq. finalkey).
+// of size N >= L+M gives those coefficients unaliased.
+//
+// Combining tiles, two ways:
+//   standard: each (output tile, key tile) pair is one cyclic convolution (forward
+//     transforms of both inputs, pointwise product, inverse) whose bits are XORed into
+//     the output (Eq. finalkey).
+//   transform-domain accumulation (fd): the window depends on the pair only through
+//     the offset d = i0 - j0, so each key-tile spectrum X_J and each distinct window
+//     spectrum W_d is computed once; output tile I is the inverse of
+//     Z_I = sum_J X_J * W_{d(I,J)}. Its coefficients are sums of at most n bit products,
+//     below p, so the residue is the integer and its low bit is the XOR over key tiles.
+//     With L = M the offsets take P + Q - 1 values: Q + (P + Q - 1) forward transforms
+//     and P inverses replace 3 P Q transforms.
 //
 // Transforms. N = R1*R2 (a four-step split; R1, R2 <= 2^11) or N <= 2^12 in one CTA.
 // Forward: decimation in frequency, natural input, bit-reversed spectrum; inverse:
 // decimation in time from the bit-reversed spectrum, so no permutation pass exists.
-// Each CTA does R-point transforms on columns in shared memory, two radix-2 stages
-// per shared-memory round trip (radix-4 groups in registers).
-//   ntt_fwd_first : pass 1 (stride R2) on the key tile and the seed window, read
-//                   straight from the packed bits, then the four-step twiddles.
-//   ntt_fused_last: pass 2 (contiguous rows of R2) of both spectra, the pointwise
-//                   product, and inverse pass 2.
-//   ntt_inv_first : twiddles, inverse pass 1, scale by N^-1, take bit 0, XOR the
-//                   tile's output bytes into the packed output.
-//   ntt_small     : N <= 2^12: all of the above in one CTA per tile.
+// A CTA does R-point transforms on columns in shared memory, four radix-2 stages per
+// shared-memory round trip (radix-16 groups in registers).
+//
+// Everything runs in ONE persistent launch (single blocks and batches alike): CTAs
+// pull work items from a list; an item depends only on items before it in the list.
+//   small  (N <= 2^12): a whole tile pair in one CTA.
+//   P1     : forward pass 1 (stride R2) of a key tile or window read straight from the
+//            packed bits, then the four-step twiddles.
+//   P2     : forward pass 2 (contiguous rows of R2) of both spectra of a pair, the
+//            pointwise product and the inverse pass 2.
+//   P3     : twiddles, inverse pass 1, scale by N^-1, low bit, XOR of output bytes.
+//   FD P1 / FD P2: the two forward passes of one fd spectrum (pass 2 in place).
+//   FD SUM : Z_I rows = sum over key tiles of the products, then inverse pass 2.
+//   FD P3  : P3 on Z_I.
+#include <math.h>
+#include <stdio.h>
+
 #include <algorithm>
 #include <mutex>
-#include <stdio.h>
 #include <string.h>
 #include <vector>
 
@@ -41,17 +59,47 @@ constexpr int kThreads = 512;
 template <class F>
 constexpr int kMinBlocks = sizeof(typename F::T) == 4 ? 2 : 1;
 
-// A transform tile of a batch: geometry plus its transform shape and spectra slot.
+// Transform-domain accumulation limits: tile pairs of one block (host tables) and
+// spectra bytes of one block.
+constexpr uint64_t kFdMaxPairs = uint64_t(1) << 22;
+constexpr uint64_t kFdMaxBytes = uint64_t(32) << 30;
+
+// Work-item types (bits 60..63 of an item; bits 32..59 tile index, 0..31 sub-index).
+enum : uint32_t {
+    IT_SMALL = 0,
+    IT_P1 = 1,
+    IT_P2 = 2,
+    IT_P3 = 3,
+    IT_FD_P1 = 4,
+    IT_FD_P2 = 5,
+    IT_FD_SUM = 6,
+    IT_FD_P3 = 7
+};
+
+// A transform of a launch: a standard tile pair, an fd spectrum or an fd output sum.
 struct NttTile {
-    TilePair p;
-    uint64_t ws_off;  // element offset of the key spectrum (window spectrum follows)
+    TilePair p;       // geometry (fd key spectrum: its key tile; window: a pair with
+                      // that offset; output sum: the pair (I, 0))
+    uint64_t ws_off;  // element offset of the spectrum (standard: the key spectrum, the
+                      // window spectrum follows)
     uint64_t scale;   // final scale as the bits of F::Tw
     uint32_t logN, logR1, logR2;
     uint32_t g1;      // pass-1 column groups (per input)
     uint32_t g2;      // pass-2 row groups
     uint32_t logC1;   // pass-1/3 columns per item (log2)
     uint32_t logC2;   // pass-2 rows per item (log2)
-    uint32_t pad;
+    uint32_t which;   // fd spectra: 0 key tile, 1 seed window
+    uint32_t fd;      // fd spectra and sums: index of the fd block
+    uint32_t out;     // fd sums: output tile index I
+};
+
+// One block under transform-domain accumulation.
+struct FdBlock {
+    uint64_t x_off;   // element offset of key spectrum 0 (key spectra at stride N)
+    uint64_t w_off;   // element offset of window spectrum 0 (stride N)
+    uint64_t wmap;    // first entry of the block's P x Q window-index table
+    uint32_t Q;       // key tiles
+    uint32_t nfwd2;   // forward pass-2 items of the block (all precede every sum)
 };
 
 // Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
@@ -420,94 +468,119 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- standalone kernels
-
+// Forward pass 2 of one fd spectrum in place: C = 2^logC rows of R2 = 2^logR2 from row
+// group rg.
 template <class F>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_small(const TilePair *__restrict__ pairs, BlockPtrs bp,
-                                                      int logN,
-                                                      const typename F::Tw *__restrict__ stage,
-                                                      typename F::Tw scale) {
-    using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Tw *stf = reinterpret_cast<Tw *>(smraw);
-    Tw *sti = stf + (1 << logN);
-    const TilePair pr = pairs[blockIdx.x];
-    load_stage<F>(stf, stage, 0, logN);
-    load_stage<F>(sti, stage, 1, logN);
-    body_small<F>(reinterpret_cast<typename F::T *>(sti + (1 << logN)), stf, sti, pr, bp, logN, scale);
+__device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint64_t rg, int logR2,
+                              int logC, typename F::T *__restrict__ A) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
+        const T *xs = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+    }
+    __syncthreads();
+    dif_columns<F, false>(sm, lay, logR2, logC, stf);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(A + base + e), ov);
+    }
+    __syncthreads();
 }
 
+// Rows of Z_I from row group rg: Z_I = sum over the Q key tiles J of X_J * W_{wrow[J]}
+// (Montgomery products summed in the field), then the inverse pass 2, written to Z.
+// A 512-thread CTA covers a row group in at most kSumVec vectors of 16 bytes per thread.
+constexpr int kSumVec = 4;
 template <class F>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fwd_first(const TilePair *__restrict__ pairs,
-                                                          BlockPtrs bp, int logN, int logR1, int logC,
-                                                          typename F::T *__restrict__ ws,
-                                                          const typename F::Tw *__restrict__ stage,
-                                                          const typename F::Tw *__restrict__ tfwd) {
-    using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Tw *st = reinterpret_cast<Tw *>(smraw);
-    const int which = blockIdx.y & 1;
-    const uint32_t pi = blockIdx.y >> 1;
-    const TilePair pr = pairs[pi];
-    typename F::T *dst = ws + (uint64_t(pi) * 2 + which) * (uint64_t(1) << logN);
-    load_stage<F>(st, stage, 0, logR1);
-    body_fwd_first<F>(reinterpret_cast<typename F::T *>(st + (1 << logR1)), st, pr, bp, which,
-                      blockIdx.x, logN, logR1, logC, dst, tfwd);
+__device__ void body_sum_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
+                                  int logR2, int logC, const typename F::T *__restrict__ X,
+                                  const typename F::T *__restrict__ W,
+                                  const uint32_t *__restrict__ wrow, uint32_t Q, uint64_t N,
+                                  typename F::T *__restrict__ Z) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    T acc[kSumVec][V];
+#pragma unroll
+    for (int q = 0; q < kSumVec; ++q)
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[q][k] = 0;
+    for (uint32_t J = 0; J < Q; ++J) {
+        const T *xj = X + uint64_t(J) * N + base;
+        const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
+#pragma unroll
+        for (int q = 0; q < kSumVec; ++q) {
+            const int e = (threadIdx.x + q * blockDim.x) * V;
+            if (e < cnt) {
+                const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
+                const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
+                const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[q][k] = F::add(acc[q][k], F::mont(xs[k], ws[k]));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSumVec; ++q) {
+        const int e = (threadIdx.x + q * blockDim.x) * V;
+        if (e < cnt) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+#pragma unroll
+            for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = acc[q][k];
+        }
+    }
+    __syncthreads();
+    dit_columns<F, false>(sm, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(Z + base + e), ov);
+    }
+    __syncthreads();
 }
 
-template <class F>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_fused_last(int logN, int logR2, int logC,
-                                                           typename F::T *__restrict__ ws,
-                                                           const typename F::Tw *__restrict__ stage) {
-    using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Tw *stf = reinterpret_cast<Tw *>(smraw);
-    Tw *sti = stf + (1 << logR2);
-    typename F::T *X = ws + (uint64_t(blockIdx.y) * 2) * (uint64_t(1) << logN);
-    load_stage<F>(stf, stage, 0, logR2);
-    load_stage<F>(sti, stage, 1, logR2);
-    body_fused_last<F>(reinterpret_cast<typename F::T *>(sti + (1 << logR2)), stf, sti, blockIdx.x,
-                       logR2, logC, X, X + (uint64_t(1) << logN));
-}
-
-template <class F>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_inv_first(const TilePair *__restrict__ pairs,
-                                                          BlockPtrs bp, int logN, int logR1, int logC,
-                                                          const typename F::T *__restrict__ ws,
-                                                          const typename F::Tw *__restrict__ stage,
-                                                          const typename F::Tw *__restrict__ tinv,
-                                                          typename F::Tw scale) {
-    using Tw = typename F::Tw;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Tw *st = reinterpret_cast<Tw *>(smraw);
-    const uint32_t pi = blockIdx.y;
-    const TilePair pr = pairs[pi];
-    const typename F::T *src = ws + (uint64_t(pi) * 2 + 1) * (uint64_t(1) << logN);
-    load_stage<F>(st, stage, 1, logR1);
-    body_inv_first<F>(reinterpret_cast<typename F::T *>(st + (1 << logR1)), st, pr, bp, blockIdx.x,
-                      logN, logR1, logC, src, tinv, scale);
-}
-
-// ---------------------------------------------------------------- persistent batched kernel
+// ---------------------------------------------------------------- the persistent kernel
 //
-// One launch runs the transform tiles of every block of a batch. CTAs pull items from
-// a work list with an atomic counter; the list is ordered so that each item depends
-// only on items before it (pass 1 -> pass 2 -> pass 3 of the same tile), which are
-// already claimed by running CTAs, so every wait ends. Waits are bounded anyway: on
-// timeout the status word gets PA_ERR_TIMEOUT and the item is skipped.
+// CTAs pull items from the list with an atomic counter; the list is ordered so that
+// each item depends only on items before it, which are already claimed by running
+// CTAs, so every wait ends. Waits are bounded anyway: on timeout the status word gets
+// PA_ERR_TIMEOUT and the item's body is skipped.
+// Counters: c1/c2/c3 per tile (pass 1, 2, 3 items done), then the list position, then
+// one per fd block (forward pass-2 items done).
 
 template <class F>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
     const uint64_t *__restrict__ items, uint32_t nitems, const NttTile *__restrict__ tiles,
-    const BlockPtrs *__restrict__ blks, typename F::T *__restrict__ ws,
+    const FdBlock *__restrict__ fds, const uint32_t *__restrict__ wmap,
+    const BlockPtrs *__restrict__ blks, BlockPtrs one, typename F::T *__restrict__ ws,
     const typename F::Tw *__restrict__ stage, const typename F::Tw *__restrict__ tfwd,
-    const typename F::Tw *__restrict__ tinv, uint32_t *c1, uint32_t *c2, uint32_t *c3,
-    uint32_t slots, uint32_t *next, int *status) {
+    const typename F::Tw *__restrict__ tinv, uint32_t *cnt, uint32_t ntiles, uint32_t slots,
+    int *status) {
     using T = typename F::T;
     using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint64_t cur;
     __shared__ int flag;
+    uint32_t *c1 = cnt, *c2 = cnt + ntiles, *c3 = cnt + 2 * uint64_t(ntiles);
+    uint32_t *next = cnt + 3 * uint64_t(ntiles), *cfd = next + 1;
     Tw *st0 = reinterpret_cast<Tw *>(smraw);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -518,47 +591,89 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
         const uint64_t it = cur;
         __syncthreads();
         if (it == ~0ull) break;
-        const uint32_t type = static_cast<uint32_t>(it >> 62);
-        const uint32_t ti = static_cast<uint32_t>((it >> 32) & 0x3FFFFFFFu);
+        const uint32_t type = static_cast<uint32_t>(it >> 60);
+        const uint32_t ti = static_cast<uint32_t>((it >> 32) & 0x0FFFFFFFu);
         const uint32_t sub = static_cast<uint32_t>(it);
         const NttTile tl = tiles[ti];
-        const BlockPtrs bp = blks[tl.p.blk];
+        const BlockPtrs bp = pick(blks, one, tl.p.blk);
         Tw scale;
         memcpy(&scale, &tl.scale, sizeof(Tw));
         const int logN = static_cast<int>(tl.logN);
         const int logR1 = static_cast<int>(tl.logR1), logR2 = static_cast<int>(tl.logR2);
+        const int logC1 = static_cast<int>(tl.logC1), logC2 = static_cast<int>(tl.logC2);
         T *X = ws + tl.ws_off;
         T *W = X + (uint64_t(1) << logN);
-        if (type == 0) {
-            Tw *sti = st0 + (1 << logN);
-            load_stage<F>(st0, stage, 0, logN);
-            load_stage<F>(sti, stage, 1, logN);
-            body_small<F>(reinterpret_cast<T *>(sti + (1 << logN)), st0, sti, tl.p, bp, logN, scale);
-        } else if (type == 1) {
-            // the spectra slot is reused: wait until the tile `slots` earlier released it
-            bool ok = true;
-            if (ti >= slots) ok = wait_count(c3 + (ti - slots), tiles[ti - slots].g1, status, &flag);
-            const int which = sub >= tl.g1 ? 1 : 0;
-            load_stage<F>(st0, stage, 0, logR1);
-            if (ok)
-                body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, which,
-                                  sub - which * tl.g1, logN, logR1, static_cast<int>(tl.logC1),
-                                  which ? W : X, tfwd);
-            signal_count(c1 + ti);
-        } else if (type == 2) {
-            Tw *sti = st0 + (1 << logR2);
-            load_stage<F>(st0, stage, 0, logR2);
-            load_stage<F>(sti, stage, 1, logR2);
-            if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
-                body_fused_last<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
-                                   static_cast<int>(tl.logC2), X, W);
-            signal_count(c2 + ti);
-        } else {
-            load_stage<F>(st0, stage, 1, logR1);
-            if (wait_count(c2 + ti, tl.g2, status, &flag))
-                body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
-                                  logN, logR1, static_cast<int>(tl.logC1), W, tinv, scale);
-            signal_count(c3 + ti);
+        switch (type) {
+            case IT_SMALL: {
+                Tw *sti = st0 + (1 << logN);
+                load_stage<F>(st0, stage, 0, logN);
+                load_stage<F>(sti, stage, 1, logN);
+                body_small<F>(reinterpret_cast<T *>(sti + (1 << logN)), st0, sti, tl.p, bp, logN, scale);
+                break;
+            }
+            case IT_P1: {
+                // the spectra slot is reused: wait until the tile `slots` earlier released it
+                bool ok = true;
+                if (ti >= slots) ok = wait_count(c3 + (ti - slots), tiles[ti - slots].g1, status, &flag);
+                const int which = sub >= tl.g1 ? 1 : 0;
+                load_stage<F>(st0, stage, 0, logR1);
+                if (ok)
+                    body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, which,
+                                      sub - which * tl.g1, logN, logR1, logC1, which ? W : X, tfwd);
+                signal_count(c1 + ti);
+                break;
+            }
+            case IT_P2: {
+                Tw *sti = st0 + (1 << logR2);
+                load_stage<F>(st0, stage, 0, logR2);
+                load_stage<F>(sti, stage, 1, logR2);
+                if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
+                    body_fused_last<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
+                                       logC2, X, W);
+                signal_count(c2 + ti);
+                break;
+            }
+            case IT_P3: {
+                load_stage<F>(st0, stage, 1, logR1);
+                if (wait_count(c2 + ti, tl.g2, status, &flag))
+                    body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
+                                      logN, logR1, logC1, W, tinv, scale);
+                signal_count(c3 + ti);
+                break;
+            }
+            case IT_FD_P1: {
+                load_stage<F>(st0, stage, 0, logR1);
+                body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp,
+                                  static_cast<int>(tl.which), sub, logN, logR1, logC1, X, tfwd);
+                signal_count(c1 + ti);
+                break;
+            }
+            case IT_FD_P2: {
+                load_stage<F>(st0, stage, 0, logR2);
+                if (wait_count(c1 + ti, tl.g1, status, &flag))
+                    body_fwd_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2, logC2, X);
+                signal_count(cfd + tl.fd);
+                break;
+            }
+            case IT_FD_SUM: {
+                const FdBlock fb = fds[tl.fd];
+                load_stage<F>(st0, stage, 1, logR2);
+                if (wait_count(cfd + tl.fd, fb.nfwd2, status, &flag))
+                    body_sum_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
+                                         logC2, ws + fb.x_off, ws + fb.w_off,
+                                         wmap + fb.wmap + uint64_t(tl.out) * fb.Q, fb.Q,
+                                         uint64_t(1) << logN, X);
+                signal_count(c2 + ti);
+                break;
+            }
+            default: {  // IT_FD_P3
+                load_stage<F>(st0, stage, 1, logR1);
+                if (wait_count(c2 + ti, tl.g2, status, &flag))
+                    body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
+                                      logN, logR1, logC1, X, tinv, scale);
+                __syncthreads();
+                break;
+            }
         }
     }
 }
@@ -569,40 +684,75 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
 
 namespace {
 
-struct Geo {
-    uint32_t logn;
-    uint64_t L, M, pairs;
-};
+// Distinct window offsets I*M - J*L over I < P, J < Q (P*Q if that is no smaller).
+uint64_t count_windows(uint64_t P, uint64_t Q, uint64_t M, uint64_t L) {
+    if (P == 1 || Q == 1) return P * Q;
+    if (L % M == 0 && L / M <= P) return P + (L / M) * (Q - 1);  // M (I - aJ): contiguous
+    if (M % L == 0 && M / L <= Q) return (M / L) * (P - 1) + Q;  // L (bI - J): contiguous
+    if (P * Q > kFdMaxPairs) return P * Q;
+    std::vector<int64_t> d;
+    d.reserve(P * Q);
+    for (uint64_t I = 0; I < P; ++I)
+        for (uint64_t J = 0; J < Q; ++J) d.push_back(int64_t(I * M) - int64_t(J * L));
+    std::sort(d.begin(), d.end());
+    return static_cast<uint64_t>(std::unique(d.begin(), d.end()) - d.begin());
+}
 
-// Tile geometry for transform size 2^logn with output tile M: key tile L = N - M
-// rounded down to 32 bits.
-bool geo_for(uint64_t n, uint64_t m, uint32_t logn, uint64_t M, Geo *g) {
+// Key tile for transform size 2^logn and output tile M: L = N - M rounded down to 32
+// bits (or the forced L), at most the key rounded up to 32 bits; 0 if none fits.
+uint64_t tile_in_for(uint64_t n, uint32_t logn, uint64_t M, uint64_t Lforce) {
     const uint64_t N = uint64_t(1) << logn;
-    if (M == 0 || M >= N) return false;
-    uint64_t L = ((N - M) / 32) * 32;
+    if (M == 0 || M >= N) return 0;
+    uint64_t L = Lforce ? round_up(Lforce, 32) : ((N - M) / 32) * 32;
+    if (L + M > N) return 0;
     const uint64_t Lneed = round_up(n, 32);
-    if (L > Lneed) L = Lneed;
-    if (L == 0) return false;
-    g->logn = logn;
-    g->L = L;
-    g->M = M;
-    g->pairs = ceil_div(n, L) * ceil_div(m, M);
-    return true;
+    if (!Lforce && L > Lneed) L = Lneed;
+    return L;
 }
 
 }  // namespace
 
+// Model: a standard pair costs three transforms plus a fixed per-pair overhead; under
+// transform-domain accumulation each forward spectrum also makes a global round trip
+// between its passes, and each (output, key tile) pair costs reading two spectra.
+double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t M, uint64_t L,
+                         uint32_t fd_mode, uint32_t *fd, uint64_t *windows) {
+    *fd = 0;
+    *windows = 0;
+    if (k > static_cast<uint32_t>(kLogMax) || M == 0 || L == 0 || L + M > (uint64_t(1) << k))
+        return INFINITY;
+    const double N = double(uint64_t(1) << k);
+    const uint64_t P = ceil_div(m, M), Q = ceil_div(n, L);
+    const double pair = N * (k + 6) + 4096.0;
+    const double std_units = double(P) * double(Q);
+    *windows = P * Q;
+    if (k <= static_cast<uint32_t>(kLogSmallMax) || fd_mode == 1 || P * Q < 2 || P * Q > kFdMaxPairs)
+        return std_units;
+    const uint64_t W = count_windows(P, Q, M, L);
+    const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
+    if (double(Q + W + P) * N * elem > double(kFdMaxBytes)) return std_units;
+    const double tr = N * (k + 6) / 3.0;
+    const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(P) * (tr + N + 1024.0) +
+                       double(P) * double(Q) * 3.0 * N;
+    if (fd_mode == 2 || fdc < 0.85 * std_units * pair) {
+        *fd = 1;
+        *windows = W;
+        return fdc / pair;
+    }
+    return std_units;
+}
+
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c) {
     *c = TransformCfg();
-    const int twoadic = path == PA_PATH_NTT31 ? F31::kTwoAdicity : F64::kTwoAdicity;
-    (void)twoadic;
     if (path == PA_PATH_NTT31 && n >= F31::P) return PA_ERR_UNSUPPORTED;  // counts must stay < p
-    Geo best{};
-    double best_cost = 1e300;
-    const uint32_t lo = 5, hi = kLogMax;
+    const uint32_t fd_mode = o ? o->fd_mode : 0;
+    if (fd_mode > 2) return PA_ERR_INVALID;
     const uint32_t force = o ? o->log2_transform : 0;
     const uint64_t Mforce = o ? o->tile_out : 0, Lforce = o ? o->tile_in : 0;
-    for (uint32_t k = lo; k <= hi; ++k) {
+    double best_cost = INFINITY;
+    uint32_t bk = 0, bfd = 0;
+    uint64_t bL = 0, bM = 0, bW = 0;
+    for (uint32_t k = 5; k <= static_cast<uint32_t>(kLogMax); ++k) {
         if (force && k != force) continue;
         const uint64_t N = uint64_t(1) << k;
         uint64_t cands[24];
@@ -615,180 +765,169 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
                 cands[nc++] = round_up(N / f, 64);
         }
         for (int i = 0; i < nc; ++i) {
-            Geo g;
             uint64_t M = cands[i];
             if (M > round_up(m, 64)) M = round_up(m, 64);
-            if (!geo_for(n, m, k, M, &g)) continue;
-            if (Lforce) {
-                const uint64_t L = round_up(Lforce, 32);
-                if (L + M > N) continue;
-                g.L = L;
-                g.pairs = ceil_div(n, L) * ceil_div(m, M);
-            }
-            // cost ~ pairs * (3 transforms of N log N + fixed per-tile overhead)
-            const double cost = double(g.pairs) * (double(N) * (k + 6) + 4096.0);
+            const uint64_t L = tile_in_for(n, k, M, Lforce);
+            if (L == 0) continue;
+            uint32_t fd = 0;
+            uint64_t W = 0;
+            const double units = ntt_geometry_cost(n, m, path, k, M, L, fd_mode, &fd, &W);
+            const double cost = units * (double(N) * (k + 6) + 4096.0);
             if (cost < best_cost) {
                 best_cost = cost;
-                best = g;
+                bk = k;
+                bL = L;
+                bM = M;
+                bfd = fd;
+                bW = W;
             }
         }
     }
-    if (best_cost >= 1e300) return PA_ERR_UNSUPPORTED;
-    c->log2n = best.logn;
-    c->L = best.L;
-    c->M = best.M;
-    c->tiles_in = ceil_div(n, best.L);
-    c->tiles_out = ceil_div(m, best.M);
-    if (best.logn <= kLogSmallMax) {
+    if (!(best_cost < INFINITY)) return PA_ERR_UNSUPPORTED;
+    c->log2n = bk;
+    c->L = bL;
+    c->M = bM;
+    c->tiles_in = ceil_div(n, bL);
+    c->tiles_out = ceil_div(m, bM);
+    c->fd = bfd;
+    c->windows = bfd ? bW : 0;
+    if (bk <= static_cast<uint32_t>(kLogSmallMax)) {
         c->passes = 1;
-        c->radix_log2[0] = best.logn;
+        c->radix_log2[0] = bk;
     } else {
         c->passes = 2;
-        c->radix_log2[0] = (best.logn + 1) / 2;  // R1 (strided pass)
-        c->radix_log2[1] = best.logn / 2;        // R2 (contiguous pass)
+        c->radix_log2[0] = (bk + 1) / 2;  // R1 (strided pass)
+        c->radix_log2[1] = bk / 2;        // R2 (contiguous pass)
     }
-    const uint64_t pairs = c->tiles_in * c->tiles_out;
-    const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
-    const uint64_t per_pair = c->passes == 1 ? 0 : 2 * (uint64_t(1) << best.logn) * elem;
-    uint64_t conc = pairs;
-    const uint64_t cap = uint64_t(2) << 30;  // 2 GiB of spectra per wave
-    if (per_pair && conc * per_pair > cap) conc = cap / per_pair ? cap / per_pair : 1;
-    if (conc > 65535 / 2) conc = 65535 / 2;
-    c->concurrent = static_cast<uint32_t>(conc);
     return PA_OK;
 }
 
-size_t ntt_workspace(int path, const TransformCfg &c) {
-    const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
-    const uint64_t pairs = c.tiles_in * c.tiles_out;
-    size_t bytes = round_up(pairs * sizeof(TilePair), 256);
-    if (c.passes > 1) bytes += size_t(c.concurrent) * 2 * (size_t(1) << c.log2n) * elem;
-    return bytes;
-}
-
-int ntt_init(const PlanCfg &cfg, void *ws) {
-    std::vector<TilePair> pairs;
-    make_pairs(cfg.n, cfg.m, cfg.tr, 0, &pairs);
-    PA_CUDA_TRY(cudaMemcpy(ws, pairs.data(), pairs.size() * sizeof(TilePair), cudaMemcpyHostToDevice));
-    Tables t;
-    if (cfg.path == PA_PATH_NTT31) return get_tables<F31>(0, &t);
-    return get_tables<F64>(1, &t);
-}
+// ---------------------------------------------------------------- work lists
 
 namespace {
 
-template <class F>
-int launch_field(const PlanCfg &cfg, void *ws, Prof *prof, const uint64_t *seed, const uint64_t *key,
-                 uint64_t *out, cudaStream_t s, int field) {
-    using T = typename F::T;
-    using Tw = typename F::Tw;
-    Tables tab;
-    int rc = get_tables<F>(field, &tab);
-    if (rc != PA_OK) return rc;
-    const TransformCfg &c = cfg.tr;
-    const uint64_t npairs = c.tiles_in * c.tiles_out;
-    const TilePair *pairs = static_cast<const TilePair *>(ws);
-    T *spec = reinterpret_cast<T *>(static_cast<char *>(ws) + round_up(npairs * sizeof(TilePair), 256));
-    BlockPtrs one{reinterpret_cast<const uint32_t *>(key), reinterpret_cast<const uint32_t *>(seed),
-                  reinterpret_cast<uint32_t *>(out), cfg.n, cfg.m};
-    const Tw *tf = static_cast<const Tw *>(tab.fwd), *ti = static_cast<const Tw *>(tab.inv);
-    const Tw *stg = static_cast<const Tw *>(tab.stage);
-    const Tw scale = FieldHost<F>::scale(c.log2n);
-    const int logN = static_cast<int>(c.log2n);
-
-    prof_begin(prof, K_MEMSET, s);
-    PA_CUDA_TRY(cudaMemsetAsync(out, 0, ceil_div(cfg.m, 64) * 8, s));
-    prof_end(prof, s);
-
-    if (c.passes == 1) {
-        const size_t smem = size_t(2) * (size_t(1) << logN) * sizeof(Tw) +
-                            size_t(ColMajor::words(1 << logN, 2)) * sizeof(T);
-        PA_CUDA_TRY(cudaFuncSetAttribute(ntt_small<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem)));
-        for (uint64_t p0 = 0; p0 < npairs; p0 += 65535) {
-            const uint64_t cnt = npairs - p0 < 65535 ? npairs - p0 : 65535;
-            prof_begin(prof, K_NTT_SMALL, s);
-            ntt_small<F><<<static_cast<unsigned>(cnt), kThreads, smem, s>>>(pairs + p0, one, logN,
-                                                                           stg, scale);
-            prof_end(prof, s);
-        }
-        PA_CUDA_TRY(cudaGetLastError());
-        return PA_OK;
-    }
-    const int logR1 = static_cast<int>(c.radix_log2[0]), logR2 = static_cast<int>(c.radix_log2[1]);
-    int logC1 = 0, logC2 = 0;
-    pass_columns(logN, sizeof(T), &logC1, &logC2);
-    const size_t sm1 = (size_t(1) << logR1) * sizeof(Tw) + (size_t(1) << (logR1 + logC1)) * sizeof(T);
-    const size_t sm2 = 2 * (size_t(1) << logR2) * sizeof(Tw) +
-                       size_t(ColMajor::words(1 << logR2, 2 << logC2)) * sizeof(T);
-    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_fwd_first<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sm1)));
-    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_inv_first<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sm1)));
-    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_fused_last<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sm2)));
-    const unsigned gx1 = static_cast<unsigned>((uint64_t(1) << (logN - logR1)) >> logC1);
-    const unsigned gx2 = static_cast<unsigned>((uint64_t(1) << logR1) >> logC2);
-    for (uint64_t p0 = 0; p0 < npairs; p0 += c.concurrent) {
-        const uint64_t cnt = npairs - p0 < c.concurrent ? npairs - p0 : c.concurrent;
-        prof_begin(prof, K_NTT_FWD_FIRST, s);
-        ntt_fwd_first<F><<<dim3(gx1, static_cast<unsigned>(2 * cnt)), kThreads, sm1, s>>>(
-            pairs + p0, one, logN, logR1, logC1, spec, stg, tf);
-        prof_end(prof, s);
-        prof_begin(prof, K_NTT_FUSED_LAST, s);
-        ntt_fused_last<F><<<dim3(gx2, static_cast<unsigned>(cnt)), kThreads, sm2, s>>>(
-            logN, logR2, logC2, spec, stg);
-        prof_end(prof, s);
-        prof_begin(prof, K_NTT_INV_FIRST, s);
-        ntt_inv_first<F><<<dim3(gx1, static_cast<unsigned>(cnt)), kThreads, sm1, s>>>(
-            pairs + p0, one, logN, logR1, logC1, spec, stg, ti, scale);
-        prof_end(prof, s);
-    }
-    PA_CUDA_TRY(cudaGetLastError());
-    return PA_OK;
-}
-
-}  // namespace
-
-// ---------------------------------------------------------------- batches
-
-namespace {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+NttTile tile_shape(uint32_t logN, int field) {
+    NttTile t{};
+    t.logN = logN;
+    if (field == 0) {
+        const F31::Tw sc = FieldHost<F31>::scale(t.logN);
+        memcpy(&t.scale, &sc, sizeof(sc));
+    } else {
+        const F64::Tw sc = FieldHost<F64>::scale(t.logN);
+        memcpy(&t.scale, &sc, sizeof(sc));
+    }
+    if (logN > static_cast<uint32_t>(kLogSmallMax)) {
+        const size_t elem = field == 0 ? 4 : 8;
+        t.logR1 = (t.logN + 1) / 2;
+        t.logR2 = t.logN / 2;
+        int logC1 = 0, logC2 = 0;
+        pass_columns(static_cast<int>(t.logN), elem, &logC1, &logC2);
+        t.logC1 = static_cast<uint32_t>(logC1);
+        t.logC2 = static_cast<uint32_t>(logC2);
+        t.g1 = static_cast<uint32_t>((uint64_t(1) << (t.logN - t.logR1)) >> logC1);
+        t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> logC2);
+    }
+    return t;
+}
+
+// The fd spectra and sums of one block: Q key spectra, W window spectra, P sums, with
+// element offsets relative to the start of the block's fd storage.
+void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<NttTile> *spectra,
+              std::vector<NttTile> *sums, FdBlock *fb, std::vector<uint32_t> *wmap,
+              uint64_t *elems) {
+    const TransformCfg &c = b.tr;
+    const uint64_t P = c.tiles_out, Q = c.tiles_in, N = uint64_t(1) << c.log2n;
+    std::vector<TilePair> pairs;
+    make_pairs(b.n, b.m, c, b.index, &pairs);
+    // distinct offsets d = I*M - J*L, each with a representative pair
+    std::vector<std::pair<int64_t, uint64_t>> d(P * Q);
+    for (uint64_t I = 0; I < P; ++I)
+        for (uint64_t J = 0; J < Q; ++J)
+            d[I * Q + J] = {int64_t(I * c.M) - int64_t(J * c.L), I * Q + J};
+    std::vector<std::pair<int64_t, uint64_t>> u = d;
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end(),
+                        [](const std::pair<int64_t, uint64_t> &a,
+                           const std::pair<int64_t, uint64_t> &b2) { return a.first == b2.first; }),
+            u.end());
+    const uint64_t W = u.size();
+    fb->x_off = 0;
+    fb->w_off = Q * N;
+    fb->wmap = wmap->size();
+    fb->Q = static_cast<uint32_t>(Q);
+    const NttTile shape = tile_shape(c.log2n, field);
+    fb->nfwd2 = static_cast<uint32_t>((Q + W) * shape.g2);
+    for (uint64_t I = 0; I < P; ++I)
+        for (uint64_t J = 0; J < Q; ++J) {
+            const int64_t off = d[I * Q + J].first;
+            const auto it = std::lower_bound(u.begin(), u.end(), std::make_pair(off, uint64_t(0)));
+            wmap->push_back(static_cast<uint32_t>(it - u.begin()));
+        }
+    for (uint64_t J = 0; J < Q; ++J) {
+        NttTile t = shape;
+        t.p = pairs[J];  // pair (0, J): key tile J
+        t.which = 0;
+        t.fd = fd_index;
+        t.ws_off = J * N;
+        spectra->push_back(t);
+    }
+    for (uint64_t w = 0; w < W; ++w) {
+        NttTile t = shape;
+        t.p = pairs[u[w].second];
+        t.which = 1;
+        t.fd = fd_index;
+        t.ws_off = (Q + w) * N;
+        spectra->push_back(t);
+    }
+    for (uint64_t I = 0; I < P; ++I) {
+        NttTile t = shape;
+        t.p = pairs[I * Q];  // pair (I, 0): output tile I
+        t.fd = fd_index;
+        t.out = static_cast<uint32_t>(I);
+        t.ws_off = (Q + W + I) * N;
+        sums->push_back(t);
+    }
+    *elems = (Q + W + P) * N;
+}
+
 }  // namespace
 
 int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
                     NttBatchInfo *info) {
     *info = NttBatchInfo();
     info->field = path == PA_PATH_NTT31 ? 0 : 1;
-    const size_t elem = info->field == 0 ? 4 : 8, twsz = 8;
-    std::vector<NttTile> big, small;
+    const int field = info->field;
+    const size_t elem = field == 0 ? 4 : 8, twsz = 8;
+    std::vector<NttTile> big, small, fd_spec, fd_sum;
+    std::vector<FdBlock> fds;
+    std::vector<uint32_t> wmap;
+    std::vector<uint64_t> fd_base;  // fd-storage offset of each fd block
+    uint64_t fd_elems = 0;
     for (const BatchBlock &b : blocks) {
+        if (b.tr.fd) {
+            if (b.tr.log2n <= static_cast<uint32_t>(kLogSmallMax) ||
+                b.tr.tiles_in * b.tr.tiles_out > kFdMaxPairs)
+                return PA_ERR_INVALID;
+            const size_t s0 = fd_spec.size(), u0 = fd_sum.size();
+            FdBlock fb{};
+            uint64_t el = 0;
+            build_fd(b, field, static_cast<uint32_t>(fds.size()), &fd_spec, &fd_sum, &fb, &wmap, &el);
+            for (size_t i = s0; i < fd_spec.size(); ++i) fd_spec[i].ws_off += fd_elems;
+            for (size_t i = u0; i < fd_sum.size(); ++i) fd_sum[i].ws_off += fd_elems;
+            fb.x_off += fd_elems;
+            fb.w_off += fd_elems;
+            fd_elems += el;
+            fds.push_back(fb);
+            continue;
+        }
         std::vector<TilePair> pairs;
         make_pairs(b.n, b.m, b.tr, b.index, &pairs);
         for (const TilePair &p : pairs) {
-            NttTile t{};
+            NttTile t = tile_shape(b.tr.log2n, field);
             t.p = p;
-            t.logN = b.tr.log2n;
-            if (info->field == 0) {
-                const F31::Tw sc = FieldHost<F31>::scale(t.logN);
-                memcpy(&t.scale, &sc, sizeof(sc));
-            } else {
-                const F64::Tw sc = FieldHost<F64>::scale(t.logN);
-                memcpy(&t.scale, &sc, sizeof(sc));
-            }
-            if (t.logN <= static_cast<uint32_t>(kLogSmallMax)) {
-                small.push_back(t);
-            } else {
-                t.logR1 = (t.logN + 1) / 2;
-                t.logR2 = t.logN / 2;
-                int logC1 = 0, logC2 = 0;
-                pass_columns(static_cast<int>(t.logN), elem, &logC1, &logC2);
-                t.logC1 = static_cast<uint32_t>(logC1);
-                t.logC2 = static_cast<uint32_t>(logC2);
-                t.g1 = static_cast<uint32_t>((uint64_t(1) << (t.logN - t.logR1)) >> logC1);
-                t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> logC2);
-                big.push_back(t);
-            }
+            (t.logN <= static_cast<uint32_t>(kLogSmallMax) ? small : big).push_back(t);
         }
     }
     // largest transforms first; slots of the largest spectra size, reused round-robin
@@ -804,27 +943,60 @@ int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t ma
     if (max_slots) slots = std::min<size_t>(slots, std::max<uint32_t>(max_slots, 4));
     if (slots > big.size()) slots = big.size();
     for (size_t i = 0; i < big.size(); ++i) big[i].ws_off = (i % (slots ? slots : 1)) * slot_elems;
+    const uint64_t fd_origin = uint64_t(slots) * slot_elems;  // fd storage after the slots
+    for (NttTile &t : fd_spec) t.ws_off += fd_origin;
+    for (NttTile &t : fd_sum) t.ws_off += fd_origin;
+    for (FdBlock &f : fds) {
+        f.x_off += fd_origin;
+        f.w_off += fd_origin;
+    }
+    // tile table: standard big tiles (indices 0..nb-1, the slot arithmetic needs them
+    // first), small tiles, fd spectra, fd sums
     std::vector<NttTile> tiles = big;
     tiles.insert(tiles.end(), small.begin(), small.end());
-    if (tiles.size() >= (size_t(1) << 30)) return PA_ERR_UNSUPPORTED;
+    const size_t i_spec = tiles.size();
+    tiles.insert(tiles.end(), fd_spec.begin(), fd_spec.end());
+    const size_t i_sum = tiles.size();
+    tiles.insert(tiles.end(), fd_sum.begin(), fd_sum.end());
+    if (tiles.size() >= (size_t(1) << 28)) return PA_ERR_UNSUPPORTED;
     std::vector<uint64_t> items;
     auto push = [&items](uint64_t type, uint64_t ti, uint64_t sub) {
-        items.push_back((type << 62) | (ti << 32) | sub);
+        items.push_back((type << 60) | (ti << 32) | sub);
     };
-    // software pipeline: pass 1 of tile t, pass 2 of tile t-1, pass 3 of tile t-2
+    // fd forward passes first, so the sums near the end of the list rarely wait
+    for (size_t i = 0; i < fd_spec.size(); ++i)
+        for (uint32_t k = 0; k < fd_spec[i].g1; ++k) push(IT_FD_P1, i_spec + i, k);
+    for (size_t i = 0; i < fd_spec.size(); ++i)
+        for (uint32_t k = 0; k < fd_spec[i].g2; ++k) push(IT_FD_P2, i_spec + i, k);
+    // standard tiles, software-pipelined: pass 1 of tile t, pass 2 of t-1, pass 3 of t-2
     const size_t nb = big.size();
     for (size_t t = 0; t < nb + 2; ++t) {
         if (t < nb)
-            for (uint32_t k = 0; k < 2 * big[t].g1; ++k) push(1, t, k);
+            for (uint32_t k = 0; k < 2 * big[t].g1; ++k) push(IT_P1, t, k);
         if (t >= 1 && t - 1 < nb)
-            for (uint32_t k = 0; k < big[t - 1].g2; ++k) push(2, t - 1, k);
+            for (uint32_t k = 0; k < big[t - 1].g2; ++k) push(IT_P2, t - 1, k);
         if (t >= 2 && t - 2 < nb)
-            for (uint32_t k = 0; k < big[t - 2].g1; ++k) push(3, t - 2, k);
+            for (uint32_t k = 0; k < big[t - 2].g1; ++k) push(IT_P3, t - 2, k);
     }
-    for (size_t i = 0; i < small.size(); ++i) push(0, nb + i, 0);
+    // fd sums row group by row group (the outputs of one block share their operands'
+    // rows in L2), then the inverse first passes
+    {
+        size_t i = 0;
+        while (i < fd_sum.size()) {
+            size_t j = i;
+            while (j < fd_sum.size() && fd_sum[j].fd == fd_sum[i].fd) ++j;
+            for (uint32_t k = 0; k < fd_sum[i].g2; ++k)
+                for (size_t q = i; q < j; ++q) push(IT_FD_SUM, i_sum + q, k);
+            i = j;
+        }
+    }
+    for (size_t i = 0; i < fd_sum.size(); ++i)
+        for (uint32_t k = 0; k < fd_sum[i].g1; ++k) push(IT_FD_P3, i_sum + i, k);
+    for (size_t i = 0; i < small.size(); ++i) push(IT_SMALL, nb + i, 0);
     if (items.size() >= (size_t(1) << 32)) return PA_ERR_UNSUPPORTED;
     info->ntiles = tiles.size();
     info->nitems = items.size();
+    info->nfd = fds.size();
     info->slots = static_cast<uint32_t>(slots ? slots : 1);
     // shared memory: the largest need among the bodies present
     size_t smem = 0;
@@ -846,78 +1018,139 @@ int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t ma
     off = align256(off + tiles.size() * sizeof(NttTile));
     info->off_items = off;
     off = align256(off + items.size() * sizeof(uint64_t));
+    info->off_fd = off;
+    off = align256(off + fds.size() * sizeof(FdBlock));
+    info->off_wmap = off;
+    off = align256(off + wmap.size() * sizeof(uint32_t));
     info->off_counters = off;
-    info->counter_bytes = (3 * tiles.size() + 1) * sizeof(uint32_t);
+    info->counter_bytes = (3 * tiles.size() + 1 + fds.size()) * sizeof(uint32_t);
     off = align256(off + info->counter_bytes);
     info->off_spec = off;
-    off = align256(off + size_t(info->slots) * slot_elems * elem);
+    off = align256(off + (size_t(info->slots) * slot_elems + fd_elems) * elem);
     info->bytes = off;
     info->host_tiles.resize(tiles.size() * sizeof(NttTile));
     memcpy(info->host_tiles.data(), tiles.data(), info->host_tiles.size());
-    info->host_items = items;
+    info->host_fd.resize(fds.size() * sizeof(FdBlock));
+    if (!fds.empty()) memcpy(info->host_fd.data(), fds.data(), info->host_fd.size());
+    info->host_items = std::move(items);
+    info->host_wmap = std::move(wmap);
     return PA_OK;
 }
 
-int ntt_batch_upload(const NttBatchInfo &info, void *ws, cudaStream_t s) {
+namespace {
+int upload(const NttBatchInfo &info, void *ws, cudaStream_t s, bool sync) {
     char *b = static_cast<char *>(ws);
-    if (!info.host_tiles.empty())
-        PA_CUDA_TRY(cudaMemcpyAsync(b + info.off_tiles, info.host_tiles.data(),
-                                    info.host_tiles.size(), cudaMemcpyHostToDevice, s));
-    if (!info.host_items.empty())
-        PA_CUDA_TRY(cudaMemcpyAsync(b + info.off_items, info.host_items.data(),
-                                    info.host_items.size() * sizeof(uint64_t),
-                                    cudaMemcpyHostToDevice, s));
+    struct Part {
+        size_t off;
+        const void *src;
+        size_t bytes;
+    } parts[] = {
+        {info.off_tiles, info.host_tiles.data(), info.host_tiles.size()},
+        {info.off_items, info.host_items.data(), info.host_items.size() * sizeof(uint64_t)},
+        {info.off_fd, info.host_fd.data(), info.host_fd.size()},
+        {info.off_wmap, info.host_wmap.data(), info.host_wmap.size() * sizeof(uint32_t)},
+    };
+    for (const Part &p : parts) {
+        if (!p.bytes) continue;
+        if (sync)
+            PA_CUDA_TRY(cudaMemcpy(b + p.off, p.src, p.bytes, cudaMemcpyHostToDevice));
+        else
+            PA_CUDA_TRY(cudaMemcpyAsync(b + p.off, p.src, p.bytes, cudaMemcpyHostToDevice, s));
+    }
     Tables t;
     return info.field == 0 ? get_tables<F31>(0, &t) : get_tables<F64>(1, &t);
 }
+}  // namespace
+
+int ntt_batch_upload(const NttBatchInfo &info, void *ws, cudaStream_t s) {
+    return upload(info, ws, s, false);
+}
+
+int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c) {
+    BatchBlock b;
+    b.index = 0;
+    b.n = n;
+    b.m = m;
+    b.tr = *c;
+    NttBatchInfo info;
+    const int rc = ntt_batch_build(path, std::vector<BatchBlock>{b}, 0, &info);
+    if (rc != PA_OK) return rc;
+    c->lay = static_cast<const NttLayout &>(info);
+    return PA_OK;
+}
+
+int ntt_init(const PlanCfg &cfg, void *ws) {
+    BatchBlock b;
+    b.index = 0;
+    b.n = cfg.n;
+    b.m = cfg.m;
+    b.tr = cfg.tr;
+    NttBatchInfo info;
+    const int rc = ntt_batch_build(cfg.path, std::vector<BatchBlock>{b}, 0, &info);
+    if (rc != PA_OK) return rc;
+    if (info.bytes != cfg.tr.lay.bytes) return PA_ERR_INVALID;
+    return upload(info, ws, nullptr, true);
+}
+
+// ---------------------------------------------------------------- launches
 
 namespace {
 template <class F>
-int batch_launch_field(const NttBatchInfo &info, void *ws, const void *blks, int *status, Prof *prof,
-                       cudaStream_t s) {
+int launch_field(const NttLayout &lay, void *ws, const BlockPtrs *blks, const BlockPtrs &one,
+                 int *status, Prof *prof, cudaStream_t s) {
     using Tw = typename F::Tw;
     Tables tab;
-    int rc = get_tables<F>(info.field, &tab);
+    int rc = get_tables<F>(lay.field, &tab);
     if (rc != PA_OK) return rc;
     char *b = static_cast<char *>(ws);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(b + info.off_counters);
-    const uint32_t nt = static_cast<uint32_t>(info.ntiles);
-    PA_CUDA_TRY(cudaMemsetAsync(cnt, 0, info.counter_bytes, s));
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(b + lay.off_counters);
+    PA_CUDA_TRY(cudaMemsetAsync(cnt, 0, lay.counter_bytes, s));
     PA_CUDA_TRY(cudaFuncSetAttribute(ntt_persistent<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(info.smem)));
+                                     static_cast<int>(lay.smem)));
     int per_sm = 0;
     PA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ntt_persistent<F>, kThreads,
-                                                              info.smem));
+                                                              lay.smem));
     int dev = 0, sms = 0;
     PA_CUDA_TRY(cudaGetDevice(&dev));
     PA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     uint64_t grid = uint64_t(per_sm > 0 ? per_sm : 1) * sms;
-    if (grid > info.nitems) grid = info.nitems;
+    if (grid > lay.nitems) grid = lay.nitems;
     prof_begin(prof, K_BATCH_PERSISTENT, s);
-    ntt_persistent<F><<<static_cast<unsigned>(grid), kThreads, info.smem, s>>>(
-        reinterpret_cast<const uint64_t *>(b + info.off_items), static_cast<uint32_t>(info.nitems),
-        reinterpret_cast<const NttTile *>(b + info.off_tiles), static_cast<const BlockPtrs *>(blks),
-        reinterpret_cast<typename F::T *>(b + info.off_spec), static_cast<const Tw *>(tab.stage),
-        static_cast<const Tw *>(tab.fwd), static_cast<const Tw *>(tab.inv), cnt, cnt + nt,
-        cnt + 2 * nt, info.slots, cnt + 3 * nt, status);
+    ntt_persistent<F><<<static_cast<unsigned>(grid), kThreads, lay.smem, s>>>(
+        reinterpret_cast<const uint64_t *>(b + lay.off_items), static_cast<uint32_t>(lay.nitems),
+        reinterpret_cast<const NttTile *>(b + lay.off_tiles),
+        reinterpret_cast<const FdBlock *>(b + lay.off_fd),
+        reinterpret_cast<const uint32_t *>(b + lay.off_wmap), blks, one,
+        reinterpret_cast<typename F::T *>(b + lay.off_spec), static_cast<const Tw *>(tab.stage),
+        static_cast<const Tw *>(tab.fwd), static_cast<const Tw *>(tab.inv), cnt,
+        static_cast<uint32_t>(lay.ntiles), lay.slots, status);
     prof_end(prof, s);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;
+}
+
+int launch_any(const NttLayout &lay, void *ws, const BlockPtrs *blks, const BlockPtrs &one,
+               int *status, Prof *prof, cudaStream_t s) {
+    if (lay.nitems == 0) return PA_OK;
+    if (lay.field == 0) return launch_field<F31>(lay, ws, blks, one, status, prof, s);
+    return launch_field<F64>(lay, ws, blks, one, status, prof, s);
 }
 }  // namespace
 
 int ntt_batch_launch(const NttBatchInfo &info, void *ws, const void *blks, int *status, Prof *prof,
                      cudaStream_t s) {
-    if (info.nitems == 0) return PA_OK;
-    if (info.field == 0) return batch_launch_field<F31>(info, ws, blks, status, prof, s);
-    return batch_launch_field<F64>(info, ws, blks, status, prof, s);
+    const BlockPtrs none{};
+    return launch_any(info, ws, static_cast<const BlockPtrs *>(blks), none, status, prof, s);
 }
 
 int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                const uint64_t *key, uint64_t *out, cudaStream_t s) {
-    (void)hdr;
-    if (cfg.path == PA_PATH_NTT31) return launch_field<F31>(cfg, ws, prof, seed, key, out, s, 0);
-    return launch_field<F64>(cfg, ws, prof, seed, key, out, s, 1);
+    const BlockPtrs one{reinterpret_cast<const uint32_t *>(key), reinterpret_cast<const uint32_t *>(seed),
+                        reinterpret_cast<uint32_t *>(out), cfg.n, cfg.m};
+    prof_begin(prof, K_MEMSET, s);
+    PA_CUDA_TRY(cudaMemsetAsync(out, 0, ceil_div(cfg.m, 64) * 8, s));
+    prof_end(prof, s);
+    return launch_any(cfg.tr.lay, ws, nullptr, one, &hdr->status, prof, s);
 }
 
 }  // namespace pa

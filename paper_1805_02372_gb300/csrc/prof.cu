@@ -6,10 +6,8 @@
 
 namespace pa {
 
-static const char *kNames[K_NUM_KERNELS] = {
-    "reverse_key", "direct",        "ntt_fwd_first", "ntt_fwd_mid",
-    "ntt_fused_last", "ntt_inv_mid", "ntt_inv_first", "ntt_small",
-    "fft_tile",    "block_mma",     "batch_persistent", "memset"};
+static const char *kNames[K_NUM_KERNELS] = {"reverse_key", "direct",           "fft_tile",
+                                             "block_mma",   "batch_persistent", "memset"};
 
 const char *kernel_name(int kid) { return (kid >= 0 && kid < K_NUM_KERNELS) ? kNames[kid] : "?"; }
 

@@ -1,0 +1,75 @@
+"""Planner of the transform-domain accumulation (host only, no GPU).
+
+Under accumulation the NTT path computes one spectrum per distinct seed-window offset
+d = I*M - J*L (Sec. 3 tiling: output tile I, key tile J). The planner's count of those
+offsets is checked against brute-force enumeration for every structure it special-cases
+(L = M, L a multiple of M, M a multiple of L, neither).
+"""
+import pytest
+
+import paper_1805_02372_gb300 as pkg
+from paper_1805_02372_gb300 import binding
+
+# (n, m, log2 N, L, M)
+GEOMS = [(50_003, 20_011, 13, 4096, 4096), (50_003, 20_011, 13, 4096, 2048),
+         (30_001, 40_003, 13, 2048, 4096), (40_000, 30_000, 13, 3008, 1088),
+         (8_191, 8_193, 13, 4096, 4096), (131_075, 70_001, 14, 8192, 8192),
+         (200_000, 3_000, 13, 4096, 1024), (9_000, 200_000, 13, 1024, 4096)]
+
+
+def brute_windows(n, m, L, M):
+    P, Q = -(-m // M), -(-n // L)
+    return len({i * M - j * L for i in range(P) for j in range(Q)})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1805_02372_gb300 import build
+    build.build()
+    return binding.load()
+
+
+@pytest.mark.parametrize("path", ["ntt31", "ntt64"])
+@pytest.mark.parametrize("n,m,k,L,M", GEOMS)
+def test_window_count_matches_enumeration(lib, path, n, m, k, L, M):
+    d = pkg.pa_plan_query(n, m, binding.make_opts(path=path, log2_transform=k, tile_in=L,
+                                                  tile_out=M, fd_mode=2))
+    assert (d["log2_transform"], d["tile_in"], d["tile_out"]) == (k, L, M)
+    assert d["fd"] == 1
+    assert d["windows"] == brute_windows(n, m, L, M)
+    assert d["kernels_per_call"] == 2
+
+
+@pytest.mark.parametrize("n,m,k,L,M", GEOMS[:3])
+def test_fd_never_when_asked(lib, n, m, k, L, M):
+    d = pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31", log2_transform=k, tile_in=L,
+                                                  tile_out=M, fd_mode=1))
+    assert d["fd"] == 0 and d["windows"] == 0
+
+
+def test_fd_needs_two_pass_transforms_and_several_pairs(lib):
+    # N <= 2^12 runs whole pairs in one CTA: no accumulation.
+    d = pkg.pa_plan_query(50_000, 20_000, binding.make_opts(path="ntt31", log2_transform=12,
+                                                            tile_in=2048, tile_out=2048,
+                                                            fd_mode=2))
+    assert d["fd"] == 0
+    # a single tile pair has nothing to accumulate
+    d = pkg.pa_plan_query(3_000, 1_000, binding.make_opts(path="ntt31", log2_transform=13,
+                                                          fd_mode=2))
+    assert d["tiles_in"] * d["tiles_out"] == 1 and d["fd"] == 0
+
+
+def test_fd_mode_validated(lib):
+    with pytest.raises(pkg.PAError) as e:
+        pkg.pa_plan_query(50_000, 20_000, binding.make_opts(path="ntt31", fd_mode=3))
+    assert e.value.status == binding.PA_ERR_INVALID
+
+
+def test_finite_size_plan_accumulates(lib):
+    # n = 1e8, m = 1e7: many output and key tiles, so the planner accumulates, with
+    # L = M (P + Q - 1 windows) and far fewer transforms than 3 P Q.
+    d = pkg.pa_plan_query(100_000_007, 10_000_000, binding.make_opts(path="ntt31"))
+    P, Q = d["tiles_out"], d["tiles_in"]
+    assert d["fd"] == 1 and P * Q > 1
+    assert d["windows"] == brute_windows(100_000_007, 10_000_000, d["tile_in"], d["tile_out"])
+    assert Q + d["windows"] + P < 3 * P * Q / 2

@@ -1,0 +1,112 @@
+"""Transform-domain accumulation on the GPU: bit-exact against the oracle.
+
+Every window-offset structure the planner distinguishes (L = M, L = 2M, M = 2L, neither
+dividing the other), both prime fields, ragged tails, fd blocks next to standard tiles
+in one persistent launch, and the finite-size workload (n = 1e8, m = 1e7) on sampled
+rows plus linearity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1805_02372_gb300 as pkg
+from paper_1805_02372_gb300 import binding, inputs
+from gpu_util import dev, host, run_path
+
+pytestmark = pytest.mark.gpu
+
+# (n, m, log2 N, L, M)
+GEOMS = [(50_003, 20_011, 13, 4096, 4096), (50_003, 20_011, 13, 4096, 2048),
+         (30_001, 40_003, 13, 2048, 4096), (40_000, 30_000, 13, 3008, 1088),
+         (8_191, 8_193, 13, 4096, 4096), (131_075, 70_001, 14, 8192, 8192),
+         (200_000, 3_000, 13, 4096, 1024), (9_000, 200_000, 13, 1024, 4096)]
+
+
+@pytest.mark.parametrize("path", ["ntt31", "ntt64"])
+@pytest.mark.parametrize("n,m,k,L,M", GEOMS)
+def test_fd_matches_oracle(path, n, m, k, L, M):
+    blk = inputs.single_block(n, m, 31 + n, 37 + m)
+    key, seed = blk.key(), blk.seed()
+    want = oracle.hash_full(n, m, seed, key)
+    got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
+                         fd_mode=2)
+    assert desc["fd"] == 1
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
+
+
+@pytest.mark.parametrize("kind", ["ones", "seed_ones"])
+def test_fd_largest_coefficients(kind):
+    # all-ones inputs give the largest sums (every coefficient counts L products per key
+    # tile), the case that needs n < p of the 31-bit field
+    n, m = 60_001, 25_003
+    key = np.full((n + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    seed = np.full((n + m - 1 + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    if kind == "seed_ones":
+        key = inputs.random_bits(n, 5)
+    want = oracle.hash_full(n, m, seed, key)
+    got, desc = run_path(n, m, key, seed, path="ntt31", log2_transform=13, tile_in=4096,
+                         tile_out=4096, fd_mode=2)
+    assert desc["fd"] == 1 and np.array_equal(got, want)
+
+
+def test_fd_and_standard_tiles_in_one_launch():
+    import torch
+    shapes = [(50_003, 20_011), (3_001, 1_000), (20_000, 9_000), (1, 1), (70_001, 64),
+              (8_191, 8_193)]
+    bl = [inputs.single_block(n, m, 500 + 2 * i, 501 + 2 * i) for i, (n, m) in enumerate(shapes)]
+    keys, seeds = [b.key() for b in bl], [b.seed() for b in bl]
+    kd, sd = [dev(k) for k in keys], [dev(s) for s in seeds]
+    od = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in bl]
+    desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sd, kd, od)]
+    opts = binding.make_opts(path="ntt31", log2_transform=13, tile_in=4096, tile_out=4096,
+                             fd_mode=2)
+    batch = pkg.pa_batch_plan(desc, opts)
+    try:
+        plans = pkg.pa_batch_describe(batch, len(bl))
+        assert {d["fd"] for d in plans} == {0, 1}
+        for run in range(3):  # first run captures the graph, later runs replay it
+            for o in od:
+                o.fill_(-1)
+            rep = pkg.pa_batch_run(batch, desc, report=True)
+            assert rep["graph_replayed"] == (1 if run else 0)
+            for b, k, s, o in zip(bl, keys, seeds, od):
+                assert np.array_equal(host(o), oracle.hash_full(b.n, b.m, s, k)), (run, b.n, b.m)
+    finally:
+        pkg.pa_batch_destroy(batch)
+
+
+def test_fd_equals_standard_at_size():
+    # n = 4e6, m = 1.5e6 at N = 2^21, L = M = 2^20: 6 output x 4 key tiles
+    n, m = 4_000_003, 1_500_001
+    blk = inputs.single_block(n, m, 71, 73)
+    key, seed = blk.key(), blk.seed()
+    a, da = run_path(n, m, key, seed, path="ntt31", log2_transform=21, tile_in=1 << 20,
+                     tile_out=1 << 20, fd_mode=2)
+    b, db = run_path(n, m, key, seed, path="ntt31", log2_transform=21, tile_in=1 << 20,
+                     tile_out=1 << 20, fd_mode=1)
+    assert da["fd"] == 1 and db["fd"] == 0
+    assert np.array_equal(a, b)
+    rows = np.unique(np.concatenate([np.random.default_rng(3).integers(0, m, 2000),
+                                     [0, m - 1, (1 << 20) - 1, 1 << 20]]))
+    assert np.array_equal(oracle.unpack(a, m)[rows], oracle.hash_rows(n, m, seed, key, rows))
+
+
+def test_finite_size_fd_sampled_rows():
+    b = inputs.FINITE_SIZE
+    key, seed = b.key(), b.seed()
+    got, desc = run_path(b.n, b.m, key, seed, path="ntt31")
+    assert desc["fd"] == 1
+    rng = np.random.default_rng(9)
+    M = desc["tile_out"]
+    edges = [r for i in range(desc["tiles_out"]) for r in (i * M - 1, i * M, i * M + 1)
+             if 0 <= r < b.m]
+    rows = np.unique(np.concatenate([rng.integers(0, b.m, 3000), edges, [b.m - 1]]))
+    want = oracle.hash_rows(b.n, b.m, seed, key, rows)
+    assert np.array_equal(oracle.unpack(got, b.m)[rows], want)
+    if b.m % 64:
+        assert int(got[-1]) >> (b.m % 64) == 0
+    key2 = inputs.random_bits(b.n, 778)
+    g2, _ = run_path(b.n, b.m, key2, seed, path="ntt31")
+    g12, _ = run_path(b.n, b.m, key ^ key2, seed, path="ntt31")
+    assert np.array_equal(g12, got ^ g2)
