@@ -52,7 +52,8 @@ typedef enum {
     PA_PATH_AUTO = 0,       /* planner / autotuner choice                                */
     PA_PATH_DIRECT = 1,     /* bit-packed AND + popcount parity (Sec. 2.1 definition)    */
     PA_PATH_NTT64 = 2,      /* exact NTT modulo 2^64-2^32+1 (Sec. 3, FFT route, exact)  */
-    PA_PATH_NTT31 = 3,      /* exact NTT modulo 15*2^27+1 (coefficients <= n < p)        */
+    PA_PATH_NTT31 = 3,      /* exact NTT modulo a prime below 2^31 (7*2^26+1 or 15*2^27+1,
+                               coefficients <= n < p)                                      */
     PA_PATH_FFT = 4,        /* FP32 FFT sub-blocks under a proven rounding bound; FP64
                                butterflies on the tile lengths where the FP32 bound fails */
     PA_PATH_BLOCK_INT8 = 5  /* block-Toeplitz Y = sum_d T_d X_d, INT8 tensor cores,
@@ -75,7 +76,10 @@ typedef struct {
                                   (each key and seed-window spectrum computed once, one
                                   inverse per output sub-block). 0 = when the planner
                                   estimates it faster, 1 = never, 2 = whenever possible   */
-    uint32_t reserved[5];
+    uint32_t ntt_prime;        /* PA_PATH_NTT31: 0 = automatic (7*2^26+1 while n is below
+                                  it, else 15*2^27+1), 29 or 31 = that prime; a prime not
+                                  above n is PA_ERR_UNSUPPORTED                          */
+    uint32_t reserved[4];
 } pa_opts;
 
 /* What a plan decided (pa_plan_query / pa_plan_describe). */
@@ -94,7 +98,8 @@ typedef struct {
     uint32_t kernels_per_call; /* kernel launches one pa_hash enqueues                    */
     uint32_t fd;               /* NTT: transform-domain accumulation (see pa_opts.fd_mode) */
     uint64_t windows;          /* with fd: seed-window spectra computed (distinct offsets) */
-    uint32_t reserved[2];
+    uint32_t prime_bits;       /* NTT paths: bits of the prime (29, 31 or 64), else 0     */
+    uint32_t reserved;
 } pa_plan_desc;
 
 typedef struct pa_plan_s *pa_plan_t;

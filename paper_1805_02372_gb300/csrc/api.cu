@@ -91,6 +91,8 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->rounding_bound = cfg.tr.bound;
         d->fd = cfg.tr.fd;
         d->windows = cfg.tr.windows;
+        if (cfg.path == PA_PATH_NTT31 || cfg.path == PA_PATH_NTT64)
+            d->prime_bits = cfg.tr.field == kFieldF64 ? 64 : (cfg.tr.field == kFieldF29 ? 29 : 31);
     }
 }
 

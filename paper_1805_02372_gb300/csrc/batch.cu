@@ -301,9 +301,9 @@ struct pa_batch_s {
     std::vector<uint64_t> n, m;
     std::vector<PlanCfg> cfg;
     std::vector<size_t> ws_off;       // per block (non-persistent paths)
-    std::vector<uint32_t> in_ntt[2];  // blocks run by the persistent launch, per field
-    NttBatchInfo ntt[2];
-    size_t off_blks = 0, off_idx[2] = {0, 0}, off_ntt[2] = {0, 0}, bytes = 0;
+    std::vector<uint32_t> in_ntt[kNumFields];  // blocks run by the persistent launches, per field
+    NttBatchInfo ntt[kNumFields];
+    size_t off_blks = 0, off_idx[kNumFields] = {}, off_ntt[kNumFields] = {}, bytes = 0;
     void *mem = nullptr;
     std::vector<BlockPtrs> hblks;
     bool blks_valid = false;
@@ -332,7 +332,7 @@ int enqueue_all(pa_batch_s *b, cudaStream_t s) {
     const BlockPtrs *dblks = reinterpret_cast<const BlockPtrs *>(base + b->off_blks);
     DevHeader *hdr = batch_hdr(b);
     Prof *prof = b->prof.on ? &b->prof : nullptr;
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < kNumFields; ++f) {
         if (b->in_ntt[f].empty()) continue;
         prof_begin(prof, K_MEMSET, s);
         batch_zero<<<static_cast<unsigned>(b->in_ntt[f].size()), 256, 0, s>>>(
@@ -397,7 +397,7 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
             return rc;
         }
     }
-    std::vector<BatchBlock> nb[2];
+    std::vector<BatchBlock> nb[kNumFields];
     size_t off = kHeaderBytes;
     b->off_blks = off;
     off = round_up(off + count * sizeof(BlockPtrs), 256);
@@ -421,7 +421,7 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         const PlanCfg &c = b->cfg[i];
         b->per_path[c.path] += 1;
         if (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64) {
-            const int f = c.path == PA_PATH_NTT31 ? 0 : 1;
+            const int f = c.tr.field;
             BatchBlock bb;
             bb.index = static_cast<uint32_t>(i);
             bb.n = n;
@@ -439,10 +439,9 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
             if (c.path == PA_PATH_FFT) b->bound = std::max(b->bound, c.tr.bound);
         }
     }
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < kNumFields; ++f) {
         if (nb[f].empty()) continue;
-        int rc = ntt_batch_build(f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64, nb[f],
-                                 opts ? opts->max_slots : 0, &b->ntt[f]);
+        int rc = ntt_batch_build(f, nb[f], opts ? opts->max_slots : 0, &b->ntt[f]);
         if (rc != PA_OK) {
             delete b;
             return rc;
@@ -458,7 +457,7 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
     e = as ? cudaMallocAsync(&b->mem, b->bytes, as) : cudaMalloc(&b->mem, b->bytes);
     if (e == cudaSuccess)
         e = as ? cudaMemsetAsync(b->mem, 0, kHeaderBytes, as) : cudaMemset(b->mem, 0, kHeaderBytes);
-    for (int f = 0; e == cudaSuccess && f < 2; ++f)
+    for (int f = 0; e == cudaSuccess && f < kNumFields; ++f)
         if (!b->in_ntt[f].empty())
             e = cudaMemcpyAsync(static_cast<char *>(b->mem) + b->off_idx[f], b->in_ntt[f].data(),
                                 b->in_ntt[f].size() * sizeof(uint32_t), cudaMemcpyHostToDevice, as);
@@ -467,7 +466,7 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         delete b;
         return cuda_fail(e);
     }
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < kNumFields; ++f) {
         if (b->in_ntt[f].empty()) continue;
         int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f], as);
         if (rc != PA_OK) {

@@ -1,5 +1,8 @@
 // Shared-memory R-point transforms over a ring policy F (a prime field or complex
-// floating point): F::T element, F::Tw twiddle, F::add, F::sub, F::mul_tw.
+// floating point): F::T element, F::Tw twiddle, and the two butterflies
+// F::dif_bfly(a, b, w): (a, b) <- (a + b, (a - b) w) and
+// F::dit_bfly(a, b, w): (a, b) <- (a + b w, a - b w), each up to the representation of
+// residues the field keeps (canonical, or lazily reduced).
 //
 // Forward = decimation in frequency (natural order in, bit-reversed out); inverse =
 // decimation in time (bit-reversed in, natural out, unnormalised). Every radix-2
@@ -83,9 +86,7 @@ __device__ __forceinline__ void dif_group(typename F::T (&x)[1 << S], const type
         for (int k = 0; k < (1 << S); ++k) {
             if (k & half) continue;
             const typename F::Tw w = tw[h - 1 + j + (k & (half - 1)) * q];
-            const typename F::T a = x[k], b = x[k + half];
-            x[k] = F::add(a, b);
-            x[k + half] = F::mul_tw(F::sub(a, b), w);
+            F::dif_bfly(x[k], x[k + half], w);
         }
     }
 }
@@ -102,10 +103,7 @@ __device__ __forceinline__ void dit_group(typename F::T (&x)[1 << S], const type
         for (int k = 0; k < (1 << S); ++k) {
             if (k & half) continue;
             const typename F::Tw w = tw[h - 1 + j + (k & (half - 1)) * q];
-            const typename F::T a = x[k];
-            const typename F::T t = F::mul_tw(x[k + half], w);
-            x[k] = F::add(a, t);
-            x[k + half] = F::sub(a, t);
+            F::dit_bfly(x[k], x[k + half], w);
         }
     }
 }

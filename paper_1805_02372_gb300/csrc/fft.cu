@@ -66,6 +66,16 @@ struct CRing {
         r.y = a.x * w.y + a.y * w.x;
         return r;
     }
+    __device__ static __forceinline__ void dif_bfly(T &a, T &b, Tw w) {
+        const T s = add(a, b);
+        b = mul_tw(sub(a, b), w);
+        a = s;
+    }
+    __device__ static __forceinline__ void dit_bfly(T &a, T &b, Tw w) {
+        const T t = mul_tw(b, w);
+        b = sub(a, t);
+        a = add(a, t);
+    }
 };
 
 // ---------------------------------------------------------------- the bound

@@ -24,9 +24,14 @@ struct DirectCfg {
 };
 
 // ---- transform paths (NTT over a prime field, FP FFT) ----
+// Prime fields of the NTT paths: PA_PATH_NTT64 runs modulo 2^64 - 2^32 + 1;
+// PA_PATH_NTT31 modulo 7*2^26 + 1 (lazily reduced) when n is below it, else 15*2^27 + 1.
+constexpr int kFieldF31 = 0, kFieldF64 = 1, kFieldF29 = 2, kNumFields = 3;
+constexpr uint64_t kPrimeF29 = 469762049ull, kPrimeF31 = 2013265921ull;
+
 // Workspace layout and launch shape of one persistent NTT launch (see ntt.cu).
 struct NttLayout {
-    int field = 0;         // 0: 31-bit prime, 1: 64-bit prime
+    int field = 0;         // kFieldF31 / kFieldF64 / kFieldF29
     uint64_t ntiles = 0, nitems = 0, nfd = 0;
     uint32_t slots = 1;    // spectra slots of standard tiles, reused round-robin
     size_t smem = 0;
@@ -44,6 +49,7 @@ struct TransformCfg {
     uint32_t radix_log2[4] = {0, 0, 0, 0};
     uint32_t fp64 = 0;           // FFT: FP64 butterflies
     double bound = 0.0;          // FFT: proven rounding bound
+    int field = 0;               // NTT: kFieldF31 / kFieldF64 / kFieldF29
     uint32_t fd = 0;             // NTT: transform-domain accumulation over key tiles
     uint64_t windows = 0;        // NTT with fd: distinct seed-window spectra
     NttLayout lay;               // NTT single-block plans: their persistent launch
@@ -154,7 +160,7 @@ struct NttBatchInfo : NttLayout {
     std::vector<uint64_t> host_items;
     std::vector<uint32_t> host_wmap;
 };
-int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
+int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
                     NttBatchInfo *info);
 // host tables are copied on stream s (kept alive by info until the copy ran)
 int ntt_batch_upload(const NttBatchInfo &info, void *ws, cudaStream_t s);

@@ -162,6 +162,24 @@ struct FieldHost<F31> {
     }
 };
 template <>
+struct FieldHost<F29> {
+    static uint64_t p() { return F29::P; }
+    static uint64_t root(int k) {
+        const uint64_t f[] = {7};
+        return root_of_unity(F29::P, f, 1, 26, k);
+    }
+    static F29::Tw tw(uint64_t w) {
+        F29::Tw t;
+        t.w = static_cast<uint32_t>(w);
+        t.q = static_cast<uint32_t>((w << 32) / F29::P);
+        return t;
+    }
+    static F29::Tw scale(int logn) {
+        uint64_t ninv = powmod_host(uint64_t(1) << logn, F29::P - 2, F29::P);
+        return tw(mulmod_host(ninv, (uint64_t(1) << 32) % F29::P, F29::P));
+    }
+};
+template <>
 struct FieldHost<F64> {
     static uint64_t p() { return F64::P; }
     static uint64_t root(int k) {
@@ -181,7 +199,7 @@ struct Tables {
 };
 constexpr int kStageBlock = 4096;  // entries per (direction, log2 R) block
 std::mutex g_tab_mu;
-Tables g_tabs[2][64];
+Tables g_tabs[kNumFields][64];
 
 template <class F>
 int get_tables(int field, Tables *out) {
@@ -729,7 +747,7 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
     if (k <= static_cast<uint32_t>(kLogSmallMax) || fd_mode == 1 || P * Q < 2 || P * Q > kFdMaxPairs)
         return std_units;
     const uint64_t W = count_windows(P, Q, M, L);
-    const size_t elem = path == PA_PATH_NTT31 ? 4 : 8;
+    const size_t elem = path == PA_PATH_NTT64 ? 8 : 4;
     if (double(Q + W + P) * N * elem > double(kFdMaxBytes)) return std_units;
     const double tr = N * (k + 6) / 3.0;
     const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(P) * (tr + N + 1024.0) +
@@ -744,7 +762,21 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c) {
     *c = TransformCfg();
-    if (path == PA_PATH_NTT31 && n >= F31::P) return PA_ERR_UNSUPPORTED;  // counts must stay < p
+    // every coefficient read is a count of at most n bit products: n < p keeps it exact
+    const uint32_t prime = o ? o->ntt_prime : 0;
+    if (path == PA_PATH_NTT64) {
+        if (prime) return PA_ERR_INVALID;
+        c->field = kFieldF64;
+    } else if (prime == 29 || (prime == 0 && n < kPrimeF29)) {
+        if (n >= kPrimeF29) return PA_ERR_UNSUPPORTED;
+        c->field = kFieldF29;
+    } else if (prime == 31 || prime == 0) {
+        if (n >= kPrimeF31) return PA_ERR_UNSUPPORTED;
+        c->field = kFieldF31;
+    } else {
+        return PA_ERR_INVALID;
+    }
+    const int field = c->field;
     const uint32_t fd_mode = o ? o->fd_mode : 0;
     if (fd_mode > 2) return PA_ERR_INVALID;
     const uint32_t force = o ? o->log2_transform : 0;
@@ -784,6 +816,7 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
         }
     }
     if (!(best_cost < INFINITY)) return PA_ERR_UNSUPPORTED;
+    c->field = field;
     c->log2n = bk;
     c->L = bL;
     c->M = bM;
@@ -811,15 +844,18 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 NttTile tile_shape(uint32_t logN, int field) {
     NttTile t{};
     t.logN = logN;
-    if (field == 0) {
+    if (field == kFieldF31) {
         const F31::Tw sc = FieldHost<F31>::scale(t.logN);
+        memcpy(&t.scale, &sc, sizeof(sc));
+    } else if (field == kFieldF29) {
+        const F29::Tw sc = FieldHost<F29>::scale(t.logN);
         memcpy(&t.scale, &sc, sizeof(sc));
     } else {
         const F64::Tw sc = FieldHost<F64>::scale(t.logN);
         memcpy(&t.scale, &sc, sizeof(sc));
     }
     if (logN > static_cast<uint32_t>(kLogSmallMax)) {
-        const size_t elem = field == 0 ? 4 : 8;
+        const size_t elem = field == kFieldF64 ? 8 : 4;
         t.logR1 = (t.logN + 1) / 2;
         t.logR2 = t.logN / 2;
         int logC1 = 0, logC2 = 0;
@@ -894,12 +930,12 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
 
 }  // namespace
 
-int ntt_batch_build(int path, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
+int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t max_slots,
                     NttBatchInfo *info) {
     *info = NttBatchInfo();
-    info->field = path == PA_PATH_NTT31 ? 0 : 1;
-    const int field = info->field;
-    const size_t elem = field == 0 ? 4 : 8, twsz = 8;
+    if (field < 0 || field >= kNumFields) return PA_ERR_INVALID;
+    info->field = field;
+    const size_t elem = field == kFieldF64 ? 8 : 4, twsz = 8;
     std::vector<NttTile> big, small, fd_spec, fd_sum;
     std::vector<FdBlock> fds;
     std::vector<uint32_t> wmap;
@@ -1058,7 +1094,11 @@ int upload(const NttBatchInfo &info, void *ws, cudaStream_t s, bool sync) {
             PA_CUDA_TRY(cudaMemcpyAsync(b + p.off, p.src, p.bytes, cudaMemcpyHostToDevice, s));
     }
     Tables t;
-    return info.field == 0 ? get_tables<F31>(0, &t) : get_tables<F64>(1, &t);
+    switch (info.field) {
+        case kFieldF31: return get_tables<F31>(kFieldF31, &t);
+        case kFieldF29: return get_tables<F29>(kFieldF29, &t);
+        default: return get_tables<F64>(kFieldF64, &t);
+    }
 }
 }  // namespace
 
@@ -1073,7 +1113,7 @@ int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c) {
     b.m = m;
     b.tr = *c;
     NttBatchInfo info;
-    const int rc = ntt_batch_build(path, std::vector<BatchBlock>{b}, 0, &info);
+    const int rc = ntt_batch_build(c->field, std::vector<BatchBlock>{b}, 0, &info);
     if (rc != PA_OK) return rc;
     c->lay = static_cast<const NttLayout &>(info);
     return PA_OK;
@@ -1086,7 +1126,7 @@ int ntt_init(const PlanCfg &cfg, void *ws) {
     b.m = cfg.m;
     b.tr = cfg.tr;
     NttBatchInfo info;
-    const int rc = ntt_batch_build(cfg.path, std::vector<BatchBlock>{b}, 0, &info);
+    const int rc = ntt_batch_build(cfg.tr.field, std::vector<BatchBlock>{b}, 0, &info);
     if (rc != PA_OK) return rc;
     if (info.bytes != cfg.tr.lay.bytes) return PA_ERR_INVALID;
     return upload(info, ws, nullptr, true);
@@ -1132,8 +1172,11 @@ int launch_field(const NttLayout &lay, void *ws, const BlockPtrs *blks, const Bl
 int launch_any(const NttLayout &lay, void *ws, const BlockPtrs *blks, const BlockPtrs &one,
                int *status, Prof *prof, cudaStream_t s) {
     if (lay.nitems == 0) return PA_OK;
-    if (lay.field == 0) return launch_field<F31>(lay, ws, blks, one, status, prof, s);
-    return launch_field<F64>(lay, ws, blks, one, status, prof, s);
+    switch (lay.field) {
+        case kFieldF31: return launch_field<F31>(lay, ws, blks, one, status, prof, s);
+        case kFieldF29: return launch_field<F29>(lay, ws, blks, one, status, prof, s);
+        default: return launch_field<F64>(lay, ws, blks, one, status, prof, s);
+    }
 }
 }  // namespace
 

@@ -1,9 +1,14 @@
-// Prime fields of the exact transform path and their host-side root tables.
+// Prime fields of the exact transform path.
 //
-// F31: p = 15 * 2^27 + 1 (2-adicity 27). Every convolution coefficient of a tile is a
-//      count of at most L < p bit products, so the residue IS the integer and its low
-//      bit is the hash bit. Twiddles carry Shoup quotients (one high-half multiply
-//      per twiddle product); the pointwise product is a Montgomery product.
+// Every convolution coefficient the path reads is a count of at most n bit products,
+// so for n < p the residue IS the integer and its low bit is the hash bit.
+// F29: p = 7 * 2^26 + 1 (2-adicity 26), for n < p. Residues are kept lazily in
+//      [0, 4p) (4p < 2^31): a butterfly needs one conditional subtraction instead of
+//      three (Harvey's lazy butterflies for Shoup multiplication); values are made
+//      canonical only when the hash bit is taken.
+// F31: p = 15 * 2^27 + 1 (2-adicity 27), canonical residues, for n < p.
+//      Twiddles carry Shoup quotients (one high-half multiply per twiddle product);
+//      the pointwise product is a Montgomery product.
 // F64: p = 2^64 - 2^32 + 1 (2-adicity 32); products reduced with 2^64 = 2^32 - 1 mod p.
 #pragma once
 
@@ -69,6 +74,88 @@ struct F31 {
         r.q = w.w ? 0xFFFFFFFFu - w.q : 0u;
         return r;
     }
+    __device__ static __forceinline__ void dif_bfly(T &a, T &b, Tw w) {
+        const T s = add(a, b);
+        b = mul_tw(sub(a, b), w);
+        a = s;
+    }
+    __device__ static __forceinline__ void dit_bfly(T &a, T &b, Tw w) {
+        const T t = mul_tw(b, w);
+        b = sub(a, t);
+        a = add(a, t);
+    }
+};
+
+// Residues in [0, 4p). Shoup's product of any 32-bit a by a canonical twiddle w with
+// quotient floor(w 2^32 / p) lies in [0, 2p) when p < 2^31 (Harvey, "Faster arithmetic
+// for number-theoretic transforms", 2014), which is what lets the corrections go.
+struct F29 {
+    using T = uint32_t;
+    using Tw = F31::Tw;  // value and Shoup quotient
+    static constexpr uint32_t P = 469762049u;
+    static constexpr uint32_t P2 = 2 * P, P4 = 4 * P;
+    static constexpr int kTwoAdicity = 26;
+    static constexpr uint32_t PINV = inverse_mod_2_32(469762049u);
+    static_assert(PINV * 469762049u == 1u, "Montgomery inverse");
+    static_assert(uint64_t(8) * 469762049u < (uint64_t(1) << 32), "8p fits 32 bits");
+
+    // [0, 4p) + [0, 4p) -> [0, 4p)
+    __device__ static __forceinline__ T add(T a, T b) {
+        const T s = a + b;
+        return min(s, s - P4);
+    }
+    __device__ static __forceinline__ T sub(T a, T b) {
+        const T d = a + (P4 - b);
+        return min(d, d - P4);
+    }
+    // any 32-bit a -> [0, 2p)
+    __device__ static __forceinline__ T mul_tw(T a, Tw w) {
+        const uint32_t q = __umulhi(a, w.q);
+        return a * w.w - q * P;
+    }
+    // a b 2^-32 for a < 4p, b < 4p: (ab - mq p) / 2^32 in (-p, 1.75p), plus p -> (0, 2.75p)
+    __device__ static __forceinline__ T mont(T a, T b) {
+        const uint32_t lo = a * b, hi = __umulhi(a, b);
+        const uint32_t mq = lo * PINV;
+        return hi - __umulhi(mq, P) + P;
+    }
+    // canonical residue of a in [0, 4p), then its low bit
+    __device__ static __forceinline__ uint32_t low_bit(T a) {
+        a = min(a, a - P2);
+        a = min(a, a - P);
+        return a & 1u;
+    }
+    static constexpr uint32_t R_MOD = static_cast<uint32_t>((uint64_t(1) << 32) % 469762049u);
+    static constexpr uint32_t R_Q = static_cast<uint32_t>((uint64_t(R_MOD) << 32) / 469762049u);
+    // w 2^32 mod p in [0, 2p)
+    __device__ static __forceinline__ T full_form(Tw w) {
+        Tw r;
+        r.w = R_MOD;
+        r.q = R_Q;
+        return mul_tw(w.w, r);
+    }
+    // a < 4p times wf < 2p: (0, 2p) after the Montgomery reduction
+    __device__ static __forceinline__ T mul_full(T a, T wf) { return mont(a, wf); }
+    __device__ static __forceinline__ T step_full(T wf, Tw step) { return mul_tw(wf, step); }
+    __device__ static __forceinline__ Tw neg_tw(Tw w) {
+        Tw r;
+        r.w = w.w ? P - w.w : 0u;
+        r.q = w.w ? 0xFFFFFFFFu - w.q : 0u;
+        return r;
+    }
+    // Gentleman-Sande: (a + b, (a - b) w); a, b in [0, 4p) -> [0, 4p), [0, 2p)
+    __device__ static __forceinline__ void dif_bfly(T &a, T &b, Tw w) {
+        const T s = a + b;
+        b = mul_tw(a + (P4 - b), w);
+        a = min(s, s - P4);
+    }
+    // Cooley-Tukey: (a + b w, a - b w); a, b in [0, 4p) -> [0, 4p), (0, 4p)
+    __device__ static __forceinline__ void dit_bfly(T &a, T &b, Tw w) {
+        const T t = mul_tw(b, w);
+        const T a2 = min(a, a - P2);
+        a = a2 + t;
+        b = a2 + (P2 - t);
+    }
 };
 
 struct F64 {
@@ -104,6 +191,16 @@ struct F64 {
     __device__ static __forceinline__ T mul_full(T a, T wf) { return mul(a, wf); }
     __device__ static __forceinline__ T step_full(T wf, Tw step) { return mul(wf, step); }
     __device__ static __forceinline__ Tw neg_tw(Tw w) { return w ? P - w : 0; }
+    __device__ static __forceinline__ void dif_bfly(T &a, T &b, Tw w) {
+        const T s = add(a, b);
+        b = mul_tw(sub(a, b), w);
+        a = s;
+    }
+    __device__ static __forceinline__ void dit_bfly(T &a, T &b, Tw w) {
+        const T t = mul_tw(b, w);
+        b = sub(a, t);
+        a = add(a, t);
+    }
 };
 
 }  // namespace pa

@@ -73,3 +73,23 @@ def test_finite_size_plan_accumulates(lib):
     assert d["fd"] == 1 and P * Q > 1
     assert d["windows"] == brute_windows(100_000_007, 10_000_000, d["tile_in"], d["tile_out"])
     assert Q + d["windows"] + P < 3 * P * Q / 2
+
+
+def test_prime_choice(lib):
+    q = pkg.pa_plan_query
+    assert q(1_000_000, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 29
+    assert q(1_000_000, 5_000, binding.make_opts(path="ntt31", ntt_prime=31))["prime_bits"] == 31
+    assert q(1_000_000, 5_000, binding.make_opts(path="ntt64"))["prime_bits"] == 64
+    # 7 * 2^26 + 1 = 469,762,049: counts up to n must stay below the prime
+    assert q(469_762_048, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 29
+    assert q(469_762_049, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 31
+    with pytest.raises(pkg.PAError) as e:
+        q(469_762_049, 5_000, binding.make_opts(path="ntt31", ntt_prime=29))
+    assert e.value.status == binding.PA_ERR_UNSUPPORTED
+    with pytest.raises(pkg.PAError) as e:
+        q(2_013_265_921, 5_000, binding.make_opts(path="ntt31"))
+    assert e.value.status == binding.PA_ERR_UNSUPPORTED
+    for bad in (7, 30):
+        with pytest.raises(pkg.PAError):
+            q(1_000, 5, binding.make_opts(path="ntt31", ntt_prime=bad))
+    assert q(1_000, 5, binding.make_opts(path="direct"))["prime_bits"] == 0

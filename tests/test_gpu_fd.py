@@ -22,15 +22,15 @@ GEOMS = [(50_003, 20_011, 13, 4096, 4096), (50_003, 20_011, 13, 4096, 2048),
          (200_000, 3_000, 13, 4096, 1024), (9_000, 200_000, 13, 1024, 4096)]
 
 
-@pytest.mark.parametrize("path", ["ntt31", "ntt64"])
+@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
 @pytest.mark.parametrize("n,m,k,L,M", GEOMS)
-def test_fd_matches_oracle(path, n, m, k, L, M):
+def test_fd_matches_oracle(path, prime, n, m, k, L, M):
     blk = inputs.single_block(n, m, 31 + n, 37 + m)
     key, seed = blk.key(), blk.seed()
     want = oracle.hash_full(n, m, seed, key)
     got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
-                         fd_mode=2)
-    assert desc["fd"] == 1
+                         fd_mode=2, ntt_prime=prime)
+    assert desc["fd"] == 1 and desc["prime_bits"] == (prime or 64)
     bad = np.flatnonzero(got != want)
     assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
 

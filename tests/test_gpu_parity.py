@@ -56,6 +56,13 @@ def test_shapes(path, n, m):
     _check(path, n, m, key, seed, want)
 
 
+@pytest.mark.parametrize("n,m", SHAPES)
+def test_shapes_31bit_prime(n, m):
+    # the NTT31 path takes the 29-bit prime below its bound; force the 31-bit one here
+    key, seed, want = _case(n, m, 11 + n, 13 + m)
+    _check("ntt31", n, m, key, seed, want, ntt_prime=31)
+
+
 @pytest.mark.parametrize("path", PATHS)
 def test_plain_single_block(path):
     b = inputs.PLAIN_SINGLE
