@@ -346,6 +346,30 @@ __device__ void body_small(typename F::T *sm, const typename F::Tw *stf, const t
     __syncthreads();
 }
 
+// A 32-byte row segment of a RowMajor tile moves as two 16-byte halves, the half
+// (lane >> 2) & 1 first: the eight lanes of a quarter warp then touch eight distinct
+// 16-byte bank groups for every row width (C = 8: two aligned row quads; C = 16, 32:
+// rows differing in the slot bit the half separates; C >= 64: segments sg and sg + 4).
+template <class T>
+__device__ __forceinline__ void seg_store(T *p, const T (&x)[32 / sizeof(T)]) {
+    constexpr int H = 16 / sizeof(T);
+    const uint32_t h = (threadIdx.x >> 2) & 1u;
+    const uint4 a = *reinterpret_cast<const uint4 *>(&x[0]);
+    const uint4 b = *reinterpret_cast<const uint4 *>(&x[H]);
+    uint4 *d = reinterpret_cast<uint4 *>(p);
+    d[h] = h ? b : a;
+    d[h ^ 1u] = h ? a : b;
+}
+template <class T>
+__device__ __forceinline__ void seg_load(T (&x)[32 / sizeof(T)], const T *p) {
+    constexpr int H = 16 / sizeof(T);
+    const uint32_t h = (threadIdx.x >> 2) & 1u;
+    const uint4 *s = reinterpret_cast<const uint4 *>(p);
+    const uint4 f = s[h], g = s[h ^ 1u];
+    *reinterpret_cast<uint4 *>(&x[0]) = h ? g : f;
+    *reinterpret_cast<uint4 *>(&x[H]) = h ? f : g;
+}
+
 // Row r of a pass-1 column group holds frequency f = brev(r); its C columns t = c0 + c
 // need the twiddles w_N^(t f): w_N^(c0 f) from the table, then powers of w_N^f.
 template <class F, int C>
@@ -379,17 +403,17 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
     for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
         const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
         const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG);
+        T x[SEG];
 #pragma unroll
-        for (int c = 0; c < SEG; ++c) sm[lay.at(r, sg * SEG + c)] = (bits >> c) & 1u;
+        for (int c = 0; c < SEG; ++c) x[c] = (bits >> c) & 1u;
+        seg_store<T>(sm + lay.at(r, sg * SEG), x);
     }
     __syncthreads();
     dif_columns<F, true>(sm, lay, logR1, logC, st);
     for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
         const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
         T x[SEG];
-        const uint4 *src = reinterpret_cast<const uint4 *>(sm + lay.at(r, sg * SEG));
-        *reinterpret_cast<uint4 *>(&x[0]) = src[0];
-        *reinterpret_cast<uint4 *>(&x[SEG / 2]) = src[1];
+        seg_load<T>(x, sm + lay.at(r, sg * SEG));
         row_twiddle<F, SEG>(x, tfwd, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
                             logN);
         uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
@@ -460,9 +484,7 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
         *reinterpret_cast<uint4 *>(&x[SEG / 2]) = __ldcg(g + 1);
         row_twiddle<F, SEG>(x, tinv, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
                             logN);
-        uint4 *d = reinterpret_cast<uint4 *>(sm + lay.at(r, sg * SEG));
-        d[0] = *reinterpret_cast<uint4 *>(&x[0]);
-        d[1] = *reinterpret_cast<uint4 *>(&x[SEG / 2]);
+        seg_store<T>(sm + lay.at(r, sg * SEG), x);
     }
     __syncthreads();
     dit_columns<F, true>(sm, lay, logR1, logC, st);
@@ -471,12 +493,14 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
         const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
         const uint64_t k0 = (uint64_t(r) << logS) + c0 + sg * SEG;
         if (k0 + SEG <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
+        T x[SEG];
+        seg_load<T>(x, sm + lay.at(r, sg * SEG));
         uint32_t byte = 0;
 #pragma unroll
         for (int c = 0; c < SEG; ++c) {
             const uint64_t k = k0 + c;
             if (k >= pr.K0 && k < uint64_t(pr.K0) + pr.out_len)
-                byte |= F::low_bit(F::mul_tw(sm[lay.at(r, sg * SEG + c)], scale)) << c;
+                byte |= F::low_bit(F::mul_tw(x[c], scale)) << c;
         }
         if (byte) {
             const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of SEG
