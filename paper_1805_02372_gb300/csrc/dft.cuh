@@ -256,4 +256,35 @@ __device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int l
     __syncthreads();
 }
 
+// For each of C column pairs (key column c, window column C + c): the last four forward
+// stages of both and acc[c] += the pointwise product Mul (field addition Add), where the
+// accumulator column c lives at acc_col0 + c. Groups are 16 consecutive rows (q = 1).
+template <class F, class Lay, class Mul, class Add>
+__device__ void product_acc_round(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                  int acc_col0, const typename F::Tw *twf, Mul mul, Add add) {
+    using T = typename F::T;
+    const int logG = logR - 4;
+    const int C = 1 << logC;
+    const int total = 1 << (logG + logC);
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int g = w & ((1 << logG) - 1), c = w >> logG;
+        const int i0 = g << 4;
+        T x[16], y[16];
+        int ax[16], ay[16], az[16];
+        lay.template addrs<0, 16>(i0, c, ax);
+        lay.template addrs<0, 16>(i0, C + c, ay);
+        lay.template addrs<0, 16>(i0, acc_col0 + c, az);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            x[k] = sm[ax[k]];
+            y[k] = sm[ay[k]];
+        }
+        dif_group<F, 4>(x, twf, 0, 1);
+        dif_group<F, 4>(y, twf, 0, 1);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sm[az[k]] = add(sm[az[k]], mul(x[k], y[k]));
+    }
+    __syncthreads();
+}
+
 }  // namespace pa

@@ -73,7 +73,8 @@ enum : uint32_t {
     IT_FD_P1 = 4,
     IT_FD_P2 = 5,
     IT_FD_SUM = 6,
-    IT_FD_P3 = 7
+    IT_FD_P3 = 7,
+    IT_FD_STREAM = 8
 };
 
 // A transform of a launch: a standard tile pair, an fd spectrum or an fd output sum.
@@ -94,12 +95,16 @@ struct NttTile {
 };
 
 // One block under transform-domain accumulation.
+// Streamed blocks (one output tile) skip the separate forward pass 2: their sum items
+// run it on the key-tile and window rows they read.
 struct FdBlock {
     uint64_t x_off;   // element offset of key spectrum 0 (key spectra at stride N)
     uint64_t w_off;   // element offset of window spectrum 0 (stride N)
     uint64_t wmap;    // first entry of the block's P x Q window-index table
     uint32_t Q;       // key tiles
     uint32_t nfwd2;   // forward pass-2 items of the block (all precede every sum)
+    uint32_t nfwd1;   // forward pass-1 items of the block (streamed sums wait for all)
+    uint32_t pad;
 };
 
 // Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
@@ -599,6 +604,59 @@ __device__ void body_sum_inv_last(typename F::T *sm, const typename F::Tw *sti, 
     __syncthreads();
 }
 
+// Streamed sum for a block with one output tile: for each key tile J, rows of row group
+// rg of X_J and W_{wrow[J]} (after their forward pass 1) get the forward pass 2 in shared
+// memory and their product is added to an accumulator; the accumulator then gets the
+// inverse pass 2 and is written to Z. Shared memory: key, window and accumulator
+// columns (3 C columns of R2 rows).
+template <class F>
+__device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
+                                const typename F::Tw *sti, uint64_t rg, int logR2, int logC,
+                                const typename F::T *__restrict__ X,
+                                const typename F::T *__restrict__ W,
+                                const uint32_t *__restrict__ wrow, uint32_t Q, uint64_t N,
+                                typename F::T *__restrict__ Z) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int C = 1 << logC;
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    T *acc = sm + 2 * C * lay.cs;
+    for (int e = threadIdx.x; e < C * lay.cs; e += blockDim.x) acc[e] = 0;
+    for (uint32_t J = 0; J < Q; ++J) {
+        const T *xj = X + uint64_t(J) * N + base;
+        const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
+        for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
+            const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
+            const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                sm[lay.at(r + k, c)] = xs[k];
+                sm[lay.at(r + k, C + c)] = ws[k];
+            }
+        }
+        __syncthreads();
+        dif_columns_head<F, false>(sm, lay, logR2, logC + 1, stf);
+        product_acc_round<F>(sm, lay, logR2, logC, 2 * C, stf,
+                             [](T a, T b) { return F::mont(a, b); },
+                             [](T a, T b) { return F::add(a, b); });
+    }
+    dit_columns<F, false>(acc, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = acc[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(Z + base + e), ov);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- the persistent kernel
 //
 // CTAs pull items from the list with an atomic counter; the list is ordered so that
@@ -606,7 +664,8 @@ __device__ void body_sum_inv_last(typename F::T *sm, const typename F::Tw *sti, 
 // CTAs, so every wait ends. Waits are bounded anyway: on timeout the status word gets
 // PA_ERR_TIMEOUT and the item's body is skipped.
 // Counters: c1/c2/c3 per tile (pass 1, 2, 3 items done), then the list position, then
-// one per fd block (forward pass-2 items done).
+// per fd block the forward pass-2 items done, then per fd block the forward pass-1 items
+// done.
 
 template <class F>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
@@ -614,15 +673,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
     const FdBlock *__restrict__ fds, const uint32_t *__restrict__ wmap,
     const BlockPtrs *__restrict__ blks, BlockPtrs one, typename F::T *__restrict__ ws,
     const typename F::Tw *__restrict__ stage, const typename F::Tw *__restrict__ tfwd,
-    const typename F::Tw *__restrict__ tinv, uint32_t *cnt, uint32_t ntiles, uint32_t slots,
-    int *status) {
+    const typename F::Tw *__restrict__ tinv, uint32_t *cnt, uint32_t ntiles, uint32_t nfd,
+    uint32_t slots, int *status) {
     using T = typename F::T;
     using Tw = typename F::Tw;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint64_t cur;
     __shared__ int flag;
     uint32_t *c1 = cnt, *c2 = cnt + ntiles, *c3 = cnt + 2 * uint64_t(ntiles);
-    uint32_t *next = cnt + 3 * uint64_t(ntiles), *cfd = next + 1;
+    uint32_t *next = cnt + 3 * uint64_t(ntiles), *cfd = next + 1, *cfd1 = cfd + nfd;
     Tw *st0 = reinterpret_cast<Tw *>(smraw);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -688,6 +747,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp,
                                   static_cast<int>(tl.which), sub, logN, logR1, logC1, X, tfwd);
                 signal_count(c1 + ti);
+                if (threadIdx.x == 0) atomicAdd(cfd1 + tl.fd, 1u);  // fenced by signal_count
                 break;
             }
             case IT_FD_P2: {
@@ -705,6 +765,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                                          logC2, ws + fb.x_off, ws + fb.w_off,
                                          wmap + fb.wmap + uint64_t(tl.out) * fb.Q, fb.Q,
                                          uint64_t(1) << logN, X);
+                signal_count(c2 + ti);
+                break;
+            }
+            case IT_FD_STREAM: {
+                const FdBlock fb = fds[tl.fd];
+                Tw *sti = st0 + (1 << logR2);
+                load_stage<F>(st0, stage, 0, logR2);
+                load_stage<F>(sti, stage, 1, logR2);
+                if (wait_count(cfd1 + tl.fd, fb.nfwd1, status, &flag))
+                    body_stream_sum<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
+                                       logC2, ws + fb.x_off, ws + fb.w_off, wmap + fb.wmap, fb.Q,
+                                       uint64_t(1) << logN, X);
                 signal_count(c2 + ti);
                 break;
             }
@@ -770,10 +842,22 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
     *windows = P * Q;
     if (k <= static_cast<uint32_t>(kLogSmallMax) || fd_mode == 1 || P * Q < 2 || P * Q > kFdMaxPairs)
         return std_units;
-    const uint64_t W = count_windows(P, Q, M, L);
     const size_t elem = path == PA_PATH_NTT64 ? 8 : 4;
-    if (double(Q + W + P) * N * elem > double(kFdMaxBytes)) return std_units;
     const double tr = N * (k + 6) / 3.0;
+    if (P == 1) {
+        // streamed: the forward pass 2 of each key tile and window runs inside the sum,
+        // so 2Q forward transforms and one inverse replace 3Q
+        if (double(2 * Q) * N * elem > double(kFdMaxBytes)) return std_units;
+        const double sc = double(Q) * (2 * tr + N + 4096.0) + tr + 4096.0;
+        if (fd_mode == 2 || sc < 0.95 * std_units * pair) {
+            *fd = 2;
+            *windows = Q;
+            return sc / pair;
+        }
+        return std_units;
+    }
+    const uint64_t W = count_windows(P, Q, M, L);
+    if (double(Q + W + P) * N * elem > double(kFdMaxBytes)) return std_units;
     const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(P) * (tr + N + 1024.0) +
                        double(P) * double(Q) * 3.0 * N;
     if (fd_mode == 2 || fdc < 0.85 * std_units * pair) {
@@ -913,12 +997,14 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
                            const std::pair<int64_t, uint64_t> &b2) { return a.first == b2.first; }),
             u.end());
     const uint64_t W = u.size();
+    const bool streamed = c.fd == 2;
     fb->x_off = 0;
     fb->w_off = Q * N;
     fb->wmap = wmap->size();
     fb->Q = static_cast<uint32_t>(Q);
     const NttTile shape = tile_shape(c.log2n, field);
-    fb->nfwd2 = static_cast<uint32_t>((Q + W) * shape.g2);
+    fb->nfwd2 = streamed ? 0u : static_cast<uint32_t>((Q + W) * shape.g2);
+    fb->nfwd1 = static_cast<uint32_t>((Q + W) * shape.g1);
     for (uint64_t I = 0; I < P; ++I)
         for (uint64_t J = 0; J < Q; ++J) {
             const int64_t off = d[I * Q + J].first;
@@ -947,9 +1033,17 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
         t.fd = fd_index;
         t.out = static_cast<uint32_t>(I);
         t.ws_off = (Q + W + I) * N;
+        if (streamed) {
+            // half the rows per sum item (key, window and accumulator columns share the
+            // shared memory two columns sets use elsewhere); the sum of row group rg
+            // overwrites rows rg of X_0, which only that item reads
+            t.logC2 = shape.logC2 - 1;
+            t.g2 = shape.g2 * 2;
+            t.ws_off = 0;
+        }
         sums->push_back(t);
     }
-    *elems = (Q + W + P) * N;
+    *elems = streamed ? (Q + W) * N : (Q + W + P) * N;
 }
 
 }  // namespace
@@ -960,22 +1054,29 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     if (field < 0 || field >= kNumFields) return PA_ERR_INVALID;
     info->field = field;
     const size_t elem = field == kFieldF64 ? 8 : 4, twsz = 8;
-    std::vector<NttTile> big, small, fd_spec, fd_sum;
+    // fd_*: blocks with accumulation over several output tiles; st_*: streamed blocks
+    // (one output tile), with the range of their spectra in st_spec
+    std::vector<NttTile> big, small, fd_spec, fd_sum, st_spec, st_sum;
+    std::vector<std::pair<size_t, size_t>> st_range;
     std::vector<FdBlock> fds;
     std::vector<uint32_t> wmap;
-    std::vector<uint64_t> fd_base;  // fd-storage offset of each fd block
     uint64_t fd_elems = 0;
     for (const BatchBlock &b : blocks) {
         if (b.tr.fd) {
             if (b.tr.log2n <= static_cast<uint32_t>(kLogSmallMax) ||
-                b.tr.tiles_in * b.tr.tiles_out > kFdMaxPairs)
+                b.tr.tiles_in * b.tr.tiles_out > kFdMaxPairs || b.tr.fd > 2 ||
+                (b.tr.fd == 2 && b.tr.tiles_out != 1))
                 return PA_ERR_INVALID;
-            const size_t s0 = fd_spec.size(), u0 = fd_sum.size();
+            const bool streamed = b.tr.fd == 2;
+            std::vector<NttTile> &spec = streamed ? st_spec : fd_spec;
+            std::vector<NttTile> &sum = streamed ? st_sum : fd_sum;
+            const size_t s0 = spec.size(), u0 = sum.size();
             FdBlock fb{};
             uint64_t el = 0;
-            build_fd(b, field, static_cast<uint32_t>(fds.size()), &fd_spec, &fd_sum, &fb, &wmap, &el);
-            for (size_t i = s0; i < fd_spec.size(); ++i) fd_spec[i].ws_off += fd_elems;
-            for (size_t i = u0; i < fd_sum.size(); ++i) fd_sum[i].ws_off += fd_elems;
+            build_fd(b, field, static_cast<uint32_t>(fds.size()), &spec, &sum, &fb, &wmap, &el);
+            for (size_t i = s0; i < spec.size(); ++i) spec[i].ws_off += fd_elems;
+            for (size_t i = u0; i < sum.size(); ++i) sum[i].ws_off += fd_elems;
+            if (streamed) st_range.push_back({s0, spec.size()});
             fb.x_off += fd_elems;
             fb.w_off += fd_elems;
             fd_elems += el;
@@ -1004,8 +1105,8 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     if (slots > big.size()) slots = big.size();
     for (size_t i = 0; i < big.size(); ++i) big[i].ws_off = (i % (slots ? slots : 1)) * slot_elems;
     const uint64_t fd_origin = uint64_t(slots) * slot_elems;  // fd storage after the slots
-    for (NttTile &t : fd_spec) t.ws_off += fd_origin;
-    for (NttTile &t : fd_sum) t.ws_off += fd_origin;
+    for (std::vector<NttTile> *v : {&fd_spec, &fd_sum, &st_spec, &st_sum})
+        for (NttTile &t : *v) t.ws_off += fd_origin;
     for (FdBlock &f : fds) {
         f.x_off += fd_origin;
         f.w_off += fd_origin;
@@ -1018,6 +1119,10 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     tiles.insert(tiles.end(), fd_spec.begin(), fd_spec.end());
     const size_t i_sum = tiles.size();
     tiles.insert(tiles.end(), fd_sum.begin(), fd_sum.end());
+    const size_t i_sspec = tiles.size();
+    tiles.insert(tiles.end(), st_spec.begin(), st_spec.end());
+    const size_t i_ssum = tiles.size();
+    tiles.insert(tiles.end(), st_sum.begin(), st_sum.end());
     if (tiles.size() >= (size_t(1) << 28)) return PA_ERR_UNSUPPORTED;
     std::vector<uint64_t> items;
     auto push = [&items](uint64_t type, uint64_t ti, uint64_t sub) {
@@ -1037,6 +1142,18 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
             for (uint32_t k = 0; k < big[t - 1].g2; ++k) push(IT_P2, t - 1, k);
         if (t >= 2 && t - 2 < nb)
             for (uint32_t k = 0; k < big[t - 2].g1; ++k) push(IT_P3, t - 2, k);
+    }
+    // streamed blocks, pipelined the same way: pass 1 of all spectra of block t, the
+    // sums of block t-1, inverse pass 1 of block t-2
+    const size_t ns = st_sum.size();
+    for (size_t t = 0; t < ns + 2; ++t) {
+        if (t < ns)
+            for (size_t i = st_range[t].first; i < st_range[t].second; ++i)
+                for (uint32_t k = 0; k < st_spec[i].g1; ++k) push(IT_FD_P1, i_sspec + i, k);
+        if (t >= 1 && t - 1 < ns)
+            for (uint32_t k = 0; k < st_sum[t - 1].g2; ++k) push(IT_FD_STREAM, i_ssum + t - 1, k);
+        if (t >= 2 && t - 2 < ns)
+            for (uint32_t k = 0; k < st_sum[t - 2].g1; ++k) push(IT_FD_P3, i_ssum + t - 2, k);
     }
     // fd sums row group by row group (the outputs of one block share their operands'
     // rows in L2), then the inverse first passes
@@ -1071,6 +1188,10 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
                                       size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
         }
     }
+    // streamed sums: key, window and accumulator columns
+    for (const NttTile &t : st_sum)
+        smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
+                                  size_t(ColMajor::words(1 << t.logR2, 3 << t.logC2)) * elem);
     info->smem = smem;
     // workspace layout
     size_t off = 0;
@@ -1083,7 +1204,7 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     info->off_wmap = off;
     off = align256(off + wmap.size() * sizeof(uint32_t));
     info->off_counters = off;
-    info->counter_bytes = (3 * tiles.size() + 1 + fds.size()) * sizeof(uint32_t);
+    info->counter_bytes = (3 * tiles.size() + 1 + 2 * fds.size()) * sizeof(uint32_t);
     off = align256(off + info->counter_bytes);
     info->off_spec = off;
     off = align256(off + (size_t(info->slots) * slot_elems + fd_elems) * elem);
@@ -1187,7 +1308,7 @@ int launch_field(const NttLayout &lay, void *ws, const BlockPtrs *blks, const Bl
         reinterpret_cast<const uint32_t *>(b + lay.off_wmap), blks, one,
         reinterpret_cast<typename F::T *>(b + lay.off_spec), static_cast<const Tw *>(tab.stage),
         static_cast<const Tw *>(tab.fwd), static_cast<const Tw *>(tab.inv), cnt,
-        static_cast<uint32_t>(lay.ntiles), lay.slots, status);
+        static_cast<uint32_t>(lay.ntiles), static_cast<uint32_t>(lay.nfd), lay.slots, status);
     prof_end(prof, s);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;

@@ -17,6 +17,11 @@ GEOMS = [(50_003, 20_011, 13, 4096, 4096), (50_003, 20_011, 13, 4096, 2048),
          (200_000, 3_000, 13, 4096, 1024), (9_000, 200_000, 13, 1024, 4096)]
 
 
+# one output tile, several key tiles: streamed accumulation (n, m, log2 N, L, M)
+STREAMED = [(50_003, 3_000, 13, 4096, 3008), (131_075, 5_000, 14, 8192, 5056),
+            (8_191, 1, 13, 4096, 64), (1_000_003, 60_000, 17, 70_016, 60_032)]
+
+
 def brute_windows(n, m, L, M):
     P, Q = -(-m // M), -(-n // L)
     return len({i * M - j * L for i in range(P) for j in range(Q)})
@@ -93,3 +98,19 @@ def test_prime_choice(lib):
         with pytest.raises(pkg.PAError):
             q(1_000, 5, binding.make_opts(path="ntt31", ntt_prime=bad))
     assert q(1_000, 5, binding.make_opts(path="direct"))["prime_bits"] == 0
+
+
+@pytest.mark.parametrize("path", ["ntt31", "ntt64"])
+@pytest.mark.parametrize("n,m,k,L,M", STREAMED)
+def test_streamed_plan(lib, path, n, m, k, L, M):
+    d = pkg.pa_plan_query(n, m, binding.make_opts(path=path, log2_transform=k, tile_in=L,
+                                                  tile_out=M, fd_mode=2))
+    assert d["tiles_out"] == 1 and d["tiles_in"] == -(-n // L) > 1
+    assert d["fd"] == 2 and d["windows"] == d["tiles_in"] == brute_windows(n, m, L, M)
+
+
+def test_streamed_chosen_for_batched_shapes(lib):
+    # n = 4e6, m = 2e6 at N = 2^22 is two key tiles and one output tile: the model
+    # prices 2Q + 1 transforms below 3Q
+    d = pkg.pa_plan_query(4_000_000, 2_000_000, binding.make_opts(path="ntt31"))
+    assert d["tiles_out"] == 1 and d["tiles_in"] >= 2 and d["fd"] == 2

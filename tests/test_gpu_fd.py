@@ -35,6 +35,24 @@ def test_fd_matches_oracle(path, prime, n, m, k, L, M):
     assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
 
 
+# one output tile, several key tiles: streamed accumulation (n, m, log2 N, L, M)
+STREAMED = [(50_003, 3_000, 13, 4096, 3008), (131_075, 5_000, 14, 8192, 5056),
+            (8_191, 1, 13, 4096, 64), (1_000_003, 60_000, 17, 70_016, 60_032)]
+
+
+@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("n,m,k,L,M", STREAMED)
+def test_streamed_matches_oracle(path, prime, n, m, k, L, M):
+    blk = inputs.single_block(n, m, 41 + n, 43 + m)
+    key, seed = blk.key(), blk.seed()
+    want = oracle.hash_full(n, m, seed, key)
+    got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
+                         fd_mode=2, ntt_prime=prime)
+    assert desc["fd"] == 2 and desc["tiles_out"] == 1
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
+
+
 @pytest.mark.parametrize("kind", ["ones", "seed_ones"])
 def test_fd_largest_coefficients(kind):
     # all-ones inputs give the largest sums (every coefficient counts L products per key
@@ -53,7 +71,7 @@ def test_fd_largest_coefficients(kind):
 def test_fd_and_standard_tiles_in_one_launch():
     import torch
     shapes = [(50_003, 20_011), (3_001, 1_000), (20_000, 9_000), (1, 1), (70_001, 64),
-              (8_191, 8_193)]
+              (8_191, 8_193), (60_007, 3_001), (40_001, 100)]
     bl = [inputs.single_block(n, m, 500 + 2 * i, 501 + 2 * i) for i, (n, m) in enumerate(shapes)]
     keys, seeds = [b.key() for b in bl], [b.seed() for b in bl]
     kd, sd = [dev(k) for k in keys], [dev(s) for s in seeds]
@@ -64,7 +82,7 @@ def test_fd_and_standard_tiles_in_one_launch():
     batch = pkg.pa_batch_plan(desc, opts)
     try:
         plans = pkg.pa_batch_describe(batch, len(bl))
-        assert {d["fd"] for d in plans} == {0, 1}
+        assert {d["fd"] for d in plans} == {0, 1, 2}
         for run in range(3):  # first run captures the graph, later runs replay it
             for o in od:
                 o.fill_(-1)
