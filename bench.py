@@ -238,8 +238,10 @@ def _source_digest(paths):
 CSRC = "paper_1805_02372_gb300/csrc/"
 KERNEL_SOURCES = {
     "direct": [CSRC + "direct.cu", CSRC + "common.cuh"],
-    "batch_persistent": [CSRC + "ntt.cu", CSRC + "dft.cuh", CSRC + "ntt_field.cuh",
-                         CSRC + "tiles.cuh", CSRC + "common.cuh"],
+    "batch_persistent": [CSRC + "ntt.cu", CSRC + "ntt_defs.cuh", CSRC + "ntt_kernel.cuh",
+                         CSRC + "ntt_f29.cu", CSRC + "ntt_f31.cu", CSRC + "ntt_f64.cu",
+                         CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh",
+                         CSRC + "common.cuh"],
     "fft_tile": [CSRC + "fft.cu", CSRC + "dft.cuh", CSRC + "tiles.cuh"],
     "block_mma": [CSRC + "block.cu", CSRC + "common.cuh"],
 }
@@ -347,7 +349,7 @@ def traffic_for(kernel: str):
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_gbps(blocks, rows_per_block: int = 1024, seed: int = 3, max_blocks: int = 256):
+def cpu_oracle_gbps(blocks, rows_per_block: int = 5120, seed: int = 3, max_blocks: int = 256):
     """The oracle as it stands (all host cores), timed on a bounded sample of each block.
 
     The oracle's full hash of a block is one set-up (seed reversal, key masking) plus m row
@@ -433,7 +435,7 @@ def run_reference(args):
     for _ in range(min(args.warmup, 1)):
         cpu_oracle_gbps(blocks, rows_per_block=64, max_blocks=8)
     for k in range(args.steps):
-        g, cores, desc = cpu_oracle_gbps(blocks, seed=100 + k, max_blocks=64)
+        g, cores, desc = cpu_oracle_gbps(blocks, rows_per_block=1024, seed=100 + k, max_blocks=64)
         per_step.append(g)
     val = float(np.mean(per_step))
     total_bits = sum(b.n for b in blocks)

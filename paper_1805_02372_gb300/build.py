@@ -36,6 +36,12 @@ def _flags(extra=()):
                    "--expt-relaxed-constexpr"] + list(extra)
 
 
+# Per-source extra flags. The 64-bit-prime persistent kernel inlines 128-bit products
+# into every radix-16 round; NVVM's -O3 pipeline takes minutes on it and ends with
+# spills, -O2 takes about a minute and allocates it without spills.
+PER_SOURCE = {"ntt_f64.cu": ["-Xcicc", "-O2"]}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -48,6 +54,7 @@ def _stamp(srcs, extra) -> str:
         with open(p, "rb") as f:
             h.update(p.encode() + f.read())
     h.update(" ".join(_flags(extra)).encode())
+    h.update(repr(sorted(PER_SOURCE.items())).encode())
     return h.hexdigest()
 
 
@@ -66,7 +73,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc] + _flags(extra) + ["-c", src, "-o", obj]
+        cmd = [cc] + _flags(extra) + PER_SOURCE.get(os.path.basename(src), []) + [
+            "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

@@ -1,0 +1,99 @@
+// Shared definitions of the exact transform path: limits, work-item encoding, the
+// launch's tile and block descriptors, the per-device twiddle tables and the
+// per-field launch entry points (each prime field's persistent kernel is compiled
+// in a translation unit of its own).
+#pragma once
+
+#include <algorithm>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "ntt_field.cuh"
+#include "tiles.cuh"
+
+namespace pa {
+
+constexpr int kLogMax = 22;           // largest transform: 2^22
+constexpr int kLogSmallMax = 12;      // one-CTA transforms up to 2^12
+constexpr int kThreads = 512;
+// Two CTAs of 512 threads per SM for the 32-bit field (<= 64 registers), one for 64-bit.
+template <class F>
+constexpr int kMinBlocks = sizeof(typename F::T) == 4 ? 2 : 1;
+
+// Transform-domain accumulation limits: tile pairs of one block (host tables) and
+// spectra bytes of one block.
+constexpr uint64_t kFdMaxPairs = uint64_t(1) << 22;
+constexpr uint64_t kFdMaxBytes = uint64_t(32) << 30;
+
+// Work-item types (bits 60..63 of an item; bits 32..59 tile index, 0..31 sub-index).
+enum : uint32_t {
+    IT_SMALL = 0,
+    IT_P1 = 1,
+    IT_P2 = 2,
+    IT_P3 = 3,
+    IT_FD_P1 = 4,
+    IT_FD_P2 = 5,
+    IT_FD_SUM = 6,
+    IT_FD_P3 = 7,
+    IT_FD_STREAM = 8
+};
+
+// A transform of a launch: a standard tile pair, an fd spectrum or an fd output sum.
+struct NttTile {
+    TilePair p;       // geometry (fd key spectrum: its key tile; window: a pair with
+                      // that offset; output sum: the pair (I, 0))
+    uint64_t ws_off;  // element offset of the spectrum (standard: the key spectrum, the
+                      // window spectrum follows)
+    uint64_t scale;   // final scale as the bits of F::Tw
+    uint32_t logN, logR1, logR2;
+    uint32_t g1;      // pass-1 column groups (per input)
+    uint32_t g2;      // pass-2 row groups
+    uint32_t logC1;   // pass-1/3 columns per item (log2)
+    uint32_t logC2;   // pass-2 rows per item (log2)
+    uint32_t which;   // fd spectra: 0 key tile, 1 seed window
+    uint32_t fd;      // fd spectra and sums: index of the fd block
+    uint32_t out;     // fd sums: output tile index I
+};
+
+// One block under transform-domain accumulation.
+// Streamed blocks (one output tile) skip the separate forward pass 2: their sum items
+// run it on the key-tile and window rows they read.
+struct FdBlock {
+    uint64_t x_off;   // element offset of key spectrum 0 (key spectra at stride N)
+    uint64_t w_off;   // element offset of window spectrum 0 (stride N)
+    uint64_t wmap;    // first entry of the block's P x Q window-index table
+    uint32_t Q;       // key tiles
+    uint32_t nfwd2;   // forward pass-2 items of the block (all precede every sum)
+    uint32_t nfwd1;   // forward pass-1 items of the block (streamed sums wait for all)
+    uint32_t pad;
+};
+
+// Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
+// segment, and enough to give a 512-thread CTA about 8192 (32-bit) elements per item.
+inline void pass_columns(int logN, size_t elem, int *logC1, int *logC2) {
+    const int logR1 = (logN + 1) / 2, logR2 = logN / 2, logS = logN - logR1;
+    const int target = elem == 4 ? 13 : 12;
+    int c1 = std::max(elem == 4 ? 3 : 2, target - logR1);
+    int c2 = std::max(elem == 4 ? 2 : 1, target - logR2);
+    *logC1 = std::min(c1, logS);
+    *logC2 = std::min(c2, logR1);
+}
+
+// Per-device tables: fwd[e] = w^e, inv[e] = w^-e for e < 2^(kLogMax-1), w of order 2^kLogMax.
+struct Tables {
+    void *fwd = nullptr, *inv = nullptr;
+    void *stage = nullptr;  // compact stage tables, see stage_table()
+};
+constexpr int kStageBlock = 4096;  // entries per (direction, log2 R) block
+
+// The tables of a field on the current device, built and uploaded on first use.
+int ntt_tables(int field, Tables *out);
+
+// One persistent launch of a field's work list (ntt_f29.cu, ntt_f31.cu, ntt_f64.cu).
+#define PA_NTT_LAUNCH_ARGS const NttLayout &lay, void *ws, const BlockPtrs *blks, \
+    const BlockPtrs &one, int *status, Prof *prof, cudaStream_t s
+int ntt_launch_f29(PA_NTT_LAUNCH_ARGS);
+int ntt_launch_f31(PA_NTT_LAUNCH_ARGS);
+int ntt_launch_f64(PA_NTT_LAUNCH_ARGS);
+
+}  // namespace pa

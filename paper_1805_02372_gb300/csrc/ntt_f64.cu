@@ -1,0 +1,11 @@
+// Persistent NTT launch over the prime field F64 (see ntt_kernel.cuh); one field per
+// translation unit so the three instantiations compile in parallel.
+#include "ntt_kernel.cuh"
+
+namespace pa {
+
+int ntt_launch_f64(PA_NTT_LAUNCH_ARGS) {
+    return launch_field<F64>(lay, ws, blks, one, status, prof, s);
+}
+
+}  // namespace pa

@@ -1,0 +1,582 @@
+// Device side of the exact transform path: the tile bodies (bit unpacking, four-step
+// passes, pointwise products, transform-domain sums, output bits) and the persistent
+// kernel that runs a work list of them, plus its host launch. Included once per
+// prime field by ntt_f29.cu, ntt_f31.cu and ntt_f64.cu.
+#pragma once
+
+#include <string.h>
+
+#include "ntt_defs.cuh"
+#include "dft.cuh"
+
+namespace pa {
+namespace {
+
+// ---------------------------------------------------------------- device pieces
+
+// Copy the compact stage table of an R-point transform (dir 0: forward, 1: inverse).
+template <class F>
+__device__ __forceinline__ void load_stage(typename F::Tw *st, const typename F::Tw *__restrict__ stage,
+                                           int dir, int logR) {
+    const typename F::Tw *src = stage + (size_t(dir) * (kLogSmallMax + 1) + logR) * kStageBlock;
+    for (int idx = threadIdx.x; idx < (1 << logR) - 1; idx += blockDim.x) st[idx] = src[idx];
+}
+
+// Twiddle w^E (E < 2^kLogMax) from a half table: w^(E + 2^(kLogMax-1)) = -w^E.
+template <class F>
+__device__ __forceinline__ typename F::Tw tw_at(const typename F::Tw *__restrict__ tab, uint32_t E) {
+    constexpr uint32_t half = 1u << (kLogMax - 1);
+    if (E < half) return tab[E];
+    return F::neg_tw(tab[E - half]);
+}
+
+// ---------------------------------------------------------------- tile bodies
+// Each body is run by all threads of a CTA, with its stage tables already in shared
+// memory; the standalone kernels and the persistent batched kernel call the same bodies.
+
+// 32 consecutive bits of the key tile (which = 0) or window (which = 1) starting at tile
+// position t; positions outside the tile or the string read as 0.
+__device__ __forceinline__ uint32_t tile_bits(const TilePair &pr, const BlockPtrs &bp, int which,
+                                              uint64_t t) {
+    uint32_t v = 0;
+    if (which == 0) {
+        if (t >= pr.key_len) return 0u;
+        const uint64_t pos = uint64_t(pr.key_bit0) + t;
+        const uint64_t kw = 2 * ((bp.n + 63) >> 6);
+        v = bits32_at(bp.key32, kw, static_cast<int64_t>(pos));
+        const uint64_t left = pr.key_len - t;  // valid bits from t
+        if (left < 32) v &= (1u << left) - 1u;
+    } else {
+        if (t >= pr.win_len) return 0u;
+        const int64_t pos = pr.win_bit0 + static_cast<int64_t>(t);
+        const uint64_t sl = bp.n + bp.m - 1;  // seed length
+        const uint64_t sw = 2 * ((sl + 63) >> 6);
+        v = bits32_at(bp.seed32, sw, pos);
+        // positions >= seed length or >= window length read as 0 (< 0 handled by bits32_at)
+        const int64_t lim1 = static_cast<int64_t>(sl) - pos;
+        const int64_t lim2 = static_cast<int64_t>(pr.win_len - t);
+        const int64_t lim = lim1 < lim2 ? lim1 : lim2;
+        if (lim <= 0) return 0u;
+        if (lim < 32) v &= (1u << lim) - 1u;
+    }
+    return v;
+}
+
+// Whole transform of size 2^logN <= 2^12 in shared memory for one tile.
+template <class F>
+__device__ void body_small(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
+                           const TilePair &pr, const BlockPtrs &bp, int logN, typename F::Tw scale) {
+    using T = typename F::T;
+    const int N = 1 << logN;
+    const ColMajor lay{ColMajor::stride(N)};
+    // 32 tile positions per thread from one or two 32-bit words of each input
+    for (int t0 = threadIdx.x * 32; t0 < N; t0 += blockDim.x * 32) {
+        const uint32_t kb = tile_bits(pr, bp, 0, t0), wb = tile_bits(pr, bp, 1, t0);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            sm[lay.at(t0 + k, 0)] = (kb >> k) & 1u;
+            sm[lay.at(t0 + k, 1)] = (wb >> k) & 1u;
+        }
+    }
+    __syncthreads();
+    const auto mul = [](T a, T b) { return F::mont(a, b); };
+    if (logN >= 4) {
+        dif_columns_head<F, false>(sm, lay, logN, 1, stf);
+        product_round<F>(sm, lay, logN, 0, stf, sti, mul);
+        dit_columns_tail<F, false>(sm + lay.cs, lay, logN, 0, sti);
+    } else {
+        dif_columns<F, false>(sm, lay, logN, 1, stf);
+        for (int t = threadIdx.x; t < N; t += blockDim.x)
+            sm[lay.at(t, 1)] = F::mont(sm[lay.at(t, 0)], sm[lay.at(t, 1)]);
+        __syncthreads();
+        dit_columns<F, false>(sm + lay.cs, lay, logN, 0, sti);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nw = (pr.out_len + 31) / 32;
+    for (uint32_t w = warp; w < nw; w += blockDim.x / 32) {
+        const uint32_t v = w * 32 + lane;
+        uint32_t bit = 0;
+        if (v < pr.out_len) bit = F::low_bit(F::mul_tw(sm[lay.at(pr.K0 + v, 1)], scale));
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+        if (lane == 0 && word) atomicXor(bp.out32 + (pr.out_bit0 >> 5) + w, word);
+    }
+    __syncthreads();
+}
+
+// A 32-byte row segment of a RowMajor tile moves as two 16-byte halves, the half
+// (lane >> 2) & 1 first: the eight lanes of a quarter warp then touch eight distinct
+// 16-byte bank groups for every row width (C = 8: two aligned row quads; C = 16, 32:
+// rows differing in the slot bit the half separates; C >= 64: segments sg and sg + 4).
+template <class T>
+__device__ __forceinline__ void seg_store(T *p, const T (&x)[32 / sizeof(T)]) {
+    constexpr int H = 16 / sizeof(T);
+    const uint32_t h = (threadIdx.x >> 2) & 1u;
+    const uint4 a = *reinterpret_cast<const uint4 *>(&x[0]);
+    const uint4 b = *reinterpret_cast<const uint4 *>(&x[H]);
+    uint4 *d = reinterpret_cast<uint4 *>(p);
+    d[h] = h ? b : a;
+    d[h ^ 1u] = h ? a : b;
+}
+template <class T>
+__device__ __forceinline__ void seg_load(T (&x)[32 / sizeof(T)], const T *p) {
+    constexpr int H = 16 / sizeof(T);
+    const uint32_t h = (threadIdx.x >> 2) & 1u;
+    const uint4 *s = reinterpret_cast<const uint4 *>(p);
+    const uint4 f = s[h], g = s[h ^ 1u];
+    *reinterpret_cast<uint4 *>(&x[0]) = h ? g : f;
+    *reinterpret_cast<uint4 *>(&x[H]) = h ? f : g;
+}
+
+// Row r of a pass-1 column group holds frequency f = brev(r); its C columns t = c0 + c
+// need the twiddles w_N^(t f): w_N^(c0 f) from the table, then powers of w_N^f.
+template <class F, int C>
+__device__ __forceinline__ void row_twiddle(typename F::T (&x)[C], const typename F::Tw *tab,
+                                            uint64_t c0, uint32_t f, int logN) {
+    const int sh = kLogMax - logN;
+    const typename F::Tw w0 = tw_at<F>(tab, static_cast<uint32_t>((c0 * f) << sh));
+    const typename F::Tw step = tw_at<F>(tab, f << sh);
+    typename F::T wf = F::full_form(w0);
+    x[0] = F::mul_tw(x[0], w0);
+#pragma unroll
+    for (int c = 1; c < C; ++c) {
+        wf = F::step_full(wf, step);
+        x[c] = F::mul_full(x[c], wf);
+    }
+}
+
+// Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1); each
+// thread handles 32-byte row segments (SEG columns).
+template <class F>
+__device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
+                               const BlockPtrs &bp, int which, uint64_t cg, int logN, int logR1,
+                               int logC, typename F::T *__restrict__ dst,
+                               const typename F::Tw *__restrict__ tfwd) {
+    using T = typename F::T;
+    constexpr int SEG = 32 / sizeof(T), logSEG = sizeof(T) == 4 ? 3 : 2;
+    const int R1 = 1 << logR1, logS = logN - logR1, C = 1 << logC;
+    const uint64_t c0 = cg << logC;
+    const RowMajor lay{logC};
+    const int seglog = logC - logSEG;  // segments per row (log2)
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG);
+        T x[SEG];
+#pragma unroll
+        for (int c = 0; c < SEG; ++c) x[c] = (bits >> c) & 1u;
+        seg_store<T>(sm + lay.at(r, sg * SEG), x);
+    }
+    __syncthreads();
+    dif_columns<F, true>(sm, lay, logR1, logC, st);
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        T x[SEG];
+        seg_load<T>(x, sm + lay.at(r, sg * SEG));
+        row_twiddle<F, SEG>(x, tfwd, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
+                            logN);
+        uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
+        __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
+        __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[SEG / 2]));
+    }
+    __syncthreads();
+    (void)C;
+}
+
+// Pass 2 of both spectra (rows of R2 = 2^logR2, C2 rows from row group rg), the pointwise
+// product and the inverse pass 2; X = key spectrum, W = window spectrum.
+template <class F>
+__device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
+                                const typename F::Tw *sti, uint64_t rg, int logR2, int logC,
+                                typename F::T *__restrict__ X, typename F::T *__restrict__ W) {
+    using T = typename F::T;
+    const int C = 1 << logC;
+    constexpr int V = 16 / sizeof(T);  // elements per 16-byte vector
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(X + base + e));
+        const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(W + base + e));
+        const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            sm[lay.at(r + k, c)] = xs[k];
+            sm[lay.at(r + k, C + c)] = ws[k];
+        }
+    }
+    __syncthreads();
+    // logR2 >= 6 for every two-pass transform (N >= 2^13)
+    dif_columns_head<F, false>(sm, lay, logR2, logC + 1, stf);
+    product_round<F>(sm, lay, logR2, logC, stf, sti, [](T a, T b) { return F::mont(a, b); });
+    dit_columns_tail<F, false>(sm + C * lay.cs, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, C + c)];
+        __stcg(reinterpret_cast<uint4 *>(W + base + e), ov);
+    }
+    __syncthreads();
+}
+
+// Inverse pass 1 on column group cg of the product, scale, low bit, XOR output bits.
+template <class F>
+__device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
+                               const BlockPtrs &bp, uint64_t cg, int logN, int logR1, int logC,
+                               const typename F::T *__restrict__ src,
+                               const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
+    using T = typename F::T;
+    constexpr int SEG = 32 / sizeof(T), logSEG = sizeof(T) == 4 ? 3 : 2;
+    const int R1 = 1 << logR1, logS = logN - logR1;
+    const uint64_t c0 = cg << logC;
+    const RowMajor lay{logC};
+    const int seglog = logC - logSEG;
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        T x[SEG];
+        const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0 + sg * SEG);
+        *reinterpret_cast<uint4 *>(&x[0]) = __ldcg(g);
+        *reinterpret_cast<uint4 *>(&x[SEG / 2]) = __ldcg(g + 1);
+        row_twiddle<F, SEG>(x, tinv, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
+                            logN);
+        seg_store<T>(sm + lay.at(r, sg * SEG), x);
+    }
+    __syncthreads();
+    dit_columns<F, true>(sm, lay, logR1, logC, st);
+    // segment (r, sg) holds conv indices k = r*S1 + c0 + sg*SEG + c: SEG output bits
+    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        const uint64_t k0 = (uint64_t(r) << logS) + c0 + sg * SEG;
+        if (k0 + SEG <= pr.K0 || k0 >= uint64_t(pr.K0) + pr.out_len) continue;
+        T x[SEG];
+        seg_load<T>(x, sm + lay.at(r, sg * SEG));
+        uint32_t byte = 0;
+#pragma unroll
+        for (int c = 0; c < SEG; ++c) {
+            const uint64_t k = k0 + c;
+            if (k >= pr.K0 && k < uint64_t(pr.K0) + pr.out_len)
+                byte |= F::low_bit(F::mul_tw(x[c], scale)) << c;
+        }
+        if (byte) {
+            const uint64_t pos = pr.out_bit0 + (k0 - pr.K0);  // multiple of SEG
+            atomicXor(bp.out32 + (pos >> 5), byte << (pos & 31));
+        }
+    }
+    __syncthreads();
+}
+
+// Forward pass 2 of one fd spectrum in place: C = 2^logC rows of R2 = 2^logR2 from row
+// group rg.
+template <class F>
+__device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint64_t rg, int logR2,
+                              int logC, typename F::T *__restrict__ A) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
+        const T *xs = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+    }
+    __syncthreads();
+    dif_columns<F, false>(sm, lay, logR2, logC, stf);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(A + base + e), ov);
+    }
+    __syncthreads();
+}
+
+// Rows of Z_I from row group rg: Z_I = sum over the Q key tiles J of X_J * W_{wrow[J]}
+// (Montgomery products summed in the field), then the inverse pass 2, written to Z.
+// A 512-thread CTA covers a row group in at most kSumVec vectors of 16 bytes per thread.
+constexpr int kSumVec = 4;
+template <class F>
+__device__ void body_sum_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
+                                  int logR2, int logC, const typename F::T *__restrict__ X,
+                                  const typename F::T *__restrict__ W,
+                                  const uint32_t *__restrict__ wrow, uint32_t Q, uint64_t N,
+                                  typename F::T *__restrict__ Z) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    T acc[kSumVec][V];
+#pragma unroll
+    for (int q = 0; q < kSumVec; ++q)
+#pragma unroll
+        for (int k = 0; k < V; ++k) acc[q][k] = 0;
+    for (uint32_t J = 0; J < Q; ++J) {
+        const T *xj = X + uint64_t(J) * N + base;
+        const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
+#pragma unroll
+        for (int q = 0; q < kSumVec; ++q) {
+            const int e = (threadIdx.x + q * blockDim.x) * V;
+            if (e < cnt) {
+                const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
+                const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
+                const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc[q][k] = F::add(acc[q][k], F::mont(xs[k], ws[k]));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSumVec; ++q) {
+        const int e = (threadIdx.x + q * blockDim.x) * V;
+        if (e < cnt) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+#pragma unroll
+            for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = acc[q][k];
+        }
+    }
+    __syncthreads();
+    dit_columns<F, false>(sm, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(Z + base + e), ov);
+    }
+    __syncthreads();
+}
+
+// Streamed sum for a block with one output tile: for each key tile J, rows of row group
+// rg of X_J and W_{wrow[J]} (after their forward pass 1) get the forward pass 2 in shared
+// memory and their product is added to an accumulator; the accumulator then gets the
+// inverse pass 2 and is written to Z. Shared memory: key, window and accumulator
+// columns (3 C columns of R2 rows).
+template <class F>
+__device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
+                                const typename F::Tw *sti, uint64_t rg, int logR2, int logC,
+                                const typename F::T *__restrict__ X,
+                                const typename F::T *__restrict__ W,
+                                const uint32_t *__restrict__ wrow, uint32_t Q, uint64_t N,
+                                typename F::T *__restrict__ Z) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int C = 1 << logC;
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    T *acc = sm + 2 * C * lay.cs;
+    for (int e = threadIdx.x; e < C * lay.cs; e += blockDim.x) acc[e] = 0;
+    for (uint32_t J = 0; J < Q; ++J) {
+        const T *xj = X + uint64_t(J) * N + base;
+        const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
+        for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
+            const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
+            const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                sm[lay.at(r + k, c)] = xs[k];
+                sm[lay.at(r + k, C + c)] = ws[k];
+            }
+        }
+        __syncthreads();
+        dif_columns_head<F, false>(sm, lay, logR2, logC + 1, stf);
+        product_acc_round<F>(sm, lay, logR2, logC, 2 * C, stf,
+                             [](T a, T b) { return F::mont(a, b); },
+                             [](T a, T b) { return F::add(a, b); });
+    }
+    dit_columns<F, false>(acc, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = acc[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(Z + base + e), ov);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- the persistent kernel
+//
+// CTAs pull items from the list with an atomic counter; the list is ordered so that
+// each item depends only on items before it, which are already claimed by running
+// CTAs, so every wait ends. Waits are bounded anyway: on timeout the status word gets
+// PA_ERR_TIMEOUT and the item's body is skipped.
+// Counters: c1/c2/c3 per tile (pass 1, 2, 3 items done), then the list position, then
+// per fd block the forward pass-2 items done, then per fd block the forward pass-1 items
+// done.
+
+template <class F>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
+    const uint64_t *__restrict__ items, uint32_t nitems, const NttTile *__restrict__ tiles,
+    const FdBlock *__restrict__ fds, const uint32_t *__restrict__ wmap,
+    const BlockPtrs *__restrict__ blks, BlockPtrs one, typename F::T *__restrict__ ws,
+    const typename F::Tw *__restrict__ stage, const typename F::Tw *__restrict__ tfwd,
+    const typename F::Tw *__restrict__ tinv, uint32_t *cnt, uint32_t ntiles, uint32_t nfd,
+    uint32_t slots, int *status) {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint64_t cur;
+    __shared__ int flag;
+    uint32_t *c1 = cnt, *c2 = cnt + ntiles, *c3 = cnt + 2 * uint64_t(ntiles);
+    uint32_t *next = cnt + 3 * uint64_t(ntiles), *cfd = next + 1, *cfd1 = cfd + nfd;
+    Tw *st0 = reinterpret_cast<Tw *>(smraw);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t i = atomicAdd(next, 1u);
+            cur = i < nitems ? items[i] : ~0ull;
+        }
+        __syncthreads();
+        const uint64_t it = cur;
+        __syncthreads();
+        if (it == ~0ull) break;
+        const uint32_t type = static_cast<uint32_t>(it >> 60);
+        const uint32_t ti = static_cast<uint32_t>((it >> 32) & 0x0FFFFFFFu);
+        const uint32_t sub = static_cast<uint32_t>(it);
+        const NttTile tl = tiles[ti];
+        const BlockPtrs bp = pick(blks, one, tl.p.blk);
+        Tw scale;
+        memcpy(&scale, &tl.scale, sizeof(Tw));
+        const int logN = static_cast<int>(tl.logN);
+        const int logR1 = static_cast<int>(tl.logR1), logR2 = static_cast<int>(tl.logR2);
+        const int logC1 = static_cast<int>(tl.logC1), logC2 = static_cast<int>(tl.logC2);
+        T *X = ws + tl.ws_off;
+        T *W = X + (uint64_t(1) << logN);
+        switch (type) {
+            case IT_SMALL: {
+                Tw *sti = st0 + (1 << logN);
+                load_stage<F>(st0, stage, 0, logN);
+                load_stage<F>(sti, stage, 1, logN);
+                body_small<F>(reinterpret_cast<T *>(sti + (1 << logN)), st0, sti, tl.p, bp, logN, scale);
+                break;
+            }
+            case IT_P1: {
+                // the spectra slot is reused: wait until the tile `slots` earlier released it
+                bool ok = true;
+                if (ti >= slots) ok = wait_count(c3 + (ti - slots), tiles[ti - slots].g1, status, &flag);
+                const int which = sub >= tl.g1 ? 1 : 0;
+                load_stage<F>(st0, stage, 0, logR1);
+                if (ok)
+                    body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, which,
+                                      sub - which * tl.g1, logN, logR1, logC1, which ? W : X, tfwd);
+                signal_count(c1 + ti);
+                break;
+            }
+            case IT_P2: {
+                Tw *sti = st0 + (1 << logR2);
+                load_stage<F>(st0, stage, 0, logR2);
+                load_stage<F>(sti, stage, 1, logR2);
+                if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
+                    body_fused_last<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
+                                       logC2, X, W);
+                signal_count(c2 + ti);
+                break;
+            }
+            case IT_P3: {
+                load_stage<F>(st0, stage, 1, logR1);
+                if (wait_count(c2 + ti, tl.g2, status, &flag))
+                    body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
+                                      logN, logR1, logC1, W, tinv, scale);
+                signal_count(c3 + ti);
+                break;
+            }
+            case IT_FD_P1: {
+                load_stage<F>(st0, stage, 0, logR1);
+                body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp,
+                                  static_cast<int>(tl.which), sub, logN, logR1, logC1, X, tfwd);
+                signal_count(c1 + ti);
+                if (threadIdx.x == 0) atomicAdd(cfd1 + tl.fd, 1u);  // fenced by signal_count
+                break;
+            }
+            case IT_FD_P2: {
+                load_stage<F>(st0, stage, 0, logR2);
+                if (wait_count(c1 + ti, tl.g1, status, &flag))
+                    body_fwd_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2, logC2, X);
+                signal_count(cfd + tl.fd);
+                break;
+            }
+            case IT_FD_SUM: {
+                const FdBlock fb = fds[tl.fd];
+                load_stage<F>(st0, stage, 1, logR2);
+                if (wait_count(cfd + tl.fd, fb.nfwd2, status, &flag))
+                    body_sum_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
+                                         logC2, ws + fb.x_off, ws + fb.w_off,
+                                         wmap + fb.wmap + uint64_t(tl.out) * fb.Q, fb.Q,
+                                         uint64_t(1) << logN, X);
+                signal_count(c2 + ti);
+                break;
+            }
+            case IT_FD_STREAM: {
+                const FdBlock fb = fds[tl.fd];
+                Tw *sti = st0 + (1 << logR2);
+                load_stage<F>(st0, stage, 0, logR2);
+                load_stage<F>(sti, stage, 1, logR2);
+                if (wait_count(cfd1 + tl.fd, fb.nfwd1, status, &flag))
+                    body_stream_sum<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
+                                       logC2, ws + fb.x_off, ws + fb.w_off, wmap + fb.wmap, fb.Q,
+                                       uint64_t(1) << logN, X);
+                signal_count(c2 + ti);
+                break;
+            }
+            default: {  // IT_FD_P3
+                load_stage<F>(st0, stage, 1, logR1);
+                if (wait_count(c2 + ti, tl.g2, status, &flag))
+                    body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
+                                      logN, logR1, logC1, X, tinv, scale);
+                __syncthreads();
+                break;
+            }
+        }
+    }
+}
+
+template <class F>
+int launch_field(const NttLayout &lay, void *ws, const BlockPtrs *blks, const BlockPtrs &one,
+                 int *status, Prof *prof, cudaStream_t s) {
+    using Tw = typename F::Tw;
+    Tables tab;
+    int rc = ntt_tables(lay.field, &tab);
+    if (rc != PA_OK) return rc;
+    char *b = static_cast<char *>(ws);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(b + lay.off_counters);
+    PA_CUDA_TRY(cudaMemsetAsync(cnt, 0, lay.counter_bytes, s));
+    PA_CUDA_TRY(cudaFuncSetAttribute(ntt_persistent<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(lay.smem)));
+    int per_sm = 0;
+    PA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ntt_persistent<F>, kThreads,
+                                                              lay.smem));
+    int dev = 0, sms = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    PA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint64_t grid = uint64_t(per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > lay.nitems) grid = lay.nitems;
+    prof_begin(prof, K_BATCH_PERSISTENT, s);
+    ntt_persistent<F><<<static_cast<unsigned>(grid), kThreads, lay.smem, s>>>(
+        reinterpret_cast<const uint64_t *>(b + lay.off_items), static_cast<uint32_t>(lay.nitems),
+        reinterpret_cast<const NttTile *>(b + lay.off_tiles),
+        reinterpret_cast<const FdBlock *>(b + lay.off_fd),
+        reinterpret_cast<const uint32_t *>(b + lay.off_wmap), blks, one,
+        reinterpret_cast<typename F::T *>(b + lay.off_spec), static_cast<const Tw *>(tab.stage),
+        static_cast<const Tw *>(tab.fwd), static_cast<const Tw *>(tab.inv), cnt,
+        static_cast<uint32_t>(lay.ntiles), static_cast<uint32_t>(lay.nfd), lay.slots, status);
+    prof_end(prof, s);
+    PA_CUDA_TRY(cudaGetLastError());
+    return PA_OK;
+}
+
+}  // namespace
+}  // namespace pa
