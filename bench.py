@@ -8,7 +8,8 @@ is input-key Gbps (sum of n over the blocks / device time, Mbit = 10^6 bits as i
 Table 1), bit-exact against the CPU oracle (checked on sampled rows every run).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                       [--path auto|direct|ntt64|ntt31|fft|block_int8] [--impl ours|reference]
+                       [--path auto|direct|ntt64|ntt31|fft|block_int8|block_fp8]
+                       [--impl ours|reference]
 Under torchrun every rank runs the same workload on its own GPU (independent
 blocks: weak scaling, no data-path collective); rank 0 prints one JSON line.
 """
@@ -244,6 +245,7 @@ KERNEL_SOURCES = {
                          CSRC + "common.cuh"],
     "fft_tile": [CSRC + "fft.cu", CSRC + "dft.cuh", CSRC + "tiles.cuh"],
     "block_mma": [CSRC + "block.cu", CSRC + "common.cuh"],
+    "block_tc": [CSRC + "block_tc.cu", CSRC + "common.cuh"],
 }
 
 CLOCK_HZ = 2070e6
@@ -285,6 +287,14 @@ def algorithmic(kernel: str, blocks, descs):
         ops = sum(2.0 * b.m * (b.n + 8192) for b, d in zip(blocks, descs)
                   if d["path_name"] == "block_int8")
         return "tensor", ops, "Tops/s", 150.8, "measured: legacy mma.sync s8 peak on GB300"
+    if kernel == "block_tc":
+        # dense FP8 MMA work the kernel performs: M = 128 rows x N = 256 blocks per output
+        # tile, over the tile's contraction length n + 128 * 255
+        ops = sum(2.0 * 32768 * -(-b.m // 32768) * (b.n + 128 * 255)
+                  for b, d in zip(blocks, descs) if d["path_name"] == "block_fp8")
+        pk, src = peaks()
+        return ("tensor", ops, "TFLOP/s", 2.0 * pk["bf16_tflops"],
+                f"{src} bf16 dense x 2 (nominal fp8 / bf16 ratio, 4.5 / 2.25 PFLOP/s)")
     if kernel == "fft_tile":
         fl = 0.0
         for b, d in zip(blocks, descs):

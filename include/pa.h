@@ -56,8 +56,12 @@ typedef enum {
                                coefficients <= n < p)                                      */
     PA_PATH_FFT = 4,        /* FP32 FFT sub-blocks under a proven rounding bound; FP64
                                butterflies on the tile lengths where the FP32 bound fails */
-    PA_PATH_BLOCK_INT8 = 5  /* block-Toeplitz Y = sum_d T_d X_d, INT8 tensor cores,
+    PA_PATH_BLOCK_INT8 = 5, /* block-Toeplitz Y = sum_d T_d X_d, INT8 tensor cores,
                                INT32 accumulation, then mod 2                            */
+    PA_PATH_BLOCK_FP8 = 6   /* the same block-Toeplitz contraction on the tcgen05 tensor
+                               cores: bits as e4m3 0 / 2^-6, FP32 accumulation in tensor
+                               memory (exact: at most 2^14 products per partial sum),
+                               then mod 2; tile edge b = 128                             */
 } pa_path;
 
 /* Planner options; zero-initialise and set what you need (0 / -1 = choose). */
@@ -65,7 +69,7 @@ typedef struct {
     int32_t path;              /* pa_path                                                 */
     int32_t device;            /* CUDA device ordinal, -1 = current device                */
     uint32_t log2_transform;   /* transform paths: log2 of the transform size N           */
-    uint32_t block_b;          /* block path: tile edge b in {128, 256, 512}              */
+    uint32_t block_b;          /* block paths: tile edge b, INT8 in {128, 256, 512}, FP8 128 */
     uint64_t tile_in;          /* key sub-block length L (the paper's batch length)       */
     uint64_t tile_out;         /* output sub-block length M (column split of Sec. 3)      */
     uint32_t force_fp64;       /* FFT path: use FP64 butterflies even where FP32 is proven */

@@ -31,7 +31,9 @@ PA_PATH_NTT64 = 2
 PA_PATH_NTT31 = 3
 PA_PATH_FFT = 4
 PA_PATH_BLOCK_INT8 = 5
-PATH_NAMES = {0: "auto", 1: "direct", 2: "ntt64", 3: "ntt31", 4: "fft", 5: "block_int8"}
+PA_PATH_BLOCK_FP8 = 6
+PATH_NAMES = {0: "auto", 1: "direct", 2: "ntt64", 3: "ntt31", 4: "fft", 5: "block_int8",
+              6: "block_fp8"}
 PATHS = {v: k for k, v in PATH_NAMES.items()}
 
 

@@ -24,7 +24,7 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
     cfg->n = n;
     cfg->m = m;
     int path = o ? o->path : PA_PATH_AUTO;
-    if (path < PA_PATH_AUTO || path > PA_PATH_BLOCK_INT8) return PA_ERR_INVALID;
+    if (path < PA_PATH_AUTO || path > PA_PATH_BLOCK_FP8) return PA_ERR_INVALID;
     if (path == PA_PATH_AUTO) {
         // Cost model (measured on GB300, see the autotuner in batch.cu): the direct
         // kernel wins while m*n is small; the exact 31-bit NTT wins beyond.
@@ -61,6 +61,11 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
             cfg->ws_bytes = block_workspace(cfg->blk);
             cfg->kernels = 2 + (cfg->blk.grid_y > 1 ? 1 : 0);
             break;
+        case PA_PATH_BLOCK_FP8:
+            rc = block_tc_plan(n, m, o, &cfg->blk);
+            cfg->ws_bytes = block_workspace(cfg->blk);
+            cfg->kernels = 3;  // output zeroing, key reversal, the MMA kernel
+            break;
     }
     return rc;
 }
@@ -76,7 +81,7 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->tile_in = cfg.n;
         d->tile_out = cfg.m;
         d->tiles_in = d->tiles_out = 1;
-    } else if (cfg.path == PA_PATH_BLOCK_INT8) {
+    } else if (cfg.path == PA_PATH_BLOCK_INT8 || cfg.path == PA_PATH_BLOCK_FP8) {
         d->block_b = cfg.blk.b;
         d->tile_in = cfg.n;
         d->tile_out = cfg.m;
@@ -123,7 +128,8 @@ int launch_plan(pa_plan_s *p, const uint64_t *seed, const uint64_t *key, uint64_
         case PA_PATH_NTT64:
         case PA_PATH_NTT31: return ntt_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
         case PA_PATH_FFT: return fft_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
-        case PA_PATH_BLOCK_INT8: return block_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
+        case PA_PATH_BLOCK_INT8:
+        case PA_PATH_BLOCK_FP8: return block_launch(p->cfg, ws, hdr, &p->prof, seed, key, out, s);
     }
     return PA_ERR_INVALID;
 }

@@ -187,7 +187,7 @@ static int launch_b(const PlanCfg &cfg, uint32_t *xr, const uint64_t *seed, uint
 
 int block_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                  const uint64_t *key, uint64_t *out, cudaStream_t s) {
-    (void)hdr;
+    if (cfg.blk.tc) return block_tc_launch(cfg, ws, hdr, prof, seed, key, out, s);
     const BlockCfg &c = cfg.blk;
     uint32_t *xr = static_cast<uint32_t *>(ws);
     const int use_atomic = c.grid_y > 1;

@@ -61,6 +61,7 @@ struct BlockCfg {
     uint64_t kc = 0;             // contraction positions per CTA (multiple of 32)
     uint32_t grid_x = 0, grid_y = 0;
     uint64_t xr_words = 0, xr_words_pad = 0;  // reversed key in the workspace
+    uint32_t tc = 0;             // 1: tcgen05 FP8 kernel (block_tc.cu), kc = chunk per CTA
 };
 
 struct PlanCfg {
@@ -97,6 +98,7 @@ enum KernelId {
     K_BLOCK_MMA,
     K_BATCH_PERSISTENT,
     K_MEMSET,
+    K_BLOCK_TC,
     K_NUM_KERNELS
 };
 const char *kernel_name(int kid);
@@ -126,6 +128,11 @@ void reverse_key_launch(const uint64_t *key, uint64_t n, uint32_t *xr, uint64_t 
 size_t direct_workspace(const DirectCfg &c);
 int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                   const uint64_t *key, uint64_t *out, cudaStream_t s);
+
+// Block-Toeplitz contraction on tcgen05 (FP8 operands, FP32 accumulation in TMEM).
+int block_tc_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c);
+int block_tc_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
+                    const uint64_t *key, uint64_t *out, cudaStream_t s);
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c);
 // Modelled cost of a tile geometry in units of one standard tile pair of size 2^k

@@ -7,7 +7,8 @@
 namespace pa {
 
 static const char *kNames[K_NUM_KERNELS] = {"reverse_key", "direct",           "fft_tile",
-                                             "block_mma",   "batch_persistent", "memset"};
+                                             "block_mma",   "batch_persistent", "memset",
+                                             "block_tc"};
 
 const char *kernel_name(int kid) { return (kid >= 0 && kid < K_NUM_KERNELS) ? kNames[kid] : "?"; }
 

@@ -43,7 +43,8 @@ def _run_batch(bl, keys, seeds, opts=None, runs=2):
     return [host(o) for o in od], reps, paths
 
 
-@pytest.mark.parametrize("path", ["auto", "ntt31", "ntt64", "direct", "fft", "block_int8"])
+@pytest.mark.parametrize("path", ["auto", "ntt31", "ntt64", "direct", "fft", "block_int8",
+                                  "block_fp8"])
 def test_mixed_batch_matches_oracle(path):
     bl, keys, seeds = _blocks(MIXED)
     if path == "fft":  # keep the FP tile count modest

@@ -16,7 +16,7 @@ from gpu_util import dev, host, run_path
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["direct", "ntt64", "ntt31", "fft", "block_int8"]
+PATHS = ["direct", "ntt64", "ntt31", "fft", "block_int8", "block_fp8"]
 
 SHAPES = [(1, 1), (1, 100), (100, 1), (2, 2), (31, 33), (64, 64), (65, 63), (1000, 1),
           (1, 5000), (4097, 4095), (12345, 777), (70001, 64), (64, 70001), (33333, 33333),
@@ -105,7 +105,7 @@ def test_finite_size_sampled_rows(path):
     b = inputs.FINITE_SIZE
     if not _supported(path, b.n, b.m):
         pytest.skip(f"{path} does not take the finite-size workload")
-    if path in ("direct", "block_int8", "fft"):
+    if path in ("direct", "block_int8", "fft"):  # block_fp8 runs it (tensor cores, ~1 s)
         pytest.skip("1e15 bit products: timed in the bench, parity at full size shown by "
                     "the transform paths")
     key, seed = b.key(), b.seed()
@@ -159,3 +159,20 @@ def test_host_entry_point(path):
 def test_block_tile_sizes(b, n, m):
     key, seed, want = _case(n, m, 21 + n, 23 + m)
     _check("block_int8", n, m, key, seed, want, block_b=b)
+
+
+@pytest.mark.parametrize("n,m", [(4_000_001, 1_000_003), (3_000_000, 40_000)])
+def test_block_fp8_full_chunks_all_ones(n, m):
+    # All-ones key and seed: every output is the parity of n (each row meets all n key
+    # bits), and every CTA of the tcgen05 kernel accumulates its whole contraction chunk
+    # (16384 positions at these sizes), the largest FP32 partial sums the kernel forms.
+    kw, sw = (n + 63) // 64, (n + m - 1 + 63) // 64
+    key = np.full(kw, np.uint64(0xFFFFFFFFFFFFFFFF))
+    seed = np.full(sw, np.uint64(0xFFFFFFFFFFFFFFFF))
+    desc = pkg.pa_plan_query(n, m, binding.make_opts(path="block_fp8"))
+    assert desc["path_name"] == "block_fp8"
+    got, _ = run_path(n, m, key, seed, path="block_fp8")
+    bits = oracle.unpack(got, m)
+    assert np.all(bits == (n & 1))
+    if m % 64:
+        assert int(got[-1]) >> (m % 64) == 0
