@@ -33,6 +33,7 @@ struct Tuner {
     bool valid = false;
     double direct = 0;           // s per bit product
     double block[3] = {0, 0, 0};  // s per (m * (n + 8192)), b = 128, 256, 512
+    double block_tc = 0;         // tcgen05 FP8: s per (256-block output tile x (n + 32640))
     double fft = 0;              // s per tile of the default FP32 geometry (per unit N log N)
     double ntt[2][kTuneLogMax + 1] = {};  // s per tile of size 2^k, field 0 / 1
     double launch = 3e-6;        // s per launch
@@ -131,6 +132,11 @@ int calibrate(Tuner *t) {
         t->block[i] = tplan(n, m, o, &cfg) / (double(m) * (n + 8192));
     }
     o.block_b = 0;
+    o.path = PA_PATH_BLOCK_FP8;
+    {
+        const uint64_t n = uint64_t(1) << 20, m = uint64_t(1) << 17;
+        t->block_tc = tplan(n, m, o, &cfg) / (double(ceil_div(m, 32768)) * double(n + 32640));
+    }
     o.path = PA_PATH_FFT;
     {
         const uint64_t n = uint64_t(1) << 18, m = uint64_t(1) << 13;
@@ -173,8 +179,8 @@ bool load_cache(Tuner *t, const char *path, const char *dev_name) {
         name[strcspn(name, "\n")] = 0;
         ok = strcmp(name, dev_name) == 0;
     }
-    ok = ok && fscanf(f, "%lf %lf %lf %lf %lf", &t->direct, &t->block[0], &t->block[1],
-                      &t->block[2], &t->fft) == 5;
+    ok = ok && fscanf(f, "%lf %lf %lf %lf %lf %lf", &t->direct, &t->block[0], &t->block[1],
+                      &t->block[2], &t->block_tc, &t->fft) == 6;
     for (int fl = 0; ok && fl < 2; ++fl)
         for (int k = 0; ok && k <= kTuneLogMax; ++k) ok = fscanf(f, "%lf", &t->ntt[fl][k]) == 1;
     fclose(f);
@@ -185,8 +191,8 @@ bool load_cache(Tuner *t, const char *path, const char *dev_name) {
 void save_cache(const Tuner &t, const char *path, const char *dev_name) {
     FILE *f = fopen(path, "w");
     if (!f) return;
-    fprintf(f, "%s\n%.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0], t.block[1],
-            t.block[2], t.fft);
+    fprintf(f, "%s\n%.6e %.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0], t.block[1],
+            t.block[2], t.block_tc, t.fft);
     for (int fl = 0; fl < 2; ++fl) {
         for (int k = 0; k <= kTuneLogMax; ++k) fprintf(f, "%.6e ", t.ntt[fl][k]);
         fprintf(f, "\n");
@@ -236,6 +242,8 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
         consider(t.block[i] * double(m) * double(n + 8192) + 2 * t.launch, o);
     }
     o.block_b = 0;
+    o.path = PA_PATH_BLOCK_FP8;
+    consider(t.block_tc * double(ceil_div(m, 32768)) * double(n + 32640) + 3 * t.launch, o);
     // FFT path at its usual proven geometry (N = 2^12, L = 1536, M = 2560)
     o.path = PA_PATH_FFT;
     consider(t.fft * double(ceil_div(n, 1536)) * double(ceil_div(m, 2560)) * 4096.0 * 14.0 +

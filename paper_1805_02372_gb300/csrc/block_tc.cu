@@ -8,23 +8,29 @@
 //   B[I][k] = x[128 I - k]         (the reversed key read at stride 128)
 // and y[128 I + a] = C[a][I] mod 2. Bits become e4m3 values 0 or 2^-6 (byte 0x08), so a
 // product is 0 or 2^-12 and C[a][I] = count * 2^-12 exactly: a CTA's contraction chunk
-// is at most 2^14 positions, so every partial sum is a multiple of 2^-12 below 4, which
+// is at most 2^15 positions, so every partial sum is a multiple of 2^-12 below 8, which
 // FP32 (24-bit significand) holds exactly whatever the order of additions.
 //
 // CTA (256 threads, two per SM): output blocks I0 .. I0+255 (128 x 256 outputs, the MMA
 // shape M = 128, N = 256, FP32 accumulator in 256 TMEM columns) and one chunk of the
 // contraction; chunks are XOR-merged into the output (Eq. finalkey). The chunk advances
-// in stages of 128 positions (4 MMAs of K = 32), double-buffered: all threads expand the
-// next stage's operands from bits into shared memory while the tensor core runs the
-// current one; one thread issues the MMAs and commits them to the buffer's mbarrier.
+// in stages of 128 positions (4 MMAs of K = 32); one thread issues the MMAs and commits
+// them to an mbarrier.
 //
-// Operand layouts (K-major, no swizzle: 8-row x 16-byte core matrices).
-//   B: core (h, c) at h*1024 + c*128 (rows of 16 bytes inside), one stage = 32 KB.
-//   A: row a, bytes [16c, 16c+16) hold seed positions a + 16c + [0, 16); with a = 8g + i
-//      that is position 8(g + 2c) + i + [0, 16), which depends on (g, c) only through
-//      u = g + 2c. So core (g, c) is stored once per u ("chunk" u: rows i = 0..7 of 16
-//      bytes at u*128 + 16i) and the descriptor steps 128 bytes per row group and 256
-//      per K core: 30 chunks (3.75 KB) instead of 16 KB per stage.
+// Both operands are Toeplitz/Hankel, and both layouts exploit it (K-major, no swizzle:
+// core matrices of 8 rows x 16 bytes).
+//   B (key): with the columns in reverse order (MMA column r' is block I0 + 255 - r'),
+//      column r' of stage s holds window positions 128 (r' + s) + [0, 128): stage s + 1
+//      is stage s moved by one column. The expanded key window is stored once as a ring
+//      of 16-byte row pieces per K core (piece R of core c at c * 16 Rtot + 16 R, rows
+//      at 16 bytes, row groups at 128, K cores at 16 Rtot), and the descriptor of stage
+//      s starts 16 s bytes in. The whole key side is expanded once per CTA.
+//   A (seed): row a, bytes [16c, 16c+16) hold seed positions a + 16c + [0, 16); with
+//      a = 8g + i that is position 8(g + 2c) + i + [0, 16), which depends on (g, c) only
+//      through u = g + 2c. So core (g, c) is stored once per u ("chunk" u: rows i = 0..7
+//      of 16 bytes at u*128 + 16i) and the descriptor steps 128 bytes per row group and
+//      256 per K core: 30 chunks (3.75 KB) per stage, double-buffered; all threads
+//      expand the next stage's chunks while the tensor core runs the current stage.
 #include <string.h>
 
 #include "common.cuh"
@@ -38,14 +44,14 @@ constexpr int kTcN = 256;           // output blocks I per CTA
 constexpr int kTcStage = 128;       // contraction positions per stage
 constexpr int kTcAChunks = 30;      // u = g + 2c, g < 16, c < 8
 constexpr int kTcABytes = 4096;
-constexpr int kTcBBytes = kTcN * kTcStage;
-constexpr int kTcMaxChunk = 16384;  // contraction positions per CTA (counts < 2^14)
+constexpr int kTcMaxChunk = 32768;  // contraction positions per CTA (counts < 2^15)
 constexpr int kTcMaxStages = kTcMaxChunk / kTcStage;
-constexpr int kTcKeyWords = 4 * (kTcN - 1 + kTcMaxStages);  // staged reversed-key words
+constexpr int kTcMaxRows = kTcN + kTcMaxStages;             // key ring rows (Rtot)
 constexpr int kTcSeedWords = 4 * kTcMaxStages + 8;          // staged seed words
-// Dynamic shared memory: A[2] | B[2] | key window | seed window. Always the maximum, so
-// that at most two CTAs (2 x 256 TMEM columns) are resident on an SM.
-constexpr size_t kTcSmem = 2 * kTcABytes + 2 * kTcBBytes + 4 * kTcKeyWords + 4 * kTcSeedWords;
+constexpr size_t kTcUsed = 2 * kTcABytes + 8 * 16 * kTcMaxRows + 4 * kTcSeedWords;
+// Dynamic shared memory: A[2] | key ring | seed window, padded so that at most two CTAs
+// (2 x 256 TMEM columns) are resident on an SM.
+constexpr size_t kTcSmem = kTcUsed > 80 * 1024 ? kTcUsed : 80 * 1024;
 static_assert(3 * kTcSmem > 228 * 1024, "three CTAs per SM would oversubscribe TMEM");
 
 // Instruction descriptor, kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3 (bits 7-9,
@@ -135,19 +141,31 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
     const uint64_t kmine = klen - kdone < chunk ? klen - kdone : chunk;
     const int S = static_cast<int>((kmine + kTcStage - 1) / kTcStage);
 
+    const int Rtot = kTcN + S;                 // key ring rows
+    const uint32_t lbo_b = 16u * static_cast<uint32_t>(Rtot);
     unsigned char *A = smt;
-    unsigned char *B = smt + 2 * kTcABytes;
-    uint32_t *KW = reinterpret_cast<uint32_t *>(smt + 2 * kTcABytes + 2 * kTcBBytes);
-    uint32_t *SW = KW + kTcKeyWords;
+    unsigned char *Bring = smt + 2 * kTcABytes;
+    uint32_t *SW = reinterpret_cast<uint32_t *>(Bring + 8 * 16 * kTcMaxRows);
 
-    // Reversed-key window: word w holds xr bits [xw0 + 32 w, +32), xw0 = kdone - 128 * 255
-    // (tile independent); row r of stage s reads words 4 (255 - r + s) .. + 3.
+    // Key ring: row R holds reversed-key window positions 128 R + [0, 128), window start
+    // xw0 = kdone - 128 * 255 (tile independent): xr words w0 + 4R .. + 3.
     {
         const int64_t w0 = static_cast<int64_t>(kdone / 32) - 4 * (kTcN - 1);
-        const int nw = 4 * (kTcN - 1 + S);
-        for (int w = tid; w < nw; w += kTcThreads) {
-            const int64_t g = w0 + w;
-            KW[w] = (g >= 0 && static_cast<uint64_t>(g) < xr_words32) ? __ldg(xr + g) : 0u;
+        const uint32_t ring = smem_addr(Bring);
+        for (int R = tid; R < Rtot; R += kTcThreads) {
+            const int64_t g = w0 + 4 * R;
+            uint32_t ws[4];
+            if (g >= 0 && static_cast<uint64_t>(g) + 4 <= xr_words32) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(xr + g));
+                ws[0] = v.x, ws[1] = v.y, ws[2] = v.z, ws[3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    ws[e] = (g + e >= 0 && static_cast<uint64_t>(g + e) < xr_words32) ? __ldg(xr + g + e) : 0u;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                sts128(ring + c * lbo_b + 16 * R, expand16((ws[c >> 1] >> (16 * (c & 1))) & 0xFFFFu));
         }
     }
     // Seed window: word w holds seed bits [sw0 + 32 w, +32), sw0 = 128 I0 + kdone; bits at
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    const uint32_t a_base = smem_addr(A), b_base = smem_addr(B);
+    const uint32_t a_base = smem_addr(A), b_base = smem_addr(Bring);
     int issued = 0;  // stages whose MMAs were issued and committed
     bool bad = false;
     for (int s = 0; s < S; ++s) {
@@ -196,13 +214,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
                 const uint32_t v = __funnelshift_r(SW[q >> 5], SW[(q >> 5) + 1], q & 31);
                 sts128(a_base + buf * kTcABytes + 16 * tid, expand16(v & 0xFFFFu));
             }
-            // B: row r = tid, reversed-key positions 128 (255 - r + s) + [0, 128)
-            const uint4 w = *reinterpret_cast<const uint4 *>(KW + 4 * (kTcN - 1 - tid + s));
-            const uint32_t rb = b_base + buf * kTcBBytes + (tid >> 3) * 1024 + (tid & 7) * 16;
-            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                sts128(rb + c * 128, expand16((ws[c >> 1] >> (16 * (c & 1))) & 0xFFFFu));
         }
         fence_proxy_async_smem();
         if (__syncthreads_or(bad)) break;
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
 #pragma unroll
             for (int kk = 0; kk < kTcStage / 32; ++kk) {
                 const uint64_t ad = smem_desc(a_base + buf * kTcABytes + kk * 512, 256, 128);
-                const uint64_t bd = smem_desc(b_base + buf * kTcBBytes + kk * 256, 128, 1024);
+                const uint64_t bd = smem_desc(b_base + 16 * s + 2 * kk * lbo_b, lbo_b, 128);
                 tc_mma(tmem, ad, bd, (s > 0 || kk > 0) ? 1u : 0u);
             }
             tc_commit(&bar[buf]);
@@ -229,8 +240,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
     } else {
         tc_fence_after();
         // Epilogue: warp w reads TMEM lanes 32 (w & 3) + lane (row a) and columns
-        // [128 (w >> 2), +128) (blocks I); a ballot over the warp's 32 rows gives one
-        // output word per block, bits 128 (I0 + I) + 32 (w & 3) + [0, 32).
+        // [128 (w >> 2), +128) (column r' is block I = 255 - r'); a ballot over the warp's
+        // 32 rows gives one output word per block, bits 128 (I0 + I) + 32 (w & 3) + [0, 32).
         const int q = warp & 3;
         const uint64_t out_words32 = 2 * ceil_div_dev(m, 64);
         for (int c0 = 128 * (warp >> 2); c0 < 128 * (warp >> 2) + 128; c0 += 32) {
@@ -246,7 +257,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
                     if (lane == 16 * h + j) mine = word;
                 }
             }
-            const uint64_t bit0 = uint64_t(kTcM) * (I0 + c0 + lane) + 32 * q;
+            const uint64_t bit0 = uint64_t(kTcM) * (I0 + (kTcN - 1) - (c0 + lane)) + 32 * q;
             const uint64_t gw = bit0 >> 5;
             if (bit0 < m && gw < out_words32) {
                 if (bit0 + 32 > m) mine &= (1u << (m - bit0)) - 1u;
@@ -272,7 +283,7 @@ int block_tc_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c) {
     c->tc = 1;
     const uint64_t tiles = ceil_div(m, uint64_t(kTcM) * kTcN);
     const uint64_t klen = n + uint64_t(kTcM) * (kTcN - 1);
-    // about four waves of two CTAs per SM, chunks of 1024 .. 16384 positions
+    // about four waves of two CTAs per SM, chunks of 1024 .. 32768 positions
     const uint64_t target = uint64_t(kNumSMsGB300) * 2 * 4;
     uint64_t chunk = round_up(ceil_div(klen * tiles, target), kTcStage);
     if (chunk < 1024) chunk = 1024;
