@@ -324,7 +324,7 @@ def compulsory_bytes(blocks):
                for b in blocks)
 
 
-def roofline(kt: dict, blocks, descs, steps: int):
+def roofline(kt: dict, blocks, descs, steps: int, workload_name: str):
     work = {k: v for k, v in kt.items() if k != "memset"}
     if not work:
         return None
@@ -344,12 +344,13 @@ def roofline(kt: dict, blocks, descs, steps: int):
     hbm = compulsory_bytes(blocks) / launches_per_step / (per_launch_ms * 1e-3) / 1e9
     out["hbm_compulsory"] = {"achieved_gbs": hbm, "peak_gbs": pk["hbm_gbs"],
                              "frac": hbm / pk["hbm_gbs"], "peak_source": psrc + " (MEASURED_PEAKS)"}
-    out["traffic"] = traffic_for(name)
+    out["traffic"] = traffic_for(name, workload_name)
     return out
 
 
-def traffic_for(kernel: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged."""
+def traffic_for(kernel: str, workload_name: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged and
+    the figure was taken on this bench workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -360,6 +361,8 @@ def traffic_for(kernel: str):
     if not ent or kernel not in KERNEL_SOURCES:
         return None
     if ent.get("source_digest") != _source_digest(KERNEL_SOURCES[kernel]):
+        return None
+    if ent.get("bench_workload") != workload_name:
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -567,7 +570,7 @@ def main():
         "config": dict(cfg, path=args.path, paths_chosen=runner.paths(),
                        l2="flushed between steps" if flush else "inputs larger than L2",
                        bit_exact_sampled=exact),
-        "roofline": roofline(kt, blocks, runner.plan_desc, args.steps),
+        "roofline": roofline(kt, blocks, runner.plan_desc, args.steps, args.workload),
         "e2e": {"value": e2e_gbps * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps, "clocks": clocks,
