@@ -369,7 +369,7 @@ def traffic_for(kernel: str, workload_name: str):
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_gbps(blocks, rows_per_block: int = 5120, seed: int = 3, max_blocks: int = 256):
+def cpu_oracle_gbps(blocks, rows_per_block: int = 40000, seed: int = 3, max_blocks: int = 256):
     """The oracle as it stands (all host cores), timed on a bounded sample of each block.
 
     The oracle's full hash of a block is one set-up (seed reversal, key masking) plus m row

@@ -304,6 +304,15 @@ __global__ void batch_zero(const BlockPtrs *__restrict__ blks, const uint32_t *_
 
 using namespace pa;
 
+namespace pa {
+// One contiguous copy of 64-bit words (pa_batch_run_host's gather and scatter kernels).
+struct CopySeg {
+    const uint64_t *src;
+    uint64_t *dst;
+    uint64_t words;
+};
+}  // namespace pa
+
 struct pa_batch_s {
     int device = 0;
     std::vector<uint64_t> n, m;
@@ -329,6 +338,8 @@ struct pa_batch_s {
     void *stage = nullptr;
     std::vector<size_t> st_seed, st_key, st_out;
     size_t stage_bytes = 0;
+    pa::CopySeg *segs = nullptr;      // device copy tables: inputs (2 per block), outputs
+    std::vector<pa::CopySeg> hsegs;
 };
 
 namespace {
@@ -501,6 +512,39 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
 
 // Release a batch. Server-owned batches free their memory in stream order and do not
 // synchronise the device; others synchronise their last stream first.
+// Copies the words of every segment; CTAs stride over the segments, threads over words
+// (four independent loads in flight per thread: the source may be host memory reached
+// over the CPU-GPU link, with a long latency).
+__global__ void __launch_bounds__(256) copy_segments(const CopySeg *__restrict__ segs, uint32_t nseg) {
+    for (uint32_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+        const CopySeg g = segs[sg];
+        for (uint64_t i = threadIdx.x; i < g.words; i += 4 * uint64_t(blockDim.x)) {
+            uint64_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t j = i + u * uint64_t(blockDim.x);
+                if (j < g.words) v[u] = g.src[j];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t j = i + u * uint64_t(blockDim.x);
+                if (j < g.words) g.dst[j] = v[u];
+            }
+        }
+    }
+}
+
+// The device address of page-locked host memory the current device can access (NULL for
+// pageable or unknown memory).
+void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 void batch_destroy_impl(pa_batch_s *b) {
     if (!b) return;
     if (!b->alloc_stream) {
@@ -511,6 +555,7 @@ void batch_destroy_impl(pa_batch_s *b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     batch_free(b);
     if (b->stage) cudaFree(b->stage);
+    if (b->segs) cudaFree(b->segs);
     prof_free(&b->prof);
     delete b;
 }
@@ -631,19 +676,63 @@ int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, v
         const pa_block &h = host_blocks[i];
         if (h.n != b->n[i] || h.m != b->m[i] || !h.seed_bits || !h.key_bits || !h.out_bits)
             return PA_ERR_INVALID;
-        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits, ceil_div(h.n + h.m - 1, 64) * 8,
-                                    cudaMemcpyHostToDevice, s));
-        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
-                                    cudaMemcpyHostToDevice, s));
         dev[i] = {h.n, h.m, reinterpret_cast<const uint64_t *>(st + b->st_seed[i]),
                   reinterpret_cast<const uint64_t *>(st + b->st_key[i]),
                   reinterpret_cast<uint64_t *>(st + b->st_out[i])};
     }
+    // When every host buffer is page-locked and mapped for this device, one gather kernel
+    // reads all keys and seeds and one scatter kernel writes all outputs (instead of three
+    // copies per block); otherwise one cudaMemcpyAsync per buffer.
+    std::vector<CopySeg> &sg = b->hsegs;
+    sg.clear();
+    bool mapped = true;
+    for (size_t i = 0; i < count && mapped; ++i) {
+        const pa_block &h = host_blocks[i];
+        void *ds = mapped_host(h.seed_bits), *dk = mapped_host(h.key_bits);
+        void *dout = mapped_host(h.out_bits);
+        mapped = ds && dk && dout;
+        sg.push_back({static_cast<const uint64_t *>(ds), reinterpret_cast<uint64_t *>(st + b->st_seed[i]),
+                      ceil_div(h.n + h.m - 1, 64)});
+        sg.push_back({static_cast<const uint64_t *>(dk), reinterpret_cast<uint64_t *>(st + b->st_key[i]),
+                      ceil_div(h.n, 64)});
+    }
+    if (mapped) {
+        for (size_t i = 0; i < count; ++i)
+            sg.push_back({reinterpret_cast<const uint64_t *>(st + b->st_out[i]),
+                          static_cast<uint64_t *>(mapped_host(host_blocks[i].out_bits)),
+                          ceil_div(b->m[i], 64)});
+        if (!b->segs) {
+            cudaError_t e = cudaMalloc(&b->segs, 3 * count * sizeof(CopySeg));
+            if (e != cudaSuccess) {
+                b->segs = nullptr;
+                return cuda_fail(e);
+            }
+        }
+        PA_CUDA_TRY(cudaMemcpyAsync(b->segs, sg.data(), sg.size() * sizeof(CopySeg),
+                                    cudaMemcpyHostToDevice, s));
+        int sms = kNumSMsGB300;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        copy_segments<<<4 * sms, 256, 0, s>>>(b->segs, static_cast<uint32_t>(2 * count));
+        PA_CUDA_TRY(cudaGetLastError());
+    } else {
+        for (size_t i = 0; i < count; ++i) {
+            const pa_block &h = host_blocks[i];
+            PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits,
+                                        ceil_div(h.n + h.m - 1, 64) * 8, cudaMemcpyHostToDevice, s));
+            PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
+                                        cudaMemcpyHostToDevice, s));
+        }
+    }
     int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
     if (rc != PA_OK) return rc;
-    for (size_t i = 0; i < count; ++i)
-        PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i],
-                                    ceil_div(b->m[i], 64) * 8, cudaMemcpyDeviceToHost, s));
+    if (mapped) {
+        copy_segments<<<4 * kNumSMsGB300, 256, 0, s>>>(b->segs + 2 * count, static_cast<uint32_t>(count));
+        PA_CUDA_TRY(cudaGetLastError());
+    } else {
+        for (size_t i = 0; i < count; ++i)
+            PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i],
+                                        ceil_div(b->m[i], 64) * 8, cudaMemcpyDeviceToHost, s));
+    }
     PA_CUDA_TRY(cudaStreamSynchronize(s));
     if (rep) {
         DevHeader h;

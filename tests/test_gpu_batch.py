@@ -103,6 +103,30 @@ def test_one_shot_and_host_entry():
         assert np.array_equal(o, w)
 
 
+def test_host_entry_pinned_buffers():
+    # Page-locked host buffers take the gather/scatter kernels; one pageable output
+    # buffer sends the whole call down the per-buffer copy path. Both must give the
+    # oracle's bits, on repeated calls.
+    import torch
+    bl, keys, seeds = _blocks(MIXED, salt=5)
+    want = [oracle.hash_full(b.n, b.m, s, k) for b, k, s in zip(bl, keys, seeds)]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()
+    kh = [pin(k) for k in keys]
+    sh = [pin(s) for s in seeds]
+    batch = pkg.pa_batch_plan([(b.n, b.m, None, None, None) for b in bl])
+    for trial in range(3):
+        oh = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64).pin_memory() for b in bl]
+        outs = list(oh)
+        if trial == 2:
+            outs[3] = np.full((bl[3].m + 63) // 64, np.uint64(7))  # pageable
+        hdesc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sh, kh, outs)]
+        pkg.pa_batch_run_host(batch, hdesc)
+        for i, (o, w) in enumerate(zip(outs, want)):
+            got = o if isinstance(o, np.ndarray) else o.numpy().view(np.uint64)
+            assert np.array_equal(got, w), (trial, i)
+    pkg.pa_batch_destroy(batch)
+
+
 def test_batched_workload_256_blocks():
     import torch
     with open(os.path.join(HERE, "golden", "batched256.json")) as f:

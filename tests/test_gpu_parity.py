@@ -105,9 +105,6 @@ def test_finite_size_sampled_rows(path):
     b = inputs.FINITE_SIZE
     if not _supported(path, b.n, b.m):
         pytest.skip(f"{path} does not take the finite-size workload")
-    if path in ("direct", "block_int8", "fft"):  # block_fp8 runs it (tensor cores, ~1 s)
-        pytest.skip("1e15 bit products: timed in the bench, parity at full size shown by "
-                    "the transform paths")
     key, seed = b.key(), b.seed()
     got, desc = run_path(b.n, b.m, key, seed, path=path)
     rng = np.random.default_rng(5)
@@ -119,6 +116,8 @@ def test_finite_size_sampled_rows(path):
     # Output tail bits zero.
     if b.m % 64:
         assert int(got[-1]) >> (b.m % 64) == 0
+    if path in ("direct", "block_int8", "fft"):
+        return  # 1e15 bit products per run (3-21 s): sampled rows only
     # Linearity in the key holds at any size: h(x1 ^ x2) = h(x1) ^ h(x2).
     key2 = inputs.random_bits(b.n, 777)
     g2, _ = run_path(b.n, b.m, key2, seed, path=path)
