@@ -273,8 +273,9 @@ int pa_batch_kernel_times(pa_batch_t batch, pa_kernel_time *out, int max, int *c
 /* Failure-detection self-test: runs a kernel whose bounded wait can never be satisfied
  * (which = 1: a dependency counter of the persistent launch that nothing signals;
  * which = 2: an mbarrier expecting bytes that never arrive) and stores the kernel's
- * device status in *device_status; PA_ERR_TIMEOUT is the expected value. Takes about
- * one to four seconds; synchronises the device. The GPU context remains usable. */
+ * device status in *device_status; PA_ERR_TIMEOUT is the expected value. Every bounded
+ * device wait gives up after 4 s (plus 0.5 s for copies in flight), so this takes about
+ * four to five seconds; synchronises the device. The GPU context remains usable. */
 int pa_selftest(int which, int *device_status);
 
 const char *pa_strerror(int status);

@@ -119,10 +119,8 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
 }
 
 // Bounded wait for the completion of the mbarrier phase with this parity (no status write).
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+    return mbar_wait_for(bar, parity, limit_ns);
 }
 
 // grid.x: contraction chunks of `chunk` positions; grid.y: output tiles of 256 blocks.
@@ -233,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
     bool ok = !bad;
     if (issued > 0) {
         const int last = issued - 1;
-        if (!tc_wait(&bar[last & 1], (last >> 1) & 1)) ok = false;
+        if (!tc_wait(&bar[last & 1], (last >> 1) & 1, bad ? kDrainNs : kWaitNs)) ok = false;
     }
     if (__syncthreads_or(!ok) || issued == 0) {
         if (tid == 0 && (bad || issued > 0)) set_status(status, PA_ERR_TIMEOUT);

@@ -9,8 +9,18 @@
 
 namespace pa {
 
-// Bounded spin: after this many polls a wait gives up and reports PA_ERR_TIMEOUT.
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Bounded waits are limited in time (the global nanosecond timer), not in polls: one
+// mbarrier poll may suspend the thread for a hardware-chosen interval. A wait gives up
+// after kWaitNs and reports PA_ERR_TIMEOUT; a wait that only lets copies already in
+// flight land before the kernel returns is limited to kDrainNs.
+constexpr uint64_t kWaitNs = 4000000000ull;
+constexpr uint64_t kDrainNs = 500000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
@@ -65,12 +75,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
 // Wait for phase completion with an iteration limit. On timeout the status word
 // records PA_ERR_TIMEOUT, and a second bounded wait gives copies still in flight
 // time to land before the caller returns. Returns true when the phase completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *status) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+// Polls the phase until it completes or `limit_ns` have passed since the first poll.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t phase, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 0;; ++i) {
         if (mbar_try_wait(bar, phase)) return true;
+        if ((i & 15u) == 15u && global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *status) {
+    if (mbar_wait_for(bar, phase, kWaitNs)) return true;
     set_status(status, PA_ERR_TIMEOUT);
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
-        if (mbar_try_wait(bar, phase)) break;
+    mbar_wait_for(bar, phase, kDrainNs);
     return false;
 }
 
@@ -85,9 +102,9 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
 __device__ __forceinline__ bool wait_count(const uint32_t *c, uint32_t target, int *status, int *flag) {
     if (threadIdx.x == 0) {
         int ok = 1;
-        uint32_t it = 0;
+        const uint64_t t0 = global_ns();
         while (ld_acquire(c) < target) {
-            if (++it > kSpinLimit) {
+            if (global_ns() - t0 > kWaitNs) {
                 set_status(status, PA_ERR_TIMEOUT);
                 ok = 0;
                 break;

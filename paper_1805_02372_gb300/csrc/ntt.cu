@@ -586,7 +586,9 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
                                       size_t(ColMajor::words(1 << t.logN, 2)) * elem);
         } else {
             const int logC1 = static_cast<int>(t.logC1), logC2 = static_cast<int>(t.logC2);
-            smem = std::max(smem, (size_t(1) << t.logR1) * twsz + (size_t(1) << (t.logR1 + logC1)) * elem);
+            const int seglog = logC1 - (elem == 4 ? 3 : 2);
+            smem = std::max(smem, (size_t(1) << t.logR1) * twsz + (size_t(1) << (t.logR1 + logC1)) * elem +
+                                      size_t(p1tw_words(static_cast<int>(t.logR1), seglog)) * elem);
             smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
                                       size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
         }

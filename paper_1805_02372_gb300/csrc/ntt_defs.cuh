@@ -79,6 +79,12 @@ inline void pass_columns(int logN, size_t elem, int *logC1, int *logC2) {
     *logC2 = std::min(c2, logR1);
 }
 
+// Words of the pass-1 twiddle tables of a forward item (p1tw_build in ntt_kernel.cuh):
+// per segment column 32 + R1/32 entries, and 32 + R1/32 shared ones (needs R1 >= 32).
+__host__ __device__ constexpr int p1tw_words(int logR1, int seglog) {
+    return ((1 << seglog) + 1) * (32 + (1 << (logR1 - 5)));
+}
+
 // Per-device tables: fwd[e] = w^e, inv[e] = w^-e for e < 2^(kLogMax-1), w of order 2^kLogMax.
 struct Tables {
     void *fwd = nullptr, *inv = nullptr;

@@ -144,6 +144,27 @@ __device__ __forceinline__ void row_twiddle(typename F::T (&x)[C], const typenam
     }
 }
 
+// Pass-1 twiddles of a forward item without a table lookup per row. Row r holds
+// frequency f = brev(r) = 32 fh + fl, and segment sg starts at column t0 = c0 + sg SEG, so
+// w^(t0 f) = w^(t0 fl) w^(32 t0 fh) and w^f = w^fl w^(32 fh): per segment column the
+// tables A[fl] = w^(t0 fl), B[fh] = w^(32 t0 fh), and once C[fl] = w^fl, D[fh] = w^(32 fh),
+// all in full form, give every row's first twiddle and step with one product each.
+// Layout (F::T): per sg, A (32) then B (R1 / 32); then C, D.
+template <class F>
+__device__ void p1tw_build(typename F::T *tb, const typename F::Tw *__restrict__ tab, uint64_t c0,
+                           int seg, int seglog, int logR1, int logN) {
+    const int per = 32 + (1 << (logR1 - 5));
+    const int total = p1tw_words(logR1, seglog);
+    const int sh = kLogMax - logN;
+    const uint64_t mask = (uint64_t(1) << logN) - 1;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int sg = i / per, k = i - sg * per;
+        const uint64_t t0 = sg < (1 << seglog) ? c0 + uint64_t(sg) * seg : 1;
+        const uint64_t e = (k < 32 ? t0 * uint64_t(k) : t0 * 32 * uint64_t(k - 32)) & mask;
+        tb[i] = F::full_form(tw_at<F>(tab, static_cast<uint32_t>(e << sh)));
+    }
+}
+
 // Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1); each
 // thread handles 32-byte row segments (SEG columns).
 template <class F>
@@ -157,6 +178,8 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
     const uint64_t c0 = cg << logC;
     const RowMajor lay{logC};
     const int seglog = logC - logSEG;  // segments per row (log2)
+    T *tb = sm + (R1 << logC);         // pass-1 twiddle tables (p1tw_build)
+    p1tw_build<F>(tb, tfwd, c0, SEG, seglog, logR1, logN);
     for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
         const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
         const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG);
@@ -167,12 +190,23 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
     }
     __syncthreads();
     dif_columns<F, true>(sm, lay, logR1, logC, st);
+    const int per = 32 + (1 << (logR1 - 5));
+    const T *tc = tb + (per << seglog);
     for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
         const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
         T x[SEG];
         seg_load<T>(x, sm + lay.at(r, sg * SEG));
-        row_twiddle<F, SEG>(x, tfwd, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
-                            logN);
+        const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
+        const T *ta = tb + sg * per;
+        const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);  // w^(t0 f), full form
+        const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);  // w^f, full form
+        x[0] = F::mul_full(x[0], base);
+        T wf = base;
+#pragma unroll
+        for (int c = 1; c < SEG; ++c) {
+            wf = F::mul_full(wf, step);
+            x[c] = F::mul_full(x[c], wf);
+        }
         uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
         __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
         __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[SEG / 2]));

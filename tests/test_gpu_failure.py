@@ -13,7 +13,11 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("which", [1, 2])
 def test_bounded_wait_reports_timeout(which):
+    import time
+    t0 = time.perf_counter()
     assert pkg.binding.pa_selftest(which) == binding.PA_ERR_TIMEOUT
+    # the wait is bounded in time (4 s, plus at most 0.5 s of draining), not in polls
+    assert 3.5 < time.perf_counter() - t0 < 15.0
     # the context is still usable: a hash right after is bit-exact
     b = inputs.single_block(50_001, 7_777, 91, 92)
     got, _ = run_path(b.n, b.m, b.key(), b.seed(), path="auto")
