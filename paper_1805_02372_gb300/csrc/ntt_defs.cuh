@@ -69,11 +69,13 @@ struct FdBlock {
 };
 
 // Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
-// segment, and enough to give a 512-thread CTA about 8192 (32-bit) elements per item.
+// segment, and enough to give a 512-thread CTA about 8192 (32-bit) elements per item in
+// pass 2 and 16384 in passes 1 and 3 (two radix-16 groups per thread and round, for
+// latency hiding; pass-2 items hold two or three column sets and stay at 8192).
 inline void pass_columns(int logN, size_t elem, int *logC1, int *logC2) {
     const int logR1 = (logN + 1) / 2, logR2 = logN / 2, logS = logN - logR1;
     const int target = elem == 4 ? 13 : 12;
-    int c1 = std::max(elem == 4 ? 3 : 2, target - logR1);
+    int c1 = std::max(elem == 4 ? 3 : 2, target + 1 - logR1);
     int c2 = std::max(elem == 4 ? 2 : 1, target - logR2);
     *logC1 = std::min(c1, logS);
     *logC2 = std::min(c2, logR1);

@@ -127,24 +127,7 @@ __device__ __forceinline__ void seg_load(T (&x)[32 / sizeof(T)], const T *p) {
     *reinterpret_cast<uint4 *>(&x[H]) = h ? f : g;
 }
 
-// Row r of a pass-1 column group holds frequency f = brev(r); its C columns t = c0 + c
-// need the twiddles w_N^(t f): w_N^(c0 f) from the table, then powers of w_N^f.
-template <class F, int C>
-__device__ __forceinline__ void row_twiddle(typename F::T (&x)[C], const typename F::Tw *tab,
-                                            uint64_t c0, uint32_t f, int logN) {
-    const int sh = kLogMax - logN;
-    const typename F::Tw w0 = tw_at<F>(tab, static_cast<uint32_t>((c0 * f) << sh));
-    const typename F::Tw step = tw_at<F>(tab, f << sh);
-    typename F::T wf = F::full_form(w0);
-    x[0] = F::mul_tw(x[0], w0);
-#pragma unroll
-    for (int c = 1; c < C; ++c) {
-        wf = F::step_full(wf, step);
-        x[c] = F::mul_full(x[c], wf);
-    }
-}
-
-// Pass-1 twiddles of a forward item without a table lookup per row. Row r holds
+// Pass-1 twiddles (forward and inverse items) without a table lookup per row. Row r holds
 // frequency f = brev(r) = 32 fh + fl, and segment sg starts at column t0 = c0 + sg SEG, so
 // w^(t0 f) = w^(t0 fl) w^(32 t0 fh) and w^f = w^fl w^(32 fh): per segment column the
 // tables A[fl] = w^(t0 fl), B[fh] = w^(32 t0 fh), and once C[fl] = w^fl, D[fh] = w^(32 fh),
@@ -267,15 +250,39 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
     const uint64_t c0 = cg << logC;
     const RowMajor lay{logC};
     const int seglog = logC - logSEG;
+    // the inverse twiddles w^-(t f) from short tables (p1tw_build with the inverse roots),
+    // looked up while the rows load, applied in one pass over shared memory
+    T *tb = sm + (R1 << logC);
+    p1tw_build<F>(tb, tinv, c0, SEG, seglog, logR1, logN);
     for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
         const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
         T x[SEG];
         const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0 + sg * SEG);
         *reinterpret_cast<uint4 *>(&x[0]) = __ldcg(g);
         *reinterpret_cast<uint4 *>(&x[SEG / 2]) = __ldcg(g + 1);
-        row_twiddle<F, SEG>(x, tinv, c0 + sg * SEG, __brev(static_cast<uint32_t>(r)) >> (32 - logR1),
-                            logN);
         seg_store<T>(sm + lay.at(r, sg * SEG), x);
+    }
+    __syncthreads();
+    {
+        const int per = 32 + (1 << (logR1 - 5));
+        const T *tc = tb + (per << seglog);
+        for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+            const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+            T x[SEG];
+            seg_load<T>(x, sm + lay.at(r, sg * SEG));
+            const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
+            const T *ta = tb + sg * per;
+            const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);
+            const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);
+            x[0] = F::mul_full(x[0], base);
+            T wf = base;
+#pragma unroll
+            for (int c = 1; c < SEG; ++c) {
+                wf = F::mul_full(wf, step);
+                x[c] = F::mul_full(x[c], wf);
+            }
+            seg_store<T>(sm + lay.at(r, sg * SEG), x);
+        }
     }
     __syncthreads();
     dit_columns<F, true>(sm, lay, logR1, logC, st);
