@@ -127,6 +127,19 @@ __device__ __forceinline__ void seg_load(T (&x)[32 / sizeof(T)], const T *p) {
     *reinterpret_cast<uint4 *>(&x[H]) = h ? f : g;
 }
 
+// Global loads a thread keeps in flight before storing them to shared memory.
+constexpr int kLoadBatch = 2;
+
+// Asynchronous global -> shared copies (no registers held while they are in flight);
+// cp_async_wait_all waits for this thread's copies, a barrier then publishes them.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Pass-1 twiddles (forward and inverse items) without a table lookup per row. Row r holds
 // frequency f = brev(r) = 32 fh + fl, and segment sg starts at column t0 = c0 + sg SEG, so
 // w^(t0 f) = w^(t0 fl) w^(32 t0 fh) and w^f = w^fl w^(32 fh): per segment column the
@@ -163,13 +176,27 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
     const int seglog = logC - logSEG;  // segments per row (log2)
     T *tb = sm + (R1 << logC);         // pass-1 twiddle tables (p1tw_build)
     p1tw_build<F>(tb, tfwd, c0, SEG, seglog, logR1, logN);
-    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
-        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
-        const uint32_t bits = tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG);
-        T x[SEG];
+    // up to kLoadBatch segments per thread: every load issued before the first store
+    for (int e0 = threadIdx.x; e0 < (R1 << seglog); e0 += kLoadBatch * blockDim.x) {
+        uint32_t bits[kLoadBatch];
 #pragma unroll
-        for (int c = 0; c < SEG; ++c) x[c] = (bits >> c) & 1u;
-        seg_store<T>(sm + lay.at(r, sg * SEG), x);
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+            bits[u] = e < (R1 << seglog)
+                          ? tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG)
+                          : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= (R1 << seglog)) break;
+            const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+            T x[SEG];
+#pragma unroll
+            for (int c = 0; c < SEG; ++c) x[c] = (bits[u] >> c) & 1u;
+            seg_store<T>(sm + lay.at(r, sg * SEG), x);
+        }
     }
     __syncthreads();
     dif_columns<F, true>(sm, lay, logR1, logC, st);
@@ -211,15 +238,24 @@ __device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
     const uint64_t base = (rg << logC) << logR2;
     const ColMajor lay{ColMajor::stride(R2)};
     const int cnt = R2 << logC;
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(X + base + e));
-        const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(W + base + e));
-        const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+    if (sizeof(T) == 4) {
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            cp_async4(sm + lay.at(r, c), X + base + e);
+            cp_async4(sm + lay.at(r, C + c), W + base + e);
+        }
+        cp_async_wait_all();
+    } else {
+        for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(X + base + e));
+            const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(W + base + e));
+            const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            sm[lay.at(r + k, c)] = xs[k];
-            sm[lay.at(r + k, C + c)] = ws[k];
+            for (int k = 0; k < V; ++k) {
+                sm[lay.at(r + k, c)] = xs[k];
+                sm[lay.at(r + k, C + c)] = ws[k];
+            }
         }
     }
     __syncthreads();
@@ -254,13 +290,16 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
     // looked up while the rows load, applied in one pass over shared memory
     T *tb = sm + (R1 << logC);
     p1tw_build<F>(tb, tinv, c0, SEG, seglog, logR1, logN);
-    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
-        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
-        T x[SEG];
-        const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0 + sg * SEG);
-        *reinterpret_cast<uint4 *>(&x[0]) = __ldcg(g);
-        *reinterpret_cast<uint4 *>(&x[SEG / 2]) = __ldcg(g + 1);
-        seg_store<T>(sm + lay.at(r, sg * SEG), x);
+    {
+        const uint32_t h = (threadIdx.x >> 2) & 1u;  // half order of seg_store
+        for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
+            const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+            const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0 + sg * SEG);
+            uint4 *d = reinterpret_cast<uint4 *>(sm + lay.at(r, sg * SEG));
+            cp_async16(d + h, g + h);
+            cp_async16(d + (h ^ 1u), g + (h ^ 1u));
+        }
+        cp_async_wait_all();
     }
     __syncthreads();
     {
@@ -421,15 +460,24 @@ __device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
     for (uint32_t J = 0; J < Q; ++J) {
         const T *xj = X + uint64_t(J) * N + base;
         const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
-        for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-            const int c = e >> logR2, r = e & (R2 - 1);
-            const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
-            const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
-            const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+        if (sizeof(T) == 4) {
+            for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+                const int c = e >> logR2, r = e & (R2 - 1);
+                cp_async4(sm + lay.at(r, c), xj + e);
+                cp_async4(sm + lay.at(r, C + c), wj + e);
+            }
+            cp_async_wait_all();
+        } else {
+            for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+                const int c = e >> logR2, r = e & (R2 - 1);
+                const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
+                const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
+                const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
 #pragma unroll
-            for (int k = 0; k < V; ++k) {
-                sm[lay.at(r + k, c)] = xs[k];
-                sm[lay.at(r + k, C + c)] = ws[k];
+                for (int k = 0; k < V; ++k) {
+                    sm[lay.at(r + k, c)] = xs[k];
+                    sm[lay.at(r + k, C + c)] = ws[k];
+                }
             }
         }
         __syncthreads();
@@ -473,6 +521,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint64_t cur;
     __shared__ int flag;
+    // Stage tables stay in shared memory across items: slot 0 at st0 and slot 1 right
+    // after it hold (direction, log2 R) = skey[slot] (-1: nothing valid). A body whose tile
+    // starts right after slot 0 overwrites slot 1.
+    __shared__ int skey[2];
+    if (threadIdx.x == 0) skey[0] = skey[1] = -1;
     uint32_t *c1 = cnt, *c2 = cnt + ntiles, *c3 = cnt + 2 * uint64_t(ntiles);
     uint32_t *next = cnt + 3 * uint64_t(ntiles), *cfd = next + 1, *cfd1 = cfd + nfd;
     Tw *st0 = reinterpret_cast<Tw *>(smraw);
@@ -483,6 +536,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
         }
         __syncthreads();
         const uint64_t it = cur;
+        const int k0 = skey[0], k1 = skey[1];
         __syncthreads();
         if (it == ~0ull) break;
         const uint32_t type = static_cast<uint32_t>(it >> 60);
@@ -500,8 +554,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
         switch (type) {
             case IT_SMALL: {
                 Tw *sti = st0 + (1 << logN);
-                load_stage<F>(st0, stage, 0, logN);
-                load_stage<F>(sti, stage, 1, logN);
+                if (k0 != logN) load_stage<F>(st0, stage, 0, logN);
+                if (k0 != logN || k1 != 32 + logN) load_stage<F>(sti, stage, 1, logN);
                 body_small<F>(reinterpret_cast<T *>(sti + (1 << logN)), st0, sti, tl.p, bp, logN, scale);
                 break;
             }
@@ -510,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 bool ok = true;
                 if (ti >= slots) ok = wait_count(c3 + (ti - slots), tiles[ti - slots].g1, status, &flag);
                 const int which = sub >= tl.g1 ? 1 : 0;
-                load_stage<F>(st0, stage, 0, logR1);
+                if (k0 != logR1) load_stage<F>(st0, stage, 0, logR1);
                 if (ok)
                     body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, which,
                                       sub - which * tl.g1, logN, logR1, logC1, which ? W : X, tfwd);
@@ -519,8 +573,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
             }
             case IT_P2: {
                 Tw *sti = st0 + (1 << logR2);
-                load_stage<F>(st0, stage, 0, logR2);
-                load_stage<F>(sti, stage, 1, logR2);
+                if (k0 != logR2) load_stage<F>(st0, stage, 0, logR2);
+                if (k0 != logR2 || k1 != 32 + logR2) load_stage<F>(sti, stage, 1, logR2);
                 if (wait_count(c1 + ti, 2 * tl.g1, status, &flag))
                     body_fused_last<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
                                        logC2, X, W);
@@ -528,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 break;
             }
             case IT_P3: {
-                load_stage<F>(st0, stage, 1, logR1);
+                if (k0 != 32 + logR1) load_stage<F>(st0, stage, 1, logR1);
                 if (wait_count(c2 + ti, tl.g2, status, &flag))
                     body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
                                       logN, logR1, logC1, W, tinv, scale);
@@ -536,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 break;
             }
             case IT_FD_P1: {
-                load_stage<F>(st0, stage, 0, logR1);
+                if (k0 != logR1) load_stage<F>(st0, stage, 0, logR1);
                 body_fwd_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp,
                                   static_cast<int>(tl.which), sub, logN, logR1, logC1, X, tfwd);
                 signal_count(c1 + ti);
@@ -544,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 break;
             }
             case IT_FD_P2: {
-                load_stage<F>(st0, stage, 0, logR2);
+                if (k0 != logR2) load_stage<F>(st0, stage, 0, logR2);
                 if (wait_count(c1 + ti, tl.g1, status, &flag))
                     body_fwd_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2, logC2, X);
                 signal_count(cfd + tl.fd);
@@ -552,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
             }
             case IT_FD_SUM: {
                 const FdBlock fb = fds[tl.fd];
-                load_stage<F>(st0, stage, 1, logR2);
+                if (k0 != 32 + logR2) load_stage<F>(st0, stage, 1, logR2);
                 if (wait_count(cfd + tl.fd, fb.nfwd2, status, &flag))
                     body_sum_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
                                          logC2, ws + fb.x_off, ws + fb.w_off,
@@ -564,8 +618,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
             case IT_FD_STREAM: {
                 const FdBlock fb = fds[tl.fd];
                 Tw *sti = st0 + (1 << logR2);
-                load_stage<F>(st0, stage, 0, logR2);
-                load_stage<F>(sti, stage, 1, logR2);
+                if (k0 != logR2) load_stage<F>(st0, stage, 0, logR2);
+                if (k0 != logR2 || k1 != 32 + logR2) load_stage<F>(sti, stage, 1, logR2);
                 if (wait_count(cfd1 + tl.fd, fb.nfwd1, status, &flag))
                     body_stream_sum<F>(reinterpret_cast<T *>(sti + (1 << logR2)), st0, sti, sub, logR2,
                                        logC2, ws + fb.x_off, ws + fb.w_off, wmap + fb.wmap, fb.Q,
@@ -574,12 +628,25 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 break;
             }
             default: {  // IT_FD_P3
-                load_stage<F>(st0, stage, 1, logR1);
+                if (k0 != 32 + logR1) load_stage<F>(st0, stage, 1, logR1);
                 if (wait_count(c2 + ti, tl.g2, status, &flag))
                     body_inv_first<F>(reinterpret_cast<T *>(st0 + (1 << logR1)), st0, tl.p, bp, sub,
                                       logN, logR1, logC1, X, tinv, scale);
                 __syncthreads();
                 break;
+            }
+        }
+        if (threadIdx.x == 0) {
+            switch (type) {
+                case IT_SMALL: skey[0] = logN; skey[1] = 32 + logN; break;
+                case IT_P2:
+                case IT_FD_STREAM: skey[0] = logR2; skey[1] = 32 + logR2; break;
+                case IT_P1:
+                case IT_FD_P1: skey[0] = logR1; skey[1] = -1; break;
+                case IT_P3:
+                case IT_FD_P3: skey[0] = 32 + logR1; skey[1] = -1; break;
+                case IT_FD_P2: skey[0] = logR2; skey[1] = -1; break;
+                default: skey[0] = 32 + logR2; skey[1] = -1; break;  // IT_FD_SUM
             }
         }
     }
