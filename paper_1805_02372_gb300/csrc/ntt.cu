@@ -546,17 +546,21 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
         if (t >= 2 && t - 2 < nb)
             for (uint32_t k = 0; k < big[t - 2].g1; ++k) push(IT_P3, t - 2, k);
     }
-    // streamed blocks, pipelined the same way: pass 1 of all spectra of block t, the
-    // sums of block t-1, inverse pass 1 of block t-2
+    // streamed blocks, pipelined: pass 1 of all spectra of block t, the sums of block
+    // t - kStreamLag, inverse pass 1 of block t - 2 kStreamLag (every streamed block has
+    // its own spectra storage, so the distance costs no memory and keeps the waits short)
+    constexpr size_t kStreamLag = 2;
     const size_t ns = st_sum.size();
-    for (size_t t = 0; t < ns + 2; ++t) {
+    for (size_t t = 0; t < ns + 2 * kStreamLag; ++t) {
         if (t < ns)
             for (size_t i = st_range[t].first; i < st_range[t].second; ++i)
                 for (uint32_t k = 0; k < st_spec[i].g1; ++k) push(IT_FD_P1, i_sspec + i, k);
-        if (t >= 1 && t - 1 < ns)
-            for (uint32_t k = 0; k < st_sum[t - 1].g2; ++k) push(IT_FD_STREAM, i_ssum + t - 1, k);
-        if (t >= 2 && t - 2 < ns)
-            for (uint32_t k = 0; k < st_sum[t - 2].g1; ++k) push(IT_FD_P3, i_ssum + t - 2, k);
+        if (t >= kStreamLag && t - kStreamLag < ns)
+            for (uint32_t k = 0; k < st_sum[t - kStreamLag].g2; ++k)
+                push(IT_FD_STREAM, i_ssum + t - kStreamLag, k);
+        if (t >= 2 * kStreamLag && t - 2 * kStreamLag < ns)
+            for (uint32_t k = 0; k < st_sum[t - 2 * kStreamLag].g1; ++k)
+                push(IT_FD_P3, i_ssum + t - 2 * kStreamLag, k);
     }
     // fd sums row group by row group (the outputs of one block share their operands'
     // rows in L2), then the inverse first passes
