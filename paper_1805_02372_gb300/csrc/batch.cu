@@ -36,6 +36,10 @@ struct Tuner {
     double block_tc = 0;         // tcgen05 FP8: s per (256-block output tile x (n + 32640))
     double fft = 0;              // s per tile of the default FP32 geometry (per unit N log N)
     double ntt[2][kTuneLogMax + 1] = {};  // s per tile of size 2^k, field 0 / 1
+    // latency floors of a single plan (one launch sequence, nothing else on the GPU): one
+    // standalone tile pair of size 2^k, and small direct and FP8 blocks (n = 2^16, m = 2^13)
+    double ntt1[2][kTuneLogMax + 1] = {};
+    double direct1 = 0, block_tc1 = 0;
     double launch = 3e-6;        // s per launch
 };
 
@@ -163,7 +167,10 @@ int calibrate(Tuner *t) {
     {
         const uint64_t n = uint64_t(1) << 20, m = uint64_t(1) << 17;
         t->block_tc = tplan(n, m, o, &cfg) / (double(ceil_div(m, 32768)) * double(n + 32640));
+        t->block_tc1 = tplan(uint64_t(1) << 16, uint64_t(1) << 13, o, &cfg);
     }
+    o.path = PA_PATH_DIRECT;
+    t->direct1 = tplan(uint64_t(1) << 16, uint64_t(1) << 13, o, &cfg);
     o.path = PA_PATH_FFT;
     {
         const uint64_t n = uint64_t(1) << 18, m = uint64_t(1) << 13;
@@ -183,6 +190,7 @@ int calibrate(Tuner *t) {
             o.fd_mode = 1;  // calibrate standard pairs
             const double tt = tplan(L * tiles, M, o, &cfg);
             t->ntt[f][k] = tt / double(cfg.tr.tiles_in * cfg.tr.tiles_out);
+            t->ntt1[f][k] = tplan(L, M, o, &cfg);
         }
         o.log2_transform = 0;
         o.tile_in = o.tile_out = 0;
@@ -206,10 +214,14 @@ bool load_cache(Tuner *t, const char *path, const char *dev_name) {
         name[strcspn(name, "\n")] = 0;
         ok = strcmp(name, dev_name) == 0;
     }
-    ok = ok && fscanf(f, "%lf %lf %lf %lf %lf %lf", &t->direct, &t->block[0], &t->block[1],
-                      &t->block[2], &t->block_tc, &t->fft) == 6;
+    int version = 0;
+    ok = ok && fscanf(f, "v%d", &version) == 1 && version == 2;
+    ok = ok && fscanf(f, "%lf %lf %lf %lf %lf %lf %lf %lf", &t->direct, &t->block[0], &t->block[1],
+                      &t->block[2], &t->block_tc, &t->fft, &t->direct1, &t->block_tc1) == 8;
     for (int fl = 0; ok && fl < 2; ++fl)
         for (int k = 0; ok && k <= kTuneLogMax; ++k) ok = fscanf(f, "%lf", &t->ntt[fl][k]) == 1;
+    for (int fl = 0; ok && fl < 2; ++fl)
+        for (int k = 0; ok && k <= kTuneLogMax; ++k) ok = fscanf(f, "%lf", &t->ntt1[fl][k]) == 1;
     fclose(f);
     t->valid = ok;
     return ok;
@@ -218,10 +230,14 @@ bool load_cache(Tuner *t, const char *path, const char *dev_name) {
 void save_cache(const Tuner &t, const char *path, const char *dev_name) {
     FILE *f = fopen(path, "w");
     if (!f) return;
-    fprintf(f, "%s\n%.6e %.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0], t.block[1],
-            t.block[2], t.block_tc, t.fft);
+    fprintf(f, "%s\nv2\n%.6e %.6e %.6e %.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0],
+            t.block[1], t.block[2], t.block_tc, t.fft, t.direct1, t.block_tc1);
     for (int fl = 0; fl < 2; ++fl) {
         for (int k = 0; k <= kTuneLogMax; ++k) fprintf(f, "%.6e ", t.ntt[fl][k]);
+        fprintf(f, "\n");
+    }
+    for (int fl = 0; fl < 2; ++fl) {
+        for (int k = 0; k <= kTuneLogMax; ++k) fprintf(f, "%.6e ", t.ntt1[fl][k]);
         fprintf(f, "\n");
     }
     fclose(f);
@@ -261,8 +277,11 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
     pa_opts o;
     memset(&o, 0, sizeof(o));
     o.device = -1;
+    // a single plan cannot beat the latency of its own launch sequence: floors measured on
+    // small blocks (batched blocks share their launches, so no floor applies)
+    const auto floor = [batched](double est, double fl) { return batched ? est : std::max(est, fl); };
     o.path = PA_PATH_DIRECT;
-    consider(t.direct * double(n) * double(m) + 2 * t.launch, o);
+    consider(floor(t.direct * double(n) * double(m) + 2 * t.launch, t.direct1), o);
     o.path = PA_PATH_BLOCK_INT8;
     for (int i = 0; i < 3; ++i) {
         o.block_b = 128u << i;
@@ -270,7 +289,8 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
     }
     o.block_b = 0;
     o.path = PA_PATH_BLOCK_FP8;
-    consider(t.block_tc * double(ceil_div(m, 32768)) * double(n + 32640) + 3 * t.launch, o);
+    consider(floor(t.block_tc * double(ceil_div(m, 32768)) * double(n + 32640) + 3 * t.launch, t.block_tc1),
+             o);
     // FFT path at its usual proven geometry (N = 2^12, L = 1536, M = 2560)
     o.path = PA_PATH_FFT;
     consider(t.fft * double(ceil_div(n, 1536)) * double(ceil_div(m, 2560)) * 4096.0 * 14.0 +
@@ -297,7 +317,7 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 o.log2_transform = static_cast<uint32_t>(k);
                 o.tile_out = M;
                 o.tile_in = L;
-                consider(units * t.ntt[f][k] + launches * t.launch, o);
+                consider(floor(units * t.ntt[f][k] + launches * t.launch, t.ntt1[f][k]), o);
             }
         }
         o.log2_transform = 0;
