@@ -91,10 +91,11 @@ typedef struct {
     uint64_t n, m;
     int32_t path;              /* resolved pa_path                                        */
     uint32_t log2_transform;   /* transform size N = 2^log2_transform (transform paths)   */
-    uint64_t tile_in;          /* key sub-block length L                                  */
-    uint64_t tile_out;         /* output sub-block length M                               */
-    uint64_t tiles_in;         /* p: number of key sub-blocks                             */
-    uint64_t tiles_out;        /* q: number of output sub-blocks                          */
+    uint64_t tile_in;          /* key sub-block length L (block FP8: contraction positions
+                                  per CTA chunk)                                          */
+    uint64_t tile_out;         /* output sub-block length M (block FP8: outputs per tile)  */
+    uint64_t tiles_in;         /* p: number of key sub-blocks (block FP8: chunks per tile) */
+    uint64_t tiles_out;        /* q: number of output sub-blocks (block FP8: output tiles) */
     uint32_t block_b;          /* block path tile edge                                    */
     uint32_t fp64;             /* FFT path runs FP64 butterflies                          */
     double rounding_bound;     /* FFT path: proven bound on |v - rint(v)|, else 0         */

@@ -81,7 +81,15 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->tile_in = cfg.n;
         d->tile_out = cfg.m;
         d->tiles_in = d->tiles_out = 1;
-    } else if (cfg.path == PA_PATH_BLOCK_INT8 || cfg.path == PA_PATH_BLOCK_FP8) {
+    } else if (cfg.path == PA_PATH_BLOCK_FP8) {
+        // tcgen05 kernel: contraction chunks of tile_in positions (one CTA each, FP32 sums
+        // exact because tile_in <= 2^15), output tiles of 256 blocks of b rows
+        d->block_b = cfg.blk.b;
+        d->tile_in = cfg.blk.kc;
+        d->tiles_in = cfg.blk.grid_x;
+        d->tile_out = uint64_t(cfg.blk.b) * 256;
+        d->tiles_out = cfg.blk.grid_y;
+    } else if (cfg.path == PA_PATH_BLOCK_INT8) {
         d->block_b = cfg.blk.b;
         d->tile_in = cfg.n;
         d->tile_out = cfg.m;

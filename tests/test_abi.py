@@ -83,3 +83,21 @@ def test_fft_fp64_only_where_fp32_bound_fails(lib):
     d = pkg.pa_plan_query(100_000, 50_000, binding.make_opts(path="fft", log2_transform=12,
                                                               tile_in=1024, tile_out=2048))
     assert d["fp64"] == 0 and d["rounding_bound"] < 0.5
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (100_003, 25_000), (1_000_000, 500_000),
+                                 (100_000_007, 10_000_000), (3_000_000, 40_000)])
+def test_plan_query_block_fp8(lib, n, m):
+    # The tcgen05 block kernel sums at most one chunk of contraction positions per CTA in
+    # FP32 (products 2^-12 each): chunks of at most 2^15 keep every partial sum exact. The
+    # chunks cover the contraction n + 128 * 255 of every output tile of 256 x 128 outputs.
+    d = pkg.pa_plan_query(n, m, binding.make_opts(path="block_fp8"))
+    assert d["path_name"] == "block_fp8" and d["block_b"] == 128
+    chunk, chunks, tiles = d["tile_in"], d["tiles_in"], d["tiles_out"]
+    assert chunk % 128 == 0 and 1024 <= chunk <= 1 << 15
+    assert chunks * chunk >= n + 128 * 255 > (chunks - 1) * chunk
+    assert d["tile_out"] == 32768 and tiles == -(-m // 32768)
+    assert d["kernels_per_call"] == 3
+    with pytest.raises(pkg.PAError) as e:
+        pkg.pa_plan_query(n, m, binding.make_opts(path="block_fp8", block_b=256))
+    assert e.value.status == binding.PA_ERR_INVALID
