@@ -597,10 +597,11 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
                                       size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
         }
     }
-    // streamed sums: key, window and accumulator columns
+    // streamed sums: key, window and accumulator columns, then the window indices
     for (const NttTile &t : st_sum)
         smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
-                                  size_t(ColMajor::words(1 << t.logR2, 3 << t.logC2)) * elem);
+                                  size_t(ColMajor::words(1 << t.logR2, 3 << t.logC2)) * elem +
+                                  size_t(fds[t.fd].Q) * sizeof(uint32_t));
     info->smem = smem;
     // workspace layout
     size_t off = 0;

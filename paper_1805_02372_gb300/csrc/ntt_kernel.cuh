@@ -456,10 +456,14 @@ __device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
     const ColMajor lay{ColMajor::stride(R2)};
     const int cnt = R2 << logC;
     T *acc = sm + 2 * C * lay.cs;
+    // the window index of every key tile, fetched once (not one dependent load per tile)
+    uint32_t *wix = reinterpret_cast<uint32_t *>(acc + C * lay.cs);
     for (int e = threadIdx.x; e < C * lay.cs; e += blockDim.x) acc[e] = 0;
+    for (uint32_t J = threadIdx.x; J < Q; J += blockDim.x) wix[J] = __ldg(wrow + J);
+    __syncthreads();
     for (uint32_t J = 0; J < Q; ++J) {
         const T *xj = X + uint64_t(J) * N + base;
-        const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
+        const T *wj = W + uint64_t(wix[J]) * N + base;
         if (sizeof(T) == 4) {
             for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
                 const int c = e >> logR2, r = e & (R2 - 1);
