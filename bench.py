@@ -57,6 +57,10 @@ def workload(name: str):
     if name == "finite_size":
         b = inputs.FINITE_SIZE
         return [b], {"workload": f"finite-size scale n={b.n} m={b.m}", "blocks": 1}
+    if name == "paper_scale":
+        # the upper range of the paper's length-compatible runs: 1 Gbit key, l = 10%
+        b = inputs.single_block(1_000_000_007, 100_000_000, 31, 32)
+        return [b], {"workload": f"paper scale n={b.n} m={b.m}", "blocks": 1}
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -26,10 +26,11 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
     int path = o ? o->path : PA_PATH_AUTO;
     if (path < PA_PATH_AUTO || path > PA_PATH_BLOCK_FP8) return PA_ERR_INVALID;
     if (path == PA_PATH_AUTO) {
-        // Cost model (measured on GB300, see the autotuner in batch.cu): the direct
-        // kernel wins while m*n is small; the exact 31-bit NTT wins beyond.
+        // Host-only rule (pa_plan_ex uses the autotuner's measured costs instead): the
+        // direct kernel while m*n is small; beyond, the exact NTT over a 32-bit prime
+        // while n is below it, else over the 64-bit prime.
         const double mn = double(n) * double(m);
-        path = (mn <= 4.0e9 || n >= 2013265921ull) ? PA_PATH_DIRECT : PA_PATH_NTT31;
+        path = mn <= 4.0e9 ? PA_PATH_DIRECT : (n >= kPrimeF31 ? PA_PATH_NTT64 : PA_PATH_NTT31);
         TransformCfg probe;
         if (path == PA_PATH_NTT31 && ntt_plan(n, m, path, o, &probe) != PA_OK)
             path = PA_PATH_NTT64;

@@ -101,3 +101,22 @@ def test_plan_query_block_fp8(lib, n, m):
     with pytest.raises(pkg.PAError) as e:
         pkg.pa_plan_query(n, m, binding.make_opts(path="block_fp8", block_b=256))
     assert e.value.status == binding.PA_ERR_INVALID
+
+
+@pytest.mark.parametrize("n,m,path,bits", [(1_000_000_007, 100_000_000, "ntt31", 31),
+                                           (300_000_007, 30_000_000, "ntt31", 29),
+                                           (3_000_000_000, 300_000_000, "ntt64", 64)])
+def test_plan_query_paper_scale(lib, n, m, path, bits):
+    # Paper-scale blocks (Fig. 3 reaches 1e10 bits): the exact transform over the smallest
+    # prime above every coefficient (counts <= n), with transform-domain accumulation so
+    # only (key + window + output) spectra of 2^22 elements are held.
+    d = pkg.pa_plan_query(n, m)
+    assert d["path_name"] == path and d["prime_bits"] == bits
+    assert d["log2_transform"] <= 22
+    if bits < 64:
+        # resident spectra: key tiles + distinct windows + outputs, about 4 (n + m) elements
+        assert d["fd"] == 1
+        assert d["workspace_bytes"] >= 4 * (d["tiles_in"] + d["windows"] + d["tiles_out"]) << 22
+    # the 64-bit plan at n = 3e9 would need about 106 GB of resident spectra, above the
+    # 32 GiB cap, so it uses standard tile pairs in 4 GiB of reused spectra slots
+    assert d["workspace_bytes"] < 24 * 2 ** 30

@@ -175,3 +175,18 @@ def test_block_fp8_full_chunks_all_ones(n, m):
     assert np.all(bits == (n & 1))
     if m % 64:
         assert int(got[-1]) >> (m % 64) == 0
+
+
+def test_paper_scale_block_sampled_rows():
+    # One block at the paper's upper range (Fig. 3: keys of 1e9 bits and more, l = 10%):
+    # n = 1e9 + 7, m = 1e8 through the autotuned plan (the 31-bit prime: counts reach n),
+    # checked on sampled rows the oracle evaluates one by one.
+    n, m = 1_000_000_007, 100_000_000
+    b = inputs.single_block(n, m, 31, 32)
+    key, seed = b.key(), b.seed()
+    got, desc = run_path(n, m, key, seed, path="auto")
+    assert desc["path_name"] in ("ntt31", "ntt64")
+    rng = np.random.default_rng(9)
+    rows = np.unique(np.concatenate([rng.integers(0, m, 200), [0, 1, 63, 64, m - 1]]))
+    want = oracle.hash_rows(n, m, seed, key, rows)
+    assert np.array_equal(oracle.unpack(got, m)[rows], want), desc
