@@ -559,24 +559,38 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
 
 // Release a batch. Server-owned batches free their memory in stream order and do not
 // synchronise the device; others synchronise their last stream first.
-// Copies the words of every segment; CTAs stride over the segments, threads over words
-// (four independent loads in flight per thread: the source may be host memory reached
-// over the CPU-GPU link, with a long latency).
+// Copies the words of every segment; CTAs stride over the segments, threads over
+// 16-byte vectors where both ends allow it (else words), eight loads in flight per
+// thread: the source may be host memory reached over the CPU-GPU link, with a long latency.
 __global__ void __launch_bounds__(256) copy_segments(const CopySeg *__restrict__ segs, uint32_t nseg) {
+    constexpr int U = 8;
     for (uint32_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const CopySeg g = segs[sg];
-        for (uint64_t i = threadIdx.x; i < g.words; i += 4 * uint64_t(blockDim.x)) {
-            uint64_t v[4];
+        uint64_t head = 0;  // words copied one by one before the vector part
+        const bool vec = ((reinterpret_cast<uintptr_t>(g.src) ^ reinterpret_cast<uintptr_t>(g.dst)) & 15u) == 0;
+        if (vec && (reinterpret_cast<uintptr_t>(g.src) & 15u)) head = 1;
+        if (head > g.words) head = g.words;
+        const uint64_t nv = vec ? (g.words - head) / 2 : 0;  // 16-byte vectors
+        const uint4 *vs = reinterpret_cast<const uint4 *>(g.src + head);
+        uint4 *vd = reinterpret_cast<uint4 *>(g.dst + head);
+        for (uint64_t i = threadIdx.x; i < nv; i += U * uint64_t(blockDim.x)) {
+            uint4 v[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const uint64_t j = i + u * uint64_t(blockDim.x);
-                if (j < g.words) v[u] = g.src[j];
+                if (j < nv) v[u] = vs[j];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const uint64_t j = i + u * uint64_t(blockDim.x);
-                if (j < g.words) g.dst[j] = v[u];
+                if (j < nv) vd[j] = v[u];
             }
+        }
+        // the words outside the vector part (all of them when the alignments differ)
+        const uint64_t tail0 = head + 2 * nv;
+        for (uint64_t w = threadIdx.x; w < head + (g.words - tail0); w += blockDim.x) {
+            const uint64_t k = w < head ? w : tail0 + (w - head);
+            g.dst[k] = g.src[k];
         }
     }
 }
