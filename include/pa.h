@@ -170,6 +170,16 @@ int pa_plan_status(pa_plan_t plan);
 int pa_hash_direct_static(uint64_t n, uint64_t m, const uint64_t *seed_bits,
                           const uint64_t *key_bits, uint64_t *out_bits, void *stream);
 
+/* The seed of the square matrix of Eq. 1 (Sec. 2.1): Eq. 1 writes an n x n Toeplitz matrix
+ * with the 2n-1 parameters t_0 .. t_{2n-2} (t_0 .. t_{n-1} down the first column, t_n ..
+ * t_{2n-2} along the first row after t_0). In this library's form T[i][j] = s[n-1+i-j] that
+ * is s[n-1+d] = t_d for d >= 0 and s[n-1-e] = t_{n-1+e} for e >= 1.
+ *   n       : matrix size, >= 1 (hash it with m = n).
+ *   t_bits  : host, ceil((2n-1)/64) words, bit d = t_d (LSB-first); bits >= 2n-1 ignored.
+ *   seed_bits: host, ceil((2n-1)/64) words, fully written, bits >= 2n-1 set to 0.
+ * Host only (no GPU, no allocation); PA_ERR_INVALID for n = 0 or a null pointer. */
+int pa_seed_from_eq1(uint64_t n, const uint64_t *t_bits, uint64_t *seed_bits);
+
 /* ---- Many independent blocks in one launch (Sec. 3: batches run in parallel) ---- */
 
 typedef struct {

@@ -98,6 +98,7 @@ class pa_kernel_time(ctypes.Structure):
 _VP = ctypes.c_void_p
 _U64 = ctypes.c_uint64
 SIGNATURES = {
+    "pa_seed_from_eq1": (ctypes.c_int, [_U64, _VP, _VP]),
     "pa_plan": (ctypes.c_int, [_U64, _U64, ctypes.POINTER(_VP)]),
     "pa_plan_ex": (ctypes.c_int, [_U64, _U64, ctypes.POINTER(pa_opts), ctypes.POINTER(_VP)]),
     "pa_plan_query": (ctypes.c_int, [_U64, _U64, ctypes.POINTER(pa_opts),
@@ -212,6 +213,18 @@ def make_opts(path=PA_PATH_AUTO, device=-1, log2_transform=0, block_b=0, tile_in
     o.tile_in, o.tile_out, o.force_fp64 = tile_in, tile_out, force_fp64
     o.max_slots, o.fd_mode, o.ntt_prime = max_slots, fd_mode, ntt_prime
     return o
+
+
+def pa_seed_from_eq1(n: int, t_bits):
+    """Seed words of Eq. 1's n x n matrix from its 2n-1 parameters t (packed u64 words)."""
+    import numpy as np
+    words = (2 * n - 1 + 63) // 64 if n > 0 else 1
+    t = np.ascontiguousarray(t_bits, dtype=np.uint64)
+    if t.size < words:
+        raise ValueError("t_bits needs ceil((2n-1)/64) words")
+    out = np.zeros(words, dtype=np.uint64)
+    _check(load().pa_seed_from_eq1(n, t.ctypes.data, out.ctypes.data), "pa_seed_from_eq1")
+    return out
 
 
 def pa_plan_query(n: int, m: int, opts: pa_opts | None = None) -> dict:

@@ -156,6 +156,19 @@ int pa_plan_query(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_desc *out
     return PA_OK;
 }
 
+int pa_seed_from_eq1(uint64_t n, const uint64_t *t_bits, uint64_t *seed_bits) {
+    if (n == 0 || !t_bits || !seed_bits || n > kMaxBits) return PA_ERR_INVALID;
+    const uint64_t len = 2 * n - 1, words = (len + 63) / 64;
+    for (uint64_t w = 0; w < words; ++w) seed_bits[w] = 0;
+    auto get = [t_bits](uint64_t i) { return (t_bits[i >> 6] >> (i & 63)) & 1u; };
+    auto set = [seed_bits](uint64_t i) { seed_bits[i >> 6] |= uint64_t(1) << (i & 63); };
+    for (uint64_t d = 0; d < n; ++d)  // on and below the diagonal
+        if (get(d)) set(n - 1 + d);
+    for (uint64_t e = 1; e < n; ++e)  // above it
+        if (get(n - 1 + e)) set(n - 1 - e);
+    return PA_OK;
+}
+
 int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
     if (!out) return PA_ERR_INVALID;
     *out = nullptr;

@@ -120,3 +120,24 @@ def test_plan_query_paper_scale(lib, n, m, path, bits):
     # the 64-bit plan at n = 3e9 would need about 106 GB of resident spectra, above the
     # 32 GiB cap, so it uses standard tile pairs in 4 GiB of reused spectra slots
     assert d["workspace_bytes"] < 24 * 2 ** 30
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 64, 65, 1000, 4097])
+def test_seed_from_eq1_matches_oracle(lib, n):
+    # The library's Eq. 1 helper against the oracle's (itself pinned to a literal Eq. 1
+    # matrix in test_oracle.py); the two are written independently.
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(n)
+    t = rng.integers(0, 2, 2 * n - 1, dtype=np.uint8)
+    words = (2 * n - 1 + 63) // 64
+    tw = np.zeros(words, dtype=np.uint64)
+    for i in np.flatnonzero(t):
+        tw[i >> 6] |= np.uint64(1) << np.uint64(i & 63)
+    tw[-1] |= ~np.uint64(0) << np.uint64((2 * n - 1) % 64) if (2 * n - 1) % 64 else np.uint64(0)
+    got = binding.pa_seed_from_eq1(n, tw)
+    assert np.array_equal(oracle.unpack(got, 2 * n - 1), oracle.seed_from_eq1(t))
+    if (2 * n - 1) % 64:
+        assert int(got[-1]) >> ((2 * n - 1) % 64) == 0
+    with pytest.raises(pkg.PAError):
+        binding.pa_seed_from_eq1(0, tw)
