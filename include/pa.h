@@ -137,8 +137,10 @@ int pa_hash(pa_plan_t plan, const uint64_t *seed_bits, const uint64_t *key_bits,
 int pa_hash_host(pa_plan_t plan, const uint64_t *seed_host, const uint64_t *key_host,
                  uint64_t *out_host, void *stream);
 
-/* Worst |v - rint(v)| seen by the FFT path in the plan's last call, with the
- * proven bound (synchronises the plan's stream). Other paths report 0. */
+/* Worst |v - rint(v)| seen in the plan's last call, with the proven bound (synchronises the
+ * plan's stream): the FFT path's rounded convolution values, and the block FP8 path's
+ * tensor-core sums scaled to counts (proven exact, bound 0, measured every run). The
+ * integer paths report 0. */
 int pa_last_residual(pa_plan_t plan, double *residual, double *bound);
 
 /* The proven bound on |v - rint(v)| used by the FFT path for a tile of transform

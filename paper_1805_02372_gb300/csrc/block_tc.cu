@@ -127,7 +127,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, uint64_t
 __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
     const uint32_t *__restrict__ seed32, uint64_t seed_words32, const uint32_t *__restrict__ xr,
     uint64_t xr_words32, uint64_t n, uint64_t m, uint32_t chunk, uint32_t *__restrict__ out32,
-    int *status) {
+    int *status, unsigned long long *residual_bits) {
     extern __shared__ __align__(1024) unsigned char smt[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_slot;
@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
         // 32 rows gives one output word per block, bits 128 (I0 + I) + 32 (w & 3) + [0, 32).
         const int q = warp & 3;
         const uint64_t out_words32 = 2 * ceil_div_dev(m, 64);
+        float rmax = 0.0f;  // |4096 acc - rint|: 0 whenever the sums are exact, as proven
         for (int c0 = 128 * (warp >> 2); c0 < 128 * (warp >> 2) + 128; c0 += 32) {
             uint32_t mine = 0;
 #pragma unroll
@@ -250,7 +251,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
                 tc_ld16(tmem + (uint32_t(32 * q) << 16) + c0 + 16 * h, v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const uint32_t cnt = __float2uint_rn(__uint_as_float(v[j]) * 4096.0f);
+                    const float x = __uint_as_float(v[j]) * 4096.0f;
+                    rmax = fmaxf(rmax, fabsf(x - rintf(x)));
+                    const uint32_t cnt = __float2uint_rn(x);
                     const uint32_t word = __ballot_sync(0xFFFFFFFFu, cnt & 1u);
                     if (lane == 16 * h + j) mine = word;
                 }
@@ -262,6 +265,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) block_tc_kernel(
                 if (mine) atomicXor(out32 + gw, mine);
             }
         }
+        // the worst pre-rounding residual, reported per run (pa_last_residual); one atomic
+        // per warp only when it is not zero
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xFFFFFFFFu, rmax, o));
+        if (lane == 0 && rmax > 0.0f)
+            atomicMax(residual_bits, static_cast<unsigned long long>(__double_as_longlong(double(rmax))));
     }
     tc_fence_before();
     __syncthreads();
@@ -311,7 +320,8 @@ int block_tc_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, co
     prof_begin(prof, K_BLOCK_TC, s);
     block_tc_kernel<<<dim3(c.grid_x, c.grid_y), kTcThreads, kTcSmem, s>>>(
         reinterpret_cast<const uint32_t *>(seed), 2 * ceil_div(cfg.n + cfg.m - 1, 64), xr, c.xr_words,
-        cfg.n, cfg.m, static_cast<uint32_t>(c.kc), reinterpret_cast<uint32_t *>(out), &hdr->status);
+        cfg.n, cfg.m, static_cast<uint32_t>(c.kc), reinterpret_cast<uint32_t *>(out), &hdr->status,
+        &hdr->residual_bits);
     prof_end(prof, s);
     PA_CUDA_TRY(cudaGetLastError());
     return PA_OK;

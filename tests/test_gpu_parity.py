@@ -173,6 +173,15 @@ def test_block_fp8_full_chunks_all_ones(n, m):
     got, _ = run_path(n, m, key, seed, path="block_fp8")
     bits = oracle.unpack(got, m)
     assert np.all(bits == (n & 1))
+    # the measured pre-rounding residual of the FP32 sums is exactly zero
+    import torch
+    from gpu_util import dev
+    plan = pkg.Plan(n, m, path="block_fp8")
+    out = torch.zeros((m + 63) // 64, dtype=torch.int64, device="cuda")
+    plan.hash(dev(seed), dev(key), out)
+    res, bound = plan.residual()
+    plan.close()
+    assert res == 0.0 and bound == 0.0
     if m % 64:
         assert int(got[-1]) >> (m % 64) == 0
 
