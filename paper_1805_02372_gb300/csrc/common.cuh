@@ -126,6 +126,16 @@ __device__ __forceinline__ void signal_count(uint32_t *c) {
     }
 }
 
+// signal_count for `count` consecutive counters (one fence and barrier for all of them)
+__device__ __forceinline__ void signal_counts(uint32_t *c, uint32_t count) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        for (uint32_t i = 0; i < count; ++i) atomicAdd(c + i, 1u);
+    }
+}
+
 // ---- bit helpers ----
 
 __device__ __forceinline__ uint64_t ceil_div_dev(uint64_t a, uint64_t b) { return (a + b - 1) / b; }

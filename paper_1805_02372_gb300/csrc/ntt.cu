@@ -405,15 +405,24 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
     fb->w_off = Q * N;
     fb->wmap = wmap->size();
     fb->Q = static_cast<uint32_t>(Q);
+    fb->P = static_cast<uint32_t>(P);
     const NttTile shape = tile_shape(c.log2n, field);
     fb->nfwd2 = streamed ? 0u : static_cast<uint32_t>((Q + W) * shape.g2);
     fb->nfwd1 = static_cast<uint32_t>((Q + W) * shape.g1);
+    const size_t w0 = wmap->size();
     for (uint64_t I = 0; I < P; ++I)
         for (uint64_t J = 0; J < Q; ++J) {
             const int64_t off = d[I * Q + J].first;
             const auto it = std::lower_bound(u.begin(), u.end(), std::make_pair(off, uint64_t(0)));
             wmap->push_back(static_cast<uint32_t>(it - u.begin()));
         }
+    fb->consec = 1;
+    for (uint64_t I = 0; I < P && fb->consec; ++I)
+        for (uint64_t J = 0; J < Q; ++J)
+            if (int64_t((*wmap)[w0 + I * Q + J]) != int64_t((*wmap)[w0]) + int64_t(I) - int64_t(J)) {
+                fb->consec = 0;
+                break;
+            }
     for (uint64_t J = 0; J < Q; ++J) {
         NttTile t = shape;
         t.p = pairs[J];  // pair (0, J): key tile J
@@ -443,6 +452,10 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
             t.logC2 = shape.logC2 - 1;
             t.g2 = shape.g2 * 2;
             t.ws_off = 0;
+        } else {
+            // sum items of 2048 elements per output row group, kSum4Out outputs at a time
+            t.logC2 = t.logR2 >= 11 ? 0u : 11u - t.logR2;
+            t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> t.logC2);
         }
         sums->push_back(t);
     }
@@ -569,8 +582,9 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
         while (i < fd_sum.size()) {
             size_t j = i;
             while (j < fd_sum.size() && fd_sum[j].fd == fd_sum[i].fd) ++j;
+            // one item per row group and group of kSum4Out consecutive output tiles
             for (uint32_t k = 0; k < fd_sum[i].g2; ++k)
-                for (size_t q = i; q < j; ++q) push(IT_FD_SUM, i_sum + q, k);
+                for (size_t q = i; q < j; q += kSum4Out) push(IT_FD_SUM, i_sum + q, k);
             i = j;
         }
     }
@@ -597,6 +611,10 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
                                       size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
         }
     }
+    // fd sums: the inverse stage table and kSum4Out x C columns of R2 rows
+    for (const NttTile &t : fd_sum)
+        smem = std::max(smem, (size_t(1) << t.logR2) * twsz +
+                                  size_t(ColMajor::words(1 << t.logR2, kSum4Out << t.logC2)) * elem);
     // streamed sums: key, window and accumulator columns, then the window indices
     for (const NttTile &t : st_sum)
         smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +

@@ -65,7 +65,9 @@ struct FdBlock {
     uint32_t Q;       // key tiles
     uint32_t nfwd2;   // forward pass-2 items of the block (all precede every sum)
     uint32_t nfwd1;   // forward pass-1 items of the block (streamed sums wait for all)
-    uint32_t pad;
+    uint32_t P;       // output tiles
+    uint32_t consec;  // 1: the window of (I, J) is wmap[0][0] + I - J (equal key and output
+                      // tiles: offsets (I - J) M), so sums can slide along J
 };
 
 // Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
@@ -80,6 +82,10 @@ inline void pass_columns(int logN, size_t elem, int *logC1, int *logC2) {
     *logC1 = std::min(c1, logS);
     *logC2 = std::min(c2, logR1);
 }
+
+// Output tiles per transform-domain sum item (ntt_kernel.cuh, body_sum4_inv_last); each
+// item covers 2048 elements of every one of them.
+constexpr int kSum4Out = 4;
 
 // Words of the pass-1 twiddle tables of a forward item (p1tw_build in ntt_kernel.cuh):
 // per segment column 32 + R1/32 entries, and 32 + R1/32 shared ones (needs R1 >= 32).

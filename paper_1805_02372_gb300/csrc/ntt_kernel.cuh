@@ -378,61 +378,107 @@ __device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint
     __syncthreads();
 }
 
-// Rows of Z_I from row group rg: Z_I = sum over the Q key tiles J of X_J * W_{wrow[J]}
-// (Montgomery products summed in the field), then the inverse pass 2, written to Z.
-// A 512-thread CTA covers a row group in at most kSumVec vectors of 16 bytes per thread.
-constexpr int kSumVec = 4;
+// Rows of up to kSum4Out output tiles I0 .. I0+nout-1 from row group rg (2048 elements of
+// each): Z_I = sum over the Q key tiles J of X_J * W_{wmap[I][J]} (Montgomery products
+// summed in the field), then the inverse pass 2 of every row, written to Z_I (output tiles
+// at stride N from Z). Each key-tile vector is loaded once for all the item's outputs.
+// Shared memory: kSum4Out x C columns of R2 rows (C = 2048 / R2 rows per output).
+constexpr int kSum4Elems = 2048;
 template <class F>
-__device__ void body_sum_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
-                                  int logR2, int logC, const typename F::T *__restrict__ X,
-                                  const typename F::T *__restrict__ W,
-                                  const uint32_t *__restrict__ wrow, uint32_t Q, uint64_t N,
-                                  typename F::T *__restrict__ Z) {
+__device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
+                                   int logR2, int logC, const typename F::T *__restrict__ X,
+                                   const typename F::T *__restrict__ W,
+                                   const uint32_t *__restrict__ wmap_blk, uint32_t Q, uint32_t I0,
+                                   uint32_t nout, uint32_t consec, uint64_t N,
+                                   typename F::T *__restrict__ Z) {
     using T = typename F::T;
     constexpr int V = 16 / sizeof(T);
-    const int R2 = 1 << logR2;
+    constexpr int VPT = kSum4Elems / (kThreads * V);  // vectors per thread: 1 (32-bit), 2 (64-bit)
+    static_assert(VPT >= 1 && VPT * kThreads * V == kSum4Elems, "row-group size");
+    const int R2 = 1 << logR2, C = 1 << logC;
     const uint64_t base = (rg << logC) << logR2;
     const ColMajor lay{ColMajor::stride(R2)};
-    const int cnt = R2 << logC;
-    T acc[kSumVec][V];
+    T acc[kSum4Out][VPT][V];
 #pragma unroll
-    for (int q = 0; q < kSumVec; ++q)
+    for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
-        for (int k = 0; k < V; ++k) acc[q][k] = 0;
-    for (uint32_t J = 0; J < Q; ++J) {
-        const T *xj = X + uint64_t(J) * N + base;
-        const T *wj = W + uint64_t(__ldg(wrow + J)) * N + base;
+        for (int v = 0; v < VPT; ++v)
 #pragma unroll
-        for (int q = 0; q < kSumVec; ++q) {
-            const int e = (threadIdx.x + q * blockDim.x) * V;
-            if (e < cnt) {
-                const uint4 xv = __ldcg(reinterpret_cast<const uint4 *>(xj + e));
-                const uint4 wv = __ldcg(reinterpret_cast<const uint4 *>(wj + e));
-                const T *xs = reinterpret_cast<const T *>(&xv), *ws = reinterpret_cast<const T *>(&wv);
+            for (int k = 0; k < V; ++k) acc[o][v][k] = 0;
+    const auto vec = [&](const T *row, int v) {
+        return __ldcg(reinterpret_cast<const uint4 *>(row + (threadIdx.x + v * kThreads) * V));
+    };
+    if (consec) {
+        // window of (I0 + o, J) = d0 + o - J: the item's window rows slide by one per key
+        // tile, so each J loads one new window row (output 0's) and the key-tile row
+        const int64_t d0 = static_cast<int64_t>(__ldg(wmap_blk)) + I0;
+        uint4 wv[kSum4Out][VPT];
 #pragma unroll
-                for (int k = 0; k < V; ++k) acc[q][k] = F::add(acc[q][k], F::mont(xs[k], ws[k]));
+        for (int o = 0; o < kSum4Out; ++o)
+#pragma unroll
+            for (int v = 0; v < VPT; ++v)
+                wv[o][v] = o < static_cast<int>(nout) ? vec(W + uint64_t(d0 + o) * N + base, v) : uint4{0, 0, 0, 0};
+        for (uint32_t J = 0; J < Q; ++J) {
+            uint4 xv[VPT];
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + base, v);
+#pragma unroll
+            for (int o = 0; o < kSum4Out; ++o)
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const T *xs = reinterpret_cast<const T *>(&xv[v]), *ws = reinterpret_cast<const T *>(&wv[o][v]);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
+                }
+            if (J + 1 < Q) {
+#pragma unroll
+                for (int o = kSum4Out - 1; o > 0; --o)
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) wv[o][v] = wv[o - 1][v];
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) wv[0][v] = vec(W + uint64_t(d0 - int64_t(J) - 1) * N + base, v);
+            }
+        }
+    } else {
+        for (uint32_t J = 0; J < Q; ++J) {
+            uint4 xv[VPT];
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + base, v);
+#pragma unroll
+            for (int o = 0; o < kSum4Out; ++o) {
+                if (o >= static_cast<int>(nout)) break;
+                const T *wj = W + uint64_t(__ldg(wmap_blk + uint64_t(I0 + o) * Q + J)) * N + base;
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) {
+                    const uint4 wv = vec(wj, v);
+                    const T *xs = reinterpret_cast<const T *>(&xv[v]), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+                    for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
+                }
             }
         }
     }
+    // output o's C rows are columns o C .. o C + C - 1 (unused outputs stay zero)
 #pragma unroll
-    for (int q = 0; q < kSumVec; ++q) {
-        const int e = (threadIdx.x + q * blockDim.x) * V;
-        if (e < cnt) {
+    for (int o = 0; o < kSum4Out; ++o)
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const int e = (threadIdx.x + v * kThreads) * V;
             const int c = e >> logR2, r = e & (R2 - 1);
 #pragma unroll
-            for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = acc[q][k];
+            for (int k = 0; k < V; ++k) sm[lay.at(r + k, o * C + c)] = acc[o][v][k];
         }
-    }
     __syncthreads();
-    dit_columns<F, false>(sm, lay, logR2, logC, sti);
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        uint4 ov;
-        T *os = reinterpret_cast<T *>(&ov);
+    dit_columns<F, false>(sm, lay, logR2, logC + 2, sti);
+    for (int o = 0; o < static_cast<int>(nout); ++o)
+        for (int e = threadIdx.x * V; e < kSum4Elems; e += blockDim.x * V) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            uint4 ov;
+            T *os = reinterpret_cast<T *>(&ov);
 #pragma unroll
-        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
-        __stcg(reinterpret_cast<uint4 *>(Z + base + e), ov);
-    }
+            for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, o * C + c)];
+            __stcg(reinterpret_cast<uint4 *>(Z + uint64_t(o) * N + base + e), ov);
+        }
     __syncthreads();
 }
 
@@ -608,15 +654,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 signal_count(cfd + tl.fd);
                 break;
             }
-            case IT_FD_SUM: {
+            case IT_FD_SUM: {  // output tiles tl.out .. + kSum4Out - 1 (sum tiles ti, ti + 1, ...)
                 const FdBlock fb = fds[tl.fd];
+                const uint32_t nout = min(static_cast<uint32_t>(kSum4Out), fb.P - tl.out);
                 if (k0 != 32 + logR2) load_stage<F>(st0, stage, 1, logR2);
                 if (wait_count(cfd + tl.fd, fb.nfwd2, status, &flag))
-                    body_sum_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
-                                         logC2, ws + fb.x_off, ws + fb.w_off,
-                                         wmap + fb.wmap + uint64_t(tl.out) * fb.Q, fb.Q,
-                                         uint64_t(1) << logN, X);
-                signal_count(c2 + ti);
+                    body_sum4_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
+                                          logC2, ws + fb.x_off, ws + fb.w_off, wmap + fb.wmap, fb.Q,
+                                          tl.out, nout, fb.consec, uint64_t(1) << logN, X);
+                signal_counts(c2 + ti, nout);
                 break;
             }
             case IT_FD_STREAM: {
