@@ -264,7 +264,8 @@ int get_tuner(Tuner *out) {
 }
 
 // Estimated seconds of one block on each path; fills opts with the best choice.
-double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *best) {
+double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *best,
+                 uint32_t fd_mode = 0) {
     memset(best, 0, sizeof(*best));
     best->device = -1;
     double bt = INFINITY;
@@ -312,11 +313,12 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 uint32_t fd = 0;
                 uint64_t windows = 0;
                 const double units = ntt_geometry_cost(n, m, o.path, static_cast<uint32_t>(k), M, L,
-                                                       0, &fd, &windows);
+                                                       fd_mode, &fd, &windows);
                 const double launches = batched ? 0.0 : 2.0;
                 o.log2_transform = static_cast<uint32_t>(k);
                 o.tile_out = M;
                 o.tile_in = L;
+                o.fd_mode = fd_mode;
                 consider(floor(units * t.ntt[f][k] + launches * t.launch, t.ntt1[f][k]), o);
             }
         }
@@ -477,7 +479,8 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         if (forced) {
             o = *opts;
         } else {
-            best_path(n, m, t, true, &o);
+            // the autotuner's choice; a caller's fd_mode still applies to NTT blocks
+            best_path(n, m, t, true, &o, opts ? opts->fd_mode : 0);
         }
         int rc = plan_resolve(n, m, &o, &b->cfg[i]);
         if (rc != PA_OK) {

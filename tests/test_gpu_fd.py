@@ -128,3 +128,24 @@ def test_finite_size_fd_sampled_rows():
     g2, _ = run_path(b.n, b.m, key2, seed, path="ntt31")
     g12, _ = run_path(b.n, b.m, key ^ key2, seed, path="ntt31")
     assert np.array_equal(g12, got ^ g2)
+
+
+def test_autotuned_batch_honours_fd_mode():
+    # pa_opts.fd_mode applies to the autotuner's NTT blocks in a batch too: 1 plans no
+    # transform-domain accumulation, and the bits stay the oracle's either way.
+    import torch
+    shapes = [(1_000_003, 60_000), (2_000_003, 400_001), (300_007, 150_001), (4_000_037, 40_009)]
+    bl = [inputs.single_block(n, m, 501 + i, 601 + i) for i, (n, m) in enumerate(shapes)]
+    keys, seeds = [b.key() for b in bl], [b.seed() for b in bl]
+    want = [oracle.hash_full(b.n, b.m, s, k) for b, k, s in zip(bl, keys, seeds)]
+    for mode in (0, 1):
+        outs = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in bl]
+        desc = [(b.n, b.m, dev(s), dev(k), o) for b, s, k, o in zip(bl, seeds, keys, outs)]
+        batch = pkg.pa_batch_plan(desc, binding.make_opts(path="auto", fd_mode=mode))
+        plans = pkg.pa_batch_describe(batch, len(bl))
+        pkg.pa_batch_run(batch, desc)
+        pkg.pa_batch_destroy(batch)
+        if mode == 1:
+            assert all(p["fd"] == 0 for p in plans if p["path_name"] in ("ntt31", "ntt64"))
+        for o, w in zip(outs, want):
+            assert np.array_equal(host(o), w), mode
