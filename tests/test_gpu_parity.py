@@ -199,3 +199,22 @@ def test_paper_scale_block_sampled_rows():
     rows = np.unique(np.concatenate([rng.integers(0, m, 200), [0, 1, 63, 64, m - 1]]))
     want = oracle.hash_rows(n, m, seed, key, rows)
     assert np.array_equal(oracle.unpack(got, m)[rows], want), desc
+
+
+def _random_shapes(count=24, seed=2024):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        n = int(np.exp(rng.uniform(0, np.log(300_000))))
+        m = int(np.exp(rng.uniform(0, np.log(100_000))))
+        if n * m <= 5e9:
+            out.append((max(n, 1), max(m, 1)))
+    return out
+
+
+@pytest.mark.parametrize("path", PATHS + ["auto"])
+@pytest.mark.parametrize("n,m", _random_shapes())
+def test_random_shapes(path, n, m):
+    # seeded log-uniform shapes: ragged tails of every tile, chunk and word boundary
+    key, seed, want = _case(n, m, 71 + n, 73 + m)
+    _check(path, n, m, key, seed, want)
