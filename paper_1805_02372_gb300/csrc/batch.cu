@@ -354,6 +354,8 @@ __global__ void batch_zero(const BlockPtrs *__restrict__ blks, const uint32_t *_
 using namespace pa;
 
 namespace pa {
+// Words per piece of pa_batch_run_host's copies (64 KB).
+constexpr uint64_t kCopyPiece = 8192;
 // One contiguous copy of 64-bit words (pa_batch_run_host's gather and scatter kernels).
 struct CopySeg {
     const uint64_t *src;
@@ -387,7 +389,8 @@ struct pa_batch_s {
     void *stage = nullptr;
     std::vector<size_t> st_seed, st_key, st_out;
     size_t stage_bytes = 0;
-    pa::CopySeg *segs = nullptr;      // device copy tables: inputs (2 per block), outputs
+    pa::CopySeg *segs = nullptr;      // device copy tables: input pieces, then output pieces
+    size_t segs_cap = 0;
     std::vector<pa::CopySeg> hsegs;
 };
 
@@ -747,36 +750,44 @@ int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, v
     // When every host buffer is page-locked and mapped for this device, one gather kernel
     // reads all keys and seeds and one scatter kernel writes all outputs (instead of three
     // copies per block); otherwise one cudaMemcpyAsync per buffer.
+    // Copies are cut into pieces of at most kCopyPiece words so that the large keys and
+    // seeds spread over many CTAs instead of setting the kernel's duration on one each.
     std::vector<CopySeg> &sg = b->hsegs;
     sg.clear();
+    const auto add = [&sg](const uint64_t *src, uint64_t *dst, uint64_t words) {
+        for (uint64_t o = 0; o < words; o += kCopyPiece)
+            sg.push_back({src + o, dst + o, std::min<uint64_t>(kCopyPiece, words - o)});
+    };
     bool mapped = true;
+    std::vector<uint64_t *> outs_dev(count, nullptr);
     for (size_t i = 0; i < count && mapped; ++i) {
         const pa_block &h = host_blocks[i];
         void *ds = mapped_host(h.seed_bits), *dk = mapped_host(h.key_bits);
-        void *dout = mapped_host(h.out_bits);
-        mapped = ds && dk && dout;
-        sg.push_back({static_cast<const uint64_t *>(ds), reinterpret_cast<uint64_t *>(st + b->st_seed[i]),
-                      ceil_div(h.n + h.m - 1, 64)});
-        sg.push_back({static_cast<const uint64_t *>(dk), reinterpret_cast<uint64_t *>(st + b->st_key[i]),
-                      ceil_div(h.n, 64)});
+        outs_dev[i] = static_cast<uint64_t *>(mapped_host(h.out_bits));
+        mapped = ds && dk && outs_dev[i];
+        if (!mapped) break;
+        add(static_cast<const uint64_t *>(ds), reinterpret_cast<uint64_t *>(st + b->st_seed[i]),
+            ceil_div(h.n + h.m - 1, 64));
+        add(static_cast<const uint64_t *>(dk), reinterpret_cast<uint64_t *>(st + b->st_key[i]),
+            ceil_div(h.n, 64));
     }
+    size_t nin = 0;
     if (mapped) {
+        nin = sg.size();
         for (size_t i = 0; i < count; ++i)
-            sg.push_back({reinterpret_cast<const uint64_t *>(st + b->st_out[i]),
-                          static_cast<uint64_t *>(mapped_host(host_blocks[i].out_bits)),
-                          ceil_div(b->m[i], 64)});
-        if (!b->segs) {
-            cudaError_t e = cudaMalloc(&b->segs, 3 * count * sizeof(CopySeg));
-            if (e != cudaSuccess) {
-                b->segs = nullptr;
-                return cuda_fail(e);
-            }
+            add(reinterpret_cast<const uint64_t *>(st + b->st_out[i]), outs_dev[i], ceil_div(b->m[i], 64));
+        if (!b->segs || b->segs_cap < sg.size()) {
+            if (b->segs) cudaFree(b->segs);
+            b->segs = nullptr;
+            cudaError_t e = cudaMalloc(&b->segs, sg.size() * sizeof(CopySeg));
+            if (e != cudaSuccess) return cuda_fail(e);
+            b->segs_cap = sg.size();
         }
         PA_CUDA_TRY(cudaMemcpyAsync(b->segs, sg.data(), sg.size() * sizeof(CopySeg),
                                     cudaMemcpyHostToDevice, s));
         int sms = kNumSMsGB300;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-        copy_segments<<<4 * sms, 256, 0, s>>>(b->segs, static_cast<uint32_t>(2 * count));
+        copy_segments<<<4 * sms, 256, 0, s>>>(b->segs, static_cast<uint32_t>(nin));
         PA_CUDA_TRY(cudaGetLastError());
     } else {
         for (size_t i = 0; i < count; ++i) {
@@ -790,7 +801,7 @@ int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, v
     int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
     if (rc != PA_OK) return rc;
     if (mapped) {
-        copy_segments<<<4 * kNumSMsGB300, 256, 0, s>>>(b->segs + 2 * count, static_cast<uint32_t>(count));
+        copy_segments<<<4 * kNumSMsGB300, 256, 0, s>>>(b->segs + nin, static_cast<uint32_t>(sg.size() - nin));
         PA_CUDA_TRY(cudaGetLastError());
     } else {
         for (size_t i = 0; i < count; ++i)
