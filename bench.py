@@ -149,8 +149,8 @@ class Runner:
         self.batched = len(blocks) > 1 and not force_single
         self.stream = torch.cuda.current_stream()
         if self.batched:
-            self.desc = [(b.n, b.m, s, k, o) for b, s, k, o in
-                         zip(blocks, self.seeds, self.keys, self.outs)]
+            self.desc = pkg.BlockList([(b.n, b.m, s, k, o) for b, s, k, o in
+                                       zip(blocks, self.seeds, self.keys, self.outs)])
             self.batch = pkg.pa_batch_plan(self.desc, pkg.make_opts(path=path))
             self.plans = None
             self.plan_desc = pkg.pa_batch_describe(self.batch, len(blocks))
@@ -201,7 +201,9 @@ class Runner:
         h2d = sum(8 * (k.numel() + s.numel()) for k, s in zip(kh, sh))
         d2h = sum(8 * o.numel() for o in oh)
         if self.batched:
-            desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh)]
+            # descriptors marshalled once (same buffers every step); every step still copies
+            # all keys and seeds in and all outputs out
+            desc = self.pkg.BlockList([(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh)])
             run = lambda: self.pkg.pa_batch_run_host(self.batch, desc, self.stream)
         else:
             run = lambda: [p.hash_host(s, k, o, self.stream)

@@ -284,7 +284,22 @@ def pa_plan_status(plan: int) -> int:
     return load().pa_plan_status(plan)
 
 
+class BlockList:
+    """Block descriptors marshalled once: pass it wherever a sequence of (n, m, seed, key,
+    out) tuples is accepted, to skip the per-call conversion when a caller hashes the same
+    buffers again (it keeps the buffers alive; their contents may change between calls)."""
+
+    def __init__(self, blocks):
+        self.blocks = list(blocks)
+        self.arr, self.count = _blocks(self.blocks)
+
+    def __len__(self):
+        return self.count
+
+
 def _blocks(blocks) -> tuple[ctypes.Array, int]:
+    if isinstance(blocks, BlockList):
+        return blocks.arr, blocks.count
     arr = (pa_block * len(blocks))()
     for i, b in enumerate(blocks):
         n, m, seed, key, out = b

@@ -120,6 +120,8 @@ def test_host_entry_pinned_buffers():
         if trial == 2:
             outs[3] = np.full((bl[3].m + 63) // 64, np.uint64(7))  # pageable
         hdesc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sh, kh, outs)]
+        if trial == 1:
+            hdesc = pkg.BlockList(hdesc)  # marshalled once, same result
         pkg.pa_batch_run_host(batch, hdesc)
         for i, (o, w) in enumerate(zip(outs, want)):
             got = o if isinstance(o, np.ndarray) else o.numpy().view(np.uint64)
