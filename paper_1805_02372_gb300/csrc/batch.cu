@@ -297,11 +297,18 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
     consider(t.fft * double(ceil_div(n, 1536)) * double(ceil_div(m, 2560)) * 4096.0 * 14.0 +
                  t.launch,
              o);
-    // transform paths: geometry search with measured per-tile costs
+    // transform paths: geometry search with measured per-tile costs; above the calibrated
+    // sizes (only multi-output accumulation runs there) a pair's cost is extrapolated from
+    // the largest calibrated one as N (log2 N + 6), the geometry model's pair cost
+    const auto per_pair = [](const double (&c)[kTuneLogMax + 1], int k) {
+        if (k <= kTuneLogMax) return c[k];
+        return c[kTuneLogMax] * double(uint64_t(1) << (k - kTuneLogMax)) * double(k + 6) /
+               double(kTuneLogMax + 6);
+    };
     for (int f = 0; f < 2; ++f) {
         if (f == 0 && n >= 2013265921ull) continue;
         o.path = f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64;
-        for (int k = kTuneLogMin; k <= kTuneLogMax; ++k) {
+        for (int k = kTuneLogMin; k <= kLogMax; ++k) {
             const uint64_t N = uint64_t(1) << k;
             const uint64_t mc = round_up(m, 64);
             for (uint64_t div = 1; div <= 256; div *= 2) {
@@ -319,7 +326,8 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 o.tile_out = M;
                 o.tile_in = L;
                 o.fd_mode = fd_mode;
-                consider(floor(units * t.ntt[f][k] + launches * t.launch, t.ntt1[f][k]), o);
+                consider(floor(units * per_pair(t.ntt[f], k) + launches * t.launch, per_pair(t.ntt1[f], k)),
+                         o);
             }
         }
         o.log2_transform = 0;

@@ -134,6 +134,11 @@ int block_tc_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c);
 int block_tc_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                     const uint64_t *key, uint64_t *out, cudaStream_t s);
 
+// Transform sizes of the exact path: standard tile pairs and streamed blocks up to 2^22,
+// multi-output transform-domain accumulation up to 2^23.
+constexpr int kLogMax = 23;
+constexpr int kLogMaxStd = 22;
+
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c);
 // Modelled cost of a tile geometry in units of one standard tile pair of size 2^k
 // (+inf if invalid); *fd / *windows: whether transform-domain accumulation is used.

@@ -241,7 +241,10 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
     const double N = double(uint64_t(1) << k);
     const uint64_t P = ceil_div(m, M), Q = ceil_div(n, L);
     const double pair = N * (k + 6) + 4096.0;
-    const double std_units = double(P) * double(Q);
+    // transforms above 2^22 run only under multi-output accumulation: their pass-2 rows
+    // of 2^12 points leave no shared memory for a fused tile pair or a streamed sum
+    const bool big = k > static_cast<uint32_t>(kLogMaxStd);
+    const double std_units = big ? INFINITY : double(P) * double(Q);
     *windows = P * Q;
     if (k <= static_cast<uint32_t>(kLogSmallMax) || fd_mode == 1 || P * Q < 2 || P * Q > kFdMaxPairs)
         return std_units;
@@ -250,7 +253,7 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
     if (P == 1) {
         // streamed: the forward pass 2 of each key tile and window runs inside the sum,
         // so 2Q forward transforms and one inverse replace 3Q
-        if (double(2 * Q) * N * elem > double(kFdMaxBytes)) return std_units;
+        if (big || double(2 * Q) * N * elem > double(kFdMaxBytes)) return std_units;
         const double sc = double(Q) * (2 * tr + N + 4096.0) + tr + 4096.0;
         if (fd_mode == 2 || sc < 0.95 * std_units * pair) {
             *fd = 2;
@@ -263,7 +266,7 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
     if (double(Q + W + P) * N * elem > double(kFdMaxBytes)) return std_units;
     const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(P) * (tr + N + 1024.0) +
                        double(P) * double(Q) * 3.0 * N;
-    if (fd_mode == 2 || fdc < 0.85 * std_units * pair) {
+    if (fd_mode == 2 || big || fdc < 0.85 * std_units * pair) {
         *fd = 1;
         *windows = W;
         return fdc / pair;
@@ -339,9 +342,11 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
         c->passes = 1;
         c->radix_log2[0] = bk;
     } else {
+        int logR1 = 0, logR2 = 0;
+        split_r(static_cast<int>(bk), &logR1, &logR2);
         c->passes = 2;
-        c->radix_log2[0] = (bk + 1) / 2;  // R1 (strided pass)
-        c->radix_log2[1] = bk / 2;        // R2 (contiguous pass)
+        c->radix_log2[0] = static_cast<uint32_t>(logR1);  // R1 (strided pass)
+        c->radix_log2[1] = static_cast<uint32_t>(logR2);  // R2 (contiguous pass)
     }
     return PA_OK;
 }
@@ -367,8 +372,10 @@ NttTile tile_shape(uint32_t logN, int field) {
     }
     if (logN > static_cast<uint32_t>(kLogSmallMax)) {
         const size_t elem = field == kFieldF64 ? 8 : 4;
-        t.logR1 = (t.logN + 1) / 2;
-        t.logR2 = t.logN / 2;
+        int logR1 = 0, logR2 = 0;
+        split_r(static_cast<int>(t.logN), &logR1, &logR2);
+        t.logR1 = static_cast<uint32_t>(logR1);
+        t.logR2 = static_cast<uint32_t>(logR2);
         int logC1 = 0, logC2 = 0;
         pass_columns(static_cast<int>(t.logN), elem, &logC1, &logC2);
         t.logC1 = static_cast<uint32_t>(logC1);
@@ -478,6 +485,9 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     std::vector<uint32_t> wmap;
     uint64_t fd_elems = 0;
     for (const BatchBlock &b : blocks) {
+        if (b.tr.log2n > static_cast<uint32_t>(kLogMax) ||
+            (b.tr.log2n > static_cast<uint32_t>(kLogMaxStd) && b.tr.fd != 1))
+            return PA_ERR_INVALID;
         if (b.tr.fd) {
             if (b.tr.log2n <= static_cast<uint32_t>(kLogSmallMax) ||
                 b.tr.tiles_in * b.tr.tiles_out > kFdMaxPairs || b.tr.fd > 2 ||
@@ -598,19 +608,26 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     info->slots = static_cast<uint32_t>(slots ? slots : 1);
     // shared memory: the largest need among the bodies present
     size_t smem = 0;
-    for (const NttTile &t : tiles) {
-        if (t.logN <= static_cast<uint32_t>(kLogSmallMax)) {
-            smem = std::max(smem, (size_t(2) << t.logN) * twsz +
-                                      size_t(ColMajor::words(1 << t.logN, 2)) * elem);
-        } else {
-            const int logC1 = static_cast<int>(t.logC1), logC2 = static_cast<int>(t.logC2);
+    for (const NttTile &t : small)
+        smem = std::max(smem, (size_t(2) << t.logN) * twsz +
+                                  size_t(ColMajor::words(1 << t.logN, 2)) * elem);
+    // passes 1 and 3 (every two-pass tile): the stage table, C1 columns of R1 rows and
+    // the pass-1 twiddle tables
+    for (const std::vector<NttTile> *v : {&big, &fd_spec, &fd_sum, &st_spec, &st_sum})
+        for (const NttTile &t : *v) {
+            const int logC1 = static_cast<int>(t.logC1);
             const int seglog = logC1 - (elem == 4 ? 3 : 2);
             smem = std::max(smem, (size_t(1) << t.logR1) * twsz + (size_t(1) << (t.logR1 + logC1)) * elem +
                                       size_t(p1tw_words(static_cast<int>(t.logR1), seglog)) * elem);
-            smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
-                                      size_t(ColMajor::words(1 << t.logR2, 2 << logC2)) * elem);
         }
-    }
+    // fused pass 2 of a standard pair: both stage tables, key and window rows
+    for (const NttTile &t : big)
+        smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
+                                  size_t(ColMajor::words(1 << t.logR2, 2 << t.logC2)) * elem);
+    // forward pass 2 of an fd spectrum: the forward stage table and C2 rows
+    for (const NttTile &t : fd_spec)
+        smem = std::max(smem, (size_t(1) << t.logR2) * twsz +
+                                  size_t(ColMajor::words(1 << t.logR2, 1 << t.logC2)) * elem);
     // fd sums: the inverse stage table and kSum4Out x C columns of R2 rows
     for (const NttTile &t : fd_sum)
         smem = std::max(smem, (size_t(1) << t.logR2) * twsz +

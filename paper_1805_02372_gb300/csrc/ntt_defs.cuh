@@ -13,8 +13,8 @@
 
 namespace pa {
 
-constexpr int kLogMax = 22;           // largest transform: 2^22
 constexpr int kLogSmallMax = 12;      // one-CTA transforms up to 2^12
+constexpr int kLogR1Max = 11;         // strided-pass columns of at most 2^11 points
 constexpr int kThreads = 512;
 // Two CTAs of 512 threads per SM for the 32-bit field (<= 64 registers), one for 64-bit.
 template <class F>
@@ -70,12 +70,22 @@ struct FdBlock {
                       // tiles: offsets (I - J) M), so sums can slide along J
 };
 
+// Four-step split N = R1 R2 of a two-pass transform: R1 = 2^ceil(logN/2) up to 2^22, and
+// above that R1 = 2^11 with the contiguous pass taking the rest (R2 = 2^12 at 2^23), so
+// that a pass-1 item keeps its 2^11-point columns.
+__host__ __device__ inline void split_r(int logN, int *logR1, int *logR2) {
+    *logR1 = (logN + 1) / 2 < kLogR1Max ? (logN + 1) / 2 : kLogR1Max;
+    *logR2 = logN - *logR1;
+}
+
 // Columns per pass-1/3 item and rows per pass-2 item (log2): at least one 32-byte row
 // segment, and enough to give a 512-thread CTA about 8192 (32-bit) elements per item in
 // pass 2 and 16384 in passes 1 and 3 (two radix-16 groups per thread and round, for
 // latency hiding; pass-2 items hold two or three column sets and stay at 8192).
 inline void pass_columns(int logN, size_t elem, int *logC1, int *logC2) {
-    const int logR1 = (logN + 1) / 2, logR2 = logN / 2, logS = logN - logR1;
+    int logR1 = 0, logR2 = 0;
+    split_r(logN, &logR1, &logR2);
+    const int logS = logN - logR1;
     const int target = elem == 4 ? 13 : 12;
     int c1 = std::max(elem == 4 ? 3 : 2, target + 1 - logR1);
     int c2 = std::max(elem == 4 ? 2 : 1, target - logR2);

@@ -378,11 +378,13 @@ __device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint
     __syncthreads();
 }
 
-// Rows of up to kSum4Out output tiles I0 .. I0+nout-1 from row group rg (2048 elements of
-// each): Z_I = sum over the Q key tiles J of X_J * W_{wmap[I][J]} (Montgomery products
-// summed in the field), then the inverse pass 2 of every row, written to Z_I (output tiles
-// at stride N from Z). Each key-tile vector is loaded once for all the item's outputs.
-// Shared memory: kSum4Out x C columns of R2 rows (C = 2048 / R2 rows per output).
+// Rows of up to kSum4Out output tiles I0 .. I0+nout-1 from row group rg (E = max(2048, R2)
+// elements of each): Z_I = sum over the Q key tiles J of X_J * W_{wmap[I][J]} (Montgomery
+// products summed in the field), then the inverse pass 2 of every row, written to Z_I
+// (output tiles at stride N from Z). The sums run over chunks of 2048 elements, each
+// accumulated in registers over all J and parked in shared memory, and each key-tile
+// vector is loaded once for all the item's outputs. Shared memory: kSum4Out x C columns
+// of R2 rows (C = 2048 / R2 rows per output, or one row when R2 > 2048).
 constexpr int kSum4Elems = 2048;
 template <class F>
 __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
@@ -395,83 +397,88 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
     constexpr int V = 16 / sizeof(T);
     constexpr int VPT = kSum4Elems / (kThreads * V);  // vectors per thread: 1 (32-bit), 2 (64-bit)
     static_assert(VPT >= 1 && VPT * kThreads * V == kSum4Elems, "row-group size");
+    static_assert(kSum4Out == 4, "the inverse pass runs on 4 C columns");
     const int R2 = 1 << logR2, C = 1 << logC;
+    const int E = R2 << logC;  // elements of one output in this item
     const uint64_t base = (rg << logC) << logR2;
     const ColMajor lay{ColMajor::stride(R2)};
-    T acc[kSum4Out][VPT][V];
-#pragma unroll
-    for (int o = 0; o < kSum4Out; ++o)
-#pragma unroll
-        for (int v = 0; v < VPT; ++v)
-#pragma unroll
-            for (int k = 0; k < V; ++k) acc[o][v][k] = 0;
-    const auto vec = [&](const T *row, int v) {
-        return __ldcg(reinterpret_cast<const uint4 *>(row + (threadIdx.x + v * kThreads) * V));
-    };
-    if (consec) {
-        // window of (I0 + o, J) = d0 + o - J: the item's window rows slide by one per key
-        // tile, so each J loads one new window row (output 0's) and the key-tile row
-        const int64_t d0 = static_cast<int64_t>(__ldg(wmap_blk)) + I0;
-        uint4 wv[kSum4Out][VPT];
+    for (int h0 = 0; h0 < E; h0 += kSum4Elems) {
+        const uint64_t hb = base + h0;
+        T acc[kSum4Out][VPT][V];
 #pragma unroll
         for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
             for (int v = 0; v < VPT; ++v)
-                wv[o][v] = o < static_cast<int>(nout) ? vec(W + uint64_t(d0 + o) * N + base, v) : uint4{0, 0, 0, 0};
-        for (uint32_t J = 0; J < Q; ++J) {
-            uint4 xv[VPT];
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + base, v);
+                for (int k = 0; k < V; ++k) acc[o][v][k] = 0;
+        const auto vec = [&](const T *row, int v) {
+            return __ldcg(reinterpret_cast<const uint4 *>(row + (threadIdx.x + v * kThreads) * V));
+        };
+        if (consec) {
+            // window of (I0 + o, J) = d0 + o - J: the item's window rows slide by one per key
+            // tile, so each J loads one new window row (output 0's) and the key-tile row
+            const int64_t d0 = static_cast<int64_t>(__ldg(wmap_blk)) + I0;
+            uint4 wv[kSum4Out][VPT];
 #pragma unroll
             for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const T *xs = reinterpret_cast<const T *>(&xv[v]), *ws = reinterpret_cast<const T *>(&wv[o][v]);
+                for (int v = 0; v < VPT; ++v)
+                    wv[o][v] = o < static_cast<int>(nout) ? vec(W + uint64_t(d0 + o) * N + hb, v) : uint4{0, 0, 0, 0};
+            for (uint32_t J = 0; J < Q; ++J) {
+                uint4 xv[VPT];
 #pragma unroll
-                    for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
-                }
-            if (J + 1 < Q) {
+                for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + hb, v);
 #pragma unroll
-                for (int o = kSum4Out - 1; o > 0; --o)
+                for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
-                    for (int v = 0; v < VPT; ++v) wv[o][v] = wv[o - 1][v];
+                    for (int v = 0; v < VPT; ++v) {
+                        const T *xs = reinterpret_cast<const T *>(&xv[v]), *ws = reinterpret_cast<const T *>(&wv[o][v]);
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) wv[0][v] = vec(W + uint64_t(d0 - int64_t(J) - 1) * N + base, v);
-            }
-        }
-    } else {
-        for (uint32_t J = 0; J < Q; ++J) {
-            uint4 xv[VPT];
+                        for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
+                    }
+                if (J + 1 < Q) {
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + base, v);
+                    for (int o = kSum4Out - 1; o > 0; --o)
 #pragma unroll
-            for (int o = 0; o < kSum4Out; ++o) {
-                if (o >= static_cast<int>(nout)) break;
-                const T *wj = W + uint64_t(__ldg(wmap_blk + uint64_t(I0 + o) * Q + J)) * N + base;
+                        for (int v = 0; v < VPT; ++v) wv[o][v] = wv[o - 1][v];
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) {
-                    const uint4 wv = vec(wj, v);
-                    const T *xs = reinterpret_cast<const T *>(&xv[v]), *ws = reinterpret_cast<const T *>(&wv);
-#pragma unroll
-                    for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
+                    for (int v = 0; v < VPT; ++v) wv[0][v] = vec(W + uint64_t(d0 - int64_t(J) - 1) * N + hb, v);
                 }
             }
+        } else {
+            for (uint32_t J = 0; J < Q; ++J) {
+                uint4 xv[VPT];
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + hb, v);
+#pragma unroll
+                for (int o = 0; o < kSum4Out; ++o) {
+                    if (o >= static_cast<int>(nout)) break;
+                    const T *wj = W + uint64_t(__ldg(wmap_blk + uint64_t(I0 + o) * Q + J)) * N + hb;
+#pragma unroll
+                    for (int v = 0; v < VPT; ++v) {
+                        const uint4 wv = vec(wj, v);
+                        const T *xs = reinterpret_cast<const T *>(&xv[v]), *ws = reinterpret_cast<const T *>(&wv);
+#pragma unroll
+                        for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
+                    }
+                }
+            }
         }
+        // output o's C rows are columns o C .. o C + C - 1 (unused outputs stay zero)
+#pragma unroll
+        for (int o = 0; o < kSum4Out; ++o)
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const int e = h0 + (threadIdx.x + v * kThreads) * V;
+                const int c = e >> logR2, r = e & (R2 - 1);
+#pragma unroll
+                for (int k = 0; k < V; ++k) sm[lay.at(r + k, o * C + c)] = acc[o][v][k];
+            }
     }
-    // output o's C rows are columns o C .. o C + C - 1 (unused outputs stay zero)
-#pragma unroll
-    for (int o = 0; o < kSum4Out; ++o)
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const int e = (threadIdx.x + v * kThreads) * V;
-            const int c = e >> logR2, r = e & (R2 - 1);
-#pragma unroll
-            for (int k = 0; k < V; ++k) sm[lay.at(r + k, o * C + c)] = acc[o][v][k];
-        }
     __syncthreads();
     dit_columns<F, false>(sm, lay, logR2, logC + 2, sti);
     for (int o = 0; o < static_cast<int>(nout); ++o)
-        for (int e = threadIdx.x * V; e < kSum4Elems; e += blockDim.x * V) {
+        for (int e = threadIdx.x * V; e < E; e += blockDim.x * V) {
             const int c = e >> logR2, r = e & (R2 - 1);
             uint4 ov;
             T *os = reinterpret_cast<T *>(&ov);

@@ -114,3 +114,37 @@ def test_streamed_chosen_for_batched_shapes(lib):
     # prices 2Q + 1 transforms below 3Q
     d = pkg.pa_plan_query(4_000_000, 2_000_000, binding.make_opts(path="ntt31"))
     assert d["tiles_out"] == 1 and d["tiles_in"] >= 2 and d["fd"] == 2
+
+
+def test_largest_transform_only_under_multi_output_accumulation(lib):
+    # 2^23-point transforms (pass-2 rows of 2^12 points) exist only for blocks with several
+    # output tiles under transform-domain accumulation; standard pairs and streamed blocks
+    # stop at 2^22, and nothing goes above 2^23.
+    q = pkg.pa_plan_query
+    n, m, L, M = 20_000_003, 9_000_000, 1 << 22, 1 << 22
+    for path in ("ntt31", "ntt64"):
+        d = q(n, m, binding.make_opts(path=path, log2_transform=23, tile_in=L, tile_out=M))
+        assert (d["log2_transform"], d["fd"]) == (23, 1)
+        assert d["windows"] == brute_windows(n, m, L, M)
+    for opts in (dict(fd_mode=1, tile_in=L, tile_out=M),          # standard pairs
+                 dict(fd_mode=2, tile_in=L, tile_out=1 << 22),    # one output tile: streamed
+                 dict()):
+        kw = dict(path="ntt31", log2_transform=23, **opts)
+        mm = 4_000_000 if opts.get("fd_mode") == 2 else m
+        with pytest.raises(pkg.PAError) as e:
+            if opts:
+                q(n, mm, binding.make_opts(**kw))
+            else:
+                q(3_000, 1_000, binding.make_opts(**kw))   # a single pair
+        assert e.value.status == binding.PA_ERR_UNSUPPORTED
+    with pytest.raises(pkg.PAError):
+        q(n, m, binding.make_opts(path="ntt31", log2_transform=24))
+
+
+def test_finite_and_paper_scale_take_the_largest_transform(lib):
+    # The summed products of accumulation number P Q N, about 4 m n / N: at n = 1e8 and
+    # 1e9 (l = 10%) the model prefers 2^23 points to 2^22.
+    for n, m in ((100_000_007, 10_000_000), (1_000_000_007, 100_000_000)):
+        d = pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31"))
+        assert (d["log2_transform"], d["fd"]) == (23, 1)
+        assert d["tile_in"] + d["tile_out"] <= 1 << 23

@@ -2,8 +2,8 @@
 
 Every window-offset structure the planner distinguishes (L = M, L = 2M, M = 2L, neither
 dividing the other), both prime fields, ragged tails, fd blocks next to standard tiles
-in one persistent launch, and the finite-size workload (n = 1e8, m = 1e7) on sampled
-rows plus linearity.
+in one persistent launch, the largest (2^23-point) transforms, and the finite-size
+workload (n = 1e8, m = 1e7) on sampled rows plus linearity.
 """
 import numpy as np
 import pytest
@@ -108,6 +108,48 @@ def test_fd_equals_standard_at_size():
     rows = np.unique(np.concatenate([np.random.default_rng(3).integers(0, m, 2000),
                                      [0, m - 1, (1 << 20) - 1, 1 << 20]]))
     assert np.array_equal(oracle.unpack(a, m)[rows], oracle.hash_rows(n, m, seed, key, rows))
+
+
+# 2^23-point transforms (the largest, multi-output accumulation only): pass-1 columns of
+# 2^11 points and pass-2 rows of 2^12, summed in two 2048-element chunks per row.
+# L = 15 * 2^19, M = 2^19: 2 x 2 tiles whose windows are looked up (L != M).
+BIG = (8_000_003, 600_001, 23, 15 << 19, 1 << 19)
+
+
+@pytest.fixture(scope="module")
+def big_case():
+    n, m = BIG[:2]
+    blk = inputs.single_block(n, m, 81, 83)
+    key, seed = blk.key(), blk.seed()
+    return key, seed, oracle.hash_full(n, m, seed, key)
+
+
+@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+def test_largest_transform_matches_oracle(big_case, path, prime):
+    n, m, k, L, M = BIG
+    key, seed, want = big_case
+    got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
+                         fd_mode=2, ntt_prime=prime)
+    assert (desc["log2_transform"], desc["fd"], desc["tiles_in"], desc["tiles_out"]) == (23, 1, 2, 2)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
+
+
+def test_largest_transform_sliding_windows_sampled_rows():
+    # L = M = 2^22: 3 output x 3 key tiles, windows d0 + I - J (the sliding sum)
+    n, m = 10_000_019, 9_000_011
+    blk = inputs.single_block(n, m, 85, 87)
+    key, seed = blk.key(), blk.seed()
+    got, desc = run_path(n, m, key, seed, path="ntt31", log2_transform=23, tile_in=1 << 22,
+                         tile_out=1 << 22, fd_mode=2)
+    assert (desc["log2_transform"], desc["fd"], desc["tiles_out"]) == (23, 1, 3)
+    M = 1 << 22
+    edges = [r for i in range(3) for r in (i * M - 1, i * M, i * M + 1, i * M + 2047, i * M + 2048)
+             if 0 <= r < m]
+    rows = np.unique(np.concatenate([np.random.default_rng(5).integers(0, m, 400), edges, [m - 1]]))
+    assert np.array_equal(oracle.unpack(got, m)[rows], oracle.hash_rows(n, m, seed, key, rows))
+    if m % 64:
+        assert int(got[-1]) >> (m % 64) == 0
 
 
 def test_finite_size_fd_sampled_rows():
