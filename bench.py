@@ -248,7 +248,7 @@ KERNEL_SOURCES = {
     "batch_persistent": [CSRC + "ntt.cu", CSRC + "ntt_defs.cuh", CSRC + "ntt_kernel.cuh",
                          CSRC + "ntt_f29.cu", CSRC + "ntt_f31.cu", CSRC + "ntt_f64.cu",
                          CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh",
-                         CSRC + "common.cuh"],
+                         CSRC + "common.cuh", CSRC + "internal.h"],
     "fft_tile": [CSRC + "fft.cu", CSRC + "dft.cuh", CSRC + "tiles.cuh"],
     "block_mma": [CSRC + "block.cu", CSRC + "common.cuh"],
     "block_tc": [CSRC + "block_tc.cu", CSRC + "common.cuh"],
