@@ -416,18 +416,27 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
         };
         if (consec) {
             // window of (I0 + o, J) = d0 + o - J: the item's window rows slide by one per key
-            // tile, so each J loads one new window row (output 0's) and the key-tile row
+            // tile, so each J needs one new window row (output 0's) and the key-tile row;
+            // both are loaded ahead (the key-tile row one step, the window row two steps)
             const int64_t d0 = static_cast<int64_t>(__ldg(wmap_blk)) + I0;
-            uint4 wv[kSum4Out][VPT];
+            uint4 wv[kSum4Out][VPT], xn[VPT], wn[VPT];
 #pragma unroll
             for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
                 for (int v = 0; v < VPT; ++v)
                     wv[o][v] = o < static_cast<int>(nout) ? vec(W + uint64_t(d0 + o) * N + hb, v) : uint4{0, 0, 0, 0};
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                xn[v] = vec(X + hb, v);
+                wn[v] = Q > 1 ? vec(W + uint64_t(d0 - 1) * N + hb, v) : uint4{0, 0, 0, 0};
+            }
             for (uint32_t J = 0; J < Q; ++J) {
                 uint4 xv[VPT];
 #pragma unroll
-                for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + hb, v);
+                for (int v = 0; v < VPT; ++v) {
+                    xv[v] = xn[v];
+                    if (J + 1 < Q) xn[v] = vec(X + uint64_t(J + 1) * N + hb, v);
+                }
 #pragma unroll
                 for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
@@ -442,7 +451,10 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
 #pragma unroll
                         for (int v = 0; v < VPT; ++v) wv[o][v] = wv[o - 1][v];
 #pragma unroll
-                    for (int v = 0; v < VPT; ++v) wv[0][v] = vec(W + uint64_t(d0 - int64_t(J) - 1) * N + hb, v);
+                    for (int v = 0; v < VPT; ++v) {
+                        wv[0][v] = wn[v];
+                        if (J + 2 < Q) wn[v] = vec(W + uint64_t(d0 - int64_t(J) - 2) * N + hb, v);
+                    }
                 }
             }
         } else {
@@ -464,7 +476,8 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
                 }
             }
         }
-        // output o's C rows are columns o C .. o C + C - 1 (unused outputs stay zero)
+        // output o's C rows are columns o C .. o C + C - 1 (the columns of outputs past nout
+        // are transformed with the rest but never written)
 #pragma unroll
         for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll

@@ -152,6 +152,39 @@ def test_largest_transform_sliding_windows_sampled_rows():
         assert int(got[-1]) >> (m % 64) == 0
 
 
+def test_largest_transform_in_a_mixed_batch():
+    # One autotuned persistent launch holding a 2^23-point accumulated block (64 Mbit,
+    # l = 10%) next to streamed, standard and one-CTA blocks: the launch's shared memory is
+    # the largest body's, and stage tables of 2^11- and 2^12-point passes alternate in the
+    # CTAs' cache. Small blocks against the full oracle, the large one on sampled rows.
+    import torch
+    shapes = [(64_000_000, 6_400_000), (1_000_003, 60_000), (300_007, 150_001), (3_001, 1_000),
+              (2_000_003, 400_001), (70_001, 64)]
+    bl = [inputs.single_block(n, m, 701 + i, 801 + i) for i, (n, m) in enumerate(shapes)]
+    keys, seeds = [b.key() for b in bl], [b.seed() for b in bl]
+    od = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in bl]
+    desc = [(b.n, b.m, dev(s), dev(k), o) for b, s, k, o in zip(bl, seeds, keys, od)]
+    batch = pkg.pa_batch_plan(desc, binding.make_opts(path="auto"))
+    try:
+        plans = pkg.pa_batch_describe(batch, len(bl))
+        assert (plans[0]["log2_transform"], plans[0]["fd"]) == (23, 1), plans[0]
+        assert any(d["path_name"] in ("ntt31", "ntt64") and d["log2_transform"] <= 22 for d in plans[1:])
+        b, m, M = bl[0], bl[0].m, plans[0]["tile_out"]
+        edges = [r for i in range(plans[0]["tiles_out"]) for r in (i * M - 1, i * M) if 0 <= r < m]
+        rows = np.unique(np.concatenate([np.random.default_rng(11).integers(0, m, 150), edges, [m - 1]]))
+        want0 = oracle.hash_rows(b.n, m, seeds[0], keys[0], rows)
+        want = [oracle.hash_full(b.n, b.m, s, k) for b, k, s in zip(bl[1:], keys[1:], seeds[1:])]
+        for run in range(2):  # first run captures the graph, the second replays it
+            for o in od:
+                o.fill_(-1)
+            pkg.pa_batch_run(batch, desc)
+            assert np.array_equal(oracle.unpack(host(od[0]), m)[rows], want0), run
+            for b, o, w in zip(bl[1:], od[1:], want):
+                assert np.array_equal(host(o), w), (run, b.n, b.m)
+    finally:
+        pkg.pa_batch_destroy(batch)
+
+
 def test_finite_size_fd_sampled_rows():
     b = inputs.FINITE_SIZE
     key, seed = b.key(), b.seed()
