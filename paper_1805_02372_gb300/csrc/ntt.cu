@@ -250,10 +250,11 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
         return std_units;
     const size_t elem = path == PA_PATH_NTT64 ? 8 : 4;
     const double tr = N * (k + 6) / 3.0;
-    if (P == 1) {
+    if (P == 1 && !big) {
         // streamed: the forward pass 2 of each key tile and window runs inside the sum,
-        // so 2Q forward transforms and one inverse replace 3Q
-        if (big || double(2 * Q) * N * elem > double(kFdMaxBytes)) return std_units;
+        // so 2Q forward transforms and one inverse replace 3Q (above 2^22 a single output
+        // tile takes the multi-output sums below, with one output per item)
+        if (double(2 * Q) * N * elem > double(kFdMaxBytes)) return std_units;
         const double sc = double(Q) * (2 * tr + N + 4096.0) + tr + 4096.0;
         if (fd_mode == 2 || sc < 0.95 * std_units * pair) {
             *fd = 2;

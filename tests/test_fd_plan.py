@@ -117,25 +117,24 @@ def test_streamed_chosen_for_batched_shapes(lib):
 
 
 def test_largest_transform_only_under_multi_output_accumulation(lib):
-    # 2^23-point transforms (pass-2 rows of 2^12 points) exist only for blocks with several
-    # output tiles under transform-domain accumulation; standard pairs and streamed blocks
-    # stop at 2^22, and nothing goes above 2^23.
+    # 2^23-point transforms (pass-2 rows of 2^12 points) run only through the multi-output
+    # sums, a single output tile included (one output per sum item); standard pairs and
+    # the streamed body stop at 2^22, and nothing goes above 2^23.
     q = pkg.pa_plan_query
     n, m, L, M = 20_000_003, 9_000_000, 1 << 22, 1 << 22
     for path in ("ntt31", "ntt64"):
         d = q(n, m, binding.make_opts(path=path, log2_transform=23, tile_in=L, tile_out=M))
         assert (d["log2_transform"], d["fd"]) == (23, 1)
         assert d["windows"] == brute_windows(n, m, L, M)
-    for opts in (dict(fd_mode=1, tile_in=L, tile_out=M),          # standard pairs
-                 dict(fd_mode=2, tile_in=L, tile_out=1 << 22),    # one output tile: streamed
-                 dict()):
-        kw = dict(path="ntt31", log2_transform=23, **opts)
-        mm = 4_000_000 if opts.get("fd_mode") == 2 else m
+        # one output tile: the sums with a single output (W = Q windows), not streamed
+        d = q(n, 4_000_000, binding.make_opts(path=path, log2_transform=23, tile_in=L,
+                                              tile_out=L, fd_mode=2))
+        assert (d["log2_transform"], d["fd"], d["tiles_out"]) == (23, 1, 1)
+        assert d["windows"] == d["tiles_in"] == brute_windows(n, 4_000_000, L, L)
+    for args in ((n, m, dict(fd_mode=1, tile_in=L, tile_out=M)),   # standard pairs
+                 (3_000, 1_000, dict())):                           # a single pair
         with pytest.raises(pkg.PAError) as e:
-            if opts:
-                q(n, mm, binding.make_opts(**kw))
-            else:
-                q(3_000, 1_000, binding.make_opts(**kw))   # a single pair
+            q(args[0], args[1], binding.make_opts(path="ntt31", log2_transform=23, **args[2]))
         assert e.value.status == binding.PA_ERR_UNSUPPORTED
     with pytest.raises(pkg.PAError):
         q(n, m, binding.make_opts(path="ntt31", log2_transform=24))

@@ -112,8 +112,10 @@ def test_fd_equals_standard_at_size():
 
 # 2^23-point transforms (the largest, multi-output accumulation only): pass-1 columns of
 # 2^11 points and pass-2 rows of 2^12, summed in two 2048-element chunks per row.
-# L = 15 * 2^19, M = 2^19: 2 x 2 tiles whose windows are looked up (L != M).
-BIG = (8_000_003, 600_001, 23, 15 << 19, 1 << 19)
+# L = 15 * 2^19, M = 2^19: 2 x 2 tiles whose windows are looked up (L != M);
+# L = 7 * 2^20, M = 2^20: one output tile, the sums with a single output per item.
+BIG = (8_000_003, 600_001, 23)
+BIG_TILES = [(15 << 19, 1 << 19, 2), (7 << 20, 1 << 20, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -124,13 +126,14 @@ def big_case():
     return key, seed, oracle.hash_full(n, m, seed, key)
 
 
+@pytest.mark.parametrize("L,M,P", BIG_TILES)
 @pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
-def test_largest_transform_matches_oracle(big_case, path, prime):
-    n, m, k, L, M = BIG
+def test_largest_transform_matches_oracle(big_case, path, prime, L, M, P):
+    n, m, k = BIG
     key, seed, want = big_case
     got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
                          fd_mode=2, ntt_prime=prime)
-    assert (desc["log2_transform"], desc["fd"], desc["tiles_in"], desc["tiles_out"]) == (23, 1, 2, 2)
+    assert (desc["log2_transform"], desc["fd"], desc["tiles_in"], desc["tiles_out"]) == (23, 1, 2, P)
     bad = np.flatnonzero(got != want)
     assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
 
