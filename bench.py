@@ -263,8 +263,8 @@ FP8_DERIVED_TFLOPS = SMS * 16384 * CLOCK_HZ / 1e12
 def _ntt_ops(descs):
     """8 integer ops per butterfly. A standard tile pair of size N costs 3 (N/2) log2 N + N/2
     butterflies (two forward transforms, one inverse, the pointwise product); a block under
-    transform-domain accumulation costs (Q + W + P) (N/2) log2 N for its Q key, W window and
-    P output transforms plus P Q N products summed."""
+    transform-domain accumulation costs (Q + W + G P) (N/2) log2 N for its Q key, W window
+    and G P output transforms (G sums per output tile) plus P Q N products summed."""
     ops = 0.0
     for d in descs:
         if d["path_name"] not in ("ntt31", "ntt64"):
@@ -273,7 +273,8 @@ def _ntt_ops(descs):
         N = 2.0 ** k
         P, Q = d["tiles_out"], d["tiles_in"]
         if d.get("fd"):
-            ops += 8.0 * ((Q + d["windows"] + P) * (N / 2) * k + P * Q * N)
+            G = d.get("sum_groups") or 1
+            ops += 8.0 * ((Q + d["windows"] + G * P) * (N / 2) * k + P * Q * N)
         else:
             ops += 8.0 * P * Q * (3 * (N / 2) * k + N / 2)
     return ops

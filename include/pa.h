@@ -80,10 +80,14 @@ typedef struct {
                                   (each key and seed-window spectrum computed once, one
                                   inverse per output sub-block). 0 = when the planner
                                   estimates it faster, 1 = never, 2 = whenever possible   */
-    uint32_t ntt_prime;        /* PA_PATH_NTT31: 0 = automatic (7*2^26+1 while n is below
-                                  it, else 15*2^27+1), 29 or 31 = that prime; a prime not
-                                  above n is PA_ERR_UNSUPPORTED                          */
-    uint32_t reserved[4];
+    uint32_t ntt_prime;        /* PA_PATH_NTT31: 0 or 29 = 7*2^26+1, 31 = 15*2^27+1. Any n:
+                                  a tile pair's counts are at most L < p, and a transform-
+                                  domain sum covers at most (p-1)/L key sub-blocks (longer
+                                  keys take several sums per output sub-block, their bits
+                                  XOR-merged as Eq. finalkey merges sub-blocks)           */
+    uint32_t fd_group;         /* transform-domain sums: at most this many key sub-blocks
+                                  per sum; 0 = the prime's exactness limit (p-1)/L        */
+    uint32_t reserved[3];
 } pa_opts;
 
 /* What a plan decided (pa_plan_query / pa_plan_describe). */
@@ -104,7 +108,7 @@ typedef struct {
     uint32_t fd;               /* NTT: transform-domain accumulation (see pa_opts.fd_mode) */
     uint64_t windows;          /* with fd: seed-window spectra computed (distinct offsets) */
     uint32_t prime_bits;       /* NTT paths: bits of the prime (29, 31 or 64), else 0     */
-    uint32_t reserved;
+    uint32_t sum_groups;       /* with fd: transform-domain sums per output sub-block     */
 } pa_plan_desc;
 
 typedef struct pa_plan_s *pa_plan_t;

@@ -27,10 +27,10 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
     if (path < PA_PATH_AUTO || path > PA_PATH_BLOCK_FP8) return PA_ERR_INVALID;
     if (path == PA_PATH_AUTO) {
         // Host-only rule (pa_plan_ex uses the autotuner's measured costs instead): the
-        // direct kernel while m*n is small; beyond, the exact NTT over a 32-bit prime
-        // while n is below it, else over the 64-bit prime.
+        // direct kernel while m*n is small; beyond, the exact NTT over the 29-bit prime
+        // (its geometry keeps every count below the prime), else over the 64-bit prime.
         const double mn = double(n) * double(m);
-        path = mn <= 4.0e9 ? PA_PATH_DIRECT : (n >= kPrimeF31 ? PA_PATH_NTT64 : PA_PATH_NTT31);
+        path = mn <= 4.0e9 ? PA_PATH_DIRECT : PA_PATH_NTT31;
         TransformCfg probe;
         if (path == PA_PATH_NTT31 && ntt_plan(n, m, path, o, &probe) != PA_OK)
             path = PA_PATH_NTT64;
@@ -105,6 +105,9 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->rounding_bound = cfg.tr.bound;
         d->fd = cfg.tr.fd;
         d->windows = cfg.tr.windows;
+        d->sum_groups = cfg.tr.fd == 1 && cfg.tr.kgroup
+                            ? static_cast<uint32_t>(ceil_div(cfg.tr.tiles_in, cfg.tr.kgroup))
+                            : (cfg.tr.fd ? 1u : 0u);
         if (cfg.path == PA_PATH_NTT31 || cfg.path == PA_PATH_NTT64)
             d->prime_bits = cfg.tr.field == kFieldF64 ? 64 : (cfg.tr.field == kFieldF29 ? 29 : 31);
     }

@@ -306,7 +306,6 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                double(kTuneLogMax + 6);
     };
     for (int f = 0; f < 2; ++f) {
-        if (f == 0 && n >= 2013265921ull) continue;
         o.path = f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64;
         for (int k = kTuneLogMin; k <= kLogMax; ++k) {
             const uint64_t N = uint64_t(1) << k;
@@ -317,10 +316,11 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 if (M == 0 || M + 32 > N) continue;
                 uint64_t L = ((N - M) / 32) * 32;
                 if (L > round_up(n, 32)) L = round_up(n, 32);
-                uint32_t fd = 0;
+                uint32_t fd = 0, kgroup = 0;
                 uint64_t windows = 0;
-                const double units = ntt_geometry_cost(n, m, o.path, static_cast<uint32_t>(k), M, L,
-                                                       fd_mode, &fd, &windows);
+                const double units = ntt_geometry_cost(n, m, f == 0 ? kFieldF29 : kFieldF64,
+                                                       static_cast<uint32_t>(k), M, L, fd_mode, 0,
+                                                       &fd, &windows, &kgroup);
                 const double launches = batched ? 0.0 : 2.0;
                 o.log2_transform = static_cast<uint32_t>(k);
                 o.tile_out = M;

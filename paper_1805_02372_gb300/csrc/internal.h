@@ -52,6 +52,8 @@ struct TransformCfg {
     int field = 0;               // NTT: kFieldF31 / kFieldF64 / kFieldF29
     uint32_t fd = 0;             // NTT: transform-domain accumulation over key tiles
     uint64_t windows = 0;        // NTT with fd: distinct seed-window spectra
+    uint32_t kgroup = 0;         // NTT with fd = 1: key tiles per transform-domain sum (the
+                                 // counts of a sum stay below the prime); 0 = all of them
     NttLayout lay;               // NTT single-block plans: their persistent launch
 };
 
@@ -140,10 +142,12 @@ constexpr int kLogMax = 23;
 constexpr int kLogMaxStd = 22;
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c);
-// Modelled cost of a tile geometry in units of one standard tile pair of size 2^k
-// (+inf if invalid); *fd / *windows: whether transform-domain accumulation is used.
-double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t M, uint64_t L,
-                         uint32_t fd_mode, uint32_t *fd, uint64_t *windows);
+// Modelled cost of a tile geometry over prime field `field` in units of one standard tile
+// pair of size 2^k (+inf if invalid); *fd / *windows / *kgroup: whether transform-domain
+// accumulation is used, its window spectra and key tiles per sum (fd_group > 0 caps it).
+double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t M, uint64_t L,
+                         uint32_t fd_mode, uint32_t fd_group, uint32_t *fd, uint64_t *windows,
+                         uint32_t *kgroup);
 // Lays out the single-block plan's persistent launch (fills c->lay; host only).
 int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c);
 int ntt_init(const PlanCfg &cfg, void *ws);  // uploads the work list, builds root tables

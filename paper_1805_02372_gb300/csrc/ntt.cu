@@ -232,10 +232,18 @@ uint64_t tile_in_for(uint64_t n, uint32_t logn, uint64_t M, uint64_t Lforce) {
 // Model: a standard pair costs three transforms plus a fixed per-pair overhead; under
 // transform-domain accumulation each forward spectrum also makes a global round trip
 // between its passes, and each (output, key tile) pair costs reading two spectra.
-double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t M, uint64_t L,
-                         uint32_t fd_mode, uint32_t *fd, uint64_t *windows) {
+//
+// Exactness: a coefficient read from a tile pair counts at most L bit products, one read
+// from a transform-domain sum over g key tiles at most g L, so a sum covers at most
+// (p - 1) / L key tiles; longer keys take several sums per output tile (one inverse
+// transform each) whose output bits are XOR-merged. A streamed block has one accumulator,
+// so it needs every key tile in one sum.
+double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t M, uint64_t L,
+                         uint32_t fd_mode, uint32_t fd_group, uint32_t *fd, uint64_t *windows,
+                         uint32_t *kgroup) {
     *fd = 0;
     *windows = 0;
+    *kgroup = 0;
     if (k > static_cast<uint32_t>(kLogMax) || M == 0 || L == 0 || L + M > (uint64_t(1) << k))
         return INFINITY;
     const double N = double(uint64_t(1) << k);
@@ -248,12 +256,18 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
     *windows = P * Q;
     if (k <= static_cast<uint32_t>(kLogSmallMax) || fd_mode == 1 || P * Q < 2 || P * Q > kFdMaxPairs)
         return std_units;
-    const size_t elem = path == PA_PATH_NTT64 ? 8 : 4;
+    const size_t elem = field == kFieldF64 ? 8 : 4;
+    const uint64_t pmax = field == kFieldF64 ? ~uint64_t(0)
+                                             : (field == kFieldF29 ? kPrimeF29 : kPrimeF31) - 1;
+    uint64_t g = std::min<uint64_t>(Q, pmax / L);
+    if (fd_group) g = std::min<uint64_t>(g, fd_group);
+    if (g == 0) return std_units;
+    const uint64_t G = ceil_div(Q, g);  // sums per output tile
     const double tr = N * (k + 6) / 3.0;
-    if (P == 1 && !big) {
+    if (P == 1 && !big && G == 1) {
         // streamed: the forward pass 2 of each key tile and window runs inside the sum,
-        // so 2Q forward transforms and one inverse replace 3Q (above 2^22 a single output
-        // tile takes the multi-output sums below, with one output per item)
+        // so 2Q forward transforms and one inverse replace 3Q (above 2^22, or with several
+        // sums, a single output tile takes the multi-output sums below, one output per item)
         if (double(2 * Q) * N * elem > double(kFdMaxBytes)) return std_units;
         const double sc = double(Q) * (2 * tr + N + 4096.0) + tr + 4096.0;
         if (fd_mode == 2 || sc < 0.95 * std_units * pair) {
@@ -264,12 +278,13 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
         return std_units;
     }
     const uint64_t W = count_windows(P, Q, M, L);
-    if (double(Q + W + P) * N * elem > double(kFdMaxBytes)) return std_units;
-    const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(P) * (tr + N + 1024.0) +
+    if (double(Q + W + G * P) * N * elem > double(kFdMaxBytes)) return std_units;
+    const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(G * P) * (tr + N + 1024.0) +
                        double(P) * double(Q) * 3.0 * N;
     if (fd_mode == 2 || big || fdc < 0.85 * std_units * pair) {
         *fd = 1;
         *windows = W;
+        *kgroup = static_cast<uint32_t>(g);
         return fdc / pair;
     }
     return std_units;
@@ -277,16 +292,14 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int path, uint32_t k, uint64_t 
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c) {
     *c = TransformCfg();
-    // every coefficient read is a count of at most n bit products: n < p keeps it exact
+    // any n: the geometry keeps every count a coefficient reaches below the prime
     const uint32_t prime = o ? o->ntt_prime : 0;
     if (path == PA_PATH_NTT64) {
         if (prime) return PA_ERR_INVALID;
         c->field = kFieldF64;
-    } else if (prime == 29 || (prime == 0 && n < kPrimeF29)) {
-        if (n >= kPrimeF29) return PA_ERR_UNSUPPORTED;
+    } else if (prime == 29 || prime == 0) {
         c->field = kFieldF29;
-    } else if (prime == 31 || prime == 0) {
-        if (n >= kPrimeF31) return PA_ERR_UNSUPPORTED;
+    } else if (prime == 31) {
         c->field = kFieldF31;
     } else {
         return PA_ERR_INVALID;
@@ -294,10 +307,11 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
     const int field = c->field;
     const uint32_t fd_mode = o ? o->fd_mode : 0;
     if (fd_mode > 2) return PA_ERR_INVALID;
+    const uint32_t fd_group = o ? o->fd_group : 0;
     const uint32_t force = o ? o->log2_transform : 0;
     const uint64_t Mforce = o ? o->tile_out : 0, Lforce = o ? o->tile_in : 0;
     double best_cost = INFINITY;
-    uint32_t bk = 0, bfd = 0;
+    uint32_t bk = 0, bfd = 0, bg = 0;
     uint64_t bL = 0, bM = 0, bW = 0;
     for (uint32_t k = 5; k <= static_cast<uint32_t>(kLogMax); ++k) {
         if (force && k != force) continue;
@@ -316,9 +330,9 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
             if (M > round_up(m, 64)) M = round_up(m, 64);
             const uint64_t L = tile_in_for(n, k, M, Lforce);
             if (L == 0) continue;
-            uint32_t fd = 0;
+            uint32_t fd = 0, g = 0;
             uint64_t W = 0;
-            const double units = ntt_geometry_cost(n, m, path, k, M, L, fd_mode, &fd, &W);
+            const double units = ntt_geometry_cost(n, m, field, k, M, L, fd_mode, fd_group, &fd, &W, &g);
             const double cost = units * (double(N) * (k + 6) + 4096.0);
             if (cost < best_cost) {
                 best_cost = cost;
@@ -327,6 +341,7 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
                 bM = M;
                 bfd = fd;
                 bW = W;
+                bg = g;
             }
         }
     }
@@ -339,6 +354,7 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
     c->tiles_out = ceil_div(m, bM);
     c->fd = bfd;
     c->windows = bfd ? bW : 0;
+    c->kgroup = bfd == 1 ? bg : 0;
     if (bk <= static_cast<uint32_t>(kLogSmallMax)) {
         c->passes = 1;
         c->radix_log2[0] = bk;
@@ -447,27 +463,34 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
         t.ws_off = (Q + w) * N;
         spectra->push_back(t);
     }
-    for (uint64_t I = 0; I < P; ++I) {
-        NttTile t = shape;
-        t.p = pairs[I * Q];  // pair (I, 0): output tile I
-        t.fd = fd_index;
-        t.out = static_cast<uint32_t>(I);
-        t.ws_off = (Q + W + I) * N;
-        if (streamed) {
-            // half the rows per sum item (key, window and accumulator columns share the
-            // shared memory two columns sets use elsewhere); the sum of row group rg
-            // overwrites rows rg of X_0, which only that item reads
-            t.logC2 = shape.logC2 - 1;
-            t.g2 = shape.g2 * 2;
-            t.ws_off = 0;
-        } else {
-            // sum items of 2048 elements per output row group, kSum4Out outputs at a time
-            t.logC2 = t.logR2 >= 11 ? 0u : 11u - t.logR2;
-            t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> t.logC2);
+    // G sums per output tile, each over at most kgroup key tiles (the counts stay below the
+    // prime); sum tile g P + I covers key tiles [g kgroup, (g + 1) kgroup) of output tile I
+    const uint64_t kg = (!streamed && c.kgroup) ? c.kgroup : Q;
+    const uint64_t G = ceil_div(Q, kg);
+    for (uint64_t g = 0; g < G; ++g)
+        for (uint64_t I = 0; I < P; ++I) {
+            NttTile t = shape;
+            t.p = pairs[I * Q];  // pair (I, 0): output tile I
+            t.fd = fd_index;
+            t.out = static_cast<uint32_t>(I);
+            t.jlo = static_cast<uint32_t>(g * kg);
+            t.jhi = static_cast<uint32_t>(std::min(Q, (g + 1) * kg));
+            t.ws_off = (Q + W + g * P + I) * N;
+            if (streamed) {
+                // half the rows per sum item (key, window and accumulator columns share the
+                // shared memory two columns sets use elsewhere); the sum of row group rg
+                // overwrites rows rg of X_0, which only that item reads
+                t.logC2 = shape.logC2 - 1;
+                t.g2 = shape.g2 * 2;
+                t.ws_off = 0;
+            } else {
+                // sum items of 2048 elements per output row group, kSum4Out outputs at a time
+                t.logC2 = t.logR2 >= 11 ? 0u : 11u - t.logR2;
+                t.g2 = static_cast<uint32_t>((uint64_t(1) << t.logR1) >> t.logC2);
+            }
+            sums->push_back(t);
         }
-        sums->push_back(t);
-    }
-    *elems = streamed ? (Q + W) * N : (Q + W + P) * N;
+    *elems = streamed ? (Q + W) * N : (Q + W + G * P) * N;
 }
 
 }  // namespace
@@ -593,9 +616,12 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
         while (i < fd_sum.size()) {
             size_t j = i;
             while (j < fd_sum.size() && fd_sum[j].fd == fd_sum[i].fd) ++j;
-            // one item per row group and group of kSum4Out consecutive output tiles
+            // one item per row group and group of kSum4Out consecutive output tiles of one
+            // group of sums (the block's sum tiles come in runs of P per group)
+            const size_t P = fds[fd_sum[i].fd].P;
             for (uint32_t k = 0; k < fd_sum[i].g2; ++k)
-                for (size_t q = i; q < j; q += kSum4Out) push(IT_FD_SUM, i_sum + q, k);
+                for (size_t g0 = i; g0 < j; g0 += P)
+                    for (size_t q = g0; q < g0 + P; q += kSum4Out) push(IT_FD_SUM, i_sum + q, k);
             i = j;
         }
     }

@@ -21,9 +21,9 @@ template <class F>
 constexpr int kMinBlocks = sizeof(typename F::T) == 4 ? 2 : 1;
 
 // Transform-domain accumulation limits: tile pairs of one block (host tables) and
-// spectra bytes of one block.
+// spectra bytes of one block (about 22 bytes per key bit with l = 10%: n = 3e9 holds 67 GB).
 constexpr uint64_t kFdMaxPairs = uint64_t(1) << 22;
-constexpr uint64_t kFdMaxBytes = uint64_t(32) << 30;
+constexpr uint64_t kFdMaxBytes = uint64_t(96) << 30;
 
 // Work-item types (bits 60..63 of an item; bits 32..59 tile index, 0..31 sub-index).
 enum : uint32_t {
@@ -53,6 +53,7 @@ struct NttTile {
     uint32_t which;   // fd spectra: 0 key tile, 1 seed window
     uint32_t fd;      // fd spectra and sums: index of the fd block
     uint32_t out;     // fd sums: output tile index I
+    uint32_t jlo, jhi;  // fd sums: the key tiles J in [jlo, jhi) this sum covers
 };
 
 // One block under transform-domain accumulation.
@@ -65,7 +66,7 @@ struct FdBlock {
     uint32_t Q;       // key tiles
     uint32_t nfwd2;   // forward pass-2 items of the block (all precede every sum)
     uint32_t nfwd1;   // forward pass-1 items of the block (streamed sums wait for all)
-    uint32_t P;       // output tiles
+    uint32_t P;       // output tiles (per group of sums: sum tiles g P .. g P + P - 1)
     uint32_t consec;  // 1: the window of (I, J) is wmap[0][0] + I - J (equal key and output
                       // tiles: offsets (I - J) M), so sums can slide along J
 };

@@ -379,8 +379,9 @@ __device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint
 }
 
 // Rows of up to kSum4Out output tiles I0 .. I0+nout-1 from row group rg (E = max(2048, R2)
-// elements of each): Z_I = sum over the Q key tiles J of X_J * W_{wmap[I][J]} (Montgomery
-// products summed in the field), then the inverse pass 2 of every row, written to Z_I
+// elements of each): Z_I = sum over the key tiles J in [jlo, jhi) of X_J * W_{wmap[I][J]}
+// (Montgomery products summed in the field; Q key tiles in all, the row length of the
+// window-index table), then the inverse pass 2 of every row, written to Z_I
 // (output tiles at stride N from Z). The sums run over chunks of 2048 elements, each
 // accumulated in registers over all J and parked in shared memory, and each key-tile
 // vector is loaded once for all the item's outputs. Shared memory: kSum4Out x C columns
@@ -390,7 +391,8 @@ template <class F>
 __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
                                    int logR2, int logC, const typename F::T *__restrict__ X,
                                    const typename F::T *__restrict__ W,
-                                   const uint32_t *__restrict__ wmap_blk, uint32_t Q, uint32_t I0,
+                                   const uint32_t *__restrict__ wmap_blk, uint32_t Q, uint32_t jlo,
+                                   uint32_t jhi, uint32_t I0,
                                    uint32_t nout, uint32_t consec, uint64_t N,
                                    typename F::T *__restrict__ Z) {
     using T = typename F::T;
@@ -424,18 +426,21 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
             for (int o = 0; o < kSum4Out; ++o)
 #pragma unroll
                 for (int v = 0; v < VPT; ++v)
-                    wv[o][v] = o < static_cast<int>(nout) ? vec(W + uint64_t(d0 + o) * N + hb, v) : uint4{0, 0, 0, 0};
+                    wv[o][v] = o < static_cast<int>(nout)
+                                   ? vec(W + uint64_t(d0 + o - int64_t(jlo)) * N + hb, v)
+                                   : uint4{0, 0, 0, 0};
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                xn[v] = vec(X + hb, v);
-                wn[v] = Q > 1 ? vec(W + uint64_t(d0 - 1) * N + hb, v) : uint4{0, 0, 0, 0};
+                xn[v] = vec(X + uint64_t(jlo) * N + hb, v);
+                wn[v] = jlo + 1 < jhi ? vec(W + uint64_t(d0 - int64_t(jlo) - 1) * N + hb, v)
+                                      : uint4{0, 0, 0, 0};
             }
-            for (uint32_t J = 0; J < Q; ++J) {
+            for (uint32_t J = jlo; J < jhi; ++J) {
                 uint4 xv[VPT];
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) {
                     xv[v] = xn[v];
-                    if (J + 1 < Q) xn[v] = vec(X + uint64_t(J + 1) * N + hb, v);
+                    if (J + 1 < jhi) xn[v] = vec(X + uint64_t(J + 1) * N + hb, v);
                 }
 #pragma unroll
                 for (int o = 0; o < kSum4Out; ++o)
@@ -445,7 +450,7 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
 #pragma unroll
                         for (int k = 0; k < V; ++k) acc[o][v][k] = F::add(acc[o][v][k], F::mont(xs[k], ws[k]));
                     }
-                if (J + 1 < Q) {
+                if (J + 1 < jhi) {
 #pragma unroll
                     for (int o = kSum4Out - 1; o > 0; --o)
 #pragma unroll
@@ -453,12 +458,12 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
 #pragma unroll
                     for (int v = 0; v < VPT; ++v) {
                         wv[0][v] = wn[v];
-                        if (J + 2 < Q) wn[v] = vec(W + uint64_t(d0 - int64_t(J) - 2) * N + hb, v);
+                        if (J + 2 < jhi) wn[v] = vec(W + uint64_t(d0 - int64_t(J) - 2) * N + hb, v);
                     }
                 }
             }
         } else {
-            for (uint32_t J = 0; J < Q; ++J) {
+            for (uint32_t J = jlo; J < jhi; ++J) {
                 uint4 xv[VPT];
 #pragma unroll
                 for (int v = 0; v < VPT; ++v) xv[v] = vec(X + uint64_t(J) * N + hb, v);
@@ -681,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 if (wait_count(cfd + tl.fd, fb.nfwd2, status, &flag))
                     body_sum4_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
                                           logC2, ws + fb.x_off, ws + fb.w_off, wmap + fb.wmap, fb.Q,
-                                          tl.out, nout, fb.consec, uint64_t(1) << logN, X);
+                                          tl.jlo, tl.jhi, tl.out, nout, fb.consec, uint64_t(1) << logN, X);
                 signal_counts(c2 + ti, nout);
                 break;
             }

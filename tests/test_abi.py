@@ -103,24 +103,24 @@ def test_plan_query_block_fp8(lib, n, m):
     assert e.value.status == binding.PA_ERR_INVALID
 
 
-@pytest.mark.parametrize("n,m,path,bits", [(1_000_000_007, 100_000_000, "ntt31", 31),
-                                           (300_000_007, 30_000_000, "ntt31", 29),
-                                           (3_000_000_000, 300_000_000, "ntt64", 64)])
-def test_plan_query_paper_scale(lib, n, m, path, bits):
-    # Paper-scale blocks (Fig. 3 reaches 1e10 bits): the exact transform over the smallest
-    # prime above every coefficient (counts <= n), with transform-domain accumulation so
-    # only (key + window + output) spectra of N <= 2^23 elements are held.
+@pytest.mark.parametrize("n,m", [(1_000_000_007, 100_000_000), (300_000_007, 30_000_000),
+                                 (3_000_000_000, 300_000_000)])
+def test_plan_query_paper_scale(lib, n, m):
+    # Paper-scale blocks (Fig. 3 reaches 1e10 bits): the exact transform over the 29-bit
+    # prime at any length, with transform-domain accumulation so only (key + window +
+    # output) spectra of N <= 2^23 elements are held. A sum over g key tiles counts at
+    # most g L products per coefficient, so each output tile takes ceil(Q / g) sums with
+    # g = (p - 1) // L, and their bits are XOR-merged.
+    p29 = 7 * 2 ** 26 + 1
     d = pkg.pa_plan_query(n, m)
-    assert d["path_name"] == path and d["prime_bits"] == bits
-    k = d["log2_transform"]
-    assert k <= 23 and (k <= 22 or d["fd"] == 1)
-    if bits < 64:
-        # resident spectra: key tiles + distinct windows + outputs, about 4 (n + m) elements
-        assert d["fd"] == 1
-        assert d["workspace_bytes"] >= 4 * (d["tiles_in"] + d["windows"] + d["tiles_out"]) << k
-    # the 64-bit plan at n = 3e9 would need about 106 GB of resident spectra, above the
-    # 32 GiB cap, so it uses standard tile pairs in 4 GiB of reused spectra slots
-    assert d["workspace_bytes"] < 24 * 2 ** 30
+    assert d["path_name"] == "ntt31" and d["prime_bits"] == 29
+    k, L, Q, P = d["log2_transform"], d["tile_in"], d["tiles_in"], d["tiles_out"]
+    assert k <= 23 and d["fd"] == 1
+    g = (p29 - 1) // L
+    assert d["sum_groups"] == -(-Q // g) and (n <= p29 - 1 or d["sum_groups"] >= 2)
+    # resident spectra: key tiles + distinct windows + one output per sum
+    assert d["workspace_bytes"] >= 4 * (Q + d["windows"] + d["sum_groups"] * P) << k
+    assert d["workspace_bytes"] < 96 * 2 ** 30
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 64, 65, 1000, 4097])

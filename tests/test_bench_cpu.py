@@ -66,3 +66,14 @@ def test_workloads_named_by_shape():
                  "batched8"):
         blocks, cfg = bench.workload(name)
         assert blocks and cfg["blocks"] == len(blocks) and cfg["workload"]
+
+
+def test_ntt_ops_counts_one_inverse_per_sum():
+    # accumulated block: (Q + W + G P) transforms of (N/2) log2 N butterflies plus P Q N
+    # summed products, 8 ops each
+    d = {"path_name": "ntt31", "log2_transform": 23, "tiles_in": 239, "tiles_out": 24,
+         "fd": 1, "windows": 262, "sum_groups": 3}
+    N = 2.0 ** 23
+    want = 8.0 * ((239 + 262 + 3 * 24) * (N / 2) * 23 + 24 * 239 * N)
+    assert bench._ntt_ops([d]) == pytest.approx(want)
+    assert bench._ntt_ops([dict(d, sum_groups=1)]) < want

@@ -85,19 +85,39 @@ def test_prime_choice(lib):
     assert q(1_000_000, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 29
     assert q(1_000_000, 5_000, binding.make_opts(path="ntt31", ntt_prime=31))["prime_bits"] == 31
     assert q(1_000_000, 5_000, binding.make_opts(path="ntt64"))["prime_bits"] == 64
-    # 7 * 2^26 + 1 = 469,762,049: counts up to n must stay below the prime
-    assert q(469_762_048, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 29
-    assert q(469_762_049, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 31
-    with pytest.raises(pkg.PAError) as e:
-        q(469_762_049, 5_000, binding.make_opts(path="ntt31", ntt_prime=29))
-    assert e.value.status == binding.PA_ERR_UNSUPPORTED
-    with pytest.raises(pkg.PAError) as e:
-        q(2_013_265_921, 5_000, binding.make_opts(path="ntt31"))
-    assert e.value.status == binding.PA_ERR_UNSUPPORTED
+    # 7 * 2^26 + 1 = 469,762,049 serves any n: tile pairs count at most L < p products,
+    # transform-domain sums at most (p - 1) // L key tiles' worth
+    for n in (469_762_048, 469_762_049, 2_013_265_921):
+        for prime in (0, 29):
+            d = q(n, 5_000, binding.make_opts(path="ntt31", ntt_prime=prime))
+            assert d["prime_bits"] == 29
+            if d["fd"] == 1:
+                assert d["sum_groups"] == -(-d["tiles_in"] // ((469_762_048) // d["tile_in"]))
+            elif d["fd"] == 2:
+                assert d["tiles_in"] * d["tile_in"] <= 469_762_048 + d["tile_in"]
     for bad in (7, 30):
         with pytest.raises(pkg.PAError):
             q(1_000, 5, binding.make_opts(path="ntt31", ntt_prime=bad))
     assert q(1_000, 5, binding.make_opts(path="direct"))["prime_bits"] == 0
+
+
+@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+def test_sum_groups(lib, path, prime):
+    # pa_opts.fd_group caps the key tiles per transform-domain sum: ceil(Q / g) sums per
+    # output tile, each with its own output spectrum
+    n, m, k, L, M = GEOMS[0]
+    base = pkg.pa_plan_query(n, m, binding.make_opts(path=path, log2_transform=k, tile_in=L,
+                                                     tile_out=M, fd_mode=2, ntt_prime=prime))
+    assert base["fd"] == 1 and base["sum_groups"] == 1
+    Q, P = base["tiles_in"], base["tiles_out"]
+    elem = 8 if path == "ntt64" else 4
+    for g in (1, 2, 4, Q - 1, Q, Q + 5):
+        d = pkg.pa_plan_query(n, m, binding.make_opts(path=path, log2_transform=k, tile_in=L,
+                                                      tile_out=M, fd_mode=2, ntt_prime=prime,
+                                                      fd_group=g))
+        G = -(-Q // min(g, Q))
+        assert d["fd"] == 1 and d["sum_groups"] == G
+        assert d["workspace_bytes"] - base["workspace_bytes"] >= (G - 1) * P * elem << k
 
 
 @pytest.mark.parametrize("path", ["ntt31", "ntt64"])

@@ -56,7 +56,7 @@ def test_streamed_matches_oracle(path, prime, n, m, k, L, M):
 @pytest.mark.parametrize("kind", ["ones", "seed_ones"])
 def test_fd_largest_coefficients(kind):
     # all-ones inputs give the largest sums (every coefficient counts L products per key
-    # tile), the case that needs n < p of the 31-bit field
+    # tile, up to n in one transform-domain sum)
     n, m = 60_001, 25_003
     key = np.full((n + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
     seed = np.full((n + m - 1 + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
@@ -66,6 +66,45 @@ def test_fd_largest_coefficients(kind):
     got, desc = run_path(n, m, key, seed, path="ntt31", log2_transform=13, tile_in=4096,
                          tile_out=4096, fd_mode=2)
     assert desc["fd"] == 1 and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("geom", [GEOMS[0], GEOMS[3], GEOMS[5], GEOMS[7]])
+@pytest.mark.parametrize("group", [1, 3])
+def test_grouped_sums_match_oracle(path, prime, geom, group):
+    # Several transform-domain sums per output tile (pa_opts.fd_group key tiles each), each
+    # with its own inverse transform, their output bits XOR-merged (Eq. finalkey): sliding
+    # (L = M) and looked-up windows, ragged last groups.
+    n, m, k, L, M = geom
+    blk = inputs.single_block(n, m, 61 + n, 67 + m)
+    key, seed = blk.key(), blk.seed()
+    want = oracle.hash_full(n, m, seed, key)
+    got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
+                         fd_mode=2, ntt_prime=prime, fd_group=group)
+    assert desc["fd"] == 1 and desc["sum_groups"] == -(-desc["tiles_in"] // group) > 1
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
+
+
+def test_grouped_sums_at_the_exactness_limit():
+    # All-ones key and seed: every coefficient of a sum over g key tiles counts g L
+    # products. With L = 2^23 - 4096 the 29-bit prime p = 469,762,049 allows g = 56
+    # (56 L = 469,532,672 < p; 57 L would wrap), so n = 5e8 + 1 takes two sums (56 + 4 key
+    # tiles) per output tile. Every output bit is n mod 2 (each row of T is all ones).
+    n, m = 500_000_001, 3_001
+    L, M = (1 << 23) - 4096, 4096
+    key = np.full((n + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    seed = np.full((n + m - 1 + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    got, desc = run_path(n, m, key, seed, path="ntt31", log2_transform=23, tile_in=L, tile_out=M,
+                         fd_mode=2)
+    assert (desc["prime_bits"], desc["fd"], desc["tiles_in"], desc["sum_groups"]) == (29, 1, 60, 2)
+    assert ((469_762_049 - 1) // L, 56 * L < 469_762_049 <= 57 * L) == (56, True)
+    bits = oracle.unpack(got, m)
+    assert np.all(bits == (n & 1))
+    if m % 64:
+        assert int(got[-1]) >> (m % 64) == 0
+    rows = np.array([0, 1, m // 2, m - 1])
+    assert np.array_equal(bits[rows], oracle.hash_rows(n, m, seed, key, rows))
 
 
 def test_fd_and_standard_tiles_in_one_launch():
@@ -116,6 +155,7 @@ def test_fd_equals_standard_at_size():
 # L = 7 * 2^20, M = 2^20: one output tile, the sums with a single output per item.
 BIG = (8_000_003, 600_001, 23)
 BIG_TILES = [(15 << 19, 1 << 19, 2), (7 << 20, 1 << 20, 1)]
+# the same at one key tile per sum: two sums per output tile
 
 
 @pytest.fixture(scope="module")
@@ -126,14 +166,16 @@ def big_case():
     return key, seed, oracle.hash_full(n, m, seed, key)
 
 
+@pytest.mark.parametrize("group", [0, 1])
 @pytest.mark.parametrize("L,M,P", BIG_TILES)
 @pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
-def test_largest_transform_matches_oracle(big_case, path, prime, L, M, P):
+def test_largest_transform_matches_oracle(big_case, path, prime, L, M, P, group):
     n, m, k = BIG
     key, seed, want = big_case
     got, desc = run_path(n, m, key, seed, path=path, log2_transform=k, tile_in=L, tile_out=M,
-                         fd_mode=2, ntt_prime=prime)
+                         fd_mode=2, ntt_prime=prime, fd_group=group)
     assert (desc["log2_transform"], desc["fd"], desc["tiles_in"], desc["tiles_out"]) == (23, 1, 2, P)
+    assert desc["sum_groups"] == (2 if group == 1 else 1)
     bad = np.flatnonzero(got != want)
     assert bad.size == 0, f"{path} {desc}: {bad.size} words differ, first at {bad[0]}"
 
