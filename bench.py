@@ -61,6 +61,10 @@ def workload(name: str):
         # the upper range of the paper's length-compatible runs: 1 Gbit key, l = 10%
         b = inputs.single_block(1_000_000_007, 100_000_000, 31, 32)
         return [b], {"workload": f"paper scale n={b.n} m={b.m}", "blocks": 1}
+    if name == "paper_scale_3e9":
+        # a 3 Gbit key (Fig. 3 runs to 1e10 bits), l = 10%
+        b = inputs.single_block(3_000_000_019, 300_000_000, 33, 34)
+        return [b], {"workload": f"paper scale n={b.n} m={b.m}", "blocks": 1}
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -201,6 +201,23 @@ def test_paper_scale_block_sampled_rows():
     assert np.array_equal(oracle.unpack(got, m)[rows], want), desc
 
 
+def test_paper_scale_3e9_sampled_rows():
+    # n = 3e9 (Fig. 3 runs to 1e10 bits), l = 10%: above both 32-bit primes, so the
+    # 29-bit field takes several transform-domain sums per output tile (67 GB of spectra),
+    # checked on sampled rows including output-tile edges.
+    n, m = 3_000_000_019, 300_000_000
+    b = inputs.single_block(n, m, 33, 34)
+    key, seed = b.key(), b.seed()
+    got, desc = run_path(n, m, key, seed, path="auto")
+    assert desc["path_name"] == "ntt31" and desc["prime_bits"] == 29, desc
+    assert desc["fd"] == 1 and desc["sum_groups"] > 1, desc
+    M = desc["tile_out"]
+    rng = np.random.default_rng(13)
+    rows = np.unique(np.concatenate([rng.integers(0, m, 12), [0, M - 1, M, m - 1]]))
+    want = oracle.hash_rows(n, m, seed, key, rows)
+    assert np.array_equal(oracle.unpack(got, m)[rows], want), desc
+
+
 def _random_shapes(count=24, seed=2024):
     rng = np.random.default_rng(seed)
     out = []
