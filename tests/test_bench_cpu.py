@@ -63,6 +63,7 @@ def test_cpu_baseline_sample_is_bounded():
 
 def test_workloads_named_by_shape():
     for name in ("plain_single", "plain_vs_transform_m250000", "finite_size", "paper_scale",
+                 "paper_scale_3e9",
                  "batched8"):
         blocks, cfg = bench.workload(name)
         assert blocks and cfg["blocks"] == len(blocks) and cfg["workload"]
