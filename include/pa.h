@@ -86,7 +86,8 @@ typedef struct {
                                   keys take several sums per output sub-block, their bits
                                   XOR-merged as Eq. finalkey merges sub-blocks)           */
     uint32_t fd_group;         /* transform-domain sums: at most this many key sub-blocks
-                                  per sum; 0 = the prime's exactness limit (p-1)/L        */
+                                  per sum; 0 = the prime's exactness limit (p-1)/L. Like
+                                  fd_mode it also binds an autotuned batch's NTT blocks  */
     uint32_t reserved[3];
 } pa_opts;
 

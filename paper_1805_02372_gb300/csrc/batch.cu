@@ -265,7 +265,7 @@ int get_tuner(Tuner *out) {
 
 // Estimated seconds of one block on each path; fills opts with the best choice.
 double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *best,
-                 uint32_t fd_mode = 0) {
+                 uint32_t fd_mode = 0, uint32_t fd_group = 0) {
     memset(best, 0, sizeof(*best));
     best->device = -1;
     double bt = INFINITY;
@@ -319,13 +319,14 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 uint32_t fd = 0, kgroup = 0;
                 uint64_t windows = 0;
                 const double units = ntt_geometry_cost(n, m, f == 0 ? kFieldF29 : kFieldF64,
-                                                       static_cast<uint32_t>(k), M, L, fd_mode, 0,
+                                                       static_cast<uint32_t>(k), M, L, fd_mode, fd_group,
                                                        &fd, &windows, &kgroup);
                 const double launches = batched ? 0.0 : 2.0;
                 o.log2_transform = static_cast<uint32_t>(k);
                 o.tile_out = M;
                 o.tile_in = L;
                 o.fd_mode = fd_mode;
+                o.fd_group = fd_group;
                 consider(floor(units * per_pair(t.ntt[f], k) + launches * t.launch, per_pair(t.ntt1[f], k)),
                          o);
             }
@@ -490,8 +491,9 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         if (forced) {
             o = *opts;
         } else {
-            // the autotuner's choice; a caller's fd_mode still applies to NTT blocks
-            best_path(n, m, t, true, &o, opts ? opts->fd_mode : 0);
+            // the autotuner's choice; a caller's fd_mode and fd_group still apply to NTT
+            // blocks
+            best_path(n, m, t, true, &o, opts ? opts->fd_mode : 0, opts ? opts->fd_group : 0);
         }
         int rc = plan_resolve(n, m, &o, &b->cfg[i]);
         if (rc != PA_OK) {

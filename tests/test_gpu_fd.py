@@ -250,6 +250,32 @@ def test_finite_size_fd_sampled_rows():
     assert np.array_equal(g12, got ^ g2)
 
 
+def test_autotuned_batch_honours_fd_group():
+    # pa_opts.fd_group binds the autotuner's NTT blocks in a batch: with one key tile per
+    # sum an accumulated block has a sum per key tile, and no block with several key
+    # tiles streams (one accumulator over all of them); the bits stay the oracle's.
+    import torch
+    shapes = [(1_000_003, 60_000), (2_000_003, 400_001), (4_000_037, 40_009), (3_000_017, 1_500_007)]
+    bl = [inputs.single_block(n, m, 521 + i, 621 + i) for i, (n, m) in enumerate(shapes)]
+    keys, seeds = [b.key() for b in bl], [b.seed() for b in bl]
+    want = [oracle.hash_full(b.n, b.m, s, k) for b, k, s in zip(bl, keys, seeds)]
+    outs = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in bl]
+    desc = [(b.n, b.m, dev(s), dev(k), o) for b, s, k, o in zip(bl, seeds, keys, outs)]
+    batch = pkg.pa_batch_plan(desc, binding.make_opts(path="auto", fd_group=1))
+    try:
+        plans = pkg.pa_batch_describe(batch, len(bl))
+        for p in plans:
+            if p["fd"] == 1:
+                assert p["sum_groups"] == p["tiles_in"], p
+            if p["fd"] == 2:
+                assert p["tiles_in"] == 1, p
+        pkg.pa_batch_run(batch, desc)
+        for o, w in zip(outs, want):
+            assert np.array_equal(host(o), w)
+    finally:
+        pkg.pa_batch_destroy(batch)
+
+
 def test_autotuned_batch_honours_fd_mode():
     # pa_opts.fd_mode applies to the autotuner's NTT blocks in a batch too: 1 plans no
     # transform-domain accumulation, and the bits stay the oracle's either way.
