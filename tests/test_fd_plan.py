@@ -167,3 +167,17 @@ def test_finite_and_paper_scale_take_the_largest_transform(lib):
         d = pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31"))
         assert (d["log2_transform"], d["fd"]) == (23, 1)
         assert d["tile_in"] + d["tile_out"] <= 1 << 23
+
+
+@pytest.mark.parametrize("n,m,k,L,M", STREAMED[:3])
+def test_several_sums_never_stream(lib, n, m, k, L, M):
+    # The streamed body keeps one accumulator over every key tile, so a block whose key
+    # needs several sums (here forced by fd_group) takes the multi-output sums with a
+    # single output tile instead.
+    opts = dict(path="ntt31", log2_transform=k, tile_in=L, tile_out=M, fd_mode=2)
+    d = pkg.pa_plan_query(n, m, binding.make_opts(**opts))
+    assert d["fd"] == 2 and d["sum_groups"] == 1
+    g = pkg.pa_plan_query(n, m, binding.make_opts(fd_group=1, **opts))
+    assert (g["fd"], g["tiles_out"], g["sum_groups"]) == (1, 1, g["tiles_in"])
+    assert g["windows"] == g["tiles_in"]
+
