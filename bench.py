@@ -9,9 +9,16 @@ Table 1), bit-exact against the CPU oracle (checked on sampled rows every run).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                        [--path auto|direct|ntt64|ntt31|fft|block_int8|block_fp8]
-                       [--impl ours|reference]
+                       [--impl ours|reference] [--quick]
 Under torchrun every rank runs the same workload on its own GPU (independent
 blocks: weak scaling, no data-path collective); rank 0 prints one JSON line.
+
+Besides the headline (the batched workload on the autotuned path), rank 0 adds to the
+same line: the plain single-block kernel on the same blocks, the batched workload with
+each path forced, the single-block workloads on several paths, Table 1's shapes, the
+serving workload at five request rates, the measured issue-rate peaks the roofline
+fractions are taken against, and the CPU oracle timed on whole blocks (all cores and
+one core). ``--quick`` leaves those out.
 """
 from __future__ import annotations
 
@@ -262,14 +269,18 @@ CLOCK_HZ = 2070e6
 SMS = 152
 # dense FP8 tensor rate: 16384 flops per SM per clock (8192 e4m3 MACs), at the maximum clock
 FP8_DERIVED_TFLOPS = SMS * 16384 * CLOCK_HZ / 1e12
+# integer operations per butterfly and per field multiply-add, the counting unit of the
+# achieved / peak figures in Tops/s (the fraction itself is a ratio of times and does
+# not depend on it)
+OPS_PER_BFLY = 8
 
 
-def _ntt_ops(descs):
-    """8 integer ops per butterfly. A standard tile pair of size N costs 3 (N/2) log2 N + N/2
-    butterflies (two forward transforms, one inverse, the pointwise product); a block under
-    transform-domain accumulation costs (Q + W + G P) (N/2) log2 N for its Q key, W window
-    and G P output transforms (G sums per output tile) plus P Q N products summed."""
-    ops = 0.0
+def ntt_work(descs):
+    """(butterflies, multiply-adds) of the NTT blocks: a standard tile pair of size N is
+    two forward transforms and one inverse, (N/2) log2 N butterflies each, and N pointwise
+    products; a block under transform-domain accumulation computes its Q key, W window and
+    G P output transforms once (G sums per output tile) and sums P Q N products."""
+    bfly = prod = 0.0
     for d in descs:
         if d["path_name"] not in ("ntt31", "ntt64"):
             continue
@@ -278,35 +289,48 @@ def _ntt_ops(descs):
         P, Q = d["tiles_out"], d["tiles_in"]
         if d.get("fd"):
             G = d.get("sum_groups") or 1
-            ops += 8.0 * ((Q + d["windows"] + G * P) * (N / 2) * k + P * Q * N)
+            bfly += (Q + d["windows"] + G * P) * (N / 2) * k
+            prod += P * Q * N
         else:
-            ops += 8.0 * P * Q * (3 * (N / 2) * k + N / 2)
-    return ops
+            bfly += P * Q * 3 * (N / 2) * k
+            prod += P * Q * N
+    return bfly, prod
 
 
-def algorithmic(kernel: str, blocks, descs):
-    """(bound, algorithmic units per step, unit, peak, peak_source) for a kernel."""
-    int_alu = SMS * 64 * CLOCK_HZ / 1e12
-    int_all = SMS * 128 * CLOCK_HZ / 1e12
+def algorithmic(kernel: str, blocks, descs, probe):
+    """(bound, algorithmic ops per step, unit, seconds those ops take at the peak per step,
+    peak_source) for a kernel; `probe` holds the issue-rate peaks measured in this run."""
     if kernel == "direct":
-        # 32 funnel shifts + 32 LOP3 per 32 rows x 32 key bits: m*n/16 integer ops.
-        ops = sum(2.0 * b.m * b.n / 32.0 for b, d in zip(blocks, descs)
-                  if d["path_name"] == "direct")
-        return "alu", ops, "Tops/s", int_alu, "derived: 152 SM x 64 INT32 lanes x 2070 MHz"
+        # one shift-and-accumulate per (row, 32 key bits): m n / 32 of them
+        ops = sum(b.m * b.n / 32.0 for b, d in zip(blocks, descs) if d["path_name"] == "direct")
+        if not probe:
+            return None, None, None, None, None
+        return ("alu", ops, "Tops/s", ops / probe["shift_and_per_s"],
+                f"measured in this run: pa_probe_peak(PA_PEAK_SHIFT_AND) = "
+                f"{probe['shift_and_per_s'] / 1e12:.2f} T shift-and-accumulates/s")
     if kernel == "batch_persistent":
-        return ("alu", _ntt_ops(descs), "Tops/s", int_all,
-                "derived: 152 SM x (64 ALU + 64 FMA-pipe IMAD) lanes x 2070 MHz")
+        bfly, prod = ntt_work(descs)
+        if not probe:
+            return None, None, None, None, None
+        t_peak = bfly / probe["butterfly_per_s"] + prod / probe["muladd_per_s"]
+        return ("alu", OPS_PER_BFLY * (bfly + prod), "Tops/s", t_peak,
+                f"measured in this run: pa_probe_peak butterflies "
+                f"{probe['butterfly_per_s'] / 1e12:.3f} T/s and multiply-adds "
+                f"{probe['muladd_per_s'] / 1e12:.3f} T/s of the 29-bit field in registers "
+                f"on all SMs; peak time = {bfly:.4g} butterflies / that + {prod:.4g} "
+                f"multiply-adds / that; {OPS_PER_BFLY} ops per butterfly or multiply-add")
     if kernel == "block_mma":
         ops = sum(2.0 * b.m * (b.n + 8192) for b, d in zip(blocks, descs)
                   if d["path_name"] == "block_int8")
-        return "tensor", ops, "Tops/s", 150.8, "measured: legacy mma.sync s8 peak on GB300"
+        return ("tensor", ops, "Tops/s", ops / 150.8e12,
+                "measured (earlier probe, not in this run): legacy mma.sync s8 at 150.8 Top/s")
     if kernel == "block_tc":
         # dense FP8 MMA work the kernel performs: M = 128 rows x N = 256 blocks per output
         # tile, over the tile's contraction length n + 128 * 255
         ops = sum(2.0 * 32768 * -(-b.m // 32768) * (b.n + 128 * 255)
                   for b, d in zip(blocks, descs) if d["path_name"] == "block_fp8")
         pk, src = peaks()
-        return ("tensor", ops, "TFLOP/s", 2.0 * pk["bf16_tflops"],
+        return ("tensor", ops, "TFLOP/s", ops / (2.0 * pk["bf16_tflops"] * 1e12),
                 f"{src} bf16 dense x 2 (nominal fp8 / bf16 ratio, 4.5 / 2.25 PFLOP/s); the bf16 "
                 f"figure was taken under the power cap (median SM clock in MEASURED_PEAKS), so a "
                 f"kernel holding the maximum clock can exceed it: the clock-derived dense FP8 "
@@ -317,7 +341,8 @@ def algorithmic(kernel: str, blocks, descs):
             if d["path_name"] == "fft":
                 N = 2.0 ** d["log2_transform"]
                 fl += d["tiles_in"] * d["tiles_out"] * 3 * (N / 2) * d["log2_transform"] * 10
-        return ("alu", fl, "TFLOP/s", SMS * 128 * 2 * CLOCK_HZ / 1e12,
+        peak = SMS * 128 * 2 * CLOCK_HZ
+        return ("alu", fl, "TFLOP/s", fl / peak,
                 "derived: 152 SM x 128 FP32 lanes x 2 flops x 2070 MHz")
     return None, None, None, None, None
 
@@ -335,18 +360,20 @@ def compulsory_bytes(blocks):
                for b in blocks)
 
 
-def roofline(kt: dict, blocks, descs, steps: int, workload_name: str):
+def roofline(kt: dict, blocks, descs, steps: int, workload_name: str, probe=None):
     work = {k: v for k, v in kt.items() if k != "memset"}
     if not work:
         return None
     name, v = max(work.items(), key=lambda kv: kv[1]["total_ms"])
     launches_per_step = max(1.0, v["launches"] / steps)
     per_launch_ms = v["total_ms"] / v["launches"]
-    bound, units, unit, peak, src = algorithmic(name, blocks, descs)
+    bound, units, unit, t_peak, src = algorithmic(name, blocks, descs, probe)
     out = {"kernel": name, "launch_ms": per_launch_ms, "launches": v["launches"],
            "share": v["total_ms"] / sum(x["total_ms"] for x in kt.values())}
     if bound is not None and units:
-        ach = units / launches_per_step / (per_launch_ms * 1e-3) / 1e12
+        t_launch = per_launch_ms * 1e-3 * launches_per_step  # kernel seconds per step
+        ach = units / t_launch / 1e12
+        peak = units / t_peak / 1e12
         out.update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                     "frac": ach / peak, "peak_source": src})
         if name == "block_tc":
@@ -354,7 +381,8 @@ def roofline(kt: dict, blocks, descs, steps: int, workload_name: str):
     pk, psrc = peaks()
     hbm = compulsory_bytes(blocks) / launches_per_step / (per_launch_ms * 1e-3) / 1e9
     out["hbm_compulsory"] = {"achieved_gbs": hbm, "peak_gbs": pk["hbm_gbs"],
-                             "frac": hbm / pk["hbm_gbs"], "peak_source": psrc + " (MEASURED_PEAKS)"}
+                             "frac": hbm / pk["hbm_gbs"], "peak_source": psrc + " (MEASURED_PEAKS)",
+                             "bytes_per_step": compulsory_bytes(blocks)}
     out["traffic"] = traffic_for(name, workload_name)
     return out
 
@@ -380,42 +408,43 @@ def traffic_for(kernel: str, workload_name: str):
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_gbps(blocks, rows_per_block: int = 40000, seed: int = 3, max_blocks: int = 256):
-    """The oracle as it stands (all host cores), timed on a bounded sample of each block.
-
-    The oracle's full hash of a block is one set-up (seed reversal, key masking) plus m row
-    evaluations spread over the cores. Per block it is timed on R/4 and on R rows: the
-    difference gives the per-row cost (set-up and thread start cancel), the full-block
-    time is set-up + m x per-row, summed over the blocks (a uniform sample of at most
-    max_blocks of them, scaled up). Returns (Gbps, cores, description)."""
+def cpu_oracle_measured(blocks, budget_s: float = 20.0, threads: int | None = None,
+                        order=None, seed: int = 3):
+    """The oracle as it stands, timed on WHOLE blocks: blocks are hashed in full, in a
+    seeded random order (or the given order), until `budget_s` seconds of oracle time have
+    passed (the block running then is finished). Returns (Gbps over the blocks hashed,
+    blocks hashed, oracle seconds, key bits, threads). Key and seed generation is not
+    timed."""
     import oracle
-    rng = np.random.default_rng(seed)
-    idx = np.arange(len(blocks))
-    if len(idx) > max_blocks:
-        idx = rng.choice(idx, max_blocks, replace=False)
-    est, measured = 0.0, 0.0
-    for i in idx:
-        b = blocks[i]
-        k, s = b.key(), b.seed()
-        # about 2e10 bit products per block sampled (bounded CPU time), at least R rows
-        r = max(8, min(b.m, max(rows_per_block, int(2e10 / b.n / len(idx)))))
-        r1 = max(1, r // 4)
-        rows = rng.integers(0, b.m, r)
+    if order is None:
+        order = np.random.default_rng(seed).permutation(len(blocks))
+    th = threads or oracle.default_threads()
+    spent, bits, done = 0.0, 0, 0
+    for i in order:
+        if done and spent >= budget_s:
+            break
+        b = blocks[int(i)]
+        k, s_ = b.key(), b.seed()
         t0 = time.perf_counter()
-        oracle.hash_rows(b.n, b.m, s, k, rows[:r1])
-        t1 = time.perf_counter()
-        oracle.hash_rows(b.n, b.m, s, k, rows)
-        t2 = time.perf_counter()
-        per_row = max((t2 - t1) - (t1 - t0), 0.0) / (r - r1)
-        setup = max((t1 - t0) - per_row * r1, 0.0)
-        est += setup + per_row * b.m
-        measured += t2 - t0
-    est *= len(blocks) / len(idx)
-    gbps = sum(b.n for b in blocks) / est / 1e9
-    cores = os.cpu_count() or 1
-    return gbps, cores, (f"{len(idx)} of {len(blocks)} blocks, each timed on R/4 and R >= "
-                         f"{rows_per_block} uniformly drawn output rows ({measured:.1f} s "
-                         f"measured); full-block time = set-up + m x per-row time")
+        oracle.hash_full(b.n, b.m, s_, k, threads=th)
+        spent += time.perf_counter() - t0
+        bits += b.n
+        done += 1
+    return bits / spent / 1e9, done, spent, bits, th
+
+
+def cpu_baseline(blocks):
+    """All host cores on a random sample of whole blocks (about 20 s), and one core on the
+    cheapest blocks (by m n, about 8 s)."""
+    g, k, t, _, th = cpu_oracle_measured(blocks, budget_s=20.0)
+    cheap = np.argsort([b.m * b.n for b in blocks], kind="stable")
+    g1, k1, t1, _, _ = cpu_oracle_measured(blocks, budget_s=8.0, threads=1, order=cheap)
+    return {"value": g, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": f"{k} of {len(blocks)} blocks hashed in full (seeded random order, "
+                      f"{t:.1f} s measured on {th} threads); Gbps = their key bits / that time",
+            "single_core": {"value": g1, "unit": UNIT, "cores": 1,
+                            "sample": f"the {k1} blocks of least m n hashed in full on one "
+                                      f"thread ({t1:.1f} s measured)"}}
 
 
 # --------------------------------------------------------------------------- main
@@ -458,44 +487,217 @@ def run_table1(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores. Each step hashes
+    in full the next blocks of a seeded random order of the workload's blocks until about
+    two seconds of oracle time have passed; the value is the key bits of the blocks timed
+    over the time they took, and ms_per_step is the measured mean step time."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle
     blocks, cfg = workload(args.workload)
-    per_step = []
-    for _ in range(min(args.warmup, 1)):
-        cpu_oracle_gbps(blocks, rows_per_block=64, max_blocks=8)
-    for k in range(args.steps):
-        g, cores, desc = cpu_oracle_gbps(blocks, rows_per_block=1024, seed=100 + k, max_blocks=64)
-        per_step.append(g)
-    val = float(np.mean(per_step))
-    total_bits = sum(b.n for b in blocks)
+    order = np.random.default_rng(11).permutation(len(blocks))
+    pos = 0
+
+    def one_step():
+        nonlocal pos
+        t_step, bits_step = 0.0, 0
+        while t_step < 2.0:
+            i = order[pos % len(order)]
+            pos += 1
+            _, _, t, bits, th = cpu_oracle_measured(blocks, budget_s=0.0, order=[i])
+            t_step += t
+            bits_step += bits
+        return t_step, bits_step, th
+
+    tot_t, tot_bits, th, per_step = 0.0, 0, oracle.default_threads(), []
+    for k in range(args.warmup + args.steps):
+        t_step, bits_step, th = one_step()
+        if k >= args.warmup:
+            tot_t += t_step
+            tot_bits += bits_step
+            per_step.append(t_step)
+    val = tot_bits / tot_t / 1e9
+    desc = (f"each step hashes whole blocks in full (next blocks of a seeded random order, "
+            f"about 2 s of oracle time per step); {args.steps} timed steps covered "
+            f"{tot_bits / 1e6:.1f} Mbit in {tot_t:.1f} s on {th} threads")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_bits / (val * 1e9) * 1e3, "higher_is_better": True,
+            "ms_per_step": float(np.mean(per_step)) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": cfg,
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "config": dict(cfg, sample="whole blocks per step, see cpu_baseline"),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": th, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+SERVING_RATES = (10.0, 100.0, 500.0, 1000.0, 2000.0)
+
+
 def serving_probe(rates, count):
     """Continuous-batching server on the serving workload: Poisson arrivals at each rate,
-    n log-uniform in [1e5, 1e8], r uniform in [0.01, 0.5], device-resident requests."""
+    n log-uniform in [1e5, 1e8], r uniform in [0.01, 0.5], device-resident requests. The
+    same `count` requests (shapes and buffers) are replayed at every rate, their arrival
+    times rescaled. The saturation rate is the lowest rate whose sustained throughput
+    falls below 0.9 of the offered load or whose late arrivals wait three times longer
+    than the early ones (the queue grows)."""
+    import torch
+
     from paper_1805_02372_gb300 import serve
+    base = serve.make_requests(count, 1000.0)
     out = []
-    for i, rate in enumerate(rates):
-        reqs = serve.make_requests(count, rate, master=4 + 100 * i)
-        st = serve.replay(reqs, slots=3, max_blocks_per_wave=32)
+    for rate in rates:
+        st = serve.replay(serve.at_rate(base, rate, 1000.0), slots=3, max_blocks_per_wave=32,
+                          timeout_s=60.0 + 3.0 * count / rate)
         st["rate_hz"] = rate
         out.append(st)
-        del reqs
+    sat = next((r["rate_hz"] for r in out
+                if r["sustained_gbps"] < 0.9 * r["offered_gbps"] or r["latency_drift"] > 3.0),
+               None)
+    del base
+    torch.cuda.empty_cache()
     return {"workload": "serving: Poisson arrivals, n log-uniform in [1e5, 1e8], r uniform "
-                        "in [0.01, 0.5], device-resident keys and seeds, 3 stream slots",
-            "requests_per_rate": count, "rates": out}
+                        "in [0.01, 0.5], device-resident keys and seeds, 3 stream slots, "
+                        "at most 32 requests per wave",
+            "requests_per_rate": count, "rates": out, "saturation_rate_hz": sat,
+            "saturation_rule": "lowest rate with sustained < 0.9 offered or latency drift > 3"}
+
+
+def probe_peaks():
+    """Issue-rate peaks of this GPU for the integer paths' operations (pa_probe_peak)."""
+    from paper_1805_02372_gb300 import binding
+    b, bms = binding.pa_probe_peak(binding.PA_PEAK_NTT_BUTTERFLY)
+    ma, mms = binding.pa_probe_peak(binding.PA_PEAK_NTT_MULADD)
+    sa, sms = binding.pa_probe_peak(binding.PA_PEAK_SHIFT_AND)
+    return {"butterfly_per_s": b, "muladd_per_s": ma, "shift_and_per_s": sa,
+            "launch_ms": {"butterfly": bms, "muladd": mms, "shift_and": sms},
+            "what": "29-bit-field lazy butterfly, 29-bit-field multiply-add, funnel-shift "
+                    "AND-XOR: register-only chains on every SM, fastest of three ~20 ms "
+                    "launches after a warm-up"}
+
+
+# --------------------------------------------------------------------------- full-output checks
+
+def _sha(words) -> str:
+    return hashlib.sha256(np.ascontiguousarray(words, dtype="<u8").tobytes()).hexdigest()
+
+
+def golden_digests(workload_name: str):
+    """SHA-256 of the oracle's full output per block, from the committed golden files
+    (written by tests/golden/make_golden.py, which calls only the oracle), or None."""
+    gd = os.path.join(ROOT, "tests", "golden")
+    try:
+        if workload_name.startswith("batched"):
+            with open(os.path.join(gd, "batched256.json")) as f:
+                d = [b["sha256"] for b in json.load(f)["blocks"]]
+            k = 256 if workload_name == "batched256" else int(workload_name[len("batched"):])
+            return d[:k]
+        if workload_name == "finite_size":
+            with open(os.path.join(gd, "finite_size.json")) as f:
+                return [json.load(f)["sha256"]]
+    except (OSError, ValueError, KeyError):
+        return None
+    return None
+
+
+def check_full(runner, digests) -> bool | None:
+    """Every block's whole output against its stored oracle digest (None: no digests)."""
+    if not digests:
+        return None
+    return all(_sha(o.cpu().numpy().view(np.uint64)) == d for o, d in zip(runner.outs, digests))
+
+
+# --------------------------------------------------------------------------- sub-records
+
+def run_record(blocks, path, device, steps, flush, scratch, probe, workload_name,
+               keys_h=None, seeds_h=None, want=None, digests=None):
+    """Time one workload on one path (warm-up, `steps` timed steps, then a traced pass for
+    the roofline) and check its output; returns a compact record."""
+    import torch
+    try:
+        r = Runner(blocks, path, device, keys_h, seeds_h)
+    except Exception as e:  # a forced path that cannot take these sizes
+        return {"path": path, "unsupported": str(e)[:160]}
+    r.step()
+    torch.cuda.synchronize()
+    ms = timed(r, steps, flush, r.stream, scratch)
+    r.profile(True)
+    timed(r, 1, flush, r.stream, scratch)
+    r.profile(False)
+    kt = r.kernel_times()
+    rec = {"path": path, "paths_chosen": r.paths(), "ms_per_step": ms,
+           "gbps": r.units / (ms * 1e-3) / 1e9}
+    rf = roofline(kt, blocks, r.plan_desc, 1, workload_name, probe)
+    if rf:
+        rec["roofline"] = {k: rf[k] for k in ("kernel", "bound", "achieved", "peak", "unit",
+                                              "frac") if k in rf}
+    if want is not None:
+        rec["bit_exact_full"] = all(np.array_equal(o.cpu().numpy().view(np.uint64), w)
+                                    for o, w in zip(r.outs, want))
+    elif digests:
+        rec["bit_exact_full"] = check_full(r, digests)
+    else:
+        rec["bit_exact_sampled"] = check_sampled(r, rows_per_block=32)
+    del r
+    torch.cuda.empty_cache()
+    return rec
+
+
+def batched_paths(blocks, keys_h, seeds_h, device, flush, scratch, probe, plain_gbps, digests):
+    """The batched workload with every path forced for all blocks (the benchmark spec: the FP32 /
+    INT8 / FP8 batched paths against the plain single-block kernel)."""
+    out = {}
+    for path in ("ntt31", "ntt64", "block_fp8", "direct", "block_int8", "fft"):
+        rec = run_record(blocks, path, device, 2, flush, scratch, probe, "batched_" + path,
+                         keys_h, seeds_h, digests=digests)
+        if "gbps" in rec and plain_gbps:
+            rec["over_plain_kernel"] = rec["gbps"] / plain_gbps
+        if path == "block_fp8" and "roofline" in rec:
+            rec["tensor_pipe_util_of_clock_derived_peak"] = (
+                rec["roofline"]["achieved"] / FP8_DERIVED_TFLOPS)
+        out[path] = rec
+    return out
+
+
+def config_records(device, flush, scratch, probe):
+    """The single-block workloads (plain single block, plain vs transform, finite size) on
+    several paths, each output checked in full against the oracle (the finite-size block
+    against its stored digest)."""
+    import oracle
+    from paper_1805_02372_gb300 import inputs
+    out = []
+    cases = [("plain_single", inputs.PLAIN_SINGLE,
+              ("auto", "direct", "ntt31", "ntt64", "fft", "block_int8", "block_fp8"))]
+    for b in inputs.PLAIN_VS_TRANSFORM:
+        cases.append((f"plain_vs_transform_m{b.m}", b,
+                      ("auto", "direct", "ntt31", "ntt64", "fft", "block_int8", "block_fp8")))
+    cases.append(("finite_size", inputs.FINITE_SIZE,
+                  ("auto", "ntt31", "ntt64", "block_fp8", "direct")))
+    for name, b, paths in cases:
+        k, s_ = b.key(), b.seed()
+        digests = golden_digests(name)
+        want = None if name == "finite_size" else [oracle.hash_full(b.n, b.m, s_, k)]
+        recs = {}
+        for path in paths:
+            recs[path] = run_record([b], path, device, 2 if b.n * b.m > 1e14 else 5, flush,
+                                    scratch, probe, name, [k], [s_], want=want, digests=digests)
+        out.append({"workload": name, "n": b.n, "m": b.m, "paths": recs})
+    return out
+
+
+def table1_records(device, flush, scratch, probe):
+    """Table 1's shapes: n = 4..128 Mbit, m = floor(n / 10), one block each, AUTO path."""
+    from paper_1805_02372_gb300 import inputs
+    rows = []
+    for mbit, paper in TABLE1_PAPER_GBPS.items():
+        n = mbit * 1_000_000
+        b = inputs.single_block(n, n // 10, 10 + mbit, 11 + mbit)
+        rec = run_record([b], "auto", device, 5, flush, scratch, probe, f"table1_{mbit}")
+        rec.update({"n_mbit": mbit, "m": b.m, "paper_titan_xp_gbps": paper})
+        rows.append(rec)
+    return rows
 
 
 def timed(runner, steps, flush, stream, scratch):
@@ -521,11 +723,14 @@ def main():
     ap.add_argument("--workload", default="batched256")
     ap.add_argument("--path", default="auto")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: no sub-records, serving, probes or CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-kernel comparison")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving latency probe")
-    ap.add_argument("--serving-rates", default="100,1000",
+    ap.add_argument("--serving-rates", default=",".join(str(int(r)) for r in SERVING_RATES),
                     help="comma-separated request rates (req/s) for the serving probe")
+    ap.add_argument("--serving-requests", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -555,6 +760,7 @@ def main():
     if group:
         group.checked_barrier("timed")
         torch.distributed.barrier()
+    probe = None
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         ms = timed(runner, args.steps, flush, stream, scratch)   # graph replay, no tracing
@@ -563,11 +769,15 @@ def main():
         runner.profile(True)
         ms_traced = timed(runner, args.steps, flush, stream, scratch)
         runner.profile(False)
+        if rank == 0 and not args.quick:
+            probe = probe_peaks()  # same clock window as the timed steps
     if group:
         ms = group.max(ms)   # the job's step time is the slowest rank's
         torch.distributed.barrier()
     kt = runner.kernel_times()
-    exact = check_sampled(runner)
+    digests = golden_digests(args.workload)
+    exact_full = check_full(runner, digests)
+    exact = check_sampled(runner) if exact_full is None else exact_full
     clocks = clk.summary()
     e2e_gbps, h2d, d2h = runner.e2e(max(3, args.steps // 2))
 
@@ -580,34 +790,46 @@ def main():
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": dict(cfg, path=args.path, paths_chosen=runner.paths(),
                        l2="flushed between steps" if flush else "inputs larger than L2",
-                       bit_exact_sampled=exact),
-        "roofline": roofline(kt, blocks, runner.plan_desc, args.steps, args.workload),
+                       **({"bit_exact_full": exact_full} if exact_full is not None
+                          else {"bit_exact_sampled": exact})),
+        "roofline": roofline(kt, blocks, runner.plan_desc, args.steps, args.workload, probe),
         "e2e": {"value": e2e_gbps * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps, "clocks": clocks,
         "kernel_times_ms": {k: round(v["total_ms"] / args.steps, 5) for k, v in kt.items()},
         "ms_per_step_traced": ms_traced, "wall_s": wall,
     }
+    if probe:
+        line["probe_peaks"] = probe
     if not exact:
-        line["error"] = "sampled rows disagree with the oracle"
+        line["error"] = "outputs disagree with the oracle"
+    keys_h, seeds_h = runner.keys_h, runner.seeds_h
+    plain_gbps = None
+    extras = rank == 0 and not args.quick
     if len(blocks) > 1 and not args.no_plain and rank == 0:
         # the plain single-block kernel (direct path), block by block, same blocks
-        plain = Runner(blocks, "direct", device, runner.keys_h, runner.seeds_h,
-                       force_single=True)
+        plain = Runner(blocks, "direct", device, keys_h, seeds_h, force_single=True)
         plain.step()
         pms = timed(plain, 2, flush, stream, scratch)
-        line["plain_kernel"] = {"value": runner.units / (pms * 1e-3) / 1e9, "unit": UNIT,
+        plain_gbps = runner.units / (pms * 1e-3) / 1e9
+        line["plain_kernel"] = {"value": plain_gbps, "unit": UNIT,
                                 "path": "direct, one pa_hash per block", "ms_per_step": pms,
-                                "batched_over_plain": value / (runner.units / (pms * 1e-3) / 1e9)}
-    if rank == 0 and not args.no_serving:
+                                "batched_over_plain": value / plain_gbps}
+        del plain
+    del runner
+    torch.cuda.empty_cache()
+    if extras and len(blocks) > 1:
+        line["paths_batched"] = batched_paths(blocks, keys_h, seeds_h, device, flush, scratch,
+                                              probe, plain_gbps, digests)
+    if extras and args.workload == "batched256":
+        line["configs"] = config_records(device, flush, scratch, probe)
+        line["table1"] = table1_records(device, flush, scratch, probe)
+    if extras and not args.no_serving:
         rates = [float(r) for r in args.serving_rates.split(",") if r]
-        line["serving"] = serving_probe(rates, 60)
-        worst = max(r["p99_ms"] for r in line["serving"]["rates"])
-        line["p99_latency_ms"] = worst
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        g, cores, desc = cpu_oracle_gbps(blocks)
-        line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": desc}
+        line["serving"] = serving_probe(rates, args.serving_requests)
+        line["p99_latency_ms"] = max(r["p99_ms"] for r in line["serving"]["rates"])
+    if extras and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(blocks)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if group:

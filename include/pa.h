@@ -70,7 +70,9 @@ typedef struct {
     int32_t device;            /* CUDA device ordinal, -1 = current device                */
     uint32_t log2_transform;   /* transform paths: log2 of the transform size N           */
     uint32_t block_b;          /* block paths: tile edge b, INT8 in {128, 256, 512}, FP8 128 */
-    uint64_t tile_in;          /* key sub-block length L (the paper's batch length)       */
+    uint64_t tile_in;          /* key sub-block length L (the paper's batch length); block
+                                  FP8: contraction positions per CTA chunk, a multiple of
+                                  128 up to 32768                                         */
     uint64_t tile_out;         /* output sub-block length M (column split of Sec. 3)      */
     uint32_t force_fp64;       /* FFT path: use FP64 butterflies even where FP32 is proven */
     uint32_t max_slots;        /* batches: at most this many transform spectra resident at
@@ -114,12 +116,18 @@ typedef struct {
 
 typedef struct pa_plan_s *pa_plan_t;
 
-/* Plan the hash of an n-bit key into m bits with the default (fastest known) path.
- * Allocates the plan's device workspace on the current device. */
+/* Plan the hash of an n-bit key into m bits with the default (fastest known) path
+ * (Sec. 3 Step 2: the sub-block lengths p and q are chosen from the sizes and the device
+ * memory before any product runs; Eq. Ti / Eq. Tij split the key and the output). The
+ * planner picks the path, the key and output sub-block lengths (L, M), the transform size
+ * N or the block tile b. Allocates the plan's device workspace on the current device.
+ * out: receives the plan handle (NULL on failure). PA_ERR_INVALID for n = 0, m = 0 or a
+ * null out; PA_ERR_NOMEM if the workspace cannot be allocated. */
 int pa_plan(uint64_t n, uint64_t m, pa_plan_t *out);
 
-/* Same with options (opts may be NULL). PA_ERR_UNSUPPORTED if a forced path
- * cannot handle (n, m); PA_ERR_PRECISION if a forced FFT tile has no proven bound. */
+/* Same with options (Sec. 3 Step 2 with the caller fixing some of the choices; opts may
+ * be NULL). PA_ERR_UNSUPPORTED if a forced path cannot handle (n, m); PA_ERR_PRECISION if
+ * a forced FFT tile has no proven bound. */
 int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out);
 
 /* Resolve a plan on the host only (no GPU, no allocation). */
@@ -168,14 +176,25 @@ int pa_plan_status(pa_plan_t plan);
  *   n <= 2^25 (33,554,432) key bits, else PA_ERR_TOO_LARGE; m as for pa_hash.
  *   seed_bits, key_bits, out_bits: device pointers, 16-byte aligned, same layout as
  *   pa_hash; stream: cudaStream_t (NULL = legacy default stream); asynchronous.
- * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture. Every call
- * shares the one array and leaves its contents behind (the status word is cleared at each
- * call, the reversed key is rewritten in full): calls that overlap on the GPU race, so
- * serialise them (one stream, or events). Calls no cudaMalloc, cudaFree or allocating
- * library routine. */
+ * Outside stream capture every call looks the array's device address up
+ * (cudaGetSymbolAddress) with the current device, so the address is never stale after a
+ * device reset. Under stream capture the address cached by an earlier uncaptured call on
+ * that device is used; a call under capture with none cached returns PA_ERR_INVALID, so
+ * make the first call on each device before any capture. Every call shares the one array
+ * and leaves its contents behind (the status word is cleared at each call, the reversed
+ * key is rewritten in full): calls that overlap on the GPU race, so serialise them (one
+ * stream, or events). Calls no cudaMalloc, cudaFree or allocating library routine. A
+ * bounded device wait that gives up leaves the output incomplete and records
+ * PA_ERR_TIMEOUT in the array's status word: read it with pa_direct_static_status. */
 int pa_hash_direct_static(uint64_t n, uint64_t m, const uint64_t *seed_bits,
                           const uint64_t *key_bits, uint64_t *out_bits, void *stream);
+
+/* Device status of the last pa_hash_direct_static call on the current device: synchronises
+ * `stream` (the stream that call used; NULL = legacy default stream), reads the status
+ * word of the static array (PA_OK, or PA_ERR_TIMEOUT if a bounded wait in the kernel gave
+ * up), clears it, and returns it; PA_ERR_CUDA if a CUDA call fails, PA_ERR_INVALID under
+ * stream capture before any uncaptured call on the device. Allocates nothing. */
+int pa_direct_static_status(void *stream);
 
 /* The seed of the square matrix of Eq. 1 (Sec. 2.1): Eq. 1 writes an n x n Toeplitz matrix
  * with the 2n-1 parameters t_0 .. t_{2n-2} (t_0 .. t_{n-1} down the first column, t_n ..
@@ -264,6 +283,17 @@ int pa_server_submit(pa_server_t server, const pa_block *request, uint64_t tag);
 /* Retires finished waves into done[0..max) (count = entries written), then admits. */
 int pa_server_poll(pa_server_t server, pa_completion *done, size_t max, size_t *count);
 int pa_server_pending(pa_server_t server, uint64_t *queued, uint64_t *in_flight);
+/* Counters of a server since its creation. */
+typedef struct {
+    uint64_t waves;               /* waves launched                                         */
+    uint64_t requests_done;       /* requests retired by poll                               */
+    double plan_s_total;          /* host seconds spent forming, planning and enqueuing the
+                                     launched waves (the batch plan is on the latency path)  */
+    double plan_s_max;            /* the longest of those, one wave                          */
+    uint64_t waves_held_back;     /* wave formations undone by the memory budget             */
+    uint64_t reserved[4];
+} pa_server_stats;
+int pa_server_get_stats(pa_server_t server, pa_server_stats *out);
 /* Waits for the waves in flight, then releases everything. */
 void pa_server_destroy(pa_server_t server);
 
@@ -295,6 +325,26 @@ int pa_batch_kernel_times(pa_batch_t batch, pa_kernel_time *out, int max, int *c
  * device wait gives up after 4 s (plus 0.5 s for copies in flight), so this takes about
  * four to five seconds; synchronises the device. The GPU context remains usable. */
 int pa_selftest(int which, int *device_status);
+
+/* Measured issue-rate peaks for the roofline of the integer paths (no counterpart in the
+ * paper: a measurement of this GPU). The NTT and direct kernels are bound by integer
+ * arithmetic, not by memory, so their roofline is the rate at which this GPU executes the
+ * operations they are built from. The probe runs one such operation on independent
+ * register chains in every thread of every SM (no memory traffic, no barriers, two CTAs of
+ * 512 threads per SM like the NTT kernel) and times it with CUDA events:
+ *   which = PA_PEAK_NTT_BUTTERFLY: the lazy Gentleman-Sande butterfly of the 29-bit field
+ *           (one operation = one butterfly, Sec. 3 Step 1's transform);
+ *   which = PA_PEAK_NTT_MULADD: acc += x y in the 29-bit field (Montgomery product plus lazy
+ *           addition: the pointwise products and transform-domain sums of Sec. 3 Step 2);
+ *   which = PA_PEAK_SHIFT_AND: acc ^= x & funnel_shift(lo, hi, k), the direct kernel's step
+ *           (one operation = one shift-and-accumulate of 32 bit products, Sec. 2.1 Eq. 1).
+ * *ops_per_s: the fastest of three launches of about 20 ms (after a warm-up);
+ * *ms (nullable): that launch's device time. Synchronous; allocates 256 bytes of device
+ * memory for the duration of the call. PA_ERR_INVALID for another `which`. */
+#define PA_PEAK_NTT_BUTTERFLY 1
+#define PA_PEAK_NTT_MULADD 2
+#define PA_PEAK_SHIFT_AND 3
+int pa_probe_peak(int which, double *ops_per_s, double *ms);
 
 const char *pa_strerror(int status);
 

@@ -89,6 +89,12 @@ class pa_completion(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class pa_server_stats(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_uint64), ("requests_done", ctypes.c_uint64),
+                ("plan_s_total", ctypes.c_double), ("plan_s_max", ctypes.c_double),
+                ("waves_held_back", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)]
+
+
 class pa_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("total_ms", ctypes.c_double)]
@@ -129,14 +135,18 @@ SIGNATURES = {
     "pa_batch_kernel_times": (ctypes.c_int, [_VP, ctypes.POINTER(pa_kernel_time), ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_int)]),
     "pa_hash_direct_static": (ctypes.c_int, [_U64, _U64, _VP, _VP, _VP, _VP]),
+    "pa_direct_static_status": (ctypes.c_int, [_VP]),
     "pa_server_create": (ctypes.c_int, [ctypes.POINTER(pa_server_opts), ctypes.POINTER(_VP)]),
     "pa_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_uint64]),
     "pa_server_poll": (ctypes.c_int, [_VP, ctypes.POINTER(pa_completion), ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
     "pa_server_pending": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "pa_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(pa_server_stats)]),
     "pa_server_destroy": (None, [_VP]),
     "pa_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pa_probe_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "pa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "pa_last_cuda_error": (ctypes.c_int, []),
     "pa_version": (ctypes.c_int, []),
@@ -385,6 +395,11 @@ def pa_hash_direct_static(n: int, m: int, seed_bits, key_bits, out_bits, stream=
                                         _stream(stream)), "pa_hash_direct_static")
 
 
+def pa_direct_static_status(stream=None) -> int:
+    """Device status of the last pa_hash_direct_static call (synchronises the stream)."""
+    return load().pa_direct_static_status(_stream(stream))
+
+
 def pa_server_create(slots: int = 2, max_blocks_per_wave: int = 64,
                      memory_budget_bytes: int = 0) -> int:
     o = pa_server_opts()
@@ -416,6 +431,12 @@ def pa_server_pending(server: int) -> tuple[int, int]:
     return q.value, f.value
 
 
+def pa_server_get_stats(server: int) -> dict:
+    st = pa_server_stats()
+    _check(load().pa_server_get_stats(server, ctypes.byref(st)), "pa_server_get_stats")
+    return {k: getattr(st, k) for k, _ in st._fields_ if k != "reserved"}
+
+
 def pa_server_destroy(server: int) -> None:
     load().pa_server_destroy(server)
 
@@ -425,6 +446,19 @@ def pa_selftest(which: int) -> int:
     st = ctypes.c_int()
     _check(load().pa_selftest(which, ctypes.byref(st)), "pa_selftest")
     return st.value
+
+
+PA_PEAK_NTT_BUTTERFLY = 1
+PA_PEAK_NTT_MULADD = 2
+PA_PEAK_SHIFT_AND = 3
+
+
+def pa_probe_peak(which: int) -> tuple[float, float]:
+    """(operations per second, device ms of the timed launch) of a register-only probe of
+    one of the integer paths' operations (see include/pa.h)."""
+    r, t = ctypes.c_double(), ctypes.c_double()
+    _check(load().pa_probe_peak(which, ctypes.byref(r), ctypes.byref(t)), "pa_probe_peak")
+    return r.value, t.value
 
 
 def pa_strerror(status: int) -> str:

@@ -178,8 +178,12 @@ int calibrate(Tuner *t) {
         t->fft = tt / double(cfg.tr.tiles_in * cfg.tr.tiles_out) /
                  (double(uint64_t(1) << cfg.tr.log2n) * (cfg.tr.log2n + 2));
     }
-    for (int f = 0; f < 2; ++f) {
-        o.path = f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64;
+    // Only the 29-bit field is calibrated: with its transform-domain sums grouped below the
+    // prime it takes every key length, and a 64-bit butterfly costs about four 32-bit ones,
+    // so the tuner never gives a block to the 64-bit field (a caller can still force it).
+    for (int k = 0; k <= kTuneLogMax; ++k) t->ntt[1][k] = t->ntt1[1][k] = INFINITY;
+    for (int f = 0; f < 1; ++f) {
+        o.path = PA_PATH_NTT31;
         for (int k = kTuneLogMin; k <= kTuneLogMax; ++k) {
             const uint64_t N = uint64_t(1) << k, M = N / 4, L = N - M;
             uint64_t tiles = std::max<uint64_t>(4, std::min<uint64_t>(1024, (uint64_t(1) << 24) >> k));
@@ -215,7 +219,7 @@ bool load_cache(Tuner *t, const char *path, const char *dev_name) {
         ok = strcmp(name, dev_name) == 0;
     }
     int version = 0;
-    ok = ok && fscanf(f, "v%d", &version) == 1 && version == 2;
+    ok = ok && fscanf(f, "v%d", &version) == 1 && version == 3;
     ok = ok && fscanf(f, "%lf %lf %lf %lf %lf %lf %lf %lf", &t->direct, &t->block[0], &t->block[1],
                       &t->block[2], &t->block_tc, &t->fft, &t->direct1, &t->block_tc1) == 8;
     for (int fl = 0; ok && fl < 2; ++fl)
@@ -230,7 +234,7 @@ bool load_cache(Tuner *t, const char *path, const char *dev_name) {
 void save_cache(const Tuner &t, const char *path, const char *dev_name) {
     FILE *f = fopen(path, "w");
     if (!f) return;
-    fprintf(f, "%s\nv2\n%.6e %.6e %.6e %.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0],
+    fprintf(f, "%s\nv3\n%.6e %.6e %.6e %.6e %.6e %.6e %.6e %.6e\n", dev_name, t.direct, t.block[0],
             t.block[1], t.block[2], t.block_tc, t.fft, t.direct1, t.block_tc1);
     for (int fl = 0; fl < 2; ++fl) {
         for (int k = 0; k <= kTuneLogMax; ++k) fprintf(f, "%.6e ", t.ntt[fl][k]);
@@ -306,6 +310,7 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                double(kTuneLogMax + 6);
     };
     for (int f = 0; f < 2; ++f) {
+        if (!(t.ntt[f][kTuneLogMax] < INFINITY)) continue;  // field not calibrated
         o.path = f == 0 ? PA_PATH_NTT31 : PA_PATH_NTT64;
         for (int k = kTuneLogMin; k <= kLogMax; ++k) {
             const uint64_t N = uint64_t(1) << k;

@@ -295,6 +295,11 @@ int block_tc_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c) {
     uint64_t chunk = round_up(ceil_div(klen * tiles, target), kTcStage);
     if (chunk < 1024) chunk = 1024;
     if (chunk > static_cast<uint64_t>(kTcMaxChunk)) chunk = kTcMaxChunk;
+    if (o && o->tile_in) {  // caller's chunk: a multiple of the stage, at most kTcMaxChunk
+        if (o->tile_in % kTcStage || o->tile_in > static_cast<uint64_t>(kTcMaxChunk))
+            return PA_ERR_INVALID;
+        chunk = o->tile_in;
+    }
     const uint64_t chunks = ceil_div(klen, chunk);
     if (tiles > 65535 || chunks > 0x7fffffffu) return PA_ERR_UNSUPPORTED;
     c->kc = chunk;

@@ -190,19 +190,30 @@ static __device__ __align__(256) uint32_t g_static_scratch[kStaticScratchWords];
 std::mutex g_static_mu;
 uint32_t *g_static_ptr[64] = {nullptr};
 
-// Device address of the array on the current device (looked up once per device).
-int static_scratch(uint32_t **out) {
+// Device address of the array on the current device. Outside stream capture it is looked
+// up on every call (cheap, and never stale: a device reset or a new primary context gives
+// the array a new address); during capture only the address cached by an earlier call on
+// this device is used, and a first call under capture is refused.
+int static_scratch(cudaStream_t s, uint32_t **out) {
     int dev = 0;
     PA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return PA_ERR_INVALID;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    PA_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        uint32_t *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_scratch);
-        if (e != cudaSuccess) return cuda_fail(e);
-        g_static_ptr[dev] = p;
+    if (cs != cudaStreamCaptureStatusNone) {
+        if (!g_static_ptr[dev]) return PA_ERR_INVALID;
+        *out = g_static_ptr[dev];
+        return PA_OK;
     }
-    *out = g_static_ptr[dev];
+    uint32_t *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_scratch);
+    if (e != cudaSuccess) {
+        g_static_ptr[dev] = nullptr;
+        return cuda_fail(e);
+    }
+    g_static_ptr[dev] = p;
+    *out = p;
     return PA_OK;
 }
 
@@ -224,12 +235,28 @@ extern "C" int pa_hash_direct_static(uint64_t n, uint64_t m, const uint64_t *see
     int rc = direct_plan(n, m, &cfg.direct);
     if (rc != PA_OK) return rc;
     if (kStaticHeaderWords + cfg.direct.key_words32_pad > kStaticScratchWords) return PA_ERR_TOO_LARGE;
-    uint32_t *scratch = nullptr;
-    rc = static_scratch(&scratch);
-    if (rc != PA_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t *scratch = nullptr;
+    rc = static_scratch(s, &scratch);
+    if (rc != PA_OK) return rc;
     // the status word must start at zero; the reversed key is fully rewritten below
     PA_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(DevHeader), s));
     return direct_launch(cfg, scratch + kStaticHeaderWords, reinterpret_cast<DevHeader *>(scratch),
                          nullptr, seed_bits, key_bits, out_bits, s);
+}
+
+extern "C" int pa_direct_static_status(void *stream) {
+    using namespace pa;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t *scratch = nullptr;
+    int rc = static_scratch(s, &scratch);
+    if (rc != PA_OK) return rc;
+    PA_CUDA_TRY(cudaStreamSynchronize(s));
+    int status = 0;
+    PA_CUDA_TRY(cudaMemcpy(&status, scratch, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        const int zero = 0;
+        PA_CUDA_TRY(cudaMemcpy(scratch, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return status;
 }

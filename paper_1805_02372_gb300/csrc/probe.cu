@@ -1,0 +1,172 @@
+// Measured issue-rate peaks for the roofline denominators of the integer paths.
+//
+// The NTT and direct kernels are bound by integer arithmetic, not by HBM, so their
+// roofline is the rate at which this GPU executes the very operations they are built
+// from. Each probe runs one of those operations, in registers, on independent chains in
+// every thread of every SM (no memory traffic, no barriers, occupancy as the real kernel),
+// and is timed with CUDA events:
+//   PA_PEAK_NTT_BUTTERFLY  the 29-bit field's lazy Gentleman-Sande butterfly (F29::dif_bfly,
+//                          the butterfly of every forward round of the NTT path);
+//   PA_PEAK_NTT_MULADD     acc += x * y in the 29-bit field (a Montgomery product and a lazy
+//                          addition: the pointwise products and transform-domain sums);
+//   PA_PEAK_SHIFT_AND      acc ^= xw & funnel_shift(lo, hi, k) (the direct kernel's step).
+// Each result is operations per second, one operation being one butterfly, one
+// multiply-add or one shift-and-accumulate.
+#include <stdint.h>
+
+#include "common.cuh"
+#include "ntt_field.cuh"
+
+namespace pa {
+namespace {
+
+constexpr int kProbeThreads = 512;
+constexpr int kChains = 8;
+
+// 2 kChains butterflies per iteration and thread.
+__global__ void __launch_bounds__(kProbeThreads, 2) probe_butterfly(uint32_t *sink, uint32_t iters,
+                                                                     F29::Tw w, uint32_t seed) {
+    uint32_t a[kChains], b[kChains];
+    const uint32_t x = seed ^ ((blockIdx.x * kProbeThreads + threadIdx.x) * 0x9E3779B9u);
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        a[c] = (x + 977u * c) & 0x0FFFFFFFu;         // < 2^28 < 4p
+        b[c] = (x * 7u + 131u * c) & 0x0FFFFFFFu;
+    }
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) F29::dif_bfly(a[c], b[c], w);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) F29::dif_bfly(b[c], a[c], w);
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) r ^= a[c] ^ b[c];
+    if (r == 0x9E3779B9u) sink[0] = r;  // keeps the chains live
+}
+
+// 2 kChains multiply-adds per iteration and thread.
+__global__ void __launch_bounds__(kProbeThreads, 2) probe_muladd(uint32_t *sink, uint32_t iters,
+                                                                  uint32_t seed) {
+    uint32_t acc[kChains], xv[kChains], yv[kChains];
+    const uint32_t x = seed ^ ((blockIdx.x * kProbeThreads + threadIdx.x) * 0x9E3779B9u);
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        acc[c] = 0;
+        xv[c] = (x + 977u * c) & 0x0FFFFFFFu;
+        yv[c] = (x * 7u + 131u * c) & 0x0FFFFFFFu;
+    }
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) acc[c] = F29::add(acc[c], F29::mont(xv[c], yv[c]));
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) xv[c] = F29::add(xv[c], F29::mont(acc[c], yv[c]));
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) r ^= acc[c] ^ xv[c];
+    if (r == 0x9E3779B9u) sink[0] = r;
+}
+
+// 32 shift-and-accumulate steps per iteration and thread (one 32 x 32 bit block of the
+// direct kernel: 32 funnel shifts and 32 AND-XORs).
+__global__ void __launch_bounds__(kProbeThreads, 2) probe_shift_and(uint32_t *sink, uint32_t iters,
+                                                                     uint32_t seed) {
+    uint32_t acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0;
+    uint32_t lo = seed ^ ((blockIdx.x * kProbeThreads + threadIdx.x) * 0x9E3779B9u);
+    uint32_t hi = lo * 0x85EBCA6Bu, xw = hi ^ 0x5BD1E995u;
+    for (uint32_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] ^= xw & __funnelshift_r(lo, hi, k);
+        const uint32_t t = lo;
+        lo = hi;
+        hi = xw;
+        xw = t + i;
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) r ^= acc[k];
+    if (r == 0x9E3779B9u) sink[0] = r;
+}
+
+// Launches probe `which` with `iters` iterations per thread; returns operations per launch.
+double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, cudaStream_t s) {
+    const double threads = double(grid) * kProbeThreads;
+    if (which == PA_PEAK_NTT_BUTTERFLY) {
+        F29::Tw w;
+        w.w = 123456789u;  // a canonical residue with its Shoup quotient
+        w.q = static_cast<uint32_t>((uint64_t(w.w) << 32) / F29::P);
+        probe_butterfly<<<grid, kProbeThreads, 0, s>>>(sink, iters, w, 0x1234567u);
+        return threads * iters * 2.0 * kChains;
+    }
+    if (which == PA_PEAK_NTT_MULADD) {
+        probe_muladd<<<grid, kProbeThreads, 0, s>>>(sink, iters, 0x1234567u);
+        return threads * iters * 2.0 * kChains;
+    }
+    probe_shift_and<<<grid, kProbeThreads, 0, s>>>(sink, iters, 0x1234567u);
+    return threads * iters * 32.0;
+}
+
+}  // namespace
+}  // namespace pa
+
+extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
+    using namespace pa;
+    if (!ops_per_s || (which != PA_PEAK_NTT_BUTTERFLY && which != PA_PEAK_NTT_MULADD &&
+                       which != PA_PEAK_SHIFT_AND))
+        return PA_ERR_INVALID;
+    int dev = 0, sms = 0, per_sm = 0;
+    PA_CUDA_TRY(cudaGetDevice(&dev));
+    PA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const void *fn = which == PA_PEAK_NTT_BUTTERFLY ? reinterpret_cast<const void *>(probe_butterfly)
+                     : which == PA_PEAK_NTT_MULADD  ? reinterpret_cast<const void *>(probe_muladd)
+                                                    : reinterpret_cast<const void *>(probe_shift_and);
+    PA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kProbeThreads, 0));
+    const unsigned grid = static_cast<unsigned>((per_sm > 0 ? per_sm : 1) * sms);
+    uint32_t *sink = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 256);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    double best = 0.0, best_ms = 0.0;
+    if (e == cudaSuccess) {
+        // size the launch to about 20 ms from a short one, then take the fastest of three
+        uint32_t iters = 256;
+        float t = 0.f;
+        for (int r = 0; r < 2 && e == cudaSuccess; ++r) {  // warm-up and sizing
+            cudaEventRecord(a, s);
+            probe_launch(which, iters, grid, sink, s);
+            cudaEventRecord(b, s);
+            e = cudaEventSynchronize(b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        }
+        if (e == cudaSuccess && t > 0.f) {
+            double scaled = double(iters) * 20.0 / double(t);
+            iters = static_cast<uint32_t>(scaled < 256.0 ? 256.0 : (scaled > 4.0e6 ? 4.0e6 : scaled));
+        }
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            cudaEventRecord(a, s);
+            const double ops = probe_launch(which, iters, grid, sink, s);
+            cudaEventRecord(b, s);
+            e = cudaEventSynchronize(b);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+            if (e == cudaSuccess && t > 0.f && ops / (t * 1e-3) > best) {
+                best = ops / (t * 1e-3);
+                best_ms = t;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(sink);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *ops_per_s = best;
+    if (ms) *ms = best_ms;
+    return PA_OK;
+}

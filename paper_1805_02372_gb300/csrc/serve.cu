@@ -10,6 +10,7 @@
 // per wave; poll returns finished requests with their tags.
 #include <string.h>
 
+#include <chrono>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -38,6 +39,8 @@ struct pa_server_s {
     std::vector<Wave> slots;  // one (possibly empty) wave per slot
     size_t bytes_in_flight = 0;
     uint64_t waves_launched = 0, requests_done = 0;
+    double plan_s_total = 0, plan_s_max = 0;  // host time of launch_wave per launched wave
+    uint64_t held_back = 0;                   // waves held back by the memory budget
 };
 
 using namespace pa;
@@ -46,8 +49,23 @@ namespace {
 
 bool slot_busy(const Wave &w) { return w.batch != nullptr; }
 
-// Launch one wave on slot i from the head of the queue. Called with the lock held.
+int launch_wave_impl(pa_server_s *s, size_t i);
+
+// Launch one wave on slot i from the head of the queue. Called with the lock held. Records
+// the host time it took (planning, workspace, upload, launch) for pa_server_get_stats.
 int launch_wave(pa_server_s *s, size_t i) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const uint64_t before = s->waves_launched;
+    const int rc = launch_wave_impl(s, i);
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (s->waves_launched != before) {
+        s->plan_s_total += dt;
+        if (dt > s->plan_s_max) s->plan_s_max = dt;
+    }
+    return rc;
+}
+
+int launch_wave_impl(pa_server_s *s, size_t i) {
     std::vector<pa_block> blocks;
     std::vector<uint64_t> tags;
     const size_t cap = s->opts.max_blocks_per_wave ? s->opts.max_blocks_per_wave : 64;
@@ -72,6 +90,7 @@ int launch_wave(pa_server_s *s, size_t i) {
         s->bytes_in_flight + w.bytes > s->opts.memory_budget_bytes) {
         batch_destroy_impl(b);
         for (size_t k = blocks.size(); k-- > 0;) s->queue.push_front({blocks[k], tags[k]});
+        ++s->held_back;
         return PA_OK;
     }
     cudaError_t e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
@@ -186,6 +205,18 @@ int pa_server_pending(pa_server_t s, uint64_t *queued, uint64_t *in_flight) {
     uint64_t f = 0;
     for (const Wave &w : s->slots) f += w.tags.size();
     if (in_flight) *in_flight = f;
+    return PA_OK;
+}
+
+int pa_server_get_stats(pa_server_t s, pa_server_stats *out) {
+    if (!s || !out) return PA_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof(*out));
+    out->waves = s->waves_launched;
+    out->requests_done = s->requests_done;
+    out->plan_s_total = s->plan_s_total;
+    out->plan_s_max = s->plan_s_max;
+    out->waves_held_back = s->held_back;
     return PA_OK;
 }
 

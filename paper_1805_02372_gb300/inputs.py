@@ -58,6 +58,14 @@ def random_bits(nbits: int, stream: int) -> np.ndarray:
     return splitmix64(stream, max(words_for(nbits), 1))
 
 
+def biased_bits(nbits: int, stream: int, density: float) -> np.ndarray:
+    """``ceil(nbits/64)`` packed words whose bits are 1 with probability ``density``
+    (bit j is 1 when output j+1 of the stream, as a double in [0, 1), is below it)."""
+    nw = max(words_for(nbits), 1)
+    ones = uniform01(stream, nw * 64) < density
+    return np.packbits(ones.astype(np.uint8), bitorder="little").view("<u8").astype(np.uint64)
+
+
 def sub_stream(master: int, index: int) -> int:
     """A per-item stream id derived from a master stream (output 1000+index)."""
     return int(splitmix64(master, 1, start=1000 + index)[0])

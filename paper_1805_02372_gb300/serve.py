@@ -39,10 +39,18 @@ def make_requests(count: int, rate_hz: float, device="cuda", master: int = input
     return reqs
 
 
+def at_rate(reqs, rate_hz: float, made_at_hz: float):
+    """The same requests (same buffers and shapes) with their Poisson arrival times
+    rescaled from the rate they were drawn at to ``rate_hz``."""
+    k = made_at_hz / rate_hz
+    return [Request(r.arrival * k, r.block, r.key, r.seed, r.out) for r in reqs]
+
+
 def replay(reqs, slots: int = 2, max_blocks_per_wave: int = 64, memory_budget_bytes: int = 0,
            timeout_s: float = 120.0) -> dict:
     """Submit each request at its arrival time; poll until all complete."""
     srv = binding.pa_server_create(slots, max_blocks_per_wave, memory_budget_bytes)
+    stats = None
     try:
         t0 = time.perf_counter()
         nxt = 0
@@ -59,13 +67,22 @@ def replay(reqs, slots: int = 2, max_blocks_per_wave: int = 64, memory_budget_by
                 left -= 1
             if now > timeout_s:
                 raise TimeoutError(f"{left} requests unfinished after {timeout_s} s")
+        stats = binding.pa_server_get_stats(srv)
     finally:
         binding.pa_server_destroy(srv)
     lat = np.array([(r.done - r.arrival) * 1e3 for r in reqs])
     span = max(r.done for r in reqs) - reqs[0].arrival
     bits = sum(r.block.n for r in reqs)
     offered = bits / max(reqs[-1].arrival - reqs[0].arrival, 1e-9)
+    q = max(1, len(reqs) // 4)
+    waves = max(1, stats["waves"])
     return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
             "sustained_gbps": bits / span / 1e9, "offered_gbps": offered / 1e9,
-            "errors": sum(1 for r in reqs if r.status != 0)}
+            "errors": sum(1 for r in reqs if r.status != 0),
+            # latency drift: median of the last quarter of arrivals over the first quarter's
+            # (well above 1 when the queue grows, i.e. past saturation)
+            "latency_drift": float(np.median(lat[-q:]) / max(np.median(lat[:q]), 1e-9)),
+            "waves": stats["waves"], "waves_held_back": stats["waves_held_back"],
+            "host_plan_ms_per_wave": stats["plan_s_total"] / waves * 1e3,
+            "host_plan_ms_max": stats["plan_s_max"] * 1e3}

@@ -21,17 +21,40 @@ def _descs(path, blocks, **extra):
                   "fd": 2, "windows": 2}, **extra) for _ in blocks]
 
 
+PROBE = {"butterfly_per_s": 5e12, "muladd_per_s": 4e12, "shift_and_per_s": 9e12}
+
+
 def test_roofline_batch_persistent_fields():
     blocks = inputs.batched_blocks()[:4]
     kt = {"batch_persistent": {"launches": 10, "total_ms": 20.0}, "memset": {"launches": 10, "total_ms": 0.1}}
-    r = bench.roofline(kt, blocks, _descs("ntt31", blocks), steps=10, workload_name="batched4")
+    descs = _descs("ntt31", blocks)
+    r = bench.roofline(kt, blocks, descs, steps=10, workload_name="batched4", probe=PROBE)
     assert r["kernel"] == "batch_persistent" and r["bound"] == "alu" and r["unit"] == "Tops/s"
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     # achieved = model ops per launch / launch time; one launch per step here
-    ops = bench._ntt_ops(_descs("ntt31", blocks))
-    assert r["achieved"] == pytest.approx(ops / 2e-3 / 1e12)
+    bfly, prod = bench.ntt_work(descs)
+    assert r["achieved"] == pytest.approx(bench.OPS_PER_BFLY * (bfly + prod) / 2e-3 / 1e12)
+    # the fraction is the time the work takes at the measured peaks over the launch time
+    t_peak = bfly / PROBE["butterfly_per_s"] + prod / PROBE["muladd_per_s"]
+    assert r["frac"] == pytest.approx(t_peak / 2e-3)
+    assert "measured in this run" in r["peak_source"]
     assert r["traffic"] is None  # no committed figure for this workload
     assert 0 < r["hbm_compulsory"]["frac"] < 1
+
+
+def test_roofline_without_probe_reports_no_fraction():
+    blocks = inputs.batched_blocks()[:2]
+    kt = {"batch_persistent": {"launches": 2, "total_ms": 2.0}}
+    r = bench.roofline(kt, blocks, _descs("ntt31", blocks), steps=2, workload_name="x")
+    assert "frac" not in r and r["hbm_compulsory"]["frac"] > 0
+
+
+def test_roofline_direct_against_shift_and_peak():
+    b = inputs.single_block(1_000_000, 500_000)
+    kt = {"direct": {"launches": 4, "total_ms": 8.0}}
+    r = bench.roofline(kt, [b], _descs("direct", [b]), steps=4, workload_name="x", probe=PROBE)
+    ops = b.m * b.n / 32.0
+    assert r["frac"] == pytest.approx(ops / PROBE["shift_and_per_s"] / 2e-3)
 
 
 def test_roofline_block_tc_tensor_bound():
@@ -55,10 +78,20 @@ def test_traffic_lookup_matches_digest_and_workload():
         assert bench.traffic_for(kernel, "another workload") is None
 
 
-def test_cpu_baseline_sample_is_bounded():
+def test_cpu_baseline_times_whole_blocks():
     blocks = [inputs.single_block(20_000, 5_000, 5, 6), inputs.single_block(3_001, 700, 7, 8)]
-    g, cores, desc = bench.cpu_oracle_gbps(blocks, rows_per_block=64, max_blocks=2)
-    assert g > 0 and cores >= 1 and "2 of 2 blocks" in desc
+    g, k, t, bits, th = bench.cpu_oracle_measured(blocks, budget_s=60.0)
+    assert k == 2 and bits == 23_001 and t > 0 and th >= 1
+    assert g == pytest.approx(bits / t / 1e9)
+    # the budget bounds the sample: with none left after the first block, one block is timed
+    g1, k1, _, bits1, _ = bench.cpu_oracle_measured(blocks, budget_s=0.0, threads=1, order=[1, 0])
+    assert k1 == 1 and bits1 == 3_001 and g1 > 0
+
+
+def test_golden_digests_for_batched_prefixes():
+    d = bench.golden_digests("batched8")
+    assert d is not None and len(d) == 8 and all(len(x) == 64 for x in d)
+    assert bench.golden_digests("plain_single") is None
 
 
 def test_workloads_named_by_shape():
@@ -69,12 +102,17 @@ def test_workloads_named_by_shape():
         assert blocks and cfg["blocks"] == len(blocks) and cfg["workload"]
 
 
-def test_ntt_ops_counts_one_inverse_per_sum():
+def test_ntt_work_counts_one_inverse_per_sum():
     # accumulated block: (Q + W + G P) transforms of (N/2) log2 N butterflies plus P Q N
-    # summed products, 8 ops each
+    # summed products
     d = {"path_name": "ntt31", "log2_transform": 23, "tiles_in": 239, "tiles_out": 24,
          "fd": 1, "windows": 262, "sum_groups": 3}
     N = 2.0 ** 23
-    want = 8.0 * ((239 + 262 + 3 * 24) * (N / 2) * 23 + 24 * 239 * N)
-    assert bench._ntt_ops([d]) == pytest.approx(want)
-    assert bench._ntt_ops([dict(d, sum_groups=1)]) < want
+    bfly, prod = bench.ntt_work([d])
+    assert bfly == pytest.approx((239 + 262 + 3 * 24) * (N / 2) * 23)
+    assert prod == pytest.approx(24 * 239 * N)
+    assert bench.ntt_work([dict(d, sum_groups=1)])[0] < bfly
+    # a standard tile pair: two forward transforms, one inverse, N pointwise products
+    p = {"path_name": "ntt31", "log2_transform": 20, "tiles_in": 3, "tiles_out": 2, "fd": 0,
+         "windows": 0}
+    assert bench.ntt_work([p]) == pytest.approx((6 * 3 * (2.0 ** 19) * 20, 6 * 2.0 ** 20))

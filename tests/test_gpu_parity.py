@@ -186,6 +186,36 @@ def test_block_fp8_full_chunks_all_ones(n, m):
         assert int(got[-1]) >> (m % 64) == 0
 
 
+@pytest.mark.parametrize("chunk", [8192, 16384, 32768])
+@pytest.mark.parametrize("density", [0.97, 0.6])
+def test_block_fp8_dense_full_chunks(chunk, density):
+    # Where the exactness of the tensor-core sums is tight: an all-ones key and a dense seed,
+    # so a CTA's count over a full chunk is about density x chunk, with random parity. At a
+    # chunk of 2^15 positions the counts lie in [2^14, 2^15) (densities 0.97 and 0.6), i.e.
+    # the FP32 accumulator holds count x 2^-12 in [4, 8) and needs all 15 significant bits
+    # of the count; a coarser internal accumulation would drop the low bit of odd counts.
+    # The whole output is compared with the oracle.
+    n, m = 4 * chunk + 12_345, 2 * 32_768 + 777
+    key = np.full((n + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    seed = inputs.biased_bits(n + m - 1, 4000 + chunk // 128 + int(density * 100), density)
+    want = oracle.hash_full(n, m, seed, key)
+    desc = pkg.pa_plan_query(n, m, binding.make_opts(path="block_fp8", tile_in=chunk))
+    assert desc["path_name"] == "block_fp8" and desc["tile_in"] == chunk, desc
+    import torch
+    plan = pkg.Plan(n, m, path="block_fp8", tile_in=chunk)
+    out = torch.full(((m + 63) // 64,), -1, dtype=torch.int64, device="cuda")
+    plan.hash(dev(seed), dev(key), out)
+    torch.cuda.synchronize()
+    res, bound = plan.residual()
+    st = plan.status()
+    plan.close()
+    got = host(out)
+    bad = np.flatnonzero(got != want)
+    assert st == 0 and bad.size == 0, (f"chunk {chunk} density {density}: {bad.size} words "
+                                       f"differ (status {st})")
+    assert res == 0.0 and bound == 0.0
+
+
 def test_paper_scale_block_sampled_rows():
     # One block at the paper's upper range (Fig. 3: keys of 1e9 bits and more, l = 10%):
     # n = 1e9 + 7, m = 1e8 through the autotuned plan (the 31-bit prime: counts reach n),
