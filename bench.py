@@ -72,6 +72,10 @@ def workload(name: str):
         # a 3 Gbit key (Fig. 3 runs to 1e10 bits), l = 10%
         b = inputs.single_block(3_000_000_019, 300_000_000, 33, 34)
         return [b], {"workload": f"paper scale n={b.n} m={b.m}", "blocks": 1}
+    if name == "paper_scale_1e10":
+        # the top of Fig. 3's range, l = 10%: segmented sums in a fixed workspace
+        b = inputs.single_block(10_000_000_019, 1_000_000_000, 35, 36)
+        return [b], {"workload": f"paper scale n={b.n} m={b.m}", "blocks": 1}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -288,8 +292,11 @@ def ntt_work(descs):
         N = 2.0 ** k
         P, Q = d["tiles_out"], d["tiles_in"]
         if d.get("fd"):
+            # segmented sums recompute the key spectra once per output slice; `windows` and
+            # `sum_groups` count every segment's
             G = d.get("sum_groups") or 1
-            bfly += (Q + d["windows"] + G * P) * (N / 2) * k
+            keys = Q * -(-P // (d.get("seg_out") or P))
+            bfly += (keys + d["windows"] + G * P) * (N / 2) * k
             prod += P * Q * N
         else:
             bfly += P * Q * 3 * (N / 2) * k

@@ -90,7 +90,12 @@ typedef struct {
     uint32_t fd_group;         /* transform-domain sums: at most this many key sub-blocks
                                   per sum; 0 = the prime's exactness limit (p-1)/L. Like
                                   fd_mode it also binds an autotuned batch's NTT blocks  */
-    uint32_t reserved[3];
+    uint32_t seg_in;           /* transform-domain sums run in segments (the paper's blocks
+                                  run serially through a fixed workspace, Sec. 3): key
+                                  sub-blocks per segment; 0 = automatic (segments only when
+                                  the resident spectra would exceed 96 GiB)               */
+    uint32_t seg_out;          /* segments: output sub-blocks per slice; 0 = automatic     */
+    uint32_t seg_cap_gib;      /* segments: GiB of spectra one segment may hold; 0 = 32    */
 } pa_opts;
 
 /* What a plan decided (pa_plan_query / pa_plan_describe). */
@@ -112,6 +117,9 @@ typedef struct {
     uint64_t windows;          /* with fd: seed-window spectra computed (distinct offsets) */
     uint32_t prime_bits;       /* NTT paths: bits of the prime (29, 31 or 64), else 0     */
     uint32_t sum_groups;       /* with fd: transform-domain sums per output sub-block     */
+    uint32_t seg_in;           /* segmented fd: key sub-blocks per segment, else 0        */
+    uint32_t seg_out;          /* segmented fd: output sub-blocks per slice, else 0       */
+    uint64_t segments;         /* segmented fd: launches run in order (slices x segments) */
 } pa_plan_desc;
 
 typedef struct pa_plan_s *pa_plan_t;

@@ -1,5 +1,6 @@
 // C ABI of the Toeplitz-hash library: planning, single-block hashing, status.
 // Every entry point returns a pa_status; no exception crosses the interface.
+#include <algorithm>
 #include <new>
 #include <string.h>
 
@@ -50,7 +51,8 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
             rc = ntt_plan(n, m, path, o, &cfg->tr);
             if (rc == PA_OK) rc = ntt_layout(n, m, path, &cfg->tr);
             cfg->ws_bytes = cfg->tr.lay.bytes;
-            cfg->kernels = 2;  // output zeroing + the persistent launch
+            // output zeroing + the persistent launch (one per segment when segmented)
+            cfg->kernels = 1 + static_cast<uint32_t>(std::max<size_t>(1, cfg->tr.segs.size()));
             break;
         case PA_PATH_FFT:
             rc = fft_plan(n, m, o, &cfg->tr);
@@ -108,6 +110,14 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->sum_groups = cfg.tr.fd == 1 && cfg.tr.kgroup
                             ? static_cast<uint32_t>(ceil_div(cfg.tr.tiles_in, cfg.tr.kgroup))
                             : (cfg.tr.fd ? 1u : 0u);
+        if (!cfg.tr.segs.empty()) {
+            // every key segment has its own sums (one per kgroup key tiles of the segment)
+            const uint64_t Sk = ceil_div(cfg.tr.tiles_in, cfg.tr.seg_in);
+            d->sum_groups = static_cast<uint32_t>(Sk * ceil_div(cfg.tr.seg_in, cfg.tr.kgroup));
+            d->seg_in = cfg.tr.seg_in;
+            d->seg_out = cfg.tr.seg_out;
+            d->segments = cfg.tr.segs.size();
+        }
         if (cfg.path == PA_PATH_NTT31 || cfg.path == PA_PATH_NTT64)
             d->prime_bits = cfg.tr.field == kFieldF64 ? 64 : (cfg.tr.field == kFieldF29 ? 29 : 31);
     }

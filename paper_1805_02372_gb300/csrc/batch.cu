@@ -323,9 +323,10 @@ double best_path(uint64_t n, uint64_t m, const Tuner &t, bool batched, pa_opts *
                 if (L > round_up(n, 32)) L = round_up(n, 32);
                 uint32_t fd = 0, kgroup = 0;
                 uint64_t windows = 0;
+                SegChoice seg;  // beyond the resident cap: segmented sums, default sizes
                 const double units = ntt_geometry_cost(n, m, f == 0 ? kFieldF29 : kFieldF64,
                                                        static_cast<uint32_t>(k), M, L, fd_mode, fd_group,
-                                                       &fd, &windows, &kgroup);
+                                                       &fd, &windows, &kgroup, &seg);
                 const double launches = batched ? 0.0 : 2.0;
                 o.log2_transform = static_cast<uint32_t>(k);
                 o.tile_out = M;
@@ -412,6 +413,13 @@ namespace {
 
 DevHeader *batch_hdr(pa_batch_s *b) { return static_cast<DevHeader *>(b->mem); }
 
+// Blocks whose transforms run in the shared persistent launch of their prime field (a
+// segmented block runs its own sequence of launches, one per segment, over its own
+// workspace).
+bool in_persistent(const PlanCfg &c) {
+    return (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64) && c.tr.segs.empty();
+}
+
 int enqueue_all(pa_batch_s *b, cudaStream_t s) {
     char *base = static_cast<char *>(b->mem);
     const BlockPtrs *dblks = reinterpret_cast<const BlockPtrs *>(base + b->off_blks);
@@ -429,7 +437,7 @@ int enqueue_all(pa_batch_s *b, cudaStream_t s) {
     }
     for (size_t i = 0; i < b->cfg.size(); ++i) {
         const PlanCfg &c = b->cfg[i];
-        if (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64) continue;
+        if (in_persistent(c)) continue;
         const BlockPtrs &p = b->hblks[i];
         const uint64_t *seed = reinterpret_cast<const uint64_t *>(p.seed32);
         const uint64_t *key = reinterpret_cast<const uint64_t *>(p.key32);
@@ -438,6 +446,8 @@ int enqueue_all(pa_batch_s *b, cudaStream_t s) {
         int rc = PA_OK;
         if (c.path == PA_PATH_DIRECT) rc = direct_launch(c, ws, hdr, prof, seed, key, out, s);
         else if (c.path == PA_PATH_FFT) rc = fft_launch(c, ws, hdr, prof, seed, key, out, s);
+        else if (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64)  // segmented block
+            rc = ntt_launch(c, ws, hdr, prof, seed, key, out, s);
         else rc = block_launch(c, ws, hdr, prof, seed, key, out, s);
         if (rc != PA_OK) return rc;
     }
@@ -507,7 +517,7 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         }
         const PlanCfg &c = b->cfg[i];
         b->per_path[c.path] += 1;
-        if (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64) {
+        if (in_persistent(c)) {
             const int f = c.tr.field;
             BatchBlock bb;
             bb.index = static_cast<uint32_t>(i);
@@ -520,9 +530,15 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
             b->ws_off[i] = off;
             off = round_up(off + c.ws_bytes, 256);
             b->work_items += c.path == PA_PATH_FFT ? c.tr.tiles_in * c.tr.tiles_out
-                                                   : (c.path == PA_PATH_DIRECT
-                                                          ? uint64_t(c.direct.grid_x) * c.direct.grid_y
-                                                          : uint64_t(c.blk.grid_x) * c.blk.grid_y);
+                             : c.path == PA_PATH_DIRECT
+                                 ? uint64_t(c.direct.grid_x) * c.direct.grid_y
+                                 : (c.path == PA_PATH_NTT31 || c.path == PA_PATH_NTT64)
+                                       ? [&c] {
+                                             uint64_t w = 0;
+                                             for (const NttLayout &l : c.tr.segs) w += l.nitems;
+                                             return w;
+                                         }()
+                                       : uint64_t(c.blk.grid_x) * c.blk.grid_y;
             if (c.path == PA_PATH_FFT) b->bound = std::max(b->bound, c.tr.bound);
         }
     }
@@ -556,6 +572,19 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
     for (int f = 0; f < kNumFields; ++f) {
         if (b->in_ntt[f].empty()) continue;
         int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f], as);
+        if (rc != PA_OK) {
+            batch_free(b);
+            delete b;
+            return rc;
+        }
+    }
+    // segmented NTT blocks: their work lists go into their own workspace now (synchronous
+    // copies, after the stream-ordered allocation has happened)
+    for (size_t i = 0; i < count; ++i) {
+        const PlanCfg &c = b->cfg[i];
+        if ((c.path != PA_PATH_NTT31 && c.path != PA_PATH_NTT64) || in_persistent(c)) continue;
+        if (as) PA_CUDA_TRY(cudaStreamSynchronize(as));
+        int rc = ntt_init(c, static_cast<char *>(b->mem) + b->ws_off[i]);
         if (rc != PA_OK) {
             batch_free(b);
             delete b;
@@ -667,8 +696,7 @@ int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *strea
         BlockPtrs &h = b->hblks[i];
         if (h.key32 != p.key32 || h.seed32 != p.seed32 || h.out32 != p.out32) {
             changed_any = true;
-            const int path = b->cfg[i].path;
-            if (path != PA_PATH_NTT31 && path != PA_PATH_NTT64) changed_other = true;
+            if (!in_persistent(b->cfg[i])) changed_other = true;
             h = p;
         }
     }

@@ -54,7 +54,14 @@ struct TransformCfg {
     uint64_t windows = 0;        // NTT with fd: distinct seed-window spectra
     uint32_t kgroup = 0;         // NTT with fd = 1: key tiles per transform-domain sum (the
                                  // counts of a sum stay below the prime); 0 = all of them
-    NttLayout lay;               // NTT single-block plans: their persistent launch
+    uint32_t seg_in = 0;         // NTT with fd = 1, segmented: key tiles per segment and
+    uint32_t seg_out = 0;        // output tiles per slice (0 = everything resident at once);
+                                 // each (slice, segment) is one persistent launch over one
+                                 // shared spectra workspace, run in order
+    NttLayout lay;               // NTT single-block plans: their persistent launch (segmented:
+                                 // lay.bytes is the whole workspace)
+    std::vector<NttLayout> segs; // segmented plans: one launch layout per (slice, segment)
+    std::vector<size_t> seg_base;  // workspace offset of each segment's tables
 };
 
 // ---- block-Toeplitz tensor-core path ----
@@ -145,9 +152,17 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
 // Modelled cost of a tile geometry over prime field `field` in units of one standard tile
 // pair of size 2^k (+inf if invalid); *fd / *windows / *kgroup: whether transform-domain
 // accumulation is used, its window spectra and key tiles per sum (fd_group > 0 caps it).
+// Geometries whose resident spectra exceed the accumulation cap run segmented (*seg_in key
+// tiles per segment, *seg_out output tiles per slice) within seg_cap bytes of spectra;
+// seg_in_force / seg_out_force fix the segment sizes (0 = choose).
+struct SegChoice {
+    uint64_t seg_cap = 0;          // bytes of spectra a segmented plan may hold (0 = default)
+    uint32_t seg_in_force = 0, seg_out_force = 0;
+    uint32_t seg_in = 0, seg_out = 0;  // out: the choice (0 = not segmented)
+};
 double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t M, uint64_t L,
                          uint32_t fd_mode, uint32_t fd_group, uint32_t *fd, uint64_t *windows,
-                         uint32_t *kgroup);
+                         uint32_t *kgroup, SegChoice *seg = nullptr);
 // Lays out the single-block plan's persistent launch (fills c->lay; host only).
 int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c);
 int ntt_init(const PlanCfg &cfg, void *ws);  // uploads the work list, builds root tables
@@ -170,6 +185,9 @@ struct BatchBlock {
     uint32_t index;        // position in the batch (BlockPtrs table index)
     uint64_t n, m;
     TransformCfg tr;
+    // fd blocks: the output tiles [I0, I1) and key tiles [J0, J1) this work list covers
+    // (I1 = J1 = 0: all of them); a segment of a segmented plan
+    uint64_t I0 = 0, I1 = 0, J0 = 0, J1 = 0;
 };
 struct NttBatchInfo : NttLayout {
     std::vector<unsigned char> host_tiles, host_fd;

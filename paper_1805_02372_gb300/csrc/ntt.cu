@@ -240,10 +240,11 @@ uint64_t tile_in_for(uint64_t n, uint32_t logn, uint64_t M, uint64_t Lforce) {
 // so it needs every key tile in one sum.
 double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t M, uint64_t L,
                          uint32_t fd_mode, uint32_t fd_group, uint32_t *fd, uint64_t *windows,
-                         uint32_t *kgroup) {
+                         uint32_t *kgroup, SegChoice *seg) {
     *fd = 0;
     *windows = 0;
     *kgroup = 0;
+    if (seg) seg->seg_in = seg->seg_out = 0;
     if (k > static_cast<uint32_t>(kLogMax) || M == 0 || L == 0 || L + M > (uint64_t(1) << k))
         return INFINITY;
     const double N = double(uint64_t(1) << k);
@@ -277,17 +278,48 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
         }
         return std_units;
     }
+    const bool forced_seg = seg && (seg->seg_in_force || seg->seg_out_force);
     const uint64_t W = count_windows(P, Q, M, L);
-    if (double(Q + W + G * P) * N * elem > double(kFdMaxBytes)) return std_units;
-    const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(G * P) * (tr + N + 1024.0) +
-                       double(P) * double(Q) * 3.0 * N;
-    if (fd_mode == 2 || big || fdc < 0.85 * std_units * pair) {
-        *fd = 1;
-        *windows = W;
-        *kgroup = static_cast<uint32_t>(g);
-        return fdc / pair;
+    if (!forced_seg && double(Q + W + G * P) * N * elem <= double(kFdMaxBytes)) {
+        const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(G * P) * (tr + N + 1024.0) +
+                           double(P) * double(Q) * 3.0 * N;
+        if (fd_mode == 2 || big || fdc < 0.85 * std_units * pair) {
+            *fd = 1;
+            *windows = W;
+            *kgroup = static_cast<uint32_t>(g);
+            return fdc / pair;
+        }
+        return std_units;
     }
-    return std_units;
+    if (!seg || fd_mode == 1) return std_units;
+    // Segmented (the length-compatible scheme's blocks run serially through a fixed
+    // workspace): key tiles in segments of si (one sum per output tile when si <= g),
+    // output tiles in slices of so; each (slice, segment) holds its si key spectra, its
+    // windows and its sums, and XORs its output bits into y (Eq. finalkey). The default
+    // takes every output tile and one sum's worth of key tiles, then halves the slice and
+    // the segment until the spectra fit the cap.
+    const uint64_t cap = seg->seg_cap ? seg->seg_cap : kSegMaxBytes;
+    uint64_t si = seg->seg_in_force ? std::min<uint64_t>(seg->seg_in_force, Q) : std::min<uint64_t>(g, Q);
+    uint64_t so = seg->seg_out_force ? std::min<uint64_t>(seg->seg_out_force, P) : P;
+    const auto seg_bytes = [&](uint64_t a, uint64_t b) {
+        const uint64_t ws = count_windows(b, a, M, L), gs = ceil_div(a, g);
+        return double(a + ws + gs * b) * N * elem;
+    };
+    while (seg_bytes(si, so) > double(cap) && !seg->seg_out_force && so > 1) so = ceil_div(so, 2);
+    while (seg_bytes(si, so) > double(cap) && !seg->seg_in_force && si > 1) si = ceil_div(si, 2);
+    if (seg_bytes(si, so) > double(cap)) return std_units;
+    const uint64_t So = ceil_div(P, so), Sk = ceil_div(Q, si);
+    if (So * Sk > kSegMax) return std_units;
+    const uint64_t ws = count_windows(so, si, M, L), gs = ceil_div(si, g);
+    const double segc = double(So * Sk) * (double(si + ws) * (tr + 2 * N + 1024.0) +
+                                           double(gs * so) * (tr + N + 1024.0) + 4.0 * N) +
+                        double(P) * double(Q) * 3.0 * N;
+    *fd = 1;
+    *windows = ws * So * Sk;
+    *kgroup = static_cast<uint32_t>(g);
+    seg->seg_in = static_cast<uint32_t>(si);
+    seg->seg_out = static_cast<uint32_t>(so);
+    return segc / pair;
 }
 
 int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c) {
@@ -310,8 +342,12 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
     const uint32_t fd_group = o ? o->fd_group : 0;
     const uint32_t force = o ? o->log2_transform : 0;
     const uint64_t Mforce = o ? o->tile_out : 0, Lforce = o ? o->tile_in : 0;
+    SegChoice seg;
+    seg.seg_cap = o ? uint64_t(o->seg_cap_gib) << 30 : 0;
+    seg.seg_in_force = o ? o->seg_in : 0;
+    seg.seg_out_force = o ? o->seg_out : 0;
     double best_cost = INFINITY;
-    uint32_t bk = 0, bfd = 0, bg = 0;
+    uint32_t bk = 0, bfd = 0, bg = 0, bsi = 0, bso = 0;
     uint64_t bL = 0, bM = 0, bW = 0;
     for (uint32_t k = 5; k <= static_cast<uint32_t>(kLogMax); ++k) {
         if (force && k != force) continue;
@@ -332,7 +368,8 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
             if (L == 0) continue;
             uint32_t fd = 0, g = 0;
             uint64_t W = 0;
-            const double units = ntt_geometry_cost(n, m, field, k, M, L, fd_mode, fd_group, &fd, &W, &g);
+            const double units =
+                ntt_geometry_cost(n, m, field, k, M, L, fd_mode, fd_group, &fd, &W, &g, &seg);
             const double cost = units * (double(N) * (k + 6) + 4096.0);
             if (cost < best_cost) {
                 best_cost = cost;
@@ -342,6 +379,8 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
                 bfd = fd;
                 bW = W;
                 bg = g;
+                bsi = seg.seg_in;
+                bso = seg.seg_out;
             }
         }
     }
@@ -355,6 +394,8 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
     c->fd = bfd;
     c->windows = bfd ? bW : 0;
     c->kgroup = bfd == 1 ? bg : 0;
+    c->seg_in = bfd == 1 ? bsi : 0;
+    c->seg_out = bfd == 1 ? bso : 0;
     if (bk <= static_cast<uint32_t>(kLogSmallMax)) {
         c->passes = 1;
         c->radix_log2[0] = bk;
@@ -403,20 +444,24 @@ NttTile tile_shape(uint32_t logN, int field) {
     return t;
 }
 
-// The fd spectra and sums of one block: Q key spectra, W window spectra, P sums, with
-// element offsets relative to the start of the block's fd storage.
+// The fd spectra and sums of one block, or of one segment of it (output tiles [I0, I1),
+// key tiles [J0, J1) of the BatchBlock): Q key spectra, W window spectra, P sums (P, Q
+// and every index below local to the segment), with element offsets relative to the start
+// of the block's fd storage.
 void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<NttTile> *spectra,
               std::vector<NttTile> *sums, FdBlock *fb, std::vector<uint32_t> *wmap,
               uint64_t *elems) {
     const TransformCfg &c = b.tr;
-    const uint64_t P = c.tiles_out, Q = c.tiles_in, N = uint64_t(1) << c.log2n;
+    const uint64_t I0 = b.I0, I1 = b.I1 ? b.I1 : c.tiles_out;
+    const uint64_t J0 = b.J0, J1 = b.J1 ? b.J1 : c.tiles_in;
+    const uint64_t P = I1 - I0, Q = J1 - J0, N = uint64_t(1) << c.log2n;
     std::vector<TilePair> pairs;
-    make_pairs(b.n, b.m, c, b.index, &pairs);
+    make_pairs(b.n, b.m, c, b.index, &pairs, I0, I1, J0, J1);
     // distinct offsets d = I*M - J*L, each with a representative pair
     std::vector<std::pair<int64_t, uint64_t>> d(P * Q);
     for (uint64_t I = 0; I < P; ++I)
         for (uint64_t J = 0; J < Q; ++J)
-            d[I * Q + J] = {int64_t(I * c.M) - int64_t(J * c.L), I * Q + J};
+            d[I * Q + J] = {int64_t((I0 + I) * c.M) - int64_t((J0 + J) * c.L), I * Q + J};
     std::vector<std::pair<int64_t, uint64_t>> u = d;
     std::sort(u.begin(), u.end());
     u.erase(std::unique(u.begin(), u.end(),
@@ -513,8 +558,10 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
             (b.tr.log2n > static_cast<uint32_t>(kLogMaxStd) && b.tr.fd != 1))
             return PA_ERR_INVALID;
         if (b.tr.fd) {
-            if (b.tr.log2n <= static_cast<uint32_t>(kLogSmallMax) ||
-                b.tr.tiles_in * b.tr.tiles_out > kFdMaxPairs || b.tr.fd > 2 ||
+            const uint64_t lp = (b.I1 ? b.I1 : b.tr.tiles_out) - b.I0;
+            const uint64_t lq = (b.J1 ? b.J1 : b.tr.tiles_in) - b.J0;
+            if (b.tr.log2n <= static_cast<uint32_t>(kLogSmallMax) || lp * lq > kFdMaxPairs ||
+                b.tr.fd > 2 ||
                 (b.tr.fd == 2 && b.tr.tiles_out != 1))
                 return PA_ERR_INVALID;
             const bool streamed = b.tr.fd == 2;
@@ -719,7 +766,59 @@ int ntt_batch_upload(const NttBatchInfo &info, void *ws, cudaStream_t s) {
     return upload(info, ws, s, false);
 }
 
+namespace {
+
+// Work list of segment `idx` of a segmented plan: output slice idx / Sk, key segment
+// idx % Sk (Sk key segments per slice).
+int seg_build(uint64_t n, uint64_t m, const TransformCfg &c, uint64_t idx, NttBatchInfo *info) {
+    const uint64_t Sk = ceil_div(c.tiles_in, c.seg_in);
+    const uint64_t a = idx / Sk, g = idx % Sk;
+    BatchBlock b;
+    b.index = 0;
+    b.n = n;
+    b.m = m;
+    b.tr = c;
+    b.tr.seg_in = b.tr.seg_out = 0;
+    b.tr.segs.clear();
+    b.tr.seg_base.clear();
+    b.I0 = a * c.seg_out;
+    b.I1 = std::min<uint64_t>(c.tiles_out, (a + 1) * c.seg_out);
+    b.J0 = g * c.seg_in;
+    b.J1 = std::min<uint64_t>(c.tiles_in, (g + 1) * c.seg_in);
+    return ntt_batch_build(c.field, std::vector<BatchBlock>{b}, 0, info);
+}
+
+// Layout of a segmented plan: each segment's tables and counters one after the other, then
+// ONE spectra region, as large as the largest segment needs, that every segment reuses
+// (the launches run in stream order).
+int seg_layout(uint64_t n, uint64_t m, TransformCfg *c) {
+    const uint64_t S = ceil_div(c->tiles_out, c->seg_out) * ceil_div(c->tiles_in, c->seg_in);
+    if (S == 0 || S > kSegMax) return PA_ERR_UNSUPPORTED;
+    c->segs.clear();
+    c->seg_base.clear();
+    size_t off = 0, spec = 0;
+    for (uint64_t idx = 0; idx < S; ++idx) {
+        NttBatchInfo info;
+        const int rc = seg_build(n, m, *c, idx, &info);
+        if (rc != PA_OK) return rc;
+        c->seg_base.push_back(off);
+        off = align256(off + info.off_spec);
+        spec = std::max(spec, info.bytes - info.off_spec);
+        c->segs.push_back(static_cast<const NttLayout &>(info));
+    }
+    for (uint64_t idx = 0; idx < S; ++idx) {
+        c->segs[idx].off_spec = off - c->seg_base[idx];
+        c->segs[idx].bytes = off + spec - c->seg_base[idx];
+    }
+    c->lay = c->segs[0];
+    c->lay.bytes = off + spec;
+    return PA_OK;
+}
+
+}  // namespace
+
 int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c) {
+    if (c->fd == 1 && c->seg_in && c->seg_out) return seg_layout(n, m, c);
     BatchBlock b;
     b.index = 0;
     b.n = n;
@@ -733,6 +832,17 @@ int ntt_layout(uint64_t n, uint64_t m, int path, TransformCfg *c) {
 }
 
 int ntt_init(const PlanCfg &cfg, void *ws) {
+    if (!cfg.tr.segs.empty()) {
+        for (size_t idx = 0; idx < cfg.tr.segs.size(); ++idx) {
+            NttBatchInfo info;
+            int rc = seg_build(cfg.n, cfg.m, cfg.tr, idx, &info);
+            if (rc != PA_OK) return rc;
+            if (info.off_spec > cfg.tr.segs[idx].off_spec) return PA_ERR_INVALID;
+            rc = upload(info, static_cast<char *>(ws) + cfg.tr.seg_base[idx], nullptr, true);
+            if (rc != PA_OK) return rc;
+        }
+        return PA_OK;
+    }
     BatchBlock b;
     b.index = 0;
     b.n = cfg.n;
@@ -772,6 +882,15 @@ int ntt_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const u
     prof_begin(prof, K_MEMSET, s);
     PA_CUDA_TRY(cudaMemsetAsync(out, 0, ceil_div(cfg.m, 64) * 8, s));
     prof_end(prof, s);
+    if (!cfg.tr.segs.empty()) {
+        // segments in order over the shared spectra region; each XORs its output bits
+        for (size_t idx = 0; idx < cfg.tr.segs.size(); ++idx) {
+            const int rc = launch_any(cfg.tr.segs[idx], static_cast<char *>(ws) + cfg.tr.seg_base[idx],
+                                      nullptr, one, &hdr->status, prof, s);
+            if (rc != PA_OK) return rc;
+        }
+        return PA_OK;
+    }
     return launch_any(cfg.tr.lay, ws, nullptr, one, &hdr->status, prof, s);
 }
 

@@ -24,6 +24,10 @@ constexpr int kMinBlocks = sizeof(typename F::T) == 4 ? 2 : 1;
 // spectra bytes of one block (about 22 bytes per key bit with l = 10%: n = 3e9 holds 67 GB).
 constexpr uint64_t kFdMaxPairs = uint64_t(1) << 22;
 constexpr uint64_t kFdMaxBytes = uint64_t(96) << 30;
+// Segmented accumulation (blocks beyond the resident cap): spectra of one segment at most
+// kSegMaxBytes by default (pa_opts.seg_cap_gib overrides), at most kSegMax segments.
+constexpr uint64_t kSegMaxBytes = uint64_t(32) << 30;
+constexpr uint64_t kSegMax = 1u << 16;
 
 // Work-item types (bits 60..63 of an item; bits 32..59 tile index, 0..31 sub-index).
 enum : uint32_t {

@@ -53,11 +53,15 @@ __device__ __forceinline__ BlockPtrs pick(const BlockPtrs *blks, const BlockPtrs
     return blks ? blks[b] : one;
 }
 
-// Pair descriptors of one block, in (output tile, key tile) order.
+// Pair descriptors of one block, in (output tile, key tile) order, for output tiles
+// [I0, I1) and key tiles [J0, J1) (I1 = 0: all output tiles; J1 = 0: all key tiles).
 inline void make_pairs(uint64_t n, uint64_t m, const TransformCfg &c, uint32_t blk,
-                       std::vector<TilePair> *out) {
-    for (uint64_t I = 0; I < c.tiles_out; ++I) {
-        for (uint64_t J = 0; J < c.tiles_in; ++J) {
+                       std::vector<TilePair> *out, uint64_t I0 = 0, uint64_t I1 = 0,
+                       uint64_t J0 = 0, uint64_t J1 = 0) {
+    if (!I1) I1 = c.tiles_out;
+    if (!J1) J1 = c.tiles_in;
+    for (uint64_t I = I0; I < I1; ++I) {
+        for (uint64_t J = J0; J < J1; ++J) {
             TilePair p{};
             const uint64_t i0 = I * c.M, j0 = J * c.L;
             p.key_bit0 = static_cast<int64_t>(j0);

@@ -181,3 +181,33 @@ def test_several_sums_never_stream(lib, n, m, k, L, M):
     assert (g["fd"], g["tiles_out"], g["sum_groups"]) == (1, 1, g["tiles_in"])
     assert g["windows"] == g["tiles_in"]
 
+
+
+def test_segmented_plan_beyond_the_resident_cap(lib):
+    # n = 1e10, l = 10%: resident spectra would need about 330 GB; the plan segments the
+    # key tiles (one sum's worth per segment) within the default 32 GiB of spectra
+    n, m = 10_000_000_019, 1_000_000_000
+    d = pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31"))
+    assert d["fd"] == 1 and d["prime_bits"] == 29 and d["segments"] > 1
+    P, Q = d["tiles_out"], d["tiles_in"]
+    assert d["segments"] == -(-P // d["seg_out"]) * -(-Q // d["seg_in"])
+    assert d["workspace_bytes"] < (33 << 30)
+    # a segment's sums stay below the 29-bit prime: at most (p - 1) / L key tiles per sum
+    assert d["seg_in"] * d["tile_in"] <= 469762049 - 1 or d["sum_groups"] > d["segments"]
+    assert d["kernels_per_call"] == d["segments"] + 1
+
+
+def test_segment_cap_shrinks_the_segments(lib):
+    n, m = 10_000_000_019, 1_000_000_000
+    big = pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31"))
+    small = pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31", seg_cap_gib=8))
+    assert small["workspace_bytes"] < (9 << 30) < big["workspace_bytes"]
+    assert small["segments"] > big["segments"]
+
+
+def test_forced_segments_shape(lib):
+    d = pkg.pa_plan_query(2_000_007, 600_003, binding.make_opts(
+        path="ntt31", log2_transform=19, tile_in=1 << 18, tile_out=1 << 18, fd_mode=2,
+        seg_in=3, seg_out=2))
+    assert (d["tiles_in"], d["tiles_out"], d["seg_in"], d["seg_out"]) == (8, 3, 3, 2)
+    assert d["segments"] == 2 * 3 and d["sum_groups"] == 3

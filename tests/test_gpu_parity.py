@@ -248,6 +248,41 @@ def test_paper_scale_3e9_sampled_rows():
     assert np.array_equal(oracle.unpack(got, m)[rows], want), desc
 
 
+@pytest.mark.parametrize("path,seg_in,seg_out,fd_group",
+                         [("ntt31", 3, 2, 0), ("ntt31", 2, 3, 0), ("ntt31", 3, 1, 2),
+                          ("ntt31", 8, 1, 0), ("ntt64", 3, 2, 0)])
+def test_segmented_sums_full(path, seg_in, seg_out, fd_group):
+    # Transform-domain sums run in segments over one reused spectra workspace (the paper's
+    # blocks run serially, Sec. 3): 8 key tiles x 3 output tiles of 2^18 at N = 2^19,
+    # forced into key segments of seg_in tiles and output slices of seg_out tiles (ragged
+    # last ones), optionally with several sums per segment; compared in full.
+    n, m = 2_000_007, 600_003
+    key, seed, want = _case(n, m, 81, 82)
+    opts = dict(log2_transform=19, tile_in=1 << 18, tile_out=1 << 18, fd_mode=2,
+                seg_in=seg_in, seg_out=seg_out, fd_group=fd_group)
+    desc = pkg.pa_plan_query(n, m, binding.make_opts(path=path, **opts))
+    assert desc["fd"] == 1 and desc["tiles_in"] == 8 and desc["tiles_out"] == 3, desc
+    assert desc["segments"] == -(-3 // seg_out) * -(-8 // seg_in), desc
+    _check(path, n, m, key, seed, want, **opts)
+
+
+def test_paper_scale_1e10_segmented_sampled_rows():
+    # Fig. 3's upper range: a 1e10-bit key, l = 10%, beyond the resident accumulation cap:
+    # the plan runs its sums in key segments through one fixed workspace (32 GiB of spectra
+    # at most), checked on sampled rows including output-tile edges.
+    n, m = 10_000_000_019, 1_000_000_000
+    b = inputs.single_block(n, m, 35, 36)
+    key, seed = b.key(), b.seed()
+    got, desc = run_path(n, m, key, seed, path="auto")
+    assert desc["path_name"] == "ntt31" and desc["segments"] > 1, desc
+    assert desc["workspace_bytes"] < (33 << 30), desc
+    M = desc["tile_out"]
+    rng = np.random.default_rng(17)
+    rows = np.unique(np.concatenate([rng.integers(0, m, 20), [0, M - 1, M, m - 1]]))
+    want = oracle.hash_rows(n, m, seed, key, rows)
+    assert np.array_equal(oracle.unpack(got, m)[rows], want), desc
+
+
 def _random_shapes(count=24, seed=2024):
     rng = np.random.default_rng(seed)
     out = []
