@@ -20,6 +20,8 @@
 //   ColMajor: element (r, c) at c * (R + R/16) + r + (r >> 4) (one word of skew per 16).
 #pragma once
 
+#include "ntt_field.cuh"  // compile-time roots of the prime fields (root16_tw)
+
 namespace pa {
 
 // addrs<LQ, K>(i0, c, a): addresses of rows i0 + k 2^LQ (k < K) of column c, for the
@@ -108,6 +110,62 @@ __device__ __forceinline__ void dit_group(typename F::T (&x)[1 << S], const type
     }
 }
 
+// Fields whose 16th roots of unity are compile-time constants (F::kRoot16).
+template <class F, class = void>
+struct HasRoot16 {
+    static constexpr bool value = false;
+};
+template <class F>
+struct HasRoot16<F, decltype(void(F::kRoot16))> {
+    static constexpr bool value = true;
+};
+
+// dif_group / dit_group of a stride-1 group (q = 1, j = 0): the twiddle of stage half-size
+// h at position k' < h is w_{2h}^(+-k') = w16^(+-8k'/h), fixed. For S = 4 and a field with
+// compile-time roots the twiddles are constants and the butterflies with w = 1 skip the
+// product; otherwise the stage tables are read as usual.
+template <class F, int S>
+__device__ __forceinline__ void dif_group_q1(typename F::T (&x)[1 << S], const typename F::Tw *tw) {
+    if constexpr (S == 4 && HasRoot16<F>::value) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int half = 8 >> s;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k & half) continue;
+                const int e = (k & (half - 1)) * (8 / half);
+                if (e == 0)
+                    F::dif_bfly1(x[k], x[k + half]);
+                else
+                    F::dif_bfly(x[k], x[k + half], root16_tw<F>(e));
+            }
+        }
+    } else {
+        dif_group<F, S>(x, tw, 0, 1);
+    }
+}
+
+template <class F, int S>
+__device__ __forceinline__ void dit_group_q1(typename F::T (&x)[1 << S], const typename F::Tw *tw) {
+    if constexpr (S == 4 && HasRoot16<F>::value) {
+#pragma unroll
+        for (int s = 3; s >= 0; --s) {
+            const int half = 8 >> s;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k & half) continue;
+                const int e = (k & (half - 1)) * (8 / half);
+                if (e == 0)
+                    F::dit_bfly1(x[k], x[k + half]);
+                else
+                    F::dit_bfly(x[k], x[k + half], root16_tw<F>(16 - e));
+            }
+        }
+    } else {
+        dit_group<F, S>(x, tw, 0, 1);
+    }
+}
+
 // One round of S stages over every column: groups g = (block, j), i0 = block 2^S q + j.
 // CF: consecutive threads take consecutive columns (RowMajor), else consecutive groups.
 template <class F, int S, bool DIF, bool CF, class Lay, int LQ>
@@ -139,10 +197,16 @@ __device__ __forceinline__ void round_s(typename F::T *sm, const Lay &lay, int l
         }
 #pragma unroll
         for (int k = 0; k < (1 << S); ++k) x[k] = sm[a[k]];
-        if (DIF)
+        if (LQ == 0) {  // q = 1, j = 0
+            if (DIF)
+                dif_group_q1<F, S>(x, tw);
+            else
+                dit_group_q1<F, S>(x, tw);
+        } else if (DIF) {
             dif_group<F, S>(x, tw, j, q);
-        else
+        } else {
             dit_group<F, S>(x, tw, j, q);
+        }
 #pragma unroll
         for (int k = 0; k < (1 << S); ++k) sm[a[k]] = x[k];
     }
@@ -245,11 +309,11 @@ __device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int l
             x[k] = sm[ax[k]];
             y[k] = sm[ay[k]];
         }
-        dif_group<F, 4>(x, twf, 0, 1);
-        dif_group<F, 4>(y, twf, 0, 1);
+        dif_group_q1<F, 4>(x, twf);
+        dif_group_q1<F, 4>(y, twf);
 #pragma unroll
         for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
-        dit_group<F, 4>(y, twi, 0, 1);
+        dit_group_q1<F, 4>(y, twi);
 #pragma unroll
         for (int k = 0; k < 16; ++k) sm[ay[k]] = y[k];
     }
@@ -279,8 +343,8 @@ __device__ void product_acc_round(typename F::T *sm, const Lay &lay, int logR, i
             x[k] = sm[ax[k]];
             y[k] = sm[ay[k]];
         }
-        dif_group<F, 4>(x, twf, 0, 1);
-        dif_group<F, 4>(y, twf, 0, 1);
+        dif_group_q1<F, 4>(x, twf);
+        dif_group_q1<F, 4>(y, twf);
 #pragma unroll
         for (int k = 0; k < 16; ++k) sm[az[k]] = add(sm[az[k]], mul(x[k], y[k]));
     }

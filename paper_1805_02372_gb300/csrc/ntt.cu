@@ -154,6 +154,12 @@ int get_tables(int field, Tables *out) {
             a = mulmod_host(a, w, p);
             b = mulmod_host(b, wi, p);
         }
+        // the stride-1 radix-16 groups use the field's compile-time 16th root: it must be
+        // this table's (a mismatch would give wrong spectra, so refuse)
+        if constexpr (HasRoot16<F>::value) {
+            if (static_cast<uint64_t>(f[size_t(1) << (kLogMax - 4)].w) != F::kRoot16)
+                return PA_ERR_INVALID;
+        }
         // compact stage tables: block (dir, logR) holds st[h-1+j] = w_{2h}^(+-j), R-1 entries
         std::vector<Tw> st(size_t(2) * (kLogSmallMax + 1) * kStageBlock);
         for (int dir = 0; dir < 2; ++dir)

@@ -16,6 +16,29 @@
 
 namespace pa {
 
+// Compile-time modular arithmetic for the 32-bit fields (p < 2^32, products fit 64 bits).
+constexpr uint64_t cx_powmod(uint64_t a, uint64_t e, uint64_t p) {
+    uint64_t r = 1;
+    a %= p;
+    while (e) {
+        if (e & 1) r = r * a % p;
+        a = a * a % p;
+        e >>= 1;
+    }
+    return r;
+}
+// The primitive 16th root of unity the twiddle tables use: g^((p-1)/16) for the smallest
+// generator g >= 2 (g^((p-1)/f) != 1 for f = 2 and the odd primes f1, f2 of p - 1; f2 = 0:
+// none), the same search as the host tables' root of order 2^23, whose 2^19-th power it is.
+constexpr uint32_t cx_root16(uint64_t p, uint64_t f1, uint64_t f2) {
+    for (uint64_t g = 2;; ++g) {
+        if (cx_powmod(g, (p - 1) / 2, p) == 1) continue;
+        if (cx_powmod(g, (p - 1) / f1, p) == 1) continue;
+        if (f2 && cx_powmod(g, (p - 1) / f2, p) == 1) continue;
+        return static_cast<uint32_t>(cx_powmod(g, (p - 1) / 16, p));
+    }
+}
+
 // Inverse of an odd 32-bit modulus mod 2^32 (Newton iteration, 3 -> 6 -> ... -> 96 bits).
 constexpr uint32_t inverse_mod_2_32(uint32_t p) {
     uint32_t x = p;
@@ -84,6 +107,18 @@ struct F31 {
         b = sub(a, t);
         a = add(a, t);
     }
+    // the same butterflies with w = 1
+    __device__ static __forceinline__ void dif_bfly1(T &a, T &b) {
+        const T s = add(a, b);
+        b = sub(a, b);
+        a = s;
+    }
+    __device__ static __forceinline__ void dit_bfly1(T &a, T &b) {
+        const T t = b;
+        b = sub(a, t);
+        a = add(a, t);
+    }
+    static constexpr uint32_t kRoot16 = cx_root16(2013265921u, 3, 5);
 };
 
 // Residues in [0, 4p). Shoup's product of any 32-bit a by a canonical twiddle w with
@@ -156,7 +191,53 @@ struct F29 {
         a = a2 + t;
         b = a2 + (P2 - t);
     }
+    // the same butterflies with w = 1 (no product: a conditional subtraction keeps the
+    // ranges of the general ones)
+    __device__ static __forceinline__ void dif_bfly1(T &a, T &b) {
+        const T s = a + b, d = a + (P4 - b);
+        b = min(d, d - P4);
+        a = min(s, s - P4);
+    }
+    __device__ static __forceinline__ void dit_bfly1(T &a, T &b) {
+        const T t = min(b, b - P2);
+        const T a2 = min(a, a - P2);
+        a = a2 + t;
+        b = a2 + (P2 - t);
+    }
+    static constexpr uint32_t kRoot16 = cx_root16(469762049u, 7, 0);
 };
+
+// Twiddle w16^E of a field with a compile-time 16th root (value and Shoup quotient).
+template <class F, int E>
+__device__ __forceinline__ typename F::Tw root16_tw() {
+    constexpr uint32_t w = static_cast<uint32_t>(cx_powmod(F::kRoot16, E & 15, F::P));
+    constexpr uint32_t q = static_cast<uint32_t>((uint64_t(w) << 32) / F::P);
+    typename F::Tw t;
+    t.w = w;
+    t.q = q;
+    return t;
+}
+template <class F>
+__device__ __forceinline__ typename F::Tw root16_tw(int e) {
+    switch (e & 15) {
+        case 1: return root16_tw<F, 1>();
+        case 2: return root16_tw<F, 2>();
+        case 3: return root16_tw<F, 3>();
+        case 4: return root16_tw<F, 4>();
+        case 5: return root16_tw<F, 5>();
+        case 6: return root16_tw<F, 6>();
+        case 7: return root16_tw<F, 7>();
+        case 8: return root16_tw<F, 8>();
+        case 9: return root16_tw<F, 9>();
+        case 10: return root16_tw<F, 10>();
+        case 11: return root16_tw<F, 11>();
+        case 12: return root16_tw<F, 12>();
+        case 13: return root16_tw<F, 13>();
+        case 14: return root16_tw<F, 14>();
+        case 15: return root16_tw<F, 15>();
+        default: return root16_tw<F, 0>();
+    }
+}
 
 struct F64 {
     using T = uint64_t;

@@ -128,7 +128,9 @@ __device__ __forceinline__ void seg_load(T (&x)[32 / sizeof(T)], const T *p) {
 }
 
 // Global loads a thread keeps in flight before storing them to shared memory.
-constexpr int kLoadBatch = 2;
+constexpr int kLoadBatch = 4;
+// Row segments whose pass-1 twiddles a thread forms at once.
+constexpr int kTwBatch = 2;
 
 // Asynchronous global -> shared copies (no registers held while they are in flight);
 // cp_async_wait_all waits for this thread's copies, a barrier then publishes them.
@@ -161,6 +163,26 @@ __device__ void p1tw_build(typename F::T *tb, const typename F::Tw *__restrict__
     }
 }
 
+// x[c] *= base step^c for c < SEG (twiddles in full form): the twiddles are formed as a
+// tree (w[c + b] = w[c] step^b, step^b by squaring), log2 SEG products deep instead of
+// SEG - 1, so the rows of a thread overlap their latencies.
+template <class F, int SEG>
+__device__ __forceinline__ void twiddle_segment(typename F::T (&x)[SEG], typename F::T base,
+                                                typename F::T step) {
+    using T = typename F::T;
+    T w[SEG];
+    w[0] = base;
+    T sp = step;
+#pragma unroll
+    for (int b = 1; b < SEG; b <<= 1) {
+#pragma unroll
+        for (int c = 0; c < b; ++c) w[c + b] = F::mul_full(w[c], sp);
+        if (2 * b < SEG) sp = F::mul_full(sp, sp);
+    }
+#pragma unroll
+    for (int c = 0; c < SEG; ++c) x[c] = F::mul_full(x[c], w[c]);
+}
+
 // Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1); each
 // thread handles 32-byte row segments (SEG columns).
 template <class F>
@@ -175,8 +197,9 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
     const RowMajor lay{logC};
     const int seglog = logC - logSEG;  // segments per row (log2)
     T *tb = sm + (R1 << logC);         // pass-1 twiddle tables (p1tw_build)
-    p1tw_build<F>(tb, tfwd, c0, SEG, seglog, logR1, logN);
-    // up to kLoadBatch segments per thread: every load issued before the first store
+    // up to kLoadBatch segments per thread: every load issued before the first store, and
+    // the twiddle tables (root-table lookups) built while the first batch is in flight
+    bool built = false;
     for (int e0 = threadIdx.x; e0 < (R1 << seglog); e0 += kLoadBatch * blockDim.x) {
         uint32_t bits[kLoadBatch];
 #pragma unroll
@@ -186,6 +209,10 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
             bits[u] = e < (R1 << seglog)
                           ? tile_bits(pr, bp, which, (uint64_t(r) << logS) + c0 + sg * SEG)
                           : 0u;
+        }
+        if (!built) {
+            p1tw_build<F>(tb, tfwd, c0, SEG, seglog, logR1, logN);
+            built = true;
         }
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
@@ -198,28 +225,31 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
             seg_store<T>(sm + lay.at(r, sg * SEG), x);
         }
     }
+    if (!built) p1tw_build<F>(tb, tfwd, c0, SEG, seglog, logR1, logN);
     __syncthreads();
     dif_columns<F, true>(sm, lay, logR1, logC, st);
     const int per = 32 + (1 << (logR1 - 5));
     const T *tc = tb + (per << seglog);
-    for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
-        const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
-        T x[SEG];
-        seg_load<T>(x, sm + lay.at(r, sg * SEG));
-        const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
-        const T *ta = tb + sg * per;
-        const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);  // w^(t0 f), full form
-        const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);  // w^f, full form
-        x[0] = F::mul_full(x[0], base);
-        T wf = base;
+    const int nseg = R1 << seglog;
+    // kTwBatch segments per thread at once, so their product chains overlap
+    for (int e0 = threadIdx.x; e0 < nseg; e0 += kTwBatch * blockDim.x) {
 #pragma unroll
-        for (int c = 1; c < SEG; ++c) {
-            wf = F::mul_full(wf, step);
-            x[c] = F::mul_full(x[c], wf);
+        for (int u = 0; u < kTwBatch; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < nseg) {
+                const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+                T x[SEG];
+                seg_load<T>(x, sm + lay.at(r, sg * SEG));
+                const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
+                const T *ta = tb + sg * per;
+                const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);  // w^(t0 f), full form
+                const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);  // w^f, full form
+                twiddle_segment<F, SEG>(x, base, step);
+                uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
+                __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
+                __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[SEG / 2]));
+            }
         }
-        uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
-        __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
-        __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[SEG / 2]));
     }
     __syncthreads();
     (void)C;
@@ -289,38 +319,40 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
     // the inverse twiddles w^-(t f) from short tables (p1tw_build with the inverse roots),
     // looked up while the rows load, applied in one pass over shared memory
     T *tb = sm + (R1 << logC);
-    p1tw_build<F>(tb, tinv, c0, SEG, seglog, logR1, logN);
     {
-        const uint32_t h = (threadIdx.x >> 2) & 1u;  // half order of seg_store
-        for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
-            const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+        // the two 16-byte halves of a row segment come from two adjacent lanes (a warp's
+        // copy reads 16 whole sectors)
+        for (int e = threadIdx.x; e < 2 * (R1 << seglog); e += blockDim.x) {
+            const int si = e >> 1, h = e & 1;
+            const int r = si >> seglog, sg = si & ((1 << seglog) - 1);
             const uint4 *g = reinterpret_cast<const uint4 *>(src + (uint64_t(r) << logS) + c0 + sg * SEG);
             uint4 *d = reinterpret_cast<uint4 *>(sm + lay.at(r, sg * SEG));
             cp_async16(d + h, g + h);
-            cp_async16(d + (h ^ 1u), g + (h ^ 1u));
         }
+        p1tw_build<F>(tb, tinv, c0, SEG, seglog, logR1, logN);
         cp_async_wait_all();
     }
     __syncthreads();
     {
         const int per = 32 + (1 << (logR1 - 5));
         const T *tc = tb + (per << seglog);
-        for (int e = threadIdx.x; e < (R1 << seglog); e += blockDim.x) {
-            const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
-            T x[SEG];
-            seg_load<T>(x, sm + lay.at(r, sg * SEG));
-            const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
-            const T *ta = tb + sg * per;
-            const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);
-            const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);
-            x[0] = F::mul_full(x[0], base);
-            T wf = base;
+        const int nseg = R1 << seglog;
+        for (int e0 = threadIdx.x; e0 < nseg; e0 += kTwBatch * blockDim.x) {
 #pragma unroll
-            for (int c = 1; c < SEG; ++c) {
-                wf = F::mul_full(wf, step);
-                x[c] = F::mul_full(x[c], wf);
+            for (int u = 0; u < kTwBatch; ++u) {
+                const int e = e0 + u * blockDim.x;
+                if (e < nseg) {
+                    const int r = e >> seglog, sg = e & ((1 << seglog) - 1);
+                    T x[SEG];
+                    seg_load<T>(x, sm + lay.at(r, sg * SEG));
+                    const uint32_t f = __brev(static_cast<uint32_t>(r)) >> (32 - logR1);
+                    const T *ta = tb + sg * per;
+                    const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);
+                    const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);
+                    twiddle_segment<F, SEG>(x, base, step);
+                    seg_store<T>(sm + lay.at(r, sg * SEG), x);
+                }
             }
-            seg_store<T>(sm + lay.at(r, sg * SEG), x);
         }
     }
     __syncthreads();
