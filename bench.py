@@ -329,8 +329,11 @@ def algorithmic(kernel: str, blocks, descs, probe):
     if kernel == "block_mma":
         ops = sum(2.0 * b.m * (b.n + 8192) for b, d in zip(blocks, descs)
                   if d["path_name"] == "block_int8")
-        return ("tensor", ops, "Tops/s", ops / 150.8e12,
-                "measured (earlier probe, not in this run): legacy mma.sync s8 at 150.8 Top/s")
+        if not probe:
+            return None, None, None, None, None
+        return ("tensor", ops, "Tops/s", ops / (2.0 * probe["mma_s8_macs_per_s"]),
+                f"measured in this run: pa_probe_peak(PA_PEAK_MMA_S8) = "
+                f"{2.0 * probe['mma_s8_macs_per_s'] / 1e12:.1f} Top/s (legacy mma.sync s8)")
     if kernel == "block_tc":
         # dense FP8 MMA work the kernel performs: M = 128 rows x N = 256 blocks per output
         # tile, over the tile's contraction length n + 128 * 255
@@ -578,11 +581,28 @@ def probe_peaks():
     b, bms = binding.pa_probe_peak(binding.PA_PEAK_NTT_BUTTERFLY)
     ma, mms = binding.pa_probe_peak(binding.PA_PEAK_NTT_MULADD)
     sa, sms = binding.pa_probe_peak(binding.PA_PEAK_SHIFT_AND)
+    s8, s8ms = binding.pa_probe_peak(binding.PA_PEAK_MMA_S8)
+    b1, b1ms = binding.pa_probe_peak(binding.PA_PEAK_MMA_B1)
     return {"butterfly_per_s": b, "muladd_per_s": ma, "shift_and_per_s": sa,
-            "launch_ms": {"butterfly": bms, "muladd": mms, "shift_and": sms},
+            "mma_s8_macs_per_s": s8, "mma_b1_and_popc_per_s": b1,
+            "launch_ms": {"butterfly": bms, "muladd": mms, "shift_and": sms, "mma_s8": s8ms,
+                          "mma_b1": b1ms},
             "what": "29-bit-field lazy butterfly, 29-bit-field multiply-add, funnel-shift "
-                    "AND-XOR: register-only chains on every SM, fastest of three ~20 ms "
-                    "launches after a warm-up"}
+                    "AND-XOR, mma.sync m16n8k32 s8 and m16n8k256 b1 AND-POPC: register-only "
+                    "chains on every SM, fastest of three ~20 ms launches after a warm-up"}
+
+
+def binary_mma_record(probe, fp8_rec):
+    """The block contraction's dense forms compared in bit products per second: the
+    binary mma.sync (one AND per bit product), the INT8 mma.sync (one MAC per bit product),
+    the tcgen05 FP8 path (measured on the batched workload: one MAC per bit product) and
+    the direct kernel's shift-and-accumulate (32 bit products each)."""
+    out = {"b1_mma_bit_products_per_s": probe["mma_b1_and_popc_per_s"],
+           "s8_mma_bit_products_per_s": probe["mma_s8_macs_per_s"],
+           "direct_bit_products_per_s": 32.0 * probe["shift_and_per_s"]}
+    if fp8_rec and "roofline" in fp8_rec:
+        out["fp8_tcgen05_bit_products_per_s"] = fp8_rec["roofline"]["achieved"] * 1e12 / 2.0
+    return out
 
 
 # --------------------------------------------------------------------------- full-output checks
@@ -828,6 +848,7 @@ def main():
     if extras and len(blocks) > 1:
         line["paths_batched"] = batched_paths(blocks, keys_h, seeds_h, device, flush, scratch,
                                               probe, plain_gbps, digests)
+        line["binary_mma"] = binary_mma_record(probe, line["paths_batched"].get("block_fp8"))
     if extras and args.workload == "batched256":
         line["configs"] = config_records(device, flush, scratch, probe)
         line["table1"] = table1_records(device, flush, scratch, probe)

@@ -252,7 +252,9 @@ int pa_batch_run_host(pa_batch_t batch, const pa_block *host_blocks, size_t coun
                       pa_report *rep);
 
 /* What the batch plan chose for each block (path, tiles, transform size); count must be
- * the batch's block count. */
+ * the batch's block count. workspace_bytes of a block in its prime field's shared
+ * persistent launch counts only a header: that launch's tables and spectra belong to the
+ * batch as a whole. */
 int pa_batch_describe(pa_batch_t batch, pa_plan_desc *out, size_t count);
 
 void pa_batch_destroy(pa_batch_t batch);
@@ -345,13 +347,19 @@ int pa_selftest(int which, int *device_status);
  *   which = PA_PEAK_NTT_MULADD: acc += x y in the 29-bit field (Montgomery product plus lazy
  *           addition: the pointwise products and transform-domain sums of Sec. 3 Step 2);
  *   which = PA_PEAK_SHIFT_AND: acc ^= x & funnel_shift(lo, hi, k), the direct kernel's step
- *           (one operation = one shift-and-accumulate of 32 bit products, Sec. 2.1 Eq. 1).
+ *           (one operation = one shift-and-accumulate of 32 bit products, Sec. 2.1 Eq. 1);
+ *   which = PA_PEAK_MMA_S8: warp-level mma.sync m16n8k32 s8 -> s32, the INT8 block path's
+ *           instruction (one operation = one multiply-accumulate);
+ *   which = PA_PEAK_MMA_B1: warp-level mma.sync m16n8k256 b1 AND + POPC -> s32, the binary
+ *           form of the block contraction (one operation = one 1-bit AND product summed).
  * *ops_per_s: the fastest of three launches of about 20 ms (after a warm-up);
  * *ms (nullable): that launch's device time. Synchronous; allocates 256 bytes of device
  * memory for the duration of the call. PA_ERR_INVALID for another `which`. */
 #define PA_PEAK_NTT_BUTTERFLY 1
 #define PA_PEAK_NTT_MULADD 2
 #define PA_PEAK_SHIFT_AND 3
+#define PA_PEAK_MMA_S8 4
+#define PA_PEAK_MMA_B1 5
 int pa_probe_peak(int which, double *ops_per_s, double *ms);
 
 const char *pa_strerror(int status);

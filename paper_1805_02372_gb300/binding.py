@@ -455,6 +455,8 @@ def pa_selftest(which: int) -> int:
 PA_PEAK_NTT_BUTTERFLY = 1
 PA_PEAK_NTT_MULADD = 2
 PA_PEAK_SHIFT_AND = 3
+PA_PEAK_MMA_S8 = 4
+PA_PEAK_MMA_B1 = 5
 
 
 def pa_probe_peak(which: int) -> tuple[float, float]:

@@ -19,7 +19,7 @@ int cuda_fail(cudaError_t e) {
 // Largest sizes accepted at all (the seed index n+m-2 must fit comfortably).
 constexpr uint64_t kMaxBits = uint64_t(1) << 40;
 
-int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
+int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool layout) {
     if (!cfg || n == 0 || m == 0 || n > kMaxBits || m > kMaxBits) return PA_ERR_INVALID;
     *cfg = PlanCfg();
     cfg->n = n;
@@ -49,7 +49,8 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg) {
         case PA_PATH_NTT64:
         case PA_PATH_NTT31:
             rc = ntt_plan(n, m, path, o, &cfg->tr);
-            if (rc == PA_OK) rc = ntt_layout(n, m, path, &cfg->tr);
+            if (rc == PA_OK && (layout || (cfg->tr.fd == 1 && cfg->tr.seg_in)))
+                rc = ntt_layout(n, m, path, &cfg->tr);
             cfg->ws_bytes = cfg->tr.lay.bytes;
             // output zeroing + the persistent launch (one per segment when segmented)
             cfg->kernels = 1 + static_cast<uint32_t>(std::max<size_t>(1, cfg->tr.segs.size()));

@@ -510,7 +510,7 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
             // blocks
             best_path(n, m, t, true, &o, opts ? opts->fd_mode : 0, opts ? opts->fd_group : 0);
         }
-        int rc = plan_resolve(n, m, &o, &b->cfg[i]);
+        int rc = plan_resolve(n, m, &o, &b->cfg[i], false);
         if (rc != PA_OK) {
             delete b;
             return rc;

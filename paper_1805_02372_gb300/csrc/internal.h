@@ -88,7 +88,9 @@ struct PlanCfg {
 int tuned_opts(uint64_t n, uint64_t m, pa_opts *out);
 
 // Host-only planning (no GPU calls).
-int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg);
+// layout = false: NTT plans skip their single-block work-list layout (a batch builds its
+// own combined list; segmented blocks still get theirs).
+int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool layout = true);
 void fill_desc(const PlanCfg &cfg, pa_plan_desc *d);
 
 // Workspace header kept at the start of every plan's device workspace.

@@ -221,6 +221,15 @@ uint64_t count_windows(uint64_t P, uint64_t Q, uint64_t M, uint64_t L) {
     return static_cast<uint64_t>(std::unique(d.begin(), d.end()) - d.begin());
 }
 
+// Distinct offsets of a P x Q segment in O(1): exact when one tile length divides the
+// other (the geometries the planner builds), else the upper bound P Q. Sizes segments.
+uint64_t count_windows_bound(uint64_t P, uint64_t Q, uint64_t M, uint64_t L) {
+    if (P == 1 || Q == 1) return P * Q;
+    if (L % M == 0) return L / M <= P ? P + (L / M) * (Q - 1) : P * Q;
+    if (M % L == 0) return M / L <= Q ? (M / L) * (P - 1) + Q : P * Q;
+    return P * Q;
+}
+
 // Key tile for transform size 2^logn and output tile M: L = N - M rounded down to 32
 // bits (or the forced L), at most the key rounded up to 32 bits; 0 if none fits.
 uint64_t tile_in_for(uint64_t n, uint32_t logn, uint64_t M, uint64_t Lforce) {
@@ -308,7 +317,7 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
     uint64_t si = seg->seg_in_force ? std::min<uint64_t>(seg->seg_in_force, Q) : std::min<uint64_t>(g, Q);
     uint64_t so = seg->seg_out_force ? std::min<uint64_t>(seg->seg_out_force, P) : P;
     const auto seg_bytes = [&](uint64_t a, uint64_t b) {
-        const uint64_t ws = count_windows(b, a, M, L), gs = ceil_div(a, g);
+        const uint64_t ws = count_windows_bound(b, a, M, L), gs = ceil_div(a, g);
         return double(a + ws + gs * b) * N * elem;
     };
     while (seg_bytes(si, so) > double(cap) && !seg->seg_out_force && so > 1) so = ceil_div(so, 2);
@@ -316,7 +325,7 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
     if (seg_bytes(si, so) > double(cap)) return std_units;
     const uint64_t So = ceil_div(P, so), Sk = ceil_div(Q, si);
     if (So * Sk > kSegMax) return std_units;
-    const uint64_t ws = count_windows(so, si, M, L), gs = ceil_div(si, g);
+    const uint64_t ws = count_windows_bound(so, si, M, L), gs = ceil_div(si, g);
     const double segc = double(So * Sk) * (double(si + ws) * (tr + 2 * N + 1024.0) +
                                            double(gs * so) * (tr + N + 1024.0) + 4.0 * N) +
                         double(P) * double(Q) * 3.0 * N;

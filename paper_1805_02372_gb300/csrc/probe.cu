@@ -9,9 +9,13 @@
 //                          the butterfly of every forward round of the NTT path);
 //   PA_PEAK_NTT_MULADD     acc += x * y in the 29-bit field (a Montgomery product and a lazy
 //                          addition: the pointwise products and transform-domain sums);
-//   PA_PEAK_SHIFT_AND      acc ^= xw & funnel_shift(lo, hi, k) (the direct kernel's step).
+//   PA_PEAK_SHIFT_AND      acc ^= xw & funnel_shift(lo, hi, k) (the direct kernel's step);
+//   PA_PEAK_MMA_S8         mma.sync m16n8k32 s8 x s8 -> s32 (the INT8 block path's MMA);
+//   PA_PEAK_MMA_B1         mma.sync m16n8k256 b1 AND + POPC -> s32 (the binary form of the
+//                          block contraction: one bit product per AND, summed by POPC).
 // Each result is operations per second, one operation being one butterfly, one
-// multiply-add or one shift-and-accumulate.
+// multiply-add, one shift-and-accumulate, or one multiply-accumulate of the MMA (an s8
+// product, or a 1-bit AND product).
 #include <stdint.h>
 
 #include "common.cuh"
@@ -91,6 +95,76 @@ __global__ void __launch_bounds__(kProbeThreads, 2) probe_shift_and(uint32_t *si
     if (r == 0x9E3779B9u) sink[0] = r;
 }
 
+// kMma independent accumulator chains per warp; MMA operands stay in registers (changing
+// each iteration so nothing is hoisted).
+constexpr int kMma = 4;
+
+__global__ void __launch_bounds__(kProbeThreads, 2) probe_mma_s8(uint32_t *sink, uint32_t iters,
+                                                                  uint32_t seed) {
+    uint32_t a[4], b[2];
+    int32_t d[kMma][4];
+    const uint32_t x = seed ^ ((blockIdx.x * kProbeThreads + threadIdx.x) * 0x9E3779B9u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = (x >> i) & 0x01010101u;
+    b[0] = (x >> 5) & 0x01010101u;
+    b[1] = (x >> 7) & 0x01010101u;
+#pragma unroll
+    for (int c = 0; c < kMma; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[c][i] = 0;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kMma; ++c)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                "{%8,%9}, {%0,%1,%2,%3};"
+                : "+r"(d[c][0]), "+r"(d[c][1]), "+r"(d[c][2]), "+r"(d[c][3])
+                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        const uint32_t t = a[0];  // rotate the A fragment (fixed indices: stays in registers)
+        a[0] = a[1];
+        a[1] = a[2];
+        a[2] = a[3];
+        a[3] = t ^ 0x01000000u;
+    }
+    int32_t r = 0;
+#pragma unroll
+    for (int c = 0; c < kMma; ++c) r ^= d[c][0] ^ d[c][1] ^ d[c][2] ^ d[c][3];
+    if (r == 0x7654321) sink[0] = static_cast<uint32_t>(r);
+}
+
+__global__ void __launch_bounds__(kProbeThreads, 2) probe_mma_b1(uint32_t *sink, uint32_t iters,
+                                                                  uint32_t seed) {
+    uint32_t a[4], b[2];
+    int32_t d[kMma][4];
+    const uint32_t x = seed ^ ((blockIdx.x * kProbeThreads + threadIdx.x) * 0x9E3779B9u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = x * (2u * i + 1u);
+    b[0] = x ^ 0x5BD1E995u;
+    b[1] = x * 0x85EBCA6Bu;
+#pragma unroll
+    for (int c = 0; c < kMma; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[c][i] = 0;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kMma; ++c)
+            asm volatile(
+                "mma.sync.aligned.m16n8k256.row.col.s32.b1.b1.s32.and.popc {%0,%1,%2,%3}, "
+                "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                : "+r"(d[c][0]), "+r"(d[c][1]), "+r"(d[c][2]), "+r"(d[c][3])
+                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        const uint32_t t = a[0];
+        a[0] = a[1];
+        a[1] = a[2];
+        a[2] = a[3];
+        a[3] = t + 0x9E3779B9u;
+    }
+    int32_t r = 0;
+#pragma unroll
+    for (int c = 0; c < kMma; ++c) r ^= d[c][0] ^ d[c][1] ^ d[c][2] ^ d[c][3];
+    if (r == 0x7654321) sink[0] = static_cast<uint32_t>(r);
+}
+
 // Launches probe `which` with `iters` iterations per thread; returns operations per launch.
 double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, cudaStream_t s) {
     const double threads = double(grid) * kProbeThreads;
@@ -105,6 +179,14 @@ double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, cu
         probe_muladd<<<grid, kProbeThreads, 0, s>>>(sink, iters, 0x1234567u);
         return threads * iters * 2.0 * kChains;
     }
+    if (which == PA_PEAK_MMA_S8) {
+        probe_mma_s8<<<grid, kProbeThreads, 0, s>>>(sink, iters, 0x1234567u);
+        return threads / 32.0 * iters * kMma * (16.0 * 8.0 * 32.0);
+    }
+    if (which == PA_PEAK_MMA_B1) {
+        probe_mma_b1<<<grid, kProbeThreads, 0, s>>>(sink, iters, 0x1234567u);
+        return threads / 32.0 * iters * kMma * (16.0 * 8.0 * 256.0);
+    }
     probe_shift_and<<<grid, kProbeThreads, 0, s>>>(sink, iters, 0x1234567u);
     return threads * iters * 32.0;
 }
@@ -114,14 +196,14 @@ double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, cu
 
 extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
     using namespace pa;
-    if (!ops_per_s || (which != PA_PEAK_NTT_BUTTERFLY && which != PA_PEAK_NTT_MULADD &&
-                       which != PA_PEAK_SHIFT_AND))
-        return PA_ERR_INVALID;
+    if (!ops_per_s || which < PA_PEAK_NTT_BUTTERFLY || which > PA_PEAK_MMA_B1) return PA_ERR_INVALID;
     int dev = 0, sms = 0, per_sm = 0;
     PA_CUDA_TRY(cudaGetDevice(&dev));
     PA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const void *fn = which == PA_PEAK_NTT_BUTTERFLY ? reinterpret_cast<const void *>(probe_butterfly)
                      : which == PA_PEAK_NTT_MULADD  ? reinterpret_cast<const void *>(probe_muladd)
+                     : which == PA_PEAK_MMA_S8      ? reinterpret_cast<const void *>(probe_mma_s8)
+                     : which == PA_PEAK_MMA_B1      ? reinterpret_cast<const void *>(probe_mma_b1)
                                                     : reinterpret_cast<const void *>(probe_shift_and);
     PA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kProbeThreads, 0));
     const unsigned grid = static_cast<unsigned>((per_sm > 0 ? per_sm : 1) * sms);

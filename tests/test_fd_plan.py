@@ -211,3 +211,16 @@ def test_forced_segments_shape(lib):
         seg_in=3, seg_out=2))
     assert (d["tiles_in"], d["tiles_out"], d["seg_in"], d["seg_out"]) == (8, 3, 3, 2)
     assert d["segments"] == 2 * 3 and d["sum_groups"] == 3
+
+
+def test_planning_stays_fast_for_serving_sizes(lib):
+    # the geometry search must not enumerate window offsets for implausible candidates (a
+    # wave of the server plans its blocks on the latency path): keys up to 1e8 bits plan
+    # in well under a tenth of a second on the host
+    import time
+    shapes = [(79_938_100, 13_501_589), (96_422_116, 11_557_350), (97_228_129, 42_449_279),
+              (27_259_615, 10_707_482)]
+    t0 = time.perf_counter()
+    for n, m in shapes:
+        pkg.pa_plan_query(n, m, binding.make_opts(path="ntt31"))
+    assert (time.perf_counter() - t0) / len(shapes) < 0.05

@@ -125,6 +125,36 @@ def test_finite_size_sampled_rows(path):
     assert np.array_equal(g12, got ^ g2)
 
 
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        return json.load(f)
+
+
+def _sha(words):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(words, dtype="<u8").tobytes()).hexdigest()
+
+
+@pytest.mark.parametrize("path,opts", [("ntt31", {}), ("ntt31", {"ntt_prime": 31}), ("ntt64", {}),
+                                       ("block_fp8", {}), ("direct", {}), ("block_int8", {}),
+                                       ("fft", {})])
+def test_finite_size_full_output(path, opts):
+    # Every output bit of the finite-size block (n = 100,000,007, m = 1e7: 1e15 bit products)
+    # against the SHA-256 of the oracle's full output, stored by tests/golden/make_golden.py;
+    # the digests of 16 equal slices of the output words name the rows of any mismatch.
+    g = _golden("finite_size.json")
+    b = inputs.FINITE_SIZE
+    assert (g["n"], g["m"]) == (b.n, b.m)
+    got, desc = run_path(b.n, b.m, b.key(), b.seed(), path=path, **opts)
+    if _sha(got) != g["sha256"]:
+        w, k = got.size, g["slices"]
+        bad = [i for i in range(k) if _sha(got[i * w // k:(i + 1) * w // k]) != g["slice_sha256"][i]]
+        pytest.fail(f"{path} {opts}: output differs from the oracle in word slices {bad} of {k} "
+                    f"({desc})")
+
+
 def test_misaligned_buffers_rejected():
     import torch
     n, m = 1000, 100
