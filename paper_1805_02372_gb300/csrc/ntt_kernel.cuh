@@ -127,6 +127,15 @@ __device__ __forceinline__ void seg_load(T (&x)[32 / sizeof(T)], const T *p) {
     *reinterpret_cast<uint4 *>(&x[H]) = h ? f : g;
 }
 
+// 32 bytes to global memory with one 256-bit store, cached in L2 only (p 32-byte aligned):
+// a lane writes a whole sector.
+__device__ __forceinline__ void stcg256(void *p, const void *v) {
+    const uint32_t *w = static_cast<const uint32_t *>(v);
+    asm volatile("st.global.cg.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]),
+                 "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 // Global loads a thread keeps in flight before storing them to shared memory.
 constexpr int kLoadBatch = 4;
 // Row segments whose pass-1 twiddles a thread forms at once.
@@ -245,9 +254,7 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
                 const T base = F::mul_full(ta[f & 31], ta[32 + (f >> 5)]);  // w^(t0 f), full form
                 const T step = F::mul_full(tc[f & 31], tc[32 + (f >> 5)]);  // w^f, full form
                 twiddle_segment<F, SEG>(x, base, step);
-                uint4 *d = reinterpret_cast<uint4 *>(dst + (uint64_t(r) << logS) + c0 + sg * SEG);
-                __stcg(d, *reinterpret_cast<uint4 *>(&x[0]));
-                __stcg(d + 1, *reinterpret_cast<uint4 *>(&x[SEG / 2]));
+                stcg256(dst + (uint64_t(r) << logS) + c0 + sg * SEG, x);
             }
         }
     }
