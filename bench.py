@@ -304,6 +304,24 @@ def ntt_work(descs):
     return bfly, prod
 
 
+def spectra_elements(descs):
+    """Transform-domain elements the NTT blocks' spectra hold over a step (every transform's
+    N): the unit the persistent launch's DRAM traffic grows with, used to scale a traffic
+    figure captured on a subset of the blocks to the whole launch."""
+    tot = 0.0
+    for d in descs:
+        if d["path_name"] not in ("ntt31", "ntt64"):
+            continue
+        N = 2.0 ** d["log2_transform"]
+        P, Q = d["tiles_out"], d["tiles_in"]
+        if d.get("fd"):
+            keys = Q * -(-P // (d.get("seg_out") or P))
+            tot += (keys + d["windows"] + (d.get("sum_groups") or 1) * P) * N
+        else:
+            tot += 3 * P * Q * N
+    return tot
+
+
 def algorithmic(kernel: str, blocks, descs, probe):
     """(bound, algorithmic ops per step, unit, seconds those ops take at the peak per step,
     peak_source) for a kernel; `probe` holds the issue-rate peaks measured in this run."""
@@ -394,6 +412,8 @@ def roofline(kt: dict, blocks, descs, steps: int, workload_name: str, probe=None
                              "frac": hbm / pk["hbm_gbs"], "peak_source": psrc + " (MEASURED_PEAKS)",
                              "bytes_per_step": compulsory_bytes(blocks)}
     out["traffic"] = traffic_for(name, workload_name)
+    if name == "batch_persistent":
+        out["spectra_elements_per_launch"] = spectra_elements(descs) / launches_per_step
     return out
 
 

@@ -117,8 +117,11 @@ __device__ __forceinline__ bool wait_count(const uint32_t *c, uint32_t target, i
     return *flag != 0;
 }
 
+// Release of a CTA's global writes to the CTAs that wait on counter c: the barrier orders
+// every thread's writes before thread 0's GPU-scope fence, which (being cumulative) orders
+// them before the counter increment; a waiter's acquire load of the counter then sees them
+// (the pattern of a grid-wide barrier: one fence per CTA, not one per thread).
 __device__ __forceinline__ void signal_count(uint32_t *c) {
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -126,9 +129,8 @@ __device__ __forceinline__ void signal_count(uint32_t *c) {
     }
 }
 
-// signal_count for `count` consecutive counters (one fence and barrier for all of them)
+// signal_count for `count` consecutive counters (one barrier and fence for all of them)
 __device__ __forceinline__ void signal_counts(uint32_t *c, uint32_t count) {
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
