@@ -147,3 +147,32 @@ def test_batched_workload_256_blocks():
         rows = rng.integers(0, b.m, 64)
         assert np.array_equal(oracle.hash_rows(b.n, b.m, seeds[i], keys[i], rows),
                               oracle.unpack(outs[i], b.m)[rows])
+
+
+def test_batch_with_segmented_blocks():
+    # Blocks whose transform-domain sums run in segments are carried by a batch as their own
+    # launch sequences over their own workspaces (captured in the batch's graph with the
+    # rest): two forced segmented geometries (8 key x 3 output tiles of 2^18 at N = 2^19,
+    # key segments of 3, output slices of 2), compared in full, on the first run and on the
+    # graph replay; the plan descriptors report the segments.
+    bl, keys, seeds = _blocks([(2_000_007, 600_003), (1_900_001, 700_001)], salt=40)
+    opts = binding.make_opts(path="ntt31", log2_transform=19, tile_in=1 << 18,
+                             tile_out=1 << 18, fd_mode=2, seg_in=3, seg_out=2)
+    import torch
+    kd = [dev(k) for k in keys]
+    sd = [dev(s) for s in seeds]
+    od = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64, device="cuda") for b in bl]
+    desc = [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sd, kd, od)]
+    batch = pkg.pa_batch_plan(desc, opts)
+    try:
+        d = pkg.pa_batch_describe(batch, len(bl))
+        assert all(x["segments"] == 6 and x["fd"] == 1 for x in d), d
+        for run in range(2):
+            rep = pkg.pa_batch_run(batch, desc, report=True)
+            assert rep["graph_replayed"] == run
+            for b, k, s, o in zip(bl, keys, seeds, od):
+                assert np.array_equal(host(o), oracle.hash_full(b.n, b.m, s, k)), (run, b.n, b.m)
+            for o in od:
+                o.fill_(-1)
+    finally:
+        pkg.pa_batch_destroy(batch)
