@@ -295,9 +295,18 @@ def ntt_work(descs):
             # segmented sums recompute the key spectra once per output slice; `windows` and
             # `sum_groups` count every segment's
             G = d.get("sum_groups") or 1
-            keys = Q * -(-P // (d.get("seg_out") or P))
+            so = d.get("seg_out") or P
+            keys = Q * -(-P // so)
             bfly += (keys + d["windows"] + G * P) * (N / 2) * k
-            prod += P * Q * N
+            if d.get("outer_log2"):
+                # sums as convolutions over the tile index: per (group, output slice) three
+                # T-point transforms and T products for every bin
+                T, lt = 2.0 ** d["outer_log2"], d["outer_log2"]
+                conv = G * -(-P // so) * -(-so // d["outer_slice"])
+                bfly += conv * N * 3 * (T / 2) * lt
+                prod += conv * N * T
+            else:
+                prod += P * Q * N
         else:
             bfly += P * Q * 3 * (N / 2) * k
             prod += P * Q * N

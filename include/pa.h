@@ -96,6 +96,13 @@ typedef struct {
                                   the resident spectra would exceed 96 GiB)               */
     uint32_t seg_out;          /* segments: output sub-blocks per slice; 0 = automatic     */
     uint32_t seg_cap_gib;      /* segments: GiB of spectra one segment may hold; 0 = 32    */
+    uint32_t outer_mode;       /* transform-domain sums with equal key and output sub-blocks
+                                  are, bin by bin, convolutions over the sub-block index
+                                  (the window of (I, J) depends on I - J); computed with
+                                  transforms over that index instead of one product per
+                                  (I, J): 0 = when the planner estimates it faster,
+                                  1 = never, 2 = whenever possible                        */
+    uint32_t reserved[3];
 } pa_opts;
 
 /* What a plan decided (pa_plan_query / pa_plan_describe). */
@@ -120,6 +127,9 @@ typedef struct {
     uint32_t seg_in;           /* segmented fd: key sub-blocks per segment, else 0        */
     uint32_t seg_out;          /* segmented fd: output sub-blocks per slice, else 0       */
     uint64_t segments;         /* segmented fd: launches run in order (slices x segments) */
+    uint32_t outer_log2;       /* fd sums by transforms over the sub-block index: log2 of
+                                  their size, else 0                                      */
+    uint32_t outer_slice;      /* ... output sub-blocks per such convolution              */
 } pa_plan_desc;
 
 typedef struct pa_plan_s *pa_plan_t;

@@ -44,7 +44,8 @@ class pa_opts(ctypes.Structure):
                 ("force_fp64", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
                 ("fd_mode", ctypes.c_uint32), ("ntt_prime", ctypes.c_uint32),
                 ("fd_group", ctypes.c_uint32), ("seg_in", ctypes.c_uint32),
-                ("seg_out", ctypes.c_uint32), ("seg_cap_gib", ctypes.c_uint32)]
+                ("seg_out", ctypes.c_uint32), ("seg_cap_gib", ctypes.c_uint32),
+                ("outer_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class pa_plan_desc(ctypes.Structure):
@@ -57,7 +58,8 @@ class pa_plan_desc(ctypes.Structure):
                 ("fd", ctypes.c_uint32), ("windows", ctypes.c_uint64),
                 ("prime_bits", ctypes.c_uint32), ("sum_groups", ctypes.c_uint32),
                 ("seg_in", ctypes.c_uint32), ("seg_out", ctypes.c_uint32),
-                ("segments", ctypes.c_uint64)]
+                ("segments", ctypes.c_uint64), ("outer_log2", ctypes.c_uint32),
+                ("outer_slice", ctypes.c_uint32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -219,7 +221,7 @@ def _stream(s) -> int | None:
 
 def make_opts(path=PA_PATH_AUTO, device=-1, log2_transform=0, block_b=0, tile_in=0,
               tile_out=0, force_fp64=0, max_slots=0, fd_mode=0, ntt_prime=0,
-              fd_group=0, seg_in=0, seg_out=0, seg_cap_gib=0) -> pa_opts:
+              fd_group=0, seg_in=0, seg_out=0, seg_cap_gib=0, outer_mode=0) -> pa_opts:
     if isinstance(path, str):
         path = PATHS[path]
     o = pa_opts()
@@ -227,6 +229,7 @@ def make_opts(path=PA_PATH_AUTO, device=-1, log2_transform=0, block_b=0, tile_in
     o.tile_in, o.tile_out, o.force_fp64 = tile_in, tile_out, force_fp64
     o.max_slots, o.fd_mode, o.ntt_prime, o.fd_group = max_slots, fd_mode, ntt_prime, fd_group
     o.seg_in, o.seg_out, o.seg_cap_gib = seg_in, seg_out, seg_cap_gib
+    o.outer_mode = outer_mode
     return o
 
 

@@ -111,6 +111,8 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
         d->sum_groups = cfg.tr.fd == 1 && cfg.tr.kgroup
                             ? static_cast<uint32_t>(ceil_div(cfg.tr.tiles_in, cfg.tr.kgroup))
                             : (cfg.tr.fd ? 1u : 0u);
+        d->outer_log2 = cfg.tr.outer_logT;
+        d->outer_slice = cfg.tr.outer_slice;
         if (!cfg.tr.segs.empty()) {
             // every key segment has its own sums (one per kgroup key tiles of the segment)
             const uint64_t Sk = ceil_div(cfg.tr.tiles_in, cfg.tr.seg_in);

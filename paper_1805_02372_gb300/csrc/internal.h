@@ -54,6 +54,10 @@ struct TransformCfg {
     uint64_t windows = 0;        // NTT with fd: distinct seed-window spectra
     uint32_t kgroup = 0;         // NTT with fd = 1: key tiles per transform-domain sum (the
                                  // counts of a sum stay below the prime); 0 = all of them
+    uint32_t outer_logT = 0;     // NTT with fd = 1 and equal tiles: the sums of each group are
+    uint32_t outer_slice = 0;    // convolutions over the tile index, computed with 2^outer_logT-
+                                 // point transforms for slices of outer_slice output tiles
+                                 // (0 = direct sums)
     uint32_t seg_in = 0;         // NTT with fd = 1, segmented: key tiles per segment and
     uint32_t seg_out = 0;        // output tiles per slice (0 = everything resident at once);
                                  // each (slice, segment) is one persistent launch over one
@@ -161,6 +165,9 @@ struct SegChoice {
     uint64_t seg_cap = 0;          // bytes of spectra a segmented plan may hold (0 = default)
     uint32_t seg_in_force = 0, seg_out_force = 0;
     uint32_t seg_in = 0, seg_out = 0;  // out: the choice (0 = not segmented)
+    uint32_t outer_mode = 0;       // outer convolutions for the sums: 0 when cheaper, 1 never,
+                                   // 2 whenever possible
+    uint32_t outer_logT = 0, outer_slice = 0;  // out: the choice (0 = direct sums)
 };
 double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t M, uint64_t L,
                          uint32_t fd_mode, uint32_t fd_group, uint32_t *fd, uint64_t *windows,

@@ -230,6 +230,46 @@ uint64_t count_windows_bound(uint64_t P, uint64_t Q, uint64_t M, uint64_t L) {
     return P * Q;
 }
 
+// Outer convolutions for the sums of a P x Q geometry with equal tiles (window of (I, J)
+// = (Q - 1) + I - J) and key tiles grouped by g: per (group, output slice) three transforms
+// of T >= Ps + Qg - 1 points over the tile index for every bin, T products per bin, and
+// the sums' round trip through global memory before their inverse pass 2. Returns the
+// modelled cost in the units of the direct sums (3 N per (output, key tile) pair) and the
+// transform size and slice, or INFINITY when a group does not fit 2^kLogOuterMax points.
+double outer_cost(uint64_t P, uint64_t Q, uint64_t g, double N, uint32_t *logT, uint32_t *slice) {
+    const uint64_t Qg = std::min(g, Q), maxT = uint64_t(1) << kLogOuterMax;
+    if (P < 2 || Qg + 1 > maxT) return INFINITY;
+    uint64_t Ps = std::min<uint64_t>(P, maxT - Qg + 1);
+    const uint64_t slices = ceil_div(P, Ps);
+    Ps = ceil_div(P, slices);  // balanced slices
+    const uint32_t lt = std::max<uint32_t>(2, log2_ceil(Ps + Qg - 1));
+    const double T = double(uint64_t(1) << lt);
+    *logT = lt;
+    *slice = static_cast<uint32_t>(Ps);
+    // measured on the GB300 (n = 1e9, 3e9, 1e10 with l = 10%): an outer item takes about 2.3x
+    // the transform units of its three T-point transforms and products, the direct sums
+    // cost what their model says (n = 1e9: outer 1.8x the direct sums; 3e9: 0.74x)
+    constexpr double kOuterUnits = 2.3;
+    const double per = kOuterUnits * N * (T * (lt + 6) + 3.0 * T) + 2.0 * N * double(Ps);
+    return double(ceil_div(Q, g) * slices) * per;
+}
+
+// The sums of an fd geometry (resident, or one segment of P x Q tiles): direct products or
+// outer convolutions, whichever the model prices lower (or as forced); records the choice.
+double sums_cost(uint64_t P, uint64_t Q, uint64_t g, double N, uint64_t M, uint64_t L,
+                 SegChoice *seg) {
+    const double direct = double(P) * double(Q) * 3.0 * N;
+    if (!seg) return direct;
+    seg->outer_logT = seg->outer_slice = 0;
+    if (seg->outer_mode == 1 || L != M) return direct;
+    uint32_t lt = 0, sl = 0;
+    const double oc = outer_cost(P, Q, g, N, &lt, &sl);
+    if (!(oc < INFINITY) || (seg->outer_mode != 2 && !(oc < 0.8 * direct))) return direct;
+    seg->outer_logT = lt;
+    seg->outer_slice = sl;
+    return oc;
+}
+
 // Key tile for transform size 2^logn and output tile M: L = N - M rounded down to 32
 // bits (or the forced L), at most the key rounded up to 32 bits; 0 if none fits.
 uint64_t tile_in_for(uint64_t n, uint32_t logn, uint64_t M, uint64_t Lforce) {
@@ -259,7 +299,7 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
     *fd = 0;
     *windows = 0;
     *kgroup = 0;
-    if (seg) seg->seg_in = seg->seg_out = 0;
+    if (seg) seg->seg_in = seg->seg_out = seg->outer_logT = seg->outer_slice = 0;
     if (k > static_cast<uint32_t>(kLogMax) || M == 0 || L == 0 || L + M > (uint64_t(1) << k))
         return INFINITY;
     const double N = double(uint64_t(1) << k);
@@ -297,13 +337,14 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
     const uint64_t W = count_windows(P, Q, M, L);
     if (!forced_seg && double(Q + W + G * P) * N * elem <= double(kFdMaxBytes)) {
         const double fdc = double(Q + W) * (tr + 2 * N + 1024.0) + double(G * P) * (tr + N + 1024.0) +
-                           double(P) * double(Q) * 3.0 * N;
+                           sums_cost(P, Q, g, N, M, L, seg);
         if (fd_mode == 2 || big || fdc < 0.85 * std_units * pair) {
             *fd = 1;
             *windows = W;
             *kgroup = static_cast<uint32_t>(g);
             return fdc / pair;
         }
+        if (seg) seg->outer_logT = seg->outer_slice = 0;
         return std_units;
     }
     if (!seg || fd_mode == 1) return std_units;
@@ -327,8 +368,8 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
     if (So * Sk > kSegMax) return std_units;
     const uint64_t ws = count_windows_bound(so, si, M, L), gs = ceil_div(si, g);
     const double segc = double(So * Sk) * (double(si + ws) * (tr + 2 * N + 1024.0) +
-                                           double(gs * so) * (tr + N + 1024.0) + 4.0 * N) +
-                        double(P) * double(Q) * 3.0 * N;
+                                           double(gs * so) * (tr + N + 1024.0) + 4.0 * N +
+                                           sums_cost(so, si, g, N, M, L, seg));
     *fd = 1;
     *windows = ws * So * Sk;
     *kgroup = static_cast<uint32_t>(g);
@@ -361,8 +402,10 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
     seg.seg_cap = o ? uint64_t(o->seg_cap_gib) << 30 : 0;
     seg.seg_in_force = o ? o->seg_in : 0;
     seg.seg_out_force = o ? o->seg_out : 0;
+    seg.outer_mode = o ? o->outer_mode : 0;
+    if (seg.outer_mode > 2) return PA_ERR_INVALID;
     double best_cost = INFINITY;
-    uint32_t bk = 0, bfd = 0, bg = 0, bsi = 0, bso = 0;
+    uint32_t bk = 0, bfd = 0, bg = 0, bsi = 0, bso = 0, bot = 0, bos = 0;
     uint64_t bL = 0, bM = 0, bW = 0;
     for (uint32_t k = 5; k <= static_cast<uint32_t>(kLogMax); ++k) {
         if (force && k != force) continue;
@@ -396,6 +439,8 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
                 bg = g;
                 bsi = seg.seg_in;
                 bso = seg.seg_out;
+                bot = seg.outer_logT;
+                bos = seg.outer_slice;
             }
         }
     }
@@ -411,6 +456,8 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
     c->kgroup = bfd == 1 ? bg : 0;
     c->seg_in = bfd == 1 ? bsi : 0;
     c->seg_out = bfd == 1 ? bso : 0;
+    c->outer_logT = bfd == 1 ? bot : 0;
+    c->outer_slice = bfd == 1 ? bos : 0;
     if (bk <= static_cast<uint32_t>(kLogSmallMax)) {
         c->passes = 1;
         c->radix_log2[0] = bk;
@@ -459,13 +506,28 @@ NttTile tile_shape(uint32_t logN, int field) {
     return t;
 }
 
+// 1/T in the field's twiddle form (the scale of an outer convolution of T = 2^logT points).
+uint64_t outer_scale(int field, uint32_t logT) {
+    uint64_t bits = 0;
+    if (field == kFieldF31) {
+        const F31::Tw t = FieldHost<F31>::tw(powmod_host(uint64_t(1) << logT, F31::P - 2, F31::P));
+        memcpy(&bits, &t, sizeof(t));
+    } else if (field == kFieldF29) {
+        const F29::Tw t = FieldHost<F29>::tw(powmod_host(uint64_t(1) << logT, F29::P - 2, F29::P));
+        memcpy(&bits, &t, sizeof(t));
+    } else {
+        bits = powmod_host(uint64_t(1) << logT, F64::P - 2, F64::P);
+    }
+    return bits;
+}
+
 // The fd spectra and sums of one block, or of one segment of it (output tiles [I0, I1),
 // key tiles [J0, J1) of the BatchBlock): Q key spectra, W window spectra, P sums (P, Q
 // and every index below local to the segment), with element offsets relative to the start
 // of the block's fd storage.
 void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<NttTile> *spectra,
-              std::vector<NttTile> *sums, FdBlock *fb, std::vector<uint32_t> *wmap,
-              uint64_t *elems) {
+              std::vector<NttTile> *sums, std::vector<NttTile> *outers, FdBlock *fb,
+              std::vector<uint32_t> *wmap, uint64_t *elems) {
     const TransformCfg &c = b.tr;
     const uint64_t I0 = b.I0, I1 = b.I1 ? b.I1 : c.tiles_out;
     const uint64_t J0 = b.J0, J1 = b.J1 ? b.J1 : c.tiles_in;
@@ -527,6 +589,11 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
     // prime); sum tile g P + I covers key tiles [g kgroup, (g + 1) kgroup) of output tile I
     const uint64_t kg = (!streamed && c.kgroup) ? c.kgroup : Q;
     const uint64_t G = ceil_div(Q, kg);
+    // outer convolutions need consecutive windows: window (I, J) = (Q - 1) + I - J
+    fb->outer = (c.outer_logT && !streamed && fb->consec && c.L == c.M && P > 1 &&
+                 (*wmap)[w0] == Q - 1) ? 1u : 0u;
+    const size_t elem = field == kFieldF64 ? 8 : 4;
+    const size_t sum0 = sums->size();
     for (uint64_t g = 0; g < G; ++g)
         for (uint64_t I = 0; I < P; ++I) {
             NttTile t = shape;
@@ -536,6 +603,12 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
             t.jlo = static_cast<uint32_t>(g * kg);
             t.jhi = static_cast<uint32_t>(std::min(Q, (g + 1) * kg));
             t.ws_off = (Q + W + g * P + I) * N;
+            if (fb->outer) {
+                // written by the outer items of its slice, then an inverse pass 2 item per
+                // row group (the forward pass-2 shape) before the inverse pass 1
+                sums->push_back(t);
+                continue;
+            }
             if (streamed) {
                 // half the rows per sum item (key, window and accumulator columns share the
                 // shared memory two columns sets use elsewhere); the sum of row group rg
@@ -550,6 +623,37 @@ void build_fd(const BatchBlock &b, int field, uint32_t fd_index, std::vector<Ntt
             }
             sums->push_back(t);
         }
+    if (fb->outer) {
+        // one outer tile per (group, output slice); octr links them both ways (indices into
+        // the `sums` and `outers` vectors; the caller makes them tile-table indices)
+        const uint64_t maxT = uint64_t(1) << kLogOuterMax;
+        for (uint64_t g = 0; g < G; ++g) {
+            const uint64_t jlo = g * kg, jhi = std::min(Q, (g + 1) * kg), Qg = jhi - jlo;
+            uint64_t Ps = std::min<uint64_t>(P, maxT - Qg + 1);
+            const uint64_t slices = ceil_div(P, Ps);
+            Ps = ceil_div(P, slices);
+            for (uint64_t I0 = 0; I0 < P; I0 += Ps) {
+                const uint64_t ns = std::min(Ps, P - I0);
+                const uint32_t lt = std::max<uint32_t>(2, log2_ceil(ns + Qg - 1));
+                NttTile o = shape;
+                o.fd = fd_index;
+                o.out = static_cast<uint32_t>(I0);
+                o.nout = static_cast<uint32_t>(ns);
+                o.jlo = static_cast<uint32_t>(jlo);
+                o.jhi = static_cast<uint32_t>(jhi);
+                o.logT = lt;
+                o.logCo = static_cast<uint32_t>(outer_log_cols(static_cast<int>(lt), elem));
+                o.g2 = static_cast<uint32_t>(N >> o.logCo);
+                o.wb = static_cast<int32_t>((Q - 1) + I0 - jlo - (Qg - 1));
+                o.ws_off = (Q + W + g * P + I0) * N;
+                o.scale = outer_scale(field, lt);
+                o.octr = static_cast<uint32_t>(sum0 + g * P + I0);
+                for (uint64_t I = I0; I < I0 + ns; ++I)
+                    (*sums)[sum0 + g * P + I].octr = static_cast<uint32_t>(outers->size());
+                outers->push_back(o);
+            }
+        }
+    }
     *elems = streamed ? (Q + W) * N : (Q + W + G * P) * N;
 }
 
@@ -563,7 +667,7 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     const size_t elem = field == kFieldF64 ? 8 : 4, twsz = 8;
     // fd_*: blocks with accumulation over several output tiles; st_*: streamed blocks
     // (one output tile), with the range of their spectra in st_spec
-    std::vector<NttTile> big, small, fd_spec, fd_sum, st_spec, st_sum;
+    std::vector<NttTile> big, small, fd_spec, fd_sum, st_spec, st_sum, fd_outer;
     std::vector<std::pair<size_t, size_t>> st_range;
     std::vector<FdBlock> fds;
     std::vector<uint32_t> wmap;
@@ -582,12 +686,14 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
             const bool streamed = b.tr.fd == 2;
             std::vector<NttTile> &spec = streamed ? st_spec : fd_spec;
             std::vector<NttTile> &sum = streamed ? st_sum : fd_sum;
-            const size_t s0 = spec.size(), u0 = sum.size();
+            const size_t s0 = spec.size(), u0 = sum.size(), o0 = fd_outer.size();
             FdBlock fb{};
             uint64_t el = 0;
-            build_fd(b, field, static_cast<uint32_t>(fds.size()), &spec, &sum, &fb, &wmap, &el);
+            build_fd(b, field, static_cast<uint32_t>(fds.size()), &spec, &sum, &fd_outer, &fb, &wmap,
+                     &el);
             for (size_t i = s0; i < spec.size(); ++i) spec[i].ws_off += fd_elems;
             for (size_t i = u0; i < sum.size(); ++i) sum[i].ws_off += fd_elems;
+            for (size_t i = o0; i < fd_outer.size(); ++i) fd_outer[i].ws_off += fd_elems;
             if (streamed) st_range.push_back({s0, spec.size()});
             fb.x_off += fd_elems;
             fb.w_off += fd_elems;
@@ -617,7 +723,7 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     if (slots > big.size()) slots = big.size();
     for (size_t i = 0; i < big.size(); ++i) big[i].ws_off = (i % (slots ? slots : 1)) * slot_elems;
     const uint64_t fd_origin = uint64_t(slots) * slot_elems;  // fd storage after the slots
-    for (std::vector<NttTile> *v : {&fd_spec, &fd_sum, &st_spec, &st_sum})
+    for (std::vector<NttTile> *v : {&fd_spec, &fd_sum, &st_spec, &st_sum, &fd_outer})
         for (NttTile &t : *v) t.ws_off += fd_origin;
     for (FdBlock &f : fds) {
         f.x_off += fd_origin;
@@ -635,7 +741,15 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     tiles.insert(tiles.end(), st_spec.begin(), st_spec.end());
     const size_t i_ssum = tiles.size();
     tiles.insert(tiles.end(), st_sum.begin(), st_sum.end());
+    const size_t i_outer = tiles.size();
+    tiles.insert(tiles.end(), fd_outer.begin(), fd_outer.end());
     if (tiles.size() >= (size_t(1) << 28)) return PA_ERR_UNSUPPORTED;
+    // outer links as tile-table indices: a sum tile of an outer block points at its outer
+    // tile (whose pass-1 counter counts the outer items done), an outer tile at its first sum
+    for (size_t i = 0; i < fd_sum.size(); ++i)
+        if (fds[fd_sum[i].fd].outer) tiles[i_sum + i].octr = static_cast<uint32_t>(i_outer + fd_sum[i].octr);
+    for (size_t i = 0; i < fd_outer.size(); ++i)
+        tiles[i_outer + i].octr = static_cast<uint32_t>(i_sum + fd_outer[i].octr);
     std::vector<uint64_t> items;
     auto push = [&items](uint64_t type, uint64_t ti, uint64_t sub) {
         items.push_back((type << 60) | (ti << 32) | sub);
@@ -678,6 +792,10 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
         while (i < fd_sum.size()) {
             size_t j = i;
             while (j < fd_sum.size() && fd_sum[j].fd == fd_sum[i].fd) ++j;
+            if (fds[fd_sum[i].fd].outer) {  // outer convolutions instead (below)
+                i = j;
+                continue;
+            }
             // one item per row group and group of kSum4Out consecutive output tiles of one
             // group of sums (the block's sum tiles come in runs of P per group)
             const size_t P = fds[fd_sum[i].fd].P;
@@ -687,6 +805,12 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
             i = j;
         }
     }
+    // outer convolutions bin block by bin block, then the inverse pass 2 of their sums
+    for (size_t i = 0; i < fd_outer.size(); ++i)
+        for (uint32_t k = 0; k < fd_outer[i].g2; ++k) push(IT_FD_OUTER, i_outer + i, k);
+    for (size_t i = 0; i < fd_sum.size(); ++i)
+        if (fds[fd_sum[i].fd].outer)
+            for (uint32_t k = 0; k < fd_sum[i].g2; ++k) push(IT_FD_INV2, i_sum + i, k);
     for (size_t i = 0; i < fd_sum.size(); ++i)
         for (uint32_t k = 0; k < fd_sum[i].g1; ++k) push(IT_FD_P3, i_sum + i, k);
     for (size_t i = 0; i < small.size(); ++i) push(IT_SMALL, nb + i, 0);
@@ -717,10 +841,17 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     for (const NttTile &t : fd_spec)
         smem = std::max(smem, (size_t(1) << t.logR2) * twsz +
                                   size_t(ColMajor::words(1 << t.logR2, 1 << t.logC2)) * elem);
-    // fd sums: the inverse stage table and kSum4Out x C columns of R2 rows
+    // fd sums: the inverse stage table and kSum4Out x C columns of R2 rows; for outer
+    // blocks the inverse pass 2 of one sum (the stage table and C rows)
     for (const NttTile &t : fd_sum)
         smem = std::max(smem, (size_t(1) << t.logR2) * twsz +
-                                  size_t(ColMajor::words(1 << t.logR2, kSum4Out << t.logC2)) * elem);
+                                  size_t(ColMajor::words(1 << t.logR2, (fds[t.fd].outer ? 1 : kSum4Out)
+                                                                          << t.logC2)) * elem);
+    // outer convolutions: both stage tables of T points, the forward tile (2 C columns of
+    // T rows) and the product tile (C columns)
+    for (const NttTile &t : fd_outer)
+        smem = std::max(smem, 2 * (size_t(1) << t.logT) * twsz +
+                                  3 * (size_t(1) << (t.logT + t.logCo)) * elem);
     // streamed sums: key, window and accumulator columns, then the window indices
     for (const NttTile &t : st_sum)
         smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +

@@ -39,7 +39,9 @@ enum : uint32_t {
     IT_FD_P2 = 5,
     IT_FD_SUM = 6,
     IT_FD_P3 = 7,
-    IT_FD_STREAM = 8
+    IT_FD_STREAM = 8,
+    IT_FD_OUTER = 9,
+    IT_FD_INV2 = 10
 };
 
 // A transform of a launch: a standard tile pair, an fd spectrum or an fd output sum.
@@ -58,7 +60,27 @@ struct NttTile {
     uint32_t fd;      // fd spectra and sums: index of the fd block
     uint32_t out;     // fd sums: output tile index I
     uint32_t jlo, jhi;  // fd sums: the key tiles J in [jlo, jhi) this sum covers
+    // Outer convolutions (tiles of IT_FD_OUTER items, one per sum group and output slice):
+    // the sums Z_I = sum_J X_J W_{d0+I-J} of output tiles out .. out + nout - 1 over key
+    // tiles [jlo, jhi) are, bin by bin, a convolution over the tile index, computed with
+    // transforms of 2^logT points over it, 2^logCo bins per item; windows from index wb.
+    uint32_t logT, logCo, nout;
+    int32_t wb;
+    uint32_t octr;    // outer tiles: tile index of the sum tile of output `out` (the slice's
+                      // sums follow it); sum tiles of an outer group: tile index of their
+                      // outer tile, whose pass-1 counter counts the outer items done
+    uint32_t pad;
 };
+
+// Outer convolutions: transform sizes up to 2^kLogOuterMax over the tile index.
+constexpr int kLogOuterMax = 9;
+// Bins per outer item (log2): the forward tile holds 2 x 2^logCo columns and the product
+// tile 2^logCo, 3 x 2^(logT + logCo) elements in all (at most 12288 words of 32 bits).
+__host__ __device__ inline int outer_log_cols(int logT, size_t elem) {
+    const int budget = elem == 4 ? 12 : 11;  // log2 of T x C
+    const int minc = elem == 4 ? 3 : 2;      // rows of at least 32 bytes
+    return budget - logT > minc ? budget - logT : minc;
+}
 
 // One block under transform-domain accumulation.
 // Streamed blocks (one output tile) skip the separate forward pass 2: their sum items
@@ -73,6 +95,8 @@ struct FdBlock {
     uint32_t P;       // output tiles (per group of sums: sum tiles g P .. g P + P - 1)
     uint32_t consec;  // 1: the window of (I, J) is wmap[0][0] + I - J (equal key and output
                       // tiles: offsets (I - J) M), so sums can slide along J
+    uint32_t outer;   // 1: the sums are outer convolutions (IT_FD_OUTER, then IT_FD_INV2)
+    uint32_t pad;
 };
 
 // Four-step split N = R1 R2 of a two-pass transform: R1 = 2^ceil(logN/2) up to 2^22, and

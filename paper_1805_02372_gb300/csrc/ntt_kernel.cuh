@@ -612,6 +612,84 @@ __device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
     __syncthreads();
 }
 
+// Outer convolution for bins [k0, k0 + C) of one sum group and output slice: with
+// A_t = X_{jlo+t}[k] (t < Qg) and B_u = W_{wb+u}[k] (u < Ps + Qg - 1), the slice's sums are
+// Z_{out+i}[k] = sum_t A_t B_{i-t+Qg-1} = (A * B)[i + Qg - 1], taken from a cyclic
+// convolution of T >= Ps + Qg - 1 points over the tile index (outputs Qg - 1 .. Qg + Ps - 2
+// are unaliased), scaled by 1/T: the same field values the direct sums give. Shared memory:
+// the forward tile (T rows of [A_t | B_t], 2C columns), the product tile (T rows of C).
+template <class F>
+__device__ void body_outer(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
+                           uint64_t k0, int logT, int logCo, uint32_t Qg, uint32_t Ps,
+                           const typename F::T *__restrict__ X, const typename F::T *__restrict__ W,
+                           typename F::T *__restrict__ Z, uint64_t N, typename F::Tw tinv) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int R = 1 << logT, C = 1 << logCo;
+    const RowMajor lay2{logCo + 1}, lay{logCo};
+    T *fw = sm, *pr = sm + (R << (logCo + 1));
+    const uint32_t nb = Ps + Qg - 1;
+    const int vpr = C / V;  // 16-byte pieces per operand row
+    for (int e = threadIdx.x; e < 2 * R * vpr; e += blockDim.x) {
+        const int r = e / (2 * vpr), q = e - r * 2 * vpr;
+        const int which = q >= vpr, v = which ? q - vpr : q;
+        T *dst = fw + lay2.at(r, which * C + v * V);
+        if (which ? uint32_t(r) < nb : uint32_t(r) < Qg)
+            cp_async16(dst, (which ? W : X) + uint64_t(r) * N + k0 + v * V);
+        else
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    dif_columns<F, true>(fw, lay2, logT, logCo + 1, stf);
+    for (int e = threadIdx.x; e < (R << logCo); e += blockDim.x) {
+        const int r = e >> logCo, c = e & (C - 1);
+        pr[lay.at(r, c)] = F::mont(fw[lay2.at(r, c)], fw[lay2.at(r, C + c)]);
+    }
+    __syncthreads();
+    dit_columns<F, true>(pr, lay, logT, logCo, sti);
+    for (int e = threadIdx.x; e < int(Ps) * vpr; e += blockDim.x) {
+        const int i = e / vpr, v = e - i * vpr;
+        const T *src = pr + lay.at(i + int(Qg) - 1, v * V);
+        T o[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) o[k] = F::mul_tw(src[k], tinv);
+        __stcg(reinterpret_cast<uint4 *>(Z + uint64_t(i) * N + k0 + v * V), *reinterpret_cast<uint4 *>(o));
+    }
+    __syncthreads();
+}
+
+// Inverse pass 2 of one fd output spectrum in place: C = 2^logC rows of R2 = 2^logR2 from
+// row group rg (the mirror of body_fwd_last).
+template <class F>
+__device__ void body_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg, int logR2,
+                              int logC, typename F::T *__restrict__ A) {
+    using T = typename F::T;
+    constexpr int V = 16 / sizeof(T);
+    const int R2 = 1 << logR2;
+    const uint64_t base = (rg << logC) << logR2;
+    const ColMajor lay{ColMajor::stride(R2)};
+    const int cnt = R2 << logC;
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
+        const T *xs = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+    }
+    __syncthreads();
+    dit_columns<F, false>(sm, lay, logR2, logC, sti);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = e >> logR2, r = e & (R2 - 1);
+        uint4 ov;
+        T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
+        __stcg(reinterpret_cast<uint4 *>(A + base + e), ov);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- the persistent kernel
 //
 // CTAs pull items from the list with an atomic counter; the list is ordered so that
@@ -741,6 +819,30 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 signal_count(c2 + ti);
                 break;
             }
+            case IT_FD_OUTER: {  // bins [sub 2^logCo, +2^logCo) of one sum group and slice
+                const FdBlock fb = fds[tl.fd];
+                const int logT = static_cast<int>(tl.logT);
+                Tw *sti = st0 + (1 << logT);
+                if (k0 != logT) load_stage<F>(st0, stage, 0, logT);
+                if (k0 != logT || k1 != 32 + logT) load_stage<F>(sti, stage, 1, logT);
+                if (wait_count(cfd + tl.fd, fb.nfwd2, status, &flag)) {
+                    const uint64_t N = uint64_t(1) << logN;
+                    body_outer<F>(reinterpret_cast<T *>(sti + (1 << logT)), st0, sti,
+                                  uint64_t(sub) << tl.logCo, logT, static_cast<int>(tl.logCo),
+                                  tl.jhi - tl.jlo, tl.nout, ws + fb.x_off + uint64_t(tl.jlo) * N,
+                                  ws + fb.w_off + uint64_t(tl.wb) * N, X, N, scale);
+                }
+                signal_count(c1 + ti);
+                break;
+            }
+            case IT_FD_INV2: {  // inverse pass 2 of sum tile ti, row group sub (after the outer items)
+                if (k0 != 32 + logR2) load_stage<F>(st0, stage, 1, logR2);
+                if (wait_count(c1 + tl.octr, tiles[tl.octr].g2, status, &flag))
+                    body_inv_last<F>(reinterpret_cast<T *>(st0 + (1 << logR2)), st0, sub, logR2,
+                                     logC2, X);
+                signal_count(c2 + ti);
+                break;
+            }
             default: {  // IT_FD_P3
                 if (k0 != 32 + logR1) load_stage<F>(st0, stage, 1, logR1);
                 if (wait_count(c2 + ti, tl.g2, status, &flag))
@@ -760,7 +862,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<F>) ntt_persistent(
                 case IT_P3:
                 case IT_FD_P3: skey[0] = 32 + logR1; skey[1] = -1; break;
                 case IT_FD_P2: skey[0] = logR2; skey[1] = -1; break;
-                default: skey[0] = 32 + logR2; skey[1] = -1; break;  // IT_FD_SUM
+                case IT_FD_OUTER:
+                    skey[0] = static_cast<int>(tl.logT);
+                    skey[1] = 32 + static_cast<int>(tl.logT);
+                    break;
+                default: skey[0] = 32 + logR2; skey[1] = -1; break;  // IT_FD_SUM, IT_FD_INV2
             }
         }
     }

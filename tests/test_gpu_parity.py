@@ -296,6 +296,23 @@ def test_segmented_sums_full(path, seg_in, seg_out, fd_group):
     _check(path, n, m, key, seed, want, **opts)
 
 
+@pytest.mark.parametrize("path,opts", [("ntt31", {}), ("ntt31", {"ntt_prime": 31}), ("ntt64", {}),
+                                       ("ntt31", {"fd_group": 50}),
+                                       ("ntt31", {"seg_in": 60, "seg_out": 20}),
+                                       ("ntt31", {"fd_group": 40, "seg_in": 90, "seg_out": 25})])
+def test_outer_convolution_sums_full(path, opts):
+    # With equal key and output tiles the sums over key tiles are, bin by bin, convolutions
+    # over the tile index: 123 key x 37 output tiles of 2^14 at N = 2^15 with those sums
+    # forced to transforms over the tile index (one group, several groups, segments with
+    # ragged slices; the 29-, 31- and 64-bit fields), compared with the oracle in full.
+    n, m = 2_000_007, 600_003
+    key, seed, want = _case(n, m, 91, 92)
+    o = dict(log2_transform=15, tile_in=1 << 14, tile_out=1 << 14, fd_mode=2, outer_mode=2, **opts)
+    desc = pkg.pa_plan_query(n, m, binding.make_opts(path=path, **o))
+    assert desc["fd"] == 1 and desc["outer_log2"] > 0, desc
+    _check(path, n, m, key, seed, want, **o)
+
+
 def test_paper_scale_1e10_segmented_sampled_rows():
     # Fig. 3's upper range: a 1e10-bit key, l = 10%, beyond the resident accumulation cap:
     # the plan runs its sums in key segments through one fixed workspace (32 GiB of spectra
