@@ -20,6 +20,8 @@
 //   ColMajor: element (r, c) at c * (R + R/16) + r + (r >> 4) (one word of skew per 16).
 #pragma once
 
+#include <type_traits>
+
 #include "ntt_field.cuh"  // compile-time roots of the prime fields (root16_tw)
 
 namespace pa {
@@ -238,11 +240,117 @@ __device__ __forceinline__ void round_any(int S, typename F::T *sm, const Lay &l
     __syncthreads();
 }
 
+// Warp-local low rounds (ColMajor tiles of 32-bit elements, R >= 256). The rounds of
+// stride 16 and 1 (stage half-sizes 128 .. 1) keep every aligned 256-row block of a column
+// to itself, so a warp can take whole (column, block) pairs, one per half-warp, with lane j
+// running group j of both rounds, and order the two rounds with __syncwarp instead of a
+// barrier of the whole CTA. The two pairs of a warp are (c, b), (c, b + 1), or (c, 0),
+// (c + 1, 0) when R = 256: 272 words, 16 banks, apart, so every access of both rounds is
+// conflict-free. Pairs are numbered p = (c << (logR - 8)) + b.
+template <class F, class Lay>
+struct WarpLocal {
+    static constexpr bool value = sizeof(typename F::T) == 4 && std::is_same<Lay, ColMajor>::value;
+};
+
+template <class F, bool DIF>
+__device__ __forceinline__ void wl_round16(typename F::T *sm, const ColMajor &lay, int c, int blk,
+                                           int j, const typename F::Tw *tw) {
+    typename F::T x[16];
+    int a[16];
+    lay.template addrs<4, 16>((blk << 8) + j, c, a);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = sm[a[k]];
+    if (DIF)
+        dif_group<F, 4>(x, tw, j, 16);
+    else
+        dit_group<F, 4>(x, tw, j, 16);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sm[a[k]] = x[k];
+}
+
+template <class F, bool DIF>
+__device__ __forceinline__ void wl_round1(typename F::T *sm, const ColMajor &lay, int c, int i0,
+                                          const typename F::Tw *tw) {
+    typename F::T x[16];
+    int a[16];
+    lay.template addrs<0, 16>(i0, c, a);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = sm[a[k]];
+    if (DIF)
+        dif_group_q1<F, 4>(x, tw);
+    else
+        dit_group_q1<F, 4>(x, tw);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sm[a[k]] = x[k];
+}
+
+// Runs body(c, blk, l16) for every (column, block) pair of ncols columns, a half-warp per
+// pair (pairs beyond the last: on = false, the lanes still reach every __syncwarp).
+template <class Body>
+__device__ __forceinline__ void wl_pairs(int logR, int ncols, Body body) {
+    const int lane = threadIdx.x & 31;
+    const int lb = logR - 8;
+    const int npairs = ncols << lb;
+    for (int p0 = (threadIdx.x >> 5) * 2; p0 < npairs; p0 += (blockDim.x >> 5) * 2) {
+        const int p = p0 + (lane >> 4);
+        body(p < npairs, p >> lb, p & ((1 << lb) - 1), lane & 15);
+    }
+}
+
+// The eight low stages of an R-point transform on every column, warp-local (no CTA
+// barrier inside; the caller's barriers order them against the other rounds).
+template <class F, bool DIF>
+__device__ void low_rounds_warp(typename F::T *sm, const ColMajor &lay, int logR, int ncols,
+                                const typename F::Tw *tw) {
+    wl_pairs(logR, ncols, [&](bool on, int c, int blk, int j) {
+        if (DIF) {
+            if (on) wl_round16<F, true>(sm, lay, c, blk, j, tw);
+            __syncwarp();
+            if (on) wl_round1<F, true>(sm, lay, c, (blk << 8) + (j << 4), tw);
+        } else {
+            if (on) wl_round1<F, false>(sm, lay, c, (blk << 8) + (j << 4), tw);
+            __syncwarp();
+            if (on) wl_round16<F, false>(sm, lay, c, blk, j, tw);
+        }
+    });
+}
+
+// The forward rounds above the low eight stages (stride >= 256), each ending in a barrier.
+template <class F, bool CF, class Lay>
+__device__ __forceinline__ void dif_top_rounds(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                               const typename F::Tw *tw) {
+    int done = 0;
+    const int s0 = logR & 3;
+    if (s0 && logR > 8) {
+        round_any<F, true, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
+        done = s0;
+    }
+    for (; done < logR - 8; done += 4) round_any<F, true, CF>(4, sm, lay, logR, logC, logR - done - 4, tw);
+}
+
+// The inverse rounds above the low eight stages, in the order dit_columns runs them.
+template <class F, bool CF, class Lay>
+__device__ __forceinline__ void dit_top_rounds(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                               const typename F::Tw *tw) {
+    const int s0 = logR & 3;
+    for (int done = logR - 8; done > s0; done -= 4)
+        round_any<F, false, CF>(4, sm, lay, logR, logC, logR - done, tw);
+    if (s0 && logR > 8) round_any<F, false, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
+}
+
 // Forward R-point DIF on every column: a top round of logR mod 4 stages (if any), then
 // rounds of four stages down to the stage of half-size 1.
 template <class F, bool CF, class Lay>
 __device__ void dif_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                             const typename F::Tw *tw) {
+    if constexpr (!CF && WarpLocal<F, Lay>::value) {
+        if (logR >= 8) {
+            dif_top_rounds<F, CF>(sm, lay, logR, logC, tw);
+            low_rounds_warp<F, true>(sm, lay, logR, 1 << logC, tw);
+            __syncthreads();
+            return;
+        }
+    }
     int done = 0;
     const int s0 = logR & 3;
     if (s0) {
@@ -256,6 +364,14 @@ __device__ void dif_columns(typename F::T *sm, const Lay &lay, int logR, int log
 template <class F, bool CF, class Lay>
 __device__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                             const typename F::Tw *tw) {
+    if constexpr (!CF && WarpLocal<F, Lay>::value) {
+        if (logR >= 8) {
+            low_rounds_warp<F, false>(sm, lay, logR, 1 << logC, tw);
+            __syncthreads();
+            dit_top_rounds<F, CF>(sm, lay, logR, logC, tw);
+            return;
+        }
+    }
     const int s0 = logR & 3;
     for (int done = logR; done > s0; done -= 4)
         round_any<F, false, CF>(4, sm, lay, logR, logC, logR - done, tw);
@@ -287,68 +403,141 @@ __device__ void dit_columns_tail(typename F::T *sm, const Lay &lay, int logR, in
     if (s0) round_any<F, false, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
 }
 
-// For each of C column pairs (key column c, window column C + c): the last four forward
-// stages of both, the pointwise product Mul, the first four inverse stages of the
-// product, written over the window column. Groups are 16 consecutive rows (q = 1).
+// One group of 16 consecutive rows from i0 of key column cx and window column cy: the last
+// four forward stages of both, the pointwise product Mul, the first four inverse stages of
+// the product, written over the window column.
+template <class F, class Lay, class Mul>
+__device__ __forceinline__ void product_group(typename F::T *sm, const Lay &lay, int i0, int cx, int cy,
+                                              const typename F::Tw *twf, const typename F::Tw *twi,
+                                              Mul mul) {
+    using T = typename F::T;
+    T x[16], y[16];
+    int ax[16], ay[16];
+    lay.template addrs<0, 16>(i0, cx, ax);
+    lay.template addrs<0, 16>(i0, cy, ay);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        x[k] = sm[ax[k]];
+        y[k] = sm[ay[k]];
+    }
+    dif_group_q1<F, 4>(x, twf);
+    dif_group_q1<F, 4>(y, twf);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
+    dit_group_q1<F, 4>(y, twi);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sm[ay[k]] = y[k];
+}
+
+// One group of 16 consecutive rows from i0: the last four forward stages of key column cx
+// and window column cy, and column cz += their pointwise product Mul (field addition Add).
+template <class F, class Lay, class Mul, class Add>
+__device__ __forceinline__ void product_acc_group(typename F::T *sm, const Lay &lay, int i0, int cx,
+                                                  int cy, int cz, const typename F::Tw *twf, Mul mul,
+                                                  Add add) {
+    using T = typename F::T;
+    T x[16], y[16];
+    int ax[16], ay[16], az[16];
+    lay.template addrs<0, 16>(i0, cx, ax);
+    lay.template addrs<0, 16>(i0, cy, ay);
+    lay.template addrs<0, 16>(i0, cz, az);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        x[k] = sm[ax[k]];
+        y[k] = sm[ay[k]];
+    }
+    dif_group_q1<F, 4>(x, twf);
+    dif_group_q1<F, 4>(y, twf);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sm[az[k]] = add(sm[az[k]], mul(x[k], y[k]));
+}
+
+// For each of C column pairs (key column c, window column C + c): product_group on every
+// group of 16 rows.
 template <class F, class Lay, class Mul>
 __device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int logC,
                               const typename F::Tw *twf, const typename F::Tw *twi, Mul mul) {
-    using T = typename F::T;
     const int logG = logR - 4;
     const int C = 1 << logC;
     const int total = 1 << (logG + logC);
     for (int w = threadIdx.x; w < total; w += blockDim.x) {
         const int g = w & ((1 << logG) - 1), c = w >> logG;
-        const int i0 = g << 4;
-        T x[16], y[16];
-        int ax[16], ay[16];
-        lay.template addrs<0, 16>(i0, c, ax);
-        lay.template addrs<0, 16>(i0, C + c, ay);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            x[k] = sm[ax[k]];
-            y[k] = sm[ay[k]];
-        }
-        dif_group_q1<F, 4>(x, twf);
-        dif_group_q1<F, 4>(y, twf);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
-        dit_group_q1<F, 4>(y, twi);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sm[ay[k]] = y[k];
+        product_group<F>(sm, lay, g << 4, c, C + c, twf, twi, mul);
     }
     __syncthreads();
 }
 
-// For each of C column pairs (key column c, window column C + c): the last four forward
-// stages of both and acc[c] += the pointwise product Mul (field addition Add), where the
-// accumulator column c lives at acc_col0 + c. Groups are 16 consecutive rows (q = 1).
+// For each of C column pairs: product_acc_group into the accumulator column acc_col0 + c.
 template <class F, class Lay, class Mul, class Add>
 __device__ void product_acc_round(typename F::T *sm, const Lay &lay, int logR, int logC,
                                   int acc_col0, const typename F::Tw *twf, Mul mul, Add add) {
-    using T = typename F::T;
     const int logG = logR - 4;
     const int C = 1 << logC;
     const int total = 1 << (logG + logC);
     for (int w = threadIdx.x; w < total; w += blockDim.x) {
         const int g = w & ((1 << logG) - 1), c = w >> logG;
-        const int i0 = g << 4;
-        T x[16], y[16];
-        int ax[16], ay[16], az[16];
-        lay.template addrs<0, 16>(i0, c, ax);
-        lay.template addrs<0, 16>(i0, C + c, ay);
-        lay.template addrs<0, 16>(i0, acc_col0 + c, az);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            x[k] = sm[ax[k]];
-            y[k] = sm[ay[k]];
-        }
-        dif_group_q1<F, 4>(x, twf);
-        dif_group_q1<F, 4>(y, twf);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sm[az[k]] = add(sm[az[k]], mul(x[k], y[k]));
+        product_acc_group<F>(sm, lay, g << 4, c, C + c, acc_col0 + c, twf, mul, add);
     }
     __syncthreads();
+}
+
+// Forward transforms of C key columns and C window columns (column C + c), their pointwise
+// products, and the inverse transforms of the products over the window columns: for
+// R >= 256 (32-bit elements) the stages below half-size 256 of both spectra, the product
+// and the first inverse stages run warp-local per (column, block) pair, between the
+// CTA-wide top rounds.
+template <class F, class Mul>
+__device__ void product_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
+                                const typename F::Tw *twf, const typename F::Tw *twi, Mul mul) {
+    const int C = 1 << logC;
+    if constexpr (WarpLocal<F, ColMajor>::value) {
+        if (logR >= 8) {
+            dif_top_rounds<F, false>(sm, lay, logR, logC + 1, twf);
+            wl_pairs(logR, C, [&](bool on, int c, int blk, int j) {
+                if (on) {
+                    wl_round16<F, true>(sm, lay, c, blk, j, twf);
+                    wl_round16<F, true>(sm, lay, C + c, blk, j, twf);
+                }
+                __syncwarp();
+                if (on) product_group<F>(sm, lay, (blk << 8) + (j << 4), c, C + c, twf, twi, mul);
+                __syncwarp();
+                if (on) wl_round16<F, false>(sm, lay, C + c, blk, j, twi);
+            });
+            __syncthreads();
+            dit_top_rounds<F, false>(sm + C * lay.cs, lay, logR, logC, twi);
+            return;
+        }
+    }
+    dif_columns_head<F, false>(sm, lay, logR, logC + 1, twf);
+    product_round<F>(sm, lay, logR, logC, twf, twi, mul);
+    dit_columns_tail<F, false>(sm + C * lay.cs, lay, logR, logC, twi);
+}
+
+// Forward transforms of C key and C window columns and acc[c] += their pointwise products
+// (accumulator column acc_col0 + c), warp-local below the top rounds as in product_columns.
+template <class F, class Mul, class Add>
+__device__ void product_acc_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
+                                    int acc_col0, const typename F::Tw *twf, Mul mul, Add add) {
+    const int C = 1 << logC;
+    if constexpr (WarpLocal<F, ColMajor>::value) {
+        if (logR >= 8) {
+            dif_top_rounds<F, false>(sm, lay, logR, logC + 1, twf);
+            wl_pairs(logR, C, [&](bool on, int c, int blk, int j) {
+                if (on) {
+                    wl_round16<F, true>(sm, lay, c, blk, j, twf);
+                    wl_round16<F, true>(sm, lay, C + c, blk, j, twf);
+                }
+                __syncwarp();
+                if (on)
+                    product_acc_group<F>(sm, lay, (blk << 8) + (j << 4), c, C + c, acc_col0 + c, twf,
+                                         mul, add);
+            });
+            __syncthreads();
+            return;
+        }
+    }
+    dif_columns_head<F, false>(sm, lay, logR, logC + 1, twf);
+    product_acc_round<F>(sm, lay, logR, logC, acc_col0, twf, mul, add);
 }
 
 }  // namespace pa

@@ -297,9 +297,7 @@ __device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
     }
     __syncthreads();
     // logR2 >= 6 for every two-pass transform (N >= 2^13)
-    dif_columns_head<F, false>(sm, lay, logR2, logC + 1, stf);
-    product_round<F>(sm, lay, logR2, logC, stf, sti, [](T a, T b) { return F::mont(a, b); });
-    dit_columns_tail<F, false>(sm + C * lay.cs, lay, logR2, logC, sti);
+    product_columns<F>(sm, lay, logR2, logC, stf, sti, [](T a, T b) { return F::mont(a, b); });
     for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
         const int c = e >> logR2, r = e & (R2 - 1);
         uint4 ov;
@@ -595,10 +593,9 @@ __device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
             }
         }
         __syncthreads();
-        dif_columns_head<F, false>(sm, lay, logR2, logC + 1, stf);
-        product_acc_round<F>(sm, lay, logR2, logC, 2 * C, stf,
-                             [](T a, T b) { return F::mont(a, b); },
-                             [](T a, T b) { return F::add(a, b); });
+        product_acc_columns<F>(sm, lay, logR2, logC, 2 * C, stf,
+                               [](T a, T b) { return F::mont(a, b); },
+                               [](T a, T b) { return F::add(a, b); });
     }
     dit_columns<F, false>(acc, lay, logR2, logC, sti);
     for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
