@@ -378,6 +378,33 @@ __device__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int log
     if (s0) round_any<F, false, CF>(s0, sm, lay, logR, logC, logR - s0, tw);
 }
 
+// dif_columns without its first stage (half-size R/2), for a caller that ran that stage
+// while loading the tile: the remaining stages, half-sizes R/4 .. 1, in rounds of
+// (logR - 1) mod 4 (if any) and then four stages.
+template <class F, bool CF, class Lay>
+__device__ void dif_columns_after_first(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                        const typename F::Tw *tw) {
+    const int rem = logR - 1, s0 = rem & 3;
+    int done = 0;
+    if (s0) {
+        round_any<F, true, CF>(s0, sm, lay, logR, logC, rem - s0, tw);
+        done = s0;
+    }
+    for (; done < rem; done += 4) round_any<F, true, CF>(4, sm, lay, logR, logC, rem - done - 4, tw);
+}
+
+// dit_columns without its last stage (half-size R/2), for a caller that runs that stage on
+// the rows it writes out: stages of half-size 1 .. R/4, in the reverse order of
+// dif_columns_after_first.
+template <class F, bool CF, class Lay>
+__device__ void dit_columns_but_last(typename F::T *sm, const Lay &lay, int logR, int logC,
+                                     const typename F::Tw *tw) {
+    const int rem = logR - 1, s0 = rem & 3;
+    for (int done = rem; done > s0; done -= 4)
+        round_any<F, false, CF>(4, sm, lay, logR, logC, rem - done, tw);
+    if (s0) round_any<F, false, CF>(s0, sm, lay, logR, logC, rem - s0, tw);
+}
+
 // The forward rounds of dif_columns except the last (the four stages of half-size 8..1),
 // and the inverse rounds of dit_columns except the first: the caller runs those two in
 // registers around the pointwise product (product_round). Needs logR >= 4.

@@ -615,42 +615,103 @@ __device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
 // convolution of T >= Ps + Qg - 1 points over the tile index (outputs Qg - 1 .. Qg + Ps - 2
 // are unaliased), scaled by 1/T: the same field values the direct sums give. Shared memory:
 // the forward tile (T rows of [A_t | B_t], 2C columns), the product tile (T rows of C).
+// When log2 T = 1 mod 4 (a one-stage round in the usual split), the forward transform's first
+// stage (rows r, r + T/2) runs on the rows as they are loaded and the inverse's last stage
+// only on the Ps rows written out, so that no round is that short.
 template <class F>
 __device__ void body_outer(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
                            uint64_t k0, int logT, int logCo, uint32_t Qg, uint32_t Ps,
                            const typename F::T *__restrict__ X, const typename F::T *__restrict__ W,
                            typename F::T *__restrict__ Z, uint64_t N, typename F::Tw tinv) {
     using T = typename F::T;
+    using Tw = typename F::Tw;
     constexpr int V = 16 / sizeof(T);
-    const int R = 1 << logT, C = 1 << logCo;
+    const int R = 1 << logT, C = 1 << logCo, H = R >> 1;
     const RowMajor lay2{logCo + 1}, lay{logCo};
     T *fw = sm, *pr = sm + (R << (logCo + 1));
     const uint32_t nb = Ps + Qg - 1;
     const int vpr = C / V;  // 16-byte pieces per operand row
-    for (int e = threadIdx.x; e < 2 * R * vpr; e += blockDim.x) {
-        const int r = e / (2 * vpr), q = e - r * 2 * vpr;
-        const int which = q >= vpr, v = which ? q - vpr : q;
-        T *dst = fw + lay2.at(r, which * C + v * V);
-        if (which ? uint32_t(r) < nb : uint32_t(r) < Qg)
-            cp_async16(dst, (which ? W : X) + uint64_t(r) * N + k0 + v * V);
-        else
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    const bool fuse = (logT & 3) == 1;
+    const int units = 2 * H * vpr;
+    if (!fuse) {
+        for (int e = threadIdx.x; e < 2 * R * vpr; e += blockDim.x) {
+            const int r = e / (2 * vpr), q = e - r * 2 * vpr;
+            const int which = q >= vpr, v = which ? q - vpr : q;
+            T *dst = fw + lay2.at(r, which * C + v * V);
+            if (which ? uint32_t(r) < nb : uint32_t(r) < Qg)
+                cp_async16(dst, (which ? W : X) + uint64_t(r) * N + k0 + v * V);
+            else
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
+    // fused: two (row pair, piece) units per thread at a time, their four loads issued together
+    for (int e0 = threadIdx.x; fuse && e0 < units; e0 += 2 * blockDim.x) {
+        uint4 lo[2], hi[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * blockDim.x;
+            lo[u] = hi[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (e < units) {
+                const int r = e / (2 * vpr), q = e - r * 2 * vpr;
+                const int which = q >= vpr, v = which ? q - vpr : q;
+                const uint32_t lim = which ? nb : Qg;
+                const T *src = (which ? W : X) + k0 + v * V;
+                if (uint32_t(r) < lim) lo[u] = __ldcg(reinterpret_cast<const uint4 *>(src + uint64_t(r) * N));
+                if (uint32_t(r + H) < lim)
+                    hi[u] = __ldcg(reinterpret_cast<const uint4 *>(src + uint64_t(r + H) * N));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= units) break;
+            const int r = e / (2 * vpr), q = e - r * 2 * vpr;
+            const int col = (q >= vpr ? C : 0) + (q >= vpr ? q - vpr : q) * V;
+            T *a = reinterpret_cast<T *>(&lo[u]), *b = reinterpret_cast<T *>(&hi[u]);
+            const Tw w = stf[H - 1 + r];
+#pragma unroll
+            for (int k = 0; k < V; ++k) F::dif_bfly(a[k], b[k], w);
+            *reinterpret_cast<uint4 *>(fw + lay2.at(r, col)) = lo[u];
+            *reinterpret_cast<uint4 *>(fw + lay2.at(r + H, col)) = hi[u];
+        }
+    }
     __syncthreads();
-    dif_columns<F, true>(fw, lay2, logT, logCo + 1, stf);
+    if (fuse)
+        dif_columns_after_first<F, true>(fw, lay2, logT, logCo + 1, stf);
+    else
+        dif_columns<F, true>(fw, lay2, logT, logCo + 1, stf);
     for (int e = threadIdx.x; e < (R << logCo); e += blockDim.x) {
         const int r = e >> logCo, c = e & (C - 1);
         pr[lay.at(r, c)] = F::mont(fw[lay2.at(r, c)], fw[lay2.at(r, C + c)]);
     }
     __syncthreads();
-    dit_columns<F, true>(pr, lay, logT, logCo, sti);
+    if (!fuse) {
+        dit_columns<F, true>(pr, lay, logT, logCo, sti);
+        for (int e = threadIdx.x; e < int(Ps) * vpr; e += blockDim.x) {
+            const int i = e / vpr, v = e - i * vpr;
+            const T *src = pr + lay.at(i + int(Qg) - 1, v * V);
+            T o[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) o[k] = F::mul_tw(src[k], tinv);
+            __stcg(reinterpret_cast<uint4 *>(Z + uint64_t(i) * N + k0 + v * V), *reinterpret_cast<uint4 *>(o));
+        }
+        __syncthreads();
+        return;
+    }
+    dit_columns_but_last<F, true>(pr, lay, logT, logCo, sti);
     for (int e = threadIdx.x; e < int(Ps) * vpr; e += blockDim.x) {
         const int i = e / vpr, v = e - i * vpr;
-        const T *src = pr + lay.at(i + int(Qg) - 1, v * V);
+        const int y = i + int(Qg) - 1, j = y & (H - 1);
+        const T *pa = pr + lay.at(j, v * V), *pb = pr + lay.at(j + H, v * V);
+        const Tw w = sti[H - 1 + j];
         T o[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) o[k] = F::mul_tw(src[k], tinv);
+        for (int k = 0; k < V; ++k) {
+            T a = pa[k], b = pb[k];
+            F::dit_bfly(a, b, w);
+            o[k] = F::mul_tw(y < H ? a : b, tinv);
+        }
         __stcg(reinterpret_cast<uint4 *>(Z + uint64_t(i) * N + k0 + v * V), *reinterpret_cast<uint4 *>(o));
     }
     __syncthreads();

@@ -313,6 +313,20 @@ def test_outer_convolution_sums_full(path, opts):
     _check(path, n, m, key, seed, want, **o)
 
 
+@pytest.mark.parametrize("path,m,opts,logT", [("ntt31", 163_843, {}, 9), ("ntt31", 163_843, {"ntt_prime": 31}, 9),
+                                              ("ntt64", 163_843, {}, 9), ("ntt31", 49_157, {"fd_group": 10}, 5)])
+def test_outer_convolution_fused_stages_full(path, m, opts, logT):
+    # Outer transforms of 2^9 and 2^5 points over the tile index (log2 T = 1 mod 4: the
+    # first forward stage runs as the rows are loaded, the last inverse stage only on the
+    # rows written out): 301 key tiles of 2^12 at N = 2^13, compared with the oracle in full.
+    n = 1_228_807
+    key, seed, want = _case(n, m, 93, 94)
+    o = dict(log2_transform=13, tile_in=1 << 12, tile_out=1 << 12, fd_mode=2, outer_mode=2, **opts)
+    desc = pkg.pa_plan_query(n, m, binding.make_opts(path=path, **o))
+    assert desc["fd"] == 1 and desc["tiles_in"] == 301 and desc["outer_log2"] == logT, desc
+    _check(path, n, m, key, seed, want, **o)
+
+
 def test_paper_scale_1e10_segmented_sampled_rows():
     # Fig. 3's upper range: a 1e10-bit key, l = 10%, beyond the resident accumulation cap:
     # the plan runs its sums in key segments through one fixed workspace (32 GiB of spectra
