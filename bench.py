@@ -261,7 +261,8 @@ CSRC = "paper_1805_02372_gb300/csrc/"
 KERNEL_SOURCES = {
     "direct": [CSRC + "direct.cu", CSRC + "common.cuh"],
     "batch_persistent": [CSRC + "ntt.cu", CSRC + "ntt_defs.cuh", CSRC + "ntt_kernel.cuh",
-                         CSRC + "ntt_f29.cu", CSRC + "ntt_f31.cu", CSRC + "ntt_f64.cu",
+                         CSRC + "ntt_f28.cu", CSRC + "ntt_f29.cu", CSRC + "ntt_f31.cu",
+                         CSRC + "ntt_f64.cu",
                          CSRC + "dft.cuh", CSRC + "ntt_field.cuh", CSRC + "tiles.cuh",
                          CSRC + "common.cuh", CSRC + "internal.h"],
     "fft_tile": [CSRC + "fft.cu", CSRC + "dft.cuh", CSRC + "tiles.cuh"],
@@ -280,36 +281,40 @@ OPS_PER_BFLY = 8
 
 
 def ntt_work(descs):
-    """(butterflies, multiply-adds) of the NTT blocks: a standard tile pair of size N is
-    two forward transforms and one inverse, (N/2) log2 N butterflies each, and N pointwise
-    products; a block under transform-domain accumulation computes its Q key, W window and
-    G P output transforms once (G sums per output tile) and sums P Q N products."""
-    bfly = prod = 0.0
+    """(butterflies by prime bits, multiply-adds) of the NTT blocks: a standard tile pair of
+    size N is two forward transforms and one inverse, (N/2) log2 N butterflies each, and N
+    pointwise products; a block under transform-domain accumulation computes its Q key, W
+    window and G P output transforms once (G sums per output tile) and sums P Q N products."""
+    bfly = {}
+    prod = 0.0
     for d in descs:
         if d["path_name"] not in ("ntt31", "ntt64"):
             continue
+        pb = d.get("prime_bits") or 29
         k = d["log2_transform"]
         N = 2.0 ** k
         P, Q = d["tiles_out"], d["tiles_in"]
+        b = 0.0
         if d.get("fd"):
             # segmented sums recompute the key spectra once per output slice; `windows` and
             # `sum_groups` count every segment's
             G = d.get("sum_groups") or 1
             so = d.get("seg_out") or P
             keys = Q * -(-P // so)
-            bfly += (keys + d["windows"] + G * P) * (N / 2) * k
+            b += (keys + d["windows"] + G * P) * (N / 2) * k
             if d.get("outer_log2"):
                 # sums as convolutions over the tile index: per (group, output slice) three
                 # T-point transforms and T products for every bin
                 T, lt = 2.0 ** d["outer_log2"], d["outer_log2"]
                 conv = G * -(-P // so) * -(-so // d["outer_slice"])
-                bfly += conv * N * 3 * (T / 2) * lt
+                b += conv * N * 3 * (T / 2) * lt
                 prod += conv * N * T
             else:
                 prod += P * Q * N
         else:
-            bfly += P * Q * 3 * (N / 2) * k
+            b += P * Q * 3 * (N / 2) * k
             prod += P * Q * N
+        bfly[pb] = bfly.get(pb, 0.0) + b
     return bfly, prod
 
 
@@ -346,13 +351,21 @@ def algorithmic(kernel: str, blocks, descs, probe):
         bfly, prod = ntt_work(descs)
         if not probe:
             return None, None, None, None, None
-        t_peak = bfly / probe["butterfly_per_s"] + prod / probe["muladd_per_s"]
-        return ("alu", OPS_PER_BFLY * (bfly + prod), "Tops/s", t_peak,
-                f"measured in this run: pa_probe_peak butterflies "
-                f"{probe['butterfly_per_s'] / 1e12:.3f} T/s and multiply-adds "
-                f"{probe['muladd_per_s'] / 1e12:.3f} T/s of the 29-bit field in registers "
-                f"on all SMs; peak time = {bfly:.4g} butterflies / that + {prod:.4g} "
-                f"multiply-adds / that; {OPS_PER_BFLY} ops per butterfly or multiply-add")
+        # butterflies at the measured rate of their field's radix-16 groups (the kernel's
+        # rounds; fields without a group probe at the single-butterfly rate)
+        rate = {28: probe["group28_per_s"], 29: probe["group29_per_s"]}
+        t_peak = sum(b / rate.get(pb, probe["butterfly_per_s"]) for pb, b in bfly.items())
+        t_peak += prod / probe["muladd_per_s"]
+        nb = sum(bfly.values())
+        fields = ", ".join(f"{b:.4g} over the {pb}-bit prime" for pb, b in sorted(bfly.items()))
+        return ("alu", OPS_PER_BFLY * (nb + prod), "Tops/s", t_peak,
+                f"measured in this run: pa_probe_peak radix-16 butterfly groups of the 28-bit "
+                f"field {probe['group28_per_s'] / 1e12:.3f} T/s and of the 29-bit field "
+                f"{probe['group29_per_s'] / 1e12:.3f} T/s (the kernel's rounds: lazy reduction "
+                f"schedule, twiddles from shared memory, values in registers, on all SMs), "
+                f"multiply-adds {probe['muladd_per_s'] / 1e12:.3f} T/s; peak time = butterflies "
+                f"({fields}) / their field's rate + {prod:.4g} multiply-adds / that; "
+                f"{OPS_PER_BFLY} ops per butterfly or multiply-add")
     if kernel == "block_mma":
         ops = sum(2.0 * b.m * (b.n + 8192) for b, d in zip(blocks, descs)
                   if d["path_name"] == "block_int8")
@@ -608,17 +621,22 @@ def probe_peaks():
     """Issue-rate peaks of this GPU for the integer paths' operations (pa_probe_peak)."""
     from paper_1805_02372_gb300 import binding
     b, bms = binding.pa_probe_peak(binding.PA_PEAK_NTT_BUTTERFLY)
+    g28, g28ms = binding.pa_probe_peak(binding.PA_PEAK_NTT_GROUP28)
+    g29, g29ms = binding.pa_probe_peak(binding.PA_PEAK_NTT_GROUP29)
     ma, mms = binding.pa_probe_peak(binding.PA_PEAK_NTT_MULADD)
     sa, sms = binding.pa_probe_peak(binding.PA_PEAK_SHIFT_AND)
     s8, s8ms = binding.pa_probe_peak(binding.PA_PEAK_MMA_S8)
     b1, b1ms = binding.pa_probe_peak(binding.PA_PEAK_MMA_B1)
-    return {"butterfly_per_s": b, "muladd_per_s": ma, "shift_and_per_s": sa,
+    return {"butterfly_per_s": b, "group28_per_s": g28, "group29_per_s": g29,
+            "muladd_per_s": ma, "shift_and_per_s": sa,
             "mma_s8_macs_per_s": s8, "mma_b1_and_popc_per_s": b1,
-            "launch_ms": {"butterfly": bms, "muladd": mms, "shift_and": sms, "mma_s8": s8ms,
-                          "mma_b1": b1ms},
-            "what": "29-bit-field lazy butterfly, 29-bit-field multiply-add, funnel-shift "
-                    "AND-XOR, mma.sync m16n8k32 s8 and m16n8k256 b1 AND-POPC: register-only "
-                    "chains on every SM, fastest of three ~20 ms launches after a warm-up"}
+            "launch_ms": {"butterfly": bms, "group28": g28ms, "group29": g29ms, "muladd": mms,
+                          "shift_and": sms, "mma_s8": s8ms, "mma_b1": b1ms},
+            "what": "29-bit-field single lazy butterfly; radix-16 forward and inverse groups of "
+                    "the 28- and 29-bit fields as the NTT rounds run them (twiddles from shared "
+                    "memory); 29-bit-field multiply-add; funnel-shift AND-XOR; mma.sync "
+                    "m16n8k32 s8 and m16n8k256 b1 AND-POPC: chains in registers on every SM, "
+                    "fastest of three ~20 ms launches after a warm-up"}
 
 
 def binary_mma_record(probe, fp8_rec):

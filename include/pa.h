@@ -82,7 +82,10 @@ typedef struct {
                                   (each key and seed-window spectrum computed once, one
                                   inverse per output sub-block). 0 = when the planner
                                   estimates it faster, 1 = never, 2 = whenever possible   */
-    uint32_t ntt_prime;        /* PA_PATH_NTT31: 0 or 29 = 7*2^26+1, 31 = 15*2^27+1. Any n:
+    uint32_t ntt_prime;        /* PA_PATH_NTT31: 28 = 5*2^25+1, 29 = 7*2^26+1, 31 =
+                                  15*2^27+1; 0 = 28 when n < 5*2^25+1 (no count exceeds
+                                  n), else 29 (the lazily reduced 28-bit field's
+                                  transforms take fewer reduction steps). Any n:
                                   a tile pair's counts are at most L < p, and a transform-
                                   domain sum covers at most (p-1)/L key sub-blocks (longer
                                   keys take several sums per output sub-block, their bits
@@ -122,7 +125,7 @@ typedef struct {
     uint32_t kernels_per_call; /* kernel launches one pa_hash enqueues                    */
     uint32_t fd;               /* NTT: transform-domain accumulation (see pa_opts.fd_mode) */
     uint64_t windows;          /* with fd: seed-window spectra computed (distinct offsets) */
-    uint32_t prime_bits;       /* NTT paths: bits of the prime (29, 31 or 64), else 0     */
+    uint32_t prime_bits;       /* NTT paths: bits of the prime (28, 29, 31 or 64), else 0 */
     uint32_t sum_groups;       /* with fd: transform-domain sums per output sub-block     */
     uint32_t seg_in;           /* segmented fd: key sub-blocks per segment, else 0        */
     uint32_t seg_out;          /* segmented fd: output sub-blocks per slice, else 0       */
@@ -362,14 +365,20 @@ int pa_selftest(int which, int *device_status);
  *           instruction (one operation = one multiply-accumulate);
  *   which = PA_PEAK_MMA_B1: warp-level mma.sync m16n8k256 b1 AND + POPC -> s32, the binary
  *           form of the block contraction (one operation = one 1-bit AND product summed).
+ *   which = PA_PEAK_NTT_GROUP28, PA_PEAK_NTT_GROUP29: radix-16 butterfly groups of the
+ *           28-bit (5*2^25+1) or 29-bit field as the NTT kernel's rounds run them (lazy
+ *           reduction schedule, twiddles read from shared memory), forward and inverse
+ *           groups alike (one operation = one butterfly).
  * *ops_per_s: the fastest of three launches of about 20 ms (after a warm-up);
- * *ms (nullable): that launch's device time. Synchronous; allocates 256 bytes of device
+ * *ms (nullable): that launch's device time. Synchronous; allocates at most 4 KB of device
  * memory for the duration of the call. PA_ERR_INVALID for another `which`. */
 #define PA_PEAK_NTT_BUTTERFLY 1
 #define PA_PEAK_NTT_MULADD 2
 #define PA_PEAK_SHIFT_AND 3
 #define PA_PEAK_MMA_S8 4
 #define PA_PEAK_MMA_B1 5
+#define PA_PEAK_NTT_GROUP28 6
+#define PA_PEAK_NTT_GROUP29 7
 int pa_probe_peak(int which, double *ops_per_s, double *ms);
 
 const char *pa_strerror(int status);

@@ -460,6 +460,8 @@ PA_PEAK_NTT_MULADD = 2
 PA_PEAK_SHIFT_AND = 3
 PA_PEAK_MMA_S8 = 4
 PA_PEAK_MMA_B1 = 5
+PA_PEAK_NTT_GROUP28 = 6
+PA_PEAK_NTT_GROUP29 = 7
 
 
 def pa_probe_peak(which: int) -> tuple[float, float]:

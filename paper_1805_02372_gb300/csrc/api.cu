@@ -122,7 +122,10 @@ void fill_desc(const PlanCfg &cfg, pa_plan_desc *d) {
             d->segments = cfg.tr.segs.size();
         }
         if (cfg.path == PA_PATH_NTT31 || cfg.path == PA_PATH_NTT64)
-            d->prime_bits = cfg.tr.field == kFieldF64 ? 64 : (cfg.tr.field == kFieldF29 ? 29 : 31);
+            d->prime_bits = cfg.tr.field == kFieldF64   ? 64
+                            : cfg.tr.field == kFieldF29 ? 29
+                            : cfg.tr.field == kFieldF28 ? 28
+                                                        : 31;
     }
 }
 

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include "ntt_field.cuh"  // compile-time roots of the prime fields (root16_tw)
 
@@ -78,9 +79,10 @@ __device__ void load_stage_tables(typename F::Tw *st, const typename F::Tw *__re
     }
 }
 
-// S decimation-in-frequency stages on x[0 .. 2^S) (element k at row i0 + k q).
+// S decimation-in-frequency stages on x[0 .. 2^S) (element k at row i0 + k q), with the
+// field's own butterflies.
 template <class F, int S>
-__device__ __forceinline__ void dif_group(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+__device__ __forceinline__ void dif_group_plain(typename F::T (&x)[1 << S], const typename F::Tw *tw,
                                           int j, int q) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -95,9 +97,9 @@ __device__ __forceinline__ void dif_group(typename F::T (&x)[1 << S], const type
     }
 }
 
-// The inverse of dif_group (times 2^S) with inverse stage tables.
+// The inverse of dif_group_plain (times 2^S) with inverse stage tables.
 template <class F, int S>
-__device__ __forceinline__ void dit_group(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+__device__ __forceinline__ void dit_group_plain(typename F::T (&x)[1 << S], const typename F::Tw *tw,
                                           int j, int q) {
 #pragma unroll
     for (int s = S - 1; s >= 0; --s) {
@@ -122,13 +124,230 @@ struct HasRoot16<F, decltype(void(F::kRoot16))> {
     static constexpr bool value = true;
 };
 
+// Fields with lazily reduced residues (LazyField: F::kRoom, F::kIoDif, F::kIoDit).
+template <class F, class = void>
+struct IsLazy {
+    static constexpr bool value = false;
+};
+template <class F>
+struct IsLazy<F, decltype(void(F::kRoom))> {
+    static constexpr bool value = true;
+};
+
+// Bound bookkeeping of the lazy groups. Every value of a group is below B p, B known at
+// compile time: LzPlan runs the group's butterflies on the bounds alone (constexpr) and
+// records where a value must be lowered and by which step, and the device code expands
+// that schedule with `if constexpr` (straight-line code, no bound arithmetic left).
+// Lowering B to T (lz_steps): one conditional subtraction of T p when B <= 2T (after one
+// of 2T p when B <= 4T), else Shoup's product by 1, which leaves x below 2p. Step codes:
+// c > 0 subtracts c p if x >= c p, c = -1 is the product by 1.
+struct LzSteps {
+    int c[2] = {0, 0};
+};
+constexpr LzSteps lz_steps(int &B, int T) {
+    LzSteps r{};
+    if (B <= T) return r;
+    int n = 0;
+    if (B > 2 * T && B <= 4 * T) {
+        r.c[n++] = 2 * T;
+        B = 2 * T;
+    }
+    if (B <= 2 * T) {
+        r.c[n++] = T;
+        B = T;
+        return r;
+    }
+    r.c[n++] = -1;
+    B = 2;
+    return r;
+}
+constexpr void lz_join(LzSteps &a, const LzSteps &b) {
+    for (int i = 0; i < 2; ++i)
+        if (b.c[i]) {
+            if (!a.c[0])
+                a.c[0] = b.c[i];
+            else
+                a.c[1] = b.c[i];
+        }
+}
+
+// The schedule of one radix-2^S group (DIF or DIT; Q1: the stride-1 group of a field with
+// compile-time 16th roots, whose butterflies with w = 1 skip the product). For butterfly k
+// (k & half == 0) of stage s: steps on x[k] (pa) and x[k + half] (pb) before it, and K, the
+// bound of the subtracted operand (the difference is formed as a - b + K p); after the last
+// stage, steps bringing every output below the group's io bound.
+template <int S>
+struct LzPlan {
+    LzSteps pa[4][16], pb[4][16], post[16];
+    int K[4][16] = {};
+};
+constexpr bool lz_w1(int S, bool q1, int k, int half) { return q1 && S == 4 && (k & (half - 1)) == 0; }
+
+template <int S>
+constexpr LzPlan<S> lz_plan(bool dif, bool q1, int room, int io_dif, int io_dit) {
+    LzPlan<S> p{};
+    int b[16] = {};
+    const int io = dif ? io_dif : io_dit;
+    for (int k = 0; k < (1 << S); ++k) b[k] = io;
+    for (int t = 0; t < S; ++t) {
+        const int s = dif ? t : S - 1 - t;  // stage, numbered as in dif_group_plain
+        const int half = 1 << (S - 1 - s);
+        for (int k = 0; k < (1 << S); ++k) {
+            if (k & half) continue;
+            const int k2 = k + half;
+            const bool w1 = lz_w1(S, q1, k, half);
+            if (dif || w1) {
+                // a + b and a - b + K p below room p: lower the larger operand (at most twice)
+                for (int i = 0; i < 2; ++i)
+                    if (b[k] + b[k2] > room) {
+                        if (b[k] >= b[k2])
+                            lz_join(p.pa[s][k], lz_steps(b[k], io_dif));
+                        else
+                            lz_join(p.pb[s][k], lz_steps(b[k2], io_dif));
+                    }
+                p.K[s][k] = b[k2];
+                const int sum = b[k] + b[k2];
+                b[k] = sum;
+                b[k2] = w1 ? sum : (dif ? 2 : sum);
+                if (!dif) b[k2] = sum;
+            } else {
+                // t = b w below 2p: a + t and a - t + 2p
+                if (b[k] + 2 > room) lz_join(p.pa[s][k], lz_steps(b[k], io_dif));
+                p.K[s][k] = 2;
+                b[k] = b[k2] = b[k] + 2;
+            }
+        }
+    }
+    for (int k = 0; k < (1 << S); ++k) p.post[k] = lz_steps(b[k], io);
+    return p;
+}
+
+template <class F, int C>
+__device__ __forceinline__ void lz_step(typename F::T &x) {
+    if constexpr (C > 0)
+        x = min(x, x - static_cast<uint32_t>(C) * F::P);
+    else if constexpr (C < 0)
+        x = F::red2(x);
+}
+
+// A lazy group: LzPlan's schedule, expanded at compile time.
+template <class F, int S, bool DIF, bool Q1>
+struct LzGroup {
+    using T = typename F::T;
+    using Tw = typename F::Tw;
+    static constexpr LzPlan<S> kPlan = lz_plan<S>(DIF, Q1, F::kRoom, F::kIoDif, F::kIoDit);
+
+    template <int s, int k>
+    __device__ static __forceinline__ void bfly(T (&x)[1 << S], const Tw *tw, int j, int q) {
+        constexpr int half = 1 << (S - 1 - s);
+        if constexpr ((k & half) == 0) {
+            constexpr int k2 = k + half;
+            lz_step<F, kPlan.pa[s][k].c[0]>(x[k]);
+            lz_step<F, kPlan.pa[s][k].c[1]>(x[k]);
+            lz_step<F, kPlan.pb[s][k].c[0]>(x[k2]);
+            lz_step<F, kPlan.pb[s][k].c[1]>(x[k2]);
+            constexpr uint32_t KP = static_cast<uint32_t>(kPlan.K[s][k]) * F::P;
+            constexpr bool w1 = lz_w1(S, Q1, k, half);
+            constexpr int e = Q1 ? (k & (half - 1)) * (8 / half) : 0;
+            if constexpr (DIF) {
+                const T a = x[k], b = x[k2];
+                x[k] = a + b;
+                if constexpr (w1) {
+                    x[k2] = a + (KP - b);
+                } else {
+                    Tw w;
+                    if constexpr (Q1)
+                        w = root16_tw<F, e>();
+                    else
+                        w = tw[q * half - 1 + j + (k & (half - 1)) * q];
+                    x[k2] = F::mul_tw(a + (KP - b), w);
+                }
+            } else {
+                T t;
+                if constexpr (w1) {
+                    t = x[k2];
+                } else {
+                    Tw w;
+                    if constexpr (Q1)
+                        w = root16_tw<F, 16 - e>();
+                    else
+                        w = tw[q * half - 1 + j + (k & (half - 1)) * q];
+                    t = F::mul_tw(x[k2], w);
+                }
+                const T a = x[k];
+                x[k] = a + t;
+                x[k2] = a + (KP - t);
+            }
+        }
+    }
+    template <int s, int... ks>
+    __device__ static __forceinline__ void stage(T (&x)[1 << S], const Tw *tw, int j, int q,
+                                                 std::integer_sequence<int, ks...>) {
+        (bfly<s, ks>(x, tw, j, q), ...);
+    }
+    template <int... ts>
+    __device__ static __forceinline__ void stages(T (&x)[1 << S], const Tw *tw, int j, int q,
+                                                  std::integer_sequence<int, ts...>) {
+        (stage<(DIF ? ts : S - 1 - ts)>(x, tw, j, q, std::make_integer_sequence<int, (1 << S)>{}), ...);
+    }
+    template <int k>
+    __device__ static __forceinline__ void post(T (&x)[1 << S]) {
+        lz_step<F, kPlan.post[k].c[0]>(x[k]);
+        lz_step<F, kPlan.post[k].c[1]>(x[k]);
+    }
+    template <int... ks>
+    __device__ static __forceinline__ void posts(T (&x)[1 << S], std::integer_sequence<int, ks...>) {
+        (post<ks>(x), ...);
+    }
+    __device__ static __forceinline__ void run(T (&x)[1 << S], const Tw *tw, int j, int q) {
+        stages(x, tw, j, q, std::make_integer_sequence<int, S>{});
+        posts(x, std::make_integer_sequence<int, (1 << S)>{});
+    }
+};
+
+// dif_group on a lazy field: inputs below kIoDif p, outputs below kIoDif p.
+template <class F, int S, bool Q1>
+__device__ __forceinline__ void dif_group_lazy(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+                                               int j, int q) {
+    LzGroup<F, S, true, Q1>::run(x, tw, j, q);
+}
+
+// dit_group on a lazy field: inputs below kIoDit p, outputs below kIoDit p.
+template <class F, int S, bool Q1>
+__device__ __forceinline__ void dit_group_lazy(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+                                               int j, int q) {
+    LzGroup<F, S, false, Q1>::run(x, tw, j, q);
+}
+
+// S decimation-in-frequency stages on x[0 .. 2^S) (element k at row i0 + k q).
+template <class F, int S>
+__device__ __forceinline__ void dif_group(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+                                          int j, int q) {
+    if constexpr (IsLazy<F>::value)
+        dif_group_lazy<F, S, false>(x, tw, j, q);
+    else
+        dif_group_plain<F, S>(x, tw, j, q);
+}
+
+// The inverse of dif_group (times 2^S) with inverse stage tables.
+template <class F, int S>
+__device__ __forceinline__ void dit_group(typename F::T (&x)[1 << S], const typename F::Tw *tw,
+                                          int j, int q) {
+    if constexpr (IsLazy<F>::value)
+        dit_group_lazy<F, S, false>(x, tw, j, q);
+    else
+        dit_group_plain<F, S>(x, tw, j, q);
+}
+
 // dif_group / dit_group of a stride-1 group (q = 1, j = 0): the twiddle of stage half-size
 // h at position k' < h is w_{2h}^(+-k') = w16^(+-8k'/h), fixed. For S = 4 and a field with
 // compile-time roots the twiddles are constants and the butterflies with w = 1 skip the
 // product; otherwise the stage tables are read as usual.
 template <class F, int S>
 __device__ __forceinline__ void dif_group_q1(typename F::T (&x)[1 << S], const typename F::Tw *tw) {
-    if constexpr (S == 4 && HasRoot16<F>::value) {
+    if constexpr (S == 4 && HasRoot16<F>::value && IsLazy<F>::value) {
+        dif_group_lazy<F, 4, true>(x, tw, 0, 1);
+    } else if constexpr (S == 4 && HasRoot16<F>::value) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int half = 8 >> s;
@@ -149,7 +368,9 @@ __device__ __forceinline__ void dif_group_q1(typename F::T (&x)[1 << S], const t
 
 template <class F, int S>
 __device__ __forceinline__ void dit_group_q1(typename F::T (&x)[1 << S], const typename F::Tw *tw) {
-    if constexpr (S == 4 && HasRoot16<F>::value) {
+    if constexpr (S == 4 && HasRoot16<F>::value && IsLazy<F>::value) {
+        dit_group_lazy<F, 4, true>(x, tw, 0, 1);
+    } else if constexpr (S == 4 && HasRoot16<F>::value) {
 #pragma unroll
         for (int s = 3; s >= 0; --s) {
             const int half = 8 >> s;
@@ -300,7 +521,7 @@ __device__ __forceinline__ void wl_pairs(int logR, int ncols, Body body) {
 // The eight low stages of an R-point transform on every column, warp-local (no CTA
 // barrier inside; the caller's barriers order them against the other rounds).
 template <class F, bool DIF>
-__device__ void low_rounds_warp(typename F::T *sm, const ColMajor &lay, int logR, int ncols,
+__device__ __forceinline__ void low_rounds_warp(typename F::T *sm, const ColMajor &lay, int logR, int ncols,
                                 const typename F::Tw *tw) {
     wl_pairs(logR, ncols, [&](bool on, int c, int blk, int j) {
         if (DIF) {
@@ -341,7 +562,7 @@ __device__ __forceinline__ void dit_top_rounds(typename F::T *sm, const Lay &lay
 // Forward R-point DIF on every column: a top round of logR mod 4 stages (if any), then
 // rounds of four stages down to the stage of half-size 1.
 template <class F, bool CF, class Lay>
-__device__ void dif_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void dif_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                             const typename F::Tw *tw) {
     if constexpr (!CF && WarpLocal<F, Lay>::value) {
         if (logR >= 8) {
@@ -362,7 +583,7 @@ __device__ void dif_columns(typename F::T *sm, const Lay &lay, int logR, int log
 
 // Inverse R-point DIT on every column: the rounds of dif_columns in reverse order.
 template <class F, bool CF, class Lay>
-__device__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                             const typename F::Tw *tw) {
     if constexpr (!CF && WarpLocal<F, Lay>::value) {
         if (logR >= 8) {
@@ -382,7 +603,7 @@ __device__ void dit_columns(typename F::T *sm, const Lay &lay, int logR, int log
 // while loading the tile: the remaining stages, half-sizes R/4 .. 1, in rounds of
 // (logR - 1) mod 4 (if any) and then four stages.
 template <class F, bool CF, class Lay>
-__device__ void dif_columns_after_first(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void dif_columns_after_first(typename F::T *sm, const Lay &lay, int logR, int logC,
                                         const typename F::Tw *tw) {
     const int rem = logR - 1, s0 = rem & 3;
     int done = 0;
@@ -397,7 +618,7 @@ __device__ void dif_columns_after_first(typename F::T *sm, const Lay &lay, int l
 // the rows it writes out: stages of half-size 1 .. R/4, in the reverse order of
 // dif_columns_after_first.
 template <class F, bool CF, class Lay>
-__device__ void dit_columns_but_last(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void dit_columns_but_last(typename F::T *sm, const Lay &lay, int logR, int logC,
                                      const typename F::Tw *tw) {
     const int rem = logR - 1, s0 = rem & 3;
     for (int done = rem; done > s0; done -= 4)
@@ -409,7 +630,7 @@ __device__ void dit_columns_but_last(typename F::T *sm, const Lay &lay, int logR
 // and the inverse rounds of dit_columns except the first: the caller runs those two in
 // registers around the pointwise product (product_round). Needs logR >= 4.
 template <class F, bool CF, class Lay>
-__device__ void dif_columns_head(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void dif_columns_head(typename F::T *sm, const Lay &lay, int logR, int logC,
                                  const typename F::Tw *tw) {
     int done = 0;
     const int s0 = logR & 3;
@@ -422,7 +643,7 @@ __device__ void dif_columns_head(typename F::T *sm, const Lay &lay, int logR, in
 }
 
 template <class F, bool CF, class Lay>
-__device__ void dit_columns_tail(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void dit_columns_tail(typename F::T *sm, const Lay &lay, int logR, int logC,
                                  const typename F::Tw *tw) {
     const int s0 = logR & 3;
     for (int done = logR - 4; done > s0; done -= 4)
@@ -482,7 +703,7 @@ __device__ __forceinline__ void product_acc_group(typename F::T *sm, const Lay &
 // For each of C column pairs (key column c, window column C + c): product_group on every
 // group of 16 rows.
 template <class F, class Lay, class Mul>
-__device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void product_round(typename F::T *sm, const Lay &lay, int logR, int logC,
                               const typename F::Tw *twf, const typename F::Tw *twi, Mul mul) {
     const int logG = logR - 4;
     const int C = 1 << logC;
@@ -496,7 +717,7 @@ __device__ void product_round(typename F::T *sm, const Lay &lay, int logR, int l
 
 // For each of C column pairs: product_acc_group into the accumulator column acc_col0 + c.
 template <class F, class Lay, class Mul, class Add>
-__device__ void product_acc_round(typename F::T *sm, const Lay &lay, int logR, int logC,
+__device__ __forceinline__ void product_acc_round(typename F::T *sm, const Lay &lay, int logR, int logC,
                                   int acc_col0, const typename F::Tw *twf, Mul mul, Add add) {
     const int logG = logR - 4;
     const int C = 1 << logC;
@@ -514,7 +735,7 @@ __device__ void product_acc_round(typename F::T *sm, const Lay &lay, int logR, i
 // and the first inverse stages run warp-local per (column, block) pair, between the
 // CTA-wide top rounds.
 template <class F, class Mul>
-__device__ void product_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
+__device__ __forceinline__ void product_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
                                 const typename F::Tw *twf, const typename F::Tw *twi, Mul mul) {
     const int C = 1 << logC;
     if constexpr (WarpLocal<F, ColMajor>::value) {
@@ -543,7 +764,7 @@ __device__ void product_columns(typename F::T *sm, const ColMajor &lay, int logR
 // Forward transforms of C key and C window columns and acc[c] += their pointwise products
 // (accumulator column acc_col0 + c), warp-local below the top rounds as in product_columns.
 template <class F, class Mul, class Add>
-__device__ void product_acc_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
+__device__ __forceinline__ void product_acc_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
                                     int acc_col0, const typename F::Tw *twf, Mul mul, Add add) {
     const int C = 1 << logC;
     if constexpr (WarpLocal<F, ColMajor>::value) {

@@ -24,14 +24,15 @@ struct DirectCfg {
 };
 
 // ---- transform paths (NTT over a prime field, FP FFT) ----
-// Prime fields of the NTT paths: PA_PATH_NTT64 runs modulo 2^64 - 2^32 + 1;
-// PA_PATH_NTT31 modulo 7*2^26 + 1 (lazily reduced) when n is below it, else 15*2^27 + 1.
-constexpr int kFieldF31 = 0, kFieldF64 = 1, kFieldF29 = 2, kNumFields = 3;
-constexpr uint64_t kPrimeF29 = 469762049ull, kPrimeF31 = 2013265921ull;
+// Prime fields of the NTT paths: PA_PATH_NTT64 runs modulo 2^64 - 2^32 + 1; PA_PATH_NTT31
+// by default modulo 5*2^25 + 1 when n is below it and 7*2^26 + 1 otherwise (both lazily
+// reduced; transform-domain sums grouped below the prime), or 15*2^27 + 1 on request.
+constexpr int kFieldF31 = 0, kFieldF64 = 1, kFieldF29 = 2, kFieldF28 = 3, kNumFields = 4;
+constexpr uint64_t kPrimeF28 = 167772161ull, kPrimeF29 = 469762049ull, kPrimeF31 = 2013265921ull;
 
 // Workspace layout and launch shape of one persistent NTT launch (see ntt.cu).
 struct NttLayout {
-    int field = 0;         // kFieldF31 / kFieldF64 / kFieldF29
+    int field = 0;         // kFieldF31 / kFieldF64 / kFieldF29 / kFieldF28
     uint64_t ntiles = 0, nitems = 0, nfd = 0;
     uint32_t slots = 1;    // spectra slots of standard tiles, reused round-robin
     size_t smem = 0;
@@ -49,7 +50,7 @@ struct TransformCfg {
     uint32_t radix_log2[4] = {0, 0, 0, 0};
     uint32_t fp64 = 0;           // FFT: FP64 butterflies
     double bound = 0.0;          // FFT: proven rounding bound
-    int field = 0;               // NTT: kFieldF31 / kFieldF64 / kFieldF29
+    int field = 0;               // NTT: kFieldF31 / kFieldF64 / kFieldF29 / kFieldF28
     uint32_t fd = 0;             // NTT: transform-domain accumulation over key tiles
     uint64_t windows = 0;        // NTT with fd: distinct seed-window spectra
     uint32_t kgroup = 0;         // NTT with fd = 1: key tiles per transform-domain sum (the

@@ -117,6 +117,24 @@ struct FieldHost<F29> {
     }
 };
 template <>
+struct FieldHost<F28> {
+    static uint64_t p() { return F28::P; }
+    static uint64_t root(int k) {
+        const uint64_t f[] = {5};
+        return root_of_unity(F28::P, f, 1, 25, k);
+    }
+    static F28::Tw tw(uint64_t w) {
+        F28::Tw t;
+        t.w = static_cast<uint32_t>(w);
+        t.q = static_cast<uint32_t>((w << 32) / F28::P);
+        return t;
+    }
+    static F28::Tw scale(int logn) {
+        uint64_t ninv = powmod_host(uint64_t(1) << logn, F28::P - 2, F28::P);
+        return tw(mulmod_host(ninv, (uint64_t(1) << 32) % F28::P, F28::P));
+    }
+};
+template <>
 struct FieldHost<F64> {
     static uint64_t p() { return F64::P; }
     static uint64_t root(int k) {
@@ -199,6 +217,7 @@ int ntt_tables(int field, Tables *out) {
     switch (field) {
         case kFieldF31: return get_tables<F31>(kFieldF31, out);
         case kFieldF29: return get_tables<F29>(kFieldF29, out);
+        case kFieldF28: return get_tables<F28>(kFieldF28, out);
         default: return get_tables<F64>(kFieldF64, out);
     }
 }
@@ -313,8 +332,10 @@ double ntt_geometry_cost(uint64_t n, uint64_t m, int field, uint32_t k, uint64_t
     if (k <= static_cast<uint32_t>(kLogSmallMax) || fd_mode == 1 || P * Q < 2 || P * Q > kFdMaxPairs)
         return std_units;
     const size_t elem = field == kFieldF64 ? 8 : 4;
-    const uint64_t pmax = field == kFieldF64 ? ~uint64_t(0)
-                                             : (field == kFieldF29 ? kPrimeF29 : kPrimeF31) - 1;
+    const uint64_t pmax = field == kFieldF64   ? ~uint64_t(0)
+                          : field == kFieldF29 ? kPrimeF29 - 1
+                          : field == kFieldF28 ? kPrimeF28 - 1
+                                               : kPrimeF31 - 1;
     uint64_t g = std::min<uint64_t>(Q, pmax / L);
     if (fd_group) g = std::min<uint64_t>(g, fd_group);
     if (g == 0) return std_units;
@@ -387,6 +408,8 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
         c->field = kFieldF64;
     } else if (prime == 29 || prime == 0) {
         c->field = kFieldF29;
+    } else if (prime == 28) {
+        c->field = kFieldF28;
     } else if (prime == 31) {
         c->field = kFieldF31;
     } else {
@@ -445,7 +468,10 @@ int ntt_plan(uint64_t n, uint64_t m, int path, const pa_opts *o, TransformCfg *c
         }
     }
     if (!(best_cost < INFINITY)) return PA_ERR_UNSUPPORTED;
-    c->field = field;
+    // Default: the geometry is the 29-bit field's; a key shorter than the 28-bit prime runs
+    // over that prime instead (no coefficient counts more than n bit products, so every sum
+    // stays below it), whose transforms subtract less often (LazyField).
+    c->field = (prime == 0 && path != PA_PATH_NTT64 && n < kPrimeF28) ? kFieldF28 : field;
     c->log2n = bk;
     c->L = bL;
     c->M = bM;
@@ -486,6 +512,9 @@ NttTile tile_shape(uint32_t logN, int field) {
     } else if (field == kFieldF29) {
         const F29::Tw sc = FieldHost<F29>::scale(t.logN);
         memcpy(&t.scale, &sc, sizeof(sc));
+    } else if (field == kFieldF28) {
+        const F28::Tw sc = FieldHost<F28>::scale(t.logN);
+        memcpy(&t.scale, &sc, sizeof(sc));
     } else {
         const F64::Tw sc = FieldHost<F64>::scale(t.logN);
         memcpy(&t.scale, &sc, sizeof(sc));
@@ -514,6 +543,9 @@ uint64_t outer_scale(int field, uint32_t logT) {
         memcpy(&bits, &t, sizeof(t));
     } else if (field == kFieldF29) {
         const F29::Tw t = FieldHost<F29>::tw(powmod_host(uint64_t(1) << logT, F29::P - 2, F29::P));
+        memcpy(&bits, &t, sizeof(t));
+    } else if (field == kFieldF28) {
+        const F28::Tw t = FieldHost<F28>::tw(powmod_host(uint64_t(1) << logT, F28::P - 2, F28::P));
         memcpy(&bits, &t, sizeof(t));
     } else {
         bits = powmod_host(uint64_t(1) << logT, F64::P - 2, F64::P);
@@ -1009,6 +1041,7 @@ int launch_any(const NttLayout &lay, void *ws, const BlockPtrs *blks, const Bloc
     switch (lay.field) {
         case kFieldF31: return ntt_launch_f31(lay, ws, blks, one, status, prof, s);
         case kFieldF29: return ntt_launch_f29(lay, ws, blks, one, status, prof, s);
+        case kFieldF28: return ntt_launch_f28(lay, ws, blks, one, status, prof, s);
         default: return ntt_launch_f64(lay, ws, blks, one, status, prof, s);
     }
 }

@@ -142,9 +142,11 @@ constexpr int kStageBlock = 4096;  // entries per (direction, log2 R) block
 // The tables of a field on the current device, built and uploaded on first use.
 int ntt_tables(int field, Tables *out);
 
-// One persistent launch of a field's work list (ntt_f29.cu, ntt_f31.cu, ntt_f64.cu).
+// One persistent launch of a field's work list (ntt_f28.cu, ntt_f29.cu, ntt_f31.cu,
+// ntt_f64.cu).
 #define PA_NTT_LAUNCH_ARGS const NttLayout &lay, void *ws, const BlockPtrs *blks, \
     const BlockPtrs &one, int *status, Prof *prof, cudaStream_t s
+int ntt_launch_f28(PA_NTT_LAUNCH_ARGS);
 int ntt_launch_f29(PA_NTT_LAUNCH_ARGS);
 int ntt_launch_f31(PA_NTT_LAUNCH_ARGS);
 int ntt_launch_f64(PA_NTT_LAUNCH_ARGS);

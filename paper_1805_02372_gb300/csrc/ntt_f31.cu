@@ -1,5 +1,5 @@
 // Persistent NTT launch over the prime field F31 (see ntt_kernel.cuh); one field per
-// translation unit so the three instantiations compile in parallel.
+// translation unit so the instantiations compile in parallel.
 #include "ntt_kernel.cuh"
 
 namespace pa {

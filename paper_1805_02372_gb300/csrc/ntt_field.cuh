@@ -6,6 +6,8 @@
 //      [0, 4p) (4p < 2^31): a butterfly needs one conditional subtraction instead of
 //      three (Harvey's lazy butterflies for Shoup multiplication); values are made
 //      canonical only when the hash bit is taken.
+// F28: p = 5 * 2^25 + 1 (2-adicity 25), as F29 for n < p, with room for 25p in 32 bits:
+//      the rounds of a transform subtract far less often (LazyField).
 // F31: p = 15 * 2^27 + 1 (2-adicity 27), canonical residues, for n < p.
 //      Twiddles carry Shoup quotients (one high-half multiply per twiddle product);
 //      the pointwise product is a Montgomery product.
@@ -121,18 +123,34 @@ struct F31 {
     static constexpr uint32_t kRoot16 = cx_root16(2013265921u, 3, 5);
 };
 
-// Residues in [0, 4p). Shoup's product of any 32-bit a by a canonical twiddle w with
-// quotient floor(w 2^32 / p) lies in [0, 2p) when p < 2^31 (Harvey, "Faster arithmetic
-// for number-theoretic transforms", 2014), which is what lets the corrections go.
-struct F29 {
+// Lazily reduced residues of a prime p < 2^29 (Harvey, "Faster arithmetic for
+// number-theoretic transforms", 2014): Shoup's product of any 32-bit a by a canonical
+// twiddle w with quotient floor(w 2^32 / p) lies in [0, 2p), so values need not be
+// canonical between operations, only below 2^32. The single-operation butterflies below
+// keep them in [0, 4p) with one conditional subtraction each. The radix-2^S rounds of
+// dft.cuh instead track, at compile time, a bound B p on every value of a group and
+// subtract only where a sum or difference could pass kRoom p (the largest multiple of p
+// below 2^32): values between forward rounds are below kIoDif p, between inverse rounds
+// below kIoDit p. Every consumer of an inverse round's output is a product (Shoup or
+// Montgomery: any 32-bit input) or another inverse round, so kIoDit may exceed 4.
+//   P = 7 * 2^26 + 1 (29-bit, 2-adicity 26): kRoom 9, kIoDit 4;
+//   P = 5 * 2^25 + 1 (28-bit, 2-adicity 25): kRoom 25, kIoDit 12 (an inverse round of four
+//   stages adds at most 8p, and 12 + 8 <= 25).
+template <uint32_t kP, int kAdic, uint32_t kOdd, int kDitIo>
+struct LazyField {
     using T = uint32_t;
     using Tw = F31::Tw;  // value and Shoup quotient
-    static constexpr uint32_t P = 469762049u;
+    static constexpr uint32_t P = kP;
     static constexpr uint32_t P2 = 2 * P, P4 = 4 * P;
-    static constexpr int kTwoAdicity = 26;
-    static constexpr uint32_t PINV = inverse_mod_2_32(469762049u);
-    static_assert(PINV * 469762049u == 1u, "Montgomery inverse");
-    static_assert(uint64_t(8) * 469762049u < (uint64_t(1) << 32), "8p fits 32 bits");
+    static constexpr int kTwoAdicity = kAdic;
+    static constexpr uint32_t PINV = inverse_mod_2_32(kP);
+    static_assert(PINV * kP == 1u, "Montgomery inverse");
+    static_assert(uint64_t(8) * kP < (uint64_t(1) << 32), "8p fits 32 bits");
+    static constexpr int kRoom = static_cast<int>((uint64_t(1) << 32) / kP);
+    static constexpr int kIoDif = 4, kIoDit = kDitIo;
+    static_assert(kIoDit >= 4 && kIoDit + 2 <= kRoom, "an inverse stage adds 2p at most");
+    // floor(2^32 / p): the Shoup quotient of the twiddle 1
+    static constexpr uint32_t kShoup1 = static_cast<uint32_t>((uint64_t(1) << 32) / kP);
 
     // [0, 4p) + [0, 4p) -> [0, 4p)
     __device__ static __forceinline__ T add(T a, T b) {
@@ -148,7 +166,11 @@ struct F29 {
         const uint32_t q = __umulhi(a, w.q);
         return a * w.w - q * P;
     }
-    // a b 2^-32 for a < 4p, b < 4p: (ab - mq p) / 2^32 in (-p, 1.75p), plus p -> (0, 2.75p)
+    // any 32-bit a -> [0, 2p) (Shoup's product by 1)
+    __device__ static __forceinline__ T red2(T a) { return a - __umulhi(a, kShoup1) * P; }
+    // a b 2^-32: (ab - mq p) / 2^32 lies in (-p, ab / 2^32), plus p: (0, p + ab / 2^32),
+    // e.g. below 2.75p (29-bit p) or 1.7p (28-bit p) for a, b < 4p, below 3p for any
+    // 32-bit a and b < 2p
     __device__ static __forceinline__ T mont(T a, T b) {
         const uint32_t lo = a * b, hi = __umulhi(a, b);
         const uint32_t mq = lo * PINV;
@@ -160,8 +182,8 @@ struct F29 {
         a = min(a, a - P);
         return a & 1u;
     }
-    static constexpr uint32_t R_MOD = static_cast<uint32_t>((uint64_t(1) << 32) % 469762049u);
-    static constexpr uint32_t R_Q = static_cast<uint32_t>((uint64_t(R_MOD) << 32) / 469762049u);
+    static constexpr uint32_t R_MOD = static_cast<uint32_t>((uint64_t(1) << 32) % kP);
+    static constexpr uint32_t R_Q = static_cast<uint32_t>((uint64_t(R_MOD) << 32) / kP);
     // w 2^32 mod p in [0, 2p)
     __device__ static __forceinline__ T full_form(Tw w) {
         Tw r;
@@ -169,7 +191,7 @@ struct F29 {
         r.q = R_Q;
         return mul_tw(w.w, r);
     }
-    // a < 4p times wf < 2p: (0, 2p) after the Montgomery reduction
+    // a < 2^32 times wf < 2p: (0, 3p) after the Montgomery reduction
     __device__ static __forceinline__ T mul_full(T a, T wf) { return mont(a, wf); }
     __device__ static __forceinline__ T step_full(T wf, Tw step) { return mul_tw(wf, step); }
     __device__ static __forceinline__ Tw neg_tw(Tw w) {
@@ -184,7 +206,7 @@ struct F29 {
         b = mul_tw(a + (P4 - b), w);
         a = min(s, s - P4);
     }
-    // Cooley-Tukey: (a + b w, a - b w); a, b in [0, 4p) -> [0, 4p), (0, 4p)
+    // Cooley-Tukey: (a + b w, a - b w); a < kIoDit p -> both below kIoDit p
     __device__ static __forceinline__ void dit_bfly(T &a, T &b, Tw w) {
         const T t = mul_tw(b, w);
         const T a2 = min(a, a - P2);
@@ -204,8 +226,11 @@ struct F29 {
         a = a2 + t;
         b = a2 + (P2 - t);
     }
-    static constexpr uint32_t kRoot16 = cx_root16(469762049u, 7, 0);
+    static constexpr uint32_t kRoot16 = cx_root16(kP, kOdd, 0);
 };
+
+using F29 = LazyField<469762049u, 26, 7, 4>;
+using F28 = LazyField<167772161u, 25, 5, 12>;
 
 // Twiddle w16^E of a field with a compile-time 16th root (value and Shoup quotient).
 template <class F, int E>

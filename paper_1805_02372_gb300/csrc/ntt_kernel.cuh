@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t tile_bits(const TilePair &pr, const BlockPtr
 
 // Whole transform of size 2^logN <= 2^12 in shared memory for one tile.
 template <class F>
-__device__ void body_small(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
+__device__ __forceinline__ void body_small(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
                            const TilePair &pr, const BlockPtrs &bp, int logN, typename F::Tw scale) {
     using T = typename F::T;
     const int N = 1 << logN;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void twiddle_segment(typename F::T (&x)[SEG], typenam
 // Pass 1 forward on column group cg (C = 2^logC columns at stride S1 = N / R1); each
 // thread handles 32-byte row segments (SEG columns).
 template <class F>
-__device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
+__device__ __forceinline__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
                                const BlockPtrs &bp, int which, uint64_t cg, int logN, int logR1,
                                int logC, typename F::T *__restrict__ dst,
                                const typename F::Tw *__restrict__ tfwd) {
@@ -265,7 +265,7 @@ __device__ void body_fwd_first(typename F::T *sm, const typename F::Tw *st, cons
 // Pass 2 of both spectra (rows of R2 = 2^logR2, C2 rows from row group rg), the pointwise
 // product and the inverse pass 2; X = key spectrum, W = window spectrum.
 template <class F>
-__device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
+__device__ __forceinline__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
                                 const typename F::Tw *sti, uint64_t rg, int logR2, int logC,
                                 typename F::T *__restrict__ X, typename F::T *__restrict__ W) {
     using T = typename F::T;
@@ -311,7 +311,7 @@ __device__ void body_fused_last(typename F::T *sm, const typename F::Tw *stf,
 
 // Inverse pass 1 on column group cg of the product, scale, low bit, XOR output bits.
 template <class F>
-__device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
+__device__ __forceinline__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, const TilePair &pr,
                                const BlockPtrs &bp, uint64_t cg, int logN, int logR1, int logC,
                                const typename F::T *__restrict__ src,
                                const typename F::Tw *__restrict__ tinv, typename F::Tw scale) {
@@ -387,7 +387,7 @@ __device__ void body_inv_first(typename F::T *sm, const typename F::Tw *st, cons
 // Forward pass 2 of one fd spectrum in place: C = 2^logC rows of R2 = 2^logR2 from row
 // group rg.
 template <class F>
-__device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint64_t rg, int logR2,
+__device__ __forceinline__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint64_t rg, int logR2,
                               int logC, typename F::T *__restrict__ A) {
     using T = typename F::T;
     constexpr int V = 16 / sizeof(T);
@@ -425,7 +425,7 @@ __device__ void body_fwd_last(typename F::T *sm, const typename F::Tw *stf, uint
 // of R2 rows (C = 2048 / R2 rows per output, or one row when R2 > 2048).
 constexpr int kSum4Elems = 2048;
 template <class F>
-__device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
+__device__ __forceinline__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg,
                                    int logR2, int logC, const typename F::T *__restrict__ X,
                                    const typename F::T *__restrict__ W,
                                    const uint32_t *__restrict__ wmap_blk, uint32_t Q, uint32_t jlo,
@@ -550,7 +550,7 @@ __device__ void body_sum4_inv_last(typename F::T *sm, const typename F::Tw *sti,
 // inverse pass 2 and is written to Z. Shared memory: key, window and accumulator
 // columns (3 C columns of R2 rows).
 template <class F>
-__device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
+__device__ __forceinline__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
                                 const typename F::Tw *sti, uint64_t rg, int logR2, int logC,
                                 const typename F::T *__restrict__ X,
                                 const typename F::T *__restrict__ W,
@@ -619,7 +619,7 @@ __device__ void body_stream_sum(typename F::T *sm, const typename F::Tw *stf,
 // stage (rows r, r + T/2) runs on the rows as they are loaded and the inverse's last stage
 // only on the Ps rows written out, so that no round is that short.
 template <class F>
-__device__ void body_outer(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
+__device__ __forceinline__ void body_outer(typename F::T *sm, const typename F::Tw *stf, const typename F::Tw *sti,
                            uint64_t k0, int logT, int logCo, uint32_t Qg, uint32_t Ps,
                            const typename F::T *__restrict__ X, const typename F::T *__restrict__ W,
                            typename F::T *__restrict__ Z, uint64_t N, typename F::Tw tinv) {
@@ -720,7 +720,7 @@ __device__ void body_outer(typename F::T *sm, const typename F::Tw *stf, const t
 // Inverse pass 2 of one fd output spectrum in place: C = 2^logC rows of R2 = 2^logR2 from
 // row group rg (the mirror of body_fwd_last).
 template <class F>
-__device__ void body_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg, int logR2,
+__device__ __forceinline__ void body_inv_last(typename F::T *sm, const typename F::Tw *sti, uint64_t rg, int logR2,
                               int logC, typename F::T *__restrict__ A) {
     using T = typename F::T;
     constexpr int V = 16 / sizeof(T);

@@ -12,13 +12,18 @@
 //   PA_PEAK_SHIFT_AND      acc ^= xw & funnel_shift(lo, hi, k) (the direct kernel's step);
 //   PA_PEAK_MMA_S8         mma.sync m16n8k32 s8 x s8 -> s32 (the INT8 block path's MMA);
 //   PA_PEAK_MMA_B1         mma.sync m16n8k256 b1 AND + POPC -> s32 (the binary form of the
-//                          block contraction: one bit product per AND, summed by POPC).
+//                          block contraction: one bit product per AND, summed by POPC);
+//   PA_PEAK_NTT_GROUP28/29 radix-16 groups of the 28- or 29-bit field exactly as the NTT
+//                          kernel's rounds run them (dif_group / dit_group of dft.cuh: the
+//                          lazy reduction schedule, twiddles read from a shared-memory stage
+//                          table), a forward and an inverse chain per thread.
 // Each result is operations per second, one operation being one butterfly, one
 // multiply-add, one shift-and-accumulate, or one multiply-accumulate of the MMA (an s8
 // product, or a 1-bit AND product).
 #include <stdint.h>
 
 #include "common.cuh"
+#include "dft.cuh"
 #include "ntt_field.cuh"
 
 namespace pa {
@@ -47,6 +52,31 @@ __global__ void __launch_bounds__(kProbeThreads, 2) probe_butterfly(uint32_t *si
 #pragma unroll
     for (int c = 0; c < kChains; ++c) r ^= a[c] ^ b[c];
     if (r == 0x9E3779B9u) sink[0] = r;  // keeps the chains live
+}
+
+// 32 butterflies per iteration and thread: iters radix-16 forward groups, then iters
+// inverse groups, chained on the same 16 registers (a forward group's outputs meet both
+// groups' input bounds, an inverse group's its own), with the twiddles of the stride-16
+// round of a 256-point transform (j = lane mod 16).
+template <class F>
+__global__ void __launch_bounds__(kProbeThreads, 2) probe_group(uint32_t *sink, uint32_t iters,
+                                                                 const typename F::Tw *__restrict__ tab,
+                                                                 uint32_t seed) {
+    using Tw = typename F::Tw;
+    __shared__ Tw st[2][256];
+    for (int i = threadIdx.x; i < 2 * 255; i += blockDim.x) st[i / 255][i % 255] = tab[i];
+    __syncthreads();
+    uint32_t x[16];
+    const uint32_t v = seed ^ ((blockIdx.x * kProbeThreads + threadIdx.x) * 0x9E3779B9u);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = (v + 977u * k) % (4u * F::P);
+    const int j = threadIdx.x & 15;
+    for (uint32_t i = 0; i < iters; ++i) dif_group<F, 4>(x, st[0], j, 16);
+    for (uint32_t i = 0; i < iters; ++i) dit_group<F, 4>(x, st[1], j, 16);
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) r ^= x[k];
+    if (r == 0x9E3779B9u) sink[0] = r;
 }
 
 // 2 kChains multiply-adds per iteration and thread.
@@ -165,9 +195,34 @@ __global__ void __launch_bounds__(kProbeThreads, 2) probe_mma_b1(uint32_t *sink,
     if (r == 0x7654321) sink[0] = static_cast<uint32_t>(r);
 }
 
+// Twiddles for the group probe: canonical residues (powers of the field's 16th root of
+// unity) with their Shoup quotients, 255 per direction. The cost of a group does not depend
+// on the values, only on the reads and the arithmetic.
+template <class F>
+void group_tables(typename F::Tw *out) {
+    const uint64_t p = F::P;
+    uint64_t w = 1;
+    for (int i = 0; i < 2 * 255; ++i) {
+        out[i].w = static_cast<uint32_t>(w);
+        out[i].q = static_cast<uint32_t>((w << 32) / p);
+        w = w * F::kRoot16 % p;
+    }
+}
+
 // Launches probe `which` with `iters` iterations per thread; returns operations per launch.
-double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, cudaStream_t s) {
+double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, const void *tabs,
+                    cudaStream_t s) {
     const double threads = double(grid) * kProbeThreads;
+    if (which == PA_PEAK_NTT_GROUP28) {
+        probe_group<F28><<<grid, kProbeThreads, 0, s>>>(sink, iters, static_cast<const F28::Tw *>(tabs),
+                                                        0x1234567u);
+        return threads * iters * 64.0;
+    }
+    if (which == PA_PEAK_NTT_GROUP29) {
+        probe_group<F29><<<grid, kProbeThreads, 0, s>>>(sink, iters, static_cast<const F29::Tw *>(tabs),
+                                                        0x1234567u);
+        return threads * iters * 64.0;
+    }
     if (which == PA_PEAK_NTT_BUTTERFLY) {
         F29::Tw w;
         w.w = 123456789u;  // a canonical residue with its Shoup quotient
@@ -196,7 +251,7 @@ double probe_launch(int which, uint32_t iters, unsigned grid, uint32_t *sink, cu
 
 extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
     using namespace pa;
-    if (!ops_per_s || which < PA_PEAK_NTT_BUTTERFLY || which > PA_PEAK_MMA_B1) return PA_ERR_INVALID;
+    if (!ops_per_s || which < PA_PEAK_NTT_BUTTERFLY || which > PA_PEAK_NTT_GROUP29) return PA_ERR_INVALID;
     int dev = 0, sms = 0, per_sm = 0;
     PA_CUDA_TRY(cudaGetDevice(&dev));
     PA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -204,13 +259,25 @@ extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
                      : which == PA_PEAK_NTT_MULADD  ? reinterpret_cast<const void *>(probe_muladd)
                      : which == PA_PEAK_MMA_S8      ? reinterpret_cast<const void *>(probe_mma_s8)
                      : which == PA_PEAK_MMA_B1      ? reinterpret_cast<const void *>(probe_mma_b1)
+                     : which == PA_PEAK_NTT_GROUP28 ? reinterpret_cast<const void *>(probe_group<F28>)
+                     : which == PA_PEAK_NTT_GROUP29 ? reinterpret_cast<const void *>(probe_group<F29>)
                                                     : reinterpret_cast<const void *>(probe_shift_and);
     PA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kProbeThreads, 0));
     const unsigned grid = static_cast<unsigned>((per_sm > 0 ? per_sm : 1) * sms);
     uint32_t *sink = nullptr;
+    void *tabs = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaMalloc(&sink, 256);
+    if (e == cudaSuccess && (which == PA_PEAK_NTT_GROUP28 || which == PA_PEAK_NTT_GROUP29)) {
+        F31::Tw host[2 * 255];  // the 32-bit fields share this twiddle layout
+        if (which == PA_PEAK_NTT_GROUP28)
+            group_tables<F28>(host);
+        else
+            group_tables<F29>(host);
+        e = cudaMalloc(&tabs, sizeof(host));
+        if (e == cudaSuccess) e = cudaMemcpy(tabs, host, sizeof(host), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -221,7 +288,7 @@ extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
         float t = 0.f;
         for (int r = 0; r < 2 && e == cudaSuccess; ++r) {  // warm-up and sizing
             cudaEventRecord(a, s);
-            probe_launch(which, iters, grid, sink, s);
+            probe_launch(which, iters, grid, sink, tabs, s);
             cudaEventRecord(b, s);
             e = cudaEventSynchronize(b);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
@@ -232,7 +299,7 @@ extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
         }
         for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
             cudaEventRecord(a, s);
-            const double ops = probe_launch(which, iters, grid, sink, s);
+            const double ops = probe_launch(which, iters, grid, sink, tabs, s);
             cudaEventRecord(b, s);
             e = cudaEventSynchronize(b);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
@@ -247,6 +314,7 @@ extern "C" int pa_probe_peak(int which, double *ops_per_s, double *ms) {
     if (b) cudaEventDestroy(b);
     if (s) cudaStreamDestroy(s);
     cudaFree(sink);
+    cudaFree(tabs);
     if (e != cudaSuccess) return cuda_fail(e);
     *ops_per_s = best;
     if (ms) *ms = best_ms;

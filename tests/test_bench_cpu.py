@@ -21,21 +21,28 @@ def _descs(path, blocks, **extra):
                   "fd": 2, "windows": 2}, **extra) for _ in blocks]
 
 
-PROBE = {"butterfly_per_s": 5e12, "muladd_per_s": 4e12, "shift_and_per_s": 9e12}
+PROBE = {"butterfly_per_s": 5e12, "group28_per_s": 7e12, "group29_per_s": 6e12,
+         "muladd_per_s": 4e12, "shift_and_per_s": 9e12}
 
 
 def test_roofline_batch_persistent_fields():
     blocks = inputs.batched_blocks()[:4]
     kt = {"batch_persistent": {"launches": 10, "total_ms": 20.0}, "memset": {"launches": 10, "total_ms": 0.1}}
-    descs = _descs("ntt31", blocks)
+    # two blocks over the 28-bit prime, one over the 29-bit, one over the 64-bit
+    descs = _descs("ntt31", blocks, prime_bits=28)
+    descs[2] = dict(descs[2], prime_bits=29)
+    descs[3] = dict(descs[3], prime_bits=64, path_name="ntt64")
     r = bench.roofline(kt, blocks, descs, steps=10, workload_name="batched4", probe=PROBE)
     assert r["kernel"] == "batch_persistent" and r["bound"] == "alu" and r["unit"] == "Tops/s"
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     # achieved = model ops per launch / launch time; one launch per step here
     bfly, prod = bench.ntt_work(descs)
-    assert r["achieved"] == pytest.approx(bench.OPS_PER_BFLY * (bfly + prod) / 2e-3 / 1e12)
-    # the fraction is the time the work takes at the measured peaks over the launch time
-    t_peak = bfly / PROBE["butterfly_per_s"] + prod / PROBE["muladd_per_s"]
+    assert set(bfly) == {28, 29, 64} and bfly[28] == pytest.approx(2 * bfly[29])
+    assert r["achieved"] == pytest.approx(bench.OPS_PER_BFLY * (sum(bfly.values()) + prod) / 2e-3 / 1e12)
+    # the fraction is the time the work takes at the measured peaks over the launch time:
+    # each field's butterflies at its group rate (the 64-bit field at the single-butterfly rate)
+    t_peak = (bfly[28] / PROBE["group28_per_s"] + bfly[29] / PROBE["group29_per_s"] +
+              bfly[64] / PROBE["butterfly_per_s"] + prod / PROBE["muladd_per_s"])
     assert r["frac"] == pytest.approx(t_peak / 2e-3)
     assert "measured in this run" in r["peak_source"]
     assert r["traffic"] is None  # no committed figure for this workload
@@ -109,10 +116,11 @@ def test_ntt_work_counts_one_inverse_per_sum():
          "fd": 1, "windows": 262, "sum_groups": 3}
     N = 2.0 ** 23
     bfly, prod = bench.ntt_work([d])
-    assert bfly == pytest.approx((239 + 262 + 3 * 24) * (N / 2) * 23)
+    assert bfly[29] == pytest.approx((239 + 262 + 3 * 24) * (N / 2) * 23)
     assert prod == pytest.approx(24 * 239 * N)
-    assert bench.ntt_work([dict(d, sum_groups=1)])[0] < bfly
+    assert bench.ntt_work([dict(d, sum_groups=1)])[0][29] < bfly[29]
     # a standard tile pair: two forward transforms, one inverse, N pointwise products
     p = {"path_name": "ntt31", "log2_transform": 20, "tiles_in": 3, "tiles_out": 2, "fd": 0,
          "windows": 0}
-    assert bench.ntt_work([p]) == pytest.approx((6 * 3 * (2.0 ** 19) * 20, 6 * 2.0 ** 20))
+    b2, p2 = bench.ntt_work([dict(p, prime_bits=28)])
+    assert b2 == {28: pytest.approx(6 * 3 * (2.0 ** 19) * 20)} and p2 == pytest.approx(6 * 2.0 ** 20)

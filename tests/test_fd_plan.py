@@ -82,7 +82,19 @@ def test_finite_size_plan_accumulates(lib):
 
 def test_prime_choice(lib):
     q = pkg.pa_plan_query
-    assert q(1_000_000, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 29
+    # default: 5 * 2^25 + 1 for keys below it (no coefficient counts more than n products),
+    # 7 * 2^26 + 1 above, with the same geometry either way
+    p28 = 167_772_161
+    assert q(1_000_000, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 28
+    for n, m in ((1_000_000, 5_000), (p28 - 1, 16_000_000), (100_000_007, 10_000_000)):
+        d0 = q(n, m, binding.make_opts(path="ntt31"))
+        d29 = q(n, m, binding.make_opts(path="ntt31", ntt_prime=29))
+        assert d0["prime_bits"] == 28 and d29["prime_bits"] == 29
+        for key in ("log2_transform", "tile_in", "tile_out", "fd", "windows", "sum_groups"):
+            assert d0[key] == d29[key], key
+    assert q(p28, 5_000, binding.make_opts(path="ntt31"))["prime_bits"] == 29
+    assert q(1_000_000, 5_000, binding.make_opts(path="ntt31", ntt_prime=28))["prime_bits"] == 28
+    assert q(1_000_000, 5_000, binding.make_opts(path="ntt31", ntt_prime=29))["prime_bits"] == 29
     assert q(1_000_000, 5_000, binding.make_opts(path="ntt31", ntt_prime=31))["prime_bits"] == 31
     assert q(1_000_000, 5_000, binding.make_opts(path="ntt64"))["prime_bits"] == 64
     # 7 * 2^26 + 1 = 469,762,049 serves any n: tile pairs count at most L < p products,
@@ -95,13 +107,17 @@ def test_prime_choice(lib):
                 assert d["sum_groups"] == -(-d["tiles_in"] // ((469_762_048) // d["tile_in"]))
             elif d["fd"] == 2:
                 assert d["tiles_in"] * d["tile_in"] <= 469_762_048 + d["tile_in"]
+    # forced 28-bit prime on a longer key: sums of at most (p - 1) // L key tiles
+    d = q(1_000_000_007, 100_000_000, binding.make_opts(path="ntt31", ntt_prime=28))
+    assert d["prime_bits"] == 28 and d["fd"] == 1
+    assert d["sum_groups"] == -(-d["tiles_in"] // ((p28 - 1) // d["tile_in"]))
     for bad in (7, 30):
         with pytest.raises(pkg.PAError):
             q(1_000, 5, binding.make_opts(path="ntt31", ntt_prime=bad))
     assert q(1_000, 5, binding.make_opts(path="direct"))["prime_bits"] == 0
 
 
-@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("path,prime", [("ntt31", 28), ("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
 def test_sum_groups(lib, path, prime):
     # pa_opts.fd_group caps the key tiles per transform-domain sum: ceil(Q / g) sums per
     # output tile, each with its own output spectrum

@@ -22,7 +22,7 @@ GEOMS = [(50_003, 20_011, 13, 4096, 4096), (50_003, 20_011, 13, 4096, 2048),
          (200_000, 3_000, 13, 4096, 1024), (9_000, 200_000, 13, 1024, 4096)]
 
 
-@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("path,prime", [("ntt31", 28), ("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
 @pytest.mark.parametrize("n,m,k,L,M", GEOMS)
 def test_fd_matches_oracle(path, prime, n, m, k, L, M):
     blk = inputs.single_block(n, m, 31 + n, 37 + m)
@@ -40,7 +40,7 @@ STREAMED = [(50_003, 3_000, 13, 4096, 3008), (131_075, 5_000, 14, 8192, 5056),
             (8_191, 1, 13, 4096, 64), (1_000_003, 60_000, 17, 70_016, 60_032)]
 
 
-@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("path,prime", [("ntt31", 28), ("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
 @pytest.mark.parametrize("n,m,k,L,M", STREAMED)
 def test_streamed_matches_oracle(path, prime, n, m, k, L, M):
     blk = inputs.single_block(n, m, 41 + n, 43 + m)
@@ -68,7 +68,7 @@ def test_fd_largest_coefficients(kind):
     assert desc["fd"] == 1 and np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("path,prime", [("ntt31", 28), ("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
 @pytest.mark.parametrize("geom", [GEOMS[0], GEOMS[3], GEOMS[5], GEOMS[7]])
 @pytest.mark.parametrize("group", [1, 3])
 def test_grouped_sums_match_oracle(path, prime, geom, group):
@@ -105,6 +105,24 @@ def test_grouped_sums_at_the_exactness_limit():
         assert int(got[-1]) >> (m % 64) == 0
     rows = np.array([0, 1, m // 2, m - 1])
     assert np.array_equal(bits[rows], oracle.hash_rows(n, m, seed, key, rows))
+
+
+def test_grouped_sums_at_the_exactness_limit_28bit():
+    # The same at the 28-bit prime p = 167,772,161 (forced): with L = 2^23 - 4096 a sum
+    # covers g = 20 key tiles (20 L = 167,690,240 < p; 21 L would wrap), so n = 2e8 + 1
+    # takes two sums (20 + 4 key tiles) per output tile and the first sum's coefficients
+    # reach 20 L, within 82,000 of p: the lazily reduced rounds run on counts next to the
+    # prime. Every output bit is n mod 2.
+    n, m = 200_000_001, 3_001
+    L, M = (1 << 23) - 4096, 4096
+    key = np.full((n + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    seed = np.full((n + m - 1 + 63) // 64, np.uint64(0xFFFFFFFFFFFFFFFF))
+    got, desc = run_path(n, m, key, seed, path="ntt31", log2_transform=23, tile_in=L, tile_out=M,
+                         fd_mode=2, ntt_prime=28)
+    assert (desc["prime_bits"], desc["fd"], desc["tiles_in"], desc["sum_groups"]) == (28, 1, 24, 2)
+    assert ((167_772_161 - 1) // L, 20 * L < 167_772_161 <= 21 * L) == (20, True)
+    bits = oracle.unpack(got, m)
+    assert np.all(bits == (n & 1))
 
 
 def test_fd_and_standard_tiles_in_one_launch():
@@ -168,7 +186,7 @@ def big_case():
 
 @pytest.mark.parametrize("group", [0, 1])
 @pytest.mark.parametrize("L,M,P", BIG_TILES)
-@pytest.mark.parametrize("path,prime", [("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
+@pytest.mark.parametrize("path,prime", [("ntt31", 28), ("ntt31", 29), ("ntt31", 31), ("ntt64", 0)])
 def test_largest_transform_matches_oracle(big_case, path, prime, L, M, P, group):
     n, m, k = BIG
     key, seed, want = big_case

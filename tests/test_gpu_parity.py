@@ -56,11 +56,12 @@ def test_shapes(path, n, m):
     _check(path, n, m, key, seed, want)
 
 
+@pytest.mark.parametrize("prime", [29, 31])
 @pytest.mark.parametrize("n,m", SHAPES)
-def test_shapes_31bit_prime(n, m):
-    # the NTT31 path takes the 29-bit prime below its bound; force the 31-bit one here
+def test_shapes_other_primes(n, m, prime):
+    # the NTT31 path takes the 28-bit prime below its bound; force the 29- and 31-bit ones
     key, seed, want = _case(n, m, 11 + n, 13 + m)
-    _check("ntt31", n, m, key, seed, want, ntt_prime=31)
+    _check("ntt31", n, m, key, seed, want, ntt_prime=prime)
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -137,7 +138,8 @@ def _sha(words):
     return hashlib.sha256(np.ascontiguousarray(words, dtype="<u8").tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("path,opts", [("ntt31", {}), ("ntt31", {"ntt_prime": 31}), ("ntt64", {}),
+@pytest.mark.parametrize("path,opts", [("ntt31", {}), ("ntt31", {"ntt_prime": 29}),
+                                       ("ntt31", {"ntt_prime": 31}), ("ntt64", {}),
                                        ("block_fp8", {}), ("direct", {}), ("block_int8", {}),
                                        ("fft", {})])
 def test_finite_size_full_output(path, opts):
@@ -296,7 +298,8 @@ def test_segmented_sums_full(path, seg_in, seg_out, fd_group):
     _check(path, n, m, key, seed, want, **opts)
 
 
-@pytest.mark.parametrize("path,opts", [("ntt31", {}), ("ntt31", {"ntt_prime": 31}), ("ntt64", {}),
+@pytest.mark.parametrize("path,opts", [("ntt31", {}), ("ntt31", {"ntt_prime": 29}),
+                                       ("ntt31", {"ntt_prime": 31}), ("ntt64", {}),
                                        ("ntt31", {"fd_group": 50}),
                                        ("ntt31", {"seg_in": 60, "seg_out": 20}),
                                        ("ntt31", {"fd_group": 40, "seg_in": 90, "seg_out": 25})])
@@ -304,7 +307,7 @@ def test_outer_convolution_sums_full(path, opts):
     # With equal key and output tiles the sums over key tiles are, bin by bin, convolutions
     # over the tile index: 123 key x 37 output tiles of 2^14 at N = 2^15 with those sums
     # forced to transforms over the tile index (one group, several groups, segments with
-    # ragged slices; the 29-, 31- and 64-bit fields), compared with the oracle in full.
+    # ragged slices; the 28-, 29-, 31- and 64-bit fields), compared with the oracle in full.
     n, m = 2_000_007, 600_003
     key, seed, want = _case(n, m, 91, 92)
     o = dict(log2_transform=15, tile_in=1 << 14, tile_out=1 << 14, fd_mode=2, outer_mode=2, **opts)
@@ -313,7 +316,8 @@ def test_outer_convolution_sums_full(path, opts):
     _check(path, n, m, key, seed, want, **o)
 
 
-@pytest.mark.parametrize("path,m,opts,logT", [("ntt31", 163_843, {}, 9), ("ntt31", 163_843, {"ntt_prime": 31}, 9),
+@pytest.mark.parametrize("path,m,opts,logT", [("ntt31", 163_843, {}, 9), ("ntt31", 163_843, {"ntt_prime": 29}, 9),
+                                              ("ntt31", 163_843, {"ntt_prime": 31}, 9),
                                               ("ntt64", 163_843, {}, 9), ("ntt31", 49_157, {"fd_group": 10}, 5)])
 def test_outer_convolution_fused_stages_full(path, m, opts, logT):
     # Outer transforms of 2^9 and 2^5 points over the tile index (log2 T = 1 mod 4: the
