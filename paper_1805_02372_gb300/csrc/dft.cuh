@@ -14,10 +14,12 @@
 //
 // Twiddles come from stage tables st[h - 1 + j] = w_{2h}^(+-j), j < h (R - 1 entries).
 //
-// Two bank-conflict-free layouts of a tile with R rows and C columns:
+// Bank-conflict-free layouts of a tile with R rows and C columns:
 //   RowMajor: element (r, c) at slot(r) * C + c, where slot rotates the rows inside each
 //             aligned group of four by (r >> 4) (C * sizeof(T) = 32 bytes per row);
-//   ColMajor: element (r, c) at c * (R + R/16) + r + (r >> 4) (one word of skew per 16).
+//   ColMajor: element (r, c) at c * (R + R/16) + r + (r >> 4) (one word of skew per 16);
+//   ColChunk: 32-bit elements, columns of R words whose 16-byte chunks (4 rows) stay whole,
+//             swizzled instead of skewed (see the struct).
 #pragma once
 
 #include <type_traits>
@@ -64,6 +66,105 @@ struct ColMajor {
     }
     static __host__ __device__ __forceinline__ int stride(int R) { return R + (R >> 4); }
     static __host__ __device__ __forceinline__ int words(int R, int C) { return C * stride(R); }
+};
+
+// Column tile of 32-bit elements (R = 2^logR >= 64 rows) for the contiguous passes of the
+// NTT. Rows of a column are stored in 64-byte lines of 16; element (r, c) lies in line
+// P = c R/16 + ((r >> 4) ^ fl), fl = ((r >> 8) ^ c) & 1 (adjacent 256-row blocks, and
+// adjacent columns, sit in opposite halves of a 128-byte bank row), at chunk
+// ((r >> 2) & 3) ^ ((P >> 1) & 3) of the line (the XOR spreads the chunks of eight
+// consecutive lines over the eight 16-byte bank groups), word r & 3. The 16-byte chunks of
+// four consecutive rows stay whole, so rows move with 16-byte copies and the stride-1
+// groups read and write four chunks; the rounds of stride 16 and >= 256 (one word per
+// lane), the stride-1 groups and the row copies (one chunk per lane, consecutive lanes on
+// consecutive chunks or groups) all meet 32 distinct banks per wavefront. A column set
+// starting at a multiple of 128 words and an even column keeps the swizzle, so
+// at(r, C0 + c) = C0 R + at(r, c) for even C0 with C0 R a multiple of 128.
+struct ColChunk {
+    int logR;
+    int cs;  // column stride: R words, no padding
+    __host__ __device__ __forceinline__ int at(int r, int c) const {
+        const int fl = ((r >> 8) ^ c) & 1;
+        const int P = (c << (logR - 4)) + ((r >> 4) ^ fl);
+        return (P << 4) + ((((r >> 2) & 3) ^ ((P >> 1) & 3)) << 2) + (r & 3);
+    }
+    // rows i0 + k 2^LQ, k < K, of column c: LQ = 4 (i0 = B + j, j < 16, the K rows within one
+    // 256-row block) or LQ >= 8
+    template <int LQ, int K>
+    __host__ __device__ __forceinline__ void addrs(int i0, int c, int (&a)[K]) const {
+        static_assert(LQ == 4 || LQ >= 8, "stride-1 groups use chunks()");
+        if constexpr (LQ == 4) {
+            // line (i0 >> 4) + k, flipped by fl (constant over k); the chunk XOR takes
+            // ((P >> 1) & 3) = h ^ ((k >> 1) & 3), h from the group's first line
+            const int j = i0 & 15, B = i0 - j;
+            const int fl = ((i0 >> 8) ^ c) & 1;
+            const int h = ((((c << (logR - 4)) + (B >> 4)) >> 1) & 3);
+            const int q1 = ((j >> 2) & 3) ^ h;
+            const int base = (c << logR) + B + (j & 3);
+            const int be = base + 16 * fl, bo = base - 16 * fl;
+#pragma unroll
+            for (int k = 0; k < K; ++k) a[k] = ((k & 1) ? bo : be) + 16 * k + 4 * (q1 ^ ((k >> 1) & 3));
+        } else {
+            // the chunk XOR is the same for every k; at LQ = 8 fl alternates with k, which
+            // moves the line by +-16 words on odd k
+            const int a0 = at(i0, c);
+            const int d = LQ == 8 ? 16 * (1 - 2 * (((i0 >> 4) ^ (((i0 >> 8) ^ c) & 1)) & 1)) : 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) a[k] = a0 + (k << LQ) + ((k & 1) ? d : 0);
+        }
+    }
+    // the four 16-byte chunks of rows i0 .. i0 + 15 (i0 a multiple of 16) of column c
+    __host__ __device__ __forceinline__ void chunks(int i0, int c, int (&a)[4]) const {
+        const int fl = ((i0 >> 8) ^ c) & 1;
+        const int P = (c << (logR - 4)) + ((i0 >> 4) ^ fl);
+        const int f = (P >> 1) & 3;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = (P << 4) + ((u ^ f) << 2);
+    }
+    static __host__ __device__ __forceinline__ int stride(int R) { return R; }
+    static __host__ __device__ __forceinline__ int words(int R, int C) { return C * R; }
+    static __host__ __device__ __forceinline__ ColChunk make(int logR) { return ColChunk{logR, 1 << logR}; }
+};
+
+// Rows i0 .. i0 + 15 of column c of a tile (a stride-1 group): sixteen words, or for
+// ColChunk four 16-byte chunks.
+template <class Lay>
+struct Rows16 {
+    int a[16];
+    __device__ __forceinline__ Rows16(const Lay &lay, int i0, int c) { lay.template addrs<0, 16>(i0, c, a); }
+    template <class T>
+    __device__ __forceinline__ void load(const T *sm, T (&x)[16]) const {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = sm[a[k]];
+    }
+    template <class T>
+    __device__ __forceinline__ void store(T *sm, const T (&x)[16]) const {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sm[a[k]] = x[k];
+    }
+};
+template <>
+struct Rows16<ColChunk> {
+    int a[4];
+    __device__ __forceinline__ Rows16(const ColChunk &lay, int i0, int c) { lay.chunks(i0, c, a); }
+    template <class T>
+    __device__ __forceinline__ void load(const T *sm, T (&x)[16]) const {
+        static_assert(sizeof(T) == 4, "ColChunk holds 32-bit elements");
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(sm + a[u]);
+            x[4 * u] = v.x;
+            x[4 * u + 1] = v.y;
+            x[4 * u + 2] = v.z;
+            x[4 * u + 3] = v.w;
+        }
+    }
+    template <class T>
+    __device__ __forceinline__ void store(T *sm, const T (&x)[16]) const {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<uint4 *>(sm + a[u]) = make_uint4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]);
+    }
 };
 
 // Stage tables of an R-point transform into shared memory: st[h-1+j] = w_{2h}^(+-j),
@@ -411,27 +512,38 @@ __device__ __forceinline__ void round_s(typename F::T *sm, const Lay &lay, int l
         const int j = g & (q - 1);
         const int i0 = ((g >> lq) << (lq + S)) + j;
         T x[1 << S];
-        int a[1 << S];
-        if (LQ >= 0) {
-            lay.template addrs<(LQ >= 0 ? LQ : 0), (1 << S)>(i0, c, a);
-        } else {
-#pragma unroll
-            for (int k = 0; k < (1 << S); ++k) a[k] = lay.at(i0 + k * q, c);
-        }
-#pragma unroll
-        for (int k = 0; k < (1 << S); ++k) x[k] = sm[a[k]];
-        if (LQ == 0) {  // q = 1, j = 0
+        if constexpr (LQ == 0 && S == 4 && std::is_same<Lay, ColChunk>::value) {
+            // a stride-1 group of a chunked tile: four 16-byte chunks
+            const Rows16<Lay> rows(lay, i0, c);
+            rows.load(sm, x);
             if (DIF)
                 dif_group_q1<F, S>(x, tw);
             else
                 dit_group_q1<F, S>(x, tw);
-        } else if (DIF) {
-            dif_group<F, S>(x, tw, j, q);
+            rows.store(sm, x);
         } else {
-            dit_group<F, S>(x, tw, j, q);
-        }
+            int a[1 << S];
+            if constexpr (LQ >= 0 && !(LQ == 0 && std::is_same<Lay, ColChunk>::value)) {
+                lay.template addrs<LQ, (1 << S)>(i0, c, a);
+            } else {
 #pragma unroll
-        for (int k = 0; k < (1 << S); ++k) sm[a[k]] = x[k];
+                for (int k = 0; k < (1 << S); ++k) a[k] = lay.at(i0 + k * q, c);
+            }
+#pragma unroll
+            for (int k = 0; k < (1 << S); ++k) x[k] = sm[a[k]];
+            if (LQ == 0) {  // q = 1, j = 0
+                if (DIF)
+                    dif_group_q1<F, S>(x, tw);
+                else
+                    dit_group_q1<F, S>(x, tw);
+            } else if (DIF) {
+                dif_group<F, S>(x, tw, j, q);
+            } else {
+                dit_group<F, S>(x, tw, j, q);
+            }
+#pragma unroll
+            for (int k = 0; k < (1 << S); ++k) sm[a[k]] = x[k];
+        }
     }
 }
 
@@ -470,11 +582,11 @@ __device__ __forceinline__ void round_any(int S, typename F::T *sm, const Lay &l
 // conflict-free. Pairs are numbered p = (c << (logR - 8)) + b.
 template <class F, class Lay>
 struct WarpLocal {
-    static constexpr bool value = sizeof(typename F::T) == 4 && std::is_same<Lay, ColMajor>::value;
+    static constexpr bool value = sizeof(typename F::T) == 4 && std::is_same<Lay, ColChunk>::value;
 };
 
-template <class F, bool DIF>
-__device__ __forceinline__ void wl_round16(typename F::T *sm, const ColMajor &lay, int c, int blk,
+template <class F, bool DIF, class Lay>
+__device__ __forceinline__ void wl_round16(typename F::T *sm, const Lay &lay, int c, int blk,
                                            int j, const typename F::Tw *tw) {
     typename F::T x[16];
     int a[16];
@@ -489,20 +601,17 @@ __device__ __forceinline__ void wl_round16(typename F::T *sm, const ColMajor &la
     for (int k = 0; k < 16; ++k) sm[a[k]] = x[k];
 }
 
-template <class F, bool DIF>
-__device__ __forceinline__ void wl_round1(typename F::T *sm, const ColMajor &lay, int c, int i0,
+template <class F, bool DIF, class Lay>
+__device__ __forceinline__ void wl_round1(typename F::T *sm, const Lay &lay, int c, int i0,
                                           const typename F::Tw *tw) {
     typename F::T x[16];
-    int a[16];
-    lay.template addrs<0, 16>(i0, c, a);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) x[k] = sm[a[k]];
+    const Rows16<Lay> rows(lay, i0, c);
+    rows.load(sm, x);
     if (DIF)
         dif_group_q1<F, 4>(x, tw);
     else
         dit_group_q1<F, 4>(x, tw);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) sm[a[k]] = x[k];
+    rows.store(sm, x);
 }
 
 // Runs body(c, blk, l16) for every (column, block) pair of ncols columns, a half-warp per
@@ -520,18 +629,18 @@ __device__ __forceinline__ void wl_pairs(int logR, int ncols, Body body) {
 
 // The eight low stages of an R-point transform on every column, warp-local (no CTA
 // barrier inside; the caller's barriers order them against the other rounds).
-template <class F, bool DIF>
-__device__ __forceinline__ void low_rounds_warp(typename F::T *sm, const ColMajor &lay, int logR, int ncols,
+template <class F, bool DIF, class Lay>
+__device__ __forceinline__ void low_rounds_warp(typename F::T *sm, const Lay &lay, int logR, int ncols,
                                 const typename F::Tw *tw) {
     wl_pairs(logR, ncols, [&](bool on, int c, int blk, int j) {
         if (DIF) {
-            if (on) wl_round16<F, true>(sm, lay, c, blk, j, tw);
+            if (on) wl_round16<F, true, Lay>(sm, lay, c, blk, j, tw);
             __syncwarp();
-            if (on) wl_round1<F, true>(sm, lay, c, (blk << 8) + (j << 4), tw);
+            if (on) wl_round1<F, true, Lay>(sm, lay, c, (blk << 8) + (j << 4), tw);
         } else {
-            if (on) wl_round1<F, false>(sm, lay, c, (blk << 8) + (j << 4), tw);
+            if (on) wl_round1<F, false, Lay>(sm, lay, c, (blk << 8) + (j << 4), tw);
             __syncwarp();
-            if (on) wl_round16<F, false>(sm, lay, c, blk, j, tw);
+            if (on) wl_round16<F, false, Lay>(sm, lay, c, blk, j, tw);
         }
     });
 }
@@ -660,21 +769,15 @@ __device__ __forceinline__ void product_group(typename F::T *sm, const Lay &lay,
                                               Mul mul) {
     using T = typename F::T;
     T x[16], y[16];
-    int ax[16], ay[16];
-    lay.template addrs<0, 16>(i0, cx, ax);
-    lay.template addrs<0, 16>(i0, cy, ay);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        x[k] = sm[ax[k]];
-        y[k] = sm[ay[k]];
-    }
+    const Rows16<Lay> rx(lay, i0, cx), ry(lay, i0, cy);
+    rx.load(sm, x);
+    ry.load(sm, y);
     dif_group_q1<F, 4>(x, twf);
     dif_group_q1<F, 4>(y, twf);
 #pragma unroll
     for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
     dit_group_q1<F, 4>(y, twi);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) sm[ay[k]] = y[k];
+    ry.store(sm, y);
 }
 
 // One group of 16 consecutive rows from i0: the last four forward stages of key column cx
@@ -684,20 +787,18 @@ __device__ __forceinline__ void product_acc_group(typename F::T *sm, const Lay &
                                                   int cy, int cz, const typename F::Tw *twf, Mul mul,
                                                   Add add) {
     using T = typename F::T;
-    T x[16], y[16];
-    int ax[16], ay[16], az[16];
-    lay.template addrs<0, 16>(i0, cx, ax);
-    lay.template addrs<0, 16>(i0, cy, ay);
-    lay.template addrs<0, 16>(i0, cz, az);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        x[k] = sm[ax[k]];
-        y[k] = sm[ay[k]];
-    }
+    T x[16], y[16], z[16];
+    const Rows16<Lay> rx(lay, i0, cx), ry(lay, i0, cy), rz(lay, i0, cz);
+    rx.load(sm, x);
+    ry.load(sm, y);
     dif_group_q1<F, 4>(x, twf);
     dif_group_q1<F, 4>(y, twf);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) sm[az[k]] = add(sm[az[k]], mul(x[k], y[k]));
+    for (int k = 0; k < 16; ++k) y[k] = mul(x[k], y[k]);
+    rz.load(sm, z);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) z[k] = add(z[k], y[k]);
+    rz.store(sm, z);
 }
 
 // For each of C column pairs (key column c, window column C + c): product_group on every
@@ -734,22 +835,22 @@ __device__ __forceinline__ void product_acc_round(typename F::T *sm, const Lay &
 // R >= 256 (32-bit elements) the stages below half-size 256 of both spectra, the product
 // and the first inverse stages run warp-local per (column, block) pair, between the
 // CTA-wide top rounds.
-template <class F, class Mul>
-__device__ __forceinline__ void product_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
+template <class F, class Lay, class Mul>
+__device__ __forceinline__ void product_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                                 const typename F::Tw *twf, const typename F::Tw *twi, Mul mul) {
     const int C = 1 << logC;
-    if constexpr (WarpLocal<F, ColMajor>::value) {
+    if constexpr (WarpLocal<F, Lay>::value) {
         if (logR >= 8) {
             dif_top_rounds<F, false>(sm, lay, logR, logC + 1, twf);
             wl_pairs(logR, C, [&](bool on, int c, int blk, int j) {
                 if (on) {
-                    wl_round16<F, true>(sm, lay, c, blk, j, twf);
-                    wl_round16<F, true>(sm, lay, C + c, blk, j, twf);
+                    wl_round16<F, true, Lay>(sm, lay, c, blk, j, twf);
+                    wl_round16<F, true, Lay>(sm, lay, C + c, blk, j, twf);
                 }
                 __syncwarp();
                 if (on) product_group<F>(sm, lay, (blk << 8) + (j << 4), c, C + c, twf, twi, mul);
                 __syncwarp();
-                if (on) wl_round16<F, false>(sm, lay, C + c, blk, j, twi);
+                if (on) wl_round16<F, false, Lay>(sm, lay, C + c, blk, j, twi);
             });
             __syncthreads();
             dit_top_rounds<F, false>(sm + C * lay.cs, lay, logR, logC, twi);
@@ -763,17 +864,17 @@ __device__ __forceinline__ void product_columns(typename F::T *sm, const ColMajo
 
 // Forward transforms of C key and C window columns and acc[c] += their pointwise products
 // (accumulator column acc_col0 + c), warp-local below the top rounds as in product_columns.
-template <class F, class Mul, class Add>
-__device__ __forceinline__ void product_acc_columns(typename F::T *sm, const ColMajor &lay, int logR, int logC,
+template <class F, class Lay, class Mul, class Add>
+__device__ __forceinline__ void product_acc_columns(typename F::T *sm, const Lay &lay, int logR, int logC,
                                     int acc_col0, const typename F::Tw *twf, Mul mul, Add add) {
     const int C = 1 << logC;
-    if constexpr (WarpLocal<F, ColMajor>::value) {
+    if constexpr (WarpLocal<F, Lay>::value) {
         if (logR >= 8) {
             dif_top_rounds<F, false>(sm, lay, logR, logC + 1, twf);
             wl_pairs(logR, C, [&](bool on, int c, int blk, int j) {
                 if (on) {
-                    wl_round16<F, true>(sm, lay, c, blk, j, twf);
-                    wl_round16<F, true>(sm, lay, C + c, blk, j, twf);
+                    wl_round16<F, true, Lay>(sm, lay, c, blk, j, twf);
+                    wl_round16<F, true, Lay>(sm, lay, C + c, blk, j, twf);
                 }
                 __syncwarp();
                 if (on)

@@ -851,7 +851,11 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     info->nitems = items.size();
     info->nfd = fds.size();
     info->slots = static_cast<uint32_t>(slots ? slots : 1);
-    // shared memory: the largest need among the bodies present
+    // shared memory: the largest need among the bodies present (the contiguous passes of the
+    // 32-bit fields use the unpadded chunked tile, the 64-bit field the skewed columns)
+    const auto pass_words = [elem](uint32_t logR, int cols) {
+        return elem == 4 ? size_t(ColChunk::words(1 << logR, cols)) : size_t(ColMajor::words(1 << logR, cols));
+    };
     size_t smem = 0;
     for (const NttTile &t : small)
         smem = std::max(smem, (size_t(2) << t.logN) * twsz +
@@ -868,17 +872,16 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     // fused pass 2 of a standard pair: both stage tables, key and window rows
     for (const NttTile &t : big)
         smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
-                                  size_t(ColMajor::words(1 << t.logR2, 2 << t.logC2)) * elem);
+                                  pass_words(t.logR2, 2 << t.logC2) * elem);
     // forward pass 2 of an fd spectrum: the forward stage table and C2 rows
     for (const NttTile &t : fd_spec)
         smem = std::max(smem, (size_t(1) << t.logR2) * twsz +
-                                  size_t(ColMajor::words(1 << t.logR2, 1 << t.logC2)) * elem);
+                                  pass_words(t.logR2, 1 << t.logC2) * elem);
     // fd sums: the inverse stage table and kSum4Out x C columns of R2 rows; for outer
     // blocks the inverse pass 2 of one sum (the stage table and C rows)
     for (const NttTile &t : fd_sum)
         smem = std::max(smem, (size_t(1) << t.logR2) * twsz +
-                                  size_t(ColMajor::words(1 << t.logR2, (fds[t.fd].outer ? 1 : kSum4Out)
-                                                                          << t.logC2)) * elem);
+                                  pass_words(t.logR2, (fds[t.fd].outer ? 1 : kSum4Out) << t.logC2) * elem);
     // outer convolutions: both stage tables of T points, the forward tile (2 C columns of
     // T rows) and the product tile (C columns)
     for (const NttTile &t : fd_outer)
@@ -887,7 +890,7 @@ int ntt_batch_build(int field, const std::vector<BatchBlock> &blocks, uint32_t m
     // streamed sums: key, window and accumulator columns, then the window indices
     for (const NttTile &t : st_sum)
         smem = std::max(smem, 2 * (size_t(1) << t.logR2) * twsz +
-                                  size_t(ColMajor::words(1 << t.logR2, 3 << t.logC2)) * elem +
+                                  pass_words(t.logR2, 3 << t.logC2) * elem +
                                   size_t(fds[t.fd].Q) * sizeof(uint32_t));
     info->smem = smem;
     // workspace layout

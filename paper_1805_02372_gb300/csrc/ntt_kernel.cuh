@@ -143,13 +143,55 @@ constexpr int kTwBatch = 2;
 
 // Asynchronous global -> shared copies (no registers held while they are in flight);
 // cp_async_wait_all waits for this thread's copies, a barrier then publishes them.
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Tile layout of the contiguous passes (pass 2 and the transform-domain sums): 32-bit
+// fields keep 16-byte chunks whole (ColChunk: rows staged and stored 16 bytes at a time),
+// the 64-bit field keeps the skewed columns.
+template <class T>
+struct PassLay {
+    using type = ColMajor;
+    static __device__ __forceinline__ ColMajor make(int logR) { return ColMajor{ColMajor::stride(1 << logR)}; }
+};
+template <>
+struct PassLay<uint32_t> {
+    using type = ColChunk;
+    static __device__ __forceinline__ ColChunk make(int logR) { return ColChunk::make(logR); }
+};
+
+// Rows of a 32-bit tile from global memory (element e of g is row e & (R - 1) of shared
+// column c0 + (e >> logR)) by 16-byte asynchronous copies, one chunk per lane; the caller
+// waits (cp_async_wait_all) and synchronises.
+template <class T>
+__device__ __forceinline__ void stage_rows(T *sm, const ColChunk &lay, int c0, const T *__restrict__ g, int cnt,
+                                           int logR) {
+    static_assert(sizeof(T) == 4, "chunked tiles hold 32-bit elements");
+    const int R = 1 << logR;
+    for (int e = threadIdx.x * 4; e < cnt; e += blockDim.x * 4)
+        cp_async16(sm + lay.at(e & (R - 1), c0 + (e >> logR)), g + e);
+}
+// The reverse: columns c0 .. of the shared tile to global rows, 16 bytes per lane.
+template <class T, class Lay>
+__device__ __forceinline__ void store_rows(T *__restrict__ g, const T *sm, const Lay &lay, int c0, int cnt,
+                                           int logR) {
+    const int R = 1 << logR;
+    constexpr int V = 16 / sizeof(T);
+    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+        const int c = c0 + (e >> logR), r = e & (R - 1);
+        uint4 ov;
+        if constexpr (sizeof(T) == 4) {
+            ov = *reinterpret_cast<const uint4 *>(sm + lay.at(r, c));
+        } else {
+            T *os = reinterpret_cast<T *>(&ov);
+#pragma unroll
+            for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
+        }
+        __stcg(reinterpret_cast<uint4 *>(g + e), ov);
+    }
+}
 
 // Pass-1 twiddles (forward and inverse items) without a table lookup per row. Row r holds
 // frequency f = brev(r) = 32 fh + fl, and segment sg starts at column t0 = c0 + sg SEG, so
@@ -273,14 +315,11 @@ __device__ __forceinline__ void body_fused_last(typename F::T *sm, const typenam
     constexpr int V = 16 / sizeof(T);  // elements per 16-byte vector
     const int R2 = 1 << logR2;
     const uint64_t base = (rg << logC) << logR2;
-    const ColMajor lay{ColMajor::stride(R2)};
+    const auto lay = PassLay<T>::make(logR2);
     const int cnt = R2 << logC;
-    if (sizeof(T) == 4) {
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            const int c = e >> logR2, r = e & (R2 - 1);
-            cp_async4(sm + lay.at(r, c), X + base + e);
-            cp_async4(sm + lay.at(r, C + c), W + base + e);
-        }
+    if constexpr (sizeof(T) == 4) {
+        stage_rows(sm, lay, 0, X + base, cnt, logR2);
+        stage_rows(sm, lay, C, W + base, cnt, logR2);
         cp_async_wait_all();
     } else {
         for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
@@ -298,14 +337,7 @@ __device__ __forceinline__ void body_fused_last(typename F::T *sm, const typenam
     __syncthreads();
     // logR2 >= 6 for every two-pass transform (N >= 2^13)
     product_columns<F>(sm, lay, logR2, logC, stf, sti, [](T a, T b) { return F::mont(a, b); });
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        uint4 ov;
-        T *os = reinterpret_cast<T *>(&ov);
-#pragma unroll
-        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, C + c)];
-        __stcg(reinterpret_cast<uint4 *>(W + base + e), ov);
-    }
+    store_rows(W + base, sm, lay, C, cnt, logR2);
     __syncthreads();
 }
 
@@ -393,25 +425,23 @@ __device__ __forceinline__ void body_fwd_last(typename F::T *sm, const typename 
     constexpr int V = 16 / sizeof(T);
     const int R2 = 1 << logR2;
     const uint64_t base = (rg << logC) << logR2;
-    const ColMajor lay{ColMajor::stride(R2)};
+    const auto lay = PassLay<T>::make(logR2);
     const int cnt = R2 << logC;
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
-        const T *xs = reinterpret_cast<const T *>(&v);
+    if constexpr (sizeof(T) == 4) {
+        stage_rows(sm, lay, 0, A + base, cnt, logR2);
+        cp_async_wait_all();
+    } else {
+        for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
+            const T *xs = reinterpret_cast<const T *>(&v);
 #pragma unroll
-        for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+            for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+        }
     }
     __syncthreads();
     dif_columns<F, false>(sm, lay, logR2, logC, stf);
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        uint4 ov;
-        T *os = reinterpret_cast<T *>(&ov);
-#pragma unroll
-        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
-        __stcg(reinterpret_cast<uint4 *>(A + base + e), ov);
-    }
+    store_rows(A + base, sm, lay, 0, cnt, logR2);
     __syncthreads();
 }
 
@@ -440,7 +470,7 @@ __device__ __forceinline__ void body_sum4_inv_last(typename F::T *sm, const type
     const int R2 = 1 << logR2, C = 1 << logC;
     const int E = R2 << logC;  // elements of one output in this item
     const uint64_t base = (rg << logC) << logR2;
-    const ColMajor lay{ColMajor::stride(R2)};
+    const auto lay = PassLay<T>::make(logR2);
     for (int h0 = 0; h0 < E; h0 += kSum4Elems) {
         const uint64_t hb = base + h0;
         T acc[kSum4Out][VPT][V];
@@ -526,21 +556,18 @@ __device__ __forceinline__ void body_sum4_inv_last(typename F::T *sm, const type
             for (int v = 0; v < VPT; ++v) {
                 const int e = h0 + (threadIdx.x + v * kThreads) * V;
                 const int c = e >> logR2, r = e & (R2 - 1);
+                if constexpr (sizeof(T) == 4) {
+                    *reinterpret_cast<uint4 *>(sm + lay.at(r, o * C + c)) =
+                        make_uint4(acc[o][v][0], acc[o][v][1], acc[o][v][2], acc[o][v][3]);
+                } else {
 #pragma unroll
-                for (int k = 0; k < V; ++k) sm[lay.at(r + k, o * C + c)] = acc[o][v][k];
+                    for (int k = 0; k < V; ++k) sm[lay.at(r + k, o * C + c)] = acc[o][v][k];
+                }
             }
     }
     __syncthreads();
     dit_columns<F, false>(sm, lay, logR2, logC + 2, sti);
-    for (int o = 0; o < static_cast<int>(nout); ++o)
-        for (int e = threadIdx.x * V; e < E; e += blockDim.x * V) {
-            const int c = e >> logR2, r = e & (R2 - 1);
-            uint4 ov;
-            T *os = reinterpret_cast<T *>(&ov);
-#pragma unroll
-            for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, o * C + c)];
-            __stcg(reinterpret_cast<uint4 *>(Z + uint64_t(o) * N + base + e), ov);
-        }
+    for (int o = 0; o < static_cast<int>(nout); ++o) store_rows(Z + uint64_t(o) * N + base, sm, lay, o * C, E, logR2);
     __syncthreads();
 }
 
@@ -561,7 +588,7 @@ __device__ __forceinline__ void body_stream_sum(typename F::T *sm, const typenam
     const int C = 1 << logC;
     const int R2 = 1 << logR2;
     const uint64_t base = (rg << logC) << logR2;
-    const ColMajor lay{ColMajor::stride(R2)};
+    const auto lay = PassLay<T>::make(logR2);
     const int cnt = R2 << logC;
     T *acc = sm + 2 * C * lay.cs;
     // the window index of every key tile, fetched once (not one dependent load per tile)
@@ -572,12 +599,9 @@ __device__ __forceinline__ void body_stream_sum(typename F::T *sm, const typenam
     for (uint32_t J = 0; J < Q; ++J) {
         const T *xj = X + uint64_t(J) * N + base;
         const T *wj = W + uint64_t(wix[J]) * N + base;
-        if (sizeof(T) == 4) {
-            for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-                const int c = e >> logR2, r = e & (R2 - 1);
-                cp_async4(sm + lay.at(r, c), xj + e);
-                cp_async4(sm + lay.at(r, C + c), wj + e);
-            }
+        if constexpr (sizeof(T) == 4) {
+            stage_rows(sm, lay, 0, xj, cnt, logR2);
+            stage_rows(sm, lay, C, wj, cnt, logR2);
             cp_async_wait_all();
         } else {
             for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
@@ -598,14 +622,7 @@ __device__ __forceinline__ void body_stream_sum(typename F::T *sm, const typenam
                                [](T a, T b) { return F::add(a, b); });
     }
     dit_columns<F, false>(acc, lay, logR2, logC, sti);
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        uint4 ov;
-        T *os = reinterpret_cast<T *>(&ov);
-#pragma unroll
-        for (int k = 0; k < V; ++k) os[k] = acc[lay.at(r + k, c)];
-        __stcg(reinterpret_cast<uint4 *>(Z + base + e), ov);
-    }
+    store_rows(Z + base, acc, lay, 0, cnt, logR2);
     __syncthreads();
 }
 
@@ -726,25 +743,23 @@ __device__ __forceinline__ void body_inv_last(typename F::T *sm, const typename 
     constexpr int V = 16 / sizeof(T);
     const int R2 = 1 << logR2;
     const uint64_t base = (rg << logC) << logR2;
-    const ColMajor lay{ColMajor::stride(R2)};
+    const auto lay = PassLay<T>::make(logR2);
     const int cnt = R2 << logC;
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
-        const T *xs = reinterpret_cast<const T *>(&v);
+    if constexpr (sizeof(T) == 4) {
+        stage_rows(sm, lay, 0, A + base, cnt, logR2);
+        cp_async_wait_all();
+    } else {
+        for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
+            const int c = e >> logR2, r = e & (R2 - 1);
+            const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(A + base + e));
+            const T *xs = reinterpret_cast<const T *>(&v);
 #pragma unroll
-        for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+            for (int k = 0; k < V; ++k) sm[lay.at(r + k, c)] = xs[k];
+        }
     }
     __syncthreads();
     dit_columns<F, false>(sm, lay, logR2, logC, sti);
-    for (int e = threadIdx.x * V; e < cnt; e += blockDim.x * V) {
-        const int c = e >> logR2, r = e & (R2 - 1);
-        uint4 ov;
-        T *os = reinterpret_cast<T *>(&ov);
-#pragma unroll
-        for (int k = 0; k < V; ++k) os[k] = sm[lay.at(r + k, c)];
-        __stcg(reinterpret_cast<uint4 *>(A + base + e), ov);
-    }
+    store_rows(A + base, sm, lay, 0, cnt, logR2);
     __syncthreads();
 }
 
