@@ -207,31 +207,69 @@ class Runner:
 
     def e2e(self, steps: int):
         """Same metric through the host-buffer entry points (pinned host memory), copies
-        inside the timed region; returns (Gbps, h2d bytes, d2h bytes) per step."""
+        inside the timed region; returns (Gbps, h2d bytes, d2h bytes, serial Gbps, how) per
+        step. Batched: every step copies all keys and seeds in and all outputs out; two
+        batches of the same plan alternate on two streams (pa_batch_run_host_async, copies
+        by the copy engines), so one step's copies run while the other step computes. The
+        serial figure runs one synchronous pa_batch_run_host per step."""
         torch = self.torch
         pin = lambda a: torch.from_numpy(a.view(np.int64)).pin_memory()
         kh = [pin(k) for k in self.keys_h]
         sh = [pin(s) for s in self.seeds_h]
-        oh = [torch.zeros((b.m + 63) // 64, dtype=torch.int64).pin_memory() for b in self.blocks]
+        zeros = lambda: [torch.zeros((b.m + 63) // 64, dtype=torch.int64).pin_memory() for b in self.blocks]
+        oh = zeros()
         h2d = sum(8 * (k.numel() + s.numel()) for k, s in zip(kh, sh))
         d2h = sum(8 * o.numel() for o in oh)
-        if self.batched:
-            # descriptors marshalled once (same buffers every step); every step still copies
-            # all keys and seeds in and all outputs out
-            desc = self.pkg.BlockList([(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh)])
-            run = lambda: self.pkg.pa_batch_run_host(self.batch, desc, self.stream)
-        else:
-            run = lambda: [p.hash_host(s, k, o, self.stream)
-                           for p, s, k, o in zip(self.plans, sh, kh, oh)]
-        run()
-        t0 = time.perf_counter()
-        for _ in range(steps):
+
+        def timed(run):
             run()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                run()
+            return (time.perf_counter() - t0) / steps
+
+        def check(outs):
+            for o, w in zip(outs, self.outs):
+                if not np.array_equal(o.numpy(), w.cpu().numpy()):
+                    raise SystemExit("host-buffer entry point disagrees with the device one")
+
+        if not self.batched:
+            dt = timed(lambda: [p.hash_host(s, k, o, self.stream)
+                                for p, s, k, o in zip(self.plans, sh, kh, oh)])
+            check(oh)
+            g = self.units / dt / 1e9
+            return g, h2d, d2h, g, "one synchronous pa_hash_host per block and step"
+        # descriptors marshalled once (same buffers every step)
+        desc = self.pkg.BlockList([(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh)])
+        serial = timed(lambda: self.pkg.pa_batch_run_host(self.batch, desc, self.stream))
+        check(oh)
+        oh2, oh3 = zeros(), zeros()
+        d2 = self.pkg.BlockList([(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh2)])
+        d3 = self.pkg.BlockList([(b.n, b.m, s, k, o) for b, s, k, o in zip(self.blocks, sh, kh, oh3)])
+        b2 = self.pkg.pa_batch_plan(self.desc, self.pkg.make_opts(path=self.path))
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        pairs = [(self.batch, d2, streams[0]), (b2, d3, streams[1])]
+
+        def piped(k):
+            for i in range(k):
+                b, d, st = pairs[i % 2]
+                self.pkg.pa_batch_run_host_async(b, d, st)
+            for st in streams:
+                st.synchronize()
+
+        piped(2)
+        t0 = time.perf_counter()
+        piped(steps)
         dt = (time.perf_counter() - t0) / steps
-        for o, w in zip(oh, self.outs):
-            if not np.array_equal(o.numpy(), w.cpu().numpy()):
-                raise SystemExit("host-buffer entry point disagrees with the device one")
-        return self.units / dt / 1e9, h2d, d2h
+        for b, _, st in pairs:
+            self.pkg.pa_batch_get_report(b, st)
+        check(oh2)
+        check(oh3)
+        self.pkg.pa_batch_destroy(b2)
+        return (self.units / dt / 1e9, h2d, d2h, self.units / serial / 1e9,
+                "two batches of the same plan alternating on two streams (pa_batch_run_host_async: "
+                "all keys and seeds copied in and all outputs out every step, by the copy engines, "
+                "one step's copies overlapping the other step's kernels)")
 
 
 def check_sampled(runner, rows_per_block=64, seed=7):
@@ -853,7 +891,7 @@ def main():
     exact_full = check_full(runner, digests)
     exact = check_sampled(runner) if exact_full is None else exact_full
     clocks = clk.summary()
-    e2e_gbps, h2d, d2h = runner.e2e(max(3, args.steps // 2))
+    e2e_gbps, h2d, d2h, e2e_serial, e2e_how = runner.e2e(max(3, args.steps // 2))
 
     units = runner.units * world
     value = units / (ms * 1e-3) / 1e9
@@ -868,7 +906,7 @@ def main():
                           else {"bit_exact_sampled": exact})),
         "roofline": roofline(kt, blocks, runner.plan_desc, args.steps, args.workload, probe),
         "e2e": {"value": e2e_gbps * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "serial_value": e2e_serial * world, "how": e2e_how},
         "gpu_launches": launches * args.steps, "clocks": clocks,
         "kernel_times_ms": {k: round(v["total_ms"] / args.steps, 5) for k, v in kt.items()},
         "ms_per_step_traced": ms_traced, "wall_s": wall,

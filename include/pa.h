@@ -264,6 +264,26 @@ int pa_batch_run(pa_batch_t batch, const pa_block *blocks, size_t count, void *s
 int pa_batch_run_host(pa_batch_t batch, const pa_block *host_blocks, size_t count, void *stream,
                       pa_report *rep);
 
+/* Same as pa_batch_run_host without synchronising: enqueues on `stream` the copies of every
+ * key and seed into the batch's device staging, the batch's kernels and the copies of the
+ * outputs back to host_blocks[i].out_bits, all copies by cudaMemcpyAsync (the copy engines,
+ * no SM time). With page-locked host buffers the call returns once everything is enqueued
+ * and the copies can overlap kernels running on other streams: two batches planned for the
+ * same blocks, run alternately on two streams, move one step's keys in and outputs out
+ * while the other step computes (the paper's blocks streamed through the GPU with copies
+ * hidden, Sec. 3). Pageable buffers work but the runtime stages them synchronously.
+ * The host buffers must stay valid, and the outputs are not ready, until the stream has
+ * passed this call's work. One call per batch in flight: the staging is the batch's, so
+ * a second call on the same batch must be ordered after the first (same stream, or an event).
+ * PA_ERR_INVALID for a mismatched block list; kernel-side errors are read afterwards with
+ * pa_batch_get_report. */
+int pa_batch_run_host_async(pa_batch_t batch, const pa_block *host_blocks, size_t count, void *stream);
+
+/* The report of the batch's last run, read after the work enqueued on `stream`: copies the
+ * batch's device header on that stream and synchronises it. rep as in pa_batch_run; returns
+ * the device status (PA_OK, or e.g. PA_ERR_TIMEOUT from a bounded wait that gave up). */
+int pa_batch_get_report(pa_batch_t batch, void *stream, pa_report *rep);
+
 /* What the batch plan chose for each block (path, tiles, transform size); count must be
  * the batch's block count. workspace_bytes of a block in its prime field's shared
  * persistent launch counts only a header: that launch's tables and spectra belong to the

@@ -8,7 +8,7 @@ loudly if it has not been built.
 """
 from . import inputs, serve  # noqa: F401
 from .binding import (BlockList, Plan, PAError, pa_batch_describe, pa_batch_destroy, pa_batch_run_host, pa_batch_plan, pa_batch_run,  # noqa: F401
-                      pa_batch_kernel_times, pa_batch_profile,
+                      pa_batch_kernel_times, pa_batch_profile, pa_batch_run_host_async, pa_batch_get_report,
                       pa_fft_rounding_bound, pa_hash, pa_hash_batched, pa_plan_kernel_times, pa_plan_profile, pa_hash_host, pa_last_residual, pa_plan,
                       pa_plan_describe, pa_plan_destroy, pa_plan_ex, pa_plan_query,
                       pa_plan_status, pa_server_create, pa_server_destroy, pa_server_pending,

@@ -130,6 +130,8 @@ SIGNATURES = {
     "pa_batch_destroy": (None, [_VP]),
     "pa_batch_run_host": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
                                          ctypes.POINTER(pa_report)]),
+    "pa_batch_run_host_async": (ctypes.c_int, [_VP, ctypes.POINTER(pa_block), ctypes.c_size_t, _VP]),
+    "pa_batch_get_report": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(pa_report)]),
     "pa_batch_describe": (ctypes.c_int, [_VP, ctypes.POINTER(pa_plan_desc), ctypes.c_size_t]),
     "pa_hash_batched": (ctypes.c_int, [ctypes.POINTER(pa_block), ctypes.c_size_t, _VP,
                                        ctypes.POINTER(pa_report)]),
@@ -350,6 +352,20 @@ def pa_batch_run_host(batch: int, blocks, stream=None, report: bool = False) -> 
     _check(load().pa_batch_run_host(batch, arr, cnt, _stream(stream),
                                     ctypes.byref(rep) if rep else None), "pa_batch_run_host")
     return rep.as_dict() if rep else None
+
+
+def pa_batch_run_host_async(batch: int, blocks, stream=None) -> None:
+    """blocks: (n, m, seed, key, out) with HOST buffers (pinned tensors for overlap) or a
+    BlockList of them; enqueues copies in, the batch and copies out on `stream`, returns."""
+    arr, cnt = _blocks(blocks)
+    _check(load().pa_batch_run_host_async(batch, arr, cnt, _stream(stream)), "pa_batch_run_host_async")
+
+
+def pa_batch_get_report(batch: int, stream=None) -> dict:
+    """The batch's report after the work enqueued on `stream` (synchronises that stream)."""
+    rep = pa_report()
+    _check(load().pa_batch_get_report(batch, _stream(stream), ctypes.byref(rep)), "pa_batch_get_report")
+    return rep.as_dict()
 
 
 def pa_batch_describe(batch: int, count: int) -> list:

@@ -759,9 +759,11 @@ int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *strea
     return PA_OK;
 }
 
-int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, void *stream,
-                      pa_report *rep) {
-    if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+namespace {
+
+// Device staging of pa_batch_run_host(_async) (allocated on first use) and the device
+// descriptors of the staged blocks; PA_ERR_INVALID if a host block does not match the plan.
+int host_stage(pa_batch_s *b, const pa_block *host_blocks, size_t count, std::vector<pa_block> *dev) {
     if (!b->stage) {
         size_t off = 0;
         for (size_t i = 0; i < count; ++i) {
@@ -775,21 +777,36 @@ int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, v
         cudaError_t e = cudaMalloc(&b->stage, off);
         if (e != cudaSuccess) {
             b->stage = nullptr;
+            b->st_seed.clear();
+            b->st_key.clear();
+            b->st_out.clear();
             return cuda_fail(e);
         }
         b->stage_bytes = off;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *st = static_cast<char *>(b->stage);
-    std::vector<pa_block> dev(count);
+    dev->resize(count);
     for (size_t i = 0; i < count; ++i) {
         const pa_block &h = host_blocks[i];
         if (h.n != b->n[i] || h.m != b->m[i] || !h.seed_bits || !h.key_bits || !h.out_bits)
             return PA_ERR_INVALID;
-        dev[i] = {h.n, h.m, reinterpret_cast<const uint64_t *>(st + b->st_seed[i]),
-                  reinterpret_cast<const uint64_t *>(st + b->st_key[i]),
-                  reinterpret_cast<uint64_t *>(st + b->st_out[i])};
+        (*dev)[i] = {h.n, h.m, reinterpret_cast<const uint64_t *>(st + b->st_seed[i]),
+                     reinterpret_cast<const uint64_t *>(st + b->st_key[i]),
+                     reinterpret_cast<uint64_t *>(st + b->st_out[i])};
     }
+    return PA_OK;
+}
+
+}  // namespace
+
+int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, void *stream,
+                      pa_report *rep) {
+    if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+    std::vector<pa_block> dev;
+    const int src = host_stage(b, host_blocks, count, &dev);
+    if (src != PA_OK) return src;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *st = static_cast<char *>(b->stage);
     // When every host buffer is page-locked and mapped for this device, one gather kernel
     // reads all keys and seeds and one scatter kernel writes all outputs (instead of three
     // copies per block); otherwise one cudaMemcpyAsync per buffer.
@@ -863,6 +880,43 @@ int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, v
         if (h.status != 0) return h.status;
     }
     return PA_OK;
+}
+
+int pa_batch_run_host_async(pa_batch_t b, const pa_block *host_blocks, size_t count, void *stream) {
+    if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+    std::vector<pa_block> dev;
+    const int src = host_stage(b, host_blocks, count, &dev);
+    if (src != PA_OK) return src;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *st = static_cast<char *>(b->stage);
+    // copies by the copy engines (no SM time: they overlap kernels of other streams)
+    for (size_t i = 0; i < count; ++i) {
+        const pa_block &h = host_blocks[i];
+        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits, ceil_div(h.n + h.m - 1, 64) * 8,
+                                    cudaMemcpyHostToDevice, s));
+        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
+                                    cudaMemcpyHostToDevice, s));
+    }
+    const int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
+    if (rc != PA_OK) return rc;
+    for (size_t i = 0; i < count; ++i)
+        PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i], ceil_div(b->m[i], 64) * 8,
+                                    cudaMemcpyDeviceToHost, s));
+    return PA_OK;
+}
+
+int pa_batch_get_report(pa_batch_t b, void *stream, pa_report *rep) {
+    if (!b || !rep) return PA_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevHeader h;
+    PA_CUDA_TRY(cudaMemcpyAsync(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PA_CUDA_TRY(cudaStreamSynchronize(s));
+    memset(rep, 0, sizeof(*rep));
+    memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
+    rep->bound = b->bound;
+    for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
+    rep->work_items = b->work_items;
+    return h.status != 0 ? h.status : PA_OK;
 }
 
 void pa_batch_destroy(pa_batch_t b) { batch_destroy_impl(b); }

@@ -129,6 +129,43 @@ def test_host_entry_pinned_buffers():
     pkg.pa_batch_destroy(batch)
 
 
+def test_host_async_two_batches_pipelined():
+    # pa_batch_run_host_async: two batches of the same plan alternate on two streams, each
+    # call copying keys and seeds in and outputs out by the copy engines without waiting;
+    # with different keys per step every output must be the oracle's for its own step's
+    # inputs (one pageable output buffer in one step takes the synchronous staging), and the
+    # reports read afterwards carry status 0.
+    import torch
+    shapes = MIXED[:8]
+    steps = []
+    for salt in (11, 13, 17, 19):
+        bl, keys, seeds = _blocks(shapes, salt=salt)
+        steps.append((bl, keys, seeds, [oracle.hash_full(b.n, b.m, s, k) for b, k, s in zip(bl, keys, seeds)]))
+    bl0 = steps[0][0]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()
+    batches = [pkg.pa_batch_plan([(b.n, b.m, None, None, None) for b in bl0]) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    held, outs = [], []
+    for t, (bl, keys, seeds, _) in enumerate(steps):
+        kh, sh = [pin(k) for k in keys], [pin(s) for s in seeds]
+        oh = [torch.full(((b.m + 63) // 64,), -1, dtype=torch.int64).pin_memory() for b in bl]
+        if t == 3:
+            oh[2] = np.full((bl[2].m + 63) // 64, np.uint64(5))  # pageable
+        held.append((kh, sh))  # the host buffers must outlive the enqueued copies
+        outs.append(oh)
+        pkg.pa_batch_run_host_async(batches[t % 2], [(b.n, b.m, s, k, o) for b, s, k, o in zip(bl, sh, kh, oh)],
+                                    streams[t % 2])
+    for b, st in zip(batches, streams):
+        rep = pkg.pa_batch_get_report(b, st)  # raises PAError on a nonzero device status
+        assert sum(rep["blocks_per_path"].values()) == len(shapes)
+    for t, (_, _, _, want) in enumerate(steps):
+        for i, (o, w) in enumerate(zip(outs[t], want)):
+            got = o if isinstance(o, np.ndarray) else o.numpy().view(np.uint64)
+            assert np.array_equal(got, w), (t, i)
+    for b in batches:
+        pkg.pa_batch_destroy(b)
+
+
 def test_batched_workload_256_blocks():
     import torch
     with open(os.path.join(HERE, "golden", "batched256.json")) as f:
