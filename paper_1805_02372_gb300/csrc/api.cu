@@ -44,7 +44,7 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool la
         case PA_PATH_DIRECT:
             rc = direct_plan(n, m, &cfg->direct);
             cfg->ws_bytes = direct_workspace(cfg->direct);
-            cfg->kernels = 2 + (cfg->direct.grid_y > 1 ? 1 : 0);
+            cfg->kernels = 2;  // key reversal (with output zeroing) and the direct kernel
             break;
         case PA_PATH_NTT64:
         case PA_PATH_NTT31:
@@ -63,12 +63,12 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool la
         case PA_PATH_BLOCK_INT8:
             rc = block_plan(n, m, o, &cfg->blk);
             cfg->ws_bytes = block_workspace(cfg->blk);
-            cfg->kernels = 2 + (cfg->blk.grid_y > 1 ? 1 : 0);
+            cfg->kernels = 2;  // key reversal (with output zeroing) and the contraction
             break;
         case PA_PATH_BLOCK_FP8:
             rc = block_tc_plan(n, m, o, &cfg->blk);
             cfg->ws_bytes = block_workspace(cfg->blk);
-            cfg->kernels = 3;  // output zeroing, key reversal, the MMA kernel
+            cfg->kernels = 2;  // key reversal (with output zeroing) and the MMA kernel
             break;
     }
     return rc;

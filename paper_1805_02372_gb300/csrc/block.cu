@@ -191,13 +191,10 @@ int block_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const
     const BlockCfg &c = cfg.blk;
     uint32_t *xr = static_cast<uint32_t *>(ws);
     const int use_atomic = c.grid_y > 1;
-    if (use_atomic) {
-        prof_begin(prof, K_MEMSET, s);
-        PA_CUDA_TRY(cudaMemsetAsync(out, 0, ceil_div(cfg.m, 64) * 8, s));
-        prof_end(prof, s);
-    }
+    // the key reversal also zeroes the output when the key chunks merge by atomicXor
     prof_begin(prof, K_REVERSE_KEY, s);
-    reverse_key_launch(key, cfg.n, xr, c.xr_words, c.xr_words_pad, s);
+    reverse_key_launch(key, cfg.n, xr, c.xr_words, c.xr_words_pad, s, use_atomic ? out : nullptr,
+                       ceil_div(cfg.m, 64));
     prof_end(prof, s);
     prof_begin(prof, K_BLOCK_MMA, s);
     int rc = PA_OK;

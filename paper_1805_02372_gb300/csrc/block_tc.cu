@@ -314,11 +314,9 @@ int block_tc_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, co
                     const uint64_t *key, uint64_t *out, cudaStream_t s) {
     const BlockCfg &c = cfg.blk;
     uint32_t *xr = static_cast<uint32_t *>(ws);
-    prof_begin(prof, K_MEMSET, s);
-    PA_CUDA_TRY(cudaMemsetAsync(out, 0, ceil_div(cfg.m, 64) * 8, s));
-    prof_end(prof, s);
+    // the key reversal also zeroes the output (the contraction merges by atomicXor)
     prof_begin(prof, K_REVERSE_KEY, s);
-    reverse_key_launch(key, cfg.n, xr, c.xr_words, c.xr_words_pad, s);
+    reverse_key_launch(key, cfg.n, xr, c.xr_words, c.xr_words_pad, s, out, ceil_div(cfg.m, 64));
     prof_end(prof, s);
     PA_CUDA_TRY(cudaFuncSetAttribute(block_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(kTcSmem)));

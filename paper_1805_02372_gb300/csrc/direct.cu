@@ -21,12 +21,16 @@ constexpr int kThreads = 128;      // 4 warps; one row group (32 rows) per threa
 constexpr int kRowGroups = kThreads;
 
 // xr[q] bit c = x[n-1-32q-c] (0 where that index is negative); zero padding past
-// ceil(n/32) words.
+// ceil(n/32) words. The same launch zeroes zero_words 64-bit words at `zero` (the output of
+// a kernel that merges its partial results with atomicXor), one operation fewer per hash.
 __global__ void reverse_key_kernel(const uint32_t *__restrict__ key32, uint64_t key_buf_words32,
                                    uint64_t n, uint32_t *__restrict__ xr, uint64_t words,
-                                   uint64_t words_pad) {
-    for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < words_pad;
+                                   uint64_t words_pad, uint64_t *__restrict__ zero, uint64_t zero_words) {
+    const uint64_t span = words_pad > zero_words ? words_pad : zero_words;
+    for (uint64_t q = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; q < span;
          q += uint64_t(gridDim.x) * blockDim.x) {
+        if (q < zero_words) zero[q] = 0;
+        if (q >= words_pad) continue;
         uint32_t v = 0;
         if (q < words) {
             int64_t lo = static_cast<int64_t>(n) - 1 - 32 * static_cast<int64_t>(q) - 31;
@@ -120,12 +124,13 @@ int direct_plan(uint64_t n, uint64_t m, DirectCfg *c) {
 }
 
 void reverse_key_launch(const uint64_t *key, uint64_t n, uint32_t *xr, uint64_t words,
-                        uint64_t words_pad, cudaStream_t s) {
-    uint64_t blocks = ceil_div(words_pad, 256);
+                        uint64_t words_pad, cudaStream_t s, uint64_t *zero, uint64_t zero_words) {
+    uint64_t blocks = ceil_div(words_pad > zero_words ? words_pad : zero_words, 256);
     if (blocks > 4096) blocks = 4096;
     if (blocks == 0) blocks = 1;
     reverse_key_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-        reinterpret_cast<const uint32_t *>(key), 2 * ceil_div(n, 64), n, xr, words, words_pad);
+        reinterpret_cast<const uint32_t *>(key), 2 * ceil_div(n, 64), n, xr, words, words_pad,
+        zero, zero ? zero_words : 0);
 }
 
 size_t direct_workspace(const DirectCfg &c) { return round_up(c.key_words32_pad * 4, 256); }
@@ -137,21 +142,11 @@ int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, cons
     uint32_t *xr = static_cast<uint32_t *>(ws);
     const uint64_t out_words64 = ceil_div(m, 64);
     const int use_atomic = c.grid_y > 1;
-    if (use_atomic) {
-        prof_begin(prof, K_MEMSET, s);
-        PA_CUDA_TRY(cudaMemsetAsync(out, 0, out_words64 * 8, s));
-        prof_end(prof, s);
-    }
-    {
-        prof_begin(prof, K_REVERSE_KEY, s);
-        const uint64_t words = c.key_words32_pad;
-        uint64_t blocks = ceil_div(words, 256);
-        if (blocks > 4096) blocks = 4096;
-        reverse_key_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(
-            reinterpret_cast<const uint32_t *>(key), 2 * ceil_div(n, 64), n, xr, c.key_words32,
-            words);
-        prof_end(prof, s);
-    }
+    // the key reversal also zeroes the output when the key chunks merge by atomicXor
+    prof_begin(prof, K_REVERSE_KEY, s);
+    reverse_key_launch(key, n, xr, c.key_words32, c.key_words32_pad, s, use_atomic ? out : nullptr,
+                       out_words64);
+    prof_end(prof, s);
     const size_t smem = (size_t(c.kc) + kRowGroups + c.kc + 4) * 4;
     if (smem > 48 * 1024)
         PA_CUDA_TRY(cudaFuncSetAttribute(direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -138,9 +138,11 @@ void prof_free(Prof *p);
 
 // Launchers (enqueue on stream; return PA_OK or PA_ERR_CUDA).
 int direct_plan(uint64_t n, uint64_t m, DirectCfg *c);
-// xr[q] bit c = x[n-1-32q-c] for q < words, zero up to words_pad.
+// xr[q] bit c = x[n-1-32q-c] for q < words, zero up to words_pad; the same launch zeroes
+// zero_words 64-bit words at `zero` when it is not null.
 void reverse_key_launch(const uint64_t *key, uint64_t n, uint32_t *xr, uint64_t words,
-                        uint64_t words_pad, cudaStream_t s);
+                        uint64_t words_pad, cudaStream_t s, uint64_t *zero = nullptr,
+                        uint64_t zero_words = 0);
 size_t direct_workspace(const DirectCfg &c);
 int direct_launch(const PlanCfg &cfg, void *ws, DevHeader *hdr, Prof *prof, const uint64_t *seed,
                   const uint64_t *key, uint64_t *out, cudaStream_t s);

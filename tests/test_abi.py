@@ -97,7 +97,7 @@ def test_plan_query_block_fp8(lib, n, m):
     assert chunk % 128 == 0 and 1024 <= chunk <= 1 << 15
     assert chunks * chunk >= n + 128 * 255 > (chunks - 1) * chunk
     assert d["tile_out"] == 32768 and tiles == -(-m // 32768)
-    assert d["kernels_per_call"] == 3
+    assert d["kernels_per_call"] == 2
     with pytest.raises(pkg.PAError) as e:
         pkg.pa_plan_query(n, m, binding.make_opts(path="block_fp8", block_b=256))
     assert e.value.status == binding.PA_ERR_INVALID
