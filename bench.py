@@ -609,7 +609,7 @@ def run_reference(args):
             per_step.append(t_step)
     val = tot_bits / tot_t / 1e9
     desc = (f"each step hashes whole blocks in full (next blocks of a seeded random order, "
-            f"about 2 s of oracle time per step); {args.steps} timed steps covered "
+            f"at least 2 s of oracle time per step); {args.steps} timed steps covered "
             f"{tot_bits / 1e6:.1f} Mbit in {tot_t:.1f} s on {th} threads")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
