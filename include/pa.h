@@ -52,15 +52,17 @@ typedef enum {
     PA_PATH_AUTO = 0,       /* planner / autotuner choice                                */
     PA_PATH_DIRECT = 1,     /* bit-packed AND + popcount parity (Sec. 2.1 definition)    */
     PA_PATH_NTT64 = 2,      /* exact NTT modulo 2^64-2^32+1 (Sec. 3, FFT route, exact)  */
-    PA_PATH_NTT31 = 3,      /* exact NTT modulo a prime below 2^31 (7*2^26+1 or 15*2^27+1,
-                               coefficients <= n < p)                                      */
+    PA_PATH_NTT31 = 3,      /* exact NTT modulo a prime below 2^31 (5*2^25+1, 7*2^26+1 or
+                               15*2^27+1: see pa_opts.ntt_prime; sums grouped so every
+                               coefficient count stays below p)                          */
     PA_PATH_FFT = 4,        /* FP32 FFT sub-blocks under a proven rounding bound; FP64
                                butterflies on the tile lengths where the FP32 bound fails */
     PA_PATH_BLOCK_INT8 = 5, /* block-Toeplitz Y = sum_d T_d X_d, INT8 tensor cores,
                                INT32 accumulation, then mod 2                            */
     PA_PATH_BLOCK_FP8 = 6   /* the same block-Toeplitz contraction on the tcgen05 tensor
                                cores: bits as e4m3 0 / 2^-6, FP32 accumulation in tensor
-                               memory (exact: at most 2^14 products per partial sum),
+                               memory (exact: at most 2^15 products per partial sum,
+                               a multiple of 2^-12 below 8),
                                then mod 2; tile edge b = 128                             */
 } pa_path;
 
@@ -73,7 +75,9 @@ typedef struct {
     uint64_t tile_in;          /* key sub-block length L (the paper's batch length); block
                                   FP8: contraction positions per CTA chunk, a multiple of
                                   128 up to 32768                                         */
-    uint64_t tile_out;         /* output sub-block length M (column split of Sec. 3)      */
+    uint64_t tile_out;         /* output sub-block length M (column split of Sec. 3). An
+                                  NTT geometry that would need more than 2^22 tile pairs
+                                  without transform-domain sums is PA_ERR_UNSUPPORTED     */
     uint32_t force_fp64;       /* FFT path: use FP64 butterflies even where FP32 is proven */
     uint32_t max_slots;        /* batches: at most this many transform spectra resident at
                                   once (reused round-robin, >= 4); 0 = automatic         */

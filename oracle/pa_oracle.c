@@ -180,7 +180,7 @@ int oracle_rows(uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t *ke
 /* Same rows, by the bit-by-bit evaluator (single thread; tiny sizes only). */
 int oracle_rows_bitloop(uint64_t n, uint64_t m, const uint64_t *seed, const uint64_t *key,
                         const uint64_t *rows, uint64_t count, uint8_t *bits) {
-    if (n == 0 || m == 0 || !seed || !key) return ORACLE_EINVAL;
+    if (n == 0 || m == 0 || !seed || !key || (count && (!rows || !bits))) return ORACLE_EINVAL;
     for (uint64_t t = 0; t < count; ++t) {
         if (rows[t] >= m) return ORACLE_EINVAL;
         bits[t] = (uint8_t)oracle_row_bitloop(n, m, seed, key, rows[t]);

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include "internal.h"
+#include "ntt_defs.cuh"
 
 namespace pa {
 
@@ -19,6 +20,25 @@ int cuda_fail(cudaError_t e) {
 // Largest sizes accepted at all (the seed index n+m-2 must fit comfortably).
 constexpr uint64_t kMaxBits = uint64_t(1) << 40;
 
+// Standard tile pairs (no transform-domain sums) a plan may lay out, and work items
+// their persistent launch may list (2^28 items: 2 GiB of work list on host and device).
+constexpr uint64_t kStdMaxPairs = uint64_t(1) << 22;
+constexpr uint64_t kStdMaxItems = uint64_t(1) << 28;
+
+// Work items of a standard NTT plan: one per one-CTA tile pair; above 2^kLogSmallMax
+// points, per pair two forward pass-1 sweeps (key tile and seed window) and one inverse
+// of g1 column groups each, and g2 row groups of pass 2 (the work list's layout).
+static double std_items(const TransformCfg &t) {
+    const double pairs = double(t.tiles_in) * double(t.tiles_out);
+    if (t.log2n <= static_cast<uint32_t>(kLogSmallMax)) return pairs;
+    int logR1 = 0, logR2 = 0, logC1 = 0, logC2 = 0;
+    split_r(static_cast<int>(t.log2n), &logR1, &logR2);
+    pass_columns(static_cast<int>(t.log2n), t.field == kFieldF64 ? 8 : 4, &logC1, &logC2);
+    const double g1 = double(uint64_t(1) << (t.log2n - logR1 - logC1));
+    const double g2 = double(uint64_t(1) << (logR1 - logC2));
+    return pairs * (3.0 * g1 + g2);
+}
+
 int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool layout) {
     if (!cfg || n == 0 || m == 0 || n > kMaxBits || m > kMaxBits) return PA_ERR_INVALID;
     *cfg = PlanCfg();
@@ -28,7 +48,7 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool la
     if (path < PA_PATH_AUTO || path > PA_PATH_BLOCK_FP8) return PA_ERR_INVALID;
     if (path == PA_PATH_AUTO) {
         // Host-only rule (pa_plan_ex uses the autotuner's measured costs instead): the
-        // direct kernel while m*n is small; beyond, the exact NTT over the 29-bit prime
+        // direct kernel while m*n is small; beyond, the exact NTT over the 28- or 29-bit prime
         // (its geometry keeps every count below the prime), else over the 64-bit prime.
         const double mn = double(n) * double(m);
         path = mn <= 4.0e9 ? PA_PATH_DIRECT : PA_PATH_NTT31;
@@ -49,6 +69,15 @@ int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool la
         case PA_PATH_NTT64:
         case PA_PATH_NTT31:
             rc = ntt_plan(n, m, path, o, &cfg->tr);
+            // Every standard tile pair is a tile record and several work items. A forced
+            // geometry of tiny tiles on a long key (1e8 bits in 4096-bit tiles: 6e7 pairs),
+            // or a key of 1e10 bits with transform-domain sums forbidden (2.3e6 pairs of
+            // 2^22 points, 3e9 work items), would take minutes and tens of gigabytes of host
+            // memory to lay out, so either is refused before any list is built.
+            if (rc == PA_OK && cfg->tr.fd == 0 &&
+                (double(cfg->tr.tiles_in) * double(cfg->tr.tiles_out) > double(kStdMaxPairs) ||
+                 std_items(cfg->tr) > double(kStdMaxItems)))
+                rc = PA_ERR_UNSUPPORTED;
             if (rc == PA_OK && (layout || (cfg->tr.fd == 1 && cfg->tr.seg_in)))
                 rc = ntt_layout(n, m, path, &cfg->tr);
             cfg->ws_bytes = cfg->tr.lay.bytes;

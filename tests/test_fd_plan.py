@@ -243,6 +243,30 @@ def test_planning_stays_fast_for_serving_sizes(lib):
     assert (time.perf_counter() - t0) / len(shapes) < 0.05
 
 
+@pytest.mark.parametrize("path", ["ntt31", "ntt64"])
+def test_oversized_standard_plans_refused_before_layout(lib, path):
+    # Without transform-domain sums a key of 1e10 bits needs about 2.3e6 tile pairs of 2^22
+    # points, each a tile record and 1280 (32-bit primes) or 2560 (64-bit prime) work items:
+    # billions of list entries. The planner refuses such a plan with PA_ERR_UNSUPPORTED at
+    # once instead of building the list (which took 40 s and 28 GB of host memory for the
+    # 29-bit prime, and threw std::bad_alloc through the C interface for the 64-bit one).
+    # Tiny forced tiles on a long key are refused the same way.
+    import time
+    cases = [(10_000_000_019, 1_000_000_000, dict(fd_mode=1)),
+             (10_000_000_019, 1_000_000_000, dict(outer_mode=1, seg_in=3, seg_out=2)),
+             (100_000_007, 10_000_000, dict(log2_transform=13, tile_in=4096, tile_out=4096,
+                                            fd_mode=1))]
+    for n, m, extra in cases:
+        t0 = time.perf_counter()
+        with pytest.raises(pkg.PAError) as e:
+            pkg.pa_plan_query(n, m, binding.make_opts(path=path, **extra))
+        assert e.value.status == binding.PA_ERR_UNSUPPORTED
+        assert time.perf_counter() - t0 < 2.0
+    # the largest standard plan still accepted: 1e9 bits with sums forbidden
+    d = pkg.pa_plan_query(1_000_000_007, 100_000_000, binding.make_opts(path=path, fd_mode=1))
+    assert d["fd"] == 0 and d["tiles_in"] * d["tiles_out"] > 1000
+
+
 def test_outer_convolutions_chosen_and_forced(lib):
     # forced on a small equal-tile geometry, refused when asked never; the model takes them
     # for long keys (many output and key tiles) and not for the finite-size block (3 x 24)
