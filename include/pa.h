@@ -151,11 +151,16 @@ typedef struct pa_plan_s *pa_plan_t;
 int pa_plan(uint64_t n, uint64_t m, pa_plan_t *out);
 
 /* Same with options (Sec. 3 Step 2 with the caller fixing some of the choices; opts may
- * be NULL). PA_ERR_UNSUPPORTED if a forced path cannot handle (n, m); PA_ERR_PRECISION if
- * a forced FFT tile has no proven bound. */
+ * be NULL). PA_ERR_UNSUPPORTED if a forced path cannot handle (n, m), including an NTT
+ * plan without transform-domain sums whose work list would exceed 2^28 items or 2^22 tile
+ * pairs (refused before anything is allocated); PA_ERR_PRECISION if a forced FFT tile has
+ * no proven bound. */
 int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out);
 
-/* Resolve a plan on the host only (no GPU, no allocation). */
+/* Resolve a plan on the host only: no GPU and no device memory are touched. An NTT plan
+ * is laid out as pa_plan_ex would (its work list is built in host memory and freed before
+ * the call returns; a key of 1e10 bits takes a few seconds). Same status codes as
+ * pa_plan_ex; out is written only on PA_OK. */
 int pa_plan_query(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_desc *out);
 
 /* Describe a created plan. */

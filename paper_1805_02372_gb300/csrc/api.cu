@@ -1,9 +1,10 @@
 // C ABI of the Toeplitz-hash library: planning, single-block hashing, status.
-// Every entry point returns a pa_status; no exception crosses the interface.
+// Every entry point returns a pa_status; no exception crosses the interface (guard.h).
 #include <algorithm>
 #include <new>
 #include <string.h>
 
+#include "guard.h"
 #include "internal.h"
 #include "ntt_defs.cuh"
 
@@ -196,12 +197,14 @@ int launch_plan(pa_plan_s *p, const uint64_t *seed, const uint64_t *key, uint64_
 extern "C" {
 
 int pa_plan_query(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_desc *out) {
-    if (!out) return PA_ERR_INVALID;
-    PlanCfg cfg;
-    int rc = plan_resolve(n, m, opts, &cfg);
-    if (rc != PA_OK) return rc;
-    fill_desc(cfg, out);
-    return PA_OK;
+    return guarded([&] {
+        if (!out) return PA_ERR_INVALID;
+        PlanCfg cfg;
+        int rc = plan_resolve(n, m, opts, &cfg);
+        if (rc != PA_OK) return rc;
+        fill_desc(cfg, out);
+        return PA_OK;
+    });
 }
 
 int pa_seed_from_eq1(uint64_t n, const uint64_t *t_bits, uint64_t *seed_bits) {
@@ -225,7 +228,7 @@ int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
     pa_opts tuned;
     if ((!opts || opts->path == PA_PATH_AUTO) && n > 0 && m > 0) {
         // AUTO: the autotuner's measured-cost choice (calibrates once per device)
-        int trc = tuned_opts(n, m, &tuned);
+        const int trc = guarded([&] { return tuned_opts(n, m, &tuned); });
         if (trc != PA_OK) {
             delete p;
             return trc;
@@ -233,7 +236,7 @@ int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
         if (opts) tuned.device = opts->device;
         opts = &tuned;
     }
-    int rc = plan_resolve(n, m, opts, &p->cfg);
+    int rc = guarded([&] { return plan_resolve(n, m, opts, &p->cfg); });
     if (rc != PA_OK) {
         delete p;
         return rc;
@@ -252,7 +255,7 @@ int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
     e = cudaMalloc(&p->mem, kHeaderBytes + p->cfg.ws_bytes);
     if (e == cudaSuccess) e = cudaMemset(p->mem, 0, kHeaderBytes);
     if (e == cudaSuccess && (p->cfg.path == PA_PATH_NTT31 || p->cfg.path == PA_PATH_NTT64)) {
-        rc = ntt_init(p->cfg, static_cast<char *>(p->mem) + kHeaderBytes);
+        rc = guarded([&] { return ntt_init(p->cfg, static_cast<char *>(p->mem) + kHeaderBytes); });
         if (rc != PA_OK) {
             if (p->device != prev) cudaSetDevice(prev);
             cudaFree(p->mem);
@@ -289,12 +292,14 @@ void pa_plan_destroy(pa_plan_t plan) {
 
 int pa_hash(pa_plan_t plan, const uint64_t *seed_bits, const uint64_t *key_bits,
             uint64_t *out_bits, void *stream) {
-    if (!plan || !seed_bits || !key_bits || !out_bits) return PA_ERR_INVALID;
-    if (!aligned16(seed_bits) || !aligned16(key_bits) || !aligned16(out_bits))
-        return PA_ERR_ALIGN;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    plan->last_stream = s;
-    return launch_plan(plan, seed_bits, key_bits, out_bits, s);
+    return guarded([&] {
+        if (!plan || !seed_bits || !key_bits || !out_bits) return PA_ERR_INVALID;
+        if (!aligned16(seed_bits) || !aligned16(key_bits) || !aligned16(out_bits))
+            return PA_ERR_ALIGN;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        plan->last_stream = s;
+        return launch_plan(plan, seed_bits, key_bits, out_bits, s);
+    });
 }
 
 int pa_hash_host(pa_plan_t plan, const uint64_t *seed_host, const uint64_t *key_host,

@@ -14,11 +14,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "common.cuh"
+#include "guard.h"
 #include "tiles.cuh"
 
 namespace pa {
@@ -474,23 +476,23 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
                     cudaStream_t alloc_stream, bool eager, pa_batch_s **out) {
     if (!out || !blocks || count == 0 || count > (size_t(1) << 24)) return PA_ERR_INVALID;
     *out = nullptr;
-    pa_batch_s *b = new (std::nothrow) pa_batch_s();
+    // the batch is freed (device memory and all) on every early return
+    const auto release = [](pa_batch_s *x) {
+        batch_free(x);
+        delete x;
+    };
+    std::unique_ptr<pa_batch_s, decltype(release)> own(new (std::nothrow) pa_batch_s(), release);
+    pa_batch_s *b = own.get();
     if (!b) return PA_ERR_NOMEM;
     b->eager = eager;
     b->alloc_stream = alloc_stream;
     cudaError_t e = cudaGetDevice(&b->device);
-    if (e != cudaSuccess) {
-        delete b;
-        return cuda_fail(e);
-    }
+    if (e != cudaSuccess) return cuda_fail(e);
     const bool forced = opts && opts->path != PA_PATH_AUTO;
     Tuner t;
     if (!forced) {
-        int rc = get_tuner(&t);
-        if (rc != PA_OK) {
-            delete b;
-            return rc;
-        }
+        const int rc = get_tuner(&t);
+        if (rc != PA_OK) return rc;
     }
     std::vector<BatchBlock> nb[kNumFields];
     size_t off = kHeaderBytes;
@@ -510,11 +512,8 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
             // blocks
             best_path(n, m, t, true, &o, opts ? opts->fd_mode : 0, opts ? opts->fd_group : 0);
         }
-        int rc = plan_resolve(n, m, &o, &b->cfg[i], false);
-        if (rc != PA_OK) {
-            delete b;
-            return rc;
-        }
+        const int rc = plan_resolve(n, m, &o, &b->cfg[i], false);
+        if (rc != PA_OK) return rc;
         const PlanCfg &c = b->cfg[i];
         b->per_path[c.path] += 1;
         if (in_persistent(c)) {
@@ -544,11 +543,8 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
     }
     for (int f = 0; f < kNumFields; ++f) {
         if (nb[f].empty()) continue;
-        int rc = ntt_batch_build(f, nb[f], opts ? opts->max_slots : 0, &b->ntt[f]);
-        if (rc != PA_OK) {
-            delete b;
-            return rc;
-        }
+        const int rc = ntt_batch_build(f, nb[f], opts ? opts->max_slots : 0, &b->ntt[f]);
+        if (rc != PA_OK) return rc;
         b->work_items += b->ntt[f].nitems;
         b->off_idx[f] = off;
         off = round_up(off + b->in_ntt[f].size() * sizeof(uint32_t), 256);
@@ -564,19 +560,11 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         if (!b->in_ntt[f].empty())
             e = cudaMemcpyAsync(static_cast<char *>(b->mem) + b->off_idx[f], b->in_ntt[f].data(),
                                 b->in_ntt[f].size() * sizeof(uint32_t), cudaMemcpyHostToDevice, as);
-    if (e != cudaSuccess) {
-        batch_free(b);
-        delete b;
-        return cuda_fail(e);
-    }
+    if (e != cudaSuccess) return cuda_fail(e);
     for (int f = 0; f < kNumFields; ++f) {
         if (b->in_ntt[f].empty()) continue;
-        int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f], as);
-        if (rc != PA_OK) {
-            batch_free(b);
-            delete b;
-            return rc;
-        }
+        const int rc = ntt_batch_upload(b->ntt[f], static_cast<char *>(b->mem) + b->off_ntt[f], as);
+        if (rc != PA_OK) return rc;
     }
     // segmented NTT blocks: their work lists go into their own workspace now (synchronous
     // copies, after the stream-ordered allocation has happened)
@@ -584,26 +572,18 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
         const PlanCfg &c = b->cfg[i];
         if ((c.path != PA_PATH_NTT31 && c.path != PA_PATH_NTT64) || in_persistent(c)) continue;
         if (as) PA_CUDA_TRY(cudaStreamSynchronize(as));
-        int rc = ntt_init(c, static_cast<char *>(b->mem) + b->ws_off[i]);
-        if (rc != PA_OK) {
-            batch_free(b);
-            delete b;
-            return rc;
-        }
+        const int rc = ntt_init(c, static_cast<char *>(b->mem) + b->ws_off[i]);
+        if (rc != PA_OK) return rc;
     }
     if (!as) PA_CUDA_TRY(cudaStreamSynchronize(nullptr));
     // root tables of the FFT path are created now, not inside a graph capture
     for (size_t i = 0; i < count; ++i)
         if (b->cfg[i].path == PA_PATH_FFT) {
-            int rc = fft_prepare(b->cfg[i].tr.fp64);
-            if (rc != PA_OK) {
-                batch_free(b);
-                delete b;
-                return rc;
-            }
+            const int rc = fft_prepare(b->cfg[i].tr.fp64);
+            if (rc != PA_OK) return rc;
         }
     b->hblks.resize(count);
-    *out = b;
+    *out = own.release();
     return PA_OK;
 }
 
@@ -678,85 +658,87 @@ size_t batch_bytes(const pa_batch_s *b) { return b ? b->bytes : 0; }
 extern "C" {
 
 int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_batch_t *out) {
-    return batch_plan_impl(blocks, count, opts, nullptr, false, out);
+    return guarded([&] { return batch_plan_impl(blocks, count, opts, nullptr, false, out); });
 }
 
 int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *stream, pa_report *rep) {
-    if (!b || !blocks || count != b->cfg.size()) return PA_ERR_INVALID;
-    bool changed_other = false, changed_any = !b->blks_valid;
-    for (size_t i = 0; i < count; ++i) {
-        const pa_block &x = blocks[i];
-        if (x.n != b->n[i] || x.m != b->m[i] || !x.seed_bits || !x.key_bits || !x.out_bits)
-            return PA_ERR_INVALID;
-        if (!aligned16(x.seed_bits) || !aligned16(x.key_bits) || !aligned16(x.out_bits))
-            return PA_ERR_ALIGN;
-        BlockPtrs p{reinterpret_cast<const uint32_t *>(x.key_bits),
-                    reinterpret_cast<const uint32_t *>(x.seed_bits),
-                    reinterpret_cast<uint32_t *>(x.out_bits), x.n, x.m};
-        BlockPtrs &h = b->hblks[i];
-        if (h.key32 != p.key32 || h.seed32 != p.seed32 || h.out32 != p.out32) {
-            changed_any = true;
-            if (!in_persistent(b->cfg[i])) changed_other = true;
-            h = p;
+    return guarded([&] {
+        if (!b || !blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+        bool changed_other = false, changed_any = !b->blks_valid;
+        for (size_t i = 0; i < count; ++i) {
+            const pa_block &x = blocks[i];
+            if (x.n != b->n[i] || x.m != b->m[i] || !x.seed_bits || !x.key_bits || !x.out_bits)
+                return PA_ERR_INVALID;
+            if (!aligned16(x.seed_bits) || !aligned16(x.key_bits) || !aligned16(x.out_bits))
+                return PA_ERR_ALIGN;
+            BlockPtrs p{reinterpret_cast<const uint32_t *>(x.key_bits),
+                        reinterpret_cast<const uint32_t *>(x.seed_bits),
+                        reinterpret_cast<uint32_t *>(x.out_bits), x.n, x.m};
+            BlockPtrs &h = b->hblks[i];
+            if (h.key32 != p.key32 || h.seed32 != p.seed32 || h.out32 != p.out32) {
+                changed_any = true;
+                if (!in_persistent(b->cfg[i])) changed_other = true;
+                h = p;
+            }
         }
-    }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (changed_any) {
-        PA_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(b->mem) + b->off_blks, b->hblks.data(),
-                                    count * sizeof(BlockPtrs), cudaMemcpyHostToDevice, s));
-        b->blks_valid = true;
-    }
-    uint32_t replayed = 0;
-    if (b->prof.on || b->eager) {
-        int rc = enqueue_all(b, s);
-        if (rc != PA_OK) return rc;
-    } else {
-        if (!b->graph_ok || changed_other) {
-            if (b->exec) {
-                cudaGraphExecDestroy(b->exec);
-                b->exec = nullptr;
-            }
-            b->graph_ok = false;
-            // capture on a private stream (the caller's may be the legacy default
-            // stream, which cannot be captured); the graph is launched on the caller's
-            if (!b->cap_stream)
-                PA_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
-            cudaGraph_t g = nullptr;
-            PA_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-            int rc = enqueue_all(b, b->cap_stream);
-            cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
-            if (rc != PA_OK) {
-                if (g) cudaGraphDestroy(g);
-                return rc;
-            }
-            if (e != cudaSuccess) return cuda_fail(e);
-            e = cudaGraphInstantiate(&b->exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return cuda_fail(e);
-            b->graph_ok = true;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (changed_any) {
+            PA_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(b->mem) + b->off_blks, b->hblks.data(),
+                                        count * sizeof(BlockPtrs), cudaMemcpyHostToDevice, s));
+            b->blks_valid = true;
+        }
+        uint32_t replayed = 0;
+        if (b->prof.on || b->eager) {
+            int rc = enqueue_all(b, s);
+            if (rc != PA_OK) return rc;
         } else {
-            replayed = 1;
+            if (!b->graph_ok || changed_other) {
+                if (b->exec) {
+                    cudaGraphExecDestroy(b->exec);
+                    b->exec = nullptr;
+                }
+                b->graph_ok = false;
+                // capture on a private stream (the caller's may be the legacy default
+                // stream, which cannot be captured); the graph is launched on the caller's
+                if (!b->cap_stream)
+                    PA_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+                cudaGraph_t g = nullptr;
+                PA_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+                int rc = enqueue_all(b, b->cap_stream);
+                cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+                if (rc != PA_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc;
+                }
+                if (e != cudaSuccess) return cuda_fail(e);
+                e = cudaGraphInstantiate(&b->exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(e);
+                b->graph_ok = true;
+            } else {
+                replayed = 1;
+            }
+            PA_CUDA_TRY(cudaGraphLaunch(b->exec, s));
         }
-        PA_CUDA_TRY(cudaGraphLaunch(b->exec, s));
-    }
-    b->last_stream = s;
-    if (rep) {
-        PA_CUDA_TRY(cudaStreamSynchronize(s));
-        DevHeader h;
-        PA_CUDA_TRY(cudaMemcpy(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost));
-        memset(rep, 0, sizeof(*rep));
-        memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
-        rep->bound = b->bound;
-        for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
-        rep->work_items = b->work_items;
-        rep->graph_replayed = replayed;
-        if (h.status != 0) {
-            int zero = 0;
-            cudaMemcpy(b->mem, &zero, sizeof(zero), cudaMemcpyHostToDevice);
-            return h.status;
+        b->last_stream = s;
+        if (rep) {
+            PA_CUDA_TRY(cudaStreamSynchronize(s));
+            DevHeader h;
+            PA_CUDA_TRY(cudaMemcpy(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost));
+            memset(rep, 0, sizeof(*rep));
+            memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
+            rep->bound = b->bound;
+            for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
+            rep->work_items = b->work_items;
+            rep->graph_replayed = replayed;
+            if (h.status != 0) {
+                int zero = 0;
+                cudaMemcpy(b->mem, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+                return h.status;
+            }
         }
-    }
-    return PA_OK;
+        return PA_OK;
+    });
 }
 
 namespace {
@@ -765,23 +747,25 @@ namespace {
 // descriptors of the staged blocks; PA_ERR_INVALID if a host block does not match the plan.
 int host_stage(pa_batch_s *b, const pa_block *host_blocks, size_t count, std::vector<pa_block> *dev) {
     if (!b->stage) {
+        // offsets first (the batch is untouched if a vector cannot grow), then the memory
+        std::vector<size_t> seed_off(count), key_off(count), out_off(count);
         size_t off = 0;
         for (size_t i = 0; i < count; ++i) {
-            b->st_seed.push_back(off);
+            seed_off[i] = off;
             off = round_up(off + ceil_div(b->n[i] + b->m[i] - 1, 64) * 8, 256);
-            b->st_key.push_back(off);
+            key_off[i] = off;
             off = round_up(off + ceil_div(b->n[i], 64) * 8, 256);
-            b->st_out.push_back(off);
+            out_off[i] = off;
             off = round_up(off + ceil_div(b->m[i], 64) * 8, 256);
         }
         cudaError_t e = cudaMalloc(&b->stage, off);
         if (e != cudaSuccess) {
             b->stage = nullptr;
-            b->st_seed.clear();
-            b->st_key.clear();
-            b->st_out.clear();
             return cuda_fail(e);
         }
+        b->st_seed = std::move(seed_off);
+        b->st_key = std::move(key_off);
+        b->st_out = std::move(out_off);
         b->stage_bytes = off;
     }
     char *st = static_cast<char *>(b->stage);
@@ -801,108 +785,112 @@ int host_stage(pa_batch_s *b, const pa_block *host_blocks, size_t count, std::ve
 
 int pa_batch_run_host(pa_batch_t b, const pa_block *host_blocks, size_t count, void *stream,
                       pa_report *rep) {
-    if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
-    std::vector<pa_block> dev;
-    const int src = host_stage(b, host_blocks, count, &dev);
-    if (src != PA_OK) return src;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    char *st = static_cast<char *>(b->stage);
-    // When every host buffer is page-locked and mapped for this device, one gather kernel
-    // reads all keys and seeds and one scatter kernel writes all outputs (instead of three
-    // copies per block); otherwise one cudaMemcpyAsync per buffer.
-    // Copies are cut into pieces of at most kCopyPiece words so that the large keys and
-    // seeds spread over many CTAs instead of setting the kernel's duration on one each.
-    std::vector<CopySeg> &sg = b->hsegs;
-    sg.clear();
-    const auto add = [&sg](const uint64_t *src, uint64_t *dst, uint64_t words) {
-        for (uint64_t o = 0; o < words; o += kCopyPiece)
-            sg.push_back({src + o, dst + o, std::min<uint64_t>(kCopyPiece, words - o)});
-    };
-    bool mapped = true;
-    std::vector<uint64_t *> outs_dev(count, nullptr);
-    for (size_t i = 0; i < count && mapped; ++i) {
-        const pa_block &h = host_blocks[i];
-        void *ds = mapped_host(h.seed_bits), *dk = mapped_host(h.key_bits);
-        outs_dev[i] = static_cast<uint64_t *>(mapped_host(h.out_bits));
-        mapped = ds && dk && outs_dev[i];
-        if (!mapped) break;
-        add(static_cast<const uint64_t *>(ds), reinterpret_cast<uint64_t *>(st + b->st_seed[i]),
-            ceil_div(h.n + h.m - 1, 64));
-        add(static_cast<const uint64_t *>(dk), reinterpret_cast<uint64_t *>(st + b->st_key[i]),
-            ceil_div(h.n, 64));
-    }
-    size_t nin = 0;
-    if (mapped) {
-        nin = sg.size();
-        for (size_t i = 0; i < count; ++i)
-            add(reinterpret_cast<const uint64_t *>(st + b->st_out[i]), outs_dev[i], ceil_div(b->m[i], 64));
-        if (!b->segs || b->segs_cap < sg.size()) {
-            if (b->segs) cudaFree(b->segs);
-            b->segs = nullptr;
-            cudaError_t e = cudaMalloc(&b->segs, sg.size() * sizeof(CopySeg));
-            if (e != cudaSuccess) return cuda_fail(e);
-            b->segs_cap = sg.size();
-        }
-        PA_CUDA_TRY(cudaMemcpyAsync(b->segs, sg.data(), sg.size() * sizeof(CopySeg),
-                                    cudaMemcpyHostToDevice, s));
-        int sms = kNumSMsGB300;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-        copy_segments<<<4 * sms, 256, 0, s>>>(b->segs, static_cast<uint32_t>(nin));
-        PA_CUDA_TRY(cudaGetLastError());
-    } else {
-        for (size_t i = 0; i < count; ++i) {
+    return guarded([&] {
+        if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+        std::vector<pa_block> dev;
+        const int src = host_stage(b, host_blocks, count, &dev);
+        if (src != PA_OK) return src;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        char *st = static_cast<char *>(b->stage);
+        // When every host buffer is page-locked and mapped for this device, one gather kernel
+        // reads all keys and seeds and one scatter kernel writes all outputs (instead of three
+        // copies per block); otherwise one cudaMemcpyAsync per buffer.
+        // Copies are cut into pieces of at most kCopyPiece words so that the large keys and
+        // seeds spread over many CTAs instead of setting the kernel's duration on one each.
+        std::vector<CopySeg> &sg = b->hsegs;
+        sg.clear();
+        const auto add = [&sg](const uint64_t *src, uint64_t *dst, uint64_t words) {
+            for (uint64_t o = 0; o < words; o += kCopyPiece)
+                sg.push_back({src + o, dst + o, std::min<uint64_t>(kCopyPiece, words - o)});
+        };
+        bool mapped = true;
+        std::vector<uint64_t *> outs_dev(count, nullptr);
+        for (size_t i = 0; i < count && mapped; ++i) {
             const pa_block &h = host_blocks[i];
-            PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits,
-                                        ceil_div(h.n + h.m - 1, 64) * 8, cudaMemcpyHostToDevice, s));
-            PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
-                                        cudaMemcpyHostToDevice, s));
+            void *ds = mapped_host(h.seed_bits), *dk = mapped_host(h.key_bits);
+            outs_dev[i] = static_cast<uint64_t *>(mapped_host(h.out_bits));
+            mapped = ds && dk && outs_dev[i];
+            if (!mapped) break;
+            add(static_cast<const uint64_t *>(ds), reinterpret_cast<uint64_t *>(st + b->st_seed[i]),
+                ceil_div(h.n + h.m - 1, 64));
+            add(static_cast<const uint64_t *>(dk), reinterpret_cast<uint64_t *>(st + b->st_key[i]),
+                ceil_div(h.n, 64));
         }
-    }
-    int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
-    if (rc != PA_OK) return rc;
-    if (mapped) {
-        copy_segments<<<4 * kNumSMsGB300, 256, 0, s>>>(b->segs + nin, static_cast<uint32_t>(sg.size() - nin));
-        PA_CUDA_TRY(cudaGetLastError());
-    } else {
-        for (size_t i = 0; i < count; ++i)
-            PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i],
-                                        ceil_div(b->m[i], 64) * 8, cudaMemcpyDeviceToHost, s));
-    }
-    PA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (rep) {
-        DevHeader h;
-        PA_CUDA_TRY(cudaMemcpy(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost));
-        memset(rep, 0, sizeof(*rep));
-        memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
-        rep->bound = b->bound;
-        for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
-        rep->work_items = b->work_items;
-        if (h.status != 0) return h.status;
-    }
-    return PA_OK;
+        size_t nin = 0;
+        if (mapped) {
+            nin = sg.size();
+            for (size_t i = 0; i < count; ++i)
+                add(reinterpret_cast<const uint64_t *>(st + b->st_out[i]), outs_dev[i], ceil_div(b->m[i], 64));
+            if (!b->segs || b->segs_cap < sg.size()) {
+                if (b->segs) cudaFree(b->segs);
+                b->segs = nullptr;
+                cudaError_t e = cudaMalloc(&b->segs, sg.size() * sizeof(CopySeg));
+                if (e != cudaSuccess) return cuda_fail(e);
+                b->segs_cap = sg.size();
+            }
+            PA_CUDA_TRY(cudaMemcpyAsync(b->segs, sg.data(), sg.size() * sizeof(CopySeg),
+                                        cudaMemcpyHostToDevice, s));
+            int sms = kNumSMsGB300;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+            copy_segments<<<4 * sms, 256, 0, s>>>(b->segs, static_cast<uint32_t>(nin));
+            PA_CUDA_TRY(cudaGetLastError());
+        } else {
+            for (size_t i = 0; i < count; ++i) {
+                const pa_block &h = host_blocks[i];
+                PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits,
+                                            ceil_div(h.n + h.m - 1, 64) * 8, cudaMemcpyHostToDevice, s));
+                PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
+                                            cudaMemcpyHostToDevice, s));
+            }
+        }
+        int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
+        if (rc != PA_OK) return rc;
+        if (mapped) {
+            copy_segments<<<4 * kNumSMsGB300, 256, 0, s>>>(b->segs + nin, static_cast<uint32_t>(sg.size() - nin));
+            PA_CUDA_TRY(cudaGetLastError());
+        } else {
+            for (size_t i = 0; i < count; ++i)
+                PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i],
+                                            ceil_div(b->m[i], 64) * 8, cudaMemcpyDeviceToHost, s));
+        }
+        PA_CUDA_TRY(cudaStreamSynchronize(s));
+        if (rep) {
+            DevHeader h;
+            PA_CUDA_TRY(cudaMemcpy(&h, b->mem, sizeof(h), cudaMemcpyDeviceToHost));
+            memset(rep, 0, sizeof(*rep));
+            memcpy(&rep->max_residual, &h.residual_bits, sizeof(double));
+            rep->bound = b->bound;
+            for (int i = 0; i < 8; ++i) rep->blocks_per_path[i] = b->per_path[i];
+            rep->work_items = b->work_items;
+            if (h.status != 0) return h.status;
+        }
+        return PA_OK;
+    });
 }
 
 int pa_batch_run_host_async(pa_batch_t b, const pa_block *host_blocks, size_t count, void *stream) {
-    if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
-    std::vector<pa_block> dev;
-    const int src = host_stage(b, host_blocks, count, &dev);
-    if (src != PA_OK) return src;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    char *st = static_cast<char *>(b->stage);
-    // copies by the copy engines (no SM time: they overlap kernels of other streams)
-    for (size_t i = 0; i < count; ++i) {
-        const pa_block &h = host_blocks[i];
-        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits, ceil_div(h.n + h.m - 1, 64) * 8,
-                                    cudaMemcpyHostToDevice, s));
-        PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
-                                    cudaMemcpyHostToDevice, s));
-    }
-    const int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
-    if (rc != PA_OK) return rc;
-    for (size_t i = 0; i < count; ++i)
-        PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i], ceil_div(b->m[i], 64) * 8,
-                                    cudaMemcpyDeviceToHost, s));
-    return PA_OK;
+    return guarded([&] {
+        if (!b || !host_blocks || count != b->cfg.size()) return PA_ERR_INVALID;
+        std::vector<pa_block> dev;
+        const int src = host_stage(b, host_blocks, count, &dev);
+        if (src != PA_OK) return src;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        char *st = static_cast<char *>(b->stage);
+        // copies by the copy engines (no SM time: they overlap kernels of other streams)
+        for (size_t i = 0; i < count; ++i) {
+            const pa_block &h = host_blocks[i];
+            PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_seed[i], h.seed_bits, ceil_div(h.n + h.m - 1, 64) * 8,
+                                        cudaMemcpyHostToDevice, s));
+            PA_CUDA_TRY(cudaMemcpyAsync(st + b->st_key[i], h.key_bits, ceil_div(h.n, 64) * 8,
+                                        cudaMemcpyHostToDevice, s));
+        }
+        const int rc = pa_batch_run(b, dev.data(), count, stream, nullptr);
+        if (rc != PA_OK) return rc;
+        for (size_t i = 0; i < count; ++i)
+            PA_CUDA_TRY(cudaMemcpyAsync(host_blocks[i].out_bits, st + b->st_out[i], ceil_div(b->m[i], 64) * 8,
+                                        cudaMemcpyDeviceToHost, s));
+        return PA_OK;
+    });
 }
 
 int pa_batch_get_report(pa_batch_t b, void *stream, pa_report *rep) {
@@ -939,25 +927,27 @@ int pa_batch_describe(pa_batch_t b, pa_plan_desc *out, size_t count) {
 
 // One-shot: the batch plan is cached for the last shape list (per thread).
 int pa_hash_batched(const pa_block *blocks, size_t count, void *stream, pa_report *rep) {
-    static thread_local pa_batch_s *cached = nullptr;
-    static thread_local std::vector<uint64_t> shape;
-    if (!blocks || count == 0) return PA_ERR_INVALID;
-    std::vector<uint64_t> sh;
-    sh.reserve(2 * count);
-    for (size_t i = 0; i < count; ++i) {
-        sh.push_back(blocks[i].n);
-        sh.push_back(blocks[i].m);
-    }
-    int dev = 0;
-    PA_CUDA_TRY(cudaGetDevice(&dev));
-    if (!cached || sh != shape || cached->device != dev) {
-        if (cached) pa_batch_destroy(cached);
-        cached = nullptr;
-        int rc = pa_batch_plan(blocks, count, nullptr, &cached);
-        if (rc != PA_OK) return rc;
-        shape = sh;
-    }
-    return pa_batch_run(cached, blocks, count, stream, rep);
+    return guarded([&] {
+        static thread_local pa_batch_s *cached = nullptr;
+        static thread_local std::vector<uint64_t> shape;
+        if (!blocks || count == 0) return PA_ERR_INVALID;
+        std::vector<uint64_t> sh;
+        sh.reserve(2 * count);
+        for (size_t i = 0; i < count; ++i) {
+            sh.push_back(blocks[i].n);
+            sh.push_back(blocks[i].m);
+        }
+        int dev = 0;
+        PA_CUDA_TRY(cudaGetDevice(&dev));
+        if (!cached || sh != shape || cached->device != dev) {
+            if (cached) pa_batch_destroy(cached);
+            cached = nullptr;
+            int rc = pa_batch_plan(blocks, count, nullptr, &cached);
+            if (rc != PA_OK) return rc;
+            shape = sh;
+        }
+        return pa_batch_run(cached, blocks, count, stream, rep);
+    });
 }
 
 }  // extern "C"

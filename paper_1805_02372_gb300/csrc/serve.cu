@@ -10,12 +10,14 @@
 // per wave; poll returns finished requests with their tags.
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <mutex>
 #include <new>
 #include <vector>
 
+#include "guard.h"
 #include "internal.h"
 
 namespace {
@@ -66,22 +68,23 @@ int launch_wave(pa_server_s *s, size_t i) {
 }
 
 int launch_wave_impl(pa_server_s *s, size_t i) {
+    // The wave takes the requests at the head of the queue; they leave the queue only once
+    // the wave is launched, so a failed plan or a held-back wave leaves them waiting in order.
+    const size_t cap = s->opts.max_blocks_per_wave ? s->opts.max_blocks_per_wave : 64;
+    const size_t k = std::min(s->queue.size(), cap);
+    if (k == 0) return PA_OK;
     std::vector<pa_block> blocks;
     std::vector<uint64_t> tags;
-    const size_t cap = s->opts.max_blocks_per_wave ? s->opts.max_blocks_per_wave : 64;
-    while (!s->queue.empty() && blocks.size() < cap) {
-        blocks.push_back(s->queue.front().first);
-        tags.push_back(s->queue.front().second);
-        s->queue.pop_front();
+    blocks.reserve(k);
+    tags.reserve(k);
+    for (size_t j = 0; j < k; ++j) {
+        blocks.push_back(s->queue[j].first);
+        tags.push_back(s->queue[j].second);
     }
-    if (blocks.empty()) return PA_OK;
     Wave w;
     pa_batch_s *b = nullptr;
     int rc = batch_plan_impl(blocks.data(), blocks.size(), nullptr, s->streams[i], true, &b);
-    if (rc != PA_OK) {
-        for (size_t k = blocks.size(); k-- > 0;) s->queue.push_front({blocks[k], tags[k]});
-        return rc;
-    }
+    if (rc != PA_OK) return rc;
     w.batch = b;
     w.bytes = batch_bytes(b);
     // memory admission: a wave that does not fit next to the waves in flight waits for
@@ -89,7 +92,6 @@ int launch_wave_impl(pa_server_s *s, size_t i) {
     if (s->opts.memory_budget_bytes && s->bytes_in_flight > 0 &&
         s->bytes_in_flight + w.bytes > s->opts.memory_budget_bytes) {
         batch_destroy_impl(b);
-        for (size_t k = blocks.size(); k-- > 0;) s->queue.push_front({blocks[k], tags[k]});
         ++s->held_back;
         return PA_OK;
     }
@@ -103,10 +105,13 @@ int launch_wave_impl(pa_server_s *s, size_t i) {
         e = cudaEventRecord(w.done, s->streams[i]);
         if (e != cudaSuccess) rc = cuda_fail(e);
     }
+    // launched (or failed on launch): the requests leave the queue and complete with the
+    // wave's status; nothing below allocates
+    for (size_t j = 0; j < k; ++j) s->queue.pop_front();
     w.status = rc;
-    w.tags = tags;
+    w.tags = std::move(tags);
     s->bytes_in_flight += w.bytes;
-    s->slots[i] = w;
+    s->slots[i] = std::move(w);
     ++s->waves_launched;
     return PA_OK;
 }
@@ -124,6 +129,16 @@ int pa_server_create(const pa_server_opts *opts, pa_server_t *out) {
     if (opts) s->opts = *opts;
     if (s->opts.slots == 0) s->opts.slots = 2;
     if (s->opts.slots > 64) s->opts.slots = 64;
+    // the containers take their final sizes before any CUDA object exists
+    const int grc = guarded([&] {
+        s->streams.reserve(s->opts.slots);
+        s->slots.resize(s->opts.slots);
+        return PA_OK;
+    });
+    if (grc != PA_OK) {
+        delete s;
+        return grc;
+    }
     cudaError_t e = cudaGetDevice(&s->device);
     for (uint32_t i = 0; e == cudaSuccess && i < s->opts.slots; ++i) {
         cudaStream_t st;
@@ -135,7 +150,6 @@ int pa_server_create(const pa_server_opts *opts, pa_server_t *out) {
         delete s;
         return cuda_fail(e);
     }
-    s->slots.resize(s->opts.slots);
     // keep freed wave memory in the device's stream-ordered pool for the next waves
     // (a property of this process's pool only)
     cudaMemPool_t pool;
@@ -145,7 +159,7 @@ int pa_server_create(const pa_server_opts *opts, pa_server_t *out) {
     }
     // calibrate the autotuner now, not while the first wave waits
     pa_opts warm;
-    int trc = tuned_opts(1 << 20, 1 << 16, &warm);
+    const int trc = guarded([&] { return tuned_opts(1 << 20, 1 << 16, &warm); });
     if (trc != PA_OK) {
         for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
         delete s;
@@ -156,46 +170,50 @@ int pa_server_create(const pa_server_opts *opts, pa_server_t *out) {
 }
 
 int pa_server_submit(pa_server_t s, const pa_block *req, uint64_t tag) {
-    if (!s || !req || req->n == 0 || req->m == 0 || !req->seed_bits || !req->key_bits ||
-        !req->out_bits)
-        return PA_ERR_INVALID;
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->queue.push_back({*req, tag});
-    return PA_OK;
+    return guarded([&] {
+        if (!s || !req || req->n == 0 || req->m == 0 || !req->seed_bits || !req->key_bits ||
+            !req->out_bits)
+            return PA_ERR_INVALID;
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->queue.push_back({*req, tag});
+        return PA_OK;
+    });
 }
 
 int pa_server_poll(pa_server_t s, pa_completion *done, size_t max, size_t *count) {
-    if (!s || (!done && max) || !count) return PA_ERR_INVALID;
-    std::lock_guard<std::mutex> lk(s->mu);
-    *count = 0;
-    // retire finished waves
-    for (size_t i = 0; i < s->slots.size(); ++i) {
-        Wave &w = s->slots[i];
-        if (!slot_busy(w)) continue;
-        if (w.tags.size() > max - *count) continue;  // no room to report this wave yet
-        const cudaError_t q = cudaEventQuery(w.done);
-        if (q == cudaErrorNotReady) continue;
-        int st = w.status;
-        if (q != cudaSuccess) st = cuda_fail(q);
-        for (uint64_t t : w.tags) {
-            done[*count].tag = t;
-            done[*count].status = st;
-            ++*count;
+    return guarded([&] {
+        if (!s || (!done && max) || !count) return PA_ERR_INVALID;
+        std::lock_guard<std::mutex> lk(s->mu);
+        *count = 0;
+        // retire finished waves
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+            Wave &w = s->slots[i];
+            if (!slot_busy(w)) continue;
+            if (w.tags.size() > max - *count) continue;  // no room to report this wave yet
+            const cudaError_t q = cudaEventQuery(w.done);
+            if (q == cudaErrorNotReady) continue;
+            int st = w.status;
+            if (q != cudaSuccess) st = cuda_fail(q);
+            for (uint64_t t : w.tags) {
+                done[*count].tag = t;
+                done[*count].status = st;
+                ++*count;
+            }
+            s->requests_done += w.tags.size();
+            cudaEventDestroy(w.done);
+            batch_destroy_impl(w.batch);
+            s->bytes_in_flight -= w.bytes;
+            w = Wave();
         }
-        s->requests_done += w.tags.size();
-        cudaEventDestroy(w.done);
-        batch_destroy_impl(w.batch);
-        s->bytes_in_flight -= w.bytes;
-        w = Wave();
-    }
-    // admit: every free slot takes the requests waiting now
-    for (size_t i = 0; i < s->slots.size() && !s->queue.empty(); ++i) {
-        if (slot_busy(s->slots[i])) continue;
-        int rc = launch_wave(s, i);
-        if (rc != PA_OK) return rc;
-        if (!slot_busy(s->slots[i])) break;  // held back by the memory budget
-    }
-    return PA_OK;
+        // admit: every free slot takes the requests waiting now
+        for (size_t i = 0; i < s->slots.size() && !s->queue.empty(); ++i) {
+            if (slot_busy(s->slots[i])) continue;
+            int rc = launch_wave(s, i);
+            if (rc != PA_OK) return rc;
+            if (!slot_busy(s->slots[i])) break;  // held back by the memory budget
+        }
+        return PA_OK;
+    });
 }
 
 int pa_server_pending(pa_server_t s, uint64_t *queued, uint64_t *in_flight) {

@@ -142,3 +142,63 @@ def test_seed_from_eq1_matches_oracle(lib, n):
         assert int(got[-1]) >> ((2 * n - 1) % 64) == 0
     with pytest.raises(pkg.PAError):
         binding.pa_seed_from_eq1(0, tw)
+
+
+NOMEM_DRIVER = r'''
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <sys/resource.h>
+#include "pa.h"
+/* the process's current address-space size in bytes (VmSize of /proc/self/status) */
+static long vm_bytes(void) {
+    FILE *f = fopen("/proc/self/status", "r");
+    char line[256];
+    long kb = -1;
+    while (f && fgets(line, sizeof(line), f))
+        if (strncmp(line, "VmSize:", 7) == 0) kb = atol(line + 7);
+    if (f) fclose(f);
+    return kb * 1024;
+}
+int main(int argc, char **argv) {
+    pa_plan_desc d;
+    pa_opts o;
+    memset(&o, 0, sizeof(o));
+    o.device = -1;
+    o.path = PA_PATH_NTT31;
+    o.fd_mode = 1;
+    if (argc > 1) {  /* leave this process 96 MiB above what it holds now */
+        const long vm = vm_bytes();
+        if (vm <= 0) return 2;
+        struct rlimit r = {(rlim_t)vm + (96l << 20), (rlim_t)vm + (96l << 20)};
+        if (setrlimit(RLIMIT_AS, &r) != 0) return 3;
+    }
+    const int big = pa_plan_query(1000000007ull, 100000000ull, &o, &d);
+    const int small = pa_plan_query(100003, 25000, NULL, &d);
+    printf("%d %d\n", big, small);
+    return 0;
+}
+'''
+
+
+def test_host_allocation_failure_is_a_status(lib, tmp_path):
+    # A 1e9-bit key with transform-domain sums forbidden lays out 2.3e4 standard tile pairs,
+    # about 3e7 work items (230 MB of list). With the process's address space capped 96 MiB
+    # above its size, the list cannot grow: the C interface must return PA_ERR_NOMEM
+    # (std::bad_alloc caught at the boundary), not terminate, and stay usable afterwards.
+    import shutil
+    import subprocess
+    from paper_1805_02372_gb300 import build
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src, exe = tmp_path / "nomem.c", tmp_path / "nomem"
+    src.write_text(NOMEM_DRIVER)
+    r = subprocess.run(["gcc", "-O1", "-I", os.path.join(ROOT, "include"), str(src), build.LIB,
+                        "-Wl,-rpath," + os.path.dirname(build.LIB), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    free = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert free.returncode == 0 and free.stdout.split() == ["0", "0"], free.stdout + free.stderr
+    capped = subprocess.run([str(exe), "cap"], capture_output=True, text=True, timeout=300)
+    assert capped.returncode == 0, capped.stdout + capped.stderr
+    assert capped.stdout.split() == [str(binding.PA_ERR_NOMEM), "0"], capped.stdout
