@@ -1,0 +1,458 @@
+"""The persistent NTT kernel's work lists, replayed on the host (no GPU).
+
+`ntt_persistent` (csrc/ntt_kernel.cuh) hands out the items of its work list in list order
+(one atomic ticket per CTA). An item may wait, with a bounded spin, for a dependency counter
+to reach a target, and signals its own counters whether or not its wait succeeded. So a
+list can never wait forever if every wait is already satisfied when the items are run one
+by one in list order: whenever an item is handed out, every item before it has a CTA that
+will finish it. The lists the library builds (csrc/ntt.cu, ntt_batch_build) are dumped here
+by a small host program linked against the built library, for every layout it makes
+(single-CTA pairs; standard four-step pairs with their spectra slots reused round-robin;
+streamed, grouped, outer-convolution and segmented transform-domain sums; mixed batches
+of all of them; the 28-, 29-, 31- and 64-bit fields), and replayed:
+
+* every wait is satisfied by the items before it (no wait can run out on a correct GPU);
+* every waited counter ends exactly at the target it was waited for (no producer of a
+  waited-for result sits after its consumer, so no consumer can start early);
+* every item's tile and sub-index are in range, and every tile's passes cover each column
+  or row group exactly once;
+* the spectra slot a standard pair reuses is shared only with the pair the kernel waits for
+  (`slots` tiles earlier), and the transform-domain spectra lie beyond all slots.
+
+The wait and signal rules restated below are the kernel's: item type -> (counter, target)
+waited for, and the counters it increments.
+"""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1805_02372_gb300", "csrc")
+
+CHECKER = r'''
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+#include "ntt_defs.cuh"
+
+using namespace pa;
+
+static int g_fail = 0;
+static unsigned g_types = 0;
+static bool g_reversed = false;  // replay every list backwards (the checker must object)
+
+#define FAIL(...)                         \
+    do {                                  \
+        printf("FAIL %s: ", name);        \
+        printf(__VA_ARGS__);              \
+        printf("\n");                     \
+        ++g_fail;                         \
+        return;                           \
+    } while (0)
+
+// Counter indices: c1 [0, nt), c2 [nt, 2nt), c3 [2nt, 3nt), cfd [3nt, 3nt + nf),
+// cfd1 [3nt + nf, 3nt + 2nf).
+struct Lists {
+    const NttTile *T;
+    const FdBlock *F;
+    uint64_t nt, nf, slots;
+};
+
+// The counters an item increments (false: the item's tile or block is out of range).
+static bool signals(const Lists &L, uint32_t type, uint32_t ti, std::vector<uint64_t> *out) {
+    const NttTile &t = L.T[ti];
+    const uint64_t nt = L.nt, nf = L.nf;
+    switch (type) {
+        case IT_SMALL:
+        case IT_FD_P3: return true;
+        case IT_P1:
+        case IT_FD_OUTER: out->push_back(ti); return true;
+        case IT_P2:
+        case IT_FD_STREAM:
+        case IT_FD_INV2: out->push_back(nt + ti); return true;
+        case IT_P3: out->push_back(2 * nt + ti); return true;
+        case IT_FD_P1:
+            if (t.fd >= nf) return false;
+            out->push_back(ti);
+            out->push_back(3 * nt + nf + t.fd);
+            return true;
+        case IT_FD_P2:
+            if (t.fd >= nf) return false;
+            out->push_back(3 * nt + t.fd);
+            return true;
+        case IT_FD_SUM: {
+            if (t.fd >= nf) return false;
+            const FdBlock &b = L.F[t.fd];
+            if (t.out >= b.P) return false;
+            const uint32_t nout = std::min<uint32_t>(kSum4Out, b.P - t.out);
+            if (ti + nout > nt) return false;
+            for (uint32_t i = 0; i < nout; ++i) {
+                const NttTile &u = L.T[ti + i];
+                if (u.fd != t.fd || u.out != t.out + i) return false;
+                out->push_back(nt + ti + i);
+            }
+            return true;
+        }
+    }
+    return false;
+}
+
+// The counter and target an item waits for: 1, or 0 if it does not wait, -1 if out of range.
+static int waits(const Lists &L, uint32_t type, uint32_t ti, uint64_t *ctr, uint64_t *target) {
+    const NttTile &t = L.T[ti];
+    const uint64_t nt = L.nt, nf = L.nf;
+    switch (type) {
+        case IT_P1:
+            if (ti < L.slots) return 0;
+            *ctr = 2 * nt + ti - L.slots;
+            *target = L.T[ti - L.slots].g1;
+            return 1;
+        case IT_P2: *ctr = ti; *target = 2ull * t.g1; return 1;
+        case IT_P3:
+        case IT_FD_P3: *ctr = nt + ti; *target = t.g2; return 1;
+        case IT_FD_P2: *ctr = ti; *target = t.g1; return 1;
+        case IT_FD_SUM:
+        case IT_FD_OUTER:
+            if (t.fd >= nf) return -1;
+            *ctr = 3 * nt + t.fd;
+            *target = L.F[t.fd].nfwd2;
+            return 1;
+        case IT_FD_STREAM:
+            if (t.fd >= nf) return -1;
+            *ctr = 3 * nt + nf + t.fd;
+            *target = L.F[t.fd].nfwd1;
+            return 1;
+        case IT_FD_INV2:
+            if (t.octr >= nt) return -1;
+            *ctr = t.octr;
+            *target = L.T[t.octr].g2;
+            return 1;
+    }
+    return 0;
+}
+
+// Sub-indices of an item type on its tile: [0, range).
+static uint64_t sub_range(const NttTile &t, uint32_t type) {
+    switch (type) {
+        case IT_SMALL: return 1;
+        case IT_P1: return 2ull * t.g1;
+        case IT_P3:
+        case IT_FD_P1:
+        case IT_FD_P3: return t.g1;
+        default: return t.g2;  // P2, FD_P2, FD_SUM, FD_STREAM, FD_OUTER, FD_INV2
+    }
+}
+
+static void check(const char *name, const NttBatchInfo &in, int field) {
+    const size_t nt = in.ntiles, nf = in.nfd, ni = in.host_items.size();
+    std::vector<uint64_t> items(in.host_items);
+    if (g_reversed) std::reverse(items.begin(), items.end());
+    if (in.host_tiles.size() != nt * sizeof(NttTile) || in.host_fd.size() != nf * sizeof(FdBlock) ||
+        ni != in.nitems || ni == 0)
+        FAIL("table sizes");
+    Lists L{reinterpret_cast<const NttTile *>(in.host_tiles.data()),
+            reinterpret_cast<const FdBlock *>(in.host_fd.data()), nt, nf, in.slots};
+    std::vector<uint64_t> fin(3 * nt + 2 * nf, 0), cnt(3 * nt + 2 * nf, 0), sig;
+    // (tile, type) -> how often each sub-index occurs; FD_SUM rows counted on every sum
+    // tile an item covers
+    std::map<std::pair<uint32_t, uint32_t>, std::vector<uint32_t>> cover;
+    auto mark = [&](uint32_t ti, uint32_t type, uint32_t sub) -> bool {
+        std::vector<uint32_t> &v = cover[{ti, type}];
+        const uint64_t r = sub_range(L.T[ti], type);
+        if (v.empty()) v.assign(r, 0);
+        if (sub >= r) return false;
+        ++v[sub];
+        return true;
+    };
+    for (size_t k = 0; k < ni; ++k) {
+        const uint64_t it = items[k];
+        const uint32_t type = static_cast<uint32_t>(it >> 60);
+        const uint32_t ti = static_cast<uint32_t>((it >> 32) & 0x0FFFFFFFu);
+        const uint32_t sub = static_cast<uint32_t>(it);
+        if (type > IT_FD_INV2 || ti >= nt) FAIL("item %zu: type %u tile %u", k, type, ti);
+        g_types |= 1u << type;
+        sig.clear();
+        if (!signals(L, type, ti, &sig)) FAIL("item %zu: signals out of range", k);
+        for (uint64_t c : sig) ++fin[c];
+        if (type == IT_FD_SUM) {
+            for (size_t i = 0; i < sig.size(); ++i)
+                if (!mark(ti + static_cast<uint32_t>(i), type, sub)) FAIL("item %zu: sum row %u", k, sub);
+        } else if (!mark(ti, type, sub)) {
+            FAIL("item %zu: sub %u out of range (type %u)", k, sub, type);
+        }
+    }
+    // replay in list order
+    for (size_t k = 0; k < ni; ++k) {
+        const uint64_t it = items[k];
+        const uint32_t type = static_cast<uint32_t>(it >> 60);
+        const uint32_t ti = static_cast<uint32_t>((it >> 32) & 0x0FFFFFFFu);
+        uint64_t c = 0, target = 0;
+        const int w = waits(L, type, ti, &c, &target);
+        if (w < 0) FAIL("item %zu: wait out of range", k);
+        if (w == 1) {
+            if (target == 0) FAIL("item %zu: waits for nothing (type %u)", k, type);
+            if (cnt[c] < target)
+                FAIL("item %zu (type %u tile %u) waits for %llu of counter %llu, %llu done before it",
+                     k, type, ti, (unsigned long long)target, (unsigned long long)c,
+                     (unsigned long long)cnt[c]);
+            if (fin[c] != target)
+                FAIL("item %zu (type %u tile %u): counter %llu ends at %llu, waited for %llu", k, type,
+                     ti, (unsigned long long)c, (unsigned long long)fin[c], (unsigned long long)target);
+        }
+        sig.clear();
+        signals(L, type, ti, &sig);
+        for (uint64_t s : sig) ++cnt[s];
+    }
+    // each pass of each tile covers its groups exactly once; every tile is used
+    std::vector<unsigned> roles(nt, 0);
+    for (const auto &e : cover) {
+        for (size_t s = 0; s < e.second.size(); ++s)
+            if (e.second[s] != 1)
+                FAIL("tile %u type %u: sub %zu covered %u times", e.first.first, e.first.second, s,
+                     e.second[s]);
+        roles[e.first.first] |= 1u << e.first.second;
+    }
+    uint64_t big_end = 0, fd_min = ~0ull;
+    const unsigned fd_types = (1u << IT_FD_P1) | (1u << IT_FD_P2) | (1u << IT_FD_SUM) |
+                              (1u << IT_FD_P3) | (1u << IT_FD_STREAM) | (1u << IT_FD_OUTER) |
+                              (1u << IT_FD_INV2);
+    for (size_t ti = 0; ti < nt; ++ti) {
+        const unsigned r = roles[ti];
+        const NttTile &t = L.T[ti];
+        if (!r) FAIL("tile %zu is in no item", ti);
+        if (r & (1u << IT_P1)) {
+            if (r != ((1u << IT_P1) | (1u << IT_P2) | (1u << IT_P3))) FAIL("standard tile %zu passes %x", ti, r);
+            big_end = std::max<uint64_t>(big_end, t.ws_off + (uint64_t(2) << t.logN));
+        }
+        if ((r & (1u << IT_FD_P1)) && t.fd < nf && L.F[t.fd].nfwd2 && !(r & (1u << IT_FD_P2)))
+            FAIL("spectrum tile %zu has no forward pass 2", ti);
+        if (r & (1u << IT_FD_P3)) {
+            const unsigned p2 = r & ((1u << IT_FD_SUM) | (1u << IT_FD_STREAM) | (1u << IT_FD_INV2));
+            if (p2 == 0 || (p2 & (p2 - 1))) FAIL("sum tile %zu pass-2 producers %x", ti, p2);
+        }
+        if (r & fd_types) fd_min = std::min<uint64_t>(fd_min, t.ws_off);
+    }
+    // spectra slots: tile ti shares its slot with ti - slots only
+    const uint64_t S = L.slots;
+    for (size_t b = 0; b < nt; ++b) {
+        if (!(roles[b] & (1u << IT_P1))) continue;
+        const NttTile &tb = L.T[b];
+        const uint64_t b0 = tb.ws_off, b1 = b0 + (uint64_t(2) << tb.logN);
+        if (b >= S) {
+            if (!(roles[b - S] & (1u << IT_P1)) || L.T[b - S].ws_off != b0)
+                FAIL("tile %zu does not reuse the slot of tile %zu", b, size_t(b - S));
+        }
+        for (size_t a = b >= S ? b - S + 1 : 0; a < b; ++a) {
+            if (!(roles[a] & (1u << IT_P1))) continue;
+            const uint64_t a0 = L.T[a].ws_off, a1 = a0 + (uint64_t(2) << L.T[a].logN);
+            if (a0 < b1 && b0 < a1) FAIL("tiles %zu and %zu share spectra without a wait", a, b);
+        }
+    }
+    if (fd_min != ~0ull && fd_min < big_end) FAIL("transform-domain spectra inside the slots");
+    printf("ok %s field %d items %zu tiles %zu fd %zu slots %llu\n", name, field, ni, nt, nf,
+           (unsigned long long)S);
+}
+
+int main(int argc, char **argv) {
+    g_reversed = argc > 1 && strcmp(argv[1], "reversed") == 0;
+    char line[512], name[128] = "";
+    uint32_t max_slots = 0;
+    std::vector<BatchBlock> groups[kNumFields];
+    while (fgets(line, sizeof(line), stdin)) {
+        if (line[0] == 'B') {
+            sscanf(line + 2, "%127s %u", name, &max_slots);
+            for (auto &g : groups) g.clear();
+        } else if (line[0] == 'X') {
+            unsigned long long n, m;
+            pa_opts o;
+            memset(&o, 0, sizeof(o));
+            o.device = -1;
+            int path;
+            sscanf(line + 2, "%llu %llu %d %u %llu %llu %u %u %u %u %u %u", &n, &m, &path,
+                   &o.log2_transform, (unsigned long long *)&o.tile_in,
+                   (unsigned long long *)&o.tile_out, &o.fd_mode, &o.fd_group, &o.outer_mode,
+                   &o.seg_in, &o.seg_out, &o.ntt_prime);
+            o.path = path;
+            PlanCfg cfg;
+            const int rc = plan_resolve(n, m, &o, &cfg, false);
+            if (rc != PA_OK || (cfg.path != PA_PATH_NTT31 && cfg.path != PA_PATH_NTT64)) {
+                printf("FAIL %s: plan n=%llu m=%llu rc %d path %d\n", name, n, m, rc, cfg.path);
+                ++g_fail;
+                continue;
+            }
+            const TransformCfg &c = cfg.tr;
+            if (!c.segs.empty()) {  // each segment is its own launch (seg_build's ranges)
+                const uint64_t Sk = (c.tiles_in + c.seg_in - 1) / c.seg_in;
+                for (uint64_t idx = 0; idx < c.segs.size(); ++idx) {
+                    BatchBlock b;
+                    b.index = 0;
+                    b.n = n;
+                    b.m = m;
+                    b.tr = c;
+                    b.tr.seg_in = b.tr.seg_out = 0;
+                    b.tr.segs.clear();
+                    b.tr.seg_base.clear();
+                    const uint64_t a = idx / Sk, g = idx % Sk;
+                    b.I0 = a * c.seg_out;
+                    b.I1 = std::min<uint64_t>(c.tiles_out, (a + 1) * c.seg_out);
+                    b.J0 = g * c.seg_in;
+                    b.J1 = std::min<uint64_t>(c.tiles_in, (g + 1) * c.seg_in);
+                    NttBatchInfo info;
+                    char sn[200];
+                    snprintf(sn, sizeof(sn), "%s/segment%llu", name, (unsigned long long)idx);
+                    if (ntt_batch_build(c.field, {b}, max_slots, &info) != PA_OK) {
+                        printf("FAIL %s: build\n", sn);
+                        ++g_fail;
+                        continue;
+                    }
+                    check(sn, info, c.field);
+                }
+                continue;
+            }
+            BatchBlock b;
+            b.n = n;
+            b.m = m;
+            b.tr = c;
+            b.index = static_cast<uint32_t>(groups[c.field].size());
+            groups[c.field].push_back(b);
+        } else if (line[0] == 'E') {
+            for (int f = 0; f < kNumFields; ++f) {
+                if (groups[f].empty()) continue;
+                NttBatchInfo info;
+                if (ntt_batch_build(f, groups[f], max_slots, &info) != PA_OK) {
+                    printf("FAIL %s: build field %d\n", name, f);
+                    ++g_fail;
+                    continue;
+                }
+                check(name, info, f);
+            }
+        }
+    }
+    printf("types %x fails %d\n", g_types, g_fail);
+    return g_fail ? 1 : 0;
+}
+'''
+
+NTT31, NTT64 = 3, 2
+
+
+def X(n, m, path=NTT31, k=0, L=0, M=0, fd=0, group=0, outer=0, si=0, so=0, prime=0):
+    return f"X {n} {m} {path} {k} {L} {M} {fd} {group} {outer} {si} {so} {prime}"
+
+
+def _batched_shapes(count, seed):
+    # the batched workload's distribution: n log-uniform in [1e5, 4e6], compression 1%-50%
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    u, v = rng.random(count), rng.random(count)
+    n = np.floor(1e5 * 40.0 ** u).astype(np.int64)
+    m = np.maximum(1, np.floor((0.01 + 0.49 * v) * n)).astype(np.int64)
+    return list(zip(n.tolist(), m.tolist()))
+
+
+def _cases():
+    cases = []
+
+    def case(name, slots, *blocks):
+        cases.append("\n".join([f"B {name} {slots}", *blocks, "E"]))
+
+    # one-CTA pairs (N <= 2^12) and standard four-step pairs, slots reused round-robin
+    case("small", 0, X(50_003, 20_011, k=12, L=2048, M=2048, fd=1))
+    for prime in (28, 29, 31):
+        case(f"standard{prime}", 4, X(200_003, 60_001, k=13, L=4096, M=4096, fd=1, prime=prime))
+    case("standard_slots5", 5, X(1_000_003, 150_001, k=14, L=8192, M=8192, fd=1))
+    case("standard_unbounded", 0, X(300_007, 90_001, k=15, L=16384, M=16384, fd=1))
+    case("standard64", 4, X(200_003, 60_001, NTT64, k=13, L=4096, M=4096, fd=1))
+    # transform-domain sums: windows of every structure, grouped sums, streamed sums
+    for path in (NTT31, NTT64):
+        case(f"fd_equal{path}", 0, X(50_003, 20_011, path, k=13, L=4096, M=4096, fd=2))
+        case(f"fd_l2m{path}", 0, X(50_003, 20_011, path, k=13, L=4096, M=2048, fd=2))
+        case(f"fd_m2l{path}", 0, X(30_001, 40_003, path, k=13, L=2048, M=4096, fd=2))
+        case(f"fd_ragged{path}", 0, X(40_000, 30_000, path, k=13, L=3008, M=1088, fd=2))
+        case(f"streamed{path}", 0, X(50_003, 3_000, path, k=13, L=4096, M=3008, fd=2))
+    case("fd_groups", 0, X(131_075, 70_001, k=14, L=8192, M=8192, fd=2, group=3))
+    case("streamed_big", 0, X(1_000_003, 60_000, k=17, L=70_016, M=60_032, fd=2))
+    case("fd_2to23", 0, X(20_000_003, 8_000_001, k=23, L=1 << 22, M=1 << 22, fd=2))
+    # outer convolutions over the tile index, with and without groups
+    case("outer", 0, X(400_003, 200_003, k=15, L=1 << 14, M=1 << 14, fd=2, outer=2))
+    case("outer_groups", 0, X(400_003, 200_003, k=15, L=1 << 14, M=1 << 14, fd=2, group=5,
+                               outer=2, prime=31))
+    case("outer64", 0, X(100_003, 60_001, NTT64, k=13, L=4096, M=4096, fd=2, outer=2))
+    # segmented sums (one launch per segment), direct and outer
+    case("segmented", 0, X(2_000_007, 600_003, k=19, L=1 << 18, M=1 << 18, fd=2, si=3, so=2))
+    case("segmented_outer", 0, X(1_000_003, 500_001, k=15, L=1 << 14, M=1 << 14, fd=2,
+                                  outer=2, si=5, so=7))
+    case("segmented64", 0, X(2_000_007, 600_003, NTT64, k=19, L=1 << 18, M=1 << 18, fd=2,
+                              si=3, so=2, prime=0))
+    # the planner's own choices
+    case("paper_scale_1e9", 0, X(1_000_000_007, 100_000_000))
+    case("table1_128M", 0, X(128 << 20, (128 << 20) // 10))
+    # batches: the batched distribution (default plans, the 28-bit field), with few slots,
+    # and one list mixing every layout
+    case("batched64", 0, *[X(n, m) for n, m in _batched_shapes(64, 11)])
+    case("batched64_slots4", 4, *[X(n, m, fd=1) for n, m in _batched_shapes(64, 12)])
+    case("mixed", 4,
+         X(50_003, 20_011, k=12, L=2048, M=2048, fd=1, prime=29),
+         X(200_003, 60_001, k=13, L=4096, M=4096, fd=1, prime=29),
+         X(50_003, 3_000, k=13, L=4096, M=3008, fd=2, prime=29),
+         X(50_003, 20_011, k=13, L=4096, M=2048, fd=2, prime=29),
+         X(131_075, 70_001, k=14, L=8192, M=8192, fd=2, group=3, prime=29),
+         X(400_003, 200_003, k=15, L=1 << 14, M=1 << 14, fd=2, outer=2, prime=29),
+         X(1_000_003, 150_001, k=14, L=8192, M=8192, fd=1, prime=29),
+         X(8_191, 8_193, k=13, L=4096, M=4096, fd=2, prime=29))
+    return "\n".join(cases) + "\n"
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    from paper_1805_02372_gb300 import build
+    lib = build.build()
+    d = tmp_path_factory.mktemp("wl")
+    src, exe = d / "check.cu", d / "check"
+    src.write_text(CHECKER)
+    r = subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O1",
+                        "-gencode", "arch=compute_103a,code=compute_103a",
+                        "-I", os.path.join(ROOT, "include"), "-I", CSRC, str(src), lib,
+                        "-Xlinker", "-rpath=" + os.path.dirname(lib), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-4000:]
+    return exe
+
+
+def test_every_wait_is_satisfied_by_earlier_items(checker):
+    r = subprocess.run([str(checker)], input=_cases(), capture_output=True, text=True,
+                       timeout=600)
+    out = r.stdout
+    fails = [line for line in out.splitlines() if line.startswith("FAIL")]
+    assert r.returncode == 0 and not fails, "\n".join(fails[:20]) + r.stderr[-2000:]
+    oks = [line for line in out.splitlines() if line.startswith("ok ")]
+    assert len(oks) >= 30
+    # every item type of the kernel occurred (IT_SMALL .. IT_FD_INV2)
+    types = int(out.splitlines()[-1].split()[1], 16)
+    assert types == (1 << 11) - 1, hex(types)
+    # the segmented and batched cases produced their launches, over several fields
+    assert sum(1 for line in oks if "/segment" in line) >= 6 + 6
+    assert {line.split()[3] for line in oks} >= {"1", "2", "3"}
+
+
+def test_replay_rejects_a_list_run_backwards(checker):
+    # the same lists reversed put every consumer before its producers: every list that has
+    # a wait at all must be rejected (only the one-CTA case has none)
+    ok = subprocess.run([str(checker)], input=_cases(), capture_output=True, text=True,
+                        timeout=600)
+    bad = subprocess.run([str(checker), "reversed"], input=_cases(), capture_output=True,
+                         text=True, timeout=600)
+    names = [line.split()[1] for line in ok.stdout.splitlines() if line.startswith("ok ")]
+    rejected = {line.split()[1].rstrip(":") for line in bad.stdout.splitlines()
+                if line.startswith("FAIL") and "waits for" in line}
+    assert bad.returncode == 1
+    assert set(names) - rejected == {"small"}, sorted(set(names) - rejected)
