@@ -17,7 +17,10 @@ of all of them; the 28-, 29-, 31- and 64-bit fields), and replayed:
 * every item's tile and sub-index are in range, and every tile's passes cover each column
   or row group exactly once;
 * the spectra slot a standard pair reuses is shared only with the pair the kernel waits for
-  (`slots` tiles earlier), and the transform-domain spectra lie beyond all slots.
+  (`slots` tiles earlier), and the transform-domain spectra lie beyond all slots;
+* every spectrum an item reads or writes (standard key and window spectra, accumulated key,
+  window and sum spectra, an outer convolution's slice of sums, every window a block's
+  window-index table names) lies inside the workspace's spectra region.
 
 The wait and signal rules restated below are the kernel's: item type -> (counter, target)
 waited for, and the counters it increments.
@@ -255,6 +258,34 @@ static void check(const char *name, const NttBatchInfo &in, int field) {
         }
     }
     if (fd_min != ~0ull && fd_min < big_end) FAIL("transform-domain spectra inside the slots");
+    // every spectrum an item reads or writes lies in the workspace's spectra region
+    const uint64_t elem = field == kFieldF64 ? 8 : 4, E = (in.bytes - in.off_spec) / elem;
+    if (in.off_spec > in.bytes || in.counter_bytes != (3 * nt + 1 + 2 * nf) * 4)
+        FAIL("workspace layout");
+    std::vector<uint64_t> fdN(nf, 0);
+    for (size_t ti = 0; ti < nt; ++ti) {
+        const unsigned r = roles[ti];
+        const NttTile &t = L.T[ti];
+        const uint64_t N = uint64_t(1) << t.logN;
+        uint64_t len = 0;
+        if (r & (1u << IT_P1)) len = 2 * N;  // key spectrum, then the window's
+        else if (r & (1u << IT_FD_OUTER)) len = uint64_t(t.nout) * N;  // the slice's sums
+        else if (r & fd_types) len = N;
+        if (len && t.ws_off + len > E)
+            FAIL("tile %zu spectra [%llu, +%llu) beyond %llu", ti, (unsigned long long)t.ws_off,
+                 (unsigned long long)len, (unsigned long long)E);
+        if ((r & fd_types) && t.fd < nf) fdN[t.fd] = N;
+    }
+    for (size_t f = 0; f < nf; ++f) {
+        const FdBlock &b = L.F[f];
+        const uint64_t N = fdN[f], pairs = uint64_t(b.P) * b.Q;
+        if (!N) FAIL("block %zu has no spectra", f);
+        if (b.x_off + uint64_t(b.Q) * N > E) FAIL("block %zu key spectra beyond the region", f);
+        if (b.wmap + pairs > in.host_wmap.size()) FAIL("block %zu window table", f);
+        for (uint64_t e = b.wmap; e < b.wmap + pairs; ++e)
+            if (b.w_off + (uint64_t(in.host_wmap[e]) + 1) * N > E)
+                FAIL("block %zu window %u beyond the region", f, in.host_wmap[e]);
+    }
     printf("ok %s field %d items %zu tiles %zu fd %zu slots %llu\n", name, field, ni, nt, nf,
            (unsigned long long)S);
 }
