@@ -18,9 +18,6 @@ int cuda_fail(cudaError_t e) {
     return PA_ERR_CUDA;
 }
 
-// Largest sizes accepted at all (the seed index n+m-2 must fit comfortably).
-constexpr uint64_t kMaxBits = uint64_t(1) << 40;
-
 // Standard tile pairs (no transform-domain sums) a plan may lay out, and work items
 // their persistent launch may list (2^28 items: 2 GiB of work list on host and device).
 constexpr uint64_t kStdMaxPairs = uint64_t(1) << 22;
@@ -41,7 +38,7 @@ static double std_items(const TransformCfg &t) {
 }
 
 int plan_resolve(uint64_t n, uint64_t m, const pa_opts *o, PlanCfg *cfg, bool layout) {
-    if (!cfg || n == 0 || m == 0 || n > kMaxBits || m > kMaxBits) return PA_ERR_INVALID;
+    if (!cfg || !sizes_valid(n, m)) return PA_ERR_INVALID;
     *cfg = PlanCfg();
     cfg->n = n;
     cfg->m = m;
@@ -223,10 +220,11 @@ int pa_seed_from_eq1(uint64_t n, const uint64_t *t_bits, uint64_t *seed_bits) {
 int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out) {
     if (!out) return PA_ERR_INVALID;
     *out = nullptr;
+    if (!sizes_valid(n, m)) return PA_ERR_INVALID;
     pa_plan_s *p = new (std::nothrow) pa_plan_s();
     if (!p) return PA_ERR_NOMEM;
     pa_opts tuned;
-    if ((!opts || opts->path == PA_PATH_AUTO) && n > 0 && m > 0) {
+    if (!opts || opts->path == PA_PATH_AUTO) {
         // AUTO: the autotuner's measured-cost choice (calibrates once per device)
         const int trc = guarded([&] { return tuned_opts(n, m, &tuned); });
         if (trc != PA_OK) {

@@ -476,6 +476,8 @@ int batch_plan_impl(const pa_block *blocks, size_t count, const pa_opts *opts,
                     cudaStream_t alloc_stream, bool eager, pa_batch_s **out) {
     if (!out || !blocks || count == 0 || count > (size_t(1) << 24)) return PA_ERR_INVALID;
     *out = nullptr;
+    for (size_t i = 0; i < count; ++i)
+        if (!sizes_valid(blocks[i].n, blocks[i].m)) return PA_ERR_INVALID;
     // the batch is freed (device memory and all) on every early return
     const auto release = [](pa_batch_s *x) {
         batch_free(x);

@@ -171,7 +171,8 @@ int pa_server_create(const pa_server_opts *opts, pa_server_t *out) {
 
 int pa_server_submit(pa_server_t s, const pa_block *req, uint64_t tag) {
     return guarded([&] {
-        if (!s || !req || req->n == 0 || req->m == 0 || !req->seed_bits || !req->key_bits ||
+        // a request no plan can take is refused here, not left to block the queue
+        if (!s || !req || !sizes_valid(req->n, req->m) || !req->seed_bits || !req->key_bits ||
             !req->out_bits)
             return PA_ERR_INVALID;
         std::lock_guard<std::mutex> lk(s->mu);

@@ -202,3 +202,110 @@ def test_host_allocation_failure_is_a_status(lib, tmp_path):
     capped = subprocess.run([str(exe), "cap"], capture_output=True, text=True, timeout=300)
     assert capped.returncode == 0, capped.stdout + capped.stderr
     assert capped.stdout.split() == [str(binding.PA_ERR_NOMEM), "0"], capped.stdout
+
+
+INVALID_DRIVER = r'''
+#include <stdio.h>
+#include <string.h>
+#include "pa.h"
+static int fails = 0;
+#define EXPECT(call, want)                                                        \
+    do {                                                                          \
+        const int got_ = (call);                                                  \
+        if (got_ != (want)) {                                                     \
+            printf("FAIL %s -> %d, expected %d\n", #call, got_, (int)(want));     \
+            ++fails;                                                              \
+        }                                                                         \
+    } while (0)
+int main(void) {
+    static uint64_t buf[8] __attribute__((aligned(16)));
+    uint64_t *odd = (uint64_t *)((char *)buf + 8);
+    pa_plan_desc d;
+    pa_plan_t plan = (pa_plan_t)0;
+    pa_batch_t batch = (pa_batch_t)0;
+    pa_server_t server = (pa_server_t)0;
+    pa_block blk = {1000, 100, buf, buf, buf};
+    pa_report rep;
+    pa_completion done[4];
+    pa_server_stats st;
+    pa_kernel_time kt[4];
+    size_t count = 0;
+    int n = 0;
+    double r = 0, b = 0;
+    /* plans */
+    EXPECT(pa_plan(0, 5, &plan), PA_ERR_INVALID);
+    EXPECT(pa_plan(5, 5, NULL), PA_ERR_INVALID);
+    EXPECT(pa_plan_ex(5, 0, NULL, &plan), PA_ERR_INVALID);
+    EXPECT(pa_plan_ex((uint64_t)1 << 41, 5, NULL, &plan), PA_ERR_INVALID);
+    EXPECT(pa_plan_query(5, 5, NULL, NULL), PA_ERR_INVALID);
+    EXPECT(pa_plan_describe(NULL, &d), PA_ERR_INVALID);
+    EXPECT(pa_hash(NULL, buf, buf, buf, NULL), PA_ERR_INVALID);
+    EXPECT(pa_hash_host(NULL, buf, buf, buf, NULL), PA_ERR_INVALID);
+    EXPECT(pa_last_residual(NULL, &r, &b), PA_ERR_INVALID);
+    EXPECT(pa_plan_status(NULL), PA_ERR_INVALID);
+    EXPECT(pa_plan_profile(NULL, 1), PA_ERR_INVALID);
+    EXPECT(pa_plan_kernel_times(NULL, kt, 4, &n), PA_ERR_INVALID);
+    pa_plan_destroy(NULL);
+    /* the no-allocation entry point: sizes and alignment first */
+    EXPECT(pa_hash_direct_static(0, 5, buf, buf, buf, NULL), PA_ERR_INVALID);
+    EXPECT(pa_hash_direct_static(5, 5, NULL, buf, buf, NULL), PA_ERR_INVALID);
+    EXPECT(pa_hash_direct_static(5, 5, odd, buf, buf, NULL), PA_ERR_ALIGN);
+    EXPECT(pa_hash_direct_static((uint64_t)1 << 26, 5, buf, buf, buf, NULL), PA_ERR_TOO_LARGE);
+    /* batches */
+    EXPECT(pa_batch_plan(NULL, 1, NULL, &batch), PA_ERR_INVALID);
+    EXPECT(pa_batch_plan(&blk, 0, NULL, &batch), PA_ERR_INVALID);
+    EXPECT(pa_batch_plan(&blk, 1, NULL, NULL), PA_ERR_INVALID);
+    blk.n = (uint64_t)1 << 41;  /* refused before the autotuner calibrates */
+    EXPECT(pa_batch_plan(&blk, 1, NULL, &batch), PA_ERR_INVALID);
+    blk.n = 1000;
+    EXPECT(pa_batch_run(NULL, &blk, 1, NULL, &rep), PA_ERR_INVALID);
+    EXPECT(pa_batch_run_host(NULL, &blk, 1, NULL, &rep), PA_ERR_INVALID);
+    EXPECT(pa_batch_run_host_async(NULL, &blk, 1, NULL), PA_ERR_INVALID);
+    EXPECT(pa_batch_get_report(NULL, NULL, &rep), PA_ERR_INVALID);
+    EXPECT(pa_batch_describe(NULL, &d, 1), PA_ERR_INVALID);
+    EXPECT(pa_batch_profile(NULL, 1), PA_ERR_INVALID);
+    EXPECT(pa_batch_kernel_times(NULL, kt, 4, &n), PA_ERR_INVALID);
+    EXPECT(pa_hash_batched(NULL, 1, NULL, &rep), PA_ERR_INVALID);
+    EXPECT(pa_hash_batched(&blk, 0, NULL, &rep), PA_ERR_INVALID);
+    pa_batch_destroy(NULL);
+    /* server */
+    EXPECT(pa_server_create(NULL, NULL), PA_ERR_INVALID);
+    EXPECT(pa_server_submit(NULL, &blk, 1), PA_ERR_INVALID);
+    EXPECT(pa_server_poll(NULL, done, 4, &count), PA_ERR_INVALID);
+    EXPECT(pa_server_pending(NULL, NULL, NULL), PA_ERR_INVALID);
+    EXPECT(pa_server_get_stats(NULL, &st), PA_ERR_INVALID);
+    pa_server_destroy(NULL);
+    /* host helpers and probes */
+    EXPECT(pa_seed_from_eq1(0, buf, buf), PA_ERR_INVALID);
+    EXPECT(pa_seed_from_eq1(5, NULL, buf), PA_ERR_INVALID);
+    EXPECT(pa_fft_rounding_bound(0, 64, 64, 0, &r), PA_ERR_INVALID);
+    EXPECT(pa_fft_rounding_bound(12, 64, 64, 0, NULL), PA_ERR_INVALID);
+    EXPECT(pa_probe_peak(-1, &r, &b), PA_ERR_INVALID);
+    EXPECT(pa_probe_peak(0, NULL, &b), PA_ERR_INVALID);
+    EXPECT(pa_selftest(0, &n), PA_ERR_INVALID);
+    EXPECT(pa_selftest(1, NULL), PA_ERR_INVALID);
+    /* none of the above reached the CUDA runtime */
+    EXPECT(pa_last_cuda_error(), 0);
+    printf("done %d\n", fails);
+    return fails != 0;
+}
+'''
+
+
+def test_invalid_arguments_refused_before_any_cuda_call(lib, tmp_path):
+    # Every entry point checks its handle, pointers, sizes and alignment before it touches
+    # the CUDA runtime: on this machine (no GPU) each call returns its documented status,
+    # and the last CUDA error stays 0 (a CUDA call would have failed here and set it).
+    import shutil
+    import subprocess
+    from paper_1805_02372_gb300 import build
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src, exe = tmp_path / "invalid.c", tmp_path / "invalid"
+    src.write_text(INVALID_DRIVER)
+    r = subprocess.run(["gcc", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"), str(src),
+                        build.LIB, "-Wl,-rpath," + os.path.dirname(build.LIB), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert run.returncode == 0 and run.stdout.strip().endswith("done 0"), run.stdout + run.stderr
