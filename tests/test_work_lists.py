@@ -20,7 +20,16 @@ of all of them; the 28-, 29-, 31- and 64-bit fields), and replayed:
   (`slots` tiles earlier), and the transform-domain spectra lie beyond all slots;
 * every spectrum an item reads or writes (standard key and window spectra, accumulated key,
   window and sum spectra, an outer convolution's slice of sums, every window a block's
-  window-index table names) lies inside the workspace's spectra region.
+  window-index table names) lies inside the workspace's spectra region;
+* the decomposition (Sec. 3, Eq. Ti / Eq. Tij): every product, a standard pair or a term
+  X_J W_d(I,J) of a transform-domain sum (its key spectrum, the window the block's table
+  names, the sum's output rows), puts seed bit n-1+i-j under output row i and key bit j
+  at the convolution index the inverse reads, with no cyclic wrap onto those rows; and the
+  products of each block, over all launches of a segmented plan, tile its m x n plane of
+  (row, key bit) exactly once.
+
+Two planted mistakes, made on the host copy of the lists, must be caught: the lists run
+backwards, and every seed window moved by one bit.
 
 The wait and signal rules restated below are the kernel's: item type -> (counter, target)
 waited for, and the counters it increments.
@@ -49,6 +58,67 @@ using namespace pa;
 static int g_fail = 0;
 static unsigned g_types = 0;
 static bool g_reversed = false;  // replay every list backwards (the checker must object)
+static bool g_shifted = false;   // move every seed window by one bit (the checker must object)
+static uint64_t g_products = 0;  // products checked against the definition
+
+// Sec. 3 decomposition: the (output rows) x (key bits) rectangle each product computes, per
+// block of the list, collected over all launches of a plan
+struct Rect {
+    uint64_t ob, ol, kb, kl;
+};
+static std::map<uint32_t, std::vector<Rect>> g_rects;
+
+// Pair (kp: key bits, wp: seed window, op: output rows and the convolution index K0 of the
+// first row) of an N-point cyclic convolution: checks it against y[i] = XOR_j x[j] s[n-1+i-j].
+static const char *pair_error(const TilePair &kp, const TilePair &wp, const TilePair &op,
+                              uint64_t N, uint64_t n, uint64_t m) {
+    if (kp.key_len == 0 || kp.key_bit0 < 0 || uint64_t(kp.key_bit0) + kp.key_len > n)
+        return "key range";
+    if (op.out_len == 0 || op.out_bit0 % 64 || op.out_bit0 + op.out_len > m) return "output range";
+    if (kp.key_len > N || wp.win_len > N) return "input longer than the transform";
+    // row i, key bit j: seed bit n-1+i-j is window position u = n-1+i-j - win_bit0, and the
+    // product's coefficient k = u + (j - key_bit0) = n-1+i - key_bit0 - win_bit0
+    const int64_t k0 = int64_t(n) - 1 + int64_t(op.out_bit0) - kp.key_bit0 - wp.win_bit0;
+    if (k0 != int64_t(op.K0)) return "convolution index of the first row";
+    const int64_t umin = k0 - int64_t(kp.key_len - 1), umax = k0 + int64_t(op.out_len) - 1;
+    if (umin < 0 || umax >= int64_t(wp.win_len)) return "seed bit outside the window";
+    // the linear product has key_len + win_len - 1 coefficients; cyclically, coefficient
+    // k + N wraps onto k: none may land on a row that is read
+    const int64_t lin = int64_t(kp.key_len) + int64_t(wp.win_len) - 1;
+    if (umax + 0 >= int64_t(N) || int64_t(op.K0) + int64_t(op.out_len) > int64_t(N) ||
+        lin - int64_t(N) > int64_t(op.K0))
+        return "cyclic wrap onto the rows read";
+    return nullptr;
+}
+
+// The rectangles of block blk tile [0, m) x [0, n) exactly once.
+static const char *partition_error(const std::vector<Rect> &r, uint64_t n, uint64_t m) {
+    std::map<uint64_t, uint64_t> rows, keys;
+    for (const Rect &x : r) {
+        if (rows.count(x.ob) && rows[x.ob] != x.ol) return "output tiles of two lengths";
+        if (keys.count(x.kb) && keys[x.kb] != x.kl) return "key tiles of two lengths";
+        rows[x.ob] = x.ol;
+        keys[x.kb] = x.kl;
+    }
+    uint64_t at = 0;
+    for (const auto &e : rows) {
+        if (e.first != at) return "output rows not tiled";
+        at += e.second;
+    }
+    if (at != m) return "output rows not covered";
+    at = 0;
+    for (const auto &e : keys) {
+        if (e.first != at) return "key bits not tiled";
+        at += e.second;
+    }
+    if (at != n) return "key bits not covered";
+    std::vector<std::pair<uint64_t, uint64_t>> cells;
+    for (const Rect &x : r) cells.push_back({x.ob, x.kb});
+    std::sort(cells.begin(), cells.end());
+    if (std::unique(cells.begin(), cells.end()) != cells.end()) return "a product computed twice";
+    if (cells.size() != rows.size() * keys.size()) return "a product missing";
+    return nullptr;
+}
 
 #define FAIL(...)                         \
     do {                                  \
@@ -152,15 +222,21 @@ static uint64_t sub_range(const NttTile &t, uint32_t type) {
     }
 }
 
-static void check(const char *name, const NttBatchInfo &in, int field) {
+static void check(const char *name, const NttBatchInfo &in, int field,
+                  const std::vector<std::pair<uint64_t, uint64_t>> &shape) {
     const size_t nt = in.ntiles, nf = in.nfd, ni = in.host_items.size();
     std::vector<uint64_t> items(in.host_items);
     if (g_reversed) std::reverse(items.begin(), items.end());
     if (in.host_tiles.size() != nt * sizeof(NttTile) || in.host_fd.size() != nf * sizeof(FdBlock) ||
         ni != in.nitems || ni == 0)
         FAIL("table sizes");
-    Lists L{reinterpret_cast<const NttTile *>(in.host_tiles.data()),
+    std::vector<NttTile> tiles(nt);
+    if (nt) memcpy(tiles.data(), in.host_tiles.data(), nt * sizeof(NttTile));
+    if (g_shifted)
+        for (NttTile &t : tiles) t.p.win_bit0 += 1;
+    Lists L{tiles.data(),
             reinterpret_cast<const FdBlock *>(in.host_fd.data()), nt, nf, in.slots};
+    const uint64_t products0 = g_products;
     std::vector<uint64_t> fin(3 * nt + 2 * nf, 0), cnt(3 * nt + 2 * nf, 0), sig;
     // (tile, type) -> how often each sub-index occurs; FD_SUM rows counted on every sum
     // tile an item covers
@@ -286,15 +362,66 @@ static void check(const char *name, const NttBatchInfo &in, int field) {
             if (b.w_off + (uint64_t(in.host_wmap[e]) + 1) * N > E)
                 FAIL("block %zu window %u beyond the region", f, in.host_wmap[e]);
     }
-    printf("ok %s field %d items %zu tiles %zu fd %zu slots %llu\n", name, field, ni, nt, nf,
-           (unsigned long long)S);
+    // the products: standard pairs directly; every term X_J W_d(I,J) of every sum through
+    // its key spectrum, the window the block's table names and the sum's output rows
+    for (size_t ti = 0; ti < nt; ++ti) {
+        const NttTile &t = L.T[ti];
+        if (!(roles[ti] & ((1u << IT_P1) | (1u << IT_SMALL)))) continue;
+        if (t.p.blk >= shape.size()) FAIL("tile %zu block %u", ti, t.p.blk);
+        const char *e = pair_error(t.p, t.p, t.p, uint64_t(1) << t.logN, shape[t.p.blk].first,
+                                   shape[t.p.blk].second);
+        ++g_products;
+        if (e) FAIL("tile %zu: %s", ti, e);
+        g_rects[t.p.blk].push_back({t.p.out_bit0, t.p.out_len, uint64_t(t.p.key_bit0), t.p.key_len});
+    }
+    for (size_t f = 0; f < nf; ++f) {
+        const FdBlock &b = L.F[f];
+        const uint64_t N = fdN[f];
+        std::map<uint64_t, uint32_t> key_at, win_at;  // spectrum offset -> tile
+        for (size_t ti = 0; ti < nt; ++ti) {
+            const NttTile &t = L.T[ti];
+            if (t.fd != f || !(roles[ti] & (1u << IT_FD_P1))) continue;
+            (t.which ? win_at : key_at)[t.ws_off] = static_cast<uint32_t>(ti);
+        }
+        if (key_at.size() != b.Q) FAIL("block %zu: %zu key spectra for %u key tiles", f, key_at.size(), b.Q);
+        for (size_t ti = 0; ti < nt; ++ti) {
+            const NttTile &s = L.T[ti];
+            if (s.fd != f || !(roles[ti] & (1u << IT_FD_P3))) continue;
+            if (s.out >= b.P || s.jlo >= s.jhi || s.jhi > b.Q) FAIL("sum tile %zu ranges", ti);
+            if (s.p.blk >= shape.size()) FAIL("sum tile %zu block %u", ti, s.p.blk);
+            const uint64_t n = shape[s.p.blk].first, m = shape[s.p.blk].second;
+            for (uint32_t J = s.jlo; J < s.jhi; ++J) {
+                const auto k = key_at.find(b.x_off + uint64_t(J) * N);
+                const uint32_t wi = in.host_wmap[b.wmap + uint64_t(s.out) * b.Q + J];
+                const auto w = win_at.find(b.w_off + uint64_t(wi) * N);
+                if (k == key_at.end() || w == win_at.end()) FAIL("sum tile %zu term %u: spectra", ti, J);
+                const TilePair &kp = L.T[k->second].p, &wp = L.T[w->second].p;
+                if (kp.blk != s.p.blk || wp.blk != s.p.blk) FAIL("sum tile %zu term %u: block", ti, J);
+                const char *e = pair_error(kp, wp, s.p, N, n, m);
+                ++g_products;
+                if (e) FAIL("sum tile %zu (output %u) term %u: %s", ti, s.out, J, e);
+                g_rects[s.p.blk].push_back({s.p.out_bit0, s.p.out_len, uint64_t(kp.key_bit0), kp.key_len});
+            }
+        }
+    }
+    printf("ok %s field %d items %zu tiles %zu fd %zu slots %llu products %llu\n", name, field,
+           ni, nt, nf, (unsigned long long)S, (unsigned long long)(g_products - products0));
 }
 
 int main(int argc, char **argv) {
     g_reversed = argc > 1 && strcmp(argv[1], "reversed") == 0;
+    g_shifted = argc > 1 && strcmp(argv[1], "shifted") == 0;
     char line[512], name[128] = "";
     uint32_t max_slots = 0;
     std::vector<BatchBlock> groups[kNumFields];
+    // every block's products must tile its m x n plane exactly once (over all its launches)
+    const auto partitioned = [&](const char *what, uint32_t blk, uint64_t n, uint64_t m) {
+        const char *e = partition_error(g_rects[blk], n, m);
+        if (e) {
+            printf("FAIL %s: block %u: %s\n", what, blk, e);
+            ++g_fail;
+        }
+    };
     while (fgets(line, sizeof(line), stdin)) {
         if (line[0] == 'B') {
             sscanf(line + 2, "%127s %u", name, &max_slots);
@@ -342,8 +469,10 @@ int main(int argc, char **argv) {
                         ++g_fail;
                         continue;
                     }
-                    check(sn, info, c.field);
+                    check(sn, info, c.field, {{n, m}});
                 }
+                partitioned(name, 0, n, m);
+                g_rects.clear();
                 continue;
             }
             BatchBlock b;
@@ -361,7 +490,12 @@ int main(int argc, char **argv) {
                     ++g_fail;
                     continue;
                 }
-                check(name, info, f);
+                std::vector<std::pair<uint64_t, uint64_t>> shape;
+                for (const BatchBlock &b : groups[f]) shape.push_back({b.n, b.m});
+                g_rects.clear();
+                check(name, info, f, shape);
+                for (const BatchBlock &b : groups[f]) partitioned(name, b.index, b.n, b.m);
+                g_rects.clear();
             }
         }
     }
@@ -470,6 +604,8 @@ def test_every_wait_is_satisfied_by_earlier_items(checker):
     # every item type of the kernel occurred (IT_SMALL .. IT_FD_INV2)
     types = int(out.splitlines()[-1].split()[1], 16)
     assert types == (1 << 11) - 1, hex(types)
+    # every list's products were checked against the definition
+    assert all(int(line.split()[-1]) > 0 for line in oks)
     # the segmented and batched cases produced their launches, over several fields
     assert sum(1 for line in oks if "/segment" in line) >= 6 + 6
     assert {line.split()[3] for line in oks} >= {"1", "2", "3"}
@@ -487,3 +623,16 @@ def test_replay_rejects_a_list_run_backwards(checker):
                 if line.startswith("FAIL") and "waits for" in line}
     assert bad.returncode == 1
     assert set(names) - rejected == {"small"}, sorted(set(names) - rejected)
+
+
+def test_decomposition_rejects_a_shifted_window(checker):
+    # every seed window moved by one bit: each list's products no longer read the seed bits
+    # the definition names, so every case must be rejected
+    ok = subprocess.run([str(checker)], input=_cases(), capture_output=True, text=True,
+                        timeout=600)
+    bad = subprocess.run([str(checker), "shifted"], input=_cases(), capture_output=True,
+                         text=True, timeout=600)
+    names = {line.split()[1] for line in ok.stdout.splitlines() if line.startswith("ok ")}
+    rejected = {line.split()[1].rstrip(":") for line in bad.stdout.splitlines()
+                if line.startswith("FAIL") and "convolution index" in line}
+    assert bad.returncode == 1 and names and names <= rejected, sorted(names - rejected)
