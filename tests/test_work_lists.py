@@ -426,7 +426,7 @@ int main(int argc, char **argv) {
         if (line[0] == 'B') {
             sscanf(line + 2, "%127s %u", name, &max_slots);
             for (auto &g : groups) g.clear();
-        } else if (line[0] == 'X') {
+        } else if (line[0] == 'X' || line[0] == 'Y') {  // Y: a refused plan is no failure
             unsigned long long n, m;
             pa_opts o;
             memset(&o, 0, sizeof(o));
@@ -439,6 +439,10 @@ int main(int argc, char **argv) {
             o.path = path;
             PlanCfg cfg;
             const int rc = plan_resolve(n, m, &o, &cfg, false);
+            if (line[0] == 'Y' && rc != PA_OK) {
+                printf("refused %s rc %d\n", name, rc);
+                continue;
+            }
             if (rc != PA_OK || (cfg.path != PA_PATH_NTT31 && cfg.path != PA_PATH_NTT64)) {
                 printf("FAIL %s: plan n=%llu m=%llu rc %d path %d\n", name, n, m, rc, cfg.path);
                 ++g_fail;
@@ -519,6 +523,44 @@ def _batched_shapes(count, seed):
     n = np.floor(1e5 * 40.0 ** u).astype(np.int64)
     m = np.maximum(1, np.floor((0.01 + 0.49 * v) * n)).astype(np.int64)
     return list(zip(n.tolist(), m.tolist()))
+
+
+def _random_cases(count, seed):
+    # forced geometries and options drawn at random (sizes kept to a few million bits):
+    # one block per case, and every fifth case a batch of up to six blocks with the same
+    # options; refused plans are fine, every plan built must pass the replay
+    import random
+    rng = random.Random(seed)
+    out = []
+    for c in range(count):
+        path = rng.choice([NTT31, NTT31, NTT64])
+        prime = rng.choice([0, 28, 29, 31]) if path == NTT31 else 0
+        k = rng.choice([0, 0, 12, 13, 14, 15, 16, 17, 18])
+        fd = rng.choice([0, 1, 2, 2])
+        group = rng.choice([0, 0, 1, 2, 3, 5])
+        outer = rng.choice([0, 1, 2])
+        si, so = (rng.choice([0, 1, 2, 3, 5]), rng.choice([0, 1, 2, 4])) if fd == 2 and rng.random() < 0.3 else (0, 0)
+        slots = rng.choice([0, 0, 4, 5, 6])
+        blocks = []
+        for _ in range(rng.randint(2, 6) if c % 5 == 4 else 1):
+            n = int(10 ** rng.uniform(2, 6.5))
+            m = max(1, int(n * rng.uniform(0.001, 0.8)))
+            L = M = 0
+            if k:
+                N = 1 << k
+                if k >= 13 and rng.random() < 0.25:
+                    # equal tiles and several output tiles: the outer convolutions' shape
+                    L = M = N // 2
+                    n = max(n, 3 * L + rng.randint(0, L))
+                    m = max(m, 2 * M + rng.randint(1, M))
+                elif rng.random() < 0.5:
+                    M = rng.choice([N // 2, N // 4, N // 8, 64 * rng.randint(1, max(1, N // 128))])
+                    L = rng.choice([0, N - M, 32 * rng.randint(1, max(1, (N - M) // 32))])
+                    if L and L + M > N:
+                        L = 0
+            blocks.append(f"Y {n} {m} {path} {k} {L} {M} {fd} {group} {outer} {si} {so} {prime}")
+        out.append("\n".join([f"B random{c} {slots}", *blocks, "E"]))
+    return "\n".join(out) + "\n"
 
 
 def _cases():
@@ -636,3 +678,16 @@ def test_decomposition_rejects_a_shifted_window(checker):
     rejected = {line.split()[1].rstrip(":") for line in bad.stdout.splitlines()
                 if line.startswith("FAIL") and "convolution index" in line}
     assert bad.returncode == 1 and names and names <= rejected, sorted(names - rejected)
+
+
+def test_random_geometries(checker):
+    r = subprocess.run([str(checker)], input=_random_cases(400, 2024), capture_output=True,
+                       text=True, timeout=900)
+    lines = r.stdout.splitlines()
+    fails = [line for line in lines if line.startswith("FAIL")]
+    assert r.returncode == 0 and not fails, "\n".join(fails[:20]) + r.stderr[-2000:]
+    oks = [line for line in lines if line.startswith("ok ")]
+    refused = [line for line in lines if line.startswith("refused")]
+    # most draws are plannable, and they reach every kind of item
+    assert len(oks) > 300 and len(refused) < len(oks), (len(oks), len(refused))
+    assert int(lines[-1].split()[1], 16) == (1 << 11) - 1
