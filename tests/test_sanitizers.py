@@ -4,7 +4,7 @@ Three instrumented programs are built and run here:
 
 * the oracle (``oracle/pa_oracle.c``) with a driver that hands it buffers of exactly the
   sizes its interface states (a read or write one word past an end is reported), over
-  ragged shapes from one bit up, with 1 and 4 threads; the driver also checks that the
+  ragged shapes from one bit up, with 1 and 4 threads; the test program also checks that the
   threaded hash, the packed row evaluator and the bit-by-bit evaluator of the definition
   (Sec. 2.1, Eq. 1) agree, and that invalid arguments are refused;
 * the same oracle and driver under ThreadSanitizer (the threads write disjoint, 64-row
