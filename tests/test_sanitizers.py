@@ -12,9 +12,9 @@ Three instrumented programs are built and run here:
 * the CUDA library's host code (planner, work-list builder, descriptor filling): every
   ``csrc/*.cu`` compiled with the instrumentation on its host side (device code as PTX
   only, never run), driven through the host-only entry points: ``pa_plan_query`` over
-  shapes from one bit to 1e10 bits, every path and every option family, including
-  refused and invalid ones, ``pa_seed_from_eq1`` on exact-size buffers and
-  ``pa_fft_rounding_bound``.
+  shapes from one bit to 1e10 bits and at the interface's 2^40-bit limit, every path and
+  every option family, including refused and invalid ones, ``pa_seed_from_eq1`` on
+  exact-size buffers and ``pa_fft_rounding_bound``.
 
 A finding aborts the program with its report and the test fails with it. One test plants
 an off-by-one read in a copy of the oracle and checks the instrumented build reports it,
@@ -171,6 +171,15 @@ int main(void) {
                           {PA_PATH_NTT64, 3}, {PA_PATH_NTT64, 6}};
     for (unsigned i = 0; i < sizeof(big) / sizeof(big[0]); ++i)
         if (query(n, m, big[i][0], big[i][1], &ok, &refused)) return 1;
+    /* the largest sizes the interface accepts (2^40 bits): every path and option family
+       plans or refuses at once, with no overflow in the geometry arithmetic */
+    const uint64_t T = (uint64_t)1 << 40;
+    const uint64_t edge[][2] = {{T, 1}, {1, T}, {T, T}, {T, T / 10}, {T - 1, 64}, {64, T - 1},
+                                {T / 2, T / 2}, {(uint64_t)1 << 36, (uint64_t)1 << 33}};
+    for (unsigned s = 0; s < sizeof(edge) / sizeof(edge[0]); ++s)
+        for (int path = PA_PATH_AUTO; path <= PA_PATH_BLOCK_FP8; ++path)
+            for (int v = 0; v <= 12; ++v)
+                if (query(edge[s][0], edge[s][1], path, v, &ok, &refused)) return 1;
     /* invalid sizes */
     pa_plan_desc d;
     if (pa_plan_query(0, 5, NULL, &d) == PA_OK || pa_plan_query(5, 0, NULL, &d) == PA_OK ||
