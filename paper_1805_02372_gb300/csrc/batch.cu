@@ -706,7 +706,8 @@ int pa_batch_run(pa_batch_t b, const pa_block *blocks, size_t count, void *strea
                     PA_CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
                 cudaGraph_t g = nullptr;
                 PA_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-                int rc = enqueue_all(b, b->cap_stream);
+                // the capture ends on every path, an exception in the enqueue included
+                int rc = guarded([&] { return enqueue_all(b, b->cap_stream); });
                 cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
                 if (rc != PA_OK) {
                     if (g) cudaGraphDestroy(g);
