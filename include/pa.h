@@ -258,18 +258,29 @@ typedef struct pa_batch_s *pa_batch_t;
 
 /* Plan a batch for these (n_i, m_i) shapes: path and tiles per block chosen by the
  * autotuner, one persistent work list, workspace allocated once. Only the
- * shapes are read from blocks[]; pointers may be NULL at planning time. */
+ * shapes are read from blocks[]; pointers may be NULL at planning time. opts may be NULL
+ * (autotuned); a forced path applies to every block. PA_ERR_INVALID for a null blocks
+ * or out, count 0 or above 2^24, or a block with n or m of 0 or above 2^40 bits (all
+ * checked before the autotuner's calibration); a block's planning status
+ * (PA_ERR_UNSUPPORTED, PA_ERR_PRECISION) if a forced path cannot take it; PA_ERR_NOMEM or
+ * PA_ERR_CUDA if the workspace cannot be set up. */
 int pa_batch_plan(const pa_block *blocks, size_t count, const pa_opts *opts, pa_batch_t *out);
 
 /* Run a planned batch with these buffers (same shapes, in the same order). The
  * launch sequence is captured once in a CUDA graph and replayed when the buffer
  * pointers and stream are unchanged. rep may be NULL; when it is not, the call
- * synchronises the stream to fill it. */
+ * synchronises the stream to fill it and returns the device status (PA_ERR_TIMEOUT if a
+ * bounded wait gave up). PA_ERR_INVALID for a null batch or blocks, a count or a shape
+ * that differs from the plan's, or a null buffer; PA_ERR_ALIGN for a buffer not 16-byte
+ * aligned; PA_ERR_CUDA if a launch fails. */
 int pa_batch_run(pa_batch_t batch, const pa_block *blocks, size_t count, void *stream,
                  pa_report *rep);
 
 /* Same as pa_batch_run with HOST bit buffers: copies every key and seed to device
- * staging owned by the batch, runs, copies the outputs back, synchronises. */
+ * staging owned by the batch (allocated on the first call), runs, copies the outputs
+ * back, synchronises. Host buffers need no alignment. PA_ERR_INVALID for a mismatched
+ * block list or a null buffer; PA_ERR_NOMEM if the staging cannot be allocated; otherwise
+ * as pa_batch_run. */
 int pa_batch_run_host(pa_batch_t batch, const pa_block *host_blocks, size_t count, void *stream,
                       pa_report *rep);
 
@@ -305,6 +316,8 @@ void pa_batch_destroy(pa_batch_t batch);
 int pa_hash_batched(const pa_block *blocks, size_t count, void *stream, pa_report *rep);
 
 /* ---- Serving: continuous batching of requests arriving by device memory ----
+ * (Sec. 3: the corrected keys come from reconciliation already in device memory, and
+ * blocks are hashed in parallel batches.)
  * A server owns `slots` CUDA streams and a device-memory budget. Submitted requests
  * queue in FIFO order; each poll retires finished waves and, for every free slot, plans
  * the requests waiting at that moment as one batch (one persistent launch for the
@@ -328,12 +341,23 @@ typedef struct {
 
 typedef struct pa_server_s *pa_server_t;
 
-/* Creates the streams and calibrates the autotuner (synchronous, once per device). */
+/* Creates the streams and calibrates the autotuner (synchronous, once per device). opts
+ * may be NULL (defaults). PA_ERR_INVALID for a null out; PA_ERR_NOMEM; PA_ERR_CUDA if a
+ * stream cannot be created; the autotuner's status if its calibration fails. */
 int pa_server_create(const pa_server_opts *opts, pa_server_t *out);
-/* Queues one request; thread-safe; does not launch (poll does). */
+/* Queues one request; thread-safe; does not launch (poll does). The request is copied;
+ * its buffers are not read until its wave runs. PA_ERR_INVALID for a null server or
+ * request, n or m of 0 or above 2^40 bits, or a null buffer; PA_ERR_NOMEM if the queue
+ * cannot grow. */
 int pa_server_submit(pa_server_t server, const pa_block *request, uint64_t tag);
-/* Retires finished waves into done[0..max) (count = entries written), then admits. */
+/* Retires finished waves into done[0..max) (count = entries written; a wave is reported
+ * whole or not at all), then admits waiting requests into free slots. Each completion
+ * carries its wave's status. A wave that cannot be planned leaves its requests queued,
+ * in order, and poll returns the plan's status (the next poll tries again).
+ * PA_ERR_INVALID for a null server or count, or done = NULL with max > 0. */
 int pa_server_poll(pa_server_t server, pa_completion *done, size_t max, size_t *count);
+/* Requests waiting and requests in flight; either pointer may be NULL. PA_ERR_INVALID
+ * for a null server. */
 int pa_server_pending(pa_server_t server, uint64_t *queued, uint64_t *in_flight);
 /* Counters of a server since its creation. */
 typedef struct {
@@ -345,6 +369,7 @@ typedef struct {
     uint64_t waves_held_back;     /* wave formations undone by the memory budget             */
     uint64_t reserved[4];
 } pa_server_stats;
+/* PA_ERR_INVALID for a null server or out. */
 int pa_server_get_stats(pa_server_t server, pa_server_stats *out);
 /* Waits for the waves in flight, then releases everything. */
 void pa_server_destroy(pa_server_t server);
