@@ -163,7 +163,7 @@ int pa_plan_ex(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_t *out);
  * pa_plan_ex; out is written only on PA_OK. */
 int pa_plan_query(uint64_t n, uint64_t m, const pa_opts *opts, pa_plan_desc *out);
 
-/* Describe a created plan. */
+/* Describe a created plan. PA_ERR_INVALID for a null plan or out. */
 int pa_plan_describe(pa_plan_t plan, pa_plan_desc *out);
 
 /* Release the plan and its workspace (synchronises the plan's last stream). */
@@ -171,30 +171,38 @@ void pa_plan_destroy(pa_plan_t plan);
 
 /* y = T x mod 2 (Sec. 2.3 Step 1/2 with the decomposition of Sec. 3).
  * seed_bits, key_bits, out_bits: device pointers, 16-byte aligned.
- * stream: a cudaStream_t (NULL = legacy default stream). Asynchronous. */
+ * stream: a cudaStream_t (NULL = legacy default stream). Asynchronous: kernel-side
+ * errors (a bounded wait that gave up) are read afterwards with pa_plan_status.
+ * PA_ERR_INVALID for a null plan or buffer; PA_ERR_ALIGN for a buffer not 16-byte
+ * aligned; PA_ERR_CUDA if a launch fails; PA_ERR_NOMEM if the first call on a device
+ * cannot build its twiddle tables. */
 int pa_hash(pa_plan_t plan, const uint64_t *seed_bits, const uint64_t *key_bits,
             uint64_t *out_bits, void *stream);
 
 /* The same hash from and to HOST buffers: copies the key and seed to the plan's
- * device staging, hashes, copies the result back and synchronises the stream. */
+ * device staging (allocated on the first call), hashes, copies the result back and
+ * synchronises the stream. Host buffers need no alignment. Errors as pa_hash, plus
+ * PA_ERR_NOMEM if the staging cannot be allocated. */
 int pa_hash_host(pa_plan_t plan, const uint64_t *seed_host, const uint64_t *key_host,
                  uint64_t *out_host, void *stream);
 
 /* Worst |v - rint(v)| seen in the plan's last call, with the proven bound (synchronises the
  * plan's stream): the FFT path's rounded convolution values, and the block FP8 path's
  * tensor-core sums scaled to counts (proven exact, bound 0, measured every run). The
- * integer paths report 0. */
+ * integer paths report 0. The residual is cleared for the next call. bound may be NULL.
+ * PA_ERR_INVALID for a null plan or residual; PA_ERR_CUDA if the read fails. */
 int pa_last_residual(pa_plan_t plan, double *residual, double *bound);
 
 /* The proven bound on |v - rint(v)| used by the FFT path for a tile of transform
  * size 2^log2_transform, key sub-block tile_in and output sub-block tile_out, for
  * FP32 (fp64 = 0) or FP64 butterflies. A tile is used only if its bound is < 1/2.
- * Host only. */
+ * Host only. PA_ERR_INVALID for a null bound or log2_transform outside 1..40. */
 int pa_fft_rounding_bound(uint32_t log2_transform, uint64_t tile_in, uint64_t tile_out, int fp64,
                           double *bound);
 
 /* Device-side status of the plan's last call: PA_OK, or PA_ERR_TIMEOUT if a
- * bounded wait in a kernel gave up (synchronises the plan's stream). */
+ * bounded wait in a kernel gave up (synchronises the plan's stream). PA_ERR_INVALID for a
+ * null plan; PA_ERR_CUDA if the read fails. */
 int pa_plan_status(pa_plan_t plan);
 
 /* y = T x mod 2 on the direct path WITHOUT allocating anything. The paper has no
@@ -384,10 +392,13 @@ typedef struct {
     double total_ms;           /* summed event-to-event device time                       */
 } pa_kernel_time;
 
-/* enable != 0 clears previous records and starts recording; 0 stops. */
+/* enable != 0 clears previous records and starts recording; 0 stops. PA_ERR_INVALID for a
+ * null plan. */
 int pa_plan_profile(pa_plan_t plan, int enable);
 
-/* Per-kernel totals (synchronises on the recorded events). count = entries written. */
+/* Per-kernel totals (synchronises on the recorded events). count = entries written (at
+ * most max; out may be NULL with max = 0). PA_ERR_INVALID for a null plan or max < 0;
+ * PA_ERR_CUDA if an event cannot be read. The batch forms behave the same. */
 int pa_plan_kernel_times(pa_plan_t plan, pa_kernel_time *out, int max, int *count);
 
 int pa_batch_profile(pa_batch_t batch, int enable);
@@ -400,7 +411,8 @@ int pa_batch_kernel_times(pa_batch_t batch, pa_kernel_time *out, int max, int *c
  * which = 2: an mbarrier expecting bytes that never arrive) and stores the kernel's
  * device status in *device_status; PA_ERR_TIMEOUT is the expected value. Every bounded
  * device wait gives up after 4 s (plus 0.5 s for copies in flight), so this takes about
- * four to five seconds; synchronises the device. The GPU context remains usable. */
+ * four to five seconds; synchronises the device. The GPU context remains usable.
+ * PA_ERR_INVALID for another `which` or a null device_status. */
 int pa_selftest(int which, int *device_status);
 
 /* Measured issue-rate peaks for the roofline of the integer paths (no counterpart in the
@@ -425,7 +437,8 @@ int pa_selftest(int which, int *device_status);
  *           groups alike (one operation = one butterfly).
  * *ops_per_s: the fastest of three launches of about 20 ms (after a warm-up);
  * *ms (nullable): that launch's device time. Synchronous; allocates at most 4 KB of device
- * memory for the duration of the call. PA_ERR_INVALID for another `which`. */
+ * memory for the duration of the call. PA_ERR_INVALID for another `which` or a null
+ * ops_per_s. */
 #define PA_PEAK_NTT_BUTTERFLY 1
 #define PA_PEAK_NTT_MULADD 2
 #define PA_PEAK_SHIFT_AND 3
