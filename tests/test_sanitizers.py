@@ -274,7 +274,8 @@ def test_planted_overread_is_reported(tmp_path, oracle_text):
 
 
 @pytest.fixture(scope="module")
-def planner_exe(tmp_path_factory):
+def san_lib(tmp_path_factory):
+    """Every csrc/*.cu with host-side ASan + UBSan (device code as PTX only), as one library."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     tmp = tmp_path_factory.mktemp("plansan")
     if not os.path.exists(nvcc) or not shutil.which("gcc") or not _gcc_can(ASAN, tmp):
@@ -297,9 +298,15 @@ def planner_exe(tmp_path_factory):
     r = _run([nvcc, "-gencode", "arch=compute_103a,code=compute_103a", "-shared",
               "-Xcompiler", "-fsanitize=address,-fsanitize=undefined", "-o", str(lib)] + objs)
     assert r.returncode == 0, r.stderr[-3000:]
+    return lib
+
+
+@pytest.fixture(scope="module")
+def planner_exe(san_lib):
+    tmp = san_lib.parent
     (tmp / "driver.c").write_text(PLANNER_DRIVER)
     exe = tmp / "driver"
-    r = _run(["gcc", "-g", "-O1"] + ASAN + ["-I", INCLUDE, str(tmp / "driver.c"), str(lib),
+    r = _run(["gcc", "-g", "-O1"] + ASAN + ["-I", INCLUDE, str(tmp / "driver.c"), str(san_lib),
               "-Wl,-rpath," + str(tmp), "-o", str(exe)])
     assert r.returncode == 0, r.stderr
     return exe
@@ -310,3 +317,24 @@ def test_planner_under_asan_ubsan(planner_exe):
     assert r.returncode == 0 and r.stdout.startswith("ok "), r.stdout[-2000:] + r.stderr[-6000:]
     ok, refused = int(r.stdout.split()[1]), int(r.stdout.split()[3])
     assert ok > 300 and refused > 100
+
+
+def test_work_list_builder_under_asan_ubsan(san_lib):
+    # The persistent kernel's work-list builder for batches of many blocks and small slot
+    # counts (reached by no single-block query): the replay program of
+    # test_work_lists.py, linked against the instrumented library, over its fixed cases
+    # and a shorter random sweep.
+    import test_work_lists as wl
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    tmp = san_lib.parent
+    src, exe = tmp / "check.cu", tmp / "check"
+    src.write_text(wl.CHECKER)
+    r = _run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O1",
+              "-gencode", "arch=compute_103a,code=compute_103a", "-I", INCLUDE, "-I", CSRC,
+              "-Xcompiler", "-fsanitize=address,-fsanitize=undefined,-fno-sanitize-recover=all,-g",
+              "-Xlinker", "-rpath=" + str(tmp), str(src), str(san_lib), "-o", str(exe)])
+    assert r.returncode == 0, r.stderr[-3000:]
+    cases = wl._cases() + wl._random_cases(40, 77)
+    run = _run([str(exe)], input=cases, env=SAN_ENV, timeout=1200)
+    tail = run.stdout.splitlines()[-1] if run.stdout else ""
+    assert run.returncode == 0 and tail.endswith("fails 0"), run.stdout[-2000:] + run.stderr[-6000:]
