@@ -150,7 +150,9 @@ int block_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c) {
     if (b != 128 && b != 256 && b != 512) return PA_ERR_INVALID;
     c->b = b;
     const uint64_t NI = kTileOutputs / b;
-    c->grid_x = static_cast<uint32_t>(ceil_div(ceil_div(m, b), NI));
+    const uint64_t gx = ceil_div(ceil_div(m, b), NI);
+    if (gx > 0x7fffffffu) return PA_ERR_UNSUPPORTED;  // checked before narrowing
+    c->grid_x = static_cast<uint32_t>(gx);
     const uint64_t klen = n + b * (NI - 1) + 64;  // contraction length per output tile
     const uint64_t target = uint64_t(kNumSMsGB300) * 8 * 4;
     uint64_t kc = ceil_div(klen * c->grid_x, target);
@@ -158,7 +160,7 @@ int block_plan(uint64_t n, uint64_t m, const pa_opts *o, BlockCfg *c) {
     if (kc > 16384) kc = 16384;
     c->kc = kc;
     const uint64_t gy = ceil_div(klen, kc);
-    if (gy > 65535 || c->grid_x > 0x7fffffffu) return PA_ERR_UNSUPPORTED;
+    if (gy > 65535) return PA_ERR_UNSUPPORTED;
     c->grid_y = static_cast<uint32_t>(gy);
     c->xr_words = ceil_div(n, 32);
     c->xr_words_pad = round_up(c->xr_words, 4);
