@@ -309,3 +309,20 @@ def test_invalid_arguments_refused_before_any_cuda_call(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert run.returncode == 0 and run.stdout.strip().endswith("done 0"), run.stdout + run.stderr
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++11")])
+def test_header_compiles_strictly(tmp_path, compiler, std):
+    # include/pa.h is a C interface: plain C99 and C++11 with every warning an error
+    import shutil
+    import subprocess
+    if not shutil.which(compiler):
+        pytest.skip(f"{compiler} not available")
+    src = tmp_path / ("h.c" if compiler == "gcc" else "h.cpp")
+    src.write_text('#include "pa.h"\n'
+                   "int main(void) { pa_plan_desc d; pa_opts o; pa_block b; pa_report r;\n"
+                   "  (void)d; (void)o; (void)b; (void)r; return pa_version() > 0 ? 0 : 1; }\n")
+    r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), "-c", str(src), "-o", os.devnull],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
